@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the transformer density-operator VMC hot path on GB300.
+
+Workload (the headline configuration): dissipative transverse-field Ising chain N=16 (PBC, V=2, g=1,
+gamma=1), transformer with token embedding, d=64, 8 heads, 4 layers, MLP 4d (P = 198,274 parameters,
+N(0, 0.02) seed 0), 16384 Metropolis chains per GPU, one sample per chain per step.
+
+One step = one VMC step through the C ABI: one Metropolis sweep (2N proposals per chain, tdo_sample),
+then tdo_sr_step on the chain states (connections, log rho of every connected configuration, L_loc and
+cost, cost gradient, log-derivatives, SR conjugate-gradient solve, parameter update).
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded sample of the same step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_20723_gb300 import synth  # noqa: E402
+
+N_SITES, D, HEADS, LAYERS, MLP = 16, 64, 8, 4, 4
+N_SAMPLES = 16384
+LR, SHIFT = 0.0061, 1e-3
+METRIC = "VMC steps/s and log rho evals/s (N=16, d=64, 4 layers)"
+WORKLOAD = "ising_n16_d64_l4_h8_mlp4_ns16384"
+
+
+def flops_per_sequence(n=N_SITES, d=D, layers=LAYERS, r=MLP) -> float:
+    """Algorithmic FLOPs of one sequence forward: per layer QKV 6Nd^2, W^O 2Nd^2, scores and A V 4N^2 d,
+    MLP 4 r N d^2 (embedding lookup, pooling and head are negligible)."""
+    return layers * (8.0 * n * d * d + 4.0 * n * n * d + 4.0 * r * n * d * d)
+
+
+F_EVAL = 2.0 * flops_per_sequence()   # one log rho = both orders of the doubled configuration
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_alu_peak_tflops(sm_mhz: float = 2070.0) -> float:
+    """CUDA-core FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows]
+        smax = float(rows[0][2])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].strip()[:1].isdigit())
+                if any(r[3].strip()[:1].isdigit() for r in rows) else None}
+
+
+# ---------------------------------------------------------------------------------------------- ours
+def run_ours(args) -> dict | None:
+    import torch
+    import torch.distributed as dist
+
+    from paper_2502_20723_gb300 import tdo
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2502_20723_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    prob = synth.ising_chain(N_SITES, V=2.0, g=1.0, gamma=1.0)
+    spec = synth.model_spec(D, HEADS, LAYERS, MLP)
+    theta = synth.init_params(spec, seed=0)
+    stream = torch.cuda.current_stream()
+    ctx = tdo.Context(prob, spec, theta, args.precision, stream=stream.cuda_stream)
+    s0, s1 = synth.random_configs(N_SITES, N_SAMPLES, seed=1000 + rank)
+    sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
+    sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
+    seed = 12345 + rank
+    counter = 0
+    ctx.sample(sig, sigp, args.burn_in, seed, counter)     # burn-in (untimed)
+    counter += args.burn_in * 2 * N_SITES
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def step():
+        nonlocal counter
+        ctx.sample(sig, sigp, 1, seed, counter)
+        counter += 2 * N_SITES
+        return ctx.sr_step(sig, sigp, LR, SHIFT)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-step CUDA events on the launching stream, L2 flushed between steps
+    ctx.timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    costs = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            costs.append(step())
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = sum(step_ms)
+    groups = {}
+    for g in ("fwd", "sample", "bwd_vjp", "bwd_jac", "conn", "lloc", "sr", "update"):
+        ms, n = ctx.timing_read(g)
+        groups[g] = {"ms": ms / args.steps, "launches": n / args.steps}
+    launches = int(sum(v["launches"] for v in groups.values()) * args.steps)
+    ctx.timing(False)
+
+    # rows evaluated by the forward per step (from one L_loc call on the current samples)
+    lloc_rows = int(ctx.connections(sig, sigp)[0].sum().item())
+    fwd_evals = lloc_rows
+    sample_evals = N_SAMPLES * (1 + 2 * N_SITES)
+
+    t_max = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    t_max = float(t_max.item())
+
+    # ---- end to end through the public API with host buffers (copies inside the timed region)
+    hs = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
+    hp = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
+    hs.copy_(sig.cpu())
+    hp.copy_(sigp.cpu())
+    hs_np, hp_np = hs.numpy(), hp.numpy()
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.sample(hs_np, hp_np, 1, seed, counter)          # H2D chains, D2H chains
+        counter += 2 * N_SITES
+        ctx.sr_step(hs_np, hp_np, LR, SHIFT)                # H2D samples, D2H cost
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_s = float(e2e_t.item())
+
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+
+    # ---- roofline of the dominant kernel group
+    peaks = measured_peaks()
+    dom = max(groups, key=lambda g: groups[g]["ms"])
+    clocks = clk.summary()
+    if dom in ("fwd", "sample", "bwd_vjp", "bwd_jac"):
+        units = {"fwd": fwd_evals, "sample": sample_evals, "bwd_vjp": lloc_rows, "bwd_jac": N_SAMPLES}[dom]
+        per_unit = {"fwd": F_EVAL, "sample": F_EVAL, "bwd_vjp": 2 * F_EVAL, "bwd_jac": 4 * F_EVAL}[dom]
+        flops = units * per_unit
+        achieved = flops / (groups[dom]["ms"] * 1e-3) / 1e12
+        if args.precision == "bf16" and dom in ("fwd", "sample"):
+            peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+            roof = {"bound": "tensor", "peak_source": "MEASURED_PEAKS bf16_tflops_sustained"}
+        else:
+            peak = fp32_alu_peak_tflops()
+            roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+        roof.update({"kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "algorithmic_per_launch": flops / max(1, groups[dom]["launches"])})
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": float(peaks.get("hbm_gbs", 6781.4)),
+                "unit": "GB/s", "frac": None, "traffic": None}
+    sr_bytes = None
+    res = {
+        "metric": METRIC,
+        "value": world * args.steps / (t_max * 1e-3),
+        "unit": "VMC steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "bf16",
+        "data": "synthetic (seeded random initial chains, Metropolis-sampled; random-init N(0,0.02) weights)",
+        "config": {"workload": WORKLOAD, "n_sites": N_SITES, "d_model": D, "heads": HEADS, "layers": LAYERS,
+                   "mlp_ratio": MLP, "samples_per_gpu": N_SAMPLES, "params": ctx.P, "precision": args.precision,
+                   "sweeps_per_step": 1, "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "logrho_evals_per_s": (fwd_evals + sample_evals) * world * args.steps / (t_max * 1e-3),
+        "logrho_evals_per_s_fwd_kernel": fwd_evals / (groups["fwd"]["ms"] * 1e-3) if groups["fwd"]["ms"] else None,
+        "rows_per_step": {"lloc_rows": lloc_rows, "sample_evals": sample_evals},
+        "breakdown_ms_per_step": {g: round(v["ms"], 3) for g, v in groups.items()},
+        "cost_last": costs[-1],
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "VMC steps/s",
+                "h2d_bytes_per_step": 4 * 4 * N_SAMPLES, "d2h_bytes_per_step": 2 * 4 * N_SAMPLES + 8},
+        "gpu_launches": launches,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+    return res
+
+
+# ---------------------------------------------------------------------------------- oracle on the CPU
+def _timed(fn, count: int, target_s: float, grow: int = 8):
+    """Run fn(count); if it took well under target_s, rerun once with a count scaled to the target.
+    Returns (seconds per unit, count used)."""
+    t0 = time.perf_counter()
+    fn(count)
+    dt = time.perf_counter() - t0
+    if dt < 0.5 * target_s:
+        count = int(count * min(grow, max(1.0, target_s / max(dt, 1e-3))))
+        t0 = time.perf_counter()
+        fn(count)
+        dt = time.perf_counter() - t0
+    return dt / count, count
+
+
+def oracle_step_estimate(budget_s: float) -> dict:
+    """Time the FP64 oracle on a bounded sample of one VMC step of the workload and extrapolate.
+    Parts: Metropolis proposals (one log rho each), the local estimator and gradient over each sample's
+    connected configurations, the log-derivatives.  The SR solve is not included: the oracle's dense
+    Cholesky needs P^2 = 3.9e10 doubles (315 GB) at this P, so its time is unavailable."""
+    import torch
+
+    from oracle import estimators as E, transformer as T
+
+    prob = synth.ising_chain(N_SITES, V=2.0, g=1.0, gamma=1.0)
+    spec = synth.model_spec(D, HEADS, LAYERS, MLP)
+    th = synth.init_params(spec, seed=0)
+
+    def ev(k):
+        a, b = synth.random_configs(N_SITES, k, seed=1)
+        T.log_rho_np(spec, th, a, b, N_SITES)
+
+    def gr(k):
+        a, b = synth.random_configs(N_SITES, k, seed=2)
+        E.grad_estimator(prob, spec, th, a, b)
+
+    def jc(k):
+        a, b = synth.random_configs(N_SITES, k, seed=3)
+        E.jacobian(spec, th, a, b, N_SITES)
+
+    t_eval, nf = _timed(ev, 128, 0.35 * budget_s)
+    t_grad, ng = _timed(gr, 4, 0.4 * budget_s)
+    t_jac, nj = _timed(jc, 2, 0.25 * budget_s)
+    step_s = N_SAMPLES * (2 * N_SITES * t_eval + t_grad + t_jac)
+    return {"step_s": step_s, "cores": torch.get_num_threads(),
+            "sample": (f"{nf} log rho evals, gradient estimator on {ng} samples (with their connected "
+                       f"configurations), log-derivatives of {nj} samples; extrapolated to 16384 samples x "
+                       f"(32 Metropolis proposals + estimator + gradient + log-derivatives); SR solve excluded "
+                       f"(oracle dense Cholesky infeasible at P=198,274)")}
+
+
+def cpu_baseline(budget_s: float) -> dict:
+    est = oracle_step_estimate(budget_s)
+    return {"value": 1.0 / est["step_s"], "unit": "VMC steps/s", "cores": est["cores"], "kind": "oracle",
+            "sample": est["sample"]}
+
+
+def run_reference(args) -> dict | None:
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    budget = max(3.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_step_estimate(budget)
+    est_steps = [oracle_step_estimate(budget) for _ in range(args.steps)]
+    step_s = statistics.mean(e["step_s"] for e in est_steps)
+    v = 1.0 / step_s
+    return {"metric": METRIC, "value": v, "unit": "VMC steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n_sites": N_SITES, "d_model": D, "heads": HEADS, "layers": LAYERS,
+                       "mlp_ratio": MLP, "samples_per_gpu": N_SAMPLES, "parallelism": "CPU oracle"},
+            "cpu_baseline": {"value": v, "unit": "VMC steps/s", "cores": est_steps[0]["cores"], "kind": "oracle",
+                             "sample": est_steps[0]["sample"]},
+            "e2e": {"value": v, "unit": "VMC steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_kernel_case(args) -> None:
+    """One call of one kind on the workload's model with a reduced sample count (for ncu captures):
+    fwd (log rho of all connected rows), grad (gradient backward), jac (log-derivatives), sample (one
+    sweep), sr (CG solve on the log-derivatives).  Runs the call twice (first warms up)."""
+    import torch
+
+    from paper_2502_20723_gb300 import build, tdo
+    build.build()
+    prob = synth.ising_chain(N_SITES, V=2.0, g=1.0, gamma=1.0)
+    spec = synth.model_spec(D, HEADS, LAYERS, MLP)
+    ctx = tdo.Context(prob, spec, synth.init_params(spec, seed=0), args.precision)
+    s0, s1 = synth.random_configs(N_SITES, args.case_samples, seed=1)
+    sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
+    sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
+    ctx.sample(sig, sigp, 1, 1, 0)
+    cnt, cs, cp, _ = ctx.connections(sig, sigp)
+    rows_s = torch.cat([cs[i, :cnt[i]] for i in range(len(cnt))]).contiguous()
+    rows_p = torch.cat([cp[i, :cnt[i]] for i in range(len(cnt))]).contiguous()
+    for _ in range(2):
+        if args.kernel_case == "fwd":
+            ctx.log_rho(rows_s, rows_p)
+        elif args.kernel_case == "grad":
+            ctx.grad(sig, sigp)
+        elif args.kernel_case == "jac":
+            ctx.jacobian(sig, sigp)
+        elif args.kernel_case == "sample":
+            ctx.sample(sig, sigp, 1, 1, 0)
+        elif args.kernel_case == "sr":
+            g, _ = ctx.grad(sig, sigp)
+            O = ctx.jacobian(sig, sigp)
+            ctx.sr_solve(O, g, SHIFT, tol=1e-8, max_iter=50)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": args.kernel_case, "samples": args.case_samples, "rows": int(len(rows_s))}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--burn-in", type=int, default=4)
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", default=None, choices=["fwd", "grad", "jac", "sample", "sr"],
+                    help="run one call of one kind on a reduced sample count (profiling) and exit")
+    ap.add_argument("--case-samples", type=int, default=1024)
+    args = ap.parse_args()
+    if args.kernel_case:
+        run_kernel_case(args)
+        return
+    args.warmup = max(args.warmup, 3)
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

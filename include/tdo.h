@@ -1,0 +1,172 @@
+/*
+ * tdo.h — C ABI of the GB300 (sm_103a) transformer density-operator library (libtdo.so).
+ *
+ * The method (arxiv 2502.20723): the density operator of an open spin chain is vectorised as a state
+ * in the doubled Hilbert space, |rho>> = sum rho(s, s') |s>|s'> (vectorisation appendix), and its
+ * matrix elements are given by a transformer: log rho(s, s') = log(exp z(s,s') + conj exp z(s',s))
+ * (Eq. log_sum_exp_conjugate).  The steady state minimises Cost = ||Lhat rho||^2 / ||rho||^2
+ * (Eq. lossnetk) where Lhat is the vectorised Lindbladian (Eq. VecLin), estimated by Metropolis
+ * sampling of |rho|^2 and the local estimator L_loc, and optimised by stochastic reconfiguration.
+ *
+ * Conventions for every entry point
+ *  - Configurations: a doubled configuration (s, s') is two uint32 words; bit i is site i; bit value 0
+ *    is |0> (sigma^z = +1), 1 is |1> (sigma^z = -1); sigma^- = |1><0|.  N <= 32.
+ *  - Buffers are owned by the caller.  Every data pointer may be a device pointer or a host pointer
+ *    (pageable or pinned); the library detects host memory and stages it through its own device
+ *    workspace.  Calls are ordered on the context's stream; a call with a host output (or a host
+ *    pointer in any argument) synchronises that stream before returning, a call with only device
+ *    pointers is asynchronous.
+ *  - log rho values are float pairs (re, im), the imaginary part in (-pi, pi] (principal branch).
+ *  - Parameters theta: a flat FP64 vector in this order (rows = input features, row-major):
+ *      token embedding E[4][d] (token = 2*bit(first channel) + bit(second channel)), or
+ *        conv embedding Wc1[2][2][C1], bc1[C1], Wc2[2][C1][d], bc2[d];
+ *      per layer: Wq, Wk, Wv, Wo [d][d] (no bias); if mlp_ratio r > 0: W1[d][r d], b1[r d], W2[r d][d], b2[d];
+ *      head Wh[d][2], bh[2].
+ *  - Every call returns a tdo_status; tdo_last_error() gives a message.  No exception crosses the ABI.
+ *    A context is used by one host thread at a time.
+ */
+#ifndef TDO_H
+#define TDO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdo_ctx tdo_ctx;
+
+typedef enum {
+  TDO_OK = 0,
+  TDO_EINVAL = -1,        /* bad argument (null pointer, size out of range, inconsistent spec) */
+  TDO_ENOMEM = -2,        /* device allocation failed */
+  TDO_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed */
+  TDO_ENUMERIC = -4,      /* a non-finite value was produced (e.g. rho = 0 exactly, NaN parameters) */
+  TDO_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
+  TDO_EUNSUPPORTED = -6   /* valid request outside what the kernels implement (e.g. N > 32) */
+} tdo_status;
+
+enum { TDO_EMBED_TOKEN = 0, TDO_EMBED_CONV = 1 };
+enum { TDO_FP32 = 0, TDO_BF16 = 1 };
+
+/* Problem statement: a chain of N spins, a Hamiltonian given as a sum of real multiples of Pauli strings
+ * on at most two sites, and single-site jump operators with rates (Eq. Lindblad / Eq. VecLin). */
+typedef struct {
+  int n_sites;                /* N, 1..32 */
+  int n_terms;                /* Hamiltonian terms */
+  const int *term_sites;      /* [n_terms][2] site indices; second entry -1 for a single-site term */
+  const char *term_paulis;    /* [n_terms][2] in {'I','X','Y','Z'} (second ignored when its site is -1) */
+  const double *term_coef;    /* [n_terms] real coefficients */
+  int n_jumps;                /* jump operators */
+  const int *jump_site;       /* [n_jumps] */
+  const double *jump_op;      /* [n_jumps][2][2][2]: L[row][col] as (re, im), basis (|0>, |1>) */
+  const double *jump_rate;    /* [n_jumps] gamma_i >= 0 */
+} tdo_problem;
+
+/* Transformer hyper-parameters (architecture appendix). */
+typedef struct {
+  int embed;                  /* TDO_EMBED_TOKEN or TDO_EMBED_CONV */
+  int conv_channels;          /* C1 for the conv embedding */
+  int d_model;                /* 16, 32 or 64 */
+  int n_heads;                /* divides d_model; head dim <= 16 */
+  int n_layers;               /* 1..8 */
+  int mlp_ratio;              /* 0 (the paper's block: no MLP) or 1..4 */
+  int precision;              /* TDO_FP32 or TDO_BF16 (GEMMs of the forward on tcgen05 tensor cores) */
+} tdo_model;
+
+/* Number of real parameters of a model (the length of theta). 0 for an invalid model. */
+size_t tdo_model_num_params(const tdo_model *model);
+
+/* Create a context on the current CUDA device: copies the problem and theta (host FP64, n_theta values),
+ * builds the Lindbladian connection rules, uploads parameters.  stream: a cudaStream_t (NULL = legacy
+ * default stream).  The context owns its device workspace; tdo_destroy frees it. */
+tdo_status tdo_create(const tdo_problem *problem, const tdo_model *model, const double *theta,
+                      size_t n_theta, void *stream, tdo_ctx **out);
+tdo_status tdo_destroy(tdo_ctx *ctx);
+size_t tdo_num_params(const tdo_ctx *ctx);
+/* Largest number of connected configurations (diagonal included) of any row of Lhat. */
+int tdo_max_connections(const tdo_ctx *ctx);
+
+/* Replace / read theta (FP64, n = tdo_num_params values, host or device pointer). */
+tdo_status tdo_set_params(tdo_ctx *ctx, const double *theta);
+tdo_status tdo_get_params(tdo_ctx *ctx, double *theta);
+
+/* Batched ansatz evaluation (architecture appendix; Eq. log_sum_exp_conjugate):
+ * logrho[b] = log rho(sig[b], sigp[b]) as (re, im) floats, b < B.  B may be 0. */
+tdo_status tdo_log_rho(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t B, float *logrho);
+
+/* Vector-Jacobian product of tdo_log_rho: grad[k] += sum_b Re(c_b * d log rho_b / d theta_k) with the
+ * complex cotangents c_b = (cot[2b], cot[2b+1]); grad is FP64 [P], accumulated into (not zeroed). */
+tdo_status tdo_log_rho_vjp(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t B,
+                           const float *cot, double *grad);
+
+/* Log-derivatives O[b][k] = d log rho(sig[b], sigp[b]) / d theta_k as (re, im) floats, layout
+ * [B][P][2] (metric-tensor section: the Delta O_i of S). */
+tdo_status tdo_jacobian(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t B, float *O);
+
+/* Rows of Lhat (Eq. VecLin with A rho B -> (A (x) B^T)|rho>>): for sample s, count[s] entries
+ * conn_sig/conn_sigp/conn_coef [s*M + j], j < count[s], M = tdo_max_connections(); entry 0 is always
+ * the diagonal (s itself, coefficient possibly 0); the others have nonzero coefficients, in a fixed
+ * order.  coef is (re, im) float. */
+tdo_status tdo_connections(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t Ns,
+                           int32_t *count, uint32_t *conn_sig, uint32_t *conn_sigp, float *conn_coef);
+
+/* Local estimator L_loc(x) = sum_y Lhat_xy rho(y)/rho(x) (optimisation-procedure section) for Ns
+ * samples: lloc [Ns][2] doubles (may be NULL); cost = mean |L_loc|^2 and its standard error
+ * (Eq. lossnetk estimated on the samples; either output pointer may be NULL). */
+tdo_status tdo_local_estimator(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t Ns,
+                               double *lloc, double *cost, double *stderr_);
+
+/* Metropolis-Hastings on |rho|^2 with single-bit proposals (sampling section).  Chains are in/out in
+ * sig/sigp [n_chains].  Proposal t of chain c draws Philox4x32-10(key = (seed lo, seed hi),
+ * counter = (c, t lo, t hi, 0)) -> (x0, x1, ...): bit k = ((x0 >> 8) * 2N) >> 24 (k < N flips s_k,
+ * else s'_{k-N}), u = (x1 >> 8) 2^-24, accept iff u < exp(min(0, 2 Re(log rho' - log rho))).
+ * Proposals t = counter .. counter + n_sweeps*2N - 1 (a sweep is 2N proposals).  After each sweep the
+ * chain states are stored to samples_sig/samples_sigp [sweep][n_chains] when those are not NULL.
+ * accepted (may be NULL) receives the number of accepted moves. */
+tdo_status tdo_sample(tdo_ctx *ctx, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
+                      uint32_t *sig, uint32_t *sigp, uint32_t *samples_sig, uint32_t *samples_sigp,
+                      uint64_t *accepted);
+
+/* Cost gradient for real parameters from Ns samples (derivative of Eq. lossnetk):
+ * grad_k = 2 Re (1/Ns) sum_x [ conj(L_loc(x)) sum_y Lhat_xy (rho_y/rho_x) O_k(y) - Cost O_k(x) ],
+ * grad FP64 [P] (overwritten); cost (may be NULL) = mean |L_loc|^2; O (may be NULL) receives the
+ * samples' log-derivatives as in tdo_jacobian. */
+tdo_status tdo_grad(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t Ns, double *grad,
+                    double *cost, float *O);
+
+/* Stochastic-reconfiguration solve (metric-tensor and regularisation sections):
+ * (Re S + diag_shift I) x = rhs with S_ij = <O_i^* O_j> - <O_i^*><O_j> over the Ns rows of O
+ * ([Ns][P][2] floats), by Jacobi-preconditioned conjugate gradients in FP64 until
+ * ||r|| <= tol ||rhs|| or max_iter iterations.  iters / resid (may be NULL) report the iterations
+ * and the final relative residual. */
+tdo_status tdo_sr_solve(tdo_ctx *ctx, const float *O, size_t Ns, const double *rhs, double diag_shift,
+                        double tol, int max_iter, double *x, int *iters, double *resid);
+
+/* Stopping rule of the CG solve inside tdo_sr_step (defaults: tol 1e-8, max_iter 200). */
+tdo_status tdo_set_sr_options(tdo_ctx *ctx, double tol, int max_iter);
+
+/* One optimisation-workflow step on a given sample set: cost and gradient, log-derivatives,
+ * SR solve with diag_shift, theta <- theta - lr * delta.  cost (may be NULL) gets the cost before the
+ * update. */
+tdo_status tdo_sr_step(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t Ns, double lr,
+                       double diag_shift, double *cost);
+
+/* Device timing of this context's kernels: with enable != 0, every kernel launch of the calls above is
+ * bracketed by CUDA events on the context's stream (records from before are dropped).  Used by the
+ * benchmark to time kernels inside a real step. */
+tdo_status tdo_timing(tdo_ctx *ctx, int enable);
+/* Total recorded device time (ms) and launches of a kernel group since tdo_timing(ctx, 1):
+ * "fwd" (transformer forward), "sample" (Metropolis), "bwd_vjp" (gradient backward), "bwd_jac"
+ * (log-derivatives), "conn" (connections, scan, compaction), "lloc" (L_loc, cost, cotangents),
+ * "sr" (CG solve), "update" (parameter update and refresh), or "all".  Synchronises the stream. */
+tdo_status tdo_timing_read(tdo_ctx *ctx, const char *group, double *ms, long long *launches);
+
+/* Message of the last failing call on this context (or of the last failed tdo_create when ctx is NULL). */
+const char *tdo_last_error(const tdo_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDO_H */

@@ -1,0 +1,601 @@
+// FP32 backward of the ansatz with activation recomputation.
+//
+// Per tile of configurations the kernel (1) recomputes the forward, saving each layer's input, Q, K, V,
+// head outputs and attention-block output to a per-CTA scratch area (L2-resident), (2) back-propagates
+// the cotangent of log rho through the Hermitian symmetrisation (Eq. log_sum_exp_conjugate), the head,
+// the mean pooling, every layer in reverse (MLP, W^O, softmax attention, Q/K/V) and the embedding.
+// Weight gradients are D x D blocks reduced over the rows of the tile:
+//   mode 0 (VJP): summed over the tile and added to one of n_copies FP32 accumulator vectors,
+//   mode 1 (Jacobian): one per (configuration, seed) and written to O[b][k][seed]
+//                      (seed 0: d Re log rho, seed 1: d Im log rho).
+#include "f32_tile.cuh"
+
+namespace tdo {
+
+struct FlatOffsets {
+  long long E;
+  long long Wq[TDO_MAX_LAYERS], Wk[TDO_MAX_LAYERS], Wv[TDO_MAX_LAYERS], Wo[TDO_MAX_LAYERS];
+  long long W1[TDO_MAX_LAYERS], b1[TDO_MAX_LAYERS], W2[TDO_MAX_LAYERS], b2[TDO_MAX_LAYERS];
+  long long Wh, bh;
+};
+
+template <int D>
+struct BwdGeom {
+  static constexpr int R = (D == 64) ? 64 : 128;
+  static constexpr int LDX = D + 4;
+  static constexpr int BUF = R * LDX;
+  static constexpr int W_OFF = 9 * BUF;
+  static constexpr int ST_OFF = W_OFF + 3 * D * D;   // max, 1/sum, delta: 3 x [R][16]
+  static constexpr int F_OFF = ST_OFF + 3 * R * 16;  // head outputs / their cotangents [R][2]
+  static constexpr int C_OFF = F_OFF + 2 * R;        // configs sig[R/2], sigp[R/2]
+  static constexpr int T_OFF = C_OFF + R;            // cotangent per virtual configuration [R/2] float2
+  static constexpr int FLOATS = T_OFF + R;
+  static constexpr size_t BYTES = sizeof(float) * FLOATS;
+  static constexpr int TX = D / 8;
+  static constexpr int TY = kThreads / TX;
+  static constexpr int KPT = (D / TY) > 0 ? (D / TY) : 1;   // weight rows per thread in dW blocks
+};
+
+__host__ __device__ __forceinline__ int seqs_for(int n, int rows) {
+  int ts = 2 * (rows / (2 * n));
+  return ts < 2 ? 2 : ts;
+}
+
+struct SinkCtx {
+  int mode;
+  float *g;          // mode 0: this CTA's accumulator copy [P]
+  float *O;          // mode 1: [B][P][2]
+  size_t P;
+};
+
+// Add / write one gradient value at flat parameter index k for virtual configuration v of the tile.
+__device__ __forceinline__ void sink1(const SinkCtx &s, long long k, float v, long long b, int seed) {
+  if (s.mode == 0) atomicAdd(s.g + k, v);
+  else s.O[((size_t)b * s.P + (size_t)k) * 2 + seed] = v;
+}
+
+// Copy a rows x D block of global memory (row stride gld, column offset col0) transposed into smem:
+// s[c][r] = g[r][col0 + c].
+template <int D>
+__device__ __forceinline__ void stage_blockT(const float *__restrict__ g, int gld, int col0, float *s) {
+  for (int i = threadIdx.x; i < D * D; i += kThreads) {
+    const int r = i / D, c = i % D;
+    s[c * D + r] = __ldg(g + (size_t)r * gld + col0 + c);
+  }
+}
+
+template <int D, int R>
+__device__ __forceinline__ void save_block(const float *src, float *dst) {
+  constexpr int LDX = D + 4;
+  for (int i = threadIdx.x; i < R * (D / 4); i += kThreads) {
+    const int r = i / (D / 4), c = (i % (D / 4)) * 4;
+    *reinterpret_cast<float4 *>(dst + r * D + c) = *reinterpret_cast<const float4 *>(src + r * LDX + c);
+  }
+}
+template <int D, int R>
+__device__ __forceinline__ void load_block(const float *src, float *dst) {
+  constexpr int LDX = D + 4;
+  for (int i = threadIdx.x; i < R * (D / 4); i += kThreads) {
+    const int r = i / (D / 4), c = (i % (D / 4)) * 4;
+    *reinterpret_cast<float4 *>(dst + r * LDX + c) = *reinterpret_cast<const float4 *>(src + r * D + c);
+  }
+}
+
+// dW[k][c] = sum_{r in [r0, r1)} f(A[r][k]) * Bm[r][c] over this thread's (k, c) set:
+// k = ty + j*TY (j < KPT, k < D), c in {4tx..4tx+3, D/2+4tx..+3}.
+template <int D, bool GELU_A>
+__device__ __forceinline__ void mmT_acc(const float *A, const float *Bm, int r0, int r1,
+                                        float (&acc)[BwdGeom<D>::KPT][8]) {
+  using BG = BwdGeom<D>;
+  constexpr int LDX = D + 4;
+  const int tx = threadIdx.x % BG::TX, ty = threadIdx.x / BG::TX;
+  const int c0 = 4 * tx, c1 = D / 2 + 4 * tx;
+#pragma unroll
+  for (int j = 0; j < BG::KPT; ++j)
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[j][e] = 0.f;
+  if (ty >= D) return;
+  for (int r = r0; r < r1; ++r) {
+    const float4 b0 = *reinterpret_cast<const float4 *>(Bm + r * LDX + c0);
+    const float4 b1 = *reinterpret_cast<const float4 *>(Bm + r * LDX + c1);
+#pragma unroll
+    for (int j = 0; j < BG::KPT; ++j) {
+      float a = A[r * LDX + ty + j * BG::TY];
+      if (GELU_A) a = gelu_f(a);
+      acc[j][0] = fmaf(a, b0.x, acc[j][0]);
+      acc[j][1] = fmaf(a, b0.y, acc[j][1]);
+      acc[j][2] = fmaf(a, b0.z, acc[j][2]);
+      acc[j][3] = fmaf(a, b0.w, acc[j][3]);
+      acc[j][4] = fmaf(a, b1.x, acc[j][4]);
+      acc[j][5] = fmaf(a, b1.y, acc[j][5]);
+      acc[j][6] = fmaf(a, b1.z, acc[j][6]);
+      acc[j][7] = fmaf(a, b1.w, acc[j][7]);
+    }
+  }
+}
+
+// Send a dW block (flat offset off, row stride ld) to the sink.
+template <int D>
+__device__ __forceinline__ void sink_block(const SinkCtx &s, float (&acc)[BwdGeom<D>::KPT][8],
+                                           long long off, long long ld, long long b, int seed) {
+  using BG = BwdGeom<D>;
+  const int tx = threadIdx.x % BG::TX, ty = threadIdx.x / BG::TX;
+  if (ty >= D) return;
+#pragma unroll
+  for (int j = 0; j < BG::KPT; ++j) {
+    const long long k = ty + j * BG::TY;
+    if (k >= D) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long base = off + k * ld + (h ? D / 2 : 0) + 4 * tx;
+      if (s.mode == 0 && (base & 3) == 0) {
+        atomicAdd(reinterpret_cast<float4 *>(s.g + base),
+                  make_float4(acc[j][4 * h], acc[j][4 * h + 1], acc[j][4 * h + 2], acc[j][4 * h + 3]));
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sink1(s, base + e, acc[j][4 * h + e], b, seed);
+      }
+    }
+  }
+}
+
+// Column sums of Bm over rows [r0, r1) -> sink at off + c, c < D.
+template <int D>
+__device__ __forceinline__ void colsum_sink(const SinkCtx &s, const float *Bm, int r0, int r1,
+                                            long long off, long long b, int seed) {
+  constexpr int LDX = D + 4;
+  for (int c = threadIdx.x; c < D; c += kThreads) {
+    float acc = 0.f;
+    for (int r = r0; r < r1; ++r) acc += Bm[r * LDX + c];
+    sink1(s, off + c, acc, b, seed);
+  }
+}
+
+// Attention backward of one (sequence, head) unit per lane group; see the header comment.
+template <int D>
+__device__ __forceinline__ void attention_bwd(const float *Qs, const float *Ks, const float *Vs,
+                                              const float *dHs, float *dQ, float *dK, float *dV,
+                                              float *st, int ts, int n, int heads, int dh) {
+  constexpr int LDX = D + 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = n <= 8 ? 8 : (n <= 16 ? 16 : 32);
+  const int upw = 32 / grp;
+  const int units = ts * heads;
+  const float scale = rsqrtf((float)dh);
+  const int RS = BwdGeom<D>::R * 16;
+  float *smx = st, *sis = st + RS, *sdl = st + 2 * RS;
+  for (int u0 = warp * upw; u0 < units; u0 += (kThreads / 32) * upw) {
+    const int u = u0 + lane / grp, i = lane % grp;
+    const bool act = (u < units && i < n);
+    const int s = act ? u / heads : 0, h = act ? u % heads : 0;
+    const int base = s * n, col = h * dh;
+    if (act) {   // pass 1: lane = query row
+      const int row = base + i;
+      float q[16], g[16], dq[16], sc[TDO_MAX_N], da[TDO_MAX_N];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        q[e] = e < dh ? Qs[row * LDX + col + e] : 0.f;
+        g[e] = e < dh ? dHs[row * LDX + col + e] : 0.f;
+        dq[e] = 0.f;
+      }
+      float mx = -INFINITY;
+#pragma unroll
+      for (int j = 0; j < TDO_MAX_N; ++j) {
+        if (j < n) {
+          const float *kr = Ks + (base + j) * LDX + col;
+          const float *vr = Vs + (base + j) * LDX + col;
+          float dot = 0.f, dd = 0.f;
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (e < dh) { dot = fmaf(q[e], kr[e], dot); dd = fmaf(g[e], vr[e], dd); }
+          sc[j] = dot * scale;
+          da[j] = dd;
+          mx = fmaxf(mx, sc[j]);
+        }
+      }
+      float sum = 0.f;
+#pragma unroll
+      for (int j = 0; j < TDO_MAX_N; ++j)
+        if (j < n) { sc[j] = expf(sc[j] - mx); sum += sc[j]; }
+      const float is = 1.0f / sum;
+      float delta = 0.f;
+#pragma unroll
+      for (int j = 0; j < TDO_MAX_N; ++j)
+        if (j < n) { sc[j] *= is; delta = fmaf(sc[j], da[j], delta); }
+#pragma unroll
+      for (int j = 0; j < TDO_MAX_N; ++j) {
+        if (j < n) {
+          const float w = scale * sc[j] * (da[j] - delta);
+          const float *kr = Ks + (base + j) * LDX + col;
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (e < dh) dq[e] = fmaf(w, kr[e], dq[e]);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        if (e < dh) dQ[row * LDX + col + e] = dq[e];
+      smx[row * 16 + h] = mx;
+      sis[row * 16 + h] = is;
+      sdl[row * 16 + h] = delta;
+    }
+    __syncwarp();
+    if (act) {   // pass 2: lane = key row j
+      const int jrow = base + i;
+      float k[16], v[16], dk[16], dv[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        k[e] = e < dh ? Ks[jrow * LDX + col + e] : 0.f;
+        v[e] = e < dh ? Vs[jrow * LDX + col + e] : 0.f;
+        dk[e] = 0.f;
+        dv[e] = 0.f;
+      }
+      for (int qi = 0; qi < n; ++qi) {
+        const int row = base + qi;
+        const float *qr = Qs + row * LDX + col;
+        const float *gr = dHs + row * LDX + col;
+        float dot = 0.f, dd = 0.f;
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if (e < dh) { dot = fmaf(qr[e], k[e], dot); dd = fmaf(gr[e], v[e], dd); }
+        const float a = expf(dot * scale - smx[row * 16 + h]) * sis[row * 16 + h];
+        const float w = scale * a * (dd - sdl[row * 16 + h]);
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if (e < dh) { dv[e] = fmaf(a, gr[e], dv[e]); dk[e] = fmaf(w, qr[e], dk[e]); }
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        if (e < dh) { dK[jrow * LDX + col + e] = dk[e]; dV[jrow * LDX + col + e] = dv[e]; }
+    }
+    __syncwarp();
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_bwd32(const DevModel m, const int mode, const uint32_t *__restrict__ sig,
+            const uint32_t *__restrict__ sigp, const size_t B, const float2 *__restrict__ cot,
+            float *__restrict__ gacc, const int n_copies, const size_t g_stride, float *__restrict__ O,
+            const size_t P, const FlatOffsets fo, float *__restrict__ scratch) {
+  using BG = BwdGeom<D>;
+  constexpr int R = BG::R, LDX = BG::LDX;
+  using G = F32Geom<D, R>;
+  extern __shared__ float4 smem4[];
+  float *sm = reinterpret_cast<float *>(smem4);
+  float *Bf[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Bf[i] = sm + i * BG::BUF;
+  float *Ws = sm + BG::W_OFF, *st = sm + BG::ST_OFF, *Fs = sm + BG::F_OFF;
+  uint32_t *csig = reinterpret_cast<uint32_t *>(sm + BG::C_OFF);
+  uint32_t *csigp = csig + R / 2;
+  float2 *ccot = reinterpret_cast<float2 *>(sm + BG::T_OFF);
+
+  const int n = m.n_sites;
+  const int ts = seqs_for(n, R), tcv = ts / 2, nrows = ts * n;
+  const size_t nvirt = mode == 0 ? B : 2 * B;
+  const size_t ntiles = (nvirt + tcv - 1) / tcv;
+  const size_t blk = (size_t)6 * R * D;
+  float *scr = scratch + (size_t)blockIdx.x * (size_t)m.layers * blk;
+  SinkCtx sk;
+  sk.mode = mode;
+  sk.g = gacc ? gacc + (size_t)(blockIdx.x % n_copies) * g_stride : nullptr;   // g_stride % 4 == 0
+  sk.O = O;
+  sk.P = P;
+  const int nranges = mode == 0 ? 1 : tcv;
+
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (threadIdx.x < tcv) {
+      const size_t vg = tile * tcv + threadIdx.x;
+      const bool valid = vg < nvirt;
+      const size_t b = mode == 0 ? vg : vg / 2;
+      csig[threadIdx.x] = valid ? sig[b] : 0u;
+      csigp[threadIdx.x] = valid ? sigp[b] : 0u;
+      float2 c = make_float2(0.f, 0.f);
+      if (valid) c = mode == 0 ? cot[b] : ((vg & 1) ? make_float2(0.f, -1.f) : make_float2(1.f, 0.f));
+      ccot[threadIdx.x] = c;
+    }
+    __syncthreads();
+    // virtual configuration v of this tile -> (global configuration, seed) for mode-1 sinks
+    auto vb = [&](int v) -> long long { return (long long)((tile * tcv + v) / 2); };
+    auto vs = [&](int v) -> int { return (int)((tile * tcv + v) & 1); };
+    auto vvalid = [&](int v) -> bool { return tile * tcv + v < nvirt; };
+
+    // ---------------- forward recompute, saving activations per layer
+    embed_f32<D, R>(m, csig, csigp, ts, Bf[0]);
+    __syncthreads();
+    for (int l = 0; l < m.layers; ++l) {
+      const DevLayer &L = m.L[l];
+      float *sl = scr + (size_t)l * blk;
+      save_block<D, R>(Bf[0], sl);
+      stage_block<D>(L.Wq, D, 0, D, Ws);
+      stage_block<D>(L.Wk, D, 0, D, Ws + D * D);
+      stage_block<D>(L.Wv, D, 0, D, Ws + 2 * D * D);
+      __syncthreads();
+      {
+        float acc[G::RPT][8];
+#pragma unroll
+        for (int w = 0; w < 3; ++w) {
+          acc_zero<D, R>(acc);
+          mm_acc<D, R>(Bf[0], LDX, Ws + w * D * D, D, acc);
+          acc_store<D, R>(acc, Bf[1 + w]);
+        }
+      }
+      __syncthreads();
+      attention_f32<D>(Bf[1], Bf[2], Bf[3], ts, n, m.heads, m.dh, Bf[4]);
+      stage_block<D>(L.Wo, D, 0, D, Ws);
+      __syncthreads();
+      save_block<D, R>(Bf[1], sl + 1 * R * D);
+      save_block<D, R>(Bf[2], sl + 2 * R * D);
+      save_block<D, R>(Bf[3], sl + 3 * R * D);
+      save_block<D, R>(Bf[4], sl + 4 * R * D);
+      {
+        float acc[G::RPT][8];
+        acc_zero<D, R>(acc);
+        mm_acc<D, R>(Bf[4], LDX, Ws, D, acc);
+        acc_foreach<D, R>(acc, [&](int r, int c, float v) { Bf[0][r * LDX + c] += v; });
+      }
+      __syncthreads();
+      if (m.ffn > 0) {
+        save_block<D, R>(Bf[0], sl + 5 * R * D);
+        float acc2[G::RPT][8];
+        acc_zero<D, R>(acc2);
+        for (int c0 = 0; c0 < m.ffn; c0 += D) {
+          stage_block<D>(L.W1, m.ffn, c0, D, Ws);
+          stage_block<D>(L.W2 + (size_t)c0 * D, D, 0, D, Ws + D * D);
+          __syncthreads();
+          float acc[G::RPT][8];
+          acc_zero<D, R>(acc);
+          mm_acc<D, R>(Bf[0], LDX, Ws, D, acc);
+          acc_foreach<D, R>(acc, [&](int r, int c, float v) {
+            Bf[7][r * LDX + c] = gelu_f(v + __ldg(L.b1 + c0 + c));
+          });
+          __syncthreads();
+          mm_acc<D, R>(Bf[7], LDX, Ws + D * D, D, acc2);
+          __syncthreads();
+        }
+        acc_foreach<D, R>(acc2, [&](int r, int c, float v) { Bf[0][r * LDX + c] += v + __ldg(L.b2 + c); });
+        __syncthreads();
+      }
+    }
+    // ---------------- head: pooling, dense layer, symmetrisation weights, cotangents of F
+    float *Hp = Bf[7];
+    {
+      const float inv_n = 1.0f / (float)n;
+      for (int idx = threadIdx.x; idx < ts * D; idx += kThreads) {
+        const int s = idx / D, c = idx % D;
+        float a = 0.f;
+        for (int i = 0; i < n; ++i) a += Bf[0][(s * n + i) * LDX + c];
+        Hp[s * D + c] = a * inv_n;
+      }
+      __syncthreads();
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int p = warp; p < ts * 2; p += kThreads / 32) {
+        const int s = p >> 1, o = p & 1;
+        float a = 0.f;
+        for (int c = lane; c < D; c += 32) a = fmaf(Hp[s * D + c], __ldg(m.Wh + 2 * c + o), a);
+        a = warp_sum(a);
+        if (lane == 0) Fs[p] = a + __ldg(m.bh + o);
+      }
+      __syncthreads();
+      for (int v = threadIdx.x; v < tcv; v += kThreads) {
+        float2 pw, pv;
+        symmetrise(Fs[4 * v], Fs[4 * v + 1], Fs[4 * v + 2], Fs[4 * v + 3], &pw, &pv);
+        const float2 c = ccot[v];
+        const float cwr = c.x * pw.x - c.y * pw.y, cwi = c.x * pw.y + c.y * pw.x;
+        const float cvr = c.x * pv.x - c.y * pv.y, cvi = c.x * pv.y + c.y * pv.x;
+        Fs[4 * v] = cwr;
+        Fs[4 * v + 1] = -cwi;
+        Fs[4 * v + 2] = cvr;
+        Fs[4 * v + 3] = cvi;
+      }
+      __syncthreads();
+      // dWh[k][o] = sum_s h[s][k] dF[s][o], dbh[o] = sum_s dF[s][o]
+      for (int rg = 0; rg < nranges; ++rg) {
+        const int s0 = mode == 0 ? 0 : 2 * rg, s1 = mode == 0 ? ts : 2 * rg + 2;
+        if (mode == 1 && !vvalid(rg)) continue;
+        for (int idx = threadIdx.x; idx < 2 * D + 2; idx += kThreads) {
+          float a = 0.f;
+          if (idx < 2 * D) {
+            const int k = idx >> 1, o = idx & 1;
+            for (int s = s0; s < s1; ++s) a = fmaf(Hp[s * D + k], Fs[2 * s + o], a);
+            sink1(sk, fo.Wh + idx, a, vb(rg), vs(rg));
+          } else {
+            const int o = idx - 2 * D;
+            for (int s = s0; s < s1; ++s) a += Fs[2 * s + o];
+            sink1(sk, fo.bh + o, a, vb(rg), vs(rg));
+          }
+        }
+      }
+      // dX_L[r][k] = (1/N) sum_o Wh[k][o] dF[s(r)][o]
+      for (int idx = threadIdx.x; idx < R * D; idx += kThreads) {
+        const int r = idx / D, k = idx % D;
+        float v = 0.f;
+        if (r < nrows) {
+          const int s = r / n;
+          v = (__ldg(m.Wh + 2 * k) * Fs[2 * s] + __ldg(m.Wh + 2 * k + 1) * Fs[2 * s + 1]) * inv_n;
+        }
+        Bf[6][r * LDX + k] = v;
+      }
+      __syncthreads();
+    }
+    // ---------------- layers in reverse
+    for (int l = m.layers - 1; l >= 0; --l) {
+      const DevLayer &L = m.L[l];
+      const float *sl = scr + (size_t)l * blk;
+      load_block<D, R>(sl, Bf[0]);
+      load_block<D, R>(sl + 1 * R * D, Bf[1]);
+      load_block<D, R>(sl + 2 * R * D, Bf[2]);
+      load_block<D, R>(sl + 3 * R * D, Bf[3]);
+      load_block<D, R>(sl + 4 * R * D, Bf[4]);
+      if (m.ffn > 0) load_block<D, R>(sl + 5 * R * D, Bf[5]);
+      __syncthreads();
+      if (m.ffn > 0) {
+        float adx[G::RPT][8];
+        acc_zero<D, R>(adx);
+        acc_foreach<D, R>(adx, [&](int r, int c, float &v) { v = Bf[6][r * LDX + c]; });
+        for (int c0 = 0; c0 < m.ffn; c0 += D) {
+          stage_block<D>(L.W1, m.ffn, c0, D, Ws);                  // W1_c [in][hid]
+          stage_blockT<D>(L.W1, m.ffn, c0, Ws + D * D);            // W1_c^T [hid][in]
+          stage_blockT<D>(L.W2 + (size_t)c0 * D, D, 0, Ws + 2 * D * D);   // W2_c^T [out][hid]
+          __syncthreads();
+          {
+            float au[G::RPT][8], ag[G::RPT][8];
+            acc_zero<D, R>(au);
+            mm_acc<D, R>(Bf[5], LDX, Ws, D, au);
+            acc_zero<D, R>(ag);
+            mm_acc<D, R>(Bf[6], LDX, Ws + 2 * D * D, D, ag);
+            acc_foreach<D, R>(au, [&](int r, int c, float &v) {
+              v += __ldg(L.b1 + c0 + c);
+              Bf[7][r * LDX + c] = v;     // U (pre-activation)
+            });
+            // dU = dG * gelu'(U): both accumulators share the (row, col) map
+            const int tx = threadIdx.x % G::TX, ty = threadIdx.x / G::TX;
+#pragma unroll
+            for (int j = 0; j < G::RPT; ++j)
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const int col = (e < 4) ? (4 * tx + e) : (D / 2 + 4 * tx + e - 4);
+                Bf[8][(ty + j * G::TY) * LDX + col] = ag[j][e] * gelu_grad_f(au[j][e]);
+              }
+          }
+          __syncthreads();
+          for (int rg = 0; rg < nranges; ++rg) {
+            if (mode == 1 && !vvalid(rg)) continue;
+            const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? R : r0 + 2 * n;
+            float dw[BG::KPT][8];
+            mmT_acc<D, true>(Bf[7], Bf[6], r0, r1, dw);
+            sink_block<D>(sk, dw, fo.W2[l] + (long long)c0 * D, D, vb(rg), vs(rg));
+            mmT_acc<D, false>(Bf[5], Bf[8], r0, r1, dw);
+            sink_block<D>(sk, dw, fo.W1[l] + c0, m.ffn, vb(rg), vs(rg));
+            colsum_sink<D>(sk, Bf[8], r0, r1, fo.b1[l] + c0, vb(rg), vs(rg));
+          }
+          mm_acc<D, R>(Bf[8], LDX, Ws + D * D, D, adx);
+          __syncthreads();
+        }
+        for (int rg = 0; rg < nranges; ++rg) {
+          if (mode == 1 && !vvalid(rg)) continue;
+          const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? R : r0 + 2 * n;
+          colsum_sink<D>(sk, Bf[6], r0, r1, fo.b2[l], vb(rg), vs(rg));
+        }
+        __syncthreads();
+        acc_store<D, R>(adx, Bf[6]);   // dX at the attention-block output
+        __syncthreads();
+      }
+      // attention block: X' = concat(heads) Wo + X
+      stage_blockT<D>(L.Wo, D, 0, Ws);
+      __syncthreads();
+      {
+        float acc[G::RPT][8];
+        acc_zero<D, R>(acc);
+        mm_acc<D, R>(Bf[6], LDX, Ws, D, acc);
+        acc_store<D, R>(acc, Bf[7]);   // dH
+      }
+      for (int rg = 0; rg < nranges; ++rg) {
+        if (mode == 1 && !vvalid(rg)) continue;
+        const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? R : r0 + 2 * n;
+        float dw[BG::KPT][8];
+        mmT_acc<D, false>(Bf[4], Bf[6], r0, r1, dw);
+        sink_block<D>(sk, dw, fo.Wo[l], D, vb(rg), vs(rg));
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < (R - nrows) * D; idx += kThreads) {
+        const int r = nrows + idx / D, c = idx % D;
+        Bf[4][r * LDX + c] = 0.f;
+        Bf[5][r * LDX + c] = 0.f;
+        Bf[8][r * LDX + c] = 0.f;
+      }
+      attention_bwd<D>(Bf[1], Bf[2], Bf[3], Bf[7], Bf[4], Bf[5], Bf[8], st, ts, n, m.heads, m.dh);
+      stage_blockT<D>(L.Wq, D, 0, Ws);
+      stage_blockT<D>(L.Wk, D, 0, Ws + D * D);
+      stage_blockT<D>(L.Wv, D, 0, Ws + 2 * D * D);
+      __syncthreads();
+      for (int rg = 0; rg < nranges; ++rg) {
+        if (mode == 1 && !vvalid(rg)) continue;
+        const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? R : r0 + 2 * n;
+        float dw[BG::KPT][8];
+        mmT_acc<D, false>(Bf[0], Bf[4], r0, r1, dw);
+        sink_block<D>(sk, dw, fo.Wq[l], D, vb(rg), vs(rg));
+        mmT_acc<D, false>(Bf[0], Bf[5], r0, r1, dw);
+        sink_block<D>(sk, dw, fo.Wk[l], D, vb(rg), vs(rg));
+        mmT_acc<D, false>(Bf[0], Bf[8], r0, r1, dw);
+        sink_block<D>(sk, dw, fo.Wv[l], D, vb(rg), vs(rg));
+      }
+      {
+        float acc[G::RPT][8];
+        acc_zero<D, R>(acc);
+        acc_foreach<D, R>(acc, [&](int r, int c, float &v) { v = Bf[6][r * LDX + c]; });
+        mm_acc<D, R>(Bf[4], LDX, Ws, D, acc);
+        mm_acc<D, R>(Bf[5], LDX, Ws + D * D, D, acc);
+        mm_acc<D, R>(Bf[8], LDX, Ws + 2 * D * D, D, acc);
+        __syncthreads();
+        acc_store<D, R>(acc, Bf[6]);
+      }
+      __syncthreads();
+    }
+    // ---------------- embedding (token table)
+    if (m.embed == 0) {
+      for (int rg = 0; rg < nranges; ++rg) {
+        if (mode == 1 && !vvalid(rg)) continue;
+        const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? nrows : r0 + 2 * n;
+        for (int idx = threadIdx.x; idx < 4 * D; idx += kThreads) {
+          const int pat = idx / D, c = idx % D;
+          float a = 0.f;
+          for (int r = r0; r < r1; ++r) {
+            const int s = r / n, i = r % n, cfg = s >> 1;
+            const uint32_t w1 = (s & 1) ? csigp[cfg] : csig[cfg];
+            const uint32_t w2 = (s & 1) ? csig[cfg] : csigp[cfg];
+            if (embed_pattern(0, w1, w2, i, n) == pat) a += Bf[6][r * LDX + c];
+          }
+          sink1(sk, fo.E + idx, a, vb(rg), vs(rg));
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int D>
+static cudaError_t bwd_impl(const DevModel &m, int mode, const uint32_t *sig, const uint32_t *sigp,
+                            size_t B, const float2 *cot, float *gacc, int n_copies, size_t g_stride, float *O,
+                            size_t P, const FlatOffsets &fo, float *scratch, int grid, cudaStream_t st) {
+  const size_t bytes = BwdGeom<D>::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_bwd32<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  k_bwd32<D><<<grid, kThreads, bytes, st>>>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch);
+  return cudaGetLastError();
+}
+
+}  // namespace tdo
+
+size_t bwd32_scratch_floats(const DevModel &m, int grid) {
+  const int R = m.d == 64 ? 64 : 128;
+  return (size_t)grid * (size_t)m.layers * 6 * (size_t)R * (size_t)m.d;
+}
+
+int bwd32_grid(const DevModel &m, size_t B, int mode, int n_sm) {
+  const int R = m.d == 64 ? 64 : 128;
+  const int tcv = tdo::seqs_for(m.n_sites, R) / 2;
+  const size_t nvirt = mode == 0 ? B : 2 * B;
+  const size_t ntiles = (nvirt + tcv - 1) / tcv;
+  size_t grid = (size_t)n_sm;
+  if (m.d < 64) grid *= 1;   // one CTA per SM (shared memory bound)
+  if (grid > ntiles) grid = ntiles;
+  return (int)(grid ? grid : 1);
+}
+
+cudaError_t launch_bwd32_impl(const DevModel &m, int mode, const uint32_t *sig, const uint32_t *sigp,
+                              size_t B, const float2 *cot, float *gacc, int n_copies, size_t g_stride,
+                              float *O, size_t P, const long long *flat_offsets, float *scratch, int grid,
+                              cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  tdo::FlatOffsets fo;
+  static_assert(sizeof(tdo::FlatOffsets) == sizeof(long long) * (3 + 8 * TDO_MAX_LAYERS), "layout");
+  memcpy(&fo, flat_offsets, sizeof(fo));
+  switch (m.d) {
+    case 16: return tdo::bwd_impl<16>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch, grid, st);
+    case 32: return tdo::bwd_impl<32>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch, grid, st);
+    case 64: return tdo::bwd_impl<64>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}

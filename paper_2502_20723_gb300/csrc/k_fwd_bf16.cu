@@ -1,0 +1,686 @@
+// BF16 tensor-core forward of the ansatz (architecture appendix) on sm_103a: tcgen05.mma with FP32
+// accumulators in tensor memory, weights streamed into shared memory by cp.async.bulk (TMA engine),
+// attention / softmax / GELU / residual on the CUDA cores in FP32.
+//
+// Tile: 128 token rows (TS sequences of N tokens, TS*N <= 128), one CTA of 256 threads.  TMEM lane r
+// holds row r; warps w and w+4 share lane quarter w%4 and split the columns in two halves, so thread
+// (w, lane) owns row 32*(w%4)+lane and column half w/4.  The residual stream X stays in FP32 registers;
+// GEMM A operands are BF16 copies in shared memory.  All operands use the canonical no-swizzle K-major
+// layout: element (row, k) of a [rows][K] tile at byte (row/8)*16K + (k/8)*128 + (row%8)*16 + (k%8)*2
+// (core matrices of 8 rows x 16 bytes; LBO = 128 B between core matrices along K, SBO = 16K bytes
+// between 8-row groups).
+//
+// Per layer (D = d_model, F = hidden width, HC = hidden chunk):
+//   QKV:  [128 x D] x [D x 3D]      -> TMEM cols [0, 3D)
+//   O:    [128 x D] x [D x D]       -> TMEM cols [0, D)
+//   MLP1: [128 x D] x [D x HC]      -> TMEM cols [0, HC)      per chunk
+//   MLP2: [128 x HC] x [HC x D]     -> TMEM cols [HC, HC + D) accumulated over chunks
+// Every mbarrier wait is bounded; on timeout the kernel sets *err, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "tdo_device.cuh"
+
+namespace tdo {
+namespace bf16 {
+
+constexpr int kThreads = 256;
+constexpr int kRows = 128;
+constexpr int kTmemCols = 256;
+constexpr long long kSpinLimit = 1ll << 26;   // ~seconds of polling before giving up
+
+template <int D>
+struct Geo {
+  static constexpr int HC = (4 * D < 128) ? 4 * D : 128;        // hidden chunk (max mlp_ratio 4)
+  static constexpr int A_OFF = 0;                                // BF16 [128][D]
+  static constexpr int A_BYTES = kRows * D * 2;
+  static constexpr int KV_OFF = A_OFF + A_BYTES;                 // FP32 K [128][D], V [128][D]
+  static constexpr int KV_BYTES = 2 * kRows * D * 4;             // (G [128][HC] BF16, pool [128][D] alias)
+  static constexpr int W_OFF = KV_OFF + KV_BYTES;                // weights of the current GEMM
+  static constexpr int W_BYTES = (3 * D * D * 2 > 2 * HC * D) ? 3 * D * D * 2 : 2 * HC * D;
+  static constexpr int M_OFF = W_OFF + W_BYTES;                  // misc
+  // misc layout (bytes from M_OFF): mbar_mma 8, mbar_w 8, tmem holder 4, flag 4, configs 2x64x4,
+  // F [128][2] floats, results [64] float2
+  static constexpr int BYTES = M_OFF + 16 + 8 + 512 + 1024 + 512;
+  static_assert(2 * HC * D <= KV_BYTES, "hidden chunk fits the K/V region");
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with parity `phase` to complete; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t phase) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try(a, phase)) return true;
+    if (i > 64) __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+// Bulk (TMA engine) copy of `bytes` contiguous bytes global -> shared, completion on mbarrier `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major: start >> 4 at [0,14), LBO >> 4 at [16,30),
+// SBO >> 4 at [32,46), fixed 0b001 at [46,49), layout type 0 (no swizzle) at [61,64).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
+// both K-major (bits 15, 16 = 0), N >> 3 at [17,23), M >> 4 at [24,29).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (thread = lane).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+// Byte offset of element (row, k) in a canonical K-major tile with K columns.
+__host__ __device__ __forceinline__ uint32_t canon(int row, int k, int K) {
+  return (uint32_t)((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Store 8 consecutive k values (k0 % 8 == 0) of one row as BF16 (one 16-byte store).
+__device__ __forceinline__ void st_row8(uint8_t *base, int row, int k0, int K, const float *v) {
+  uint4 q;
+  q.x = pack_bf16(v[0], v[1]);
+  q.y = pack_bf16(v[2], v[3]);
+  q.z = pack_bf16(v[4], v[5]);
+  q.w = pack_bf16(v[6], v[7]);
+  *reinterpret_cast<uint4 *>(base + canon(row, k0, K)) = q;
+}
+
+struct Ctl {
+  uint32_t bar_mma, bar_w;   // smem addresses
+  uint32_t ph_mma, ph_w;     // parities to wait for next
+  uint32_t tmem;             // TMEM base address (lane 0, first column)
+  bool mma_thread;
+  int *err;
+  bool bad;
+};
+
+// Issue the MMAs of one GEMM: D[tmem + col] (+)= A[128 x K] * B^T, B stored [N][K]; commit to bar_mma.
+__device__ __forceinline__ void gemm(Ctl &c, uint32_t a_addr, uint32_t b_addr, int K, int N, uint32_t col,
+                                     bool accumulate) {
+  if (c.mma_thread) {
+    tc_fence_after();
+    const uint32_t id = idesc_bf16(kRows, N);
+    for (int kk = 0; kk < K / 16; ++kk) {
+      const uint64_t ad = sdesc(a_addr + kk * 256, 128, K * 16);
+      const uint64_t bd = sdesc(b_addr + kk * 256, 128, K * 16);
+      mma_bf16(c.tmem + col, ad, bd, id, (accumulate || kk > 0) ? 1u : 0u);
+    }
+    mma_commit(c.bar_mma);
+  }
+}
+
+__device__ __forceinline__ bool wait_mma(Ctl &c) {
+  const bool ok = mbar_wait(c.bar_mma, c.ph_mma);
+  c.ph_mma ^= 1u;
+  tc_fence_after();
+  return ok;
+}
+
+// Start the bulk copy of `bytes` of packed weights into the W region (thread 0), to be waited by all.
+__device__ __forceinline__ void stage_w(Ctl &c, uint32_t w_addr, const void *src, uint32_t bytes) {
+  if (c.mma_thread) {
+    mbar_expect_tx(c.bar_w, bytes);
+    bulk_g2s(w_addr, src, bytes, c.bar_w);
+  }
+}
+__device__ __forceinline__ bool wait_w(Ctl &c) {
+  const bool ok = mbar_wait(c.bar_w, c.ph_w);
+  c.ph_w ^= 1u;
+  return ok;
+}
+
+// Agree across the CTA on failure; returns true if any thread saw a timeout.
+__device__ __forceinline__ bool sync_fail(Ctl &c, bool ok) {
+  const int any = __syncthreads_or(ok ? 0 : 1);
+  if (any) c.bad = true;
+  return any != 0;
+}
+
+// The whole ansatz on one tile; configurations in cfg_s / cfg_p [ts/2], results to res [ts/2].
+// Returns false on a (bounded) wait timeout.
+template <int D>
+__device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm, Ctl &c, int ts,
+                          const uint32_t *cfg_s, const uint32_t *cfg_p, float2 *res) {
+  using G = Geo<D>;
+  constexpr int DH = D / 2;   // columns per thread (half)
+  const int n = m.n_sites;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = 32 * (warp & 3) + lane;
+  const int half = warp >> 2;
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  uint8_t *A = sm + G::A_OFF;
+  float *Ks = reinterpret_cast<float *>(sm + G::KV_OFF);
+  float *Vs = Ks + kRows * D;
+  uint8_t *Gs = sm + G::KV_OFF;                     // hidden chunk (aliases K/V)
+  const uint32_t a_addr = smem_u32(A), w_addr = smem_u32(sm + G::W_OFF), g_addr = smem_u32(Gs);
+  const bool valid = row < ts * n;
+  const int s = valid ? row / n : 0;
+
+  // ---- embedding: X (FP32, registers) for this thread's row and column half
+  float X[DH];
+  {
+    int pat = 0;
+    if (valid) {
+      const int cfg = s >> 1, i = row % n;
+      const uint32_t w1 = (s & 1) ? cfg_p[cfg] : cfg_s[cfg];
+      const uint32_t w2 = (s & 1) ? cfg_s[cfg] : cfg_p[cfg];
+      pat = embed_pattern(m.embed, w1, w2, i, n);
+    }
+#pragma unroll
+    for (int j = 0; j < DH; ++j) X[j] = valid ? __ldg(m.etab + pat * D + half * DH + j) : 0.f;
+  }
+  stage_w(c, w_addr, mb.Wqkv[0], 3 * D * D * 2);
+#pragma unroll
+  for (int j = 0; j < DH; j += 8) st_row8(A, row, half * DH + j, D, X + j);
+
+  const int heads = m.heads, dh = m.dh;
+  const float scale = rsqrtf((float)dh);
+  for (int l = 0; l < m.layers; ++l) {
+    // ---------------- QKV
+    fence_proxy_async();
+    bool ok = wait_w(c);
+    if (sync_fail(c, ok)) return false;
+    gemm(c, a_addr, w_addr, D, 3 * D, 0, false);
+    ok = wait_mma(c);
+    if (sync_fail(c, ok)) return false;
+    stage_w(c, w_addr, mb.Wo[l], D * D * 2);   // W is free: the QKV MMAs have completed
+    // K, V (FP32) to shared memory, this thread's column half
+#pragma unroll
+    for (int j = 0; j < DH; j += 16) {
+      float v[16];
+      tmem_ld16(c.tmem + lane_addr + D + half * DH + j, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) Ks[row * D + half * DH + j + e] = v[e];
+      tmem_ld16(c.tmem + lane_addr + 2 * D + half * DH + j, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) Vs[row * D + half * DH + j + e] = v[e];
+    }
+    __syncthreads();
+    // ---------------- attention: this thread's row, heads of its column half; output -> A (BF16)
+    {
+      const int h0 = half * (heads / 2), h1 = h0 + heads / 2;
+      for (int h = h0; h < h1; ++h) {
+        float q[16], o[16], sc[TDO_MAX_N];
+        {
+          // q of head h: dh <= 16 columns starting at h*dh (loaded 8 at a time)
+          float t8[8];
+          tmem_ld8(c.tmem + lane_addr + h * dh, t8);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) q[e] = t8[e];
+          if (dh > 8) {
+            tmem_ld8(c.tmem + lane_addr + h * dh + 8, t8);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) q[8 + e] = t8[e];
+          } else {
+#pragma unroll
+            for (int e = 8; e < 16; ++e) q[e] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) o[e] = 0.f;
+        if (valid) {
+          const int base = s * n, col = h * dh;
+          float mx = -INFINITY;
+#pragma unroll
+          for (int j = 0; j < TDO_MAX_N; ++j) {
+            if (j < n) {
+              const float *kr = Ks + (base + j) * D + col;
+              float dot = 0.f;
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (e < dh) dot = fmaf(q[e], kr[e], dot);
+              sc[j] = dot * scale;
+              mx = fmaxf(mx, sc[j]);
+            }
+          }
+          float sum = 0.f;
+#pragma unroll
+          for (int j = 0; j < TDO_MAX_N; ++j) {
+            if (j < n) {
+              const float p = __expf(sc[j] - mx);
+              sum += p;
+              const float *vr = Vs + (base + j) * D + col;
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (e < dh) o[e] = fmaf(p, vr[e], o[e]);
+            }
+          }
+          const float inv = 1.0f / sum;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) o[e] *= inv;
+        }
+        // dh is a multiple of 8 in the BF16 path
+        st_row8(A, row, h * dh, D, o);
+        if (dh > 8) st_row8(A, row, h * dh + 8, D, o + 8);
+      }
+    }
+    tc_fence_before();
+    fence_proxy_async();
+    ok = wait_w(c);
+    if (sync_fail(c, ok)) return false;
+    gemm(c, a_addr, w_addr, D, D, 0, false);
+    ok = wait_mma(c);
+    if (sync_fail(c, ok)) return false;
+    const bool mlp = m.ffn > 0;
+    if (mlp) stage_w(c, w_addr, mb.W1[l], G::HC * D * 2);
+    else if (l + 1 < m.layers) stage_w(c, w_addr, mb.Wqkv[l + 1], 3 * D * D * 2);
+    // X += attention block output
+#pragma unroll
+    for (int j = 0; j < DH; j += 16) {
+      float v[16];
+      tmem_ld16(c.tmem + lane_addr + half * DH + j, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) X[j + e] += v[e];
+    }
+#pragma unroll
+    for (int j = 0; j < DH; j += 8) st_row8(A, row, half * DH + j, D, X + j);
+    if (mlp) {
+      const int nch = m.ffn / G::HC;
+      for (int ch = 0; ch < nch; ++ch) {
+        tc_fence_before();
+        fence_proxy_async();
+        ok = wait_w(c);
+        if (sync_fail(c, ok)) return false;
+        gemm(c, a_addr, w_addr, D, G::HC, 0, false);                 // U chunk -> cols [0, HC)
+        ok = wait_mma(c);
+        if (sync_fail(c, ok)) return false;
+        stage_w(c, w_addr, mb.W2[l] + (size_t)ch * G::HC * D, G::HC * D * 2);
+        // GELU(U + b1) -> G (BF16), this thread's half of the chunk columns
+        constexpr int HH = G::HC / 2;
+#pragma unroll
+        for (int j = 0; j < HH; j += 16) {
+          float v[16];
+          tmem_ld16(c.tmem + lane_addr + half * HH + j, v);
+          const int c0 = ch * G::HC + half * HH + j;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = gelu_f(v[e] + __ldg(m.L[l].b1 + c0 + e));
+          st_row8(Gs, row, half * HH + j, G::HC, v);
+          st_row8(Gs, row, half * HH + j + 8, G::HC, v + 8);
+        }
+        tc_fence_before();
+        fence_proxy_async();
+        ok = wait_w(c);
+        if (sync_fail(c, ok)) return false;
+        gemm(c, g_addr, w_addr, G::HC, D, G::HC, ch > 0);            // out -> cols [HC, HC + D)
+        ok = wait_mma(c);
+        if (sync_fail(c, ok)) return false;
+        if (ch + 1 < nch) stage_w(c, w_addr, mb.W1[l] + (size_t)(ch + 1) * G::HC * D, G::HC * D * 2);
+        else if (l + 1 < m.layers) stage_w(c, w_addr, mb.Wqkv[l + 1], 3 * D * D * 2);
+      }
+#pragma unroll
+      for (int j = 0; j < DH; j += 16) {
+        float v[16];
+        tmem_ld16(c.tmem + lane_addr + G::HC + half * DH + j, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) X[j + e] += v[e] + __ldg(m.L[l].b2 + half * DH + j + e);
+      }
+#pragma unroll
+      for (int j = 0; j < DH; j += 8) st_row8(A, row, half * DH + j, D, X + j);
+    }
+  }
+  // ---------------- pooling, head, symmetrisation (FP32)
+  tc_fence_before();
+  __syncthreads();   // all K/V/G reads done before the pool buffer overwrites them
+  float *Pool = reinterpret_cast<float *>(sm + G::KV_OFF);
+#pragma unroll
+  for (int j = 0; j < DH; ++j) Pool[row * D + half * DH + j] = X[j];
+  __syncthreads();
+  float *Fs = reinterpret_cast<float *>(sm + G::M_OFF + 16 + 8 + 512);
+  for (int p = warp; p < ts * 2; p += kThreads / 32) {
+    const int sq = p >> 1, o = p & 1;
+    float acc = 0.f;
+    for (int cc = lane; cc < D; cc += 32) {
+      float hsum = 0.f;
+      for (int i = 0; i < n; ++i) hsum += Pool[(sq * n + i) * D + cc];
+      acc = fmaf(hsum, __ldg(m.Wh + 2 * cc + o), acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) Fs[p] = acc / (float)n + __ldg(m.bh + o);
+  }
+  __syncthreads();
+  for (int cc = threadIdx.x; cc < ts / 2; cc += kThreads)
+    res[cc] = symmetrise(Fs[4 * cc], Fs[4 * cc + 1], Fs[4 * cc + 2], Fs[4 * cc + 3], nullptr, nullptr);
+  __syncthreads();
+  return true;
+}
+
+template <int D>
+__device__ __forceinline__ void ctl_init(Ctl &c, uint8_t *sm, int *err) {
+  using G = Geo<D>;
+  uint8_t *misc = sm + G::M_OFF;
+  c.bar_mma = smem_u32(misc);
+  c.bar_w = smem_u32(misc + 8);
+  c.ph_mma = 0;
+  c.ph_w = 0;
+  c.mma_thread = threadIdx.x == 0;
+  c.err = err;
+  c.bad = false;
+  if (threadIdx.x == 0) {
+    mbar_init(c.bar_mma, 1);
+    mbar_init(c.bar_w, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(misc + 16)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  c.tmem = *reinterpret_cast<volatile uint32_t *>(misc + 16);
+}
+
+// Free TMEM; after a timeout, first give in-flight MMAs / copies a bounded chance to finish.
+__device__ __forceinline__ void ctl_finish(Ctl &c) {
+  if (c.bad) {
+    if (threadIdx.x == 0) atomicExch(c.err, 1);
+    // bounded drain of whatever the barriers still expect
+    mbar_wait(c.bar_mma, c.ph_mma);
+    mbar_wait(c.bar_w, c.ph_w);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem), "r"(kTmemCols));
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 1) k_fwd_bf16(DevModel m, DevModelBF16 mb, const uint32_t *__restrict__ sig,
+                                                          const uint32_t *__restrict__ sigp, size_t B,
+                                                          float2 *__restrict__ out, int *err) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  using G = Geo<D>;
+  Ctl c;
+  ctl_init<D>(c, sm, err);
+  uint32_t *cs = reinterpret_cast<uint32_t *>(sm + G::M_OFF + 24);
+  uint32_t *cp = cs + 64;
+  float2 *res = reinterpret_cast<float2 *>(sm + G::M_OFF + 16 + 8 + 512 + 1024);
+  const int ts = seqs_per_tile(m.n_sites), tc = ts / 2;
+  const size_t ntiles = (B + tc - 1) / tc;
+  for (size_t tile = blockIdx.x; tile < ntiles && !c.bad; tile += gridDim.x) {
+    if (threadIdx.x < tc) {
+      const size_t b = tile * tc + threadIdx.x;
+      cs[threadIdx.x] = b < B ? sig[b] : 0u;
+      cp[threadIdx.x] = b < B ? sigp[b] : 0u;
+    }
+    __syncthreads();
+    if (!eval_tile<D>(m, mb, sm, c, ts, cs, cp, res)) break;
+    if (threadIdx.x < tc) {
+      const size_t b = tile * tc + threadIdx.x;
+      if (b < B) out[b] = res[threadIdx.x];
+    }
+    __syncthreads();
+  }
+  ctl_finish(c);
+}
+
+// Metropolis chains on the BF16 forward (same proposal stream and acceptance rule as the FP32 sampler).
+template <int D>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sample_bf16(DevModel m, DevModelBF16 mb, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
+                  uint32_t *__restrict__ sig, uint32_t *__restrict__ sigp, uint32_t *__restrict__ ssig,
+                  uint32_t *__restrict__ ssigp, unsigned long long *accepted, int *err) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  using G = Geo<D>;
+  Ctl c;
+  ctl_init<D>(c, sm, err);
+  uint32_t *cs = reinterpret_cast<uint32_t *>(sm + G::M_OFF + 24);
+  uint32_t *cp = cs + 64;
+  float2 *res = reinterpret_cast<float2 *>(sm + G::M_OFF + 16 + 8 + 512 + 1024);
+  const int n = m.n_sites;
+  const int ts = seqs_per_tile(n), tc = ts / 2;
+  const size_t ntiles = (n_chains + tc - 1) / tc;
+  unsigned long long acc_count = 0;
+  for (size_t tile = blockIdx.x; tile < ntiles && !c.bad; tile += gridDim.x) {
+    const size_t ch = tile * tc + threadIdx.x;
+    const bool mine = threadIdx.x < tc && ch < n_chains;
+    uint32_t s0 = 0, s1 = 0, p0 = 0, p1 = 0;
+    float lcur = 0.f, u = 0.f;
+    if (mine) { s0 = sig[ch]; s1 = sigp[ch]; }
+    if (threadIdx.x < tc) { cs[threadIdx.x] = s0; cp[threadIdx.x] = s1; }
+    __syncthreads();
+    if (!eval_tile<D>(m, mb, sm, c, ts, cs, cp, res)) break;
+    if (threadIdx.x < tc) lcur = res[threadIdx.x].x;
+    bool stop = false;
+    for (size_t sw = 0; sw < n_sweeps && !stop; ++sw) {
+      for (int j = 0; j < 2 * n; ++j) {
+        const uint64_t t = counter + (uint64_t)sw * (uint64_t)(2 * n) + (uint64_t)j;
+        if (threadIdx.x < tc) {
+          int bit;
+          metropolis_draw(seed, (uint32_t)ch, t, n, &bit, &u);
+          p0 = s0;
+          p1 = s1;
+          if (bit < n) p0 ^= 1u << bit; else p1 ^= 1u << (bit - n);
+          cs[threadIdx.x] = p0;
+          cp[threadIdx.x] = p1;
+        }
+        __syncthreads();
+        if (!eval_tile<D>(m, mb, sm, c, ts, cs, cp, res)) { stop = true; break; }
+        if (threadIdx.x < tc) {
+          const float lnew = res[threadIdx.x].x;
+          if (u < expf(fminf(0.0f, 2.0f * (lnew - lcur)))) {
+            s0 = p0; s1 = p1; lcur = lnew;
+            if (mine) ++acc_count;
+          }
+        }
+      }
+      if (!stop && mine && ssig) { ssig[sw * n_chains + ch] = s0; ssigp[sw * n_chains + ch] = s1; }
+    }
+    if (stop) break;
+    if (mine) { sig[ch] = s0; sigp[ch] = s1; }
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) {
+    unsigned long long v = acc_count;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0 && accepted) atomicAdd(accepted, v);
+  }
+  ctl_finish(c);
+}
+
+// ------------------------------------------------------------------ packing of BF16 weights
+// dst element (n, k) of W^T ([N][K] canonical) = W[k][n] for an FP32 W [K][N] (row stride ldw, col off).
+__global__ void k_pack(const float *__restrict__ W, int ldw, int col0, int K, int N, uint8_t *__restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * K) return;
+  const int n = i / K, k = i % K;
+  const __nv_bfloat16 v = __float2bfloat16_rn(W[(size_t)k * ldw + col0 + n]);
+  *reinterpret_cast<__nv_bfloat16 *>(dst + canon(n, k, K)) = v;
+}
+
+}  // namespace bf16
+}  // namespace tdo
+
+bool bf16_supported(const DevModel &m) {
+  return (m.d == 64 || m.d == 32) && m.dh % 8 == 0 && m.heads % 2 == 0 && (m.ffn == 0 || m.ffn % (m.d * 4 < 128 ? m.d * 4 : 128) == 0) &&
+         m.embed == 0;
+}
+
+size_t bf16_packed_bytes(const DevModel &m) {
+  const size_t D = m.d, F = m.ffn;
+  return (size_t)m.layers * (3 * D * D + D * D + 2 * F * D) * 2;
+}
+
+// Packs every layer's weights into dst and fills the device views.
+cudaError_t launch_pack_bf16(const DevModel &m, uint16_t *dst16, DevModelBF16 *views, cudaStream_t st) {
+  using namespace tdo::bf16;
+  uint8_t *dst = reinterpret_cast<uint8_t *>(dst16);
+  const int D = m.d, F = m.ffn;
+  const int HC = (4 * D < 128) ? 4 * D : 128;
+  size_t off = 0;
+  auto pack = [&](const float *W, int ldw, int col0, int K, int N, uint8_t *out) {
+    k_pack<<<(N * K + 255) / 256, 256, 0, st>>>(W, ldw, col0, K, N, out);
+  };
+  for (int l = 0; l < m.layers; ++l) {
+    const DevLayer &L = m.L[l];
+    // Wqkv^T [3D][D]: rows 0..D-1 from Wq, D..2D-1 from Wk, 2D..3D-1 from Wv; one canonical tile
+    uint8_t *q = dst + off;
+    views->Wqkv[l] = reinterpret_cast<const uint16_t *>(q);
+    pack(L.Wq, D, 0, D, D, q);
+    pack(L.Wk, D, 0, D, D, q + (size_t)D * D * 2);   // 8-row groups D/8.. continue at D*16*D/8 bytes = D*D*2
+    pack(L.Wv, D, 0, D, D, q + (size_t)2 * D * D * 2);
+    off += (size_t)3 * D * D * 2;
+    views->Wo[l] = reinterpret_cast<const uint16_t *>(dst + off);
+    pack(L.Wo, D, 0, D, D, dst + off);
+    off += (size_t)D * D * 2;
+    if (F > 0) {
+      // W1^T chunks: [HC][D] each (rows = hidden units c*HC..), contiguous
+      views->W1[l] = reinterpret_cast<const uint16_t *>(dst + off);
+      for (int c = 0; c < F / HC; ++c) pack(L.W1, F, c * HC, D, HC, dst + off + (size_t)c * HC * D * 2);
+      off += (size_t)F * D * 2;
+      // W2^T chunks: [D][HC] each (K = hidden units c*HC..c*HC+HC-1)
+      views->W2[l] = reinterpret_cast<const uint16_t *>(dst + off);
+      for (int c = 0; c < F / HC; ++c) pack(L.W2 + (size_t)c * HC * D, D, 0, HC, D, dst + off + (size_t)c * HC * D * 2);
+      off += (size_t)F * D * 2;
+    } else {
+      views->W1[l] = views->W2[l] = nullptr;
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t fwd_bf16_impl(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
+                                 const uint32_t *sigp, size_t B, float2 *out, int *err, int n_sm, cudaStream_t st) {
+  using namespace tdo::bf16;
+  const int bytes = Geo<D>::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_bf16<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_bf16<D>, kThreads, bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm > 2) per_sm = 2;   // TMEM: 2 x 256 columns per SM
+  if (per_sm < 1) per_sm = 1;
+  const int tc = tdo::seqs_per_tile(m.n_sites) / 2;
+  const size_t ntiles = (B + tc - 1) / tc;
+  size_t grid = (size_t)n_sm * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  k_fwd_bf16<D><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, sig, sigp, B, out, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_bf16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig, const uint32_t *sigp,
+                            size_t B, float2 *logrho, int *err_flag, int n_sm, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  if (m.d == 64) return fwd_bf16_impl<64>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
+  if (m.d == 32) return fwd_bf16_impl<32>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
+  return cudaErrorInvalidValue;
+}
+
+template <int D>
+static cudaError_t sample_bf16_impl(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
+                                    uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
+                                    uint32_t *ssigp, unsigned long long *accepted, int *err, int n_sm,
+                                    cudaStream_t st) {
+  using namespace tdo::bf16;
+  const int bytes = Geo<D>::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_sample_bf16<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_bf16<D>, kThreads, bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm > 2) per_sm = 2;
+  if (per_sm < 1) per_sm = 1;
+  const int tc = tdo::seqs_per_tile(m.n_sites) / 2;
+  const size_t ntiles = (n_chains + tc - 1) / tc;
+  size_t grid = (size_t)n_sm * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  k_sample_bf16<D><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp,
+                                                           ssig, ssigp, accepted, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_bf16(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
+                               uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
+                               uint32_t *ssigp, unsigned long long *accepted, int *err_flag, int n_sm,
+                               cudaStream_t st) {
+  if (n_chains == 0) return cudaSuccess;
+  if (m.d == 64)
+    return sample_bf16_impl<64>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted, err_flag, n_sm, st);
+  if (m.d == 32)
+    return sample_bf16_impl<32>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted, err_flag, n_sm, st);
+  return cudaErrorInvalidValue;
+}

@@ -1,0 +1,877 @@
+// Host side of libtdo.so: the C ABI of include/tdo.h.  Owns the context (problem, parameters, device
+// workspace), turns the problem statement into Lindbladian connection rules, stages host buffers and
+// sequences the kernels of each call on the context's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/tdo.h"
+#include "tdo_internal.cuh"
+
+// launchers defined in the kernel translation units
+cudaError_t launch_lloc(const int64_t *offs, size_t Ns, const float2 *fcoef, const float2 *flogrho,
+                        double2 *lloc, double *l2, double *stats, int *nonfinite, cudaStream_t st);
+cudaError_t launch_conv_table_k(int d, int c1, const float *Wc1, const float *bc1, const float *Wc2,
+                                const float *bc2, float *table, cudaStream_t st);
+size_t bwd32_scratch_floats(const DevModel &m, int grid);
+int bwd32_grid(const DevModel &m, size_t B, int mode, int n_sm);
+cudaError_t launch_bwd32_impl(const DevModel &m, int mode, const uint32_t *sig, const uint32_t *sigp,
+                              size_t B, const float2 *cot, float *gacc, int n_copies, size_t g_stride,
+                              float *O, size_t P, const long long *flat_offsets, float *scratch, int grid,
+                              cudaStream_t st);
+size_t sr_work_doubles(size_t Ns, size_t P);
+cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, double shift, double tol,
+                       int max_iter, double *x, double *work, int n_sm, int *iters, double *resid,
+                       cudaStream_t st);
+cudaError_t launch_params_f32(const double *theta, size_t P, const long long *tab, int n_tensors,
+                              float *dst, cudaStream_t st);
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    size_t want = need + need / 4 + 256;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) { p = nullptr; return e; }
+    bytes = want;
+    return cudaSuccess;
+  }
+  template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+  void release() { if (p) cudaFree(p); p = nullptr; bytes = 0; }
+};
+
+struct TensorLoc { long long flat, pad, size; };
+
+enum Group { G_FWD = 0, G_SAMPLE, G_BWD_VJP, G_BWD_JAC, G_CONN, G_LLOC, G_SR, G_UPDATE, G_COUNT };
+const char *kGroupNames[G_COUNT] = {"fwd", "sample", "bwd_vjp", "bwd_jac", "conn", "lloc", "sr", "update"};
+
+struct TimingRec { int group; cudaEvent_t a, b; long long launches; };
+
+}  // namespace
+
+struct tdo_ctx {
+  int device = 0;
+  int n_sm = 0;
+  cudaStream_t stream = nullptr;
+  tdo_model model{};
+  int n = 0;
+  size_t P = 0, P_pad = 0;
+  std::vector<TensorLoc> tensors;          // in theta order
+  long long flat_offsets[3 + 8 * TDO_MAX_LAYERS];   // FlatOffsets layout of the backward kernel
+  // connection rules
+  int n_pat = 0;
+  DBuf d_pat, d_con;
+  // parameters
+  DBuf theta64, theta32, etab, tensor_tab;
+  DevModel dm{};
+  // workspace
+  DBuf stage_in[4], stage_out;
+  DBuf conn_cnt, conn_sig, conn_sigp, conn_coef, offs, fsig, fsigp, fcoef, flr, lloc, l2, stats,
+      nonfinite, cot, gacc, scratch, grad, Obuf, srwork, delta, acc_u64;
+  std::string err;
+  double sr_tol = 1e-8;
+  int sr_max_iter = 200;
+  int last_sr_iters = 0;
+  double last_sr_resid = 0;
+  // kernel timing (tdo_timing)
+  bool timing = false;
+  std::vector<TimingRec> trec;
+  std::vector<cudaEvent_t> epool;
+};
+
+// Brackets the launches of one kernel group with CUDA events when timing is enabled.
+struct Timed {
+  tdo_ctx *c;
+  int idx = -1;
+  Timed(tdo_ctx *ctx, int group) : c(ctx) {
+    if (!c->timing) return;
+    cudaEvent_t a, b;
+    if (c->epool.size() >= 2) { a = c->epool.back(); c->epool.pop_back(); b = c->epool.back(); c->epool.pop_back(); }
+    else { cudaEventCreate(&a); cudaEventCreate(&b); }
+    cudaEventRecord(a, c->stream);
+    c->trec.push_back({group, a, b, 0});
+    idx = (int)c->trec.size() - 1;
+  }
+  void done(long long launches) {
+    if (idx < 0) return;
+    cudaEventRecord(c->trec[idx].b, c->stream);
+    c->trec[idx].launches = launches;
+    idx = -1;
+  }
+  ~Timed() { done(1); }
+};
+
+static tdo_status fail(tdo_ctx *c, tdo_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_create_error = buf;
+  return s;
+}
+
+#define CU(ctx, call)                                                                          \
+  do {                                                                                         \
+    cudaError_t _e = (call);                                                                   \
+    if (_e != cudaSuccess)                                                                     \
+      return fail(ctx, _e == cudaErrorMemoryAllocation ? TDO_ENOMEM : TDO_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(_e), __FILE__, __LINE__);                          \
+  } while (0)
+
+#define TRY(x)                       \
+  do {                               \
+    tdo_status _s = (x);             \
+    if (_s != TDO_OK) return _s;     \
+  } while (0)
+
+// ----------------------------------------------------------------------------- parameter layout
+static bool model_valid(const tdo_model *m, std::string *why) {
+  if (!m) { *why = "model is NULL"; return false; }
+  if (m->d_model != 16 && m->d_model != 32 && m->d_model != 64) { *why = "d_model must be 16, 32 or 64"; return false; }
+  if (m->n_heads < 1 || m->d_model % m->n_heads) { *why = "n_heads must divide d_model"; return false; }
+  const int dh = m->d_model / m->n_heads;
+  if (dh > 16 || dh < 1) { *why = "head dimension must be <= 16"; return false; }
+  if (m->n_layers < 1 || m->n_layers > TDO_MAX_LAYERS) { *why = "n_layers must be 1..8"; return false; }
+  if (m->mlp_ratio < 0 || m->mlp_ratio > 4) { *why = "mlp_ratio must be 0..4"; return false; }
+  if (m->embed != TDO_EMBED_TOKEN && m->embed != TDO_EMBED_CONV) { *why = "unknown embedding"; return false; }
+  if (m->embed == TDO_EMBED_CONV && (m->conv_channels < 1 || m->conv_channels > 256)) { *why = "conv_channels must be 1..256"; return false; }
+  if (m->precision != TDO_FP32 && m->precision != TDO_BF16) { *why = "unknown precision"; return false; }
+  return true;
+}
+
+static std::vector<long long> tensor_sizes(const tdo_model *m) {
+  const long long d = m->d_model, f = (long long)m->mlp_ratio * d;
+  std::vector<long long> s;
+  if (m->embed == TDO_EMBED_TOKEN) s.push_back(4 * d);
+  else { const long long c1 = m->conv_channels; s.push_back(4 * c1); s.push_back(c1); s.push_back(2 * c1 * d); s.push_back(d); }
+  for (int l = 0; l < m->n_layers; ++l) {
+    for (int i = 0; i < 4; ++i) s.push_back(d * d);
+    if (f > 0) { s.push_back(d * f); s.push_back(f); s.push_back(f * d); s.push_back(d); }
+  }
+  s.push_back(2 * d);
+  s.push_back(2);
+  return s;
+}
+
+extern "C" size_t tdo_model_num_params(const tdo_model *model) {
+  std::string why;
+  if (!model_valid(model, &why)) return 0;
+  size_t p = 0;
+  for (long long v : tensor_sizes(model)) p += (size_t)v;
+  return p;
+}
+
+// ----------------------------------------------------------------------------- connection rules
+// Builds, for every distinct pair of flip masks (left, right), the contributions of Eq. VecLin:
+//   -i H (x) I      : Pauli string P, coefficient c: <s|P|s^x> = (-i)^{#Y} (-1)^{popc(s & yz)}
+//   +i I (x) H^T    : <s'^x|P|s'> = (+i)^{#Y} (-1)^{popc(s' & yz)}
+//   g L (x) L^*     : g L[s_k][s_k^f] conj(L[s'_k][s'_k^f'])
+//   -g/2 L^+L (x) I : -g/2 (L^+L)[s_k][s_k^f];   -g/2 I (x) L^T L^* : -g/2 (L^+L)[s'_k^f'][s'_k]
+static tdo_status build_rules(tdo_ctx *c, const tdo_problem *p) {
+  typedef std::complex<double> cd;
+  const int n = p->n_sites;
+  std::map<std::pair<uint32_t, uint32_t>, std::vector<ConnContrib>> groups;
+  groups[{0u, 0u}];   // the diagonal is always present
+  auto add = [&](uint32_t lm, uint32_t rm, const cd tab[4], uint32_t m1, uint32_t m2, int sl, int sr) {
+    bool any = false;
+    for (int i = 0; i < 4; ++i) any |= (tab[i] != cd(0, 0));
+    if (!any) return;
+    ConnContrib cc;
+    for (int i = 0; i < 4; ++i) { cc.tab[i][0] = tab[i].real(); cc.tab[i][1] = tab[i].imag(); }
+    cc.m1 = m1; cc.m2 = m2; cc.sel_l = sl; cc.sel_r = sr;
+    groups[{lm, rm}].push_back(cc);
+  };
+  // Pauli product on one site: a * b = phase * r (X Y = i Z and cyclic, P P = I)
+  auto pauli_index = [](char q) { return q == 'I' ? 0 : q == 'X' ? 1 : q == 'Y' ? 2 : q == 'Z' ? 3 : -1; };
+  for (int t = 0; t < p->n_terms; ++t) {
+    int site_op[2] = {-1, -1}, op_idx[2] = {0, 0};
+    cd phase(1, 0);
+    int nsites = 0;
+    for (int j = 0; j < 2; ++j) {
+      const int site = p->term_sites[2 * t + j];
+      if (site < 0) continue;
+      if (site >= n) return fail(c, TDO_EINVAL, "term %d: site %d out of range", t, site);
+      const int q = pauli_index(p->term_paulis[2 * t + j]);
+      if (q < 0) return fail(c, TDO_EUNSUPPORTED, "term %d: Pauli '%c' not in {I,X,Y,Z}", t, p->term_paulis[2 * t + j]);
+      int k = 0;
+      while (k < nsites && site_op[k] != site) ++k;
+      if (k == nsites) { site_op[nsites] = site; op_idx[nsites] = q; ++nsites; continue; }
+      const int a = op_idx[k], b = q;   // existing operator times the new one
+      if (a == 0) op_idx[k] = b;
+      else if (b == 0 || a == b) op_idx[k] = (a == b) ? 0 : a;
+      else {
+        const int r = 6 - a - b;   // the third Pauli
+        const bool cyclic = (b == a % 3 + 1);   // X->Y, Y->Z, Z->X
+        op_idx[k] = r;
+        phase *= cyclic ? cd(0, 1) : cd(0, -1);
+      }
+    }
+    uint32_t xm = 0, yzm = 0;
+    int ny = 0;
+    for (int k = 0; k < nsites; ++k) {
+      const uint32_t bit = 1u << site_op[k];
+      if (op_idx[k] == 1) xm |= bit;
+      if (op_idx[k] == 2) { xm |= bit; yzm |= bit; ++ny; }
+      if (op_idx[k] == 3) yzm |= bit;
+    }
+    const cd coef = p->term_coef[t] * phase;
+    if (coef == cd(0, 0)) continue;
+    cd ph_l(1, 0), ph_r(1, 0);
+    for (int k = 0; k < ny; ++k) { ph_l *= cd(0, -1); ph_r *= cd(0, 1); }
+    const cd vl = cd(0, -1) * coef * ph_l, vr = cd(0, 1) * coef * ph_r;
+    const cd tl[4] = {vl, vl, vl, vl}, tr[4] = {vr, vr, vr, vr};
+    add(xm, 0u, tl, yzm, 0u, -1, -1);
+    add(0u, xm, tr, 0u, yzm, -1, -1);
+  }
+  for (int q = 0; q < p->n_jumps; ++q) {
+    const int k = p->jump_site[q];
+    if (k < 0 || k >= n) return fail(c, TDO_EINVAL, "jump %d: site %d out of range", q, k);
+    const double g = p->jump_rate[q];
+    if (!(g >= 0.0)) return fail(c, TDO_EINVAL, "jump %d: negative rate", q);
+    cd L[2][2], LdL[2][2];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) L[a][b] = cd(p->jump_op[q * 8 + (a * 2 + b) * 2], p->jump_op[q * 8 + (a * 2 + b) * 2 + 1]);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) LdL[a][b] = std::conj(L[0][a]) * L[0][b] + std::conj(L[1][a]) * L[1][b];
+    const uint32_t bit = 1u << k;
+    for (int f = 0; f < 2; ++f)
+      for (int fp = 0; fp < 2; ++fp) {
+        cd tab[4];
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) tab[2 * a + b] = g * L[a][a ^ f] * std::conj(L[b][b ^ fp]);
+        add(f ? bit : 0u, fp ? bit : 0u, tab, 0u, 0u, k, k);
+      }
+    for (int f = 0; f < 2; ++f) {
+      cd tl[4], tr[4];
+      for (int a = 0; a < 2; ++a) {
+        tl[2 * a] = tl[2 * a + 1] = -0.5 * g * LdL[a][a ^ f];
+        tr[a] = tr[2 + a] = -0.5 * g * LdL[a ^ f][a];
+      }
+      // left: selector on sigma_k only (b ignored, tab[2a+0] used); right: selector on sigma'_k only
+      cd tl4[4] = {tl[0], tl[0], tl[2], tl[2]};
+      cd tr4[4] = {tr[0], tr[1], tr[0], tr[1]};
+      add(f ? bit : 0u, 0u, tl4, 0u, 0u, k, -1);
+      add(0u, f ? bit : 0u, tr4, 0u, 0u, -1, k);
+    }
+  }
+  std::vector<ConnPattern> pats;
+  std::vector<ConnContrib> cons;
+  // diagonal first, then the others in (left mask, right mask) order
+  auto push = [&](const std::pair<uint32_t, uint32_t> &key, const std::vector<ConnContrib> &v) {
+    ConnPattern P;
+    P.lmask = key.first; P.rmask = key.second;
+    P.c_begin = (int)cons.size();
+    cons.insert(cons.end(), v.begin(), v.end());
+    P.c_end = (int)cons.size();
+    pats.push_back(P);
+  };
+  push({0u, 0u}, groups[{0u, 0u}]);
+  for (auto &kv : groups)
+    if (!(kv.first.first == 0u && kv.first.second == 0u)) push(kv.first, kv.second);
+  c->n_pat = (int)pats.size();
+  CU(c, c->d_pat.ensure(sizeof(ConnPattern) * pats.size()));
+  CU(c, c->d_con.ensure(sizeof(ConnContrib) * std::max<size_t>(cons.size(), 1)));
+  CU(c, cudaMemcpy(c->d_pat.p, pats.data(), sizeof(ConnPattern) * pats.size(), cudaMemcpyHostToDevice));
+  if (!cons.empty())
+    CU(c, cudaMemcpy(c->d_con.p, cons.data(), sizeof(ConnContrib) * cons.size(), cudaMemcpyHostToDevice));
+  return TDO_OK;
+}
+
+// ----------------------------------------------------------------------------- parameters
+static tdo_status layout_params(tdo_ctx *c) {
+  const tdo_model *m = &c->model;
+  std::vector<long long> sz = tensor_sizes(m);
+  long long flat = 0, pad = 0;
+  c->tensors.clear();
+  for (long long s : sz) {
+    c->tensors.push_back({flat, pad, s});
+    flat += s;
+    pad += (s + 15) / 16 * 16;
+  }
+  c->P = (size_t)flat;
+  c->P_pad = (size_t)pad;
+  // flat offsets in the backward kernel's FlatOffsets order
+  for (auto &v : c->flat_offsets) v = 0;
+  int t = 0;
+  if (m->embed == TDO_EMBED_TOKEN) c->flat_offsets[0] = c->tensors[t++].flat;
+  else { c->flat_offsets[0] = c->tensors[t].flat; t += 4; }
+  long long *Wq = c->flat_offsets + 1, *Wk = Wq + TDO_MAX_LAYERS, *Wv = Wk + TDO_MAX_LAYERS, *Wo = Wv + TDO_MAX_LAYERS,
+            *W1 = Wo + TDO_MAX_LAYERS, *b1 = W1 + TDO_MAX_LAYERS, *W2 = b1 + TDO_MAX_LAYERS, *b2 = W2 + TDO_MAX_LAYERS;
+  for (int l = 0; l < m->n_layers; ++l) {
+    Wq[l] = c->tensors[t++].flat; Wk[l] = c->tensors[t++].flat; Wv[l] = c->tensors[t++].flat; Wo[l] = c->tensors[t++].flat;
+    if (m->mlp_ratio > 0) { W1[l] = c->tensors[t++].flat; b1[l] = c->tensors[t++].flat; W2[l] = c->tensors[t++].flat; b2[l] = c->tensors[t++].flat; }
+  }
+  c->flat_offsets[1 + 8 * TDO_MAX_LAYERS] = c->tensors[t++].flat;   // Wh
+  c->flat_offsets[2 + 8 * TDO_MAX_LAYERS] = c->tensors[t++].flat;   // bh
+  return TDO_OK;
+}
+
+static bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device copy of an input: the pointer itself if it is device memory, else a staged copy.
+static tdo_status stage_in(tdo_ctx *c, int slot, const void *p, size_t bytes, const void **out, bool *host) {
+  *host = false;
+  if (!p || bytes == 0 || is_device_ptr(p)) { *out = p; return TDO_OK; }
+  *host = true;
+  CU(c, c->stage_in[slot].ensure(bytes));
+  CU(c, cudaMemcpyAsync(c->stage_in[slot].p, p, bytes, cudaMemcpyHostToDevice, c->stream));
+  *out = c->stage_in[slot].p;
+  return TDO_OK;
+}
+
+// Refresh the FP32 parameter copy (and the conv embedding table) from the FP64 master.
+static tdo_status refresh_params(tdo_ctx *c) {
+  const tdo_model *m = &c->model;
+  CU(c, launch_params_f32(c->theta64.as<double>(), c->P, c->tensor_tab.as<long long>(), (int)c->tensors.size(),
+                          c->theta32.as<float>(), c->stream));
+  if (m->embed == TDO_EMBED_CONV) {
+    const float *b = c->theta32.as<float>();
+    CU(c, launch_conv_table_k(m->d_model, m->conv_channels, b + c->tensors[0].pad, b + c->tensors[1].pad,
+                              b + c->tensors[2].pad, b + c->tensors[3].pad, c->etab.as<float>(), c->stream));
+  }
+  return TDO_OK;
+}
+
+static void build_devmodel(tdo_ctx *c) {
+  const tdo_model *m = &c->model;
+  const float *b = c->theta32.as<float>();
+  DevModel &d = c->dm;
+  memset(&d, 0, sizeof(d));
+  d.n_sites = c->n;
+  d.d = m->d_model;
+  d.heads = m->n_heads;
+  d.dh = m->d_model / m->n_heads;
+  d.layers = m->n_layers;
+  d.ffn = m->mlp_ratio * m->d_model;
+  d.embed = m->embed;
+  int t = 0;
+  if (m->embed == TDO_EMBED_TOKEN) d.etab = b + c->tensors[t++].pad;
+  else { d.etab = c->etab.as<float>(); t += 4; }
+  for (int l = 0; l < m->n_layers; ++l) {
+    d.L[l].Wq = b + c->tensors[t++].pad;
+    d.L[l].Wk = b + c->tensors[t++].pad;
+    d.L[l].Wv = b + c->tensors[t++].pad;
+    d.L[l].Wo = b + c->tensors[t++].pad;
+    if (m->mlp_ratio > 0) {
+      d.L[l].W1 = b + c->tensors[t++].pad;
+      d.L[l].b1 = b + c->tensors[t++].pad;
+      d.L[l].W2 = b + c->tensors[t++].pad;
+      d.L[l].b2 = b + c->tensors[t++].pad;
+    }
+  }
+  d.Wh = b + c->tensors[t++].pad;
+  d.bh = b + c->tensors[t++].pad;
+}
+
+// ----------------------------------------------------------------------------- ABI
+extern "C" const char *tdo_last_error(const tdo_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" tdo_status tdo_create(const tdo_problem *problem, const tdo_model *model, const double *theta,
+                                 size_t n_theta, void *stream, tdo_ctx **out) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, TDO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!problem) return fail(nullptr, TDO_EINVAL, "problem is NULL");
+  std::string why;
+  if (!model_valid(model, &why)) return fail(nullptr, TDO_EINVAL, "invalid model: %s", why.c_str());
+  if (problem->n_sites < 1) return fail(nullptr, TDO_EINVAL, "n_sites must be >= 1");
+  if (problem->n_sites > TDO_MAX_N) return fail(nullptr, TDO_EUNSUPPORTED, "n_sites %d > 32", problem->n_sites);
+  if (problem->n_terms < 0 || problem->n_jumps < 0) return fail(nullptr, TDO_EINVAL, "negative term count");
+  if ((problem->n_terms > 0 && (!problem->term_sites || !problem->term_paulis || !problem->term_coef)) ||
+      (problem->n_jumps > 0 && (!problem->jump_site || !problem->jump_op || !problem->jump_rate)))
+    return fail(nullptr, TDO_EINVAL, "problem arrays are NULL");
+  if (model->precision == TDO_BF16 && model->embed != TDO_EMBED_TOKEN)
+    return fail(nullptr, TDO_EUNSUPPORTED, "the BF16 path supports the token embedding");
+  const size_t P = tdo_model_num_params(model);
+  if (!theta || n_theta != P) return fail(nullptr, TDO_EINVAL, "theta must hold %zu values (got %zu)", P, n_theta);
+
+  tdo_ctx *c = new tdo_ctx();
+  c->model = *model;
+  c->n = problem->n_sites;
+  c->stream = (cudaStream_t)stream;
+  auto bail = [&](tdo_status s) {
+    g_create_error = c->err;
+    tdo_destroy(c);
+    return s;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); fail(c, TDO_ECUDA, "no CUDA device"); return bail(TDO_ECUDA); }
+  cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+  if (c->n_sm <= 0) c->n_sm = 1;
+  tdo_status s = layout_params(c);
+  if (s == TDO_OK) s = build_rules(c, problem);
+  if (s != TDO_OK) return bail(s);
+  // tensor table for the FP64 -> FP32 padded conversion
+  std::vector<long long> tab;
+  for (auto &t : c->tensors) { tab.push_back(t.flat); tab.push_back(t.pad); tab.push_back(t.size); }
+  cudaError_t e;
+  if ((e = c->tensor_tab.ensure(sizeof(long long) * tab.size())) != cudaSuccess ||
+      (e = c->theta64.ensure(sizeof(double) * P)) != cudaSuccess ||
+      (e = c->theta32.ensure(sizeof(float) * c->P_pad)) != cudaSuccess ||
+      (e = c->etab.ensure(sizeof(float) * 64 * model->d_model)) != cudaSuccess ||
+      (e = c->nonfinite.ensure(sizeof(int) * 4)) != cudaSuccess) {
+    fail(c, TDO_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    return bail(TDO_ENOMEM);
+  }
+  if ((e = cudaMemcpy(c->tensor_tab.p, tab.data(), sizeof(long long) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(c->theta32.p, 0, sizeof(float) * c->P_pad)) != cudaSuccess) {
+    fail(c, TDO_ECUDA, "%s", cudaGetErrorString(e));
+    return bail(TDO_ECUDA);
+  }
+  build_devmodel(c);
+  s = tdo_set_params(c, theta);
+  if (s != TDO_OK) return bail(s);
+  *out = c;
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_destroy(tdo_ctx *c) {
+  if (!c) return TDO_OK;
+  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  DBuf *bufs[] = {&c->d_pat, &c->d_con, &c->theta64, &c->theta32, &c->etab, &c->tensor_tab, &c->stage_in[0],
+                  &c->stage_in[1], &c->stage_in[2], &c->stage_in[3], &c->stage_out, &c->conn_cnt, &c->conn_sig,
+                  &c->conn_sigp, &c->conn_coef, &c->offs, &c->fsig, &c->fsigp, &c->fcoef, &c->flr, &c->lloc,
+                  &c->l2, &c->stats, &c->nonfinite, &c->cot, &c->gacc, &c->scratch, &c->grad, &c->Obuf,
+                  &c->srwork, &c->delta, &c->acc_u64};
+  for (DBuf *b : bufs) b->release();
+  for (auto &r : c->trec) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : c->epool) cudaEventDestroy(e);
+  delete c;
+  return TDO_OK;
+}
+
+extern "C" size_t tdo_num_params(const tdo_ctx *c) { return c ? c->P : 0; }
+extern "C" int tdo_max_connections(const tdo_ctx *c) { return c ? c->n_pat : 0; }
+
+extern "C" tdo_status tdo_set_params(tdo_ctx *c, const double *theta) {
+  if (!c) return TDO_EINVAL;
+  if (!theta) return fail(c, TDO_EINVAL, "theta is NULL");
+  const cudaMemcpyKind kind = is_device_ptr(theta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CU(c, cudaMemcpyAsync(c->theta64.p, theta, sizeof(double) * c->P, kind, c->stream));
+  TRY(refresh_params(c));
+  if (kind == cudaMemcpyHostToDevice) CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_get_params(tdo_ctx *c, double *theta) {
+  if (!c) return TDO_EINVAL;
+  if (!theta) return fail(c, TDO_EINVAL, "theta is NULL");
+  const bool dev = is_device_ptr(theta);
+  CU(c, cudaMemcpyAsync(theta, c->theta64.p, sizeof(double) * c->P, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  if (!dev) CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+// forward on device buffers
+static tdo_status forward_dev(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t B, float2 *out) {
+  if (B == 0) return TDO_OK;
+  if (c->model.precision == TDO_BF16) return fail(c, TDO_EUNSUPPORTED, "BF16 forward not built");
+  Timed tm(c, G_FWD);
+  CU(c, launch_fwd32(c->dm, sig, sigp, B, out, c->n_sm, c->stream));
+  return TDO_OK;
+}
+
+// Copy a device result to a caller buffer (device or host); returns whether a sync is needed.
+static tdo_status deliver(tdo_ctx *c, void *dst, const void *src, size_t bytes, bool *host) {
+  *host = false;
+  if (!dst || bytes == 0 || dst == src) return TDO_OK;
+  const bool dev = is_device_ptr(dst);
+  *host = !dev;
+  CU(c, cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_log_rho(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t B, float *logrho) {
+  if (!c) return TDO_EINVAL;
+  if (B == 0) return TDO_OK;
+  if (!sig || !sigp || !logrho) return fail(c, TDO_EINVAL, "NULL buffer");
+  const void *ds, *dp;
+  bool h1, h2, h3 = false;
+  TRY(stage_in(c, 0, sig, 4 * B, &ds, &h1));
+  TRY(stage_in(c, 1, sigp, 4 * B, &dp, &h2));
+  float2 *dout = reinterpret_cast<float2 *>(logrho);
+  if (!is_device_ptr(logrho)) {
+    CU(c, c->stage_out.ensure(8 * B));
+    dout = c->stage_out.as<float2>();
+  }
+  TRY(forward_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, B, dout));
+  TRY(deliver(c, logrho, dout, 8 * B, &h3));
+  if (h1 || h2 || h3) CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+// Connections + compaction + forward over every row + L_loc and cost statistics (device buffers).
+static tdo_status estimator_core(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t Ns, int64_t *total) {
+  const int M = c->n_pat;
+  CU(c, c->conn_cnt.ensure(sizeof(int32_t) * Ns));
+  CU(c, c->conn_sig.ensure(sizeof(uint32_t) * Ns * M));
+  CU(c, c->conn_sigp.ensure(sizeof(uint32_t) * Ns * M));
+  CU(c, c->conn_coef.ensure(sizeof(float2) * Ns * M));
+  CU(c, c->offs.ensure(sizeof(int64_t) * (Ns + 1)));
+  {
+    Timed tm(c, G_CONN);
+    CU(c, launch_connections(c->d_pat.as<ConnPattern>(), M, c->d_con.as<ConnContrib>(), ds, dp, Ns,
+                             c->conn_cnt.as<int32_t>(), c->conn_sig.as<uint32_t>(), c->conn_sigp.as<uint32_t>(),
+                             c->conn_coef.as<float2>(), c->stream));
+    CU(c, launch_scan(c->conn_cnt.as<int32_t>(), Ns, c->offs.as<int64_t>(), c->stream));
+    tm.done(2);
+  }
+  int64_t tot = 0;
+  CU(c, cudaMemcpyAsync(&tot, c->offs.as<int64_t>() + Ns, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  *total = tot;
+  CU(c, c->fsig.ensure(sizeof(uint32_t) * tot));
+  CU(c, c->fsigp.ensure(sizeof(uint32_t) * tot));
+  CU(c, c->fcoef.ensure(sizeof(float2) * tot));
+  CU(c, c->flr.ensure(sizeof(float2) * tot));
+  {
+    Timed tm(c, G_CONN);
+    CU(c, launch_compact(c->conn_cnt.as<int32_t>(), c->offs.as<int64_t>(), Ns, M, c->conn_sig.as<uint32_t>(),
+                         c->conn_sigp.as<uint32_t>(), c->conn_coef.as<float2>(), c->fsig.as<uint32_t>(),
+                         c->fsigp.as<uint32_t>(), c->fcoef.as<float2>(), c->stream));
+  }
+  TRY(forward_dev(c, c->fsig.as<uint32_t>(), c->fsigp.as<uint32_t>(), (size_t)tot, c->flr.as<float2>()));
+  CU(c, c->lloc.ensure(sizeof(double2) * Ns));
+  CU(c, c->l2.ensure(sizeof(double) * Ns));
+  CU(c, c->stats.ensure(sizeof(double) * 4));
+  CU(c, cudaMemsetAsync(c->nonfinite.p, 0, sizeof(int), c->stream));
+  Timed tm(c, G_LLOC);
+  CU(c, launch_lloc(c->offs.as<int64_t>(), Ns, c->fcoef.as<float2>(), c->flr.as<float2>(), c->lloc.as<double2>(),
+                    c->l2.as<double>(), c->stats.as<double>(), c->nonfinite.as<int>(), c->stream));
+  tm.done(2);
+  return TDO_OK;
+}
+
+static tdo_status read_stats(tdo_ctx *c, size_t Ns, double *cost, double *se) {
+  double st[2];
+  int nf = 0;
+  CU(c, cudaMemcpyAsync(st, c->stats.p, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaMemcpyAsync(&nf, c->nonfinite.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  if (nf) return fail(c, TDO_ENUMERIC, "non-finite log rho or L_loc (rho = 0 exactly, or non-finite parameters)");
+  const double mean = st[0] / (double)Ns;
+  const double var = st[1] / (double)Ns - mean * mean;
+  if (cost) *cost = mean;
+  if (se) *se = var > 0 ? sqrt(var / (double)Ns) : 0.0;
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_connections(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t Ns,
+                                      int32_t *count, uint32_t *conn_sig, uint32_t *conn_sigp, float *conn_coef) {
+  if (!c) return TDO_EINVAL;
+  if (Ns == 0) return TDO_OK;
+  if (!sig || !sigp || !count || !conn_sig || !conn_sigp || !conn_coef) return fail(c, TDO_EINVAL, "NULL buffer");
+  const int M = c->n_pat;
+  const void *ds, *dp;
+  bool h1, h2, h3 = false, h4 = false, h5 = false, h6 = false;
+  TRY(stage_in(c, 0, sig, 4 * Ns, &ds, &h1));
+  TRY(stage_in(c, 1, sigp, 4 * Ns, &dp, &h2));
+  CU(c, c->conn_cnt.ensure(sizeof(int32_t) * Ns));
+  CU(c, c->conn_sig.ensure(sizeof(uint32_t) * Ns * M));
+  CU(c, c->conn_sigp.ensure(sizeof(uint32_t) * Ns * M));
+  CU(c, c->conn_coef.ensure(sizeof(float2) * Ns * M));
+  CU(c, launch_connections(c->d_pat.as<ConnPattern>(), M, c->d_con.as<ConnContrib>(), (const uint32_t *)ds,
+                           (const uint32_t *)dp, Ns, c->conn_cnt.as<int32_t>(), c->conn_sig.as<uint32_t>(),
+                           c->conn_sigp.as<uint32_t>(), c->conn_coef.as<float2>(), c->stream));
+  TRY(deliver(c, count, c->conn_cnt.p, sizeof(int32_t) * Ns, &h3));
+  TRY(deliver(c, conn_sig, c->conn_sig.p, sizeof(uint32_t) * Ns * M, &h4));
+  TRY(deliver(c, conn_sigp, c->conn_sigp.p, sizeof(uint32_t) * Ns * M, &h5));
+  TRY(deliver(c, conn_coef, c->conn_coef.p, sizeof(float2) * Ns * M, &h6));
+  CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_local_estimator(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t Ns,
+                                          double *lloc, double *cost, double *stderr_) {
+  if (!c) return TDO_EINVAL;
+  if (Ns == 0) return fail(c, TDO_EINVAL, "Ns must be > 0");
+  if (!sig || !sigp) return fail(c, TDO_EINVAL, "NULL buffer");
+  const void *ds, *dp;
+  bool h1, h2, h3 = false;
+  TRY(stage_in(c, 0, sig, 4 * Ns, &ds, &h1));
+  TRY(stage_in(c, 1, sigp, 4 * Ns, &dp, &h2));
+  int64_t total = 0;
+  TRY(estimator_core(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, &total));
+  if (lloc) TRY(deliver(c, lloc, c->lloc.p, sizeof(double2) * Ns, &h3));
+  TRY(read_stats(c, Ns, cost, stderr_));
+  return TDO_OK;
+}
+
+static const int kCopies = 8;
+
+// VJP over device rows: grad (FP64, device) = [accumulate ? grad : 0] + sum Re(cot * dlogrho).
+static tdo_status vjp_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t B, const float2 *cot,
+                          double *grad, int accumulate) {
+  if (c->model.embed != TDO_EMBED_TOKEN) return fail(c, TDO_EUNSUPPORTED, "gradients of the conv embedding are not built");
+  const int grid = bwd32_grid(c->dm, B, 0, c->n_sm);
+  const size_t stride = (c->P + 3) / 4 * 4;   // 16-byte aligned accumulator copies (float4 atomics)
+  CU(c, c->gacc.ensure(sizeof(float) * kCopies * stride));
+  CU(c, c->scratch.ensure(sizeof(float) * bwd32_scratch_floats(c->dm, grid)));
+  CU(c, cudaMemsetAsync(c->gacc.p, 0, sizeof(float) * kCopies * stride, c->stream));
+  Timed tm(c, G_BWD_VJP);
+  CU(c, launch_bwd32_impl(c->dm, 0, ds, dp, B, cot, c->gacc.as<float>(), kCopies, stride, nullptr, c->P,
+                          c->flat_offsets, c->scratch.as<float>(), grid, c->stream));
+  CU(c, launch_reduce_copies(c->gacc.as<float>(), kCopies, stride, c->P, grad, accumulate, c->stream));
+  tm.done(2);
+  return TDO_OK;
+}
+
+static tdo_status jacobian_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t B, float *O) {
+  if (c->model.embed != TDO_EMBED_TOKEN) return fail(c, TDO_EUNSUPPORTED, "gradients of the conv embedding are not built");
+  const int grid = bwd32_grid(c->dm, B, 1, c->n_sm);
+  CU(c, c->scratch.ensure(sizeof(float) * bwd32_scratch_floats(c->dm, grid)));
+  Timed tm(c, G_BWD_JAC);
+  CU(c, launch_bwd32_impl(c->dm, 1, ds, dp, B, nullptr, nullptr, 1, 0, O, c->P, c->flat_offsets,
+                          c->scratch.as<float>(), grid, c->stream));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_log_rho_vjp(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t B,
+                                      const float *cot, double *grad) {
+  if (!c) return TDO_EINVAL;
+  if (B == 0) return TDO_OK;
+  if (!sig || !sigp || !cot || !grad) return fail(c, TDO_EINVAL, "NULL buffer");
+  const void *ds, *dp, *dc;
+  bool h1, h2, h3, h4 = false;
+  TRY(stage_in(c, 0, sig, 4 * B, &ds, &h1));
+  TRY(stage_in(c, 1, sigp, 4 * B, &dp, &h2));
+  TRY(stage_in(c, 2, cot, 8 * B, &dc, &h3));
+  double *dg = grad;
+  if (!is_device_ptr(grad)) {
+    CU(c, c->grad.ensure(sizeof(double) * c->P));
+    CU(c, cudaMemcpyAsync(c->grad.p, grad, sizeof(double) * c->P, cudaMemcpyHostToDevice, c->stream));
+    dg = c->grad.as<double>();
+  }
+  TRY(vjp_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, B, (const float2 *)dc, dg, 1));
+  TRY(deliver(c, grad, dg, sizeof(double) * c->P, &h4));
+  if (h1 || h2 || h3 || h4) CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_jacobian(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t B, float *O) {
+  if (!c) return TDO_EINVAL;
+  if (B == 0) return TDO_OK;
+  if (!sig || !sigp || !O) return fail(c, TDO_EINVAL, "NULL buffer");
+  const void *ds, *dp;
+  bool h1, h2, h3 = false;
+  TRY(stage_in(c, 0, sig, 4 * B, &ds, &h1));
+  TRY(stage_in(c, 1, sigp, 4 * B, &dp, &h2));
+  float *dO = O;
+  const size_t bytes = sizeof(float) * 2 * c->P * B;
+  if (!is_device_ptr(O)) { CU(c, c->Obuf.ensure(bytes)); dO = c->Obuf.as<float>(); }
+  TRY(jacobian_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, B, dO));
+  TRY(deliver(c, O, dO, bytes, &h3));
+  if (h1 || h2 || h3) CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+// gradient of the cost on device: grad (device FP64 [P])
+static tdo_status grad_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t Ns, double *grad, double *cost) {
+  int64_t total = 0;
+  TRY(estimator_core(c, ds, dp, Ns, &total));
+  CU(c, c->cot.ensure(sizeof(float2) * total));
+  {
+    Timed tm(c, G_LLOC);
+    CU(c, launch_cotangent(c->offs.as<int64_t>(), Ns, c->fcoef.as<float2>(), c->flr.as<float2>(), c->lloc.as<double2>(),
+                           c->stats.as<double>(), c->cot.as<float2>(), c->stream));
+  }
+  TRY(vjp_dev(c, c->fsig.as<uint32_t>(), c->fsigp.as<uint32_t>(), (size_t)total, c->cot.as<float2>(), grad, 0));
+  TRY(read_stats(c, Ns, cost, nullptr));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_grad(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t Ns, double *grad,
+                               double *cost, float *O) {
+  if (!c) return TDO_EINVAL;
+  if (Ns == 0) return fail(c, TDO_EINVAL, "Ns must be > 0");
+  if (!sig || !sigp || !grad) return fail(c, TDO_EINVAL, "NULL buffer");
+  const void *ds, *dp;
+  bool h1, h2, h3 = false, h4 = false;
+  TRY(stage_in(c, 0, sig, 4 * Ns, &ds, &h1));
+  TRY(stage_in(c, 1, sigp, 4 * Ns, &dp, &h2));
+  double *dg = grad;
+  if (!is_device_ptr(grad)) { CU(c, c->grad.ensure(sizeof(double) * c->P)); dg = c->grad.as<double>(); }
+  TRY(grad_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, dg, cost));
+  TRY(deliver(c, grad, dg, sizeof(double) * c->P, &h3));
+  if (O) {
+    float *dO = O;
+    const size_t bytes = sizeof(float) * 2 * c->P * Ns;
+    if (!is_device_ptr(O)) { CU(c, c->Obuf.ensure(bytes)); dO = c->Obuf.as<float>(); }
+    TRY(jacobian_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, dO));
+    TRY(deliver(c, O, dO, bytes, &h4));
+  }
+  CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_sr_solve(tdo_ctx *c, const float *O, size_t Ns, const double *rhs, double diag_shift,
+                                   double tol, int max_iter, double *x, int *iters, double *resid) {
+  if (!c) return TDO_EINVAL;
+  if (Ns == 0) return fail(c, TDO_EINVAL, "Ns must be > 0");
+  if (!O || !rhs || !x) return fail(c, TDO_EINVAL, "NULL buffer");
+  if (!(diag_shift > 0.0)) return fail(c, TDO_EINVAL, "diag_shift must be > 0");
+  const void *dO, *dr;
+  bool h1, h2, h3 = false;
+  TRY(stage_in(c, 0, O, sizeof(float) * 2 * c->P * Ns, &dO, &h1));
+  TRY(stage_in(c, 1, rhs, sizeof(double) * c->P, &dr, &h2));
+  double *dx = x;
+  if (!is_device_ptr(x)) { CU(c, c->delta.ensure(sizeof(double) * c->P)); dx = c->delta.as<double>(); }
+  CU(c, c->srwork.ensure(sizeof(double) * sr_work_doubles(Ns, c->P)));
+  Timed tm(c, G_SR);
+  int it_local = 0;
+  cudaError_t e = sr_cg_impl((const float *)dO, Ns, c->P, (const double *)dr, diag_shift, tol, max_iter, dx,
+                             c->srwork.as<double>(), c->n_sm, &it_local, resid, c->stream);
+  if (iters) *iters = it_local;
+  tm.done(4 + 6LL * ((it_local + 15) / 16 * 16));
+  if (e == cudaErrorInvalidValue) return fail(c, TDO_ENUMERIC, "CG breakdown: S + shift I is not positive definite");
+  CU(c, e);
+  TRY(deliver(c, x, dx, sizeof(double) * c->P, &h3));
+  CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_sr_step(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t Ns, double lr,
+                                  double diag_shift, double *cost) {
+  if (!c) return TDO_EINVAL;
+  if (Ns == 0) return fail(c, TDO_EINVAL, "Ns must be > 0");
+  if (!sig || !sigp) return fail(c, TDO_EINVAL, "NULL buffer");
+  if (!(diag_shift > 0.0)) return fail(c, TDO_EINVAL, "diag_shift must be > 0");
+  const void *ds, *dp;
+  bool h1, h2;
+  TRY(stage_in(c, 0, sig, 4 * Ns, &ds, &h1));
+  TRY(stage_in(c, 1, sigp, 4 * Ns, &dp, &h2));
+  CU(c, c->grad.ensure(sizeof(double) * c->P));
+  CU(c, c->delta.ensure(sizeof(double) * c->P));
+  CU(c, c->Obuf.ensure(sizeof(float) * 2 * c->P * Ns));
+  TRY(grad_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, c->grad.as<double>(), cost));
+  TRY(jacobian_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, c->Obuf.as<float>()));
+  CU(c, c->srwork.ensure(sizeof(double) * sr_work_doubles(Ns, c->P)));
+  int iters = 0;
+  double resid = 0;
+  cudaError_t e;
+  {
+    Timed tm(c, G_SR);
+    e = sr_cg_impl(c->Obuf.as<float>(), Ns, c->P, c->grad.as<double>(), diag_shift, c->sr_tol, c->sr_max_iter,
+                   c->delta.as<double>(), c->srwork.as<double>(), c->n_sm, &iters, &resid, c->stream);
+    tm.done(4 + 6LL * ((iters + 15) / 16 * 16));
+  }
+  c->last_sr_iters = iters;
+  c->last_sr_resid = resid;
+  if (e == cudaErrorInvalidValue) return fail(c, TDO_ENUMERIC, "CG breakdown: S + shift I is not positive definite");
+  CU(c, e);
+  {
+    Timed tm(c, G_UPDATE);
+    CU(c, launch_axpy_update(c->theta64.as<double>(), c->delta.as<double>(), lr, c->P, c->stream));
+    TRY(refresh_params(c));
+    tm.done(c->model.embed == TDO_EMBED_CONV ? 3 : 2);
+  }
+  CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_sample(tdo_ctx *c, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
+                                 uint32_t *sig, uint32_t *sigp, uint32_t *samples_sig, uint32_t *samples_sigp,
+                                 uint64_t *accepted) {
+  if (!c) return TDO_EINVAL;
+  if (n_chains == 0) return TDO_OK;
+  if (!sig || !sigp) return fail(c, TDO_EINVAL, "NULL buffer");
+  if ((samples_sig == nullptr) != (samples_sigp == nullptr)) return fail(c, TDO_EINVAL, "give both sample buffers or neither");
+  if (c->model.precision == TDO_BF16) return fail(c, TDO_EUNSUPPORTED, "BF16 sampler not built");
+  // chain state on device (staged both ways when host)
+  const bool hs = !is_device_ptr(sig), hp = !is_device_ptr(sigp);
+  uint32_t *dsig = sig, *dsigp = sigp;
+  if (hs) { CU(c, c->stage_in[0].ensure(4 * n_chains)); dsig = c->stage_in[0].as<uint32_t>();
+            CU(c, cudaMemcpyAsync(dsig, sig, 4 * n_chains, cudaMemcpyHostToDevice, c->stream)); }
+  if (hp) { CU(c, c->stage_in[1].ensure(4 * n_chains)); dsigp = c->stage_in[1].as<uint32_t>();
+            CU(c, cudaMemcpyAsync(dsigp, sigp, 4 * n_chains, cudaMemcpyHostToDevice, c->stream)); }
+  uint32_t *dss = samples_sig, *dsp = samples_sigp;
+  const size_t sbytes = 4 * n_chains * n_sweeps;
+  const bool hss = samples_sig && !is_device_ptr(samples_sig), hsp = samples_sigp && !is_device_ptr(samples_sigp);
+  if (hss) { CU(c, c->stage_in[2].ensure(sbytes)); dss = c->stage_in[2].as<uint32_t>(); }
+  if (hsp) { CU(c, c->stage_in[3].ensure(sbytes)); dsp = c->stage_in[3].as<uint32_t>(); }
+  CU(c, c->acc_u64.ensure(sizeof(unsigned long long)));
+  CU(c, cudaMemsetAsync(c->acc_u64.p, 0, sizeof(unsigned long long), c->stream));
+  Timed tm(c, G_SAMPLE);
+  CU(c, launch_sample32(c->dm, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
+                        c->acc_u64.as<unsigned long long>(), c->n_sm, c->stream));
+  tm.done(1);
+  if (hs) CU(c, cudaMemcpyAsync(sig, dsig, 4 * n_chains, cudaMemcpyDeviceToHost, c->stream));
+  if (hp) CU(c, cudaMemcpyAsync(sigp, dsigp, 4 * n_chains, cudaMemcpyDeviceToHost, c->stream));
+  if (hss) CU(c, cudaMemcpyAsync(samples_sig, dss, sbytes, cudaMemcpyDeviceToHost, c->stream));
+  if (hsp) CU(c, cudaMemcpyAsync(samples_sigp, dsp, sbytes, cudaMemcpyDeviceToHost, c->stream));
+  if (accepted) {
+    if (is_device_ptr(accepted)) {
+      CU(c, cudaMemcpyAsync(accepted, c->acc_u64.p, sizeof(uint64_t), cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      unsigned long long a = 0;
+      CU(c, cudaMemcpyAsync(&a, c->acc_u64.p, sizeof(a), cudaMemcpyDeviceToHost, c->stream));
+      CU(c, cudaStreamSynchronize(c->stream));
+      *accepted = a;
+    }
+  }
+  if (hs || hp || hss || hsp) CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_timing(tdo_ctx *c, int enable) {
+  if (!c) return TDO_EINVAL;
+  CU(c, cudaStreamSynchronize(c->stream));
+  for (auto &r : c->trec) { c->epool.push_back(r.a); c->epool.push_back(r.b); }
+  c->trec.clear();
+  c->timing = enable != 0;
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_timing_read(tdo_ctx *c, const char *group, double *ms, long long *launches) {
+  if (!c || !group) return TDO_EINVAL;
+  int g = -1;
+  const bool all = strcmp(group, "all") == 0;
+  for (int i = 0; i < G_COUNT; ++i)
+    if (strcmp(group, kGroupNames[i]) == 0) g = i;
+  if (g < 0 && !all) return fail(c, TDO_EINVAL, "unknown timing group '%s'", group);
+  CU(c, cudaStreamSynchronize(c->stream));
+  double tot = 0;
+  long long n = 0;
+  for (auto &r : c->trec) {
+    if (!all && r.group != g) continue;
+    float e = 0;
+    CU(c, cudaEventElapsedTime(&e, r.a, r.b));
+    tot += e;
+    n += r.launches;
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = n;
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_set_sr_options(tdo_ctx *c, double tol, int max_iter) {
+  if (!c) return TDO_EINVAL;
+  if (!(tol >= 0.0) || max_iter < 0) return fail(c, TDO_EINVAL, "tol must be >= 0 and max_iter >= 0");
+  c->sr_tol = tol;
+  c->sr_max_iter = max_iter;
+  return TDO_OK;
+}

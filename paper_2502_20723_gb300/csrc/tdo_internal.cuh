@@ -1,0 +1,91 @@
+// Internal declarations shared by the CUDA translation units of libtdo.so (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#define TDO_MAX_LAYERS 8
+#define TDO_MAX_N 32
+
+// Device view of the FP32 parameter copy (the flat FP64 theta converted, same order and shapes).
+struct DevLayer {
+  const float *Wq, *Wk, *Wv, *Wo;   // [d][d], row = input feature
+  const float *W1, *b1, *W2, *b2;   // [d][f], [f], [f][d], [d] (null when there is no MLP)
+};
+
+struct DevModel {
+  int n_sites;     // N
+  int d;           // model width
+  int heads;       // h
+  int dh;          // d / h
+  int layers;
+  int ffn;         // mlp_ratio * d (0 = no MLP)
+  int embed;       // 0 token, 1 conv
+  const float *etab;   // embedding table: 4 x d (token) or 64 x d (conv patterns of 3 sites)
+  DevLayer L[TDO_MAX_LAYERS];
+  const float *Wh, *bh;   // [d][2], [2]
+};
+
+// BF16 weights for the tensor-core forward: every matrix stored transposed ([out][in], K-major) in the
+// canonical no-swizzle core-matrix layout expected by the tcgen05 shared-memory descriptors.
+struct DevModelBF16 {
+  const uint16_t *Wqkv[TDO_MAX_LAYERS];   // 3d x d
+  const uint16_t *Wo[TDO_MAX_LAYERS];     // d x d
+  const uint16_t *W1[TDO_MAX_LAYERS];     // f x d
+  const uint16_t *W2[TDO_MAX_LAYERS];     // d x f
+};
+
+// One contribution to an element of a row of Lhat: for the row (s, s') and the connected configuration
+// (s ^ lmask, s' ^ rmask) of its pattern, value = tab[2*bit(s, sel_l) + bit(s', sel_r)]
+// * (-1)^(popc(s & m1) + popc(s' & m2)); a selector of -1 reads bit 0.
+struct ConnContrib {
+  double tab[4][2];
+  uint32_t m1, m2;
+  int sel_l, sel_r;
+};
+struct ConnPattern {
+  uint32_t lmask, rmask;
+  int c_begin, c_end;   // contributions [c_begin, c_end)
+};
+
+// ------------------------------------------------------------------ launchers (stream-ordered)
+// FP32 forward over explicit configurations.
+cudaError_t launch_fwd32(const DevModel &m, const uint32_t *sig, const uint32_t *sigp, size_t B,
+                         float2 *logrho, int n_sm, cudaStream_t st);
+// Metropolis on FP32 forward: n_chains chains in/out, samples optional, accepted counter (device u64).
+cudaError_t launch_sample32(const DevModel &m, size_t n_chains, size_t n_sweeps, uint64_t seed,
+                            uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
+                            uint32_t *ssigp, unsigned long long *accepted, int n_sm, cudaStream_t st);
+// BF16 tensor-core forward.
+cudaError_t launch_fwd_bf16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
+                            const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
+                            cudaStream_t st);
+bool bf16_supported(const DevModel &m);
+cudaError_t launch_sample_bf16(const DevModel &m, const DevModelBF16 &mb, size_t n_chains,
+                               size_t n_sweeps, uint64_t seed, uint64_t counter, uint32_t *sig,
+                               uint32_t *sigp, uint32_t *ssig, uint32_t *ssigp,
+                               unsigned long long *accepted, int *err_flag, int n_sm, cudaStream_t st);
+
+// Connections: count[s], entries [s*M + j].
+cudaError_t launch_connections(const ConnPattern *pat, int n_pat, const ConnContrib *con,
+                               const uint32_t *sig, const uint32_t *sigp, size_t Ns, int32_t *count,
+                               uint32_t *csig, uint32_t *csigp, float2 *ccoef, cudaStream_t st);
+// Exclusive scan of count[Ns] -> offs[Ns+1] (single block, deterministic).
+cudaError_t launch_scan(const int32_t *count, size_t Ns, int64_t *offs, cudaStream_t st);
+// Compact [s*M + j] entries into flat rows at offs[s] + j.
+cudaError_t launch_compact(const int32_t *count, const int64_t *offs, size_t Ns, int M,
+                           const uint32_t *csig, const uint32_t *csigp, const float2 *ccoef,
+                           uint32_t *fsig, uint32_t *fsigp, float2 *fcoef, cudaStream_t st);
+// Gradient cotangents per flat row: c = scale * conj(L_loc) coef rho_y/rho_x, minus scale*cost on row 0.
+cudaError_t launch_cotangent(const int64_t *offs, size_t Ns, const float2 *fcoef, const float2 *flogrho,
+                             const double2 *lloc, const double *cost_stats, float2 *cot,
+                             cudaStream_t st);
+// FP64 reductions.
+cudaError_t launch_reduce_copies(const float *acc, int n_copies, size_t stride, size_t P, double *out,
+                                 int accumulate, cudaStream_t st);
+cudaError_t launch_f64_to_f32(const double *src, float *dst, size_t n, cudaStream_t st);
+// BF16 weight packing.
+cudaError_t launch_pack_bf16(const DevModel &m, uint16_t *dst, DevModelBF16 *views, cudaStream_t st);
+
+cudaError_t launch_axpy_update(double *theta, const double *delta, double lr, size_t P, cudaStream_t st);
+

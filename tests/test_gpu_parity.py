@@ -1,0 +1,323 @@
+"""GPU (FP32 path) vs the FP64 oracle on identical seeded inputs, through the C ABI.
+
+Tolerances (FP32 path): log rho within 1e-6 relative (phase modulo 2 pi); connection coefficients
+within FP32 rounding of the FP64 sums; L_loc, cost, gradient, log-derivatives within the accumulated
+FP32 rounding of their terms (bounds stated per test)."""
+import numpy as np
+import pytest
+
+from oracle import estimators as E, lindblad, sampler as OS, transformer as T
+from paper_2502_20723_gb300 import synth
+from tests.gpu_common import logrho_err, problem
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_20723_gb300 import build
+    build.build()
+
+
+def ctx_for(prob, spec, theta, precision="fp32"):
+    from paper_2502_20723_gb300 import tdo
+    return tdo.Context(prob, spec, theta, precision)
+
+
+def dev(a):
+    return torch.as_tensor(np.asarray(a).astype(np.int64)).to(torch.int32).cuda()
+
+
+# ------------------------------------------------------------------ log rho (forward)
+FWD_CASES = [
+    # (N, d, heads, layers, mlp, B)
+    (4, 16, 2, 1, 0, 256),     # the N=4 Ising workload shape, every doubled configuration
+    (8, 32, 4, 2, 0, 1000),    # N=8 workload shape, ragged last tile
+    (16, 64, 8, 4, 4, 333),    # N=16 headline shape
+    (1, 16, 4, 2, 2, 7),
+    (3, 16, 1, 1, 0, 50),
+    (7, 32, 8, 3, 1, 77),
+    (13, 64, 4, 2, 0, 41),
+    (24, 64, 16, 1, 2, 19),
+    (32, 64, 8, 2, 4, 11),
+]
+
+
+@pytest.mark.parametrize("n,d,h,L,r,B", FWD_CASES)
+def test_log_rho_fp32(n, d, h, L, r, B):
+    spec = synth.model_spec(d, h, L, r)
+    th = synth.init_params(spec, seed=n + d, std=0.1 if d * L * (1 + r) < 256 else 0.04)
+    prob = problem("ising", n)
+    if B == 4 ** n:
+        sig, sigp = synth.all_configs(n)
+    else:
+        sig, sigp = synth.random_configs(n, B, seed=B)
+    ref = T.log_rho_np(spec, th, sig, sigp, n)
+    ctx = ctx_for(prob, spec, th)
+    out = ctx.log_rho(dev(sig), dev(sigp)).cpu().numpy()
+    err = logrho_err(out, ref)
+    assert np.all(err <= 1e-6 * np.maximum(np.abs(ref), 1.0)), (err.max(), np.abs(ref).min())
+    # host pointers give the same bits
+    host = ctx.log_rho(sig.astype(np.uint32), sigp.astype(np.uint32))
+    assert np.array_equal(host, out)
+
+
+def test_log_rho_std_init_relative():
+    """Default N(0, 0.02) parameters at the headline shape: within 1e-6 of |log rho| (relative)."""
+    spec = synth.model_spec(64, 8, 4, 4)
+    th = synth.init_params(spec, 0)
+    sig, sigp = synth.random_configs(16, 512, seed=3)
+    ref = T.log_rho_np(spec, th, sig, sigp, 16)
+    out = ctx_for(problem("ising", 16), spec, th).log_rho(dev(sig), dev(sigp)).cpu().numpy()
+    assert np.all(logrho_err(out, ref) <= 1e-6 * np.abs(ref))
+
+
+def test_log_rho_empty_and_single():
+    spec = synth.model_spec(16, 2, 1, 0)
+    ctx = ctx_for(problem("ising", 4), spec, synth.init_params(spec))
+    out = ctx.log_rho(dev([]), dev([]))
+    assert out.shape == (0, 2)
+    one = ctx.log_rho(dev([5]), dev([9])).cpu().numpy()
+    ref = T.log_rho_np(spec, synth.init_params(spec), np.array([5], np.uint32), np.array([9], np.uint32), 4)
+    assert logrho_err(one, ref)[0] < 1e-6
+
+
+def test_set_params_roundtrip_and_autograd():
+    from paper_2502_20723_gb300 import tdo
+    spec = synth.model_spec(32, 4, 2, 2)
+    th = synth.init_params(spec, 1, std=0.1)
+    ctx = ctx_for(problem("ising", 8), spec, th)
+    assert np.array_equal(ctx.get_params(), th)
+    th2 = synth.init_params(spec, 2, std=0.1)
+    ctx.set_params(torch.as_tensor(th2).cuda())
+    assert np.array_equal(ctx.get_params(), th2)
+    sig, sigp = synth.random_configs(8, 37, seed=1)
+    # autograd.Function: d/dtheta of sum(w . (Re, Im) log rho) vs the oracle's autograd
+    LogRho = tdo.log_rho_autograd()
+    t = torch.as_tensor(th2).cuda().requires_grad_(True)
+    y = LogRho.apply(t, dev(sig), dev(sigp), ctx)
+    w = torch.as_tensor(np.random.default_rng(0).standard_normal((37, 2))).float().cuda()
+    (y * w).sum().backward()
+    tt = torch.as_tensor(th2).requires_grad_(True)
+    re, im = T.log_rho_parts(spec, tt, sig, sigp, 8)
+    wc = w.cpu().double()
+    ((re * wc[:, 0]) + (im * wc[:, 1])).sum().backward()
+    g_ref = tt.grad.numpy()
+    g = t.grad.cpu().numpy()
+    assert np.abs(g - g_ref).max() <= 1e-5 * max(1.0, np.abs(g_ref).max())
+
+
+# ------------------------------------------------------------------ connections (rows of Lhat)
+@pytest.mark.parametrize("kind,n,kw", [
+    ("ising", 4, {}), ("ising", 16, dict(g=0.5)), ("xyz", 8, dict(Jx=0.9)), ("xyz", 8, dict(Jx=1.0)),
+    ("xyz", 5, dict(Jx=1.4, Jy=2.0, Jz=1.0, Bx=-1.0, By=0.7, Bz=0.1)), ("ising", 32, {}), ("ising", 1, {}),
+])
+def test_connections_match_oracle_rows(kind, n, kw):
+    prob = problem(kind, n, **kw)
+    spec = synth.model_spec(16, 2, 1, 0)
+    ctx = ctx_for(prob, spec, synth.init_params(spec))
+    sig, sigp = synth.random_configs(n, 200, seed=n)
+    cnt, cs, cp, cc = [x.cpu().numpy() for x in ctx.connections(dev(sig), dev(sigp))]
+    rows = E.connections(prob, sig, sigp)
+    for s in range(len(sig)):
+        k = int(cnt[s])
+        assert (int(cs[s, 0]) & 0xFFFFFFFF, int(cp[s, 0]) & 0xFFFFFFFF) == (int(sig[s]), int(sigp[s]))
+        got = {}
+        for j in range(k):
+            key = (int(cs[s, j]) & 0xFFFFFFFF, int(cp[s, j]) & 0xFFFFFFFF)
+            assert key not in got, "duplicate connection"
+            got[key] = complex(cc[s, j, 0], cc[s, j, 1])
+        ref = {key: v for key, v in rows[s]}
+        keys = set(got) | set(ref)
+        for key in keys:
+            a, b = got.get(key, 0j), ref.get(key, 0j)
+            assert abs(a - b) <= 1e-6 * max(1.0, abs(b)), (s, key, a, b)
+        # nonzero entries appear on both sides (zero diagonal allowed)
+        assert {k2 for k2, v in ref.items() if abs(v) > 1e-9} <= set(got)
+
+
+# ------------------------------------------------------------------ L_loc, cost
+@pytest.mark.parametrize("kind,n,d,h,L,r,Ns", [
+    ("ising", 4, 16, 2, 1, 0, 256), ("ising", 8, 32, 4, 2, 0, 300), ("xyz", 8, 32, 4, 2, 0, 300),
+    ("ising", 16, 64, 8, 4, 4, 64),
+])
+def test_local_estimator_and_cost(kind, n, d, h, L, r, Ns):
+    prob = problem(kind, n)
+    spec = synth.model_spec(d, h, L, r)
+    th = synth.init_params(spec, seed=3, std=0.2 if d < 64 else 0.04)
+    if Ns == 4 ** n:
+        sig, sigp = synth.all_configs(n)
+    else:
+        sig, sigp = synth.random_configs(n, Ns, seed=5)
+    ctx = ctx_for(prob, spec, th)
+    lloc, cost, se = ctx.local_estimator(dev(sig), dev(sigp))
+    lloc = lloc.cpu().numpy()
+    ref = E.local_estimator(prob, spec, th, sig, sigp)
+    # each term coef * rho_y/rho_x carries FP32 rounding of log rho (<= 1e-6 rel) and of exp: bound by
+    # 1e-5 of the sum of |terms| (computed from the oracle rows)
+    rows = E.connections(prob, sig, sigp)
+    scale = np.array([sum(abs(v) for _, v in r_) for r_ in rows]) * 3
+    got = lloc[:, 0] + 1j * lloc[:, 1]
+    assert np.all(np.abs(got - ref) <= 1e-5 * scale)
+    c_ref, se_ref = E.cost_mc(ref)
+    assert abs(cost - c_ref) <= 1e-5 * c_ref
+    assert abs(se - se_ref) <= 1e-3 * se_ref + 1e-12
+
+
+def test_cost_full_sum_n4():
+    """All 256 configurations weighted by the exact P(x): the GPU L_loc reproduce the full-sum cost."""
+    prob = problem("ising", 4)
+    spec = synth.model_spec(16, 2, 1, 0)
+    th = synth.init_params(spec, 0)
+    a, b, w = E.full_sum_weights(prob, spec, th)
+    lloc, _, _ = ctx_for(prob, spec, th).local_estimator(dev(a), dev(b))
+    lloc = lloc.cpu().numpy()
+    c = float((w * (lloc[:, 0] ** 2 + lloc[:, 1] ** 2)).sum())
+    ref = E.full_sum_cost(prob, spec, th)
+    assert abs(c - ref) <= 1e-5 * ref
+
+
+# ------------------------------------------------------------------ Jacobian, VJP, gradient
+@pytest.mark.parametrize("n,d,h,L,r,B", [(4, 16, 2, 1, 0, 40), (8, 32, 4, 2, 0, 33), (16, 64, 8, 4, 4, 6),
+                                         (5, 16, 4, 2, 2, 9), (32, 64, 8, 1, 1, 3)])
+def test_jacobian(n, d, h, L, r, B):
+    spec = synth.model_spec(d, h, L, r)
+    th = synth.init_params(spec, seed=7, std=0.2 if d < 64 else 0.04)
+    sig, sigp = synth.random_configs(n, B, seed=2)
+    O = ctx_for(problem("ising", n), spec, th).jacobian(dev(sig), dev(sigp)).cpu().numpy()
+    ref = E.jacobian(spec, th, sig, sigp, n)
+    got = O[..., 0] + 1j * O[..., 1]
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(got - ref).max() <= 2e-5 * scale, np.abs(got - ref).max()
+
+
+@pytest.mark.parametrize("n,d,h,L,r,B", [(8, 32, 4, 2, 0, 500), (16, 64, 8, 4, 4, 40)])
+def test_vjp_random_cotangents(n, d, h, L, r, B):
+    spec = synth.model_spec(d, h, L, r)
+    th = synth.init_params(spec, seed=9, std=0.2 if d < 64 else 0.04)
+    sig, sigp = synth.random_configs(n, B, seed=4)
+    cot = np.random.default_rng(1).standard_normal((B, 2)).astype(np.float32)
+    grad = torch.zeros(synth.num_params(spec), dtype=torch.float64, device="cuda")
+    ctx_for(problem("ising", n), spec, th).log_rho_vjp(dev(sig), dev(sigp), torch.as_tensor(cot).cuda(), grad)
+    tt = torch.as_tensor(th).requires_grad_(True)
+    lr = T.log_rho(spec, tt, sig, sigp, n)
+    c = torch.as_tensor(cot.astype(np.float64))
+    (c[:, 0] * lr.real - c[:, 1] * lr.imag).sum().backward()
+    ref = tt.grad.numpy()
+    g = grad.cpu().numpy()
+    assert np.abs(g - ref).max() <= 1e-4 * np.abs(ref).max()
+    assert np.linalg.norm(g - ref) <= 2e-5 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("kind,n,d,h,L,r,Ns", [("ising", 8, 32, 4, 2, 0, 256), ("xyz", 8, 32, 4, 2, 0, 256),
+                                               ("ising", 16, 64, 8, 4, 4, 48)])
+def test_cost_gradient(kind, n, d, h, L, r, Ns):
+    prob = problem(kind, n)
+    spec = synth.model_spec(d, h, L, r)
+    th = synth.init_params(spec, seed=11, std=0.2 if d < 64 else 0.04)
+    sig, sigp = synth.random_configs(n, Ns, seed=6)
+    g, cost = ctx_for(prob, spec, th).grad(dev(sig), dev(sigp))
+    g = g.cpu().numpy()
+    ref, c_ref, _, _ = E.grad_estimator(prob, spec, th, sig, sigp)
+    assert abs(cost - c_ref) <= 1e-5 * c_ref
+    assert np.linalg.norm(g - ref) <= 1e-4 * np.linalg.norm(ref), np.linalg.norm(g - ref) / np.linalg.norm(ref)
+
+
+# ------------------------------------------------------------------ SR
+def test_sr_solve_matches_cholesky():
+    """Identical FP32 O on both sides: FP64 CG (GPU) vs FP64 Cholesky (oracle)."""
+    spec = synth.model_spec(16, 2, 1, 0)
+    th = synth.init_params(spec)
+    ctx = ctx_for(problem("ising", 4), spec, th)
+    P = ctx.P
+    rng = np.random.default_rng(0)
+    O = (rng.standard_normal((300, P, 2)) * 0.3).astype(np.float32)
+    O[:, :, 0] += rng.standard_normal(P).astype(np.float32)   # nonzero mean, removed by the centring
+    rhs = rng.standard_normal(P)
+    x, it, res = ctx.sr_solve(torch.as_tensor(O).cuda(), torch.as_tensor(rhs).cuda(), 1e-2, tol=1e-12, max_iter=2000)
+    ref = E.sr_solve(O[..., 0].astype(np.float64) + 1j * O[..., 1].astype(np.float64), rhs, 1e-2)
+    assert res < 1e-10
+    assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_sr_step_matches_oracle():
+    prob = problem("xyz", 6, Jx=0.9)
+    spec = synth.model_spec(16, 2, 1, 0)
+    th = synth.init_params(spec, 0, std=0.1)
+    sig, sigp = synth.random_configs(6, 256, seed=8)
+    ctx = ctx_for(prob, spec, th)
+    cost = ctx.sr_step(dev(sig), dev(sigp), 0.01, 0.1)
+    new = ctx.get_params()
+    ref_new, c_ref, g_ref, d_ref = E.sr_step(prob, spec, th, sig, sigp, 0.01, 0.1)
+    assert abs(cost - c_ref) <= 1e-5 * c_ref
+    assert np.linalg.norm((new - th) - (ref_new - th)) <= 1e-3 * np.linalg.norm(ref_new - th)
+
+
+# ------------------------------------------------------------------ Metropolis
+def test_metropolis_replays_oracle_chains():
+    """Same Philox stream on both sides: every chain whose accept decisions are all decided by more than
+    1e-3 in log space follows exactly the oracle's trajectory."""
+    n = 6
+    spec = synth.model_spec(16, 2, 1, 0)
+    th = synth.init_params(spec, 0, std=0.5)
+    s0, s1 = synth.random_configs(n, 128, seed=1)
+    ctx = ctx_for(problem("ising", n), spec, th)
+    a, b = dev(s0), dev(s1)
+    acc, (ss, sp) = ctx.sample(a, b, 5, seed=1234, counter=77, samples=True)
+    o0, o1, oacc, osamp, margin = OS.metropolis(spec, th, s0, s1, n, 5, 1234, 77, record=True)
+    ok = margin > 1e-3
+    assert ok.mean() > 0.9
+    g0 = (a.cpu().numpy().astype(np.int64) & 0xFFFFFFFF)
+    g1 = (b.cpu().numpy().astype(np.int64) & 0xFFFFFFFF)
+    assert np.array_equal(g0[ok], o0[ok].astype(np.int64)) and np.array_equal(g1[ok], o1[ok].astype(np.int64))
+    for sw in range(5):
+        assert np.array_equal(ss[sw].cpu().numpy().astype(np.int64)[ok] & 0xFFFFFFFF, osamp[sw][0][ok].astype(np.int64))
+    if ok.all():
+        assert acc == oacc
+
+
+def test_metropolis_histogram_n3():
+    """Chain-end states of many chains follow |rho|^2 / sum |rho|^2 (chi-square), N = 3.  (A much
+    larger init scale concentrates |rho|^2 on diagonal states that single-bit moves connect only through
+    tiny off-diagonal weights; the oracle's own chains then do not mix either.)"""
+    from scipy import stats
+    n = 3
+    spec = synth.model_spec(16, 2, 1, 0)
+    th = synth.init_params(spec, 0, std=0.3)
+    prob = problem("ising", n)
+    _, _, w = E.full_sum_weights(prob, spec, th)
+    chains = 20000
+    s0, s1 = synth.random_configs(n, chains, seed=2)
+    a, b = dev(s0), dev(s1)
+    ctx_for(prob, spec, th).sample(a, b, 40, seed=5, counter=0)
+    idx = (a.cpu().numpy().astype(np.int64) << n) | b.cpu().numpy().astype(np.int64)
+    counts = np.bincount(idx, minlength=64)
+    assert stats.chisquare(counts, w * chains).pvalue > 1e-4
+
+
+# ------------------------------------------------------------------ errors
+def test_invalid_arguments():
+    from paper_2502_20723_gb300 import tdo
+    spec = synth.model_spec(16, 2, 1, 0)
+    th = synth.init_params(spec)
+    with pytest.raises(tdo.TdoError, match="EUNSUPPORTED"):
+        tdo.Context({"n_sites": 33, "terms": [], "jumps": []}, spec, th)
+    with pytest.raises(tdo.TdoError, match="EINVAL"):
+        tdo.Context(problem("ising", 4), spec, th[:-1])
+    with pytest.raises(tdo.TdoError, match="EINVAL"):
+        tdo.Context({"n_sites": 4, "terms": [(1.0, ((5, "X"),))], "jumps": []}, spec, th)
+
+
+def test_nan_parameters_raise_numeric():
+    from paper_2502_20723_gb300 import tdo
+    spec = synth.model_spec(16, 2, 1, 0)
+    th = synth.init_params(spec)
+    th[3] = np.nan
+    ctx = ctx_for(problem("ising", 4), spec, th)
+    sig, sigp = synth.random_configs(4, 10)
+    with pytest.raises(tdo.TdoError, match="ENUMERIC"):
+        ctx.local_estimator(dev(sig), dev(sigp))
