@@ -147,6 +147,7 @@ def run_ours(args) -> dict | None:
     ctx.timing(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     costs = []
+    sr_iters = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -156,6 +157,7 @@ def run_ours(args) -> dict | None:
             ev[i][0].record(stream)
             costs.append(step())
             ev[i][1].record(stream)
+            sr_iters.append(ctx.sr_info()[0])
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -246,6 +248,7 @@ def run_ours(args) -> dict | None:
         "rows_per_step": {"lloc_rows": lloc_rows, "sample_evals": sample_evals},
         "breakdown_ms_per_step": {g: round(v["ms"], 3) for g, v in groups.items()},
         "cost_last": costs[-1],
+        "sr_cg_iterations": sr_iters,
         "roofline": roof,
         "clocks": clocks,
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "VMC steps/s",

@@ -144,7 +144,8 @@ tdo_status tdo_grad(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, siz
 tdo_status tdo_sr_solve(tdo_ctx *ctx, const float *O, size_t Ns, const double *rhs, double diag_shift,
                         double tol, int max_iter, double *x, int *iters, double *resid);
 
-/* Stopping rule of the CG solve inside tdo_sr_step (defaults: tol 1e-8, max_iter 200). */
+/* Stopping rule of the CG solve inside tdo_sr_step (defaults: tol 1e-6, max_iter 100).  The solve
+ * starts from the previous step's solution when there is one (reset by tdo_set_params). */
 tdo_status tdo_set_sr_options(tdo_ctx *ctx, double tol, int max_iter);
 
 /* One optimisation-workflow step on a given sample set: cost and gradient, log-derivatives,
@@ -162,6 +163,9 @@ tdo_status tdo_timing(tdo_ctx *ctx, int enable);
  * (log-derivatives), "conn" (connections, scan, compaction), "lloc" (L_loc, cost, cotangents),
  * "sr" (CG solve), "update" (parameter update and refresh), or "all".  Synchronises the stream. */
 tdo_status tdo_timing_read(tdo_ctx *ctx, const char *group, double *ms, long long *launches);
+
+/* Iterations and final relative residual of the last tdo_sr_step's CG solve. */
+tdo_status tdo_sr_info(const tdo_ctx *ctx, int *iters, double *resid);
 
 /* Message of the last failing call on this context (or of the last failed tdo_create when ctx is NULL). */
 const char *tdo_last_error(const tdo_ctx *ctx);

@@ -5,7 +5,8 @@
 // the cotangent of log rho through the Hermitian symmetrisation (Eq. log_sum_exp_conjugate), the head,
 // the mean pooling, every layer in reverse (MLP, W^O, softmax attention, Q/K/V) and the embedding.
 // Weight gradients are D x D blocks reduced over the rows of the tile:
-//   mode 0 (VJP): summed over the tile and added to one of n_copies FP32 accumulator vectors,
+//   mode 0 (VJP): summed over the tile and added (plain read-modify-write, no atomics) to the CTA's own
+//                 FP32 accumulator vector; the host reduces the per-CTA vectors in FP64 (deterministic),
 //   mode 1 (Jacobian): one per (configuration, seed) and written to O[b][k][seed]
 //                      (seed 0: d Re log rho, seed 1: d Im log rho).
 #include "f32_tile.cuh"
@@ -43,14 +44,14 @@ __host__ __device__ __forceinline__ int seqs_for(int n, int rows) {
 
 struct SinkCtx {
   int mode;
-  float *g;          // mode 0: this CTA's accumulator copy [P]
+  float *g;          // mode 0: this CTA's private accumulator [P] (16-byte aligned)
   float *O;          // mode 1: [B][P][2]
   size_t P;
 };
 
 // Add / write one gradient value at flat parameter index k for virtual configuration v of the tile.
 __device__ __forceinline__ void sink1(const SinkCtx &s, long long k, float v, long long b, int seed) {
-  if (s.mode == 0) atomicAdd(s.g + k, v);
+  if (s.mode == 0) s.g[k] += v;   // private to this CTA; each index has one owning thread
   else s.O[((size_t)b * s.P + (size_t)k) * 2 + seed] = v;
 }
 
@@ -129,8 +130,13 @@ __device__ __forceinline__ void sink_block(const SinkCtx &s, float (&acc)[BwdGeo
     for (int h = 0; h < 2; ++h) {
       const long long base = off + k * ld + (h ? D / 2 : 0) + 4 * tx;
       if (s.mode == 0 && (base & 3) == 0) {
-        atomicAdd(reinterpret_cast<float4 *>(s.g + base),
-                  make_float4(acc[j][4 * h], acc[j][4 * h + 1], acc[j][4 * h + 2], acc[j][4 * h + 3]));
+        float4 *q = reinterpret_cast<float4 *>(s.g + base);
+        float4 v = *q;
+        v.x += acc[j][4 * h];
+        v.y += acc[j][4 * h + 1];
+        v.z += acc[j][4 * h + 2];
+        v.w += acc[j][4 * h + 3];
+        *q = v;
       } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e) sink1(s, base + e, acc[j][4 * h + e], b, seed);
@@ -279,7 +285,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   float *scr = scratch + (size_t)blockIdx.x * (size_t)m.layers * blk;
   SinkCtx sk;
   sk.mode = mode;
-  sk.g = gacc ? gacc + (size_t)(blockIdx.x % n_copies) * g_stride : nullptr;   // g_stride % 4 == 0
+  sk.g = gacc ? gacc + (size_t)blockIdx.x * g_stride : nullptr;   // one per CTA; g_stride % 4 == 0
+  (void)n_copies;
   sk.O = O;
   sk.P = P;
   const int nranges = mode == 0 ? 1 : tcv;

@@ -255,7 +255,8 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
   const int heads = m.heads, dh = m.dh;
   const float scale = rsqrtf((float)dh);
   for (int l = 0; l < m.layers; ++l) {
-    // ---------------- QKV
+    // ---------------- QKV (TMEM reads of the previous sub-layer done before the MMA overwrites them)
+    tc_fence_before();
     fence_proxy_async();
     bool ok = wait_w(c);
     if (sync_fail(c, ok)) return false;
@@ -467,7 +468,7 @@ __device__ __forceinline__ void ctl_finish(Ctl &c) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads, 1) k_fwd_bf16(DevModel m, DevModelBF16 mb, const uint32_t *__restrict__ sig,
+__global__ void __launch_bounds__(kThreads, 2) k_fwd_bf16(DevModel m, DevModelBF16 mb, const uint32_t *__restrict__ sig,
                                                           const uint32_t *__restrict__ sigp, size_t B,
                                                           float2 *__restrict__ out, int *err) {
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fwd_bf16(DevModel m, DevModelBF
 
 // Metropolis chains on the BF16 forward (same proposal stream and acceptance rule as the FP32 sampler).
 template <int D>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_sample_bf16(DevModel m, DevModelBF16 mb, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
                   uint32_t *__restrict__ sig, uint32_t *__restrict__ sigp, uint32_t *__restrict__ ssig,
                   uint32_t *__restrict__ ssigp, unsigned long long *accepted, int *err) {

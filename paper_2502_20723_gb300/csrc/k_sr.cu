@@ -1,55 +1,24 @@
 // Stochastic reconfiguration solve (metric-tensor and regularisation sections):
 //   (Re S + lambda I) x = rhs,  S_ij = <O_i^* O_j> - <O_i^*><O_j>  over Ns samples,
-// by Jacobi-preconditioned conjugate gradients, matrix-free: S v = (1/Ns) Re[Obar^H (Obar v)] with
-// Obar = O - mean(O), O stored as FP32 (re, im) [Ns][P].  Each iteration streams O twice from HBM
-// (the bound of this solver).  Products are formed in FP32 over short runs and accumulated in FP64
-// (GB300's FP64 rate is far below its FP32 rate); all CG vectors and scalars are FP64 and stay on the
-// device (no host round trip per iteration; a device flag ends the iteration).
+// by Jacobi-preconditioned conjugate gradients, matrix-free: with Obar = O - mean(O),
+//   S v = (1/Ns) Re[Obar^H (Obar v)],
+// O stored as FP32 (re, im) [Ns][P].  One iteration streams O twice from HBM (t = Obar v per sample,
+// then w = Obar^H t per parameter) and is HBM-bound; both passes keep many independent loads in flight.
+// Products are formed in FP32 over runs of 32 terms and accumulated in FP64 (GB300's FP64 rate is far
+// below its FP32 rate); CG vectors and scalars are FP64 and stay on the device: a device flag ends the
+// iteration, the host looks at it between groups of iterations only.
 #include "tdo_internal.cuh"
 #include "tdo_device.cuh"
 
 namespace tdo {
 
 constexpr int kSrBlock = 256;
-constexpr int kRun = 32;   // FP32 products per FP64 accumulation
+constexpr int kRun = 32;     // FP32 products per FP64 accumulation
+constexpr int kGroup = 4;    // samples per block pass in the t kernel
 
-// scalars: [0] rz, [1] bnorm2, [2] alpha, [3] rnorm2, [4] done flag, [5] iterations, [6] tol2, [7] pAp
-enum { S_RZ = 0, S_BN = 1, S_AL = 2, S_RN = 3, S_DONE = 4, S_IT = 5, S_TOL = 6, S_PAP = 7 };
-
-// mean[k] = (1/Ns) sum_s O[s][k]; thread per k, coalesced over k.
-__global__ void k_sr_mean(const float2 *__restrict__ O, size_t Ns, size_t P, double2 *__restrict__ mean) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
-    double ar = 0.0, ai = 0.0;
-    for (size_t s0 = 0; s0 < Ns; s0 += kRun) {
-      float fr = 0.f, fi = 0.f;
-      const size_t s1 = s0 + kRun < Ns ? s0 + kRun : Ns;
-      for (size_t s = s0; s < s1; ++s) { const float2 o = O[s * P + k]; fr += o.x; fi += o.y; }
-      ar += fr;
-      ai += fi;
-    }
-    mean[k] = make_double2(ar / (double)Ns, ai / (double)Ns);
-  }
-}
-
-// diag[k] = (1/Ns) sum_s |O[s][k] - mean[k]|^2 + shift   (Jacobi preconditioner of S + shift I)
-__global__ void k_sr_diag(const float2 *__restrict__ O, size_t Ns, size_t P, const double2 *__restrict__ mean,
-                          double shift, double *__restrict__ diag) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
-    const float mr = (float)mean[k].x, mi = (float)mean[k].y;
-    double a = 0.0;
-    for (size_t s0 = 0; s0 < Ns; s0 += kRun) {
-      float f = 0.f;
-      const size_t s1 = s0 + kRun < Ns ? s0 + kRun : Ns;
-      for (size_t s = s0; s < s1; ++s) {
-        const float2 o = O[s * P + k];
-        const float dr = o.x - mr, di = o.y - mi;
-        f = fmaf(dr, dr, fmaf(di, di, f));
-      }
-      a += f;
-    }
-    diag[k] = a / (double)Ns + shift;
-  }
-}
+enum {
+  S_RZ = 0, S_BN, S_AL, S_RN, S_DONE, S_IT, S_TOL, S_PAP, S_CR, S_CI, S_TR, S_TI, S_COUNT
+};
 
 __device__ __forceinline__ double block_sum_d(double v, double *sh) {
   v = warp_sum_d(v);
@@ -65,64 +34,173 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
   return t;   // valid in thread 0
 }
 
-// t[s] = sum_k (O[s][k] - mean[k]) v[k]  (complex), one block per sample.
-__global__ void k_sr_t(const float2 *__restrict__ O, size_t Ns, size_t P, const double2 *__restrict__ mean,
-                       const double *__restrict__ v, double2 *__restrict__ t, const double *__restrict__ sc) {
-  __shared__ double sh[32];
-  if (sc[S_DONE] != 0.0) return;
-  for (size_t s = blockIdx.x; s < Ns; s += gridDim.x) {
-    const float2 *row = O + s * P;
+__device__ __forceinline__ double sum_parts(const double *part, int n, double *sh) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+  return block_sum_d(a, sh);
+}
+
+// mean[k] = (1/Ns) sum_s O[s][k]   (thread per k, 4 independent loads in flight)
+__global__ void k_sr_mean(const float2 *__restrict__ O, size_t Ns, size_t P, double2 *__restrict__ mean) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
     double ar = 0.0, ai = 0.0;
-    float fr = 0.f, fi = 0.f;
-    int run = 0;
-    for (size_t k = threadIdx.x; k < P; k += blockDim.x) {
-      const float2 o = row[k];
-      const double2 m = mean[k];
-      const float vk = (float)v[k];
-      fr = fmaf(o.x - (float)m.x, vk, fr);
-      fi = fmaf(o.y - (float)m.y, vk, fi);
-      if (++run == kRun) { ar += fr; ai += fi; fr = fi = 0.f; run = 0; }
+    for (size_t s0 = 0; s0 < Ns; s0 += kRun) {
+      const size_t s1 = s0 + kRun < Ns ? s0 + kRun : Ns;
+      float fr[4] = {0, 0, 0, 0}, fi[4] = {0, 0, 0, 0};
+      size_t s = s0;
+      for (; s + 4 <= s1; s += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { const float2 o = __ldg(O + (s + u) * P + k); fr[u] += o.x; fi[u] += o.y; }
+      }
+      for (; s < s1; ++s) { const float2 o = __ldg(O + s * P + k); fr[0] += o.x; fi[0] += o.y; }
+      ar += (double)((fr[0] + fr[1]) + (fr[2] + fr[3]));
+      ai += (double)((fi[0] + fi[1]) + (fi[2] + fi[3]));
     }
-    ar += fr;
-    ai += fi;
-    const double r = block_sum_d(ar, sh);
-    const double i = block_sum_d(ai, sh);
-    if (threadIdx.x == 0) t[s] = make_double2(r, i);
+    mean[k] = make_double2(ar / (double)Ns, ai / (double)Ns);
   }
 }
 
-// Ap[k] = (1/Ns) sum_s Re(conj(O[s][k] - mean[k]) t[s]) + shift p[k]; block partials of p . Ap.
-__global__ void k_sr_w(const float2 *__restrict__ O, size_t Ns, size_t P, const double2 *__restrict__ mean,
-                       const double2 *__restrict__ t, const double *__restrict__ p, double shift,
-                       double *__restrict__ Ap, double *__restrict__ part, const double *__restrict__ sc) {
-  __shared__ double sh[32];
-  if (sc[S_DONE] != 0.0) return;
-  double loc = 0.0;
+// diag[k] = (1/Ns) sum_s |O[s][k] - mean[k]|^2 + shift   (Jacobi preconditioner of S + shift I)
+__global__ void k_sr_diag(const float2 *__restrict__ O, size_t Ns, size_t P, const double2 *__restrict__ mean,
+                          double shift, double *__restrict__ diag) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
     const float mr = (float)mean[k].x, mi = (float)mean[k].y;
     double a = 0.0;
     for (size_t s0 = 0; s0 < Ns; s0 += kRun) {
-      float f = 0.f;
       const size_t s1 = s0 + kRun < Ns ? s0 + kRun : Ns;
-      for (size_t s = s0; s < s1; ++s) {
-        const float2 o = O[s * P + k];
-        const double2 ts = t[s];
-        f = fmaf(o.x - mr, (float)ts.x, fmaf(o.y - mi, (float)ts.y, f));
+      float f[4] = {0, 0, 0, 0};
+      size_t s = s0;
+      for (; s + 4 <= s1; s += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 o = __ldg(O + (s + u) * P + k);
+          const float dr = o.x - mr, di = o.y - mi;
+          f[u] = fmaf(dr, dr, fmaf(di, di, f[u]));
+        }
       }
-      a += f;
+      for (; s < s1; ++s) {
+        const float2 o = __ldg(O + s * P + k);
+        const float dr = o.x - mr, di = o.y - mi;
+        f[0] = fmaf(dr, dr, fmaf(di, di, f[0]));
+      }
+      a += (double)((f[0] + f[1]) + (f[2] + f[3]));
     }
-    const double v = a / (double)Ns + shift * p[k];
+    diag[k] = a / (double)Ns + shift;
+  }
+}
+
+// vf = (float) v; block partials of mean . v (re, im)
+__global__ void k_sr_vprep(size_t P, const double *__restrict__ v, const double2 *__restrict__ mean,
+                           float *__restrict__ vf, double *__restrict__ part, double *__restrict__ part2,
+                           const double *__restrict__ sc) {
+  __shared__ double sh[32];
+  if (sc[S_DONE] != 0.0) return;
+  double cr = 0.0, ci = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
+    const double x = v[k];
+    vf[k] = (float)x;
+    cr += mean[k].x * x;
+    ci += mean[k].y * x;
+  }
+  const double a = block_sum_d(cr, sh);
+  const double b = block_sum_d(ci, sh);
+  if (threadIdx.x == 0) { part[blockIdx.x] = a; part2[blockIdx.x] = b; }
+}
+
+__global__ void k_sr_cfin(const double *__restrict__ part, const double *__restrict__ part2, int nb,
+                          double *__restrict__ sc) {
+  __shared__ double sh[32];
+  if (sc[S_DONE] != 0.0) return;
+  const double a = sum_parts(part, nb, sh);
+  const double b = sum_parts(part2, nb, sh);
+  if (threadIdx.x == 0) { sc[S_CR] = a; sc[S_CI] = b; }
+}
+
+// t[s] = sum_k O[s][k] v[k] - mean . v  for kGroup samples per pass (v read once per group).
+__global__ void k_sr_t(const float2 *__restrict__ O, size_t Ns, size_t P, const float *__restrict__ vf,
+                       float2 *__restrict__ t, const double *__restrict__ sc) {
+  __shared__ double sh[32];
+  if (sc[S_DONE] != 0.0) return;
+  const double cr = sc[S_CR], ci = sc[S_CI];
+  for (size_t s0 = (size_t)blockIdx.x * kGroup; s0 < Ns; s0 += (size_t)gridDim.x * kGroup) {
+    const int ng = (int)((Ns - s0) < (size_t)kGroup ? (Ns - s0) : (size_t)kGroup);
+    double ar[kGroup], ai[kGroup];
+    float fr[kGroup], fi[kGroup];
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) { ar[g] = ai[g] = 0.0; fr[g] = fi[g] = 0.f; }
+    int run = 0;
+    for (size_t k = threadIdx.x; k < P; k += blockDim.x) {
+      const float x = __ldg(vf + k);
+#pragma unroll
+      for (int g = 0; g < kGroup; ++g) {
+        if (g < ng) {
+          const float2 o = __ldg(O + (s0 + g) * P + k);
+          fr[g] = fmaf(o.x, x, fr[g]);
+          fi[g] = fmaf(o.y, x, fi[g]);
+        }
+      }
+      if (++run == kRun) {
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g) { ar[g] += fr[g]; ai[g] += fi[g]; fr[g] = fi[g] = 0.f; }
+        run = 0;
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) {
+      const double r = block_sum_d(ar[g] + fr[g], sh);
+      const double i = block_sum_d(ai[g] + fi[g], sh);
+      if (threadIdx.x == 0 && g < ng) t[s0 + g] = make_float2((float)(r - cr), (float)(i - ci));
+    }
+  }
+}
+
+// T = sum_s t[s]  (zero in exact arithmetic; subtracted explicitly below)
+__global__ void k_sr_tsum(const float2 *__restrict__ t, size_t Ns, double *__restrict__ sc) {
+  __shared__ double sh[32];
+  if (sc[S_DONE] != 0.0) return;
+  double a = 0.0, b = 0.0;
+  for (size_t s = threadIdx.x; s < Ns; s += blockDim.x) { a += t[s].x; b += t[s].y; }
+  a = block_sum_d(a, sh);
+  b = block_sum_d(b, sh);
+  if (threadIdx.x == 0) { sc[S_TR] = a; sc[S_TI] = b; }
+}
+
+// Ap[k] = (1/Ns) [sum_s Re(conj(O[s][k]) t[s]) - Re(conj(mean[k]) T)] + shift p[k]; partials of p . Ap.
+__global__ void k_sr_w(const float2 *__restrict__ O, size_t Ns, size_t P, const double2 *__restrict__ mean,
+                       const float2 *__restrict__ t, const double *__restrict__ p, double shift,
+                       double *__restrict__ Ap, double *__restrict__ part, const double *__restrict__ sc) {
+  __shared__ double sh[32];
+  if (sc[S_DONE] != 0.0) return;
+  const double Tr = sc[S_TR], Ti = sc[S_TI];
+  double loc = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
+    double a = 0.0;
+    for (size_t s0 = 0; s0 < Ns; s0 += kRun) {
+      const size_t s1 = s0 + kRun < Ns ? s0 + kRun : Ns;
+      float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      size_t s = s0;
+      for (; s + 8 <= s1; s += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float2 o = __ldg(O + (s + u) * P + k);
+          const float2 ts = t[s + u];
+          f[u] = fmaf(o.x, ts.x, fmaf(o.y, ts.y, f[u]));
+        }
+      }
+      for (; s < s1; ++s) {
+        const float2 o = __ldg(O + s * P + k);
+        const float2 ts = t[s];
+        f[0] = fmaf(o.x, ts.x, fmaf(o.y, ts.y, f[0]));
+      }
+      a += (double)(((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])));
+    }
+    const double2 m = mean[k];
+    const double v = (a - (m.x * Tr + m.y * Ti)) / (double)Ns + shift * p[k];
     Ap[k] = v;
     loc += v * p[k];
   }
   const double b = block_sum_d(loc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = b;
-}
-
-__device__ __forceinline__ double sum_parts(const double *part, int n, double *sh) {
-  double a = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
-  return block_sum_d(a, sh);
 }
 
 __global__ void k_sr_alpha(const double *__restrict__ part, int nb, double *__restrict__ sc) {
@@ -181,99 +259,152 @@ __global__ void k_sr_p(size_t P, double *__restrict__ p, const double *__restric
     p[k] = z[k] + be * p[k];
 }
 
-// initial state: x = 0, r = rhs, z = r/diag, p = z; partials of r.r and r.z
-__global__ void k_sr_init(size_t P, const double *__restrict__ rhs, double *__restrict__ x, double *__restrict__ r,
+// Initial state.  Without x0: x = 0, r = rhs.  With x0 (Ap holds S' x0): x = x0, r = rhs - Ap.
+// Then z = r/diag, p = z; partials of r.r, r.z and rhs.rhs.
+__global__ void k_sr_init(size_t P, const double *__restrict__ rhs, const double *__restrict__ x0,
+                          const double *__restrict__ Ap, double *__restrict__ x, double *__restrict__ r,
                           double *__restrict__ z, double *__restrict__ p, const double *__restrict__ diag,
-                          double *__restrict__ part, double *__restrict__ part2) {
+                          double *__restrict__ part, double *__restrict__ part2, double *__restrict__ part3) {
   __shared__ double sh[32];
-  double rr = 0.0, rz = 0.0;
+  double rr = 0.0, rz = 0.0, bb = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
-    const double rk = rhs[k];
-    x[k] = 0.0;
+    const double b = rhs[k];
+    const double rk = x0 ? b - Ap[k] : b;
+    x[k] = x0 ? x0[k] : 0.0;
     r[k] = rk;
     const double zk = rk / diag[k];
     z[k] = zk;
     p[k] = zk;
     rr += rk * rk;
     rz += rk * zk;
+    bb += b * b;
   }
   const double a = block_sum_d(rr, sh);
-  const double b = block_sum_d(rz, sh);
-  if (threadIdx.x == 0) { part[blockIdx.x] = a; part2[blockIdx.x] = b; }
+  const double b2 = block_sum_d(rz, sh);
+  const double c = block_sum_d(bb, sh);
+  if (threadIdx.x == 0) { part[blockIdx.x] = a; part2[blockIdx.x] = b2; part3[blockIdx.x] = c; }
 }
 
-__global__ void k_sr_init_scalars(const double *__restrict__ part, const double *__restrict__ part2, int nb,
-                                  double tol, double *__restrict__ sc) {
+__global__ void k_sr_init_scalars(const double *__restrict__ part, const double *__restrict__ part2,
+                                  const double *__restrict__ part3, int nb, double tol, double *__restrict__ sc) {
   __shared__ double sh[32];
   const double rr = sum_parts(part, nb, sh);
   const double rz = sum_parts(part2, nb, sh);
+  const double bb = sum_parts(part3, nb, sh);
   if (threadIdx.x == 0) {
     sc[S_RZ] = rz;
-    sc[S_BN] = rr;
+    sc[S_BN] = bb;
     sc[S_RN] = rr;
     sc[S_AL] = 0.0;
     sc[S_IT] = 0.0;
     sc[S_TOL] = tol * tol;
     sc[S_PAP] = 0.0;
-    sc[S_DONE] = (rr == 0.0) ? 1.0 : 0.0;
+    sc[S_DONE] = (rr <= tol * tol * bb) ? 1.0 : 0.0;
   }
+}
+
+__global__ void k_sr_clear(double *__restrict__ sc) {
+  if (threadIdx.x < S_COUNT) sc[threadIdx.x] = 0.0;
+}
+
+struct SrPtrs {
+  double2 *mean;
+  double *diag, *r, *z, *p, *Ap, *part, *part2, *part3, *sc;
+  float *vf;
+  float2 *t;
+};
+
+static SrPtrs sr_carve(double *work, size_t Ns, size_t P) {
+  SrPtrs q;
+  q.mean = reinterpret_cast<double2 *>(work);
+  q.diag = work + 2 * P;
+  q.r = q.diag + P;
+  q.z = q.r + P;
+  q.p = q.z + P;
+  q.Ap = q.p + P;
+  q.part = q.Ap + P;
+  q.part2 = q.part + 1024;
+  q.part3 = q.part2 + 1024;
+  q.sc = q.part3 + 1024;
+  q.vf = reinterpret_cast<float *>(q.sc + 32);
+  q.t = reinterpret_cast<float2 *>(q.vf + ((P + 3) / 4 * 4));
+  (void)Ns;
+  return q;
+}
+
+// S' v -> Ap (and the partials of v . Ap in q.part), all on the device.
+static void matvec(const float2 *O, size_t Ns, size_t P, const double *v, double shift, SrPtrs &q, int nb,
+                   int ngrid_t, cudaStream_t st) {
+  k_sr_vprep<<<nb, kSrBlock, 0, st>>>(P, v, q.mean, q.vf, q.part, q.part2, q.sc);
+  k_sr_cfin<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
+  k_sr_t<<<ngrid_t, kSrBlock, 0, st>>>(O, Ns, P, q.vf, q.t, q.sc);
+  k_sr_tsum<<<1, 1024, 0, st>>>(q.t, Ns, q.sc);
+  k_sr_w<<<nb, kSrBlock, 0, st>>>(O, Ns, P, q.mean, q.t, v, shift, q.Ap, q.part, q.sc);
 }
 
 }  // namespace tdo
 
 size_t sr_work_doubles(size_t Ns, size_t P) {
-  // mean 2P, diag, r, z, p, Ap (5P), t 2Ns, partials 2*1024, scalars 16
-  return 2 * P + 5 * P + 2 * Ns + 2 * 1024 + 16;
+  // mean 2P, diag r z p Ap 5P, partials 3x1024, scalars 32, vf P floats, t 2Ns floats
+  return 2 * P + 5 * P + 3 * 1024 + 32 + ((P + 3) / 4 * 4) / 2 + Ns + 16;
 }
 
-cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, double shift, double tol,
-                       int max_iter, double *x, double *work, int n_sm, int *iters, double *resid,
-                       cudaStream_t st) {
+int sr_launches_per_iter() { return 9; }
+
+cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, const double *x0, double shift,
+                       double tol, int max_iter, double *x, double *work, int n_sm, int *iters, double *resid,
+                       long long *launches, cudaStream_t st) {
   using namespace tdo;
-  double2 *mean = reinterpret_cast<double2 *>(work);
-  double *diag = work + 2 * P, *r = diag + P, *z = r + P, *p = z + P, *Ap = p + P;
-  double2 *t = reinterpret_cast<double2 *>(Ap + P);
-  double *part = reinterpret_cast<double *>(t + Ns), *part2 = part + 1024, *sc = part2 + 1024;
+  SrPtrs q = sr_carve(work, Ns, P);
   const float2 *O2 = reinterpret_cast<const float2 *>(O);
   int nb = (int)((P + kSrBlock - 1) / kSrBlock);
   if (nb > 1024) nb = 1024;
   if (nb < 1) nb = 1;
-  const int ngrid_t = (int)(Ns < (size_t)(8 * n_sm) ? Ns : (size_t)(8 * n_sm));
-  k_sr_mean<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, mean);
-  k_sr_diag<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, mean, shift, diag);
-  k_sr_init<<<nb, kSrBlock, 0, st>>>(P, rhs, x, r, z, p, diag, part, part2);
-  k_sr_init_scalars<<<1, 1024, 0, st>>>(part, part2, nb, tol, sc);
+  const size_t groups = (Ns + kGroup - 1) / kGroup;
+  const int ngrid_t = (int)(groups < (size_t)(16 * n_sm) ? groups : (size_t)(16 * n_sm));
+  long long nl = 0;
+  k_sr_mean<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, q.mean);
+  k_sr_diag<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, q.mean, shift, q.diag);
+  k_sr_clear<<<1, 32, 0, st>>>(q.sc);
+  nl += 3;
+  if (x0) { matvec(O2, Ns, P, x0, shift, q, nb, ngrid_t > 0 ? ngrid_t : 1, st); nl += 5; }
+  k_sr_init<<<nb, kSrBlock, 0, st>>>(P, rhs, x0, q.Ap, x, q.r, q.z, q.p, q.diag, q.part, q.part2, q.part3);
+  k_sr_init_scalars<<<1, 1024, 0, st>>>(q.part, q.part2, q.part3, nb, tol, q.sc);
+  nl += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // Iterations are launched in groups; the done flag on the device makes the rest of a group a no-op,
   // and the host looks at it between groups only.
-  const int group = 16;
-  double h[8];
+  const int group = 8;
+  double h[S_COUNT];
+  bool fetched = false;
   for (int it = 0; it < max_iter;) {
     const int end = it + group < max_iter ? it + group : max_iter;
     for (; it < end; ++it) {
-      k_sr_t<<<ngrid_t > 0 ? ngrid_t : 1, kSrBlock, 0, st>>>(O2, Ns, P, mean, p, t, sc);
-      k_sr_w<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, mean, t, p, shift, Ap, part, sc);
-      k_sr_alpha<<<1, 1024, 0, st>>>(part, nb, sc);
-      k_sr_xr<<<nb, kSrBlock, 0, st>>>(P, x, r, z, p, Ap, diag, part, part2, sc);
-      k_sr_beta<<<1, 1024, 0, st>>>(part, part2, nb, sc);
-      k_sr_p<<<nb, kSrBlock, 0, st>>>(P, p, z, sc);
+      matvec(O2, Ns, P, q.p, shift, q, nb, ngrid_t > 0 ? ngrid_t : 1, st);
+      k_sr_alpha<<<1, 1024, 0, st>>>(q.part, nb, q.sc);
+      k_sr_xr<<<nb, kSrBlock, 0, st>>>(P, x, q.r, q.z, q.p, q.Ap, q.diag, q.part, q.part2, q.sc);
+      k_sr_beta<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
+      k_sr_p<<<nb, kSrBlock, 0, st>>>(P, q.p, q.z, q.sc);
+      nl += 9;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(h, q.sc, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
+    fetched = true;
     if (h[S_DONE] != 0.0) break;
   }
-  if (max_iter <= 0) {
-    e = cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (!fetched) {
+    e = cudaMemcpyAsync(h, q.sc, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
   }
   if (iters) *iters = (int)h[S_IT];
   if (resid) *resid = h[S_BN] > 0 ? sqrt(h[S_RN] / h[S_BN]) : 0.0;
+  if (launches) *launches = nl;
   if (h[S_DONE] == 2.0) return cudaErrorInvalidValue;   // not positive definite
   return cudaSuccess;
 }

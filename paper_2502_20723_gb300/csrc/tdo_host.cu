@@ -29,11 +29,12 @@ cudaError_t launch_bwd32_impl(const DevModel &m, int mode, const uint32_t *sig, 
                               float *O, size_t P, const long long *flat_offsets, float *scratch, int grid,
                               cudaStream_t st);
 size_t sr_work_doubles(size_t Ns, size_t P);
-cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, double shift, double tol,
-                       int max_iter, double *x, double *work, int n_sm, int *iters, double *resid,
-                       cudaStream_t st);
+cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, const double *x0, double shift,
+                       double tol, int max_iter, double *x, double *work, int n_sm, int *iters, double *resid,
+                       long long *launches, cudaStream_t st);
 cudaError_t launch_params_f32(const double *theta, size_t P, const long long *tab, int n_tensors,
                               float *dst, cudaStream_t st);
+size_t bf16_packed_bytes(const DevModel &m);
 
 namespace {
 
@@ -79,15 +80,17 @@ struct tdo_ctx {
   int n_pat = 0;
   DBuf d_pat, d_con;
   // parameters
-  DBuf theta64, theta32, etab, tensor_tab;
+  DBuf theta64, theta32, etab, tensor_tab, wbf16, errflag;
   DevModel dm{};
+  DevModelBF16 dmb{};
   // workspace
   DBuf stage_in[4], stage_out;
   DBuf conn_cnt, conn_sig, conn_sigp, conn_coef, offs, fsig, fsigp, fcoef, flr, lloc, l2, stats,
       nonfinite, cot, gacc, scratch, grad, Obuf, srwork, delta, acc_u64;
   std::string err;
-  double sr_tol = 1e-8;
-  int sr_max_iter = 200;
+  double sr_tol = 1e-6;
+  int sr_max_iter = 100;
+  bool have_delta = false;
   int last_sr_iters = 0;
   double last_sr_resid = 0;
   // kernel timing (tdo_timing)
@@ -352,6 +355,20 @@ static tdo_status refresh_params(tdo_ctx *c) {
     CU(c, launch_conv_table_k(m->d_model, m->conv_channels, b + c->tensors[0].pad, b + c->tensors[1].pad,
                               b + c->tensors[2].pad, b + c->tensors[3].pad, c->etab.as<float>(), c->stream));
   }
+  if (m->precision == TDO_BF16) CU(c, launch_pack_bf16(c->dm, c->wbf16.as<uint16_t>(), &c->dmb, c->stream));
+  return TDO_OK;
+}
+
+// Reports (and clears) a timeout flagged by a BF16 kernel's bounded waits.
+static tdo_status check_err_flag(tdo_ctx *c) {
+  if (c->model.precision != TDO_BF16) return TDO_OK;
+  int f = 0;
+  CU(c, cudaMemcpyAsync(&f, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  if (f) {
+    CU(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->stream));
+    return fail(c, TDO_ETIMEOUT, "a tensor-core kernel's bounded wait gave up (results of that launch are invalid)");
+  }
   return TDO_OK;
 }
 
@@ -443,6 +460,19 @@ extern "C" tdo_status tdo_create(const tdo_problem *problem, const tdo_model *mo
     return bail(TDO_ECUDA);
   }
   build_devmodel(c);
+  if (model->precision == TDO_BF16) {
+    if (!bf16_supported(c->dm)) {
+      fail(c, TDO_EUNSUPPORTED, "BF16 path: d_model 32 or 64, head dim a multiple of 8, an even head count, "
+                                 "MLP width a multiple of min(4 d_model, 128)");
+      return bail(TDO_EUNSUPPORTED);
+    }
+    if ((e = c->wbf16.ensure(bf16_packed_bytes(c->dm))) != cudaSuccess ||
+        (e = c->errflag.ensure(sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(c->errflag.p, 0, sizeof(int))) != cudaSuccess) {
+      fail(c, TDO_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+      return bail(TDO_ENOMEM);
+    }
+  }
   s = tdo_set_params(c, theta);
   if (s != TDO_OK) return bail(s);
   *out = c;
@@ -456,7 +486,7 @@ extern "C" tdo_status tdo_destroy(tdo_ctx *c) {
                   &c->stage_in[1], &c->stage_in[2], &c->stage_in[3], &c->stage_out, &c->conn_cnt, &c->conn_sig,
                   &c->conn_sigp, &c->conn_coef, &c->offs, &c->fsig, &c->fsigp, &c->fcoef, &c->flr, &c->lloc,
                   &c->l2, &c->stats, &c->nonfinite, &c->cot, &c->gacc, &c->scratch, &c->grad, &c->Obuf,
-                  &c->srwork, &c->delta, &c->acc_u64};
+                  &c->srwork, &c->delta, &c->acc_u64, &c->wbf16, &c->errflag};
   for (DBuf *b : bufs) b->release();
   for (auto &r : c->trec) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : c->epool) cudaEventDestroy(e);
@@ -469,6 +499,7 @@ extern "C" int tdo_max_connections(const tdo_ctx *c) { return c ? c->n_pat : 0; 
 
 extern "C" tdo_status tdo_set_params(tdo_ctx *c, const double *theta) {
   if (!c) return TDO_EINVAL;
+  c->have_delta = false;
   if (!theta) return fail(c, TDO_EINVAL, "theta is NULL");
   const cudaMemcpyKind kind = is_device_ptr(theta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CU(c, cudaMemcpyAsync(c->theta64.p, theta, sizeof(double) * c->P, kind, c->stream));
@@ -489,9 +520,11 @@ extern "C" tdo_status tdo_get_params(tdo_ctx *c, double *theta) {
 // forward on device buffers
 static tdo_status forward_dev(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t B, float2 *out) {
   if (B == 0) return TDO_OK;
-  if (c->model.precision == TDO_BF16) return fail(c, TDO_EUNSUPPORTED, "BF16 forward not built");
   Timed tm(c, G_FWD);
-  CU(c, launch_fwd32(c->dm, sig, sigp, B, out, c->n_sm, c->stream));
+  if (c->model.precision == TDO_BF16)
+    CU(c, launch_fwd_bf16(c->dm, c->dmb, sig, sigp, B, out, c->errflag.as<int>(), c->n_sm, c->stream));
+  else
+    CU(c, launch_fwd32(c->dm, sig, sigp, B, out, c->n_sm, c->stream));
   return TDO_OK;
 }
 
@@ -520,7 +553,10 @@ extern "C" tdo_status tdo_log_rho(tdo_ctx *c, const uint32_t *sig, const uint32_
   }
   TRY(forward_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, B, dout));
   TRY(deliver(c, logrho, dout, 8 * B, &h3));
-  if (h1 || h2 || h3) CU(c, cudaStreamSynchronize(c->stream));
+  if (h1 || h2 || h3) {
+    CU(c, cudaStreamSynchronize(c->stream));
+    TRY(check_err_flag(c));
+  }
   return TDO_OK;
 }
 
@@ -572,6 +608,7 @@ static tdo_status read_stats(tdo_ctx *c, size_t Ns, double *cost, double *se) {
   CU(c, cudaMemcpyAsync(st, c->stats.p, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaMemcpyAsync(&nf, c->nonfinite.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaStreamSynchronize(c->stream));
+  TRY(check_err_flag(c));
   if (nf) return fail(c, TDO_ENUMERIC, "non-finite log rho or L_loc (rho = 0 exactly, or non-finite parameters)");
   const double mean = st[0] / (double)Ns;
   const double var = st[1] / (double)Ns - mean * mean;
@@ -621,21 +658,20 @@ extern "C" tdo_status tdo_local_estimator(tdo_ctx *c, const uint32_t *sig, const
   return TDO_OK;
 }
 
-static const int kCopies = 8;
 
 // VJP over device rows: grad (FP64, device) = [accumulate ? grad : 0] + sum Re(cot * dlogrho).
 static tdo_status vjp_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t B, const float2 *cot,
                           double *grad, int accumulate) {
   if (c->model.embed != TDO_EMBED_TOKEN) return fail(c, TDO_EUNSUPPORTED, "gradients of the conv embedding are not built");
   const int grid = bwd32_grid(c->dm, B, 0, c->n_sm);
-  const size_t stride = (c->P + 3) / 4 * 4;   // 16-byte aligned accumulator copies (float4 atomics)
-  CU(c, c->gacc.ensure(sizeof(float) * kCopies * stride));
+  const size_t stride = (c->P + 3) / 4 * 4;   // one 16-byte aligned accumulator per CTA
+  CU(c, c->gacc.ensure(sizeof(float) * grid * stride));
   CU(c, c->scratch.ensure(sizeof(float) * bwd32_scratch_floats(c->dm, grid)));
-  CU(c, cudaMemsetAsync(c->gacc.p, 0, sizeof(float) * kCopies * stride, c->stream));
+  CU(c, cudaMemsetAsync(c->gacc.p, 0, sizeof(float) * grid * stride, c->stream));
   Timed tm(c, G_BWD_VJP);
-  CU(c, launch_bwd32_impl(c->dm, 0, ds, dp, B, cot, c->gacc.as<float>(), kCopies, stride, nullptr, c->P,
+  CU(c, launch_bwd32_impl(c->dm, 0, ds, dp, B, cot, c->gacc.as<float>(), grid, stride, nullptr, c->P,
                           c->flat_offsets, c->scratch.as<float>(), grid, c->stream));
-  CU(c, launch_reduce_copies(c->gacc.as<float>(), kCopies, stride, c->P, grad, accumulate, c->stream));
+  CU(c, launch_reduce_copies(c->gacc.as<float>(), grid, stride, c->P, grad, accumulate, c->stream));
   tm.done(2);
   return TDO_OK;
 }
@@ -743,10 +779,11 @@ extern "C" tdo_status tdo_sr_solve(tdo_ctx *c, const float *O, size_t Ns, const 
   CU(c, c->srwork.ensure(sizeof(double) * sr_work_doubles(Ns, c->P)));
   Timed tm(c, G_SR);
   int it_local = 0;
-  cudaError_t e = sr_cg_impl((const float *)dO, Ns, c->P, (const double *)dr, diag_shift, tol, max_iter, dx,
-                             c->srwork.as<double>(), c->n_sm, &it_local, resid, c->stream);
+  long long nl = 0;
+  cudaError_t e = sr_cg_impl((const float *)dO, Ns, c->P, (const double *)dr, nullptr, diag_shift, tol, max_iter,
+                             dx, c->srwork.as<double>(), c->n_sm, &it_local, resid, &nl, c->stream);
   if (iters) *iters = it_local;
-  tm.done(4 + 6LL * ((it_local + 15) / 16 * 16));
+  tm.done(nl);
   if (e == cudaErrorInvalidValue) return fail(c, TDO_ENUMERIC, "CG breakdown: S + shift I is not positive definite");
   CU(c, e);
   TRY(deliver(c, x, dx, sizeof(double) * c->P, &h3));
@@ -774,11 +811,15 @@ extern "C" tdo_status tdo_sr_step(tdo_ctx *c, const uint32_t *sig, const uint32_
   double resid = 0;
   cudaError_t e;
   {
+    // warm start from the previous step's solution (same parameter layout)
     Timed tm(c, G_SR);
-    e = sr_cg_impl(c->Obuf.as<float>(), Ns, c->P, c->grad.as<double>(), diag_shift, c->sr_tol, c->sr_max_iter,
-                   c->delta.as<double>(), c->srwork.as<double>(), c->n_sm, &iters, &resid, c->stream);
-    tm.done(4 + 6LL * ((iters + 15) / 16 * 16));
+    long long nl = 0;
+    e = sr_cg_impl(c->Obuf.as<float>(), Ns, c->P, c->grad.as<double>(), c->have_delta ? c->delta.as<double>() : nullptr,
+                   diag_shift, c->sr_tol, c->sr_max_iter, c->delta.as<double>(), c->srwork.as<double>(), c->n_sm,
+                   &iters, &resid, &nl, c->stream);
+    tm.done(nl);
   }
+  c->have_delta = (e == cudaSuccess);
   c->last_sr_iters = iters;
   c->last_sr_resid = resid;
   if (e == cudaErrorInvalidValue) return fail(c, TDO_ENUMERIC, "CG breakdown: S + shift I is not positive definite");
@@ -800,7 +841,6 @@ extern "C" tdo_status tdo_sample(tdo_ctx *c, size_t n_chains, size_t n_sweeps, u
   if (n_chains == 0) return TDO_OK;
   if (!sig || !sigp) return fail(c, TDO_EINVAL, "NULL buffer");
   if ((samples_sig == nullptr) != (samples_sigp == nullptr)) return fail(c, TDO_EINVAL, "give both sample buffers or neither");
-  if (c->model.precision == TDO_BF16) return fail(c, TDO_EUNSUPPORTED, "BF16 sampler not built");
   // chain state on device (staged both ways when host)
   const bool hs = !is_device_ptr(sig), hp = !is_device_ptr(sigp);
   uint32_t *dsig = sig, *dsigp = sigp;
@@ -816,8 +856,12 @@ extern "C" tdo_status tdo_sample(tdo_ctx *c, size_t n_chains, size_t n_sweeps, u
   CU(c, c->acc_u64.ensure(sizeof(unsigned long long)));
   CU(c, cudaMemsetAsync(c->acc_u64.p, 0, sizeof(unsigned long long), c->stream));
   Timed tm(c, G_SAMPLE);
-  CU(c, launch_sample32(c->dm, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
-                        c->acc_u64.as<unsigned long long>(), c->n_sm, c->stream));
+  if (c->model.precision == TDO_BF16)
+    CU(c, launch_sample_bf16(c->dm, c->dmb, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
+                             c->acc_u64.as<unsigned long long>(), c->errflag.as<int>(), c->n_sm, c->stream));
+  else
+    CU(c, launch_sample32(c->dm, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
+                          c->acc_u64.as<unsigned long long>(), c->n_sm, c->stream));
   tm.done(1);
   if (hs) CU(c, cudaMemcpyAsync(sig, dsig, 4 * n_chains, cudaMemcpyDeviceToHost, c->stream));
   if (hp) CU(c, cudaMemcpyAsync(sigp, dsigp, 4 * n_chains, cudaMemcpyDeviceToHost, c->stream));
@@ -833,7 +877,10 @@ extern "C" tdo_status tdo_sample(tdo_ctx *c, size_t n_chains, size_t n_sweeps, u
       *accepted = a;
     }
   }
-  if (hs || hp || hss || hsp) CU(c, cudaStreamSynchronize(c->stream));
+  if (hs || hp || hss || hsp || accepted) {
+    CU(c, cudaStreamSynchronize(c->stream));
+    TRY(check_err_flag(c));
+  }
   return TDO_OK;
 }
 
@@ -873,5 +920,12 @@ extern "C" tdo_status tdo_set_sr_options(tdo_ctx *c, double tol, int max_iter) {
   if (!(tol >= 0.0) || max_iter < 0) return fail(c, TDO_EINVAL, "tol must be >= 0 and max_iter >= 0");
   c->sr_tol = tol;
   c->sr_max_iter = max_iter;
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_sr_info(const tdo_ctx *c, int *iters, double *resid) {
+  if (!c) return TDO_EINVAL;
+  if (iters) *iters = c->last_sr_iters;
+  if (resid) *resid = c->last_sr_resid;
   return TDO_OK;
 }

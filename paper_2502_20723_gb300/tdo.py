@@ -22,7 +22,7 @@ STATUS = {0: "TDO_OK", -1: "TDO_EINVAL", -2: "TDO_ENOMEM", -3: "TDO_ECUDA", -4: 
 EXPORTS = ["tdo_model_num_params", "tdo_create", "tdo_destroy", "tdo_num_params", "tdo_max_connections",
            "tdo_set_params", "tdo_get_params", "tdo_log_rho", "tdo_log_rho_vjp", "tdo_jacobian",
            "tdo_connections", "tdo_local_estimator", "tdo_sample", "tdo_grad", "tdo_sr_solve", "tdo_set_sr_options", "tdo_sr_step",
-           "tdo_timing", "tdo_timing_read", "tdo_last_error"]
+           "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_last_error"]
 
 
 class TdoError(RuntimeError):
@@ -78,6 +78,7 @@ def lib() -> C.CDLL:
         L.tdo_set_sr_options.argtypes = [vp, C.c_double, i32]
         L.tdo_timing.argtypes = [vp, i32]
         L.tdo_timing_read.argtypes = [vp, C.c_char_p, dp, C.POINTER(C.c_longlong)]
+        L.tdo_sr_info.argtypes = [vp, C.POINTER(i32), dp]
         L.tdo_last_error.argtypes = [vp]
         L.tdo_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -260,6 +261,11 @@ class Context:
         ms, n = C.c_double(), C.c_longlong()
         self._chk(lib().tdo_timing_read(self.h, group.encode(), C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def sr_info(self):
+        it, res = C.c_int(), C.c_double()
+        self._chk(lib().tdo_sr_info(self.h, C.byref(it), C.byref(res)))
+        return it.value, res.value
 
     def set_sr_options(self, tol: float, max_iter: int):
         self._chk(lib().tdo_set_sr_options(self.h, float(tol), int(max_iter)))

@@ -1,0 +1,88 @@
+"""BF16 tensor-core path (tcgen05) vs the FP64 oracle, through the C ABI.
+
+Tolerances: log rho within 2e-2 absolute (phase modulo 2 pi), cost within 1e-3 relative on the same
+samples, Metropolis decisions identical wherever the oracle's margin |2 Re dlogrho - log u| exceeds
+twice the log rho tolerance."""
+import numpy as np
+import pytest
+
+from oracle import estimators as E, sampler as OS, transformer as T
+from paper_2502_20723_gb300 import synth
+from tests.gpu_common import logrho_err, problem
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_20723_gb300 import build
+    build.build()
+
+
+def ctx_for(prob, spec, theta):
+    from paper_2502_20723_gb300 import tdo
+    return tdo.Context(prob, spec, theta, "bf16")
+
+
+def dev(a):
+    return torch.as_tensor(np.asarray(a).astype(np.int64)).to(torch.int32).cuda()
+
+
+@pytest.mark.parametrize("n,d,h,L,r,B,std", [
+    (16, 64, 8, 4, 4, 2000, 0.02),    # headline shape, default init
+    (16, 64, 8, 4, 4, 301, 0.05),
+    (8, 32, 4, 2, 0, 777, 0.1),       # N=8 / XYZ workload shapes (no MLP)
+    (8, 32, 4, 2, 4, 129, 0.1),
+    (13, 64, 8, 2, 2, 97, 0.05),      # ragged tile (9 sequences of 13 tokens)
+    (32, 64, 8, 1, 4, 33, 0.05),
+    (1, 64, 8, 2, 0, 5, 0.05),
+])
+def test_log_rho_bf16(n, d, h, L, r, B, std):
+    spec = synth.model_spec(d, h, L, r)
+    th = synth.init_params(spec, seed=5 + n, std=std)
+    sig, sigp = synth.random_configs(n, B, seed=B)
+    ref = T.log_rho_np(spec, th, sig, sigp, n)
+    out = ctx_for(problem("ising", n), spec, th).log_rho(dev(sig), dev(sigp)).cpu().numpy()
+    err = logrho_err(out, ref)
+    assert err.max() <= 2e-2, err.max()
+
+
+@pytest.mark.parametrize("kind,n,d,h,L,r,Ns", [("ising", 16, 64, 8, 4, 4, 512), ("xyz", 8, 32, 4, 2, 0, 1024)])
+def test_cost_bf16(kind, n, d, h, L, r, Ns):
+    prob = problem(kind, n)
+    spec = synth.model_spec(d, h, L, r)
+    th = synth.init_params(spec, seed=3, std=0.02 if d == 64 else 0.1)
+    sig, sigp = synth.random_configs(n, Ns, seed=7)
+    _, cost, _ = ctx_for(prob, spec, th).local_estimator(dev(sig), dev(sigp))
+    ref = E.local_estimator(prob, spec, th, sig, sigp)
+    c_ref, _ = E.cost_mc(ref)
+    assert abs(cost - c_ref) <= 1e-3 * c_ref, (cost, c_ref)
+
+
+def test_metropolis_bf16_replays_decided_chains():
+    """One sweep (12 proposals) per chain; a chain counts as decided when every one of its proposals has
+    an oracle margin above 4e-2 (about 60% of chains for uniform u)."""
+    n = 6
+    spec = synth.model_spec(32, 4, 1, 0)
+    th = synth.init_params(spec, 0, std=0.3)
+    s0, s1 = synth.random_configs(n, 1024, seed=3)
+    a, b = dev(s0), dev(s1)
+    ctx_for(problem("ising", n), spec, th).sample(a, b, 1, seed=99, counter=5)
+    o0, o1, _, _, margin = OS.metropolis(spec, th, s0, s1, n, 1, 99, 5)
+    ok = margin > 4e-2
+    assert ok.sum() >= 300, ok.sum()
+    g0 = a.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    g1 = b.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    assert np.array_equal(g0[ok], o0[ok].astype(np.int64))
+    assert np.array_equal(g1[ok], o1[ok].astype(np.int64))
+
+
+def test_bf16_unsupported_shapes():
+    from paper_2502_20723_gb300 import tdo
+    spec = synth.model_spec(16, 2, 1, 0)
+    with pytest.raises(tdo.TdoError, match="EUNSUPPORTED"):
+        ctx_for(problem("ising", 4), spec, synth.init_params(spec))
