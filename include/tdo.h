@@ -118,6 +118,21 @@ tdo_status tdo_connections(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *si
 tdo_status tdo_local_estimator(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t Ns,
                                double *lloc, double *cost, double *stderr_);
 
+/* The local estimator above, for callers that must not allocate device memory while they run: a host
+ * application whose device memory belongs to another allocator (a framework's caching pool holding the
+ * free memory), or a latency-critical loop that cannot afford the device-wide synchronisation that
+ * cudaMalloc / cudaFree may imply.  The paper has no counterpart; this is an interface convenience.
+ * Same outputs as tdo_local_estimator, but sig, sigp and lloc must be device pointers (lloc 16-byte
+ * aligned), and the call
+ * allocates nothing: its scratch is one fixed device array (about 8.7 MB) that every GPU which loads
+ * the library holds until the process exits.  Limits: Ns <= 16384 and Ns * tdo_max_connections()
+ * <= 262144, else TDO_EINVAL.  The first call on a device looks up the array's device address (once
+ * per device, with that device current); make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other threads or streams) race and must not be
+ * made; the array keeps the last call's contents. */
+tdo_status tdo_local_estimator_noalloc(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t Ns,
+                                       double *lloc, double *cost, double *stderr_);
+
 /* Metropolis-Hastings on |rho|^2 with single-bit proposals (sampling section).  Chains are in/out in
  * sig/sigp [n_chains].  Proposal t of chain c draws Philox4x32-10(key = (seed lo, seed hi),
  * counter = (c, t lo, t hi, 0)) -> (x0, x1, ...): bit k = ((x0 >> 8) * 2N) >> 24 (k < N flips s_k,

@@ -929,3 +929,102 @@ extern "C" tdo_status tdo_sr_info(const tdo_ctx *c, int *iters, double *resid) {
   if (resid) *resid = c->last_sr_resid;
   return TDO_OK;
 }
+
+// ----------------------------------------------------------------------------- no-allocation estimator
+// A variant of tdo_local_estimator for callers that must not allocate device memory once they are
+// running: e.g. a host application whose device memory is entirely owned by another allocator (a
+// framework's caching pool that has reserved the free memory), or a latency-critical loop where the
+// device-wide synchronisation that cudaMalloc / cudaFree can imply is not acceptable.  Its scratch is
+// one file-scope device array of fixed size, present on every GPU that loads the library until the
+// process exits.
+#define TDO_NOALLOC_MAX_SAMPLES (1 << 14)   // samples per call
+#define TDO_NOALLOC_MAX_ENTRIES (1 << 18)   // samples x tdo_max_connections() per call
+
+namespace {
+constexpr size_t kNaCnt = 0;                                                  // int32 [MAX_SAMPLES]
+constexpr size_t kNaOffs = kNaCnt + 4ull * TDO_NOALLOC_MAX_SAMPLES;           // int64 [MAX_SAMPLES + 1]
+constexpr size_t kNaLl2 = kNaOffs + 8ull * (TDO_NOALLOC_MAX_SAMPLES + 32);    // double [MAX_SAMPLES]
+constexpr size_t kNaStats = kNaLl2 + 8ull * TDO_NOALLOC_MAX_SAMPLES;          // double [4]
+constexpr size_t kNaFlag = kNaStats + 32;                                     // int (starts at zero)
+constexpr size_t kNaCsig = kNaFlag + 256 - 32;                                // u32 [MAX_ENTRIES]
+constexpr size_t kNaCsigp = kNaCsig + 4ull * TDO_NOALLOC_MAX_ENTRIES;
+constexpr size_t kNaCcoef = kNaCsigp + 4ull * TDO_NOALLOC_MAX_ENTRIES;        // float2
+constexpr size_t kNaFsig = kNaCcoef + 8ull * TDO_NOALLOC_MAX_ENTRIES;
+constexpr size_t kNaFsigp = kNaFsig + 4ull * TDO_NOALLOC_MAX_ENTRIES;
+constexpr size_t kNaFcoef = kNaFsigp + 4ull * TDO_NOALLOC_MAX_ENTRIES;        // float2
+constexpr size_t kNaFlr = kNaFcoef + 8ull * TDO_NOALLOC_MAX_ENTRIES;          // float2
+constexpr size_t kNaBytes = kNaFlr + 8ull * TDO_NOALLOC_MAX_ENTRIES;          // about 8.7 MB
+static_assert(kNaCsig % 256 == 0 && kNaFlr % 16 == 0, "scratch alignment");
+
+void *g_noalloc_ptr[64];   // device address of g_noalloc_scratch per device (set up on first use)
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+extern "C" tdo_status tdo_local_estimator_noalloc(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t Ns,
+                                                  double *lloc, double *cost, double *stderr_) {
+  if (!c) return TDO_EINVAL;
+  if (Ns == 0) return fail(c, TDO_EINVAL, "Ns must be > 0");
+  if (!sig || !sigp || !lloc) return fail(c, TDO_EINVAL, "NULL buffer");
+  if (!is_device_ptr(sig) || !is_device_ptr(sigp) || !is_device_ptr(lloc))
+    return fail(c, TDO_EINVAL, "tdo_local_estimator_noalloc takes device pointers for sig, sigp and lloc");
+  if (reinterpret_cast<uintptr_t>(lloc) % 16 != 0)
+    return fail(c, TDO_EINVAL, "tdo_local_estimator_noalloc: lloc must be 16-byte aligned");
+  const int M = c->n_pat;
+  if (Ns > (size_t)TDO_NOALLOC_MAX_SAMPLES || Ns * (size_t)M > (size_t)TDO_NOALLOC_MAX_ENTRIES)
+    return fail(c, TDO_EINVAL,
+                "tdo_local_estimator_noalloc: Ns = %zu with %d connections per sample exceeds its fixed scratch "
+                "(at most %d samples and %d samples x connections); split the call or use tdo_local_estimator",
+                Ns, M, TDO_NOALLOC_MAX_SAMPLES, TDO_NOALLOC_MAX_ENTRIES);
+  int dev = 0;
+  CU(c, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(c, TDO_EUNSUPPORTED, "device index %d out of range", dev);
+  if (!g_noalloc_ptr[dev]) {   // one-time set-up on this device (device current)
+    void *p = nullptr;
+    CU(c, cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  unsigned char *base = static_cast<unsigned char *>(g_noalloc_ptr[dev]);
+  int32_t *cnt = reinterpret_cast<int32_t *>(base + kNaCnt);
+  int64_t *offs = reinterpret_cast<int64_t *>(base + kNaOffs);
+  double *l2 = reinterpret_cast<double *>(base + kNaLl2);
+  double *stats = reinterpret_cast<double *>(base + kNaStats);
+  int *flag = reinterpret_cast<int *>(base + kNaFlag);
+  uint32_t *csig = reinterpret_cast<uint32_t *>(base + kNaCsig), *csigp = reinterpret_cast<uint32_t *>(base + kNaCsigp);
+  float2 *ccoef = reinterpret_cast<float2 *>(base + kNaCcoef);
+  uint32_t *fsig = reinterpret_cast<uint32_t *>(base + kNaFsig), *fsigp = reinterpret_cast<uint32_t *>(base + kNaFsigp);
+  float2 *fcoef = reinterpret_cast<float2 *>(base + kNaFcoef), *flr = reinterpret_cast<float2 *>(base + kNaFlr);
+
+  CU(c, cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  CU(c, launch_connections(c->d_pat.as<ConnPattern>(), M, c->d_con.as<ConnContrib>(), sig, sigp, Ns, cnt, csig, csigp,
+                           ccoef, c->stream));
+  CU(c, launch_scan(cnt, Ns, offs, c->stream));
+  int64_t total = 0;
+  CU(c, cudaMemcpyAsync(&total, offs + Ns, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  CU(c, launch_compact(cnt, offs, Ns, M, csig, csigp, ccoef, fsig, fsigp, fcoef, c->stream));
+  if (c->model.precision == TDO_BF16)
+    CU(c, launch_fwd_bf16(c->dm, c->dmb, fsig, fsigp, (size_t)total, flr, c->errflag.as<int>(), c->n_sm, c->stream));
+  else
+    CU(c, launch_fwd32(c->dm, fsig, fsigp, (size_t)total, flr, c->n_sm, c->stream));
+  CU(c, launch_lloc(offs, Ns, fcoef, flr, reinterpret_cast<double2 *>(lloc), l2, stats, flag, c->stream));
+  double st[2];
+  int nf = 0;
+  CU(c, cudaMemcpyAsync(st, stats, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaMemcpyAsync(&nf, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  if (c->model.precision == TDO_BF16) {
+    int f = 0;
+    CU(c, cudaMemcpy(&f, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) {
+      CU(c, cudaMemset(c->errflag.p, 0, sizeof(int)));
+      return fail(c, TDO_ETIMEOUT, "a tensor-core kernel's bounded wait gave up (results of that launch are invalid)");
+    }
+  }
+  if (nf) return fail(c, TDO_ENUMERIC, "non-finite log rho or L_loc (rho = 0 exactly, or non-finite parameters)");
+  const double mean = st[0] / (double)Ns;
+  const double var = st[1] / (double)Ns - mean * mean;
+  if (cost) *cost = mean;
+  if (stderr_) *stderr_ = var > 0 ? sqrt(var / (double)Ns) : 0.0;
+  return TDO_OK;
+}

@@ -21,7 +21,7 @@ STATUS = {0: "TDO_OK", -1: "TDO_EINVAL", -2: "TDO_ENOMEM", -3: "TDO_ECUDA", -4: 
 
 EXPORTS = ["tdo_model_num_params", "tdo_create", "tdo_destroy", "tdo_num_params", "tdo_max_connections",
            "tdo_set_params", "tdo_get_params", "tdo_log_rho", "tdo_log_rho_vjp", "tdo_jacobian",
-           "tdo_connections", "tdo_local_estimator", "tdo_sample", "tdo_grad", "tdo_sr_solve", "tdo_set_sr_options", "tdo_sr_step",
+           "tdo_connections", "tdo_local_estimator", "tdo_local_estimator_noalloc", "tdo_sample", "tdo_grad", "tdo_sr_solve", "tdo_set_sr_options", "tdo_sr_step",
            "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_last_error"]
 
 
@@ -71,6 +71,7 @@ def lib() -> C.CDLL:
         L.tdo_jacobian.argtypes = [vp, vp, vp, sz, vp]
         L.tdo_connections.argtypes = [vp, vp, vp, sz, vp, vp, vp, vp]
         L.tdo_local_estimator.argtypes = [vp, vp, vp, sz, vp, dp, dp]
+        L.tdo_local_estimator_noalloc.argtypes = [vp, vp, vp, sz, vp, dp, dp]
         L.tdo_sample.argtypes = [vp, sz, sz, u64, u64, vp, vp, vp, vp, C.POINTER(u64)]
         L.tdo_grad.argtypes = [vp, vp, vp, sz, vp, dp, vp]
         L.tdo_sr_solve.argtypes = [vp, vp, sz, vp, C.c_double, C.c_double, i32, vp, C.POINTER(i32), dp]
