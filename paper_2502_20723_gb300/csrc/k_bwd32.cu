@@ -5,8 +5,8 @@
 // the cotangent of log rho through the Hermitian symmetrisation (Eq. log_sum_exp_conjugate), the head,
 // the mean pooling, every layer in reverse (MLP, W^O, softmax attention, Q/K/V) and the embedding.
 // Weight gradients are D x D blocks reduced over the rows of the tile:
-//   mode 0 (VJP): summed over the tile and added (plain read-modify-write, no atomics) to the CTA's own
-//                 FP32 accumulator vector; the host reduces the per-CTA vectors in FP64 (deterministic),
+//   mode 0 (VJP): summed over the tile and added with float4 atomics to one of n_copies FP32 accumulator
+//                 vectors (CTA b uses copy b % n_copies; 16 copies stay L2-resident), reduced in FP64,
 //   mode 1 (Jacobian): one per (configuration, seed) and written to O[b][k][seed]
 //                      (seed 0: d Re log rho, seed 1: d Im log rho).
 #include "f32_tile.cuh"
@@ -44,23 +44,25 @@ __host__ __device__ __forceinline__ int seqs_for(int n, int rows) {
 
 struct SinkCtx {
   int mode;
-  float *g;          // mode 0: this CTA's private accumulator [P] (16-byte aligned)
+  float *g;          // mode 0: this CTA's accumulator copy [P] (16-byte aligned)
   float *O;          // mode 1: [B][P][2]
   size_t P;
 };
 
 // Add / write one gradient value at flat parameter index k for virtual configuration v of the tile.
 __device__ __forceinline__ void sink1(const SinkCtx &s, long long k, float v, long long b, int seed) {
-  if (s.mode == 0) s.g[k] += v;   // private to this CTA; each index has one owning thread
+  if (s.mode == 0) atomicAdd(s.g + k, v);
   else s.O[((size_t)b * s.P + (size_t)k) * 2 + seed] = v;
 }
 
 // Copy a rows x D block of global memory (row stride gld, column offset col0) transposed into smem:
 // s[c][r] = g[r][col0 + c].
+// Consecutive threads take consecutive r: conflict-free shared stores; the strided global reads of the
+// block (16 KB at D = 64) are served from L1 after the first touch of each line.
 template <int D>
 __device__ __forceinline__ void stage_blockT(const float *__restrict__ g, int gld, int col0, float *s) {
   for (int i = threadIdx.x; i < D * D; i += kThreads) {
-    const int r = i / D, c = i % D;
+    const int r = i % D, c = i / D;
     s[c * D + r] = __ldg(g + (size_t)r * gld + col0 + c);
   }
 }
@@ -130,13 +132,8 @@ __device__ __forceinline__ void sink_block(const SinkCtx &s, float (&acc)[BwdGeo
     for (int h = 0; h < 2; ++h) {
       const long long base = off + k * ld + (h ? D / 2 : 0) + 4 * tx;
       if (s.mode == 0 && (base & 3) == 0) {
-        float4 *q = reinterpret_cast<float4 *>(s.g + base);
-        float4 v = *q;
-        v.x += acc[j][4 * h];
-        v.y += acc[j][4 * h + 1];
-        v.z += acc[j][4 * h + 2];
-        v.w += acc[j][4 * h + 3];
-        *q = v;
+        atomicAdd(reinterpret_cast<float4 *>(s.g + base),
+                  make_float4(acc[j][4 * h], acc[j][4 * h + 1], acc[j][4 * h + 2], acc[j][4 * h + 3]));
       } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e) sink1(s, base + e, acc[j][4 * h + e], b, seed);
@@ -285,8 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float *scr = scratch + (size_t)blockIdx.x * (size_t)m.layers * blk;
   SinkCtx sk;
   sk.mode = mode;
-  sk.g = gacc ? gacc + (size_t)blockIdx.x * g_stride : nullptr;   // one per CTA; g_stride % 4 == 0
-  (void)n_copies;
+  sk.g = gacc ? gacc + (size_t)(blockIdx.x % n_copies) * g_stride : nullptr;   // g_stride % 4 == 0
   sk.O = O;
   sk.P = P;
   const int nranges = mode == 0 ? 1 : tcv;
@@ -469,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           __syncthreads();
           for (int rg = 0; rg < nranges; ++rg) {
             if (mode == 1 && !vvalid(rg)) continue;
-            const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? R : r0 + 2 * n;
+            const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? nrows : r0 + 2 * n;
             float dw[BG::KPT][8];
             mmT_acc<D, true>(Bf[7], Bf[6], r0, r1, dw);
             sink_block<D>(sk, dw, fo.W2[l] + (long long)c0 * D, D, vb(rg), vs(rg));
@@ -482,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int rg = 0; rg < nranges; ++rg) {
           if (mode == 1 && !vvalid(rg)) continue;
-          const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? R : r0 + 2 * n;
+          const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? nrows : r0 + 2 * n;
           colsum_sink<D>(sk, Bf[6], r0, r1, fo.b2[l], vb(rg), vs(rg));
         }
         __syncthreads();
@@ -500,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       for (int rg = 0; rg < nranges; ++rg) {
         if (mode == 1 && !vvalid(rg)) continue;
-        const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? R : r0 + 2 * n;
+        const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? nrows : r0 + 2 * n;
         float dw[BG::KPT][8];
         mmT_acc<D, false>(Bf[4], Bf[6], r0, r1, dw);
         sink_block<D>(sk, dw, fo.Wo[l], D, vb(rg), vs(rg));
@@ -519,7 +515,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncthreads();
       for (int rg = 0; rg < nranges; ++rg) {
         if (mode == 1 && !vvalid(rg)) continue;
-        const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? R : r0 + 2 * n;
+        const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? nrows : r0 + 2 * n;
         float dw[BG::KPT][8];
         mmT_acc<D, false>(Bf[0], Bf[4], r0, r1, dw);
         sink_block<D>(sk, dw, fo.Wq[l], D, vb(rg), vs(rg));

@@ -33,8 +33,9 @@ struct Geo {
   static constexpr int HC = (4 * D < 128) ? 4 * D : 128;        // hidden chunk (max mlp_ratio 4)
   static constexpr int A_OFF = 0;                                // BF16 [128][D]
   static constexpr int A_BYTES = kRows * D * 2;
-  static constexpr int KV_OFF = A_OFF + A_BYTES;                 // FP32 K [128][D], V [128][D]
-  static constexpr int KV_BYTES = 2 * kRows * D * 4;             // (G [128][HC] BF16, pool [128][D] alias)
+  static constexpr int KS = D + 1;                               // K/V/pool row stride (floats): no bank conflicts
+  static constexpr int KV_OFF = A_OFF + A_BYTES;                 // FP32 K [128][KS], V [128][KS]
+  static constexpr int KV_BYTES = 2 * kRows * KS * 4;            // (G [128][HC] BF16, pool [128][KS] alias)
   static constexpr int W_OFF = KV_OFF + KV_BYTES;                // weights of the current GEMM
   static constexpr int W_BYTES = (3 * D * D * 2 > 2 * HC * D) ? 3 * D * D * 2 : 2 * HC * D;
   static constexpr int M_OFF = W_OFF + W_BYTES;                  // misc
@@ -143,6 +144,22 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 2^x and tanh(x) on the SFU (PTX ex2.approx / tanh.approx); the BF16 path's error budget allows them.
+__device__ __forceinline__ float ex2_fast(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float gelu_fast(float u) {
+  const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+  return 0.5f * u * (1.0f + tanh_fast(k0 * fmaf(k1 * u, u * u, u)));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(a), "f"(b));
@@ -217,11 +234,12 @@ __device__ __forceinline__ bool sync_fail(Ctl &c, bool ok) {
 
 // The whole ansatz on one tile; configurations in cfg_s / cfg_p [ts/2], results to res [ts/2].
 // Returns false on a (bounded) wait timeout.
-template <int D>
+template <int D, int HD>
 __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm, Ctl &c, int ts,
                           const uint32_t *cfg_s, const uint32_t *cfg_p, float2 *res) {
   using G = Geo<D>;
   constexpr int DH = D / 2;   // columns per thread (half)
+  constexpr int KS = G::KS;
   const int n = m.n_sites;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (warp & 3) + lane;
@@ -229,7 +247,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
   uint8_t *A = sm + G::A_OFF;
   float *Ks = reinterpret_cast<float *>(sm + G::KV_OFF);
-  float *Vs = Ks + kRows * D;
+  float *Vs = Ks + kRows * KS;
   uint8_t *Gs = sm + G::KV_OFF;                     // hidden chunk (aliases K/V)
   const uint32_t a_addr = smem_u32(A), w_addr = smem_u32(sm + G::W_OFF), g_addr = smem_u32(Gs);
   const bool valid = row < ts * n;
@@ -252,8 +270,8 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
 #pragma unroll
   for (int j = 0; j < DH; j += 8) st_row8(A, row, half * DH + j, D, X + j);
 
-  const int heads = m.heads, dh = m.dh;
-  const float scale = rsqrtf((float)dh);
+  const int heads = m.heads;
+  const float qscale = rsqrtf((float)HD) * 1.4426950408889634f;   // softmax in base 2
   for (int l = 0; l < m.layers; ++l) {
     // ---------------- QKV (TMEM reads of the previous sub-layer done before the MMA overwrites them)
     tc_fence_before();
@@ -270,68 +288,56 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
       float v[16];
       tmem_ld16(c.tmem + lane_addr + D + half * DH + j, v);
 #pragma unroll
-      for (int e = 0; e < 16; ++e) Ks[row * D + half * DH + j + e] = v[e];
+      for (int e = 0; e < 16; ++e) Ks[row * KS + half * DH + j + e] = v[e];
       tmem_ld16(c.tmem + lane_addr + 2 * D + half * DH + j, v);
 #pragma unroll
-      for (int e = 0; e < 16; ++e) Vs[row * D + half * DH + j + e] = v[e];
+      for (int e = 0; e < 16; ++e) Vs[row * KS + half * DH + j + e] = v[e];
     }
     __syncthreads();
-    // ---------------- attention: this thread's row, heads of its column half; output -> A (BF16)
+    // ---------------- attention: this thread's row, heads of its column half, single-pass (online)
+    // softmax in base 2; output -> A (BF16)
     {
       const int h0 = half * (heads / 2), h1 = h0 + heads / 2;
       for (int h = h0; h < h1; ++h) {
-        float q[16], o[16], sc[TDO_MAX_N];
+        float q[HD], o[HD];
         {
-          // q of head h: dh <= 16 columns starting at h*dh (loaded 8 at a time)
           float t8[8];
-          tmem_ld8(c.tmem + lane_addr + h * dh, t8);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) q[e] = t8[e];
-          if (dh > 8) {
-            tmem_ld8(c.tmem + lane_addr + h * dh + 8, t8);
+          for (int e8 = 0; e8 < HD; e8 += 8) {
+            tmem_ld8(c.tmem + lane_addr + h * HD + e8, t8);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) q[8 + e] = t8[e];
-          } else {
-#pragma unroll
-            for (int e = 8; e < 16; ++e) q[e] = 0.f;
+            for (int e = 0; e < 8; ++e) q[e8 + e] = t8[e] * qscale;
           }
         }
 #pragma unroll
-        for (int e = 0; e < 16; ++e) o[e] = 0.f;
+        for (int e = 0; e < HD; ++e) o[e] = 0.f;
         if (valid) {
-          const int base = s * n, col = h * dh;
-          float mx = -INFINITY;
+          const float *kr = Ks + s * n * KS + h * HD;
+          const float *vr = Vs + s * n * KS + h * HD;
+          float mx = -INFINITY, l = 0.f;
+#pragma unroll 2
+          for (int j = 0; j < n; ++j, kr += KS, vr += KS) {
+            float sc = 0.f;
 #pragma unroll
-          for (int j = 0; j < TDO_MAX_N; ++j) {
-            if (j < n) {
-              const float *kr = Ks + (base + j) * D + col;
-              float dot = 0.f;
+            for (int e = 0; e < HD; ++e) sc = fmaf(q[e], kr[e], sc);
+            if (sc > mx) {
+              const float cr = ex2_fast(mx - sc);
+              l *= cr;
 #pragma unroll
-              for (int e = 0; e < 16; ++e)
-                if (e < dh) dot = fmaf(q[e], kr[e], dot);
-              sc[j] = dot * scale;
-              mx = fmaxf(mx, sc[j]);
+              for (int e = 0; e < HD; ++e) o[e] *= cr;
+              mx = sc;
             }
+            const float p = ex2_fast(sc - mx);
+            l += p;
+#pragma unroll
+            for (int e = 0; e < HD; ++e) o[e] = fmaf(p, vr[e], o[e]);
           }
-          float sum = 0.f;
+          const float inv = 1.0f / l;
 #pragma unroll
-          for (int j = 0; j < TDO_MAX_N; ++j) {
-            if (j < n) {
-              const float p = __expf(sc[j] - mx);
-              sum += p;
-              const float *vr = Vs + (base + j) * D + col;
-#pragma unroll
-              for (int e = 0; e < 16; ++e)
-                if (e < dh) o[e] = fmaf(p, vr[e], o[e]);
-            }
-          }
-          const float inv = 1.0f / sum;
-#pragma unroll
-          for (int e = 0; e < 16; ++e) o[e] *= inv;
+          for (int e = 0; e < HD; ++e) o[e] *= inv;
         }
-        // dh is a multiple of 8 in the BF16 path
-        st_row8(A, row, h * dh, D, o);
-        if (dh > 8) st_row8(A, row, h * dh + 8, D, o + 8);
+#pragma unroll
+        for (int e8 = 0; e8 < HD; e8 += 8) st_row8(A, row, h * HD + e8, D, o + e8);
       }
     }
     tc_fence_before();
@@ -373,7 +379,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
           tmem_ld16(c.tmem + lane_addr + half * HH + j, v);
           const int c0 = ch * G::HC + half * HH + j;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] = gelu_f(v[e] + __ldg(m.L[l].b1 + c0 + e));
+          for (int e = 0; e < 16; ++e) v[e] = gelu_fast(v[e] + __ldg(m.L[l].b1 + c0 + e));
           st_row8(Gs, row, half * HH + j, G::HC, v);
           st_row8(Gs, row, half * HH + j + 8, G::HC, v + 8);
         }
@@ -403,7 +409,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
   __syncthreads();   // all K/V/G reads done before the pool buffer overwrites them
   float *Pool = reinterpret_cast<float *>(sm + G::KV_OFF);
 #pragma unroll
-  for (int j = 0; j < DH; ++j) Pool[row * D + half * DH + j] = X[j];
+  for (int j = 0; j < DH; ++j) Pool[row * KS + half * DH + j] = X[j];
   __syncthreads();
   float *Fs = reinterpret_cast<float *>(sm + G::M_OFF + 16 + 8 + 512);
   for (int p = warp; p < ts * 2; p += kThreads / 32) {
@@ -411,7 +417,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
     float acc = 0.f;
     for (int cc = lane; cc < D; cc += 32) {
       float hsum = 0.f;
-      for (int i = 0; i < n; ++i) hsum += Pool[(sq * n + i) * D + cc];
+      for (int i = 0; i < n; ++i) hsum += Pool[(sq * n + i) * KS + cc];
       acc = fmaf(hsum, __ldg(m.Wh + 2 * cc + o), acc);
     }
     acc = warp_sum(acc);
@@ -467,7 +473,7 @@ __device__ __forceinline__ void ctl_finish(Ctl &c) {
   }
 }
 
-template <int D>
+template <int D, int HD>
 __global__ void __launch_bounds__(kThreads, 2) k_fwd_bf16(DevModel m, DevModelBF16 mb, const uint32_t *__restrict__ sig,
                                                           const uint32_t *__restrict__ sigp, size_t B,
                                                           float2 *__restrict__ out, int *err) {
@@ -487,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_bf16(DevModel m, DevModelBF
       cp[threadIdx.x] = b < B ? sigp[b] : 0u;
     }
     __syncthreads();
-    if (!eval_tile<D>(m, mb, sm, c, ts, cs, cp, res)) break;
+    if (!eval_tile<D, HD>(m, mb, sm, c, ts, cs, cp, res)) break;
     if (threadIdx.x < tc) {
       const size_t b = tile * tc + threadIdx.x;
       if (b < B) out[b] = res[threadIdx.x];
@@ -498,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_bf16(DevModel m, DevModelBF
 }
 
 // Metropolis chains on the BF16 forward (same proposal stream and acceptance rule as the FP32 sampler).
-template <int D>
+template <int D, int HD>
 __global__ void __launch_bounds__(kThreads, 2)
     k_sample_bf16(DevModel m, DevModelBF16 mb, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
                   uint32_t *__restrict__ sig, uint32_t *__restrict__ sigp, uint32_t *__restrict__ ssig,
@@ -522,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (mine) { s0 = sig[ch]; s1 = sigp[ch]; }
     if (threadIdx.x < tc) { cs[threadIdx.x] = s0; cp[threadIdx.x] = s1; }
     __syncthreads();
-    if (!eval_tile<D>(m, mb, sm, c, ts, cs, cp, res)) break;
+    if (!eval_tile<D, HD>(m, mb, sm, c, ts, cs, cp, res)) break;
     if (threadIdx.x < tc) lcur = res[threadIdx.x].x;
     bool stop = false;
     for (size_t sw = 0; sw < n_sweeps && !stop; ++sw) {
@@ -538,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           cp[threadIdx.x] = p1;
         }
         __syncthreads();
-        if (!eval_tile<D>(m, mb, sm, c, ts, cs, cp, res)) { stop = true; break; }
+        if (!eval_tile<D, HD>(m, mb, sm, c, ts, cs, cp, res)) { stop = true; break; }
         if (threadIdx.x < tc) {
           const float lnew = res[threadIdx.x].x;
           if (u < expf(fminf(0.0f, 2.0f * (lnew - lcur)))) {
@@ -576,7 +582,7 @@ __global__ void k_pack(const float *__restrict__ W, int ldw, int col0, int K, in
 }  // namespace tdo
 
 bool bf16_supported(const DevModel &m) {
-  return (m.d == 64 || m.d == 32) && m.dh % 8 == 0 && m.heads % 2 == 0 && (m.ffn == 0 || m.ffn % (m.d * 4 < 128 ? m.d * 4 : 128) == 0) &&
+  return (m.d == 64 || m.d == 32) && (m.dh == 8 || m.dh == 16) && m.heads % 2 == 0 && (m.ffn == 0 || m.ffn % (m.d * 4 < 128 ? m.d * 4 : 128) == 0) &&
          m.embed == 0;
 }
 
@@ -623,15 +629,17 @@ cudaError_t launch_pack_bf16(const DevModel &m, uint16_t *dst16, DevModelBF16 *v
   return cudaGetLastError();
 }
 
-template <int D>
+template <int D, int HD>
 static cudaError_t fwd_bf16_impl(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                                  const uint32_t *sigp, size_t B, float2 *out, int *err, int n_sm, cudaStream_t st) {
   using namespace tdo::bf16;
   const int bytes = Geo<D>::BYTES;
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_bf16<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_bf16<D, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fwd_bf16<D, HD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_bf16<D>, kThreads, bytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_bf16<D, HD>, kThreads, bytes);
   if (e != cudaSuccess) return e;
   if (per_sm > 2) per_sm = 2;   // TMEM: 2 x 256 columns per SM
   if (per_sm < 1) per_sm = 1;
@@ -639,29 +647,33 @@ static cudaError_t fwd_bf16_impl(const DevModel &m, const DevModelBF16 &mb, cons
   const size_t ntiles = (B + tc - 1) / tc;
   size_t grid = (size_t)n_sm * per_sm;
   if (grid > ntiles) grid = ntiles;
-  k_fwd_bf16<D><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, sig, sigp, B, out, err);
+  k_fwd_bf16<D, HD><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, sig, sigp, B, out, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_bf16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig, const uint32_t *sigp,
                             size_t B, float2 *logrho, int *err_flag, int n_sm, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
-  if (m.d == 64) return fwd_bf16_impl<64>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
-  if (m.d == 32) return fwd_bf16_impl<32>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
+  if (m.d == 64 && m.dh == 8) return fwd_bf16_impl<64, 8>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
+  if (m.d == 64 && m.dh == 16) return fwd_bf16_impl<64, 16>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
+  if (m.d == 32 && m.dh == 8) return fwd_bf16_impl<32, 8>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
+  if (m.d == 32 && m.dh == 16) return fwd_bf16_impl<32, 16>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
   return cudaErrorInvalidValue;
 }
 
-template <int D>
+template <int D, int HD>
 static cudaError_t sample_bf16_impl(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
                                     uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
                                     uint32_t *ssigp, unsigned long long *accepted, int *err, int n_sm,
                                     cudaStream_t st) {
   using namespace tdo::bf16;
   const int bytes = Geo<D>::BYTES;
-  cudaError_t e = cudaFuncSetAttribute(k_sample_bf16<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_sample_bf16<D, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sample_bf16<D, HD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_bf16<D>, kThreads, bytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_bf16<D, HD>, kThreads, bytes);
   if (e != cudaSuccess) return e;
   if (per_sm > 2) per_sm = 2;
   if (per_sm < 1) per_sm = 1;
@@ -669,8 +681,8 @@ static cudaError_t sample_bf16_impl(const DevModel &m, const DevModelBF16 &mb, s
   const size_t ntiles = (n_chains + tc - 1) / tc;
   size_t grid = (size_t)n_sm * per_sm;
   if (grid > ntiles) grid = ntiles;
-  k_sample_bf16<D><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp,
-                                                           ssig, ssigp, accepted, err);
+  k_sample_bf16<D, HD><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp,
+                                                               ssig, ssigp, accepted, err);
   return cudaGetLastError();
 }
 
@@ -679,9 +691,14 @@ cudaError_t launch_sample_bf16(const DevModel &m, const DevModelBF16 &mb, size_t
                                uint32_t *ssigp, unsigned long long *accepted, int *err_flag, int n_sm,
                                cudaStream_t st) {
   if (n_chains == 0) return cudaSuccess;
-  if (m.d == 64)
-    return sample_bf16_impl<64>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted, err_flag, n_sm, st);
-  if (m.d == 32)
-    return sample_bf16_impl<32>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted, err_flag, n_sm, st);
+#define TDO_SAMPLE_BF16(DD, HH)                                                                                   \
+  if (m.d == DD && m.dh == HH)                                                                                     \
+    return sample_bf16_impl<DD, HH>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted,     \
+                                    err_flag, n_sm, st);
+  TDO_SAMPLE_BF16(64, 8)
+  TDO_SAMPLE_BF16(64, 16)
+  TDO_SAMPLE_BF16(32, 8)
+  TDO_SAMPLE_BF16(32, 16)
+#undef TDO_SAMPLE_BF16
   return cudaErrorInvalidValue;
 }

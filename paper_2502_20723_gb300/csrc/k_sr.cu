@@ -14,7 +14,6 @@ namespace tdo {
 
 constexpr int kSrBlock = 256;
 constexpr int kRun = 32;     // FP32 products per FP64 accumulation
-constexpr int kGroup = 4;    // samples per block pass in the t kernel
 
 enum {
   S_RZ = 0, S_BN, S_AL, S_RN, S_DONE, S_IT, S_TOL, S_PAP, S_CR, S_CI, S_TR, S_TI, S_COUNT
@@ -116,41 +115,49 @@ __global__ void k_sr_cfin(const double *__restrict__ part, const double *__restr
   if (threadIdx.x == 0) { sc[S_CR] = a; sc[S_CI] = b; }
 }
 
-// t[s] = sum_k O[s][k] v[k] - mean . v  for kGroup samples per pass (v read once per group).
-__global__ void k_sr_t(const float2 *__restrict__ O, size_t Ns, size_t P, const float *__restrict__ vf,
-                       float2 *__restrict__ t, const double *__restrict__ sc) {
-  __shared__ double sh[32];
+// Partial dot products of the rows of O with v over one chunk of kChunk parameters: block (chunk, sg)
+// streams the chunk of every sample row of sample group sg (8 KB contiguous per row), one warp per
+// row at a time, with the chunk of v in shared memory.  part[chunk][s] = sum_{k in chunk} O[s][k] v[k].
+constexpr int kChunk = 1024;
+constexpr int kSampleGroups = 8;
+
+__global__ void k_sr_tpart(const float2 *__restrict__ O, size_t Ns, size_t P, const float *__restrict__ vf,
+                           double2 *__restrict__ part, const double *__restrict__ sc) {
+  __shared__ float vs[kChunk];
+  if (sc[S_DONE] != 0.0) return;
+  const size_t k0 = (size_t)blockIdx.x * kChunk;
+  const int kn = (int)((P - k0) < (size_t)kChunk ? (P - k0) : (size_t)kChunk);
+  for (int i = threadIdx.x; i < kChunk; i += blockDim.x) vs[i] = i < kn ? vf[k0 + i] : 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const size_t per = (Ns + kSampleGroups - 1) / kSampleGroups;
+  const size_t s_begin = (size_t)blockIdx.y * per;
+  const size_t s_end = s_begin + per < Ns ? s_begin + per : Ns;
+  for (size_t s = s_begin + warp; s < s_end; s += nw) {
+    const float2 *row = O + s * P + k0;
+    float ar = 0.f, ai = 0.f;
+#pragma unroll 8
+    for (int i = lane; i < kn; i += 32) {
+      const float2 o = __ldg(row + i);
+      const float x = vs[i];
+      ar = fmaf(o.x, x, ar);
+      ai = fmaf(o.y, x, ai);
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if (lane == 0) part[(size_t)blockIdx.x * Ns + s] = make_double2(ar, ai);
+  }
+}
+
+// t[s] = sum_chunks part[chunk][s] - mean . v   (thread per sample, FP64)
+__global__ void k_sr_tred(const double2 *__restrict__ part, int nchunks, size_t Ns, float2 *__restrict__ t,
+                          const double *__restrict__ sc) {
   if (sc[S_DONE] != 0.0) return;
   const double cr = sc[S_CR], ci = sc[S_CI];
-  for (size_t s0 = (size_t)blockIdx.x * kGroup; s0 < Ns; s0 += (size_t)gridDim.x * kGroup) {
-    const int ng = (int)((Ns - s0) < (size_t)kGroup ? (Ns - s0) : (size_t)kGroup);
-    double ar[kGroup], ai[kGroup];
-    float fr[kGroup], fi[kGroup];
-#pragma unroll
-    for (int g = 0; g < kGroup; ++g) { ar[g] = ai[g] = 0.0; fr[g] = fi[g] = 0.f; }
-    int run = 0;
-    for (size_t k = threadIdx.x; k < P; k += blockDim.x) {
-      const float x = __ldg(vf + k);
-#pragma unroll
-      for (int g = 0; g < kGroup; ++g) {
-        if (g < ng) {
-          const float2 o = __ldg(O + (s0 + g) * P + k);
-          fr[g] = fmaf(o.x, x, fr[g]);
-          fi[g] = fmaf(o.y, x, fi[g]);
-        }
-      }
-      if (++run == kRun) {
-#pragma unroll
-        for (int g = 0; g < kGroup; ++g) { ar[g] += fr[g]; ai[g] += fi[g]; fr[g] = fi[g] = 0.f; }
-        run = 0;
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < kGroup; ++g) {
-      const double r = block_sum_d(ar[g] + fr[g], sh);
-      const double i = block_sum_d(ai[g] + fi[g], sh);
-      if (threadIdx.x == 0 && g < ng) t[s0 + g] = make_float2((float)(r - cr), (float)(i - ci));
-    }
+  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Ns; s += gridDim.x * (size_t)blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int c = 0; c < nchunks; ++c) { const double2 q = part[(size_t)c * Ns + s]; a += q.x; b += q.y; }
+    t[s] = make_float2((float)(a - cr), (float)(b - ci));
   }
 }
 
@@ -312,32 +319,40 @@ struct SrPtrs {
   double *diag, *r, *z, *p, *Ap, *part, *part2, *part3, *sc;
   float *vf;
   float2 *t;
+  double2 *tpart;
 };
 
+// Carves the workspace; every region starts on a 16-byte boundary (double2 / float2 / float4 access).
 static SrPtrs sr_carve(double *work, size_t Ns, size_t P) {
+  char *b = reinterpret_cast<char *>(work);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char *p = b + off; off += (bytes + 15) / 16 * 16; return p; };
   SrPtrs q;
-  q.mean = reinterpret_cast<double2 *>(work);
-  q.diag = work + 2 * P;
-  q.r = q.diag + P;
-  q.z = q.r + P;
-  q.p = q.z + P;
-  q.Ap = q.p + P;
-  q.part = q.Ap + P;
-  q.part2 = q.part + 1024;
-  q.part3 = q.part2 + 1024;
-  q.sc = q.part3 + 1024;
-  q.vf = reinterpret_cast<float *>(q.sc + 32);
-  q.t = reinterpret_cast<float2 *>(q.vf + ((P + 3) / 4 * 4));
-  (void)Ns;
+  q.mean = reinterpret_cast<double2 *>(take(16 * P));
+  q.diag = reinterpret_cast<double *>(take(8 * P));
+  q.r = reinterpret_cast<double *>(take(8 * P));
+  q.z = reinterpret_cast<double *>(take(8 * P));
+  q.p = reinterpret_cast<double *>(take(8 * P));
+  q.Ap = reinterpret_cast<double *>(take(8 * P));
+  q.part = reinterpret_cast<double *>(take(8 * 1024));
+  q.part2 = reinterpret_cast<double *>(take(8 * 1024));
+  q.part3 = reinterpret_cast<double *>(take(8 * 1024));
+  q.sc = reinterpret_cast<double *>(take(8 * 32));
+  q.vf = reinterpret_cast<float *>(take(4 * P));
+  q.t = reinterpret_cast<float2 *>(take(8 * Ns));
+  q.tpart = reinterpret_cast<double2 *>(take(16 * ((P + kChunk - 1) / kChunk) * Ns));
   return q;
 }
 
 // S' v -> Ap (and the partials of v . Ap in q.part), all on the device.
 static void matvec(const float2 *O, size_t Ns, size_t P, const double *v, double shift, SrPtrs &q, int nb,
                    int ngrid_t, cudaStream_t st) {
+  (void)ngrid_t;
+  const int nchunks = (int)((P + kChunk - 1) / kChunk);
   k_sr_vprep<<<nb, kSrBlock, 0, st>>>(P, v, q.mean, q.vf, q.part, q.part2, q.sc);
   k_sr_cfin<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
-  k_sr_t<<<ngrid_t, kSrBlock, 0, st>>>(O, Ns, P, q.vf, q.t, q.sc);
+  k_sr_tpart<<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.vf, q.tpart, q.sc);
+  k_sr_tred<<<(unsigned)((Ns + 255) / 256), 256, 0, st>>>(q.tpart, nchunks, Ns, q.t, q.sc);
   k_sr_tsum<<<1, 1024, 0, st>>>(q.t, Ns, q.sc);
   k_sr_w<<<nb, kSrBlock, 0, st>>>(O, Ns, P, q.mean, q.t, v, shift, q.Ap, q.part, q.sc);
 }
@@ -345,11 +360,12 @@ static void matvec(const float2 *O, size_t Ns, size_t P, const double *v, double
 }  // namespace tdo
 
 size_t sr_work_doubles(size_t Ns, size_t P) {
-  // mean 2P, diag r z p Ap 5P, partials 3x1024, scalars 32, vf P floats, t 2Ns floats
-  return 2 * P + 5 * P + 3 * 1024 + 32 + ((P + 3) / 4 * 4) / 2 + Ns + 16;
+  // the regions carved by sr_carve, each rounded up to 16 bytes, plus slack
+  const size_t nchunks = (P + tdo::kChunk - 1) / tdo::kChunk;
+  const size_t bytes = 16 * P + 5 * (8 * P + 16) + 3 * 8 * 1024 + 8 * 32 + (4 * P + 16) + (8 * Ns + 16) +
+                       16 * nchunks * Ns + 64;
+  return (bytes + 7) / 8;
 }
-
-int sr_launches_per_iter() { return 9; }
 
 cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, const double *x0, double shift,
                        double tol, int max_iter, double *x, double *work, int n_sm, int *iters, double *resid,
@@ -360,14 +376,13 @@ cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, c
   int nb = (int)((P + kSrBlock - 1) / kSrBlock);
   if (nb > 1024) nb = 1024;
   if (nb < 1) nb = 1;
-  const size_t groups = (Ns + kGroup - 1) / kGroup;
-  const int ngrid_t = (int)(groups < (size_t)(16 * n_sm) ? groups : (size_t)(16 * n_sm));
+  const int ngrid_t = n_sm;
   long long nl = 0;
   k_sr_mean<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, q.mean);
   k_sr_diag<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, q.mean, shift, q.diag);
   k_sr_clear<<<1, 32, 0, st>>>(q.sc);
   nl += 3;
-  if (x0) { matvec(O2, Ns, P, x0, shift, q, nb, ngrid_t > 0 ? ngrid_t : 1, st); nl += 5; }
+  if (x0) { matvec(O2, Ns, P, x0, shift, q, nb, ngrid_t > 0 ? ngrid_t : 1, st); nl += 6; }
   k_sr_init<<<nb, kSrBlock, 0, st>>>(P, rhs, x0, q.Ap, x, q.r, q.z, q.p, q.diag, q.part, q.part2, q.part3);
   k_sr_init_scalars<<<1, 1024, 0, st>>>(q.part, q.part2, q.part3, nb, tol, q.sc);
   nl += 2;
@@ -386,7 +401,7 @@ cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, c
       k_sr_xr<<<nb, kSrBlock, 0, st>>>(P, x, q.r, q.z, q.p, q.Ap, q.diag, q.part, q.part2, q.sc);
       k_sr_beta<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
       k_sr_p<<<nb, kSrBlock, 0, st>>>(P, q.p, q.z, q.sc);
-      nl += 9;
+      nl += 10;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

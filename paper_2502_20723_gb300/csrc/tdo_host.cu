@@ -664,14 +664,15 @@ static tdo_status vjp_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, si
                           double *grad, int accumulate) {
   if (c->model.embed != TDO_EMBED_TOKEN) return fail(c, TDO_EUNSUPPORTED, "gradients of the conv embedding are not built");
   const int grid = bwd32_grid(c->dm, B, 0, c->n_sm);
-  const size_t stride = (c->P + 3) / 4 * 4;   // one 16-byte aligned accumulator per CTA
-  CU(c, c->gacc.ensure(sizeof(float) * grid * stride));
+  const int copies = grid < 16 ? grid : 16;   // 16 accumulator copies: L2-resident, low contention
+  const size_t stride = (c->P + 3) / 4 * 4;   // 16-byte aligned copies (float4 atomics)
+  CU(c, c->gacc.ensure(sizeof(float) * copies * stride));
   CU(c, c->scratch.ensure(sizeof(float) * bwd32_scratch_floats(c->dm, grid)));
-  CU(c, cudaMemsetAsync(c->gacc.p, 0, sizeof(float) * grid * stride, c->stream));
+  CU(c, cudaMemsetAsync(c->gacc.p, 0, sizeof(float) * copies * stride, c->stream));
   Timed tm(c, G_BWD_VJP);
-  CU(c, launch_bwd32_impl(c->dm, 0, ds, dp, B, cot, c->gacc.as<float>(), grid, stride, nullptr, c->P,
+  CU(c, launch_bwd32_impl(c->dm, 0, ds, dp, B, cot, c->gacc.as<float>(), copies, stride, nullptr, c->P,
                           c->flat_offsets, c->scratch.as<float>(), grid, c->stream));
-  CU(c, launch_reduce_copies(c->gacc.as<float>(), grid, stride, c->P, grad, accumulate, c->stream));
+  CU(c, launch_reduce_copies(c->gacc.as<float>(), copies, stride, c->P, grad, accumulate, c->stream));
   tm.done(2);
   return TDO_OK;
 }

@@ -195,8 +195,11 @@ def test_jacobian(n, d, h, L, r, B):
     assert np.abs(got - ref).max() <= 2e-5 * scale, np.abs(got - ref).max()
 
 
-@pytest.mark.parametrize("n,d,h,L,r,B", [(8, 32, 4, 2, 0, 500), (16, 64, 8, 4, 4, 40)])
+@pytest.mark.parametrize("n,d,h,L,r,B", [(8, 32, 4, 2, 0, 500), (16, 64, 8, 4, 4, 40),
+                                         (6, 16, 2, 1, 0, 300), (13, 64, 8, 2, 2, 50), (5, 32, 4, 1, 4, 77)])
 def test_vjp_random_cotangents(n, d, h, L, r, B):
+    """Includes ragged tiles (N not dividing the 64/128-row tile): padding rows must not leak into the
+    weight-gradient sums."""
     spec = synth.model_spec(d, h, L, r)
     th = synth.init_params(spec, seed=9, std=0.2 if d < 64 else 0.04)
     sig, sigp = synth.random_configs(n, B, seed=4)
