@@ -123,82 +123,86 @@ def run_ours(args) -> dict | None:
     spec = synth.model_spec(D, HEADS, LAYERS, MLP)
     theta = synth.init_params(spec, seed=0)
     stream = torch.cuda.current_stream()
-    ctx = tdo.Context(prob, spec, theta, args.precision, stream=stream.cuda_stream)
-    s0, s1 = synth.random_configs(N_SITES, N_SAMPLES, seed=1000 + rank)
-    sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
-    sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
-    seed = 12345 + rank
-    counter = 0
-    ctx.sample(sig, sigp, args.burn_in, seed, counter)     # burn-in (untimed)
-    counter += args.burn_in * 2 * N_SITES
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
-    def step():
-        nonlocal counter
-        ctx.sample(sig, sigp, 1, seed, counter)
-        counter += 2 * N_SITES
-        return ctx.sr_step(sig, sigp, LR, SHIFT)
+    def measure(precision: str, steps: int, warmup: int, e2e: bool):
+        ctx = tdo.Context(prob, spec, theta, precision, stream=stream.cuda_stream)
+        s0, s1 = synth.random_configs(N_SITES, N_SAMPLES, seed=1000 + rank)
+        sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
+        sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
+        seed = 12345 + rank
+        counter = [0]
+        ctx.sample(sig, sigp, args.burn_in, seed, counter[0])     # burn-in (untimed)
+        counter[0] += args.burn_in * 2 * N_SITES
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
+        def step():
+            ctx.sample(sig, sigp, 1, seed, counter[0])
+            counter[0] += 2 * N_SITES
+            return ctx.sr_step(sig, sigp, LR, SHIFT)
 
-    # ---- timed region: K steps, per-step CUDA events on the launching stream, L2 flushed between steps
-    ctx.timing(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    costs = []
-    sr_iters = []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            costs.append(step())
-            ev[i][1].record(stream)
-            sr_iters.append(ctx.sr_info()[0])
+        for _ in range(warmup):
+            step()
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_ms = sum(step_ms)
-    groups = {}
-    for g in ("fwd", "sample", "bwd_vjp", "bwd_jac", "conn", "lloc", "sr", "update"):
-        ms, n = ctx.timing_read(g)
-        groups[g] = {"ms": ms / args.steps, "launches": n / args.steps}
-    launches = int(sum(v["launches"] for v in groups.values()) * args.steps)
-    ctx.timing(False)
+        # timed region: per-step CUDA events on the launching stream, L2 flushed between steps
+        ctx.timing(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        costs, sr_iters = [], []
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for i in range(steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                costs.append(step())
+                ev[i][1].record(stream)
+                sr_iters.append(ctx.sr_info()[0])
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t_ms = sum(a.elapsed_time(b) for a, b in ev)
+        groups = {}
+        for g in ("fwd", "sample", "bwd_vjp", "bwd_jac", "conn", "lloc", "sr", "update"):
+            ms, n = ctx.timing_read(g)
+            groups[g] = {"ms": ms / steps, "launches": n / steps}
+        launches = int(sum(v["launches"] for v in groups.values()) * steps)
+        ctx.timing(False)
+        lloc_rows = int(ctx.connections(sig, sigp)[0].sum().item())
+        t_max = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        out = {"t_ms": float(t_max.item()), "groups": groups, "launches": launches, "lloc_rows": lloc_rows,
+               "costs": costs, "sr_iters": sr_iters, "clocks": clk.summary(), "P": ctx.P}
+        if e2e:
+            # end to end through the public API with host buffers (copies inside the timed region)
+            hs = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
+            hp = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
+            hs.copy_(sig.cpu())
+            hp.copy_(sigp.cpu())
+            hs_np, hp_np = hs.numpy(), hp.numpy()
+            torch.cuda.synchronize()
+            n_e2e = max(1, min(steps, 5))
+            t0 = time.perf_counter()
+            for _ in range(n_e2e):
+                ctx.sample(hs_np, hp_np, 1, seed, counter[0])          # H2D chains, D2H chains
+                counter[0] += 2 * N_SITES
+                ctx.sr_step(hs_np, hp_np, LR, SHIFT)                   # H2D samples, D2H cost
+            torch.cuda.synchronize()
+            e2e_t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+            if world > 1:
+                dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+            out["e2e_steps_per_s"] = world * n_e2e / float(e2e_t.item())
+        ctx.close()
+        return out
 
-    # rows evaluated by the forward per step (from one L_loc call on the current samples)
-    lloc_rows = int(ctx.connections(sig, sigp)[0].sum().item())
+    main = measure(args.precision, args.steps, args.warmup, True)
+    other = None
+    if not args.no_compare:
+        other = measure("fp32" if args.precision == "bf16" else "bf16", max(2, min(args.steps, 3)), 3, False)
+    t_max, groups, launches, lloc_rows = main["t_ms"], main["groups"], main["launches"], main["lloc_rows"]
     fwd_evals = lloc_rows
     sample_evals = N_SAMPLES * (1 + 2 * N_SITES)
-
-    t_max = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    t_max = float(t_max.item())
-
-    # ---- end to end through the public API with host buffers (copies inside the timed region)
-    hs = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
-    hp = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
-    hs.copy_(sig.cpu())
-    hp.copy_(sigp.cpu())
-    hs_np, hp_np = hs.numpy(), hp.numpy()
-    torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.sample(hs_np, hp_np, 1, seed, counter)          # H2D chains, D2H chains
-        counter += 2 * N_SITES
-        ctx.sr_step(hs_np, hp_np, LR, SHIFT)                # H2D samples, D2H cost
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_s = float(e2e_t.item())
+    clk_summary = main["clocks"]
 
     if world > 1:
         dist.destroy_process_group()
@@ -208,24 +212,33 @@ def run_ours(args) -> dict | None:
     # ---- roofline of the dominant kernel group
     peaks = measured_peaks()
     dom = max(groups, key=lambda g: groups[g]["ms"])
-    clocks = clk.summary()
+    clocks = clk_summary
+    P = main["P"]
     if dom in ("fwd", "sample", "bwd_vjp", "bwd_jac"):
         units = {"fwd": fwd_evals, "sample": sample_evals, "bwd_vjp": lloc_rows, "bwd_jac": N_SAMPLES}[dom]
         per_unit = {"fwd": F_EVAL, "sample": F_EVAL, "bwd_vjp": 2 * F_EVAL, "bwd_jac": 4 * F_EVAL}[dom]
         flops = units * per_unit
         achieved = flops / (groups[dom]["ms"] * 1e-3) / 1e12
-        if args.precision == "bf16" and dom in ("fwd", "sample"):
+        tensor = args.precision == "bf16" and dom in ("fwd", "sample", "bwd_vjp")
+        if tensor:
             peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-            roof = {"bound": "tensor", "peak_source": "MEASURED_PEAKS bf16_tflops_sustained"}
+            roof = {"bound": "tensor", "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
         else:
             peak = fp32_alu_peak_tflops()
-            roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-        roof.update({"kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "algorithmic_per_launch": flops / max(1, groups[dom]["launches"])})
+            roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
+        roof.update({"kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "algorithmic_per_launch": flops / max(1, groups[dom]["launches"])})
     else:
-        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": float(peaks.get("hbm_gbs", 6781.4)),
-                "unit": "GB/s", "frac": None, "traffic": None}
-    sr_bytes = None
+        # SR: each CG iteration streams O (Ns x P complex FP32) twice; the group's time includes its small
+        # vector kernels, so this is a lower bound on the streaming kernels' bandwidth
+        it = statistics.mean(main["sr_iters"]) if main["sr_iters"] else 0
+        byts = (2 * it + 2 + 2) * N_SAMPLES * P * 8
+        achieved = byts / (groups[dom]["ms"] * 1e-3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6781.4))
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)",
+                "algorithmic_per_launch": byts / max(1, groups[dom]["launches"])}
+    fwd_tflops = fwd_evals * F_EVAL / (groups["fwd"]["ms"] * 1e-3) / 1e12 if groups["fwd"]["ms"] else None
     res = {
         "metric": METRIC,
         "value": world * args.steps / (t_max * 1e-3),
@@ -240,21 +253,30 @@ def run_ours(args) -> dict | None:
         "dtype": "f32" if args.precision == "fp32" else "bf16",
         "data": "synthetic (seeded random initial chains, Metropolis-sampled; random-init N(0,0.02) weights)",
         "config": {"workload": WORKLOAD, "n_sites": N_SITES, "d_model": D, "heads": HEADS, "layers": LAYERS,
-                   "mlp_ratio": MLP, "samples_per_gpu": N_SAMPLES, "params": ctx.P, "precision": args.precision,
+                   "mlp_ratio": MLP, "samples_per_gpu": N_SAMPLES, "params": P, "precision": args.precision,
                    "sweeps_per_step": 1, "l2": "256 MB buffer written between timed steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "logrho_evals_per_s": (fwd_evals + sample_evals) * world * args.steps / (t_max * 1e-3),
         "logrho_evals_per_s_fwd_kernel": fwd_evals / (groups["fwd"]["ms"] * 1e-3) if groups["fwd"]["ms"] else None,
         "rows_per_step": {"lloc_rows": lloc_rows, "sample_evals": sample_evals},
         "breakdown_ms_per_step": {g: round(v["ms"], 3) for g, v in groups.items()},
-        "cost_last": costs[-1],
-        "sr_cg_iterations": sr_iters,
+        "cost_last": main["costs"][-1],
+        "sr_cg_iterations": main["sr_iters"],
+        "fwd_kernel_tflops": fwd_tflops,
         "roofline": roof,
         "clocks": clocks,
-        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "VMC steps/s",
+        "e2e": {"value": main["e2e_steps_per_s"], "unit": "VMC steps/s",
                 "h2d_bytes_per_step": 4 * 4 * N_SAMPLES, "d2h_bytes_per_step": 2 * 4 * N_SAMPLES + 8},
         "gpu_launches": launches,
     }
+    if other is not None:
+        og = other["groups"]
+        res["compare"] = {"precision": "fp32" if args.precision == "bf16" else "bf16",
+                          "value": world * len(other["costs"]) / (other["t_ms"] * 1e-3), "unit": "VMC steps/s",
+                          "ms_per_step": other["t_ms"] / len(other["costs"]),
+                          "logrho_evals_per_s_fwd_kernel": fwd_evals / (og["fwd"]["ms"] * 1e-3) if og["fwd"]["ms"] else None,
+                          "breakdown_ms_per_step": {g: round(v["ms"], 3) for g, v in og.items()},
+                          "cost_last": other["costs"][-1]}
     if world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     return res
@@ -379,7 +401,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the other-precision comparison run")
     ap.add_argument("--burn-in", type=int, default=4)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")

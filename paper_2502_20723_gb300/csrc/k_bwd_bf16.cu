@@ -1,0 +1,884 @@
+// Tensor-core (tcgen05, BF16) backward of the ansatz: the cost gradient as one vector-Jacobian product
+// over every connected row (derivative of Eq. lossnetk through Eq. log_sum_exp_conjugate, the head,
+// the mean pooling and every layer of the architecture appendix).
+//
+// The forward (k_fwd_bf16 with stores) parks, per tile of 128 token rows, the BF16 image of each layer's
+// input and of each MLP input (canonical K-major [128][D] layout), the pooled vectors and the head
+// outputs.  The backward then runs sub-layer by sub-layer over all tiles, so that the weight
+// gradients of one sub-layer stay in tensor memory for all the tiles a CTA processes and leave it once
+// per CTA (float atomics into 16 accumulator copies), instead of once per tile:
+//   head:      k_head_bwd (dF, dWh, dbh), k_head_dx (dX at the last layer output, FP32 per row)
+//   per layer: k_bwd_mlp  x2 (one pass per 128-wide half of the hidden layer):
+//                U = Xmid W1, dG = dX W2^T (MMA), dU = dG gelu'(U) (CUDA cores),
+//                dX' = dX + dU W1^T, dW1^T += dU^T Xmid, dW2 += G^T dX (MMA, MN-major operands)
+//              k_bwd_attn1: QKV = X Wqkv, dH = dX' Wo^T (MMA); softmax attention forward and backward
+//                per (sequence, head) on the CUDA cores -> dQ, dK, dV (BF16 images); dWo += H^T dX'
+//              k_bwd_attn2: dWqkv += X^T [dQ dK dV], dX = dX' + [dQ dK dV] Wqkv^T (MMA); embedding
+//                gradient at the first layer
+// Weight-gradient MMAs read the row-major activation images as MN-major operands: M or N = the
+// image's feature dimension, K = the 128 rows of the tile.
+#include <cuda_bf16.h>
+
+#include "tcgen05.cuh"
+#include "tdo_device.cuh"
+
+namespace tdo {
+namespace bwdtc {
+
+using namespace tdo::tc;
+
+constexpr int kThreads = 256;
+constexpr int kRows = 128;
+constexpr int kCopiesMax = 16;
+
+// Descriptors. K-major image [rows][K]: LBO 128 B (next 8 k), SBO 16K B (next 8 rows), 256 B per 16 k.
+// The same image read MN-major (the stored K is the MMA's M or N, the rows are the MMA's K):
+// 8-element MN groups 128 B apart, 8-row K groups 16K B apart, 32K B per 16 rows.
+__device__ __forceinline__ uint64_t dk(uint32_t addr, int K) { return sdesc(addr, 128, K * 16); }
+__device__ __forceinline__ uint64_t dmn(uint32_t addr, int Kimg) { return sdesc(addr, Kimg * 16, 128); }
+
+struct Sync {
+  uint32_t bar_mma, bar_ld;
+  uint32_t ph_mma, ph_ld;
+  uint32_t tmem;
+  bool bad;
+  int *err;
+};
+
+__device__ __forceinline__ bool sync_ok(Sync &s, bool ok) {
+  const int any = __syncthreads_or(ok ? 0 : 1);
+  if (any) s.bad = true;
+  return any == 0;
+}
+__device__ __forceinline__ bool wait_mma(Sync &s) {
+  const bool ok = mbar_wait(s.bar_mma, s.ph_mma);
+  s.ph_mma ^= 1u;
+  tc_fence_after();
+  return ok;
+}
+__device__ __forceinline__ bool wait_ld(Sync &s) {
+  const bool ok = mbar_wait(s.bar_ld, s.ph_ld);
+  s.ph_ld ^= 1u;
+  return ok;
+}
+
+// K-major x K-major: D[tmem + col] (+)= A[128 x K] B[N x K]^T
+__device__ __forceinline__ void mma_kk(const Sync &s, uint32_t a, uint32_t b, int K, int N, uint32_t col, bool acc) {
+  const uint32_t id = idesc_bf16(kRows, N);
+  for (int kk = 0; kk < K / 16; ++kk)
+    mma_bf16(s.tmem + col, dk(a + kk * 256, K), dk(b + kk * 256, K), id, (acc || kk > 0) ? 1u : 0u);
+}
+// MN-major x MN-major over the 128 rows: D[tmem + col][M = Ka][N = Kb] (+)= A_img^T B_img
+__device__ __forceinline__ void mma_mm(const Sync &s, uint32_t a, int Ka, uint32_t b, int Kb, int N, uint32_t col,
+                                       bool acc) {
+  const uint32_t id = idesc_bf16_major(kRows, N, 1, 1);
+  for (int kk = 0; kk < kRows / 16; ++kk)
+    mma_bf16(s.tmem + col, dmn(a + kk * Ka * 32, Ka), dmn(b + kk * Kb * 32, Kb), id, (acc || kk > 0) ? 1u : 0u);
+}
+
+__device__ __forceinline__ void sync_init(Sync &s, uint8_t *misc, int *err) {
+  s.bar_mma = smem_u32(misc);
+  s.bar_ld = smem_u32(misc + 8);
+  s.ph_mma = s.ph_ld = 0;
+  s.bad = false;
+  s.err = err;
+  if (threadIdx.x == 0) {
+    mbar_init(s.bar_mma, 1);
+    mbar_init(s.bar_ld, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(misc + 16)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  s.tmem = *reinterpret_cast<volatile uint32_t *>(misc + 16);
+}
+
+__device__ __forceinline__ void sync_finish(Sync &s) {
+  if (s.bad) {
+    if (threadIdx.x == 0) atomicExch(s.err, 1);
+    mbar_wait(s.bar_mma, s.ph_mma);
+    mbar_wait(s.bar_ld, s.ph_ld);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem), "r"(512));
+  }
+}
+
+// Thread 0 starts bulk copies (sizes multiples of 16) completing on bar_ld.
+__device__ __forceinline__ void load2(Sync &s, uint32_t d0, const void *s0, uint32_t n0, uint32_t d1, const void *s1,
+                                      uint32_t n1) {
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(s.bar_ld, n0 + n1);
+    bulk_g2s(d0, s0, n0, s.bar_ld);
+    if (n1) bulk_g2s(d1, s1, n1, s.bar_ld);
+  }
+}
+
+__device__ __forceinline__ float gelu_grad_fast(float u, float *g) {
+  const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(k0 * fmaf(k1 * u, u * u, u)));
+  *g = 0.5f * u * (1.0f + t);
+  return 0.5f * (1.0f + t) + 0.5f * u * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * u * u);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Flush a TMEM accumulator block [128 lanes][N cols] (this thread: lane m, its half of the columns) to
+// the gradient accumulator with index(m, n) (negative = skip).
+template <typename IDX>
+__device__ __forceinline__ void flush_block(const Sync &s, uint32_t col, int N, float *g, IDX idx) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = 32 * (warp & 3) + lane, half = warp >> 2;
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  for (int j = 0; j < N / 2; j += 16) {
+    float v[16];
+    tmem_ld16(s.tmem + lane_addr + col + half * (N / 2) + j, v);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const long long k = idx(m, half * (N / 2) + j + e);
+      if (k >= 0) atomicAdd(g + k, v[e]);
+    }
+  }
+}
+
+// ====================================================================================== head
+struct HeadArgs {
+  const float2 *cot;   // [B] cotangents of log rho
+  const float *F;      // [B][4] head outputs (F0, F1 of both orders)
+  const float *H;      // [2B][D] pooled vectors
+  const float *Wh;     // [D][2]
+  float *dF;           // [Bpad][4]
+  size_t B, Bpad;
+  float *g;            // gradient accumulator copies
+  size_t g_stride;
+  long long off_wh, off_bh;
+  int D;
+};
+
+__global__ void k_head_bwd(HeadArgs a) {
+  extern __shared__ float acc[];   // [2D + 2]
+  const int nacc = 2 * a.D + 2;
+  for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[i] = 0.f;
+  __syncthreads();
+  for (size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x; b < a.Bpad; b += gridDim.x * (size_t)blockDim.x) {
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+    if (b < a.B) {
+      float2 pw, pv;
+      symmetrise(a.F[4 * b], a.F[4 * b + 1], a.F[4 * b + 2], a.F[4 * b + 3], &pw, &pv);
+      const float2 c = a.cot[b];
+      const float cwr = c.x * pw.x - c.y * pw.y, cwi = c.x * pw.y + c.y * pw.x;
+      const float cvr = c.x * pv.x - c.y * pv.y, cvi = c.x * pv.y + c.y * pv.x;
+      d0 = cwr; d1 = -cwi; d2 = cvr; d3 = cvi;
+      const float *hA = a.H + (2 * b) * a.D, *hB = hA + a.D;
+      for (int k = 0; k < a.D; ++k) {
+        atomicAdd(&acc[2 * k], hA[k] * d0 + hB[k] * d2);
+        atomicAdd(&acc[2 * k + 1], hA[k] * d1 + hB[k] * d3);
+      }
+      atomicAdd(&acc[2 * a.D], d0 + d2);
+      atomicAdd(&acc[2 * a.D + 1], d1 + d3);
+    }
+    reinterpret_cast<float4 *>(a.dF)[b] = make_float4(d0, d1, d2, d3);
+  }
+  __syncthreads();
+  float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
+  for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
+    const long long k = i < 2 * a.D ? a.off_wh + i : a.off_bh + (i - 2 * a.D);
+    atomicAdd(g + k, acc[i]);
+  }
+}
+
+// dX at the last layer output: (1/N) sum_o Wh[c][o] dF[seq(r)][o] for valid rows, 0 for padding.
+__global__ void k_head_dx(const float *__restrict__ dF, const float *__restrict__ Wh, int D, int n, int ts,
+                          size_t tiles, float *__restrict__ dX) {
+  const int tc = ts / 2;
+  const size_t total = tiles * kRows * (size_t)D;
+  const float inv_n = 1.0f / (float)n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += gridDim.x * (size_t)blockDim.x) {
+    const size_t rowg = i / D;
+    const int c = (int)(i % D);
+    const size_t tile = rowg / kRows;
+    const int r = (int)(rowg % kRows);
+    float v = 0.f;
+    if (r < ts * n) {
+      const int s = r / n;
+      const size_t b = tile * tc + (s >> 1);
+      const float f0 = dF[4 * b + 2 * (s & 1)], f1 = dF[4 * b + 2 * (s & 1) + 1];
+      v = (Wh[2 * c] * f0 + Wh[2 * c + 1] * f1) * inv_n;
+    }
+    dX[i] = v;
+  }
+}
+
+// ====================================================================================== MLP pass
+template <int D>
+struct MlpGeo {
+  static constexpr int HC = 128;
+  static constexpr int IMG = kRows * D * 2;            // [128][D] BF16 image
+  static constexpr int W1T_OFF = 0;                    // [HC][D]  (U = Xmid W1_c)
+  static constexpr int W2_OFF = W1T_OFF + HC * D * 2;  // [HC][D]  (dG = dX W2_c^T)
+  static constexpr int W1_OFF = W2_OFF + HC * D * 2;   // [D][HC]  (dX' = dU W1_c^T)
+  static constexpr int X_OFF = W1_OFF + HC * D * 2;    // Xmid image [128][D]
+  static constexpr int DX_OFF = X_OFF + IMG;           // dX (BF16) [128][D]
+  static constexpr int G_OFF = DX_OFF + IMG;           // G  [128][HC]
+  static constexpr int DU_OFF = G_OFF + kRows * HC * 2;  // dU [128][HC]
+  static constexpr int M_OFF = DU_OFF + kRows * HC * 2;  // misc: bars, holder, db1[HC], db2[D]
+  static constexpr int BYTES = M_OFF + 64 + 4 * HC + 4 * D;
+  // TMEM columns
+  static constexpr int C_U = 0, C_DG = 128, C_DX = 256, C_W1 = 320, C_W2 = 384;
+};
+
+struct MlpArgs {
+  const uint8_t *w1t, *w2, *w1;   // packed images of this half: W1^T [HC][D], W2 rows [HC][D], W1 rows [D][HC]
+  const float *b1;                // b1 of this half
+  const uint8_t *xmid;            // [tiles] images
+  const float *dxo, *base;        // FP32 [tiles*128][D]
+  float *dxm;                     // FP32 out
+  size_t tiles;
+  int do_db2;
+  float *g;
+  size_t g_stride;
+  long long off_w1, off_b1, off_w2, off_b2;   // flat offsets (off_w1 / off_b1 / off_w2 already at this half)
+  int F;
+  int *err;
+};
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 1) k_bwd_mlp(MlpArgs a) {
+  using G = MlpGeo<D>;
+  extern __shared__ __align__(1024) uint8_t sm[];
+  constexpr int HALF = D / 2, HH = G::HC / 2;
+  Sync s;
+  sync_init(s, sm + G::M_OFF, a.err);
+  float *db1 = reinterpret_cast<float *>(sm + G::M_OFF + 64);
+  float *db2 = db1 + G::HC;
+  for (int i = threadIdx.x; i < G::HC + D; i += kThreads) db1[i] = 0.f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  const uint32_t w1t = smem_u32(sm + G::W1T_OFF), w2 = smem_u32(sm + G::W2_OFF), w1 = smem_u32(sm + G::W1_OFF);
+  const uint32_t xs = smem_u32(sm + G::X_OFF), dxs = smem_u32(sm + G::DX_OFF), gs = smem_u32(sm + G::G_OFF),
+                 dus = smem_u32(sm + G::DU_OFF);
+  // weights once per kernel
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(s.bar_ld, 3 * G::HC * D * 2);
+    bulk_g2s(w1t, a.w1t, G::HC * D * 2, s.bar_ld);
+    bulk_g2s(w2, a.w2, G::HC * D * 2, s.bar_ld);
+    bulk_g2s(w1, a.w1, G::HC * D * 2, s.bar_ld);
+  }
+  bool ok = wait_ld(s);
+  bool first = true;
+  if (sync_ok(s, ok)) {
+    for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
+      load2(s, xs, a.xmid + tile * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+      const size_t rg = (tile * kRows + row) * (size_t)D + half * HALF;
+      float dxo[HALF], base[HALF];
+#pragma unroll
+      for (int j = 0; j < HALF; j += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(a.dxo + rg + j);
+        dxo[j] = v.x; dxo[j + 1] = v.y; dxo[j + 2] = v.z; dxo[j + 3] = v.w;
+        const float4 q = *reinterpret_cast<const float4 *>(a.base + rg + j);
+        base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
+      }
+#pragma unroll
+      for (int j = 0; j < HALF; j += 8) st_row8(sm + G::DX_OFF, row, half * HALF + j, D, dxo + j);
+      if (a.do_db2) {
+#pragma unroll
+        for (int j = 0; j < HALF; ++j) {
+          const float t = warp_sum_f(dxo[j]);
+          if (lane == 0) atomicAdd(&db2[half * HALF + j], t);
+        }
+      }
+      ok = wait_ld(s);
+      fence_proxy_async();
+      if (!sync_ok(s, ok)) break;
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        mma_kk(s, xs, w1t, D, G::HC, G::C_U, false);    // U  = Xmid W1_c
+        mma_kk(s, dxs, w2, D, G::HC, G::C_DG, false);   // dG = dX W2_c^T
+        mma_commit(s.bar_mma);
+      }
+      ok = wait_mma(s);
+      if (!sync_ok(s, ok)) break;
+      // dU = dG gelu'(U + b1), G = gelu(U + b1) -> shared images; db1 column sums
+#pragma unroll
+      for (int j = 0; j < HH; j += 16) {
+        float u[16], dg[16], gl[16], du[16];
+        tmem_ld16(s.tmem + lane_addr + G::C_U + half * HH + j, u);
+        tmem_ld16(s.tmem + lane_addr + G::C_DG + half * HH + j, dg);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const float uu = u[e] + __ldg(a.b1 + half * HH + j + e);
+          du[e] = dg[e] * gelu_grad_fast(uu, &gl[e]);
+        }
+        st_row8(sm + G::G_OFF, row, half * HH + j, G::HC, gl);
+        st_row8(sm + G::G_OFF, row, half * HH + j + 8, G::HC, gl + 8);
+        st_row8(sm + G::DU_OFF, row, half * HH + j, G::HC, du);
+        st_row8(sm + G::DU_OFF, row, half * HH + j + 8, G::HC, du + 8);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const float t = warp_sum_f(du[e]);
+          if (lane == 0) atomicAdd(&db1[half * HH + j + e], t);
+        }
+      }
+      tc_fence_before();
+      fence_proxy_async();
+      if (!sync_ok(s, true)) break;
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        mma_kk(s, dus, w1, G::HC, D, G::C_DX, false);              // dX' part = dU W1_c^T
+        mma_mm(s, dus, G::HC, xs, D, D, G::C_W1, !first);          // dW1_c^T += dU^T Xmid
+        mma_mm(s, gs, G::HC, dxs, D, D, G::C_W2, !first);          // dW2_c   += G^T dX
+        mma_commit(s.bar_mma);
+      }
+      ok = wait_mma(s);
+      if (!sync_ok(s, ok)) break;
+#pragma unroll
+      for (int j = 0; j < HALF; j += 16) {
+        float v[16];
+        tmem_ld16(s.tmem + lane_addr + G::C_DX + half * HALF + j, v);
+#pragma unroll
+        for (int e = 0; e < 16; e += 4)
+          *reinterpret_cast<float4 *>(a.dxm + rg + j + e) =
+              make_float4(base[j + e] + v[e], base[j + e + 1] + v[e + 1], base[j + e + 2] + v[e + 2],
+                          base[j + e + 3] + v[e + 3]);
+      }
+      first = false;
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  if (!s.bad && !first) {
+    float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
+    const int F = a.F;
+    // dW1_c^T block: lane m = hidden unit (of this half), column n = input feature i
+    flush_block(s, G::C_W1, D, g, [&](int m, int n) -> long long { return a.off_w1 + (long long)n * F + m; });
+    flush_block(s, G::C_W2, D, g, [&](int m, int n) -> long long { return a.off_w2 + (long long)m * D + n; });
+    __syncthreads();
+    for (int i = threadIdx.x; i < G::HC; i += kThreads) atomicAdd(g + a.off_b1 + i, db1[i]);
+    if (a.do_db2)
+      for (int i = threadIdx.x; i < D; i += kThreads) atomicAdd(g + a.off_b2 + i, db2[i]);
+  }
+  sync_finish(s);
+}
+
+// ====================================================================================== attention pass 1
+template <int D>
+struct A1Geo {
+  static constexpr int KS = D + 1;
+  static constexpr int IMG = kRows * D * 2;
+  static constexpr int W_OFF = 0;                      // Wqkv^T [3D][D], later Wo rows [D][D], then stats
+  static constexpr int W_BYTES = 3 * D * D * 2;
+  static constexpr int X_OFF = W_OFF + W_BYTES;        // X image
+  static constexpr int DX_OFF = X_OFF + IMG;           // dX' BF16 image
+  static constexpr int H_OFF = DX_OFF + IMG;           // head outputs [128][128] BF16 (upper half zero)
+  static constexpr int F_OFF = H_OFF + kRows * 128 * 2;   // Q, K, V, dH FP32 [128][KS] each
+  static constexpr int M_OFF = F_OFF + 4 * kRows * KS * 4;
+  static constexpr int BYTES = M_OFF + 64;
+  static constexpr int C_QKV = 0, C_DH = 3 * D, C_WO = 256;
+  static_assert(3 * kRows * 8 * 4 <= W_BYTES, "stats fit the weight region");
+};
+
+struct A1Args {
+  const uint8_t *wqkvT, *wo;      // packed: Wqkv^T [3D][D] (forward image), Wo rows [D][D]
+  const uint8_t *x;               // [tiles] layer-input images
+  const float *dxm;               // FP32 [tiles*128][D]
+  uint8_t *dqkv;                  // out [tiles] images [128][3D]
+  size_t tiles;
+  int n, ts, heads;
+  float *g;
+  size_t g_stride;
+  long long off_wo;
+  int *err;
+};
+
+template <int D, int HD>
+__global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
+  using G = A1Geo<D>;
+  extern __shared__ __align__(1024) uint8_t sm[];
+  constexpr int HALF = D / 2, KS = G::KS;
+  Sync s;
+  sync_init(s, sm + G::M_OFF, a.err);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  const uint32_t wr = smem_u32(sm + G::W_OFF), xs = smem_u32(sm + G::X_OFF), dxs = smem_u32(sm + G::DX_OFF),
+                 hs = smem_u32(sm + G::H_OFF);
+  float *Qs = reinterpret_cast<float *>(sm + G::F_OFF), *Ks = Qs + kRows * KS, *Vs = Ks + kRows * KS,
+        *dHs = Vs + kRows * KS;
+  float *st_m = reinterpret_cast<float *>(sm + G::W_OFF), *st_l = st_m + kRows * 8, *st_d = st_l + kRows * 8;
+  for (int i = threadIdx.x; i < kRows * 128 * 2 / 16; i += kThreads)
+    reinterpret_cast<uint4 *>(sm + G::H_OFF)[i] = make_uint4(0, 0, 0, 0);
+  const int n = a.n, heads = a.heads, nvalid = a.ts * n;
+  const bool valid = row < nvalid;
+  const int sq = valid ? row / n : 0;
+  const float qscale = rsqrtf((float)HD) * 1.4426950408889634f;   // scores in base 2
+  const float scale = rsqrtf((float)HD);
+  bool first = true;
+  for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
+    load2(s, xs, a.x + tile * (size_t)G::IMG, G::IMG, wr, a.wqkvT, G::W_BYTES);
+    const size_t rg = (tile * kRows + row) * (size_t)D + half * HALF;
+    {
+      float v[HALF];
+#pragma unroll
+      for (int j = 0; j < HALF; j += 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(a.dxm + rg + j);
+        v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
+      }
+#pragma unroll
+      for (int j = 0; j < HALF; j += 8) st_row8(sm + G::DX_OFF, row, half * HALF + j, D, v + j);
+    }
+    bool ok = wait_ld(s);
+    fence_proxy_async();
+    if (!sync_ok(s, ok)) break;
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      mma_kk(s, xs, wr, D, 3 * D, G::C_QKV, false);   // Q, K, V
+      mma_commit(s.bar_mma);
+    }
+    ok = wait_mma(s);
+    if (!sync_ok(s, ok)) break;
+    load2(s, wr, a.wo, D * D * 2, 0, nullptr, 0);    // W is free: the QKV MMA has completed
+#pragma unroll
+    for (int j = 0; j < HALF; j += 16) {
+      float v[16];
+      tmem_ld16(s.tmem + lane_addr + G::C_QKV + half * HALF + j, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) Qs[row * KS + half * HALF + j + e] = v[e];
+      tmem_ld16(s.tmem + lane_addr + G::C_QKV + D + half * HALF + j, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) Ks[row * KS + half * HALF + j + e] = v[e];
+      tmem_ld16(s.tmem + lane_addr + G::C_QKV + 2 * D + half * HALF + j, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) Vs[row * KS + half * HALF + j + e] = v[e];
+    }
+    ok = wait_ld(s);
+    if (!sync_ok(s, ok)) break;
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      mma_kk(s, dxs, wr, D, D, G::C_DH, false);       // dH = dX' Wo^T
+      mma_commit(s.bar_mma);
+    }
+    ok = wait_mma(s);
+    if (!sync_ok(s, ok)) break;
+#pragma unroll
+    for (int j = 0; j < HALF; j += 16) {
+      float v[16];
+      tmem_ld16(s.tmem + lane_addr + G::C_DH + half * HALF + j, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) dHs[row * KS + half * HALF + j + e] = v[e];
+    }
+    __syncthreads();   // Q, K, V, dH of every row visible; Wo no longer read (stats reuse the region)
+    uint8_t *dq_img = a.dqkv + tile * (size_t)(kRows * 3 * D * 2);
+    // ---- pass 1: this thread = query row; forward output (-> H image) and dQ
+    const int h0 = half * (heads / 2), h1 = h0 + heads / 2;
+    for (int h = h0; h < h1; ++h) {
+      float o[HD], dq[HD];
+#pragma unroll
+      for (int e = 0; e < HD; ++e) { o[e] = 0.f; dq[e] = 0.f; }
+      float mx = -INFINITY, l = 0.f, delta = 0.f;
+      if (valid) {
+        const float *qr = Qs + row * KS + h * HD, *gr = dHs + row * KS + h * HD;
+        const float *kb = Ks + sq * n * KS + h * HD, *vb = Vs + sq * n * KS + h * HD;
+        float q[HD], gg[HD];
+#pragma unroll
+        for (int e = 0; e < HD; ++e) { q[e] = qr[e] * qscale; gg[e] = gr[e]; }
+        // online softmax with dA_ij = dH_i . v_j accumulated alongside: delta = sum_j p_j dA_j / l
+        for (int j = 0; j < n; ++j) {
+          const float *kr = kb + j * KS, *vr = vb + j * KS;
+          float sc = 0.f, da = 0.f;
+#pragma unroll
+          for (int e = 0; e < HD; ++e) { sc = fmaf(q[e], kr[e], sc); da = fmaf(gg[e], vr[e], da); }
+          if (sc > mx) {
+            const float cr = ex2_fast(mx - sc);
+            l *= cr;
+            delta *= cr;
+#pragma unroll
+            for (int e = 0; e < HD; ++e) o[e] *= cr;
+            mx = sc;
+          }
+          const float p = ex2_fast(sc - mx);
+          l += p;
+          delta = fmaf(p, da, delta);
+#pragma unroll
+          for (int e = 0; e < HD; ++e) o[e] = fmaf(p, vr[e], o[e]);
+        }
+        const float inv = 1.0f / l;
+        delta *= inv;
+#pragma unroll
+        for (int e = 0; e < HD; ++e) o[e] *= inv;
+        // dQ_i = scale sum_j a_ij (dA_ij - delta_i) k_j
+        for (int j = 0; j < n; ++j) {
+          const float *kr = kb + j * KS, *vr = vb + j * KS;
+          float sc = 0.f, da = 0.f;
+#pragma unroll
+          for (int e = 0; e < HD; ++e) { sc = fmaf(q[e], kr[e], sc); da = fmaf(gg[e], vr[e], da); }
+          const float w = scale * ex2_fast(sc - mx) * inv * (da - delta);
+#pragma unroll
+          for (int e = 0; e < HD; ++e) dq[e] = fmaf(w, kr[e], dq[e]);
+        }
+      }
+      st_m[row * 8 + h] = mx;
+      st_l[row * 8 + h] = l;
+      st_d[row * 8 + h] = delta;
+#pragma unroll
+      for (int e8 = 0; e8 < HD; e8 += 8) {
+        st_row8(sm + G::H_OFF, row, h * HD + e8, 128, o + e8);
+        st_row8(dq_img, row, h * HD + e8, 3 * D, dq + e8);
+      }
+    }
+    __syncthreads();
+    // ---- pass 2: this thread = key row j; dK_j, dV_j
+    for (int h = h0; h < h1; ++h) {
+      float dk[HD], dv[HD];
+#pragma unroll
+      for (int e = 0; e < HD; ++e) { dk[e] = 0.f; dv[e] = 0.f; }
+      if (valid) {
+        float kj[HD], vj[HD];
+#pragma unroll
+        for (int e = 0; e < HD; ++e) { kj[e] = Ks[row * KS + h * HD + e]; vj[e] = Vs[row * KS + h * HD + e]; }
+        for (int i = 0; i < n; ++i) {
+          const int ri = sq * n + i;
+          const float *qr = Qs + ri * KS + h * HD, *gr = dHs + ri * KS + h * HD;
+          float sc = 0.f, da = 0.f;
+#pragma unroll
+          for (int e = 0; e < HD; ++e) { sc = fmaf(qr[e], kj[e], sc); da = fmaf(gr[e], vj[e], da); }
+          const float aij = ex2_fast(sc * qscale - st_m[ri * 8 + h]) / st_l[ri * 8 + h];
+          const float w = scale * aij * (da - st_d[ri * 8 + h]);
+#pragma unroll
+          for (int e = 0; e < HD; ++e) { dv[e] = fmaf(aij, gr[e], dv[e]); dk[e] = fmaf(w, qr[e], dk[e]); }
+        }
+      }
+#pragma unroll
+      for (int e8 = 0; e8 < HD; e8 += 8) {
+        st_row8(dq_img, row, D + h * HD + e8, 3 * D, dk + e8);
+        st_row8(dq_img, row, 2 * D + h * HD + e8, 3 * D, dv + e8);
+      }
+    }
+    fence_proxy_async();
+    if (!sync_ok(s, true)) break;
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      mma_mm(s, hs, 128, dxs, D, D, G::C_WO, !first);   // dWo += H^T dX'   (rows of H beyond D are zero)
+      mma_commit(s.bar_mma);
+    }
+    ok = wait_mma(s);
+    first = false;
+    tc_fence_before();
+    if (!sync_ok(s, ok)) break;
+  }
+  if (!s.bad && !first) {
+    float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
+    flush_block(s, G::C_WO, D, g, [&](int m, int nn) -> long long {
+      return m < D ? a.off_wo + (long long)m * D + nn : -1;
+    });
+  }
+  sync_finish(s);
+}
+
+// ====================================================================================== attention pass 2
+template <int D>
+struct A2Geo {
+  static constexpr int IMG = kRows * D * 2;
+  static constexpr int QIMG = kRows * 3 * D * 2;
+  static constexpr int W_OFF = 0;                       // Wqkv rows [D][3D]
+  static constexpr int W_BYTES = 3 * D * D * 2;
+  static constexpr int XR_OFF = W_OFF + W_BYTES;        // X image as stored [128][D]
+  static constexpr int XP_OFF = XR_OFF + IMG;           // X padded [128][128] (columns >= D zero)
+  static constexpr int DQ_OFF = XP_OFF + kRows * 128 * 2;   // [dQ dK dV] image [128][3D]
+  static constexpr int M_OFF = DQ_OFF + QIMG;           // misc: bars, holder, dE [4][D]
+  static constexpr int BYTES = M_OFF + 64 + 4 * 4 * D;
+  static constexpr int C_W = 0, C_DX = 256;
+};
+
+struct A2Args {
+  const uint8_t *wqkv;            // packed Wqkv rows [D][3D]
+  const uint8_t *x, *dqkv;        // [tiles] images
+  const float *dxm;               // FP32 [tiles*128][D] (dX')
+  float *dxo;                     // FP32 out: dX at the layer input
+  size_t tiles;
+  int n, ts, embed_grad;
+  const uint32_t *sig, *sigp;     // configurations (for the embedding gradient)
+  size_t B;
+  float *g;
+  size_t g_stride;
+  long long off_wq, off_wk, off_wv, off_e;
+  int *err;
+};
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
+  using G = A2Geo<D>;
+  extern __shared__ __align__(1024) uint8_t sm[];
+  constexpr int HALF = D / 2;
+  Sync s;
+  sync_init(s, sm + G::M_OFF, a.err);
+  float *dE = reinterpret_cast<float *>(sm + G::M_OFF + 64);
+  for (int i = threadIdx.x; i < 4 * D; i += kThreads) dE[i] = 0.f;
+  for (int i = threadIdx.x; i < kRows * 128 * 2 / 16; i += kThreads)
+    reinterpret_cast<uint4 *>(sm + G::XP_OFF)[i] = make_uint4(0, 0, 0, 0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  const uint32_t wq = smem_u32(sm + G::W_OFF), xr = smem_u32(sm + G::XR_OFF), xp = smem_u32(sm + G::XP_OFF),
+                 dq = smem_u32(sm + G::DQ_OFF);
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(s.bar_ld, G::W_BYTES);
+    bulk_g2s(wq, a.wqkv, G::W_BYTES, s.bar_ld);
+  }
+  bool ok = wait_ld(s);
+  const int n = a.n, nvalid = a.ts * n, tc = a.ts / 2;
+  bool first = true;
+  if (sync_ok(s, ok)) {
+    for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
+      load2(s, xr, a.x + tile * (size_t)G::IMG, G::IMG, dq, a.dqkv + tile * (size_t)G::QIMG, G::QIMG);
+      const size_t rg = (tile * kRows + row) * (size_t)D + half * HALF;
+      float base[HALF];
+#pragma unroll
+      for (int j = 0; j < HALF; j += 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(a.dxm + rg + j);
+        base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
+      }
+      ok = wait_ld(s);
+      if (!sync_ok(s, ok)) break;
+      // X padded to 128 columns: each 8-row group of the stored image (16D bytes) -> first half of 2048
+      for (int i = threadIdx.x; i < kRows / 8 * (D * 16 / 16); i += kThreads) {
+        const int grp = i / (D * 16 / 16), c = i % (D * 16 / 16);
+        reinterpret_cast<uint4 *>(sm + G::XP_OFF + grp * 2048)[c] =
+            reinterpret_cast<const uint4 *>(sm + G::XR_OFF + grp * D * 16)[c];
+      }
+      fence_proxy_async();
+      if (!sync_ok(s, true)) break;
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        mma_mm(s, xp, 128, dq, 3 * D, 3 * D, G::C_W, !first);   // dWqkv += X^T [dQ dK dV]
+        mma_kk(s, dq, wq, 3 * D, D, G::C_DX, false);            // [dQ dK dV] Wqkv^T
+        mma_commit(s.bar_mma);
+      }
+      ok = wait_mma(s);
+      if (!sync_ok(s, ok)) break;
+      float out[HALF];
+#pragma unroll
+      for (int j = 0; j < HALF; j += 16) {
+        float v[16];
+        tmem_ld16(s.tmem + lane_addr + G::C_DX + half * HALF + j, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) out[j + e] = base[j + e] + v[e];
+      }
+#pragma unroll
+      for (int j = 0; j < HALF; j += 4)
+        *reinterpret_cast<float4 *>(a.dxo + rg + j) = make_float4(out[j], out[j + 1], out[j + 2], out[j + 3]);
+      if (a.embed_grad && row < nvalid) {
+        const int sqn = row / n, i = row % n;
+        const size_t b = tile * tc + (sqn >> 1);
+        if (b < a.B) {
+          const uint32_t w1 = (sqn & 1) ? a.sigp[b] : a.sig[b];
+          const uint32_t w2 = (sqn & 1) ? a.sig[b] : a.sigp[b];
+          const int pat = embed_pattern(0, w1, w2, i, n);
+#pragma unroll
+          for (int j = 0; j < HALF; ++j) atomicAdd(&dE[pat * D + half * HALF + j], out[j]);
+        }
+      }
+      first = false;
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  if (!s.bad && !first) {
+    float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
+    flush_block(s, G::C_W, 3 * D, g, [&](int m, int nn) -> long long {
+      if (m >= D) return -1;
+      if (nn < D) return a.off_wq + (long long)m * D + nn;
+      if (nn < 2 * D) return a.off_wk + (long long)m * D + (nn - D);
+      return a.off_wv + (long long)m * D + (nn - 2 * D);
+    });
+    __syncthreads();
+    if (a.embed_grad)
+      for (int i = threadIdx.x; i < 4 * D; i += kThreads) atomicAdd(g + a.off_e + i, dE[i]);
+  }
+  sync_finish(s);
+}
+
+// Non-transposed BF16 packing: dst canonical [N][Ktot], element (n, koff + k) = W[n * ldw + col0 + k].
+__global__ void k_pack_nt(const float *__restrict__ W, int ldw, int col0, int K, int N, int Ktot, int koff,
+                          uint8_t *__restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * K) return;
+  const int nn = i / K, k = i % K;
+  const __nv_bfloat16 v = __float2bfloat16_rn(W[(size_t)nn * ldw + col0 + k]);
+  *reinterpret_cast<__nv_bfloat16 *>(dst + canon(nn, koff + k, Ktot)) = v;
+}
+
+}  // namespace bwdtc
+}  // namespace tdo
+
+// ------------------------------------------------------------------------------------- host side
+#include "../../include/tdo.h"
+
+struct BwdTcLayer {
+  const uint8_t *w1t[2], *w2r[2], *w1r[2];   // per hidden half
+  const uint8_t *wqkvT, *wor, *wqkvr;
+};
+
+size_t bwdtc_packed_bytes(const DevModel &m) {
+  const size_t D = m.d, F = m.ffn;
+  return (size_t)m.layers * (2 * F * D + D * D + 3 * D * D) * 2;
+}
+
+// Row-major (non-transposed) BF16 images for the backward; views per layer into dst.
+cudaError_t launch_pack_bwdtc(const DevModel &m, uint8_t *dst, BwdTcLayer *views, cudaStream_t st) {
+  using namespace tdo::bwdtc;
+  const int D = m.d, F = m.ffn;
+  size_t off = 0;
+  auto pack = [&](const float *W, int ldw, int col0, int K, int N, int Ktot, int koff, uint8_t *out) {
+    k_pack_nt<<<(N * K + 255) / 256, 256, 0, st>>>(W, ldw, col0, K, N, Ktot, koff, out);
+  };
+  for (int l = 0; l < m.layers; ++l) {
+    const DevLayer &L = m.L[l];
+    BwdTcLayer &v = views[l];
+    if (F > 0) {
+      for (int hb = 0; hb < F / 128; ++hb) {
+        v.w2r[hb] = dst + off;    // W2 rows hb*128.. : [128][D]
+        pack(L.W2 + (size_t)hb * 128 * D, D, 0, D, 128, D, 0, dst + off);
+        off += (size_t)128 * D * 2;
+        v.w1r[hb] = dst + off;    // W1 rows, columns hb*128.. : [D][128]
+        pack(L.W1, F, hb * 128, 128, D, 128, 0, dst + off);
+        off += (size_t)128 * D * 2;
+      }
+    }
+    v.wor = dst + off;
+    pack(L.Wo, D, 0, D, D, D, 0, dst + off);
+    off += (size_t)D * D * 2;
+    v.wqkvr = dst + off;
+    pack(L.Wq, D, 0, D, D, 3 * D, 0, dst + off);
+    pack(L.Wk, D, 0, D, D, 3 * D, D, dst + off);
+    pack(L.Wv, D, 0, D, D, 3 * D, 2 * D, dst + off);
+    off += (size_t)3 * D * D * 2;
+  }
+  return cudaGetLastError();
+}
+
+bool bwdtc_supported(const DevModel &m) {
+  return m.d == 64 && (m.dh == 8 || m.dh == 16) && m.heads % 2 == 0 && m.heads <= 16 &&
+         (m.ffn == 0 || m.ffn == 128 || m.ffn == 256) && m.embed == 0;
+}
+
+struct BwdTcBuffers {
+  uint8_t *x, *xmid, *dqkv;
+  float *h, *f, *dF, *dxa, *dxb;
+  size_t tiles;
+};
+
+// The whole tensor-core VJP given the forward's parked activations and the row cotangents.
+cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcLayer *views, const BwdTcBuffers &bf,
+                         const uint32_t *sig, const uint32_t *sigp, size_t B, const float2 *cot, float *gacc,
+                         size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st) {
+  using namespace tdo::bwdtc;
+  constexpr int D = 64;
+  const int n = m.n_sites, ts = tdo::seqs_per_tile(n), tc = ts / 2;
+  const size_t tiles = bf.tiles, Bpad = tiles * tc;
+  const long long *Wq = fo + 1, *Wk = Wq + TDO_MAX_LAYERS, *Wv = Wk + TDO_MAX_LAYERS, *Wo = Wv + TDO_MAX_LAYERS,
+                  *W1 = Wo + TDO_MAX_LAYERS, *b1 = W1 + TDO_MAX_LAYERS, *W2 = b1 + TDO_MAX_LAYERS,
+                  *b2 = W2 + TDO_MAX_LAYERS;
+  const long long off_e = fo[0], off_wh = fo[1 + 8 * TDO_MAX_LAYERS], off_bh = fo[2 + 8 * TDO_MAX_LAYERS];
+  cudaError_t e;
+  {
+    HeadArgs h{cot, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, gacc, g_stride, off_wh, off_bh, D};
+    const unsigned grid = (unsigned)((Bpad + 255) / 256 < 1024 ? (Bpad + 255) / 256 : 1024);
+    k_head_bwd<<<grid ? grid : 1, 256, (2 * D + 2) * sizeof(float), st>>>(h);
+    k_head_dx<<<(unsigned)(tiles * kRows * D / 256 < 65535 * 8 ? (tiles * kRows * D + 255) / 256 : 65535 * 8), 256, 0,
+                st>>>(bf.dF, m.Wh, D, n, ts, tiles, bf.dxa);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int grid = (int)(tiles < (size_t)n_sm ? tiles : (size_t)n_sm);
+  const size_t img = (size_t)kRows * D * 2;
+#define TDO_COMMA ,
+#define TDO_SET_SMEM(K, BYTES)                                                                 \
+  if ((e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES)) != cudaSuccess) return e;
+  TDO_SET_SMEM(k_bwd_mlp<D>, MlpGeo<D>::BYTES);
+  TDO_SET_SMEM(k_bwd_attn2<D>, A2Geo<D>::BYTES);
+  TDO_SET_SMEM(k_bwd_attn1<D TDO_COMMA 8>, A1Geo<D>::BYTES);
+  TDO_SET_SMEM(k_bwd_attn1<D TDO_COMMA 16>, A1Geo<D>::BYTES);
+#undef TDO_SET_SMEM
+#undef TDO_COMMA
+  for (int l = m.layers - 1; l >= 0; --l) {
+    const BwdTcLayer &v = views[l];
+    const float *dxmid = bf.dxa;
+    if (m.ffn > 0) {
+      for (int hb = 0; hb < m.ffn / 128; ++hb) {
+        MlpArgs ma;
+        ma.w1t = reinterpret_cast<const uint8_t *>(mb.W1[l]) + (size_t)hb * 128 * D * 2;
+        ma.w2 = v.w2r[hb];
+        ma.w1 = v.w1r[hb];
+        ma.b1 = m.L[l].b1 + hb * 128;
+        ma.xmid = bf.xmid + (size_t)l * tiles * img;
+        ma.dxo = bf.dxa;
+        ma.base = hb == 0 ? bf.dxa : bf.dxb;
+        ma.dxm = bf.dxb;
+        ma.tiles = tiles;
+        ma.do_db2 = hb == 0;
+        ma.g = gacc;
+        ma.g_stride = g_stride;
+        ma.off_w1 = W1[l] + hb * 128;
+        ma.off_b1 = b1[l] + hb * 128;
+        ma.off_w2 = W2[l] + (long long)hb * 128 * D;
+        ma.off_b2 = b2[l];
+        ma.F = m.ffn;
+        ma.err = err;
+        k_bwd_mlp<D><<<grid, kThreads, MlpGeo<D>::BYTES, st>>>(ma);
+      }
+      dxmid = bf.dxb;
+    }
+    A1Args a1;
+    a1.wqkvT = reinterpret_cast<const uint8_t *>(mb.Wqkv[l]);
+    a1.wo = v.wor;
+    a1.x = bf.x + (size_t)l * tiles * img;
+    a1.dxm = dxmid;
+    a1.dqkv = bf.dqkv;
+    a1.tiles = tiles;
+    a1.n = n;
+    a1.ts = ts;
+    a1.heads = m.heads;
+    a1.g = gacc;
+    a1.g_stride = g_stride;
+    a1.off_wo = Wo[l];
+    a1.err = err;
+    if (m.dh == 8) k_bwd_attn1<D, 8><<<grid, kThreads, A1Geo<D>::BYTES, st>>>(a1);
+    else k_bwd_attn1<D, 16><<<grid, kThreads, A1Geo<D>::BYTES, st>>>(a1);
+    A2Args a2;
+    a2.wqkv = v.wqkvr;
+    a2.x = bf.x + (size_t)l * tiles * img;
+    a2.dqkv = bf.dqkv;
+    a2.dxm = dxmid;
+    a2.dxo = bf.dxa;
+    a2.tiles = tiles;
+    a2.n = n;
+    a2.ts = ts;
+    a2.embed_grad = l == 0;
+    a2.sig = sig;
+    a2.sigp = sigp;
+    a2.B = B;
+    a2.g = gacc;
+    a2.g_stride = g_stride;
+    a2.off_wq = Wq[l];
+    a2.off_wk = Wk[l];
+    a2.off_wv = Wv[l];
+    a2.off_e = off_e;
+    a2.err = err;
+    k_bwd_attn2<D><<<grid, kThreads, A2Geo<D>::BYTES, st>>>(a2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}

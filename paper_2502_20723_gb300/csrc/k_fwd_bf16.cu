@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include "tdo_device.cuh"
+#include "tcgen05.cuh"
 
 namespace tdo {
 namespace bf16 {
@@ -26,7 +27,6 @@ namespace bf16 {
 constexpr int kThreads = 256;
 constexpr int kRows = 128;
 constexpr int kTmemCols = 256;
-constexpr long long kSpinLimit = 1ll << 26;   // ~seconds of polling before giving up
 
 template <int D>
 struct Geo {
@@ -45,141 +45,16 @@ struct Geo {
   static_assert(2 * HC * D <= KV_BYTES, "hidden chunk fits the K/V region");
 };
 
-// ------------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+using namespace tdo::tc;
 
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase with parity `phase` to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t phase) {
-  for (long long i = 0; i < kSpinLimit; ++i) {
-    if (mbar_try(a, phase)) return true;
-    if (i > 64) __nanosleep(32);
-  }
-  return false;
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-
-// Bulk (TMA engine) copy of `bytes` contiguous bytes global -> shared, completion on mbarrier `bar`.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor, no swizzle, K-major: start >> 4 at [0,14), LBO >> 4 at [16,30),
-// SBO >> 4 at [32,46), fixed 0b001 at [46,49), layout type 0 (no swizzle) at [61,64).
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
-// both K-major (bits 15, 16 = 0), N >> 3 at [17,23), M >> 4 at [24,29).
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (thread = lane).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 2^x and tanh(x) on the SFU (PTX ex2.approx / tanh.approx); the BF16 path's error budget allows them.
-__device__ __forceinline__ float ex2_fast(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float tanh_fast(float x) {
-  float y;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float gelu_fast(float u) {
-  const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-  return 0.5f * u * (1.0f + tanh_fast(k0 * fmaf(k1 * u, u * u, u)));
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(a), "f"(b));
-  return r;
-}
-
-// Byte offset of element (row, k) in a canonical K-major tile with K columns.
-__host__ __device__ __forceinline__ uint32_t canon(int row, int k, int K) {
-  return (uint32_t)((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
-}
-
-// Store 8 consecutive k values (k0 % 8 == 0) of one row as BF16 (one 16-byte store).
-__device__ __forceinline__ void st_row8(uint8_t *base, int row, int k0, int K, const float *v) {
-  uint4 q;
-  q.x = pack_bf16(v[0], v[1]);
-  q.y = pack_bf16(v[2], v[3]);
-  q.z = pack_bf16(v[4], v[5]);
-  q.w = pack_bf16(v[6], v[7]);
-  *reinterpret_cast<uint4 *>(base + canon(row, k0, K)) = q;
-}
+// Activations parked by the forward for the tensor-core backward (all null = no stores).
+struct FwdStore {
+  uint8_t *X;      // [L][tiles] images of each layer's BF16 input (canonical [128][D], 2*128*D bytes)
+  uint8_t *Xmid;   // [L][tiles] images of each MLP input (null without MLP)
+  float *H;        // [tiles][ts][D] pooled vectors of the tile's sequences
+  float *F;        // [tiles][ts][2] head outputs (F0, F1)
+  size_t tiles;
+};
 
 struct Ctl {
   uint32_t bar_mma, bar_w;   // smem addresses
@@ -234,9 +109,18 @@ __device__ __forceinline__ bool sync_fail(Ctl &c, bool ok) {
 
 // The whole ansatz on one tile; configurations in cfg_s / cfg_p [ts/2], results to res [ts/2].
 // Returns false on a (bounded) wait timeout.
+// Copy the A image (BF16 [128][D], complete: callers are past a barrier) to global memory.
+template <int D>
+__device__ __forceinline__ void park_image(const uint8_t *A, uint8_t *dst) {
+  constexpr int N16 = 128 * D * 2 / 16;
+  for (int i = threadIdx.x; i < N16; i += kThreads)
+    reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(A)[i];
+}
+
 template <int D, int HD>
 __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm, Ctl &c, int ts,
-                          const uint32_t *cfg_s, const uint32_t *cfg_p, float2 *res) {
+                          const uint32_t *cfg_s, const uint32_t *cfg_p, float2 *res,
+                          const FwdStore *store = nullptr, size_t tile = 0) {
   using G = Geo<D>;
   constexpr int DH = D / 2;   // columns per thread (half)
   constexpr int KS = G::KS;
@@ -279,6 +163,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
     bool ok = wait_w(c);
     if (sync_fail(c, ok)) return false;
     gemm(c, a_addr, w_addr, D, 3 * D, 0, false);
+    if (store) park_image<D>(A, store->X + ((size_t)l * store->tiles + tile) * (size_t)G::A_BYTES);
     ok = wait_mma(c);
     if (sync_fail(c, ok)) return false;
     stage_w(c, w_addr, mb.Wo[l], D * D * 2);   // W is free: the QKV MMAs have completed
@@ -368,6 +253,8 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
         ok = wait_w(c);
         if (sync_fail(c, ok)) return false;
         gemm(c, a_addr, w_addr, D, G::HC, 0, false);                 // U chunk -> cols [0, HC)
+        if (store && ch == 0)
+          park_image<D>(A, store->Xmid + ((size_t)l * store->tiles + tile) * (size_t)G::A_BYTES);
         ok = wait_mma(c);
         if (sync_fail(c, ok)) return false;
         stage_w(c, w_addr, mb.W2[l] + (size_t)ch * G::HC * D, G::HC * D * 2);
@@ -426,6 +313,16 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
   __syncthreads();
   for (int cc = threadIdx.x; cc < ts / 2; cc += kThreads)
     res[cc] = symmetrise(Fs[4 * cc], Fs[4 * cc + 1], Fs[4 * cc + 2], Fs[4 * cc + 3], nullptr, nullptr);
+  if (store) {
+    for (int p = threadIdx.x; p < 2 * ts; p += kThreads) store->F[tile * (size_t)(2 * ts) + p] = Fs[p];
+    const float inv_n = 1.0f / (float)n;
+    for (int idx = threadIdx.x; idx < ts * D; idx += kThreads) {
+      const int sq = idx / D, cc = idx % D;
+      float hsum = 0.f;
+      for (int i = 0; i < n; ++i) hsum += Pool[(sq * n + i) * KS + cc];
+      store->H[(tile * (size_t)ts + sq) * D + cc] = hsum * inv_n;
+    }
+  }
   __syncthreads();
   return true;
 }
@@ -476,7 +373,7 @@ __device__ __forceinline__ void ctl_finish(Ctl &c) {
 template <int D, int HD>
 __global__ void __launch_bounds__(kThreads, 2) k_fwd_bf16(DevModel m, DevModelBF16 mb, const uint32_t *__restrict__ sig,
                                                           const uint32_t *__restrict__ sigp, size_t B,
-                                                          float2 *__restrict__ out, int *err) {
+                                                          float2 *__restrict__ out, int *err, FwdStore st) {
   extern __shared__ __align__(1024) uint8_t sm[];
   using G = Geo<D>;
   Ctl c;
@@ -493,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_bf16(DevModel m, DevModelBF
       cp[threadIdx.x] = b < B ? sigp[b] : 0u;
     }
     __syncthreads();
-    if (!eval_tile<D, HD>(m, mb, sm, c, ts, cs, cp, res)) break;
+    if (!eval_tile<D, HD>(m, mb, sm, c, ts, cs, cp, res, st.X ? &st : nullptr, tile)) break;
     if (threadIdx.x < tc) {
       const size_t b = tile * tc + threadIdx.x;
       if (b < B) out[b] = res[threadIdx.x];
@@ -631,7 +528,8 @@ cudaError_t launch_pack_bf16(const DevModel &m, uint16_t *dst16, DevModelBF16 *v
 
 template <int D, int HD>
 static cudaError_t fwd_bf16_impl(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
-                                 const uint32_t *sigp, size_t B, float2 *out, int *err, int n_sm, cudaStream_t st) {
+                                 const uint32_t *sigp, size_t B, float2 *out, int *err, int n_sm, cudaStream_t st,
+                                 const tdo::bf16::FwdStore &store) {
   using namespace tdo::bf16;
   const int bytes = Geo<D>::BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_fwd_bf16<D, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -647,18 +545,26 @@ static cudaError_t fwd_bf16_impl(const DevModel &m, const DevModelBF16 &mb, cons
   const size_t ntiles = (B + tc - 1) / tc;
   size_t grid = (size_t)n_sm * per_sm;
   if (grid > ntiles) grid = ntiles;
-  k_fwd_bf16<D, HD><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, sig, sigp, B, out, err);
+  k_fwd_bf16<D, HD><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, sig, sigp, B, out, err, store);
   return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_bf16_store(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
+                                  const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
+                                  cudaStream_t st, uint8_t *x_img, uint8_t *xmid_img, float *h, float *f,
+                                  size_t tiles) {
+  if (B == 0) return cudaSuccess;
+  tdo::bf16::FwdStore fs{x_img, xmid_img, h, f, tiles};
+  if (m.d == 64 && m.dh == 8) return fwd_bf16_impl<64, 8>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, fs);
+  if (m.d == 64 && m.dh == 16) return fwd_bf16_impl<64, 16>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, fs);
+  if (m.d == 32 && m.dh == 8) return fwd_bf16_impl<32, 8>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, fs);
+  if (m.d == 32 && m.dh == 16) return fwd_bf16_impl<32, 16>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, fs);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fwd_bf16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig, const uint32_t *sigp,
                             size_t B, float2 *logrho, int *err_flag, int n_sm, cudaStream_t st) {
-  if (B == 0) return cudaSuccess;
-  if (m.d == 64 && m.dh == 8) return fwd_bf16_impl<64, 8>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
-  if (m.d == 64 && m.dh == 16) return fwd_bf16_impl<64, 16>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
-  if (m.d == 32 && m.dh == 8) return fwd_bf16_impl<32, 8>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
-  if (m.d == 32 && m.dh == 16) return fwd_bf16_impl<32, 16>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st);
-  return cudaErrorInvalidValue;
+  return launch_fwd_bf16_store(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, nullptr, nullptr, nullptr, nullptr, 0);
 }
 
 template <int D, int HD>

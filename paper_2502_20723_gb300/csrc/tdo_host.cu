@@ -35,6 +35,25 @@ cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, c
 cudaError_t launch_params_f32(const double *theta, size_t P, const long long *tab, int n_tensors,
                               float *dst, cudaStream_t st);
 size_t bf16_packed_bytes(const DevModel &m);
+struct BwdTcLayer {
+  const uint8_t *w1t[2], *w2r[2], *w1r[2];
+  const uint8_t *wqkvT, *wor, *wqkvr;
+};
+struct BwdTcBuffers {
+  uint8_t *x, *xmid, *dqkv;
+  float *h, *f, *dF, *dxa, *dxb;
+  size_t tiles;
+};
+size_t bwdtc_packed_bytes(const DevModel &m);
+bool bwdtc_supported(const DevModel &m);
+cudaError_t launch_pack_bwdtc(const DevModel &m, uint8_t *dst, BwdTcLayer *views, cudaStream_t st);
+cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcLayer *views, const BwdTcBuffers &bf,
+                         const uint32_t *sig, const uint32_t *sigp, size_t B, const float2 *cot, float *gacc,
+                         size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st);
+cudaError_t launch_fwd_bf16_store(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
+                                  const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
+                                  cudaStream_t st, uint8_t *x_img, uint8_t *xmid_img, float *h, float *f,
+                                  size_t tiles);
 
 namespace {
 
@@ -80,9 +99,12 @@ struct tdo_ctx {
   int n_pat = 0;
   DBuf d_pat, d_con;
   // parameters
-  DBuf theta64, theta32, etab, tensor_tab, wbf16, errflag;
+  DBuf theta64, theta32, etab, tensor_tab, wbf16, errflag, wbwd;
   DevModel dm{};
   DevModelBF16 dmb{};
+  bool tc_bwd = false;                 // tensor-core gradient (BF16 contexts whose shape it supports)
+  BwdTcLayer bwl[TDO_MAX_LAYERS];
+  DBuf act_x, act_xmid, act_h, act_f, act_dF, act_dxa, act_dxb, act_dqkv;
   // workspace
   DBuf stage_in[4], stage_out;
   DBuf conn_cnt, conn_sig, conn_sigp, conn_coef, offs, fsig, fsigp, fcoef, flr, lloc, l2, stats,
@@ -356,6 +378,7 @@ static tdo_status refresh_params(tdo_ctx *c) {
                               b + c->tensors[2].pad, b + c->tensors[3].pad, c->etab.as<float>(), c->stream));
   }
   if (m->precision == TDO_BF16) CU(c, launch_pack_bf16(c->dm, c->wbf16.as<uint16_t>(), &c->dmb, c->stream));
+  if (c->tc_bwd) CU(c, launch_pack_bwdtc(c->dm, c->wbwd.as<uint8_t>(), c->bwl, c->stream));
   return TDO_OK;
 }
 
@@ -472,6 +495,11 @@ extern "C" tdo_status tdo_create(const tdo_problem *problem, const tdo_model *mo
       fail(c, TDO_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
       return bail(TDO_ENOMEM);
     }
+    c->tc_bwd = bwdtc_supported(c->dm);
+    if (c->tc_bwd && (e = c->wbwd.ensure(bwdtc_packed_bytes(c->dm))) != cudaSuccess) {
+      fail(c, TDO_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+      return bail(TDO_ENOMEM);
+    }
   }
   s = tdo_set_params(c, theta);
   if (s != TDO_OK) return bail(s);
@@ -486,7 +514,8 @@ extern "C" tdo_status tdo_destroy(tdo_ctx *c) {
                   &c->stage_in[1], &c->stage_in[2], &c->stage_in[3], &c->stage_out, &c->conn_cnt, &c->conn_sig,
                   &c->conn_sigp, &c->conn_coef, &c->offs, &c->fsig, &c->fsigp, &c->fcoef, &c->flr, &c->lloc,
                   &c->l2, &c->stats, &c->nonfinite, &c->cot, &c->gacc, &c->scratch, &c->grad, &c->Obuf,
-                  &c->srwork, &c->delta, &c->acc_u64, &c->wbf16, &c->errflag};
+                  &c->srwork, &c->delta, &c->acc_u64, &c->wbf16, &c->errflag, &c->wbwd, &c->act_x, &c->act_xmid,
+                  &c->act_h, &c->act_f, &c->act_dF, &c->act_dxa, &c->act_dxb, &c->act_dqkv};
   for (DBuf *b : bufs) b->release();
   for (auto &r : c->trec) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : c->epool) cudaEventDestroy(e);
@@ -561,7 +590,12 @@ extern "C" tdo_status tdo_log_rho(tdo_ctx *c, const uint32_t *sig, const uint32_
 }
 
 // Connections + compaction + forward over every row + L_loc and cost statistics (device buffers).
-static tdo_status estimator_core(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t Ns, int64_t *total) {
+static tdo_status estimator_core(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t Ns, int64_t *total,
+                                 bool park = false);
+static tdo_status forward_park(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t B, float2 *out);
+
+static tdo_status estimator_core(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t Ns, int64_t *total,
+                                 bool park) {
   const int M = c->n_pat;
   CU(c, c->conn_cnt.ensure(sizeof(int32_t) * Ns));
   CU(c, c->conn_sig.ensure(sizeof(uint32_t) * Ns * M));
@@ -590,7 +624,8 @@ static tdo_status estimator_core(tdo_ctx *c, const uint32_t *ds, const uint32_t 
                          c->conn_sigp.as<uint32_t>(), c->conn_coef.as<float2>(), c->fsig.as<uint32_t>(),
                          c->fsigp.as<uint32_t>(), c->fcoef.as<float2>(), c->stream));
   }
-  TRY(forward_dev(c, c->fsig.as<uint32_t>(), c->fsigp.as<uint32_t>(), (size_t)tot, c->flr.as<float2>()));
+  if (park) TRY(forward_park(c, c->fsig.as<uint32_t>(), c->fsigp.as<uint32_t>(), (size_t)tot, c->flr.as<float2>()));
+  else TRY(forward_dev(c, c->fsig.as<uint32_t>(), c->fsigp.as<uint32_t>(), (size_t)tot, c->flr.as<float2>()));
   CU(c, c->lloc.ensure(sizeof(double2) * Ns));
   CU(c, c->l2.ensure(sizeof(double) * Ns));
   CU(c, c->stats.ensure(sizeof(double) * 4));
@@ -726,17 +761,64 @@ extern "C" tdo_status tdo_jacobian(tdo_ctx *c, const uint32_t *sig, const uint32
   return TDO_OK;
 }
 
+// BF16 forward that also parks the activations the tensor-core backward needs.
+static size_t tc_tiles(tdo_ctx *c, size_t B) {
+  const int tc = (2 * (128 / (2 * c->n)) < 2 ? 2 : 2 * (128 / (2 * c->n))) / 2;
+  return (B + tc - 1) / tc;
+}
+static tdo_status forward_park(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t B, float2 *out) {
+  const size_t tiles = tc_tiles(c, B);
+  const int ts = 2 * (128 / (2 * c->n)) < 2 ? 2 : 2 * (128 / (2 * c->n));
+  const size_t img = (size_t)128 * c->dm.d * 2, L = c->dm.layers;
+  CU(c, c->act_x.ensure(L * tiles * img));
+  CU(c, c->act_xmid.ensure(c->dm.ffn > 0 ? L * tiles * img : 16));
+  CU(c, c->act_h.ensure(sizeof(float) * tiles * ts * c->dm.d));
+  CU(c, c->act_f.ensure(sizeof(float) * tiles * ts * 2));
+  Timed tm(c, G_FWD);
+  CU(c, launch_fwd_bf16_store(c->dm, c->dmb, sig, sigp, B, out, c->errflag.as<int>(), c->n_sm, c->stream,
+                              c->act_x.as<uint8_t>(), c->dm.ffn > 0 ? c->act_xmid.as<uint8_t>() : nullptr,
+                              c->act_h.as<float>(), c->act_f.as<float>(), tiles));
+  return TDO_OK;
+}
+
+// Tensor-core VJP of the rows parked by forward_park (same rows, same order).
+static tdo_status vjp_tc(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t B, const float2 *cot,
+                         double *grad) {
+  const size_t tiles = tc_tiles(c, B);
+  const int ts = 2 * (128 / (2 * c->n)) < 2 ? 2 : 2 * (128 / (2 * c->n));
+  const size_t D = c->dm.d;
+  const int copies = 16;
+  const size_t stride = (c->P + 3) / 4 * 4;
+  CU(c, c->act_dF.ensure(sizeof(float) * tiles * ts * 2));
+  CU(c, c->act_dxa.ensure(sizeof(float) * tiles * 128 * D));
+  CU(c, c->act_dxb.ensure(sizeof(float) * tiles * 128 * D));
+  CU(c, c->act_dqkv.ensure(tiles * 128 * 3 * D * 2));
+  CU(c, c->gacc.ensure(sizeof(float) * copies * stride));
+  CU(c, cudaMemsetAsync(c->gacc.p, 0, sizeof(float) * copies * stride, c->stream));
+  BwdTcBuffers bf{c->act_x.as<uint8_t>(), c->act_xmid.as<uint8_t>(), c->act_dqkv.as<uint8_t>(), c->act_h.as<float>(),
+                  c->act_f.as<float>(), c->act_dF.as<float>(), c->act_dxa.as<float>(), c->act_dxb.as<float>(), tiles};
+  Timed tm(c, G_BWD_VJP);
+  CU(c, launch_bwdtc(c->dm, c->dmb, c->bwl, bf, ds, dp, B, cot, c->gacc.as<float>(), stride, c->flat_offsets,
+                     c->errflag.as<int>(), c->n_sm, c->stream));
+  CU(c, launch_reduce_copies(c->gacc.as<float>(), copies, stride, c->P, grad, 0, c->stream));
+  tm.done(2 + (long long)c->dm.layers * (2 + (c->dm.ffn > 0 ? c->dm.ffn / 128 : 0)) + 1);
+  return TDO_OK;
+}
+
 // gradient of the cost on device: grad (device FP64 [P])
 static tdo_status grad_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t Ns, double *grad, double *cost) {
   int64_t total = 0;
-  TRY(estimator_core(c, ds, dp, Ns, &total));
+  TRY(estimator_core(c, ds, dp, Ns, &total, c->tc_bwd));
   CU(c, c->cot.ensure(sizeof(float2) * total));
   {
     Timed tm(c, G_LLOC);
     CU(c, launch_cotangent(c->offs.as<int64_t>(), Ns, c->fcoef.as<float2>(), c->flr.as<float2>(), c->lloc.as<double2>(),
                            c->stats.as<double>(), c->cot.as<float2>(), c->stream));
   }
-  TRY(vjp_dev(c, c->fsig.as<uint32_t>(), c->fsigp.as<uint32_t>(), (size_t)total, c->cot.as<float2>(), grad, 0));
+  if (c->tc_bwd)
+    TRY(vjp_tc(c, c->fsig.as<uint32_t>(), c->fsigp.as<uint32_t>(), (size_t)total, c->cot.as<float2>(), grad));
+  else
+    TRY(vjp_dev(c, c->fsig.as<uint32_t>(), c->fsigp.as<uint32_t>(), (size_t)total, c->cot.as<float2>(), grad, 0));
   TRY(read_stats(c, Ns, cost, nullptr));
   return TDO_OK;
 }

@@ -86,3 +86,20 @@ def test_bf16_unsupported_shapes():
     spec = synth.model_spec(16, 2, 1, 0)
     with pytest.raises(tdo.TdoError, match="EUNSUPPORTED"):
         ctx_for(problem("ising", 4), spec, synth.init_params(spec))
+
+
+@pytest.mark.parametrize("kind,n,h,L,r,Ns", [("ising", 16, 8, 4, 4, 96), ("xyz", 13, 4, 2, 2, 64), ("ising", 8, 8, 2, 0, 128)])
+def test_cost_gradient_bf16_tensor_core(kind, n, h, L, r, Ns):
+    """tdo_grad on a BF16 context runs the tensor-core backward (BF16 activations, FP32 accumulation):
+    the gradient is within 5e-2 of the oracle's in norm (measured values are reported)."""
+    prob = problem(kind, n)
+    spec = synth.model_spec(64, h, L, r)
+    th = synth.init_params(spec, seed=21, std=0.05)
+    sig, sigp = synth.random_configs(n, Ns, seed=9)
+    g, cost = ctx_for(prob, spec, th).grad(dev(sig), dev(sigp))
+    g = g.cpu().numpy()
+    ref, c_ref, _, _ = E.grad_estimator(prob, spec, th, sig, sigp)
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    print(f"bf16 gradient relative error {rel:.3e}, cost {cost:.6f} vs {c_ref:.6f}")
+    assert abs(cost - c_ref) <= 1e-3 * c_ref
+    assert rel <= 5e-2
