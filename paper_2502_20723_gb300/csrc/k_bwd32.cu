@@ -47,6 +47,7 @@ struct SinkCtx {
   float *g;          // mode 0: this CTA's accumulator copy [P] (16-byte aligned)
   float *O;          // mode 1: [B][P][2]
   size_t P;
+  float *dtab;       // conv embedding: mode 0 [64][D] accumulator; mode 1 [B][2][64][D]
 };
 
 // Add / write one gradient value at flat parameter index k for virtual configuration v of the tile.
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_bwd32(const DevModel m, const int mode, const uint32_t *__restrict__ sig,
             const uint32_t *__restrict__ sigp, const size_t B, const float2 *__restrict__ cot,
             float *__restrict__ gacc, const int n_copies, const size_t g_stride, float *__restrict__ O,
-            const size_t P, const FlatOffsets fo, float *__restrict__ scratch) {
+            const size_t P, const FlatOffsets fo, float *__restrict__ scratch, float *__restrict__ dtab) {
   using BG = BwdGeom<D>;
   constexpr int R = BG::R, LDX = BG::LDX;
   using G = F32Geom<D, R>;
@@ -285,6 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   sk.g = gacc ? gacc + (size_t)(blockIdx.x % n_copies) * g_stride : nullptr;   // g_stride % 4 == 0
   sk.O = O;
   sk.P = P;
+  sk.dtab = dtab;
   const int nranges = mode == 0 ? 1 : tcv;
 
   for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -536,21 +538,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       __syncthreads();
     }
-    // ---------------- embedding (token table)
-    if (m.embed == 0) {
+    // ---------------- embedding: gradient of the table row each token read (4 token rows, or the 64
+    // conv patterns whose table is back-propagated to the conv parameters by k_conv_vjp).  The layer-0
+    // input buffer is dead here and holds each row's pattern.
+    {
+      const int npat = m.embed == 0 ? 4 : 64;
+      int *rpat = reinterpret_cast<int *>(Bf[0]);
+      for (int r = threadIdx.x; r < nrows; r += kThreads) {
+        const int s = r / n, i = r % n, cfg = s >> 1;
+        const uint32_t w1 = (s & 1) ? csigp[cfg] : csig[cfg];
+        const uint32_t w2 = (s & 1) ? csig[cfg] : csigp[cfg];
+        rpat[r] = embed_pattern(m.embed, w1, w2, i, n);
+      }
+      __syncthreads();
+      float *dcopy = (m.embed != 0 && mode == 0) ? sk.dtab + (size_t)(blockIdx.x % n_copies) * (64 * D) : nullptr;
       for (int rg = 0; rg < nranges; ++rg) {
         if (mode == 1 && !vvalid(rg)) continue;
         const int r0 = mode == 0 ? 0 : rg * 2 * n, r1 = mode == 0 ? nrows : r0 + 2 * n;
-        for (int idx = threadIdx.x; idx < 4 * D; idx += kThreads) {
+        for (int idx = threadIdx.x; idx < npat * D; idx += kThreads) {
           const int pat = idx / D, c = idx % D;
           float a = 0.f;
-          for (int r = r0; r < r1; ++r) {
-            const int s = r / n, i = r % n, cfg = s >> 1;
-            const uint32_t w1 = (s & 1) ? csigp[cfg] : csig[cfg];
-            const uint32_t w2 = (s & 1) ? csig[cfg] : csigp[cfg];
-            if (embed_pattern(0, w1, w2, i, n) == pat) a += Bf[6][r * LDX + c];
-          }
-          sink1(sk, fo.E + idx, a, vb(rg), vs(rg));
+          for (int r = r0; r < r1; ++r)
+            if (rpat[r] == pat) a += Bf[6][r * LDX + c];
+          if (m.embed == 0) sink1(sk, fo.E + idx, a, vb(rg), vs(rg));
+          else if (mode == 0) { if (a != 0.f) atomicAdd(dcopy + idx, a); }
+          else sk.dtab[((size_t)vb(rg) * 2 + vs(rg)) * (64 * D) + idx] = a;
         }
       }
     }
@@ -561,11 +573,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int D>
 static cudaError_t bwd_impl(const DevModel &m, int mode, const uint32_t *sig, const uint32_t *sigp,
                             size_t B, const float2 *cot, float *gacc, int n_copies, size_t g_stride, float *O,
-                            size_t P, const FlatOffsets &fo, float *scratch, int grid, cudaStream_t st) {
+                            size_t P, const FlatOffsets &fo, float *scratch, float *dtab, int grid, cudaStream_t st) {
   const size_t bytes = BwdGeom<D>::BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_bwd32<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_bwd32<D><<<grid, kThreads, bytes, st>>>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch);
+  k_bwd32<D><<<grid, kThreads, bytes, st>>>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch,
+                                            dtab);
   return cudaGetLastError();
 }
 
@@ -589,16 +602,111 @@ int bwd32_grid(const DevModel &m, size_t B, int mode, int n_sm) {
 
 cudaError_t launch_bwd32_impl(const DevModel &m, int mode, const uint32_t *sig, const uint32_t *sigp,
                               size_t B, const float2 *cot, float *gacc, int n_copies, size_t g_stride,
-                              float *O, size_t P, const long long *flat_offsets, float *scratch, int grid,
-                              cudaStream_t st) {
+                              float *O, size_t P, const long long *flat_offsets, float *scratch, float *dtab,
+                              int grid, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
   tdo::FlatOffsets fo;
   static_assert(sizeof(tdo::FlatOffsets) == sizeof(long long) * (3 + 8 * TDO_MAX_LAYERS), "layout");
   memcpy(&fo, flat_offsets, sizeof(fo));
   switch (m.d) {
-    case 16: return tdo::bwd_impl<16>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch, grid, st);
-    case 32: return tdo::bwd_impl<32>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch, grid, st);
-    case 64: return tdo::bwd_impl<64>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch, grid, st);
+    case 16: return tdo::bwd_impl<16>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch, dtab, grid, st);
+    case 32: return tdo::bwd_impl<32>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch, dtab, grid, st);
+    case 64: return tdo::bwd_impl<64>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, P, fo, scratch, dtab, grid, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ---------------------------------------------------------------------------------- conv embedding VJP
+// Back-propagates per-pattern table gradients dT[p][e] through the conv embedding table
+//   a1[p][o2][f] = bc1[f] + sum_{o1,ch} Wc1[o1][ch][f] x[p][o2+o1][ch],  h1 = gelu(a1)
+//   a2[p][e]     = bc2[e] + sum_{o2,f} Wc2[o2][f][e] h1[p][o2][f],        T  = gelu(a2)
+// (two kernel-2 circular convolutions over sites i, i+1, i+2; x = +-1 spins of both channels).
+// One block per table-gradient set (the sum of ncopy consecutive [64][d] copies); mode 0 adds into the
+// accumulator g at the flat offsets, mode 1 writes O[set/2][k][set%2].
+namespace tdo {
+__global__ void k_conv_vjp(int d, int c1, const float *__restrict__ Wc1, const float *__restrict__ bc1,
+                           const float *__restrict__ Wc2, const float *__restrict__ bc2,
+                           const float *__restrict__ dT, int nsets, int ncopy, int mode, float *__restrict__ g,
+                           float *__restrict__ O, size_t P, long long o_wc1, long long o_bc1, long long o_wc2,
+                           long long o_bc2) {
+  extern __shared__ float sh[];
+  float *a1 = sh;                       // [64][2][c1]
+  float *dh = a1 + 64 * 2 * c1;         // [64][2][c1] (da1 in place)
+  float *a2 = dh + 64 * 2 * c1;         // [64][d]     (da2 in place)
+  for (int set = blockIdx.x; set < nsets; set += gridDim.x) {
+    const float *dts = dT + (size_t)set * ncopy * 64 * d;
+    for (int i = threadIdx.x; i < 64 * 2 * c1; i += blockDim.x) {
+      const int p = i / (2 * c1), o2 = (i / c1) % 2, f = i % c1;
+      float acc = bc1[f];
+      for (int o1 = 0; o1 < 2; ++o1)
+        for (int ch = 0; ch < 2; ++ch) {
+          const int bit = (p >> (ch * 3 + o2 + o1)) & 1;
+          acc = fmaf(Wc1[(o1 * 2 + ch) * c1 + f], 1.0f - 2.0f * (float)bit, acc);
+        }
+      a1[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64 * d; i += blockDim.x) {
+      const int p = i / d, e = i % d;
+      float acc = bc2[e];
+      for (int o2 = 0; o2 < 2; ++o2)
+        for (int f = 0; f < c1; ++f) acc = fmaf(Wc2[(o2 * c1 + f) * d + e], gelu_f(a1[(p * 2 + o2) * c1 + f]), acc);
+      float dt = 0.f;
+      for (int k = 0; k < ncopy; ++k) dt += dts[(size_t)k * 64 * d + i];
+      a2[i] = dt * gelu_grad_f(acc);   // da2
+    }
+    __syncthreads();
+    auto put = [&](long long k, float v) {
+      if (mode == 0) atomicAdd(g + k, v);
+      else O[((size_t)(set >> 1) * P + (size_t)k) * 2 + (set & 1)] = v;
+    };
+    for (int e = threadIdx.x; e < d; e += blockDim.x) {
+      float acc = 0.f;
+      for (int p = 0; p < 64; ++p) acc += a2[p * d + e];
+      put(o_bc2 + e, acc);
+    }
+    for (int i = threadIdx.x; i < 2 * c1 * d; i += blockDim.x) {
+      const int o2 = i / (c1 * d), f = (i / d) % c1, e = i % d;
+      float acc = 0.f;
+      for (int p = 0; p < 64; ++p) acc = fmaf(a2[p * d + e], gelu_f(a1[(p * 2 + o2) * c1 + f]), acc);
+      put(o_wc2 + i, acc);
+    }
+    for (int i = threadIdx.x; i < 64 * 2 * c1; i += blockDim.x) {
+      const int p = i / (2 * c1), o2 = (i / c1) % 2, f = i % c1;
+      float acc = 0.f;
+      for (int e = 0; e < d; ++e) acc = fmaf(Wc2[(o2 * c1 + f) * d + e], a2[p * d + e], acc);
+      dh[i] = acc * gelu_grad_f(a1[i]);   // da1
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < c1; f += blockDim.x) {
+      float acc = 0.f;
+      for (int p = 0; p < 64; ++p) acc += dh[(p * 2) * c1 + f] + dh[(p * 2 + 1) * c1 + f];
+      put(o_bc1 + f, acc);
+    }
+    for (int i = threadIdx.x; i < 4 * c1; i += blockDim.x) {
+      const int o1 = i / (2 * c1), ch = (i / c1) % 2, f = i % c1;
+      float acc = 0.f;
+      for (int p = 0; p < 64; ++p)
+        for (int o2 = 0; o2 < 2; ++o2) {
+          const int bit = (p >> (ch * 3 + o2 + o1)) & 1;
+          acc = fmaf(dh[(p * 2 + o2) * c1 + f], 1.0f - 2.0f * (float)bit, acc);
+        }
+      put(o_wc1 + i, acc);
+    }
+    __syncthreads();
+  }
+}
+}  // namespace tdo
+
+cudaError_t launch_conv_vjp(int d, int c1, const float *Wc1, const float *bc1, const float *Wc2, const float *bc2,
+                            const float *dT, int nsets, int ncopy, int mode, float *g, float *O, size_t P,
+                            long long o_wc1, long long o_bc1, long long o_wc2, long long o_bc2, cudaStream_t st) {
+  if (nsets <= 0) return cudaSuccess;
+  const size_t bytes = sizeof(float) * (2 * 64 * 2 * c1 + 64 * d);
+  cudaError_t e = cudaFuncSetAttribute(tdo::k_conv_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  const int grid = nsets < 1024 ? nsets : 1024;
+  tdo::k_conv_vjp<<<grid, 256, bytes, st>>>(d, c1, Wc1, bc1, Wc2, bc2, dT, nsets, ncopy, mode, g, O, P, o_wc1,
+                                            o_bc1, o_wc2, o_bc2);
+  return cudaGetLastError();
 }

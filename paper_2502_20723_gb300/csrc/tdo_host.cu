@@ -26,8 +26,11 @@ size_t bwd32_scratch_floats(const DevModel &m, int grid);
 int bwd32_grid(const DevModel &m, size_t B, int mode, int n_sm);
 cudaError_t launch_bwd32_impl(const DevModel &m, int mode, const uint32_t *sig, const uint32_t *sigp,
                               size_t B, const float2 *cot, float *gacc, int n_copies, size_t g_stride,
-                              float *O, size_t P, const long long *flat_offsets, float *scratch, int grid,
-                              cudaStream_t st);
+                              float *O, size_t P, const long long *flat_offsets, float *scratch, float *dtab,
+                              int grid, cudaStream_t st);
+cudaError_t launch_conv_vjp(int d, int c1, const float *Wc1, const float *bc1, const float *Wc2, const float *bc2,
+                            const float *dT, int nsets, int ncopy, int mode, float *g, float *O, size_t P,
+                            long long o_wc1, long long o_bc1, long long o_wc2, long long o_bc2, cudaStream_t st);
 size_t sr_work_doubles(size_t Ns, size_t P);
 cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, const double *x0, double shift,
                        double tol, int max_iter, double *x, double *work, int n_sm, int *iters, double *resid,
@@ -100,6 +103,7 @@ struct tdo_ctx {
   DBuf d_pat, d_con;
   // parameters
   DBuf theta64, theta32, etab, tensor_tab, wbf16, errflag, wbwd;
+  DBuf dtab;   // conv embedding: per-pattern table gradients
   DevModel dm{};
   DevModelBF16 dmb{};
   bool tc_bwd = false;                 // tensor-core gradient (BF16 contexts whose shape it supports)
@@ -694,31 +698,52 @@ extern "C" tdo_status tdo_local_estimator(tdo_ctx *c, const uint32_t *sig, const
 }
 
 
+// Back-propagates the per-pattern table gradients the backward kernel left in c->dtab to the conv
+// embedding parameters (mode 0: added into g; mode 1: written into O[b][k][seed]).
+static tdo_status conv_vjp(tdo_ctx *c, int nsets, int ncopy, int mode, float *g, float *O) {
+  const float *b = c->theta32.as<float>();
+  CU(c, launch_conv_vjp(c->model.d_model, c->model.conv_channels, b + c->tensors[0].pad, b + c->tensors[1].pad,
+                        b + c->tensors[2].pad, b + c->tensors[3].pad, c->dtab.as<float>(), nsets, ncopy, mode, g, O,
+                        c->P,
+                        c->tensors[0].flat, c->tensors[1].flat, c->tensors[2].flat, c->tensors[3].flat, c->stream));
+  return TDO_OK;
+}
+
 // VJP over device rows: grad (FP64, device) = [accumulate ? grad : 0] + sum Re(cot * dlogrho).
 static tdo_status vjp_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t B, const float2 *cot,
                           double *grad, int accumulate) {
-  if (c->model.embed != TDO_EMBED_TOKEN) return fail(c, TDO_EUNSUPPORTED, "gradients of the conv embedding are not built");
+  const bool conv = c->model.embed == TDO_EMBED_CONV;
   const int grid = bwd32_grid(c->dm, B, 0, c->n_sm);
   const int copies = grid < 16 ? grid : 16;   // 16 accumulator copies: L2-resident, low contention
   const size_t stride = (c->P + 3) / 4 * 4;   // 16-byte aligned copies (float4 atomics)
+  const size_t tab = (size_t)64 * c->model.d_model;
   CU(c, c->gacc.ensure(sizeof(float) * copies * stride));
   CU(c, c->scratch.ensure(sizeof(float) * bwd32_scratch_floats(c->dm, grid)));
   CU(c, cudaMemsetAsync(c->gacc.p, 0, sizeof(float) * copies * stride, c->stream));
+  if (conv) {   // one [64][d] table-gradient copy per accumulator copy
+    CU(c, c->dtab.ensure(sizeof(float) * copies * tab));
+    CU(c, cudaMemsetAsync(c->dtab.p, 0, sizeof(float) * copies * tab, c->stream));
+  }
   Timed tm(c, G_BWD_VJP);
   CU(c, launch_bwd32_impl(c->dm, 0, ds, dp, B, cot, c->gacc.as<float>(), copies, stride, nullptr, c->P,
-                          c->flat_offsets, c->scratch.as<float>(), grid, c->stream));
+                          c->flat_offsets, c->scratch.as<float>(), conv ? c->dtab.as<float>() : nullptr, grid,
+                          c->stream));
+  if (conv) TRY(conv_vjp(c, 1, copies, 0, c->gacc.as<float>(), nullptr));
   CU(c, launch_reduce_copies(c->gacc.as<float>(), copies, stride, c->P, grad, accumulate, c->stream));
-  tm.done(2);
+  tm.done(conv ? 3 : 2);
   return TDO_OK;
 }
 
 static tdo_status jacobian_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t B, float *O) {
-  if (c->model.embed != TDO_EMBED_TOKEN) return fail(c, TDO_EUNSUPPORTED, "gradients of the conv embedding are not built");
+  const bool conv = c->model.embed == TDO_EMBED_CONV;
   const int grid = bwd32_grid(c->dm, B, 1, c->n_sm);
   CU(c, c->scratch.ensure(sizeof(float) * bwd32_scratch_floats(c->dm, grid)));
+  if (conv) CU(c, c->dtab.ensure(sizeof(float) * 2 * B * 64 * c->model.d_model));
   Timed tm(c, G_BWD_JAC);
   CU(c, launch_bwd32_impl(c->dm, 1, ds, dp, B, nullptr, nullptr, 1, 0, O, c->P, c->flat_offsets,
-                          c->scratch.as<float>(), grid, c->stream));
+                          c->scratch.as<float>(), conv ? c->dtab.as<float>() : nullptr, grid, c->stream));
+  if (conv) TRY(conv_vjp(c, (int)(2 * B), 1, 1, nullptr, O));
+  tm.done(conv ? 2 : 1);
   return TDO_OK;
 }
 
@@ -868,6 +893,7 @@ extern "C" tdo_status tdo_sr_solve(tdo_ctx *c, const float *O, size_t Ns, const 
   if (iters) *iters = it_local;
   tm.done(nl);
   if (e == cudaErrorInvalidValue) return fail(c, TDO_ENUMERIC, "CG breakdown: S + shift I is not positive definite");
+  if (e == cudaErrorTimeout) return fail(c, TDO_ETIMEOUT, "the SR matvec's bounded inter-block wait gave up");
   CU(c, e);
   TRY(deliver(c, x, dx, sizeof(double) * c->P, &h3));
   CU(c, cudaStreamSynchronize(c->stream));
@@ -906,6 +932,7 @@ extern "C" tdo_status tdo_sr_step(tdo_ctx *c, const uint32_t *sig, const uint32_
   c->last_sr_iters = iters;
   c->last_sr_resid = resid;
   if (e == cudaErrorInvalidValue) return fail(c, TDO_ENUMERIC, "CG breakdown: S + shift I is not positive definite");
+  if (e == cudaErrorTimeout) return fail(c, TDO_ETIMEOUT, "the SR matvec's bounded inter-block wait gave up");
   CU(c, e);
   {
     Timed tm(c, G_UPDATE);

@@ -247,6 +247,31 @@ def test_sr_solve_matches_cholesky():
     assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("d,h,L,r,Ns", [(32, 4, 2, 0, 301), (64, 8, 2, 4, 77), (64, 8, 4, 4, 69),
+                                         (64, 8, 8, 4, 45), (64, 8, 8, 8, 37)])
+def test_sr_solve_residual_any_size(d, h, L, r, Ns):
+    """P from 8k to 660k parameters (one to eight parameters per thread of the one-pass matvec, and past
+    it), Ns not a multiple of the row block: the true residual of (Re S + lambda I) x = rhs, formed in
+    FP64 from the same FP32 O, is at the FP32-product level."""
+    spec = synth.model_spec(d, h, L, r)
+    ctx = ctx_for(problem("ising", 4), spec, synth.init_params(spec))
+    P = ctx.P
+    rng = np.random.default_rng(P)
+    O = (rng.standard_normal((Ns, P, 2)) * 0.3).astype(np.float32)
+    O[:, :, 1] += rng.standard_normal(P).astype(np.float32)
+    rhs = rng.standard_normal(P)
+    lam = 1e-2
+    x, it, res = ctx.sr_solve(torch.as_tensor(O).cuda(), torch.as_tensor(rhs).cuda(), lam, tol=1e-8, max_iter=500)
+    x = x.cpu().numpy()
+    Or = O[..., 0].astype(np.float64)
+    Oi = O[..., 1].astype(np.float64)
+    Or -= Or.mean(axis=0)
+    Oi -= Oi.mean(axis=0)
+    Sx = (Or.T @ (Or @ x) + Oi.T @ (Oi @ x)) / Ns + lam * x
+    assert res <= 1e-8 and it < 500
+    assert np.linalg.norm(Sx - rhs) <= 1e-5 * np.linalg.norm(rhs), np.linalg.norm(Sx - rhs) / np.linalg.norm(rhs)
+
+
 def test_sr_step_matches_oracle():
     prob = problem("xyz", 6, Jx=0.9)
     spec = synth.model_spec(16, 2, 1, 0)
@@ -324,3 +349,68 @@ def test_nan_parameters_raise_numeric():
     sig, sigp = synth.random_configs(4, 10)
     with pytest.raises(tdo.TdoError, match="ENUMERIC"):
         ctx.local_estimator(dev(sig), dev(sigp))
+
+
+# ------------------------------------------------------------------ conv embedding (Eq. circ-conv)
+CONV_CASES = [
+    # (N, d, heads, layers, mlp, C1, B)
+    (4, 16, 2, 1, 0, 4, 40),
+    (8, 32, 4, 2, 0, 8, 33),
+    (13, 64, 8, 2, 2, 16, 21),    # ragged tile
+    (3, 16, 4, 1, 1, 3, 17),      # sites i+1, i+2 wrap twice
+]
+
+
+def _conv(d, h, L, r, c1, seed):
+    spec = synth.model_spec(d, h, L, r, embed="conv", conv_channels=c1)
+    return spec, synth.init_params(spec, seed=seed, std=0.2 if d < 64 else 0.05)
+
+
+@pytest.mark.parametrize("n,d,h,L,r,c1,B", CONV_CASES)
+def test_conv_log_rho(n, d, h, L, r, c1, B):
+    spec, th = _conv(d, h, L, r, c1, 3)
+    sig, sigp = synth.random_configs(n, B, seed=5)
+    out = ctx_for(problem("ising", n), spec, th).log_rho(dev(sig), dev(sigp)).cpu().numpy()
+    ref = T.log_rho_np(spec, th, sig, sigp, n)
+    assert np.all(logrho_err(out, ref) <= 1e-6 * np.maximum(np.abs(ref), 1.0))
+
+
+@pytest.mark.parametrize("n,d,h,L,r,c1,B", CONV_CASES)
+def test_conv_jacobian(n, d, h, L, r, c1, B):
+    """Per-configuration log-derivatives including the two conv layers (table gradient per pattern,
+    then back through both convolutions and GELUs)."""
+    spec, th = _conv(d, h, L, r, c1, 4)
+    sig, sigp = synth.random_configs(n, B, seed=6)
+    O = ctx_for(problem("ising", n), spec, th).jacobian(dev(sig), dev(sigp)).cpu().numpy()
+    ref = E.jacobian(spec, th, sig, sigp, n)
+    got = O[..., 0] + 1j * O[..., 1]
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(got - ref).max() <= 2e-5 * scale, np.abs(got - ref).max()
+
+
+@pytest.mark.parametrize("n,d,h,L,r,c1,B", CONV_CASES)
+def test_conv_vjp(n, d, h, L, r, c1, B):
+    spec, th = _conv(d, h, L, r, c1, 5)
+    sig, sigp = synth.random_configs(n, B, seed=7)
+    cot = np.random.default_rng(2).standard_normal((B, 2)).astype(np.float32)
+    grad = torch.zeros(synth.num_params(spec), dtype=torch.float64, device="cuda")
+    ctx_for(problem("ising", n), spec, th).log_rho_vjp(dev(sig), dev(sigp), torch.as_tensor(cot).cuda(), grad)
+    tt = torch.as_tensor(th).requires_grad_(True)
+    lr = T.log_rho(spec, tt, sig, sigp, n)
+    c = torch.as_tensor(cot.astype(np.float64))
+    (c[:, 0] * lr.real - c[:, 1] * lr.imag).sum().backward()
+    ref = tt.grad.numpy()
+    g = grad.cpu().numpy()
+    assert np.abs(g - ref).max() <= 1e-4 * np.abs(ref).max()
+    assert np.linalg.norm(g - ref) <= 2e-5 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("kind,n", [("ising", 8), ("xyz", 6)])
+def test_conv_cost_gradient(kind, n):
+    prob = problem(kind, n)
+    spec, th = _conv(32, 4, 2, 0, 8, 8)
+    sig, sigp = synth.random_configs(n, 200, seed=9)
+    g, cost = ctx_for(prob, spec, th).grad(dev(sig), dev(sigp))
+    ref, c_ref, _, _ = E.grad_estimator(prob, spec, th, sig, sigp)
+    assert abs(cost - c_ref) <= 1e-5 * c_ref
+    assert np.linalg.norm(g.cpu().numpy() - ref) <= 1e-4 * np.linalg.norm(ref)
