@@ -166,12 +166,15 @@ def run_ours(args) -> dict | None:
             ms, n = ctx.timing_read(g)
             groups[g] = {"ms": ms / steps, "launches": n / steps}
         launches = int(sum(v["launches"] for v in groups.values()) * steps)
+        ms, n = ctx.timing_read("sr_mv")   # the S' v kernel alone (inside "sr")
+        sr_mv = {"ms": ms / steps, "launches": n / steps}
         ctx.timing(False)
         lloc_rows = int(ctx.connections(sig, sigp)[0].sum().item())
         t_max = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
         if world > 1:
             dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        out = {"t_ms": float(t_max.item()), "groups": groups, "launches": launches, "lloc_rows": lloc_rows,
+        out = {"t_ms": float(t_max.item()), "groups": groups, "sr_mv": sr_mv, "launches": launches,
+               "lloc_rows": lloc_rows,
                "costs": costs, "sr_iters": sr_iters, "clocks": clk.summary(), "P": ctx.P}
         if e2e:
             # end to end through the public API with host buffers (copies inside the timed region)
@@ -229,15 +232,16 @@ def run_ours(args) -> dict | None:
         roof.update({"kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "algorithmic_per_launch": flops / max(1, groups[dom]["launches"])})
     else:
-        # SR: each CG iteration streams O (Ns x P complex FP32) twice; the group's time includes its small
-        # vector kernels, so this is a lower bound on the streaming kernels' bandwidth
-        it = statistics.mean(main["sr_iters"]) if main["sr_iters"] else 0
-        byts = (2 * it + 2 + 2) * N_SAMPLES * P * 8
-        achieved = byts / (groups[dom]["ms"] * 1e-3) / 1e9
+        # SR: the dominant work is the S' v product of each CG iteration (k_sr_tpart + k_sr_wpart and their
+        # small reductions, timed product by product): it streams O (Ns x P complex FP32) from HBM twice
+        mv = main["sr_mv"]
+        byts = 2 * N_SAMPLES * P * 8
+        achieved = byts * mv["launches"] / (mv["ms"] * 1e-3) / 1e9 if mv["ms"] else 0.0
         peak = float(peaks.get("hbm_gbs", 6781.4))
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)",
-                "algorithmic_per_launch": byts / max(1, groups[dom]["launches"])}
+        roof = {"bound": "hbm", "kernel": "S' v product (k_sr_tpart + k_sr_wpart, group sr_mv)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)", "algorithmic_per_launch": byts,
+                "products_per_step": mv["launches"], "ms_per_product": mv["ms"] / max(1e-9, mv["launches"])}
     fwd_tflops = fwd_evals * F_EVAL / (groups["fwd"]["ms"] * 1e-3) / 1e12 if groups["fwd"]["ms"] else None
     res = {
         "metric": METRIC,

@@ -176,7 +176,8 @@ tdo_status tdo_timing(tdo_ctx *ctx, int enable);
 /* Total recorded device time (ms) and launches of a kernel group since tdo_timing(ctx, 1):
  * "fwd" (transformer forward), "sample" (Metropolis), "bwd_vjp" (gradient backward), "bwd_jac"
  * (log-derivatives), "conn" (connections, scan, compaction), "lloc" (L_loc, cost, cotangents),
- * "sr" (CG solve), "update" (parameter update and refresh), or "all".  Synchronises the stream. */
+ * "sr" (CG solve), "sr_mv" (the S' v products inside "sr", each launch bracketed on its own), "update"
+ * (parameter update and refresh), or "all" (every group but "sr_mv").  Synchronises the stream. */
 tdo_status tdo_timing_read(tdo_ctx *ctx, const char *group, double *ms, long long *launches);
 
 /* Iterations and final relative residual of the last tdo_sr_step's CG solve. */

@@ -234,10 +234,11 @@ struct MlpGeo {
   static constexpr int DX_OFF = X_OFF + IMG;           // dX (BF16) [128][D]
   static constexpr int G_OFF = DX_OFF + IMG;           // G  [128][HC]
   static constexpr int DU_OFF = G_OFF + kRows * HC * 2;  // dU [128][HC]
-  static constexpr int M_OFF = DU_OFF + kRows * HC * 2;  // misc: bars, holder, db1[HC], db2[D]
-  static constexpr int BYTES = M_OFF + 64 + 4 * HC + 4 * D;
-  // TMEM columns
-  static constexpr int C_U = 0, C_DG = 128, C_DX = 256, C_W1 = 320, C_W2 = 384;
+  static constexpr int ONE_OFF = DU_OFF + kRows * HC * 2;  // all-ones [128][16] (row sums by MMA)
+  static constexpr int M_OFF = ONE_OFF + kRows * 16 * 2;    // misc: bars, holder, db2[D]
+  static constexpr int BYTES = M_OFF + 64 + 4 * D;
+  // TMEM columns (C_B1: db1 = dU^T 1, every one of its 16 columns holds the same sums)
+  static constexpr int C_U = 0, C_DG = 128, C_DX = 256, C_W1 = 320, C_W2 = 384, C_B1 = 448;
 };
 
 struct MlpArgs {
@@ -262,15 +263,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_mlp(MlpArgs a) {
   constexpr int HALF = D / 2, HH = G::HC / 2;
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
-  float *db1 = reinterpret_cast<float *>(sm + G::M_OFF + 64);
-  float *db2 = db1 + G::HC;
-  for (int i = threadIdx.x; i < G::HC + D; i += kThreads) db1[i] = 0.f;
+  float *db2 = reinterpret_cast<float *>(sm + G::M_OFF + 64);
+  for (int i = threadIdx.x; i < D; i += kThreads) db2[i] = 0.f;
+  for (int i = threadIdx.x; i < kRows * 16 / 8; i += kThreads)   // bf16 1.0 = 0x3F80
+    reinterpret_cast<uint4 *>(sm + G::ONE_OFF)[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (warp & 3) + lane, half = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
   const uint32_t w1t = smem_u32(sm + G::W1T_OFF), w2 = smem_u32(sm + G::W2_OFF), w1 = smem_u32(sm + G::W1_OFF);
   const uint32_t xs = smem_u32(sm + G::X_OFF), dxs = smem_u32(sm + G::DX_OFF), gs = smem_u32(sm + G::G_OFF),
-                 dus = smem_u32(sm + G::DU_OFF);
+                 dus = smem_u32(sm + G::DU_OFF), ones = smem_u32(sm + G::ONE_OFF);
+  fence_proxy_async();   // the ones image is read by the tensor cores
   // weights once per kernel
   if (threadIdx.x == 0) {
     mbar_expect_tx(s.bar_ld, 3 * G::HC * D * 2);
@@ -327,11 +330,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_mlp(MlpArgs a) {
         st_row8(sm + G::G_OFF, row, half * HH + j + 8, G::HC, gl + 8);
         st_row8(sm + G::DU_OFF, row, half * HH + j, G::HC, du);
         st_row8(sm + G::DU_OFF, row, half * HH + j + 8, G::HC, du + 8);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const float t = warp_sum_f(du[e]);
-          if (lane == 0) atomicAdd(&db1[half * HH + j + e], t);
-        }
       }
       tc_fence_before();
       fence_proxy_async();
@@ -341,6 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_mlp(MlpArgs a) {
         mma_kk(s, dus, w1, G::HC, D, G::C_DX, false);              // dX' part = dU W1_c^T
         mma_mm(s, dus, G::HC, xs, D, D, G::C_W1, !first);          // dW1_c^T += dU^T Xmid
         mma_mm(s, gs, G::HC, dxs, D, D, G::C_W2, !first);          // dW2_c   += G^T dX
+        mma_mm(s, dus, G::HC, ones, 16, 16, G::C_B1, !first);       // db1_c   += dU^T 1
         mma_commit(s.bar_mma);
       }
       ok = wait_mma(s);
@@ -366,8 +365,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_mlp(MlpArgs a) {
     // dW1_c^T block: lane m = hidden unit (of this half), column n = input feature i
     flush_block(s, G::C_W1, D, g, [&](int m, int n) -> long long { return a.off_w1 + (long long)n * F + m; });
     flush_block(s, G::C_W2, D, g, [&](int m, int n) -> long long { return a.off_w2 + (long long)m * D + n; });
+    if (half == 0) {   // lane m of the db1 accumulator = hidden unit m of this half
+      float v[16];
+      tmem_ld16(s.tmem + lane_addr + G::C_B1, v);
+      atomicAdd(g + a.off_b1 + row, v[0]);
+    }
     __syncthreads();
-    for (int i = threadIdx.x; i < G::HC; i += kThreads) atomicAdd(g + a.off_b1 + i, db1[i]);
     if (a.do_db2)
       for (int i = threadIdx.x; i < D; i += kThreads) atomicAdd(g + a.off_b2 + i, db2[i]);
   }

@@ -18,6 +18,7 @@ constexpr int kRun = 32;     // FP32 products per FP64 accumulation
 enum {
   S_RZ = 0, S_BN, S_AL, S_RN, S_DONE, S_IT, S_TOL, S_PAP, S_CR, S_CI, S_TR, S_TI, S_COUNT
 };
+// S_DONE: 1 converged, 2 breakdown (S' not positive definite)
 
 __device__ __forceinline__ double block_sum_d(double v, double *sh) {
   v = warp_sum_d(v);
@@ -39,52 +40,42 @@ __device__ __forceinline__ double sum_parts(const double *part, int n, double *s
   return block_sum_d(a, sh);
 }
 
-// mean[k] = (1/Ns) sum_s O[s][k]   (thread per k, 4 independent loads in flight)
-__global__ void k_sr_mean(const float2 *__restrict__ O, size_t Ns, size_t P, double2 *__restrict__ mean) {
+// mean[k] = (1/Ns) sum_s O[s][k] and the Jacobi preconditioner diag[k] = (1/Ns) sum_s |O[s][k]|^2 -
+// |mean[k]|^2 + shift (the variance of O_k floored at 0; 1 where that sum is 0), in one pass over O: thread per k, 4
+// independent loads in flight, FP32 runs of kRun samples accumulated in FP64.  The preconditioner only
+// sets the CG's convergence rate, so the one-pass variance formula is accurate enough for it.
+__global__ void k_sr_moments(const float2 *__restrict__ O, size_t Ns, size_t P, double shift,
+                             double2 *__restrict__ mean, double *__restrict__ diag) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
-    double ar = 0.0, ai = 0.0;
+    double ar = 0.0, ai = 0.0, aa = 0.0;
     for (size_t s0 = 0; s0 < Ns; s0 += kRun) {
       const size_t s1 = s0 + kRun < Ns ? s0 + kRun : Ns;
-      float fr[4] = {0, 0, 0, 0}, fi[4] = {0, 0, 0, 0};
-      size_t s = s0;
-      for (; s + 4 <= s1; s += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) { const float2 o = __ldg(O + (s + u) * P + k); fr[u] += o.x; fi[u] += o.y; }
-      }
-      for (; s < s1; ++s) { const float2 o = __ldg(O + s * P + k); fr[0] += o.x; fi[0] += o.y; }
-      ar += (double)((fr[0] + fr[1]) + (fr[2] + fr[3]));
-      ai += (double)((fi[0] + fi[1]) + (fi[2] + fi[3]));
-    }
-    mean[k] = make_double2(ar / (double)Ns, ai / (double)Ns);
-  }
-}
-
-// diag[k] = (1/Ns) sum_s |O[s][k] - mean[k]|^2 + shift   (Jacobi preconditioner of S + shift I)
-__global__ void k_sr_diag(const float2 *__restrict__ O, size_t Ns, size_t P, const double2 *__restrict__ mean,
-                          double shift, double *__restrict__ diag) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
-    const float mr = (float)mean[k].x, mi = (float)mean[k].y;
-    double a = 0.0;
-    for (size_t s0 = 0; s0 < Ns; s0 += kRun) {
-      const size_t s1 = s0 + kRun < Ns ? s0 + kRun : Ns;
-      float f[4] = {0, 0, 0, 0};
+      float fr[4] = {0, 0, 0, 0}, fi[4] = {0, 0, 0, 0}, fa[4] = {0, 0, 0, 0};
       size_t s = s0;
       for (; s + 4 <= s1; s += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float2 o = __ldg(O + (s + u) * P + k);
-          const float dr = o.x - mr, di = o.y - mi;
-          f[u] = fmaf(dr, dr, fmaf(di, di, f[u]));
+          fr[u] += o.x;
+          fi[u] += o.y;
+          fa[u] = fmaf(o.x, o.x, fmaf(o.y, o.y, fa[u]));
         }
       }
       for (; s < s1; ++s) {
         const float2 o = __ldg(O + s * P + k);
-        const float dr = o.x - mr, di = o.y - mi;
-        f[0] = fmaf(dr, dr, fmaf(di, di, f[0]));
+        fr[0] += o.x;
+        fi[0] += o.y;
+        fa[0] = fmaf(o.x, o.x, fmaf(o.y, o.y, fa[0]));
       }
-      a += (double)((f[0] + f[1]) + (f[2] + f[3]));
+      ar += (double)((fr[0] + fr[1]) + (fr[2] + fr[3]));
+      ai += (double)((fi[0] + fi[1]) + (fi[2] + fi[3]));
+      aa += (double)((fa[0] + fa[1]) + (fa[2] + fa[3]));
     }
-    diag[k] = a / (double)Ns + shift;
+    const double mr = ar / (double)Ns, mi = ai / (double)Ns;
+    mean[k] = make_double2(mr, mi);
+    const double var = aa / (double)Ns - (mr * mr + mi * mi);
+    const double dk = (var > 0.0 ? var : 0.0) + shift;
+    diag[k] = dk > 0.0 ? dk : 1.0;   // a constant O_k with no shift: leave that coordinate unscaled
   }
 }
 
@@ -172,35 +163,92 @@ __global__ void k_sr_tsum(const float2 *__restrict__ t, size_t Ns, double *__res
   if (threadIdx.x == 0) { sc[S_TR] = a; sc[S_TI] = b; }
 }
 
-// Ap[k] = (1/Ns) [sum_s Re(conj(O[s][k]) t[s]) - Re(conj(mean[k]) T)] + shift p[k]; partials of p . Ap.
-__global__ void k_sr_w(const float2 *__restrict__ O, size_t Ns, size_t P, const double2 *__restrict__ mean,
-                       const float2 *__restrict__ t, const double *__restrict__ p, double shift,
-                       double *__restrict__ Ap, double *__restrict__ part, const double *__restrict__ sc) {
+// Partial products w = Re(O^H t) over one chunk of kChunk parameters and one sample group: block
+// (chunk, sg) streams the chunk (8 KB contiguous) of every sample row of its group, each thread owning
+// 4 consecutive parameters (two 16-byte loads per row when rows are 16-byte aligned, i.e. P even), with
+// the group's t in shared memory.  FP32 runs of kRun rows, FP64 across runs.
+// wpart[sg][k] = sum_{s in group sg} Re(conj(O[s][k]) t[s]).
+constexpr int kWRows = 2048;   // t values of a sample group staged at a time (16 KB)
+template <bool VEC>
+__global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const float2 *__restrict__ O, size_t Ns, size_t P,
+                                                       const float2 *__restrict__ t, double *__restrict__ wpart,
+                                                       const double *__restrict__ sc) {
+  __shared__ float2 ts[kWRows];
+  if (sc[S_DONE] != 0.0) return;
+  const size_t k = (size_t)blockIdx.x * kChunk + 4 * threadIdx.x;
+  const int kn = k < P ? (int)(P - k < 4 ? P - k : 4) : 0;
+  const size_t per = (Ns + kSampleGroups - 1) / kSampleGroups;
+  const size_t s_begin = (size_t)blockIdx.y * per;
+  const size_t s_end = s_begin + per < Ns ? s_begin + per : Ns;
+  double w[4] = {0.0, 0.0, 0.0, 0.0};
+  for (size_t g0 = s_begin; g0 < s_end; g0 += kWRows) {
+    const int gn = (int)(s_end - g0 < (size_t)kWRows ? s_end - g0 : (size_t)kWRows);
+    __syncthreads();
+    for (int i = threadIdx.x; i < gn; i += blockDim.x) ts[i] = t[g0 + i];
+    __syncthreads();
+    if (kn == 0) continue;
+    for (int r0 = 0; r0 < gn; r0 += kRun) {
+      const int r1 = r0 + kRun < gn ? r0 + kRun : gn;
+      float f[4] = {0.f, 0.f, 0.f, 0.f};
+      if (VEC && kn == 4) {
+        int r = r0;
+        for (; r + 4 <= r1; r += 4) {
+          float4 a[4], b[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 *row = reinterpret_cast<const float4 *>(O + (g0 + r + u) * P + k);
+            a[u] = __ldcs(row);
+            b[u] = __ldcs(row + 1);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 tv = ts[r + u];
+            f[0] = fmaf(a[u].x, tv.x, fmaf(a[u].y, tv.y, f[0]));
+            f[1] = fmaf(a[u].z, tv.x, fmaf(a[u].w, tv.y, f[1]));
+            f[2] = fmaf(b[u].x, tv.x, fmaf(b[u].y, tv.y, f[2]));
+            f[3] = fmaf(b[u].z, tv.x, fmaf(b[u].w, tv.y, f[3]));
+          }
+        }
+        for (; r < r1; ++r) {
+          const float4 *row = reinterpret_cast<const float4 *>(O + (g0 + r) * P + k);
+          const float4 a = __ldcs(row), b = __ldcs(row + 1);
+          const float2 tv = ts[r];
+          f[0] = fmaf(a.x, tv.x, fmaf(a.y, tv.y, f[0]));
+          f[1] = fmaf(a.z, tv.x, fmaf(a.w, tv.y, f[1]));
+          f[2] = fmaf(b.x, tv.x, fmaf(b.y, tv.y, f[2]));
+          f[3] = fmaf(b.z, tv.x, fmaf(b.w, tv.y, f[3]));
+        }
+      } else {
+        for (int r = r0; r < r1; ++r) {
+          const float2 tv = ts[r];
+          const float2 *row = O + (g0 + r) * P + k;
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (e < kn) {
+              const float2 o = __ldcs(row + e);
+              f[e] = fmaf(o.x, tv.x, fmaf(o.y, tv.y, f[e]));
+            }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) w[e] += (double)f[e];
+    }
+  }
+  for (int e = 0; e < kn; ++e) wpart[(size_t)blockIdx.y * P + k + e] = w[e];
+}
+
+// Ap[k] = (1/Ns) [sum_sg wpart[sg][k] - Re(conj(mean[k]) T)] + shift p[k]; partials of p . Ap.
+__global__ void k_sr_wfin(size_t Ns, size_t P, const double2 *__restrict__ mean, const double *__restrict__ wpart,
+                          const double *__restrict__ p, double shift, double *__restrict__ Ap,
+                          double *__restrict__ part, const double *__restrict__ sc) {
   __shared__ double sh[32];
   if (sc[S_DONE] != 0.0) return;
   const double Tr = sc[S_TR], Ti = sc[S_TI];
   double loc = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
     double a = 0.0;
-    for (size_t s0 = 0; s0 < Ns; s0 += kRun) {
-      const size_t s1 = s0 + kRun < Ns ? s0 + kRun : Ns;
-      float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      size_t s = s0;
-      for (; s + 8 <= s1; s += 8) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float2 o = __ldg(O + (s + u) * P + k);
-          const float2 ts = t[s + u];
-          f[u] = fmaf(o.x, ts.x, fmaf(o.y, ts.y, f[u]));
-        }
-      }
-      for (; s < s1; ++s) {
-        const float2 o = __ldg(O + s * P + k);
-        const float2 ts = t[s];
-        f[0] = fmaf(o.x, ts.x, fmaf(o.y, ts.y, f[0]));
-      }
-      a += (double)(((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])));
-    }
+    for (int g = 0; g < kSampleGroups; ++g) a += wpart[(size_t)g * P + k];
     const double2 m = mean[k];
     const double v = (a - (m.x * Tr + m.y * Ti)) / (double)Ns + shift * p[k];
     Ap[k] = v;
@@ -314,12 +362,14 @@ __global__ void k_sr_clear(double *__restrict__ sc) {
   if (threadIdx.x < S_COUNT) sc[threadIdx.x] = 0.0;
 }
 
+
 struct SrPtrs {
   double2 *mean;
   double *diag, *r, *z, *p, *Ap, *part, *part2, *part3, *sc;
   float *vf;
   float2 *t;
   double2 *tpart;
+  double *wpart;
 };
 
 // Carves the workspace; every region starts on a 16-byte boundary (double2 / float2 / float4 access).
@@ -341,20 +391,25 @@ static SrPtrs sr_carve(double *work, size_t Ns, size_t P) {
   q.vf = reinterpret_cast<float *>(take(4 * P));
   q.t = reinterpret_cast<float2 *>(take(8 * Ns));
   q.tpart = reinterpret_cast<double2 *>(take(16 * ((P + kChunk - 1) / kChunk) * Ns));
+  q.wpart = reinterpret_cast<double *>(take(8 * kSampleGroups * P));
   return q;
 }
 
 // S' v -> Ap (and the partials of v . Ap in q.part), all on the device.
+// S' v -> Ap (and the partials of v . Ap in q.part), all on the device: 7 launches, O streamed twice.
 static void matvec(const float2 *O, size_t Ns, size_t P, const double *v, double shift, SrPtrs &q, int nb,
-                   int ngrid_t, cudaStream_t st) {
-  (void)ngrid_t;
+                   cudaStream_t st) {
   const int nchunks = (int)((P + kChunk - 1) / kChunk);
   k_sr_vprep<<<nb, kSrBlock, 0, st>>>(P, v, q.mean, q.vf, q.part, q.part2, q.sc);
   k_sr_cfin<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
   k_sr_tpart<<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.vf, q.tpart, q.sc);
   k_sr_tred<<<(unsigned)((Ns + 255) / 256), 256, 0, st>>>(q.tpart, nchunks, Ns, q.t, q.sc);
   k_sr_tsum<<<1, 1024, 0, st>>>(q.t, Ns, q.sc);
-  k_sr_w<<<nb, kSrBlock, 0, st>>>(O, Ns, P, q.mean, q.t, v, shift, q.Ap, q.part, q.sc);
+  if (P % 2 == 0)   // every row starts on a 16-byte boundary
+    k_sr_wpart<true><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.t, q.wpart, q.sc);
+  else
+    k_sr_wpart<false><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.t, q.wpart, q.sc);
+  k_sr_wfin<<<nb, kSrBlock, 0, st>>>(Ns, P, q.mean, q.wpart, v, shift, q.Ap, q.part, q.sc);
 }
 
 }  // namespace tdo
@@ -363,30 +418,45 @@ size_t sr_work_doubles(size_t Ns, size_t P) {
   // the regions carved by sr_carve, each rounded up to 16 bytes, plus slack
   const size_t nchunks = (P + tdo::kChunk - 1) / tdo::kChunk;
   const size_t bytes = 16 * P + 5 * (8 * P + 16) + 3 * 8 * 1024 + 8 * 32 + (4 * P + 16) + (8 * Ns + 16) +
-                       16 * nchunks * Ns + 64;
+                       16 * nchunks * Ns + 16 + 8 * tdo::kSampleGroups * P + 16 + 64;
   return (bytes + 7) / 8;
 }
 
+// mv_ev (optional): mv_cap event pairs recorded around the S' v launches; *mv_used = pairs recorded.
 cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, const double *x0, double shift,
                        double tol, int max_iter, double *x, double *work, int n_sm, int *iters, double *resid,
-                       long long *launches, cudaStream_t st) {
+                       long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used, cudaStream_t st) {
   using namespace tdo;
+  (void)n_sm;
   SrPtrs q = sr_carve(work, Ns, P);
   const float2 *O2 = reinterpret_cast<const float2 *>(O);
   int nb = (int)((P + kSrBlock - 1) / kSrBlock);
   if (nb > 1024) nb = 1024;
   if (nb < 1) nb = 1;
-  const int ngrid_t = n_sm;
   long long nl = 0;
-  k_sr_mean<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, q.mean);
-  k_sr_diag<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, q.mean, shift, q.diag);
+  int nmv = 0;
+  if (mv_used) *mv_used = 0;
+  auto mv = [&](const double *v) -> cudaError_t {
+    const bool rec = mv_ev && nmv < mv_cap;
+    if (rec) cudaEventRecord(mv_ev[2 * nmv], st);
+    matvec(O2, Ns, P, v, shift, q, nb, st);
+    nl += 7;
+    if (rec) {
+      cudaEventRecord(mv_ev[2 * nmv + 1], st);
+      ++nmv;
+      if (mv_used) *mv_used = nmv;
+    }
+    return cudaSuccess;
+  };
+  k_sr_moments<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, shift, q.mean, q.diag);
   k_sr_clear<<<1, 32, 0, st>>>(q.sc);
-  nl += 3;
-  if (x0) { matvec(O2, Ns, P, x0, shift, q, nb, ngrid_t > 0 ? ngrid_t : 1, st); nl += 6; }
+  nl += 2;
+  cudaError_t e;
+  if (x0 && (e = mv(x0)) != cudaSuccess) return e;
   k_sr_init<<<nb, kSrBlock, 0, st>>>(P, rhs, x0, q.Ap, x, q.r, q.z, q.p, q.diag, q.part, q.part2, q.part3);
   k_sr_init_scalars<<<1, 1024, 0, st>>>(q.part, q.part2, q.part3, nb, tol, q.sc);
   nl += 2;
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // Iterations are launched in groups; the done flag on the device makes the rest of a group a no-op,
   // and the host looks at it between groups only.
@@ -396,12 +466,12 @@ cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, c
   for (int it = 0; it < max_iter;) {
     const int end = it + group < max_iter ? it + group : max_iter;
     for (; it < end; ++it) {
-      matvec(O2, Ns, P, q.p, shift, q, nb, ngrid_t > 0 ? ngrid_t : 1, st);
+      if ((e = mv(q.p)) != cudaSuccess) return e;
       k_sr_alpha<<<1, 1024, 0, st>>>(q.part, nb, q.sc);
       k_sr_xr<<<nb, kSrBlock, 0, st>>>(P, x, q.r, q.z, q.p, q.Ap, q.diag, q.part, q.part2, q.sc);
       k_sr_beta<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
       k_sr_p<<<nb, kSrBlock, 0, st>>>(P, q.p, q.z, q.sc);
-      nl += 10;
+      nl += 4;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -418,6 +488,10 @@ cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, c
     if (e != cudaSuccess) return e;
   }
   if (iters) *iters = (int)h[S_IT];
+  if (mv_used) {   // launches after convergence returned at once: keep the pairs of real products only
+    const int real = (x0 ? 1 : 0) + (int)h[S_IT] + (h[S_DONE] == 1.0 ? 0 : 1);
+    if (*mv_used > real) *mv_used = real;
+  }
   if (resid) *resid = h[S_BN] > 0 ? sqrt(h[S_RN] / h[S_BN]) : 0.0;
   if (launches) *launches = nl;
   if (h[S_DONE] == 2.0) return cudaErrorInvalidValue;   // not positive definite
