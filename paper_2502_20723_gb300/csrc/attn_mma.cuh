@@ -1,0 +1,207 @@
+// Softmax attention of one (sequence, head) pair on one warp with warp-level tensor-core MMAs
+// (mma.sync m16n8k16 / m16n8k8, FP16 operands, FP32 accumulation), for sequences of at most 16
+// tokens and head dimension HD in {8, 16} (Eq. attn-head-appendix and its derivative).
+//
+// A 16 x 16 score block is 1/8 of one tcgen05 tile and lives in registers across the whole
+// forward-and-backward of the pair, so these blocks use the warp-synchronous MMA, while the
+// projections around them use tcgen05.  Fragment layouts (m16n8k16, lane = 4 g + t):
+//   A [16][16]: a0 = (g, 2t..2t+1), a1 = (g+8, 2t..), a2 = (g, 8+2t..), a3 = (g+8, 8+2t..)
+//   B [16][8] : b0 = (k = 2t..2t+1, n = g), b1 = (k = 8+2t.., n = g)
+//   C [16][8] : c0,c1 = (g, 2t..2t+1), c2,c3 = (g+8, 2t..2t+1)
+// m16n8k8 uses a0, a1 and b0 only.  The C fragments of the two key halves of a score block are,
+// packed pairwise, the A fragment of the same block, and movmatrix transposes an 8 x 8 piece.
+#pragma once
+#include <cstdint>
+
+#include "tcgen05.cuh"
+
+namespace tdo {
+namespace amma {
+
+__device__ __forceinline__ uint32_t h2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma1688(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(b0));
+}
+
+__device__ __forceinline__ uint32_t trans8(uint32_t x) {
+  uint32_t r;
+  asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(r) : "r"(x));
+  return r;
+}
+
+__device__ __forceinline__ void zero4(float (&d)[4]) { d[0] = d[1] = d[2] = d[3] = 0.f; }
+
+// S = A B^T over the feature dimension for a [16 rows][HD] A block and a [16 keys][HD] B block, both
+// FP32 in shared memory (row stride ld, rows >= n read as 0).  Returns the two key halves s[0], s[1].
+template <int HD>
+__device__ __forceinline__ void scores(const float *A, const float *B, int ld, int n, float ascale, float (&s)[2][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  auto ld2 = [&](const float *M, int r, int c, float sc) -> uint32_t {
+    return r < n ? h2(M[r * ld + c] * sc, M[r * ld + c + 1] * sc) : 0u;
+  };
+#pragma unroll
+  for (int j = 0; j < 2; ++j) zero4(s[j]);
+  if (HD == 8) {
+    const uint32_t a0 = ld2(A, g, 2 * t, ascale), a1 = ld2(A, g + 8, 2 * t, ascale);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) mma1688(s[j], a0, a1, ld2(B, 8 * j + g, 2 * t, 1.f));
+  } else {
+    const uint32_t a[4] = {ld2(A, g, 2 * t, ascale), ld2(A, g + 8, 2 * t, ascale), ld2(A, g, 8 + 2 * t, ascale),
+                           ld2(A, g + 8, 8 + 2 * t, ascale)};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) mma16816(s[j], a, ld2(B, 8 * j + g, 2 * t, 1.f), ld2(B, 8 * j + g, 8 + 2 * t, 1.f));
+  }
+}
+
+// Y[16 rows][HD] = X[16][16 keys] M[16 keys][HD] with X given as an A fragment and M FP32 in shared
+// memory (row stride ld, rows >= n read as 0): out[c] holds features 8c .. 8c+7.
+template <int HD>
+__device__ __forceinline__ void times_rows(const uint32_t (&x)[4], const float *M, int ld, int n,
+                                           float (&out)[HD / 8][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  auto col2 = [&](int r, int c) -> uint32_t {   // (M[r][c], M[r+1][c])
+    const float lo = r < n ? M[r * ld + c] : 0.f, hi = r + 1 < n ? M[(r + 1) * ld + c] : 0.f;
+    return h2(lo, hi);
+  };
+#pragma unroll
+  for (int c = 0; c < HD / 8; ++c) {
+    zero4(out[c]);
+    mma16816(out[c], x, col2(2 * t, 8 * c + g), col2(8 + 2 * t, 8 * c + g));
+  }
+}
+
+// Forward and backward of softmax attention for one (sequence, head) on one warp.
+//   Q, K, V, dH: FP32 [n][ld] blocks of this head (column 0 = the head's first feature), n <= 16.
+//   qscale: 1/sqrt(HD) * log2(e) (scores in base 2); scale: 1/sqrt(HD).
+//   emit(kind, row, col, v0, v1): kind 0 = attention output O, 1 = dQ, 2 = dK, 3 = dV, for
+//   (row, col..col+1) with row < n.
+template <int HD, typename EMIT>
+__device__ __forceinline__ void attn_fwd_bwd(const float *Q, const float *K, const float *V, const float *dH, int ld,
+                                             int n, float qscale, float scale, EMIT emit) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float s[2][4];
+  scores<HD>(Q, K, ld, n, qscale, s);
+  // softmax over the keys of rows g (s[.][0..1]) and g + 8 (s[.][2..3]); keys >= n masked
+  float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const bool ok = 8 * j + 2 * t + e < n;
+      s[j][e] = ok ? s[j][e] : -INFINITY;
+      s[j][2 + e] = ok ? s[j][2 + e] : -INFINITY;
+      m0 = fmaxf(m0, s[j][e]);
+      m1 = fmaxf(m1, s[j][2 + e]);
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      s[j][e] = tc::ex2_fast(s[j][e] - m0);
+      s[j][2 + e] = tc::ex2_fast(s[j][2 + e] - m1);
+      l0 += s[j][e];
+      l1 += s[j][2 + e];
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+  }
+  const float i0 = 1.f / l0, i1 = 1.f / l1;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    s[j][0] *= i0; s[j][1] *= i0;
+    s[j][2] *= i1; s[j][3] *= i1;
+  }
+  const uint32_t pa[4] = {h2(s[0][0], s[0][1]), h2(s[0][2], s[0][3]), h2(s[1][0], s[1][1]), h2(s[1][2], s[1][3])};
+  // O = P V
+  {
+    float o[HD / 8][4];
+    times_rows<HD>(pa, V, ld, n, o);
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      if (g < n) emit(0, g, 8 * c + 2 * t, o[c][0], o[c][1]);
+      if (g + 8 < n) emit(0, g + 8, 8 * c + 2 * t, o[c][2], o[c][3]);
+    }
+  }
+  // dA = dH V^T; delta_i = sum_j P_ij dA_ij; dS = scale P (dA - delta)
+  float da[2][4];
+  scores<HD>(dH, V, ld, n, 1.f, da);
+  float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    d0 = fmaf(s[j][0], da[j][0], fmaf(s[j][1], da[j][1], d0));
+    d1 = fmaf(s[j][2], da[j][2], fmaf(s[j][3], da[j][3], d1));
+  }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    da[j][0] = scale * s[j][0] * (da[j][0] - d0);
+    da[j][1] = scale * s[j][1] * (da[j][1] - d0);
+    da[j][2] = scale * s[j][2] * (da[j][2] - d1);
+    da[j][3] = scale * s[j][3] * (da[j][3] - d1);
+  }
+  const uint32_t x00 = h2(da[0][0], da[0][1]), x10 = h2(da[0][2], da[0][3]), x01 = h2(da[1][0], da[1][1]),
+                 x11 = h2(da[1][2], da[1][3]);
+  // dQ = dS K
+  {
+    const uint32_t dsa[4] = {x00, x10, x01, x11};
+    float y[HD / 8][4];
+    times_rows<HD>(dsa, K, ld, n, y);
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      if (g < n) emit(1, g, 8 * c + 2 * t, y[c][0], y[c][1]);
+      if (g + 8 < n) emit(1, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
+    }
+  }
+  // dK = dS^T Q, dV = P^T dH (transposed A fragments: block (I, J) of X^T is block (J, I) of X transposed)
+  {
+    const uint32_t dst[4] = {trans8(x00), trans8(x01), trans8(x10), trans8(x11)};
+    float y[HD / 8][4];
+    times_rows<HD>(dst, Q, ld, n, y);
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      if (g < n) emit(2, g, 8 * c + 2 * t, y[c][0], y[c][1]);
+      if (g + 8 < n) emit(2, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
+    }
+  }
+  {
+    const uint32_t pt[4] = {trans8(pa[0]), trans8(pa[2]), trans8(pa[1]), trans8(pa[3])};
+    float y[HD / 8][4];
+    times_rows<HD>(pt, dH, ld, n, y);
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      if (g < n) emit(3, g, 8 * c + 2 * t, y[c][0], y[c][1]);
+      if (g + 8 < n) emit(3, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
+    }
+  }
+}
+
+}  // namespace amma
+}  // namespace tdo

@@ -19,6 +19,7 @@
 // image's feature dimension, K = the 128 rows of the tile.
 #include <cuda_bf16.h>
 
+#include "attn_mma.cuh"
 #include "tcgen05.cuh"
 #include "tdo_device.cuh"
 
@@ -138,17 +139,18 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 
 // Flush a TMEM accumulator block [128 lanes][N cols] (this thread: lane m, its half of the columns) to
 // the gradient accumulator with index(m, n) (negative = skip).
-template <typename IDX>
+// NQ = threads / 128 column groups (warp >> 2); N / NQ must be a multiple of 16.
+template <typename IDX, int NQ = 2>
 __device__ __forceinline__ void flush_block(const Sync &s, uint32_t col, int N, float *g, IDX idx) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m = 32 * (warp & 3) + lane, half = warp >> 2;
+  const int m = 32 * (warp & 3) + lane, cg = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
-  for (int j = 0; j < N / 2; j += 16) {
+  for (int j = 0; j < N / NQ; j += 16) {
     float v[16];
-    tmem_ld16(s.tmem + lane_addr + col + half * (N / 2) + j, v);
+    tmem_ld16(s.tmem + lane_addr + col + cg * (N / NQ) + j, v);
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-      const long long k = idx(m, half * (N / 2) + j + e);
+      const long long k = idx(m, cg * (N / NQ) + j + e);
       if (k >= 0) atomicAdd(g + k, v[e]);
     }
   }
@@ -230,8 +232,8 @@ struct MlpGeo {
   static constexpr int W1T_OFF = 0;                    // [HC][D]  (U = Xmid W1_c)
   static constexpr int W2_OFF = W1T_OFF + HC * D * 2;  // [HC][D]  (dG = dX W2_c^T)
   static constexpr int W1_OFF = W2_OFF + HC * D * 2;   // [D][HC]  (dX' = dU W1_c^T)
-  static constexpr int X_OFF = W1_OFF + HC * D * 2;    // Xmid image [128][D]
-  static constexpr int DX_OFF = X_OFF + IMG;           // dX (BF16) [128][D]
+  static constexpr int X_OFF = W1_OFF + HC * D * 2;    // Xmid images [2][128][D] (the next tile's loads early)
+  static constexpr int DX_OFF = X_OFF + 2 * IMG;       // dX (BF16) [128][D]
   static constexpr int G_OFF = DX_OFF + IMG;           // G  [128][HC]
   static constexpr int DU_OFF = G_OFF + kRows * HC * 2;  // dU [128][HC]
   static constexpr int ONE_OFF = DU_OFF + kRows * HC * 2;  // all-ones [128][16] (row sums by MMA)
@@ -256,22 +258,28 @@ struct MlpArgs {
   int *err;
 };
 
+// 512 threads: thread (row, cg) owns a quarter of the hidden chunk's and of dX's columns; 16 warps hide
+// the latency of the CUDA-core phases.  The next tile's Xmid image is loaded during this tile.
+constexpr int kMlpThreads = 512;
+
 template <int D>
-__global__ void __launch_bounds__(kThreads, 1) k_bwd_mlp(MlpArgs a) {
+__global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   using G = MlpGeo<D>;
   extern __shared__ __align__(1024) uint8_t sm[];
-  constexpr int HALF = D / 2, HH = G::HC / 2;
+  constexpr int NQ = kMlpThreads / 128;
+  constexpr int QD = D / NQ, QH = G::HC / NQ;   // dX columns and hidden columns per thread
+  static_assert(QD % 16 == 0 && QH % 16 == 0, "column groups of 16");
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
   float *db2 = reinterpret_cast<float *>(sm + G::M_OFF + 64);
-  for (int i = threadIdx.x; i < D; i += kThreads) db2[i] = 0.f;
-  for (int i = threadIdx.x; i < kRows * 16 / 8; i += kThreads)   // bf16 1.0 = 0x3F80
+  for (int i = threadIdx.x; i < D; i += kMlpThreads) db2[i] = 0.f;
+  for (int i = threadIdx.x; i < kRows * 16 / 8; i += kMlpThreads)   // bf16 1.0 = 0x3F80
     reinterpret_cast<uint4 *>(sm + G::ONE_OFF)[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+  const int row = 32 * (warp & 3) + lane, cg = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
   const uint32_t w1t = smem_u32(sm + G::W1T_OFF), w2 = smem_u32(sm + G::W2_OFF), w1 = smem_u32(sm + G::W1_OFF);
-  const uint32_t xs = smem_u32(sm + G::X_OFF), dxs = smem_u32(sm + G::DX_OFF), gs = smem_u32(sm + G::G_OFF),
+  const uint32_t xs0 = smem_u32(sm + G::X_OFF), dxs = smem_u32(sm + G::DX_OFF), gs = smem_u32(sm + G::G_OFF),
                  dus = smem_u32(sm + G::DU_OFF), ones = smem_u32(sm + G::ONE_OFF);
   fence_proxy_async();   // the ones image is read by the tensor cores
   // weights once per kernel
@@ -284,29 +292,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_mlp(MlpArgs a) {
   bool ok = wait_ld(s);
   bool first = true;
   if (sync_ok(s, ok)) {
-    for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
-      load2(s, xs, a.xmid + tile * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
-      const size_t rg = (tile * kRows + row) * (size_t)D + half * HALF;
-      float dxo[HALF], base[HALF];
+    if ((size_t)blockIdx.x < a.tiles) load2(s, xs0, a.xmid + blockIdx.x * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+    int buf = 0;
+    for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, buf ^= 1) {
+      const uint32_t xs = xs0 + buf * G::IMG;
+      const size_t rg = (tile * kRows + row) * (size_t)D + cg * QD;
+      float dxo[QD], base[QD];
 #pragma unroll
-      for (int j = 0; j < HALF; j += 4) {
+      for (int j = 0; j < QD; j += 4) {
         const float4 v = *reinterpret_cast<const float4 *>(a.dxo + rg + j);
         dxo[j] = v.x; dxo[j + 1] = v.y; dxo[j + 2] = v.z; dxo[j + 3] = v.w;
         const float4 q = *reinterpret_cast<const float4 *>(a.base + rg + j);
         base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
       }
 #pragma unroll
-      for (int j = 0; j < HALF; j += 8) st_row8(sm + G::DX_OFF, row, half * HALF + j, D, dxo + j);
+      for (int j = 0; j < QD; j += 8) st_row8(sm + G::DX_OFF, row, cg * QD + j, D, dxo + j);
       if (a.do_db2) {
 #pragma unroll
-        for (int j = 0; j < HALF; ++j) {
+        for (int j = 0; j < QD; ++j) {
           const float t = warp_sum_f(dxo[j]);
-          if (lane == 0) atomicAdd(&db2[half * HALF + j], t);
+          if (lane == 0) atomicAdd(&db2[cg * QD + j], t);
         }
       }
-      ok = wait_ld(s);
+      ok = wait_ld(s);   // this tile's Xmid image
       fence_proxy_async();
       if (!sync_ok(s, ok)) break;
+      // the other buffer was last read by the previous tile's MMAs, which have completed
+      const size_t nxt = tile + gridDim.x;
+      if (nxt < a.tiles) load2(s, xs0 + (buf ^ 1) * G::IMG, a.xmid + nxt * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
       if (threadIdx.x == 0) {
         tc_fence_after();
         mma_kk(s, xs, w1t, D, G::HC, G::C_U, false);    // U  = Xmid W1_c
@@ -315,21 +328,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_mlp(MlpArgs a) {
       }
       ok = wait_mma(s);
       if (!sync_ok(s, ok)) break;
-      // dU = dG gelu'(U + b1), G = gelu(U + b1) -> shared images; db1 column sums
+      // dU = dG gelu'(U + b1), G = gelu(U + b1) -> shared images
 #pragma unroll
-      for (int j = 0; j < HH; j += 16) {
+      for (int j = 0; j < QH; j += 16) {
         float u[16], dg[16], gl[16], du[16];
-        tmem_ld16(s.tmem + lane_addr + G::C_U + half * HH + j, u);
-        tmem_ld16(s.tmem + lane_addr + G::C_DG + half * HH + j, dg);
+        tmem_ld16(s.tmem + lane_addr + G::C_U + cg * QH + j, u);
+        tmem_ld16(s.tmem + lane_addr + G::C_DG + cg * QH + j, dg);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const float uu = u[e] + __ldg(a.b1 + half * HH + j + e);
+          const float uu = u[e] + __ldg(a.b1 + cg * QH + j + e);
           du[e] = dg[e] * gelu_grad_fast(uu, &gl[e]);
         }
-        st_row8(sm + G::G_OFF, row, half * HH + j, G::HC, gl);
-        st_row8(sm + G::G_OFF, row, half * HH + j + 8, G::HC, gl + 8);
-        st_row8(sm + G::DU_OFF, row, half * HH + j, G::HC, du);
-        st_row8(sm + G::DU_OFF, row, half * HH + j + 8, G::HC, du + 8);
+        st_row8(sm + G::G_OFF, row, cg * QH + j, G::HC, gl);
+        st_row8(sm + G::G_OFF, row, cg * QH + j + 8, G::HC, gl + 8);
+        st_row8(sm + G::DU_OFF, row, cg * QH + j, G::HC, du);
+        st_row8(sm + G::DU_OFF, row, cg * QH + j + 8, G::HC, du + 8);
       }
       tc_fence_before();
       fence_proxy_async();
@@ -345,9 +358,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_mlp(MlpArgs a) {
       ok = wait_mma(s);
       if (!sync_ok(s, ok)) break;
 #pragma unroll
-      for (int j = 0; j < HALF; j += 16) {
+      for (int j = 0; j < QD; j += 16) {
         float v[16];
-        tmem_ld16(s.tmem + lane_addr + G::C_DX + half * HALF + j, v);
+        tmem_ld16(s.tmem + lane_addr + G::C_DX + cg * QD + j, v);
 #pragma unroll
         for (int e = 0; e < 16; e += 4)
           *reinterpret_cast<float4 *>(a.dxm + rg + j + e) =
@@ -363,16 +376,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_mlp(MlpArgs a) {
     float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
     const int F = a.F;
     // dW1_c^T block: lane m = hidden unit (of this half), column n = input feature i
-    flush_block(s, G::C_W1, D, g, [&](int m, int n) -> long long { return a.off_w1 + (long long)n * F + m; });
-    flush_block(s, G::C_W2, D, g, [&](int m, int n) -> long long { return a.off_w2 + (long long)m * D + n; });
-    if (half == 0) {   // lane m of the db1 accumulator = hidden unit m of this half
+    auto i1 = [&](int m, int n) -> long long { return a.off_w1 + (long long)n * F + m; };
+    auto i2 = [&](int m, int n) -> long long { return a.off_w2 + (long long)m * D + n; };
+    flush_block<decltype(i1), NQ>(s, G::C_W1, D, g, i1);
+    flush_block<decltype(i2), NQ>(s, G::C_W2, D, g, i2);
+    if (cg == 0) {   // lane m of the db1 accumulator = hidden unit m of this half
       float v[16];
       tmem_ld16(s.tmem + lane_addr + G::C_B1, v);
       atomicAdd(g + a.off_b1 + row, v[0]);
     }
     __syncthreads();
     if (a.do_db2)
-      for (int i = threadIdx.x; i < D; i += kThreads) atomicAdd(g + a.off_b2 + i, db2[i]);
+      for (int i = threadIdx.x; i < D; i += kMlpThreads) atomicAdd(g + a.off_b2 + i, db2[i]);
   }
   sync_finish(s);
 }
@@ -485,6 +500,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
     }
     __syncthreads();   // Q, K, V, dH of every row visible; Wo no longer read (stats reuse the region)
     uint8_t *dq_img = a.dqkv + tile * (size_t)(kRows * 3 * D * 2);
+    if (n <= 16) {
+      // ---- one warp per (sequence, head): warp-level MMAs (the 16 x 16 blocks stay in registers)
+      for (int i = threadIdx.x; i < (kRows - nvalid) * (3 * D / 8); i += kThreads) {   // padding rows: dQKV = 0
+        const int r = nvalid + i / (3 * D / 8), c8 = i % (3 * D / 8);
+        *reinterpret_cast<uint4 *>(dq_img + canon(r, 8 * c8, 3 * D)) = make_uint4(0, 0, 0, 0);
+      }
+      for (int u = warp; u < a.ts * heads; u += kThreads / 32) {
+        const int sq = u / heads, h = u % heads, rb = sq * n, off = rb * KS + h * HD;
+        amma::attn_fwd_bwd<HD>(Qs + off, Ks + off, Vs + off, dHs + off, KS, n, qscale, scale,
+                               [&](int kind, int r, int c, float v0, float v1) {
+                                 const int row = rb + r, col = h * HD + c;
+                                 if (kind == 0)
+                                   *reinterpret_cast<uint32_t *>(sm + G::H_OFF + canon(row, col, 128)) = pack_bf16(v0, v1);
+                                 else
+                                   *reinterpret_cast<uint32_t *>(dq_img + canon(row, (kind - 1) * D + col, 3 * D)) =
+                                       pack_bf16(v0, v1);
+                               });
+      }
+    } else {
     // ---- pass 1: this thread = query row; forward output (-> H image) and dQ
     const int h0 = half * (heads / 2), h1 = h0 + heads / 2;
     for (int h = h0; h < h1; ++h) {
@@ -569,6 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
         st_row8(dq_img, row, D + h * HD + e8, 3 * D, dk + e8);
         st_row8(dq_img, row, 2 * D + h * HD + e8, 3 * D, dv + e8);
       }
+    }
     }
     fence_proxy_async();
     if (!sync_ok(s, true)) break;
@@ -840,7 +875,7 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
         ma.off_b2 = b2[l];
         ma.F = m.ffn;
         ma.err = err;
-        k_bwd_mlp<D><<<grid, kThreads, MlpGeo<D>::BYTES, st>>>(ma);
+        k_bwd_mlp<D><<<grid, kMlpThreads, MlpGeo<D>::BYTES, st>>>(ma);
       }
       dxmid = bf.dxb;
     }
