@@ -233,12 +233,14 @@ def run_ours(args) -> dict | None:
                      "traffic": None, "algorithmic_per_launch": flops / max(1, groups[dom]["launches"])})
     else:
         # SR: the dominant work is the S' v product of each CG iteration (k_sr_tpart + k_sr_wpart and their
-        # small reductions, timed product by product): it streams O (Ns x P complex FP32) from HBM twice
+        # small reductions, timed product by product): it streams O (Ns x P complex elements, BF16 pairs in
+        # BF16 contexts, FP32 pairs otherwise) from HBM twice
         mv = main["sr_mv"]
-        byts = 2 * N_SAMPLES * P * 8
+        byts = 2 * N_SAMPLES * P * (4 if args.precision == "bf16" else 8)
         achieved = byts * mv["launches"] / (mv["ms"] * 1e-3) / 1e9 if mv["ms"] else 0.0
         peak = float(peaks.get("hbm_gbs", 6781.4))
         roof = {"bound": "hbm", "kernel": "S' v product (k_sr_tpart + k_sr_wpart, group sr_mv)",
+                "o_element_bytes": 4 if args.precision == "bf16" else 8,
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)", "algorithmic_per_launch": byts,
                 "products_per_step": mv["launches"], "ms_per_product": mv["ms"] / max(1e-9, mv["launches"])}

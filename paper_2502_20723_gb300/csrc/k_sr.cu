@@ -2,7 +2,9 @@
 //   (Re S + lambda I) x = rhs,  S_ij = <O_i^* O_j> - <O_i^*><O_j>  over Ns samples,
 // by Jacobi-preconditioned conjugate gradients, matrix-free: with Obar = O - mean(O),
 //   S v = (1/Ns) Re[Obar^H (Obar v)],
-// O stored as FP32 (re, im) [Ns][P].  One iteration streams O twice from HBM (t = Obar v per sample,
+// O stored as FP32 (re, im) [Ns][P], or as BF16 pairs of O - oref (a per-parameter shift that the
+// centring removes exactly; it keeps the BF16 rounding at the scale of O's spread, not of its mean).
+// One iteration streams O twice from HBM (t = Obar v per sample,
 // then w = Obar^H t per parameter) and is HBM-bound; both passes keep many independent loads in flight.
 // Products are formed in FP32 over runs of 32 terms and accumulated in FP64 (GB300's FP64 rate is far
 // below its FP32 rate); CG vectors and scalars are FP64 and stay on the device: a device flag ends the
@@ -14,6 +16,22 @@ namespace tdo {
 
 constexpr int kSrBlock = 256;
 constexpr int kRun = 32;     // FP32 products per FP64 accumulation
+
+// One complex element of O: FP32 (re, im) or a BF16 pair (re in the low half).
+__device__ __forceinline__ float2 cplx(float2 v) { return v; }
+__device__ __forceinline__ float2 cplx(uint32_t v) {
+  return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+}
+// Four consecutive elements from a 16-byte-aligned address.
+__device__ __forceinline__ void load4(const float2 *p, float2 (&c)[4]) {
+  const float4 a = __ldcs(reinterpret_cast<const float4 *>(p)), b = __ldcs(reinterpret_cast<const float4 *>(p) + 1);
+  c[0] = make_float2(a.x, a.y); c[1] = make_float2(a.z, a.w);
+  c[2] = make_float2(b.x, b.y); c[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load4(const uint32_t *p, float2 (&c)[4]) {
+  const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(p));
+  c[0] = cplx(q.x); c[1] = cplx(q.y); c[2] = cplx(q.z); c[3] = cplx(q.w);
+}
 
 enum {
   S_RZ = 0, S_BN, S_AL, S_RN, S_DONE, S_IT, S_TOL, S_PAP, S_CR, S_CI, S_TR, S_TI, S_COUNT
@@ -44,7 +62,8 @@ __device__ __forceinline__ double sum_parts(const double *part, int n, double *s
 // |mean[k]|^2 + shift (the variance of O_k floored at 0; 1 where that sum is 0), in one pass over O: thread per k, 4
 // independent loads in flight, FP32 runs of kRun samples accumulated in FP64.  The preconditioner only
 // sets the CG's convergence rate, so the one-pass variance formula is accurate enough for it.
-__global__ void k_sr_moments(const float2 *__restrict__ O, size_t Ns, size_t P, double shift,
+template <typename OT>
+__global__ void k_sr_moments(const OT *__restrict__ O, size_t Ns, size_t P, double shift,
                              double2 *__restrict__ mean, double *__restrict__ diag) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
     double ar = 0.0, ai = 0.0, aa = 0.0;
@@ -55,14 +74,14 @@ __global__ void k_sr_moments(const float2 *__restrict__ O, size_t Ns, size_t P, 
       for (; s + 4 <= s1; s += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float2 o = __ldg(O + (s + u) * P + k);
+          const float2 o = cplx(__ldg(O + (s + u) * P + k));
           fr[u] += o.x;
           fi[u] += o.y;
           fa[u] = fmaf(o.x, o.x, fmaf(o.y, o.y, fa[u]));
         }
       }
       for (; s < s1; ++s) {
-        const float2 o = __ldg(O + s * P + k);
+        const float2 o = cplx(__ldg(O + s * P + k));
         fr[0] += o.x;
         fi[0] += o.y;
         fa[0] = fmaf(o.x, o.x, fmaf(o.y, o.y, fa[0]));
@@ -112,7 +131,8 @@ __global__ void k_sr_cfin(const double *__restrict__ part, const double *__restr
 constexpr int kChunk = 1024;
 constexpr int kSampleGroups = 8;
 
-__global__ void k_sr_tpart(const float2 *__restrict__ O, size_t Ns, size_t P, const float *__restrict__ vf,
+template <typename OT>
+__global__ void k_sr_tpart(const OT *__restrict__ O, size_t Ns, size_t P, const float *__restrict__ vf,
                            double2 *__restrict__ part, const double *__restrict__ sc) {
   __shared__ float vs[kChunk];
   if (sc[S_DONE] != 0.0) return;
@@ -125,11 +145,11 @@ __global__ void k_sr_tpart(const float2 *__restrict__ O, size_t Ns, size_t P, co
   const size_t s_begin = (size_t)blockIdx.y * per;
   const size_t s_end = s_begin + per < Ns ? s_begin + per : Ns;
   for (size_t s = s_begin + warp; s < s_end; s += nw) {
-    const float2 *row = O + s * P + k0;
+    const OT *row = O + s * P + k0;
     float ar = 0.f, ai = 0.f;
 #pragma unroll 8
     for (int i = lane; i < kn; i += 32) {
-      const float2 o = __ldg(row + i);
+      const float2 o = cplx(__ldg(row + i));
       const float x = vs[i];
       ar = fmaf(o.x, x, ar);
       ai = fmaf(o.y, x, ai);
@@ -164,13 +184,13 @@ __global__ void k_sr_tsum(const float2 *__restrict__ t, size_t Ns, double *__res
 }
 
 // Partial products w = Re(O^H t) over one chunk of kChunk parameters and one sample group: block
-// (chunk, sg) streams the chunk (8 KB contiguous) of every sample row of its group, each thread owning
-// 4 consecutive parameters (two 16-byte loads per row when rows are 16-byte aligned, i.e. P even), with
-// the group's t in shared memory.  FP32 runs of kRun rows, FP64 across runs.
+// (chunk, sg) streams the chunk (8 KB of FP32 O, 4 KB of BF16 O, contiguous) of every sample row of its
+// group, each thread owning 4 consecutive parameters (16-byte loads when every row starts on a 16-byte
+// boundary), with the group's t in shared memory.  FP32 runs of kRun rows, FP64 across runs.
 // wpart[sg][k] = sum_{s in group sg} Re(conj(O[s][k]) t[s]).
 constexpr int kWRows = 2048;   // t values of a sample group staged at a time (16 KB)
-template <bool VEC>
-__global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const float2 *__restrict__ O, size_t Ns, size_t P,
+template <typename OT, bool VEC>
+__global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const OT *__restrict__ O, size_t Ns, size_t P,
                                                        const float2 *__restrict__ t, double *__restrict__ wpart,
                                                        const double *__restrict__ sc) {
   __shared__ float2 ts[kWRows];
@@ -193,39 +213,31 @@ __global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const float2 *__restrict_
       if (VEC && kn == 4) {
         int r = r0;
         for (; r + 4 <= r1; r += 4) {
-          float4 a[4], b[4];
+          float2 c[4][4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 *row = reinterpret_cast<const float4 *>(O + (g0 + r + u) * P + k);
-            a[u] = __ldcs(row);
-            b[u] = __ldcs(row + 1);
-          }
+          for (int u = 0; u < 4; ++u) load4(O + (g0 + r + u) * P + k, c[u]);
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const float2 tv = ts[r + u];
-            f[0] = fmaf(a[u].x, tv.x, fmaf(a[u].y, tv.y, f[0]));
-            f[1] = fmaf(a[u].z, tv.x, fmaf(a[u].w, tv.y, f[1]));
-            f[2] = fmaf(b[u].x, tv.x, fmaf(b[u].y, tv.y, f[2]));
-            f[3] = fmaf(b[u].z, tv.x, fmaf(b[u].w, tv.y, f[3]));
+#pragma unroll
+            for (int e = 0; e < 4; ++e) f[e] = fmaf(c[u][e].x, tv.x, fmaf(c[u][e].y, tv.y, f[e]));
           }
         }
         for (; r < r1; ++r) {
-          const float4 *row = reinterpret_cast<const float4 *>(O + (g0 + r) * P + k);
-          const float4 a = __ldcs(row), b = __ldcs(row + 1);
+          float2 c[4];
+          load4(O + (g0 + r) * P + k, c);
           const float2 tv = ts[r];
-          f[0] = fmaf(a.x, tv.x, fmaf(a.y, tv.y, f[0]));
-          f[1] = fmaf(a.z, tv.x, fmaf(a.w, tv.y, f[1]));
-          f[2] = fmaf(b.x, tv.x, fmaf(b.y, tv.y, f[2]));
-          f[3] = fmaf(b.z, tv.x, fmaf(b.w, tv.y, f[3]));
+#pragma unroll
+          for (int e = 0; e < 4; ++e) f[e] = fmaf(c[e].x, tv.x, fmaf(c[e].y, tv.y, f[e]));
         }
       } else {
         for (int r = r0; r < r1; ++r) {
           const float2 tv = ts[r];
-          const float2 *row = O + (g0 + r) * P + k;
+          const OT *row = O + (g0 + r) * P + k;
 #pragma unroll
           for (int e = 0; e < 4; ++e)
             if (e < kn) {
-              const float2 o = __ldcs(row + e);
+              const float2 o = cplx(__ldcs(row + e));
               f[e] = fmaf(o.x, tv.x, fmaf(o.y, tv.y, f[e]));
             }
         }
@@ -397,18 +409,20 @@ static SrPtrs sr_carve(double *work, size_t Ns, size_t P) {
 
 // S' v -> Ap (and the partials of v . Ap in q.part), all on the device.
 // S' v -> Ap (and the partials of v . Ap in q.part), all on the device: 7 launches, O streamed twice.
-static void matvec(const float2 *O, size_t Ns, size_t P, const double *v, double shift, SrPtrs &q, int nb,
+template <typename OT>
+static void matvec(const OT *O, size_t Ns, size_t P, const double *v, double shift, SrPtrs &q, int nb,
                    cudaStream_t st) {
   const int nchunks = (int)((P + kChunk - 1) / kChunk);
+  constexpr size_t align = 16 / sizeof(OT);   // elements per 16 bytes
   k_sr_vprep<<<nb, kSrBlock, 0, st>>>(P, v, q.mean, q.vf, q.part, q.part2, q.sc);
   k_sr_cfin<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
-  k_sr_tpart<<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.vf, q.tpart, q.sc);
+  k_sr_tpart<OT><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.vf, q.tpart, q.sc);
   k_sr_tred<<<(unsigned)((Ns + 255) / 256), 256, 0, st>>>(q.tpart, nchunks, Ns, q.t, q.sc);
   k_sr_tsum<<<1, 1024, 0, st>>>(q.t, Ns, q.sc);
-  if (P % 2 == 0)   // every row starts on a 16-byte boundary
-    k_sr_wpart<true><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.t, q.wpart, q.sc);
+  if (P % align == 0)   // every row starts on a 16-byte boundary
+    k_sr_wpart<OT, true><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.t, q.wpart, q.sc);
   else
-    k_sr_wpart<false><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.t, q.wpart, q.sc);
+    k_sr_wpart<OT, false><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.t, q.wpart, q.sc);
   k_sr_wfin<<<nb, kSrBlock, 0, st>>>(Ns, P, q.mean, q.wpart, v, shift, q.Ap, q.part, q.sc);
 }
 
@@ -422,14 +436,12 @@ size_t sr_work_doubles(size_t Ns, size_t P) {
   return (bytes + 7) / 8;
 }
 
-// mv_ev (optional): mv_cap event pairs recorded around the S' v launches; *mv_used = pairs recorded.
-cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, const double *x0, double shift,
-                       double tol, int max_iter, double *x, double *work, int n_sm, int *iters, double *resid,
-                       long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used, cudaStream_t st) {
-  using namespace tdo;
-  (void)n_sm;
+namespace tdo {
+template <typename OT>
+static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, const double *rhs, const double *x0, double shift,
+                           double tol, int max_iter, double *x, double *work, int *iters, double *resid,
+                           long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used, cudaStream_t st) {
   SrPtrs q = sr_carve(work, Ns, P);
-  const float2 *O2 = reinterpret_cast<const float2 *>(O);
   int nb = (int)((P + kSrBlock - 1) / kSrBlock);
   if (nb > 1024) nb = 1024;
   if (nb < 1) nb = 1;
@@ -448,7 +460,7 @@ cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, c
     }
     return cudaSuccess;
   };
-  k_sr_moments<<<nb, kSrBlock, 0, st>>>(O2, Ns, P, shift, q.mean, q.diag);
+  k_sr_moments<OT><<<nb, kSrBlock, 0, st>>>(O2, Ns, P, shift, q.mean, q.diag);
   k_sr_clear<<<1, 32, 0, st>>>(q.sc);
   nl += 2;
   cudaError_t e;
@@ -496,4 +508,19 @@ cudaError_t sr_cg_impl(const float *O, size_t Ns, size_t P, const double *rhs, c
   if (launches) *launches = nl;
   if (h[S_DONE] == 2.0) return cudaErrorInvalidValue;   // not positive definite
   return cudaSuccess;
+}
+}  // namespace tdo
+
+// mv_ev (optional): mv_cap event pairs recorded around the S' v launches; *mv_used = pairs recorded.
+// o_bf16: O holds BF16 pairs (uint32 per element) instead of FP32 (re, im).
+cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, const double *rhs, const double *x0,
+                       double shift, double tol, int max_iter, double *x, double *work, int n_sm, int *iters,
+                       double *resid, long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used,
+                       cudaStream_t st) {
+  (void)n_sm;
+  if (o_bf16)
+    return tdo::sr_cg_t(reinterpret_cast<const uint32_t *>(O), Ns, P, rhs, x0, shift, tol, max_iter, x, work, iters,
+                        resid, launches, mv_ev, mv_cap, mv_used, st);
+  return tdo::sr_cg_t(reinterpret_cast<const float2 *>(O), Ns, P, rhs, x0, shift, tol, max_iter, x, work, iters,
+                      resid, launches, mv_ev, mv_cap, mv_used, st);
 }

@@ -105,3 +105,22 @@ def test_cost_gradient_bf16_tensor_core(kind, n, h, L, r, Ns):
     print(f"bf16 gradient relative error {rel:.3e}, cost {cost:.6f} vs {c_ref:.6f}")
     assert abs(cost - c_ref) <= 1e-3 * c_ref
     assert rel <= 5e-2
+
+
+@pytest.mark.parametrize("kind,n,d,h,L,r,Ns", [("xyz", 6, 32, 4, 1, 0, 256), ("ising", 8, 32, 4, 1, 0, 40)])
+def test_sr_step_bf16(kind, n, d, h, L, r, Ns):
+    """One SR step of a BF16 context: BF16 forward and backward, the SR matrix's log-derivatives stored
+    in BF16 (shifted by their mean over the first 64 samples), FP64 CG.  The parameter update is within
+    5e-2 of the oracle's FP64 step in norm (measured values are reported)."""
+    prob = problem(kind, n)
+    spec = synth.model_spec(d, h, L, r)
+    th = synth.init_params(spec, 0, std=0.1 if d == 32 else 0.05)
+    sig, sigp = synth.random_configs(n, Ns, seed=8)
+    ctx = ctx_for(prob, spec, th)
+    cost = ctx.sr_step(dev(sig), dev(sigp), 0.01, 0.1)
+    new = ctx.get_params()
+    ref_new, c_ref, _, _ = E.sr_step(prob, spec, th, sig, sigp, 0.01, 0.1)
+    rel = np.linalg.norm((new - th) - (ref_new - th)) / np.linalg.norm(ref_new - th)
+    print(f"bf16 SR update relative error {rel:.3e}, cost {cost:.6f} vs {c_ref:.6f}")
+    assert abs(cost - c_ref) <= 1e-3 * c_ref
+    assert rel <= 5e-2
