@@ -7,8 +7,8 @@
 // Weight gradients are D x D blocks reduced over the rows of the tile:
 //   mode 0 (VJP): summed over the tile and added with float4 atomics to one of n_copies FP32 accumulator
 //                 vectors (CTA b uses copy b % n_copies; 16 copies stay L2-resident), reduced in FP64,
-//   mode 1 (Jacobian): one per (configuration, seed) and written to O[b][k][seed]
-//                      (seed 0: d Re log rho, seed 1: d Im log rho).
+//   mode 1 (Jacobian): one per (configuration, seed) and written to O[b][k][seed] (row stride ldo >= P),
+//                      FP32 or BF16 of O - oref (seed 0: d Re log rho, seed 1: d Im log rho).
 #include <cuda_bf16.h>
 
 #include "f32_tile.cuh"
@@ -50,7 +50,7 @@ struct SinkCtx {
   float *O;          // mode 1: [B][P][2] FP32, or
   uint16_t *O16;     //         [B][P][2] BF16 of O - oref (oref: [P] (re, im))
   const float2 *oref;
-  size_t P;
+  size_t P, ldo;     // parameters; elements per row of O (>= P)
   float *dtab;       // conv embedding: mode 0 [64][D] accumulator; mode 1 [B][2][64][D]
 };
 
@@ -63,7 +63,7 @@ __device__ __forceinline__ void sink1(const SinkCtx &s, long long k, float v, lo
   if (s.mode == 0) {
     atomicAdd(s.g + k, v);
   } else {
-    const size_t i = ((size_t)b * s.P + (size_t)k) * 2 + seed;
+    const size_t i = ((size_t)b * s.ldo + (size_t)k) * 2 + seed;
     if (s.O16) s.O16[i] = bf16_bits(v - (seed ? s.oref[k].y : s.oref[k].x));
     else s.O[i] = v;
   }
@@ -274,8 +274,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_bwd32(const DevModel m, const int mode, const uint32_t *__restrict__ sig,
             const uint32_t *__restrict__ sigp, const size_t B, const float2 *__restrict__ cot,
             float *__restrict__ gacc, const int n_copies, const size_t g_stride, float *__restrict__ O,
-            uint16_t *__restrict__ O16, const float2 *__restrict__ oref, const size_t P, const FlatOffsets fo,
-            float *__restrict__ scratch, float *__restrict__ dtab) {
+            uint16_t *__restrict__ O16, const float2 *__restrict__ oref, const size_t P, const size_t ldo,
+            const FlatOffsets fo, float *__restrict__ scratch, float *__restrict__ dtab) {
   using BG = BwdGeom<D>;
   constexpr int R = BG::R, LDX = BG::LDX;
   using G = F32Geom<D, R>;
@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   sk.O16 = O16;
   sk.oref = oref;
   sk.P = P;
+  sk.ldo = ldo;
   sk.dtab = dtab;
   const int nranges = mode == 0 ? 1 : tcv;
 
@@ -589,13 +590,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int D>
 static cudaError_t bwd_impl(const DevModel &m, int mode, const uint32_t *sig, const uint32_t *sigp,
                             size_t B, const float2 *cot, float *gacc, int n_copies, size_t g_stride, float *O,
-                            uint16_t *O16, const float2 *oref, size_t P, const FlatOffsets &fo, float *scratch,
-                            float *dtab, int grid, cudaStream_t st) {
+                            uint16_t *O16, const float2 *oref, size_t P, size_t ldo, const FlatOffsets &fo,
+                            float *scratch, float *dtab, int grid, cudaStream_t st) {
   const size_t bytes = BwdGeom<D>::BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_bwd32<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   k_bwd32<D><<<grid, kThreads, bytes, st>>>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, O16, oref, P,
-                                            fo, scratch, dtab);
+                                            ldo, fo, scratch, dtab);
   return cudaGetLastError();
 }
 
@@ -619,16 +620,19 @@ int bwd32_grid(const DevModel &m, size_t B, int mode, int n_sm) {
 
 cudaError_t launch_bwd32_impl(const DevModel &m, int mode, const uint32_t *sig, const uint32_t *sigp,
                               size_t B, const float2 *cot, float *gacc, int n_copies, size_t g_stride,
-                              float *O, uint16_t *O16, const float2 *oref, size_t P, const long long *flat_offsets,
-                              float *scratch, float *dtab, int grid, cudaStream_t st) {
+                              float *O, uint16_t *O16, const float2 *oref, size_t P, size_t ldo,
+                              const long long *flat_offsets, float *scratch, float *dtab, int grid, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
   tdo::FlatOffsets fo;
   static_assert(sizeof(tdo::FlatOffsets) == sizeof(long long) * (3 + 8 * TDO_MAX_LAYERS), "layout");
   memcpy(&fo, flat_offsets, sizeof(fo));
   switch (m.d) {
-    case 16: return tdo::bwd_impl<16>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, O16, oref, P, fo, scratch, dtab, grid, st);
-    case 32: return tdo::bwd_impl<32>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, O16, oref, P, fo, scratch, dtab, grid, st);
-    case 64: return tdo::bwd_impl<64>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, O16, oref, P, fo, scratch, dtab, grid, st);
+    case 16: return tdo::bwd_impl<16>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, O16, oref, P, ldo, fo, scratch,
+                                      dtab, grid, st);
+    case 32: return tdo::bwd_impl<32>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, O16, oref, P, ldo, fo, scratch,
+                                      dtab, grid, st);
+    case 64: return tdo::bwd_impl<64>(m, mode, sig, sigp, B, cot, gacc, n_copies, g_stride, O, O16, oref, P, ldo, fo, scratch,
+                                      dtab, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -645,7 +649,7 @@ __global__ void k_conv_vjp(int d, int c1, const float *__restrict__ Wc1, const f
                            const float *__restrict__ Wc2, const float *__restrict__ bc2,
                            const float *__restrict__ dT, int nsets, int ncopy, int mode, float *__restrict__ g,
                            float *__restrict__ O, uint16_t *__restrict__ O16, const float2 *__restrict__ oref,
-                           size_t P, long long o_wc1, long long o_bc1, long long o_wc2, long long o_bc2) {
+                           size_t ldo, long long o_wc1, long long o_bc1, long long o_wc2, long long o_bc2) {
   extern __shared__ float sh[];
   float *a1 = sh;                       // [64][2][c1]
   float *dh = a1 + 64 * 2 * c1;         // [64][2][c1] (da1 in place)
@@ -677,7 +681,7 @@ __global__ void k_conv_vjp(int d, int c1, const float *__restrict__ Wc1, const f
       if (mode == 0) {
         atomicAdd(g + k, v);
       } else {
-        const size_t i = ((size_t)(set >> 1) * P + (size_t)k) * 2 + (set & 1);
+        const size_t i = ((size_t)(set >> 1) * ldo + (size_t)k) * 2 + (set & 1);
         if (O16) O16[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v - ((set & 1) ? oref[k].y : oref[k].x)));
         else O[i] = v;
       }
@@ -722,14 +726,14 @@ __global__ void k_conv_vjp(int d, int c1, const float *__restrict__ Wc1, const f
 
 cudaError_t launch_conv_vjp(int d, int c1, const float *Wc1, const float *bc1, const float *Wc2, const float *bc2,
                             const float *dT, int nsets, int ncopy, int mode, float *g, float *O, uint16_t *O16,
-                            const float2 *oref, size_t P, long long o_wc1, long long o_bc1, long long o_wc2,
+                            const float2 *oref, size_t ldo, long long o_wc1, long long o_bc1, long long o_wc2,
                             long long o_bc2, cudaStream_t st) {
   if (nsets <= 0) return cudaSuccess;
   const size_t bytes = sizeof(float) * (2 * 64 * 2 * c1 + 64 * d);
   cudaError_t e = cudaFuncSetAttribute(tdo::k_conv_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   const int grid = nsets < 1024 ? nsets : 1024;
-  tdo::k_conv_vjp<<<grid, 256, bytes, st>>>(d, c1, Wc1, bc1, Wc2, bc2, dT, nsets, ncopy, mode, g, O, O16, oref, P,
+  tdo::k_conv_vjp<<<grid, 256, bytes, st>>>(d, c1, Wc1, bc1, Wc2, bc2, dT, nsets, ncopy, mode, g, O, O16, oref, ldo,
                                             o_wc1, o_bc1, o_wc2, o_bc2);
   return cudaGetLastError();
 }

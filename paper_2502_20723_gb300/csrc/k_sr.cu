@@ -63,7 +63,7 @@ __device__ __forceinline__ double sum_parts(const double *part, int n, double *s
 // independent loads in flight, FP32 runs of kRun samples accumulated in FP64.  The preconditioner only
 // sets the CG's convergence rate, so the one-pass variance formula is accurate enough for it.
 template <typename OT>
-__global__ void k_sr_moments(const OT *__restrict__ O, size_t Ns, size_t P, double shift,
+__global__ void k_sr_moments(const OT *__restrict__ O, size_t Ns, size_t P, size_t ldo, double shift,
                              double2 *__restrict__ mean, double *__restrict__ diag) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
     double ar = 0.0, ai = 0.0, aa = 0.0;
@@ -74,14 +74,14 @@ __global__ void k_sr_moments(const OT *__restrict__ O, size_t Ns, size_t P, doub
       for (; s + 4 <= s1; s += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float2 o = cplx(__ldg(O + (s + u) * P + k));
+          const float2 o = cplx(__ldg(O + (s + u) * ldo + k));
           fr[u] += o.x;
           fi[u] += o.y;
           fa[u] = fmaf(o.x, o.x, fmaf(o.y, o.y, fa[u]));
         }
       }
       for (; s < s1; ++s) {
-        const float2 o = cplx(__ldg(O + s * P + k));
+        const float2 o = cplx(__ldg(O + s * ldo + k));
         fr[0] += o.x;
         fi[0] += o.y;
         fa[0] = fmaf(o.x, o.x, fmaf(o.y, o.y, fa[0]));
@@ -126,15 +126,17 @@ __global__ void k_sr_cfin(const double *__restrict__ part, const double *__restr
 }
 
 // Partial dot products of the rows of O with v over one chunk of kChunk parameters: block (chunk, sg)
-// streams the chunk of every sample row of sample group sg (8 KB contiguous per row), one warp per
-// row at a time, with the chunk of v in shared memory.  part[chunk][s] = sum_{k in chunk} O[s][k] v[k].
+// streams the chunk of every sample row of sample group sg (8 KB of FP32 O or 4 KB of BF16 O,
+// contiguous), one warp per row at a time, 16-byte loads per lane when every row starts on a 16-byte
+// boundary, with the chunk of v in shared memory.  part[chunk][s] = sum_{k in chunk} O[s][k] v[k].
 constexpr int kChunk = 1024;
 constexpr int kSampleGroups = 8;
 
-template <typename OT>
-__global__ void k_sr_tpart(const OT *__restrict__ O, size_t Ns, size_t P, const float *__restrict__ vf,
+template <typename OT, bool VEC>
+__global__ void k_sr_tpart(const OT *__restrict__ O, size_t Ns, size_t P, size_t ldo, const float *__restrict__ vf,
                            double2 *__restrict__ part, const double *__restrict__ sc) {
-  __shared__ float vs[kChunk];
+  __shared__ float4 vs4[kChunk / 4];
+  float *vs = reinterpret_cast<float *>(vs4);
   if (sc[S_DONE] != 0.0) return;
   const size_t k0 = (size_t)blockIdx.x * kChunk;
   const int kn = (int)((P - k0) < (size_t)kChunk ? (P - k0) : (size_t)kChunk);
@@ -145,14 +147,30 @@ __global__ void k_sr_tpart(const OT *__restrict__ O, size_t Ns, size_t P, const 
   const size_t s_begin = (size_t)blockIdx.y * per;
   const size_t s_end = s_begin + per < Ns ? s_begin + per : Ns;
   for (size_t s = s_begin + warp; s < s_end; s += nw) {
-    const OT *row = O + s * P + k0;
+    const OT *row = O + s * ldo + k0;
     float ar = 0.f, ai = 0.f;
+    if (VEC) {   // 4 elements per lane and load, then the chunk's last kn % 4 one by one
+#pragma unroll 4
+      for (int i4 = lane; i4 < kn / 4; i4 += 32) {
+        float2 c[4];
+        load4(row + 4 * i4, c);
+        const float4 x = vs4[i4];
+        ar = fmaf(c[0].x, x.x, fmaf(c[1].x, x.y, fmaf(c[2].x, x.z, fmaf(c[3].x, x.w, ar))));
+        ai = fmaf(c[0].y, x.x, fmaf(c[1].y, x.y, fmaf(c[2].y, x.z, fmaf(c[3].y, x.w, ai))));
+      }
+      for (int i = (kn & ~3) + lane; i < kn; i += 32) {
+        const float2 o = cplx(__ldg(row + i));
+        ar = fmaf(o.x, vs[i], ar);
+        ai = fmaf(o.y, vs[i], ai);
+      }
+    } else {
 #pragma unroll 8
-    for (int i = lane; i < kn; i += 32) {
-      const float2 o = cplx(__ldg(row + i));
-      const float x = vs[i];
-      ar = fmaf(o.x, x, ar);
-      ai = fmaf(o.y, x, ai);
+      for (int i = lane; i < kn; i += 32) {
+        const float2 o = cplx(__ldg(row + i));
+        const float x = vs[i];
+        ar = fmaf(o.x, x, ar);
+        ai = fmaf(o.y, x, ai);
+      }
     }
     ar = warp_sum(ar);
     ai = warp_sum(ai);
@@ -190,7 +208,7 @@ __global__ void k_sr_tsum(const float2 *__restrict__ t, size_t Ns, double *__res
 // wpart[sg][k] = sum_{s in group sg} Re(conj(O[s][k]) t[s]).
 constexpr int kWRows = 2048;   // t values of a sample group staged at a time (16 KB)
 template <typename OT, bool VEC>
-__global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const OT *__restrict__ O, size_t Ns, size_t P,
+__global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const OT *__restrict__ O, size_t Ns, size_t P, size_t ldo,
                                                        const float2 *__restrict__ t, double *__restrict__ wpart,
                                                        const double *__restrict__ sc) {
   __shared__ float2 ts[kWRows];
@@ -215,7 +233,7 @@ __global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const OT *__restrict__ O,
         for (; r + 4 <= r1; r += 4) {
           float2 c[4][4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) load4(O + (g0 + r + u) * P + k, c[u]);
+          for (int u = 0; u < 4; ++u) load4(O + (g0 + r + u) * ldo + k, c[u]);
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const float2 tv = ts[r + u];
@@ -225,7 +243,7 @@ __global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const OT *__restrict__ O,
         }
         for (; r < r1; ++r) {
           float2 c[4];
-          load4(O + (g0 + r) * P + k, c);
+          load4(O + (g0 + r) * ldo + k, c);
           const float2 tv = ts[r];
 #pragma unroll
           for (int e = 0; e < 4; ++e) f[e] = fmaf(c[e].x, tv.x, fmaf(c[e].y, tv.y, f[e]));
@@ -233,7 +251,7 @@ __global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const OT *__restrict__ O,
       } else {
         for (int r = r0; r < r1; ++r) {
           const float2 tv = ts[r];
-          const OT *row = O + (g0 + r) * P + k;
+          const OT *row = O + (g0 + r) * ldo + k;
 #pragma unroll
           for (int e = 0; e < 4; ++e)
             if (e < kn) {
@@ -410,19 +428,23 @@ static SrPtrs sr_carve(double *work, size_t Ns, size_t P) {
 // S' v -> Ap (and the partials of v . Ap in q.part), all on the device.
 // S' v -> Ap (and the partials of v . Ap in q.part), all on the device: 7 launches, O streamed twice.
 template <typename OT>
-static void matvec(const OT *O, size_t Ns, size_t P, const double *v, double shift, SrPtrs &q, int nb,
-                   cudaStream_t st) {
+static void matvec(const OT *O, size_t Ns, size_t P, size_t ldo, const double *v, double shift, SrPtrs &q,
+                   int nb, cudaStream_t st) {
   const int nchunks = (int)((P + kChunk - 1) / kChunk);
   constexpr size_t align = 16 / sizeof(OT);   // elements per 16 bytes
   k_sr_vprep<<<nb, kSrBlock, 0, st>>>(P, v, q.mean, q.vf, q.part, q.part2, q.sc);
   k_sr_cfin<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
-  k_sr_tpart<OT><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.vf, q.tpart, q.sc);
+  const bool vec = ldo % align == 0 && reinterpret_cast<uintptr_t>(O) % 16 == 0;   // 16-byte-aligned rows
+  if (vec)
+    k_sr_tpart<OT, true><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, ldo, q.vf, q.tpart, q.sc);
+  else
+    k_sr_tpart<OT, false><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, ldo, q.vf, q.tpart, q.sc);
   k_sr_tred<<<(unsigned)((Ns + 255) / 256), 256, 0, st>>>(q.tpart, nchunks, Ns, q.t, q.sc);
   k_sr_tsum<<<1, 1024, 0, st>>>(q.t, Ns, q.sc);
-  if (P % align == 0)   // every row starts on a 16-byte boundary
-    k_sr_wpart<OT, true><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.t, q.wpart, q.sc);
+  if (vec)
+    k_sr_wpart<OT, true><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, ldo, q.t, q.wpart, q.sc);
   else
-    k_sr_wpart<OT, false><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, q.t, q.wpart, q.sc);
+    k_sr_wpart<OT, false><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, ldo, q.t, q.wpart, q.sc);
   k_sr_wfin<<<nb, kSrBlock, 0, st>>>(Ns, P, q.mean, q.wpart, v, shift, q.Ap, q.part, q.sc);
 }
 
@@ -438,7 +460,8 @@ size_t sr_work_doubles(size_t Ns, size_t P) {
 
 namespace tdo {
 template <typename OT>
-static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, const double *rhs, const double *x0, double shift,
+static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const double *rhs, const double *x0,
+                           double shift,
                            double tol, int max_iter, double *x, double *work, int *iters, double *resid,
                            long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used, cudaStream_t st) {
   SrPtrs q = sr_carve(work, Ns, P);
@@ -451,7 +474,7 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, const double *rhs,
   auto mv = [&](const double *v) -> cudaError_t {
     const bool rec = mv_ev && nmv < mv_cap;
     if (rec) cudaEventRecord(mv_ev[2 * nmv], st);
-    matvec(O2, Ns, P, v, shift, q, nb, st);
+    matvec(O2, Ns, P, ldo, v, shift, q, nb, st);
     nl += 7;
     if (rec) {
       cudaEventRecord(mv_ev[2 * nmv + 1], st);
@@ -460,7 +483,7 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, const double *rhs,
     }
     return cudaSuccess;
   };
-  k_sr_moments<OT><<<nb, kSrBlock, 0, st>>>(O2, Ns, P, shift, q.mean, q.diag);
+  k_sr_moments<OT><<<nb, kSrBlock, 0, st>>>(O2, Ns, P, ldo, shift, q.mean, q.diag);
   k_sr_clear<<<1, 32, 0, st>>>(q.sc);
   nl += 2;
   cudaError_t e;
@@ -512,15 +535,15 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, const double *rhs,
 }  // namespace tdo
 
 // mv_ev (optional): mv_cap event pairs recorded around the S' v launches; *mv_used = pairs recorded.
-// o_bf16: O holds BF16 pairs (uint32 per element) instead of FP32 (re, im).
-cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, const double *rhs, const double *x0,
+// o_bf16: O holds BF16 pairs (uint32 per element) instead of FP32 (re, im); ldo >= P: elements per row.
+cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, size_t ldo, const double *rhs, const double *x0,
                        double shift, double tol, int max_iter, double *x, double *work, int n_sm, int *iters,
                        double *resid, long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used,
                        cudaStream_t st) {
   (void)n_sm;
   if (o_bf16)
-    return tdo::sr_cg_t(reinterpret_cast<const uint32_t *>(O), Ns, P, rhs, x0, shift, tol, max_iter, x, work, iters,
+    return tdo::sr_cg_t(reinterpret_cast<const uint32_t *>(O), Ns, P, ldo, rhs, x0, shift, tol, max_iter, x, work, iters,
                         resid, launches, mv_ev, mv_cap, mv_used, st);
-  return tdo::sr_cg_t(reinterpret_cast<const float2 *>(O), Ns, P, rhs, x0, shift, tol, max_iter, x, work, iters,
+  return tdo::sr_cg_t(reinterpret_cast<const float2 *>(O), Ns, P, ldo, rhs, x0, shift, tol, max_iter, x, work, iters,
                       resid, launches, mv_ev, mv_cap, mv_used, st);
 }

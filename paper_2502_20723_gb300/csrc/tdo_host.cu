@@ -26,15 +26,15 @@ size_t bwd32_scratch_floats(const DevModel &m, int grid);
 int bwd32_grid(const DevModel &m, size_t B, int mode, int n_sm);
 cudaError_t launch_bwd32_impl(const DevModel &m, int mode, const uint32_t *sig, const uint32_t *sigp,
                               size_t B, const float2 *cot, float *gacc, int n_copies, size_t g_stride,
-                              float *O, uint16_t *O16, const float2 *oref, size_t P, const long long *flat_offsets,
-                              float *scratch, float *dtab, int grid, cudaStream_t st);
+                              float *O, uint16_t *O16, const float2 *oref, size_t P, size_t ldo,
+                              const long long *flat_offsets, float *scratch, float *dtab, int grid, cudaStream_t st);
 cudaError_t launch_oref(const float *O32, int n, size_t P, float *oref, cudaStream_t st);
 cudaError_t launch_conv_vjp(int d, int c1, const float *Wc1, const float *bc1, const float *Wc2, const float *bc2,
                             const float *dT, int nsets, int ncopy, int mode, float *g, float *O, uint16_t *O16,
-                            const float2 *oref, size_t P, long long o_wc1, long long o_bc1, long long o_wc2,
+                            const float2 *oref, size_t ldo, long long o_wc1, long long o_bc1, long long o_wc2,
                             long long o_bc2, cudaStream_t st);
 size_t sr_work_doubles(size_t Ns, size_t P);
-cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, const double *rhs, const double *x0,
+cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, size_t ldo, const double *rhs, const double *x0,
                        double shift, double tol, int max_iter, double *x, double *work, int n_sm, int *iters,
                        double *resid, long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used,
                        cudaStream_t st);
@@ -707,11 +707,11 @@ extern "C" tdo_status tdo_local_estimator(tdo_ctx *c, const uint32_t *sig, const
 // Back-propagates the per-pattern table gradients the backward kernel left in c->dtab to the conv
 // embedding parameters (mode 0: added into g; mode 1: written into O[b][k][seed]).
 static tdo_status conv_vjp(tdo_ctx *c, int nsets, int ncopy, int mode, float *g, float *O, uint16_t *O16 = nullptr,
-                           const float2 *oref = nullptr) {
+                           const float2 *oref = nullptr, size_t ldo = 0) {
   const float *b = c->theta32.as<float>();
   CU(c, launch_conv_vjp(c->model.d_model, c->model.conv_channels, b + c->tensors[0].pad, b + c->tensors[1].pad,
                         b + c->tensors[2].pad, b + c->tensors[3].pad, c->dtab.as<float>(), nsets, ncopy, mode, g, O,
-                        O16, oref, c->P,
+                        O16, oref, ldo ? ldo : c->P,
                         c->tensors[0].flat, c->tensors[1].flat, c->tensors[2].flat, c->tensors[3].flat, c->stream));
   return TDO_OK;
 }
@@ -733,7 +733,7 @@ static tdo_status vjp_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, si
   }
   Timed tm(c, G_BWD_VJP);
   CU(c, launch_bwd32_impl(c->dm, 0, ds, dp, B, cot, c->gacc.as<float>(), copies, stride, nullptr, nullptr, nullptr,
-                          c->P, c->flat_offsets, c->scratch.as<float>(), conv ? c->dtab.as<float>() : nullptr, grid,
+                          c->P, c->P, c->flat_offsets, c->scratch.as<float>(), conv ? c->dtab.as<float>() : nullptr, grid,
                           c->stream));
   if (conv) TRY(conv_vjp(c, 1, copies, 0, c->gacc.as<float>(), nullptr));
   CU(c, launch_reduce_copies(c->gacc.as<float>(), copies, stride, c->P, grad, accumulate, c->stream));
@@ -741,17 +741,19 @@ static tdo_status vjp_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, si
   return TDO_OK;
 }
 
-// Log-derivatives of B configurations: FP32 into O, or (O16 non-null) BF16 of O - oref.
+// Log-derivatives of B configurations: FP32 into O, or (O16 non-null) BF16 of O - oref; rows of ldo
+// elements (0: P).
 static tdo_status jacobian_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t B, float *O,
-                               uint16_t *O16 = nullptr, const float2 *oref = nullptr) {
+                               uint16_t *O16 = nullptr, const float2 *oref = nullptr, size_t ldo = 0) {
+  if (!ldo) ldo = c->P;
   const bool conv = c->model.embed == TDO_EMBED_CONV;
   const int grid = bwd32_grid(c->dm, B, 1, c->n_sm);
   CU(c, c->scratch.ensure(sizeof(float) * bwd32_scratch_floats(c->dm, grid)));
   if (conv) CU(c, c->dtab.ensure(sizeof(float) * 2 * B * 64 * c->model.d_model));
   Timed tm(c, G_BWD_JAC);
-  CU(c, launch_bwd32_impl(c->dm, 1, ds, dp, B, nullptr, nullptr, 1, 0, O, O16, oref, c->P, c->flat_offsets,
+  CU(c, launch_bwd32_impl(c->dm, 1, ds, dp, B, nullptr, nullptr, 1, 0, O, O16, oref, c->P, ldo, c->flat_offsets,
                           c->scratch.as<float>(), conv ? c->dtab.as<float>() : nullptr, grid, c->stream));
-  if (conv) TRY(conv_vjp(c, (int)(2 * B), 1, 1, nullptr, O, O16, oref));
+  if (conv) TRY(conv_vjp(c, (int)(2 * B), 1, 1, nullptr, O, O16, oref, ldo));
   tm.done(conv ? 2 : 1);
   return TDO_OK;
 }
@@ -759,7 +761,7 @@ static tdo_status jacobian_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *d
 // The SR matrix's log-derivatives in BF16 (BF16 contexts): the shift oref is the mean log-derivative of
 // the first min(Ns, 64) samples (an FP32 Jacobian of those), so the stored values are spread-sized and
 // their rounding does not scale with a parameter's mean (the centring of S removes the shift exactly).
-static tdo_status jacobian_bf16_for_sr(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t Ns) {
+static tdo_status jacobian_bf16_for_sr(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t Ns, size_t ldo) {
   const int nref = Ns < 64 ? (int)Ns : 64;
   const size_t ref_bytes = sizeof(float) * 2 * c->P * (size_t)nref;
   float *O32 = nullptr;
@@ -775,7 +777,7 @@ static tdo_status jacobian_bf16_for_sr(tdo_ctx *c, const uint32_t *ds, const uin
     Timed tm(c, G_BWD_JAC);
     CU(c, launch_oref(O32, nref, c->P, c->oref.as<float>(), c->stream));
   }
-  TRY(jacobian_dev(c, ds, dp, Ns, nullptr, c->Obuf.as<uint16_t>(), c->oref.as<float2>()));
+  TRY(jacobian_dev(c, ds, dp, Ns, nullptr, c->Obuf.as<uint16_t>(), c->oref.as<float2>(), ldo));
   return TDO_OK;
 }
 
@@ -906,7 +908,8 @@ extern "C" tdo_status tdo_grad(tdo_ctx *c, const uint32_t *sig, const uint32_t *
 
 
 // sr_cg_impl with, when timing is on, one event pair around every S' v launch (group "sr_mv").
-static cudaError_t sr_cg_timed(tdo_ctx *c, const void *O, int o_bf16, size_t Ns, const double *rhs, const double *x0,
+static cudaError_t sr_cg_timed(tdo_ctx *c, const void *O, int o_bf16, size_t ldo, size_t Ns, const double *rhs,
+                               const double *x0,
                                double shift, double tol, int max_iter, double *x, int *iters, double *resid,
                                long long *launches) {
   std::vector<cudaEvent_t> ev;
@@ -920,7 +923,7 @@ static cudaError_t sr_cg_timed(tdo_ctx *c, const void *O, int o_bf16, size_t Ns,
     }
   }
   int used = 0;
-  const cudaError_t err = sr_cg_impl(O, o_bf16, Ns, c->P, rhs, x0, shift, tol, max_iter, x, c->srwork.as<double>(), c->n_sm,
+  const cudaError_t err = sr_cg_impl(O, o_bf16, Ns, c->P, ldo, rhs, x0, shift, tol, max_iter, x, c->srwork.as<double>(), c->n_sm,
                                      iters, resid, launches, ev.empty() ? nullptr : ev.data(), (int)ev.size() / 2,
                                      &used, c->stream);
   for (int i = 0; i < (int)ev.size(); ++i) {
@@ -946,7 +949,7 @@ extern "C" tdo_status tdo_sr_solve(tdo_ctx *c, const float *O, size_t Ns, const 
   Timed tm(c, G_SR);
   int it_local = 0;
   long long nl = 0;
-  cudaError_t e = sr_cg_timed(c, dO, 0, Ns, (const double *)dr, nullptr, diag_shift, tol, max_iter, dx,
+  cudaError_t e = sr_cg_timed(c, dO, 0, c->P, Ns, (const double *)dr, nullptr, diag_shift, tol, max_iter, dx,
                               &it_local, resid, &nl);
   if (iters) *iters = it_local;
   tm.done(nl);
@@ -970,10 +973,11 @@ extern "C" tdo_status tdo_sr_step(tdo_ctx *c, const uint32_t *sig, const uint32_
   CU(c, c->grad.ensure(sizeof(double) * c->P));
   CU(c, c->delta.ensure(sizeof(double) * c->P));
   const int o_bf16 = c->model.precision == TDO_BF16 ? 1 : 0;   // SR's O in BF16 for BF16 contexts
-  CU(c, c->Obuf.ensure((o_bf16 ? sizeof(uint16_t) : sizeof(float)) * 2 * c->P * Ns));
+  const size_t ldo = o_bf16 ? (c->P + 3) / 4 * 4 : (c->P + 1) / 2 * 2;   // rows on 16-byte boundaries
+  CU(c, c->Obuf.ensure((o_bf16 ? sizeof(uint16_t) : sizeof(float)) * 2 * ldo * Ns));
   TRY(grad_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, c->grad.as<double>(), cost));
-  if (o_bf16) TRY(jacobian_bf16_for_sr(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns));
-  else TRY(jacobian_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, c->Obuf.as<float>()));
+  if (o_bf16) TRY(jacobian_bf16_for_sr(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, ldo));
+  else TRY(jacobian_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, c->Obuf.as<float>(), nullptr, nullptr, ldo));
   CU(c, c->srwork.ensure(sizeof(double) * sr_work_doubles(Ns, c->P)));
   int iters = 0;
   double resid = 0;
@@ -982,7 +986,7 @@ extern "C" tdo_status tdo_sr_step(tdo_ctx *c, const uint32_t *sig, const uint32_
     // warm start from the previous step's solution (same parameter layout)
     Timed tm(c, G_SR);
     long long nl = 0;
-    e = sr_cg_timed(c, c->Obuf.p, o_bf16, Ns, c->grad.as<double>(), c->have_delta ? c->delta.as<double>() : nullptr,
+    e = sr_cg_timed(c, c->Obuf.p, o_bf16, ldo, Ns, c->grad.as<double>(), c->have_delta ? c->delta.as<double>() : nullptr,
                     diag_shift, c->sr_tol, c->sr_max_iter, c->delta.as<double>(), &iters, &resid, &nl);
     tm.done(nl);
   }

@@ -84,7 +84,7 @@ def train(n, spec, steps, chains, lr, shift, sweeps, seed=0):
 
 @pytest.mark.parametrize("n,d,h,L,c1,steps,chains,lr,shift,sweeps", [
     (4, 16, 2, 1, 8, 600, 8192, 0.03, 1e-3, 4),
-    (8, 16, 2, 1, 8, 1200, 8192, 0.03, 1e-2, 4),   # at N = 8 a shift of 1e-3 diverges
+    (8, 16, 2, 1, 8, 1500, 8192, 0.03, 1e-2, 4),   # at N = 8 a shift of 1e-3 diverges
 ])
 def test_vmc_reaches_exact_magnetisations(n, d, h, L, c1, steps, chains, lr, shift, sweeps):
     spec = synth.model_spec(d, h, L, 0, embed="conv", conv_channels=c1)
