@@ -156,6 +156,69 @@ __device__ __forceinline__ void flush_block(const Sync &s, uint32_t col, int N, 
   }
 }
 
+// ---- per-configuration (log-derivative) mode.  The rows are virtual configurations v = 2 b + seed
+// (sample b, cotangent (1, 0) for seed 0 and (0, -1) for seed 1), 32 rows (two sequences of N = 16)
+// each, so a tile holds the two seeds of two samples.  Weight gradients are then MMAs over each
+// configuration's 32 rows (two K steps) into their own TMEM columns, written to O[b][k] as the pair
+// (seed 0, seed 1) = (d Re log rho, d Im log rho): FP32, or BF16 of O - oref.
+struct JacOut {
+  float *o32;            // [nvirt / 2][ldo] float2, or
+  uint16_t *o16;         // [nvirt / 2][ldo] BF16 pairs of O - oref
+  const float2 *oref;
+  size_t ldo;
+  size_t nvirt;          // virtual configurations (0: the kernels run in VJP mode)
+};
+
+__device__ __forceinline__ void jac_put2(const JacOut &j, size_t b, long long k, float re, float im) {
+  const size_t i = b * j.ldo + (size_t)k;
+  if (j.o16) {
+    const float2 r = j.oref[k];
+    reinterpret_cast<uint32_t *>(j.o16)[i] = pack_bf16(re - r.x, im - r.y);
+  } else {
+    reinterpret_cast<float2 *>(j.o32)[i] = make_float2(re, im);
+  }
+}
+__device__ __forceinline__ void jac_put1(const JacOut &j, size_t v, long long k, float x) {
+  const size_t i = ((v >> 1) * j.ldo + (size_t)k) * 2 + (v & 1);
+  if (j.o16) j.o16[i] = __bfloat16_as_ushort(__float2bfloat16_rn(x - ((v & 1) ? j.oref[k].y : j.oref[k].x)));
+  else j.o32[i] = x;
+}
+
+// MN-major x MN-major over rows [r0, r0 + 16 nsteps) of the images: D[tmem + col] = A_img^T B_img
+__device__ __forceinline__ void mma_mm_rows(const Sync &s, uint32_t a, int Ka, uint32_t b, int Kb, int N,
+                                            uint32_t col, int r0, int nsteps) {
+  const uint32_t id = idesc_bf16_major(kRows, N, 1, 1);
+  for (int kk = 0; kk < nsteps; ++kk) {
+    const int r = r0 / 16 + kk;
+    mma_bf16(s.tmem + col, dmn(a + r * Ka * 32, Ka), dmn(b + r * Kb * 32, Kb), id, kk > 0 ? 1u : 0u);
+  }
+}
+
+// Flush per-configuration TMEM blocks [lanes M][N cols] at columns col0 + c * N for the tile's 4 virtual
+// configurations: each thread (lane quarter, column group of NQ) pairs the two seeds of a sample.
+// idx(m, n) < 0 skips an element.
+template <typename IDX, int NQ>
+__device__ __forceinline__ void jac_flush(const Sync &s, const JacOut &j, size_t tile, uint32_t col0, int N, IDX idx) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = 32 * (warp & 3) + lane, cg = warp >> 2;
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  for (int pr = 0; pr < 2; ++pr) {   // sample tile * 2 + pr: configurations 2 pr (seed 0) and 2 pr + 1
+    const size_t v0 = tile * 4 + 2 * pr;
+    for (int jj = 0; jj < N / NQ; jj += 16) {
+      float re[16], im[16];
+      tmem_ld16(s.tmem + lane_addr + col0 + (2 * pr) * N + cg * (N / NQ) + jj, re);
+      tmem_ld16(s.tmem + lane_addr + col0 + (2 * pr + 1) * N + cg * (N / NQ) + jj, im);
+      if (v0 + 1 < j.nvirt) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const long long k = idx(m, cg * (N / NQ) + jj + e);
+          if (k >= 0) jac_put2(j, v0 >> 1, k, re[e], im[e]);
+        }
+      }
+    }
+  }
+}
+
 // ====================================================================================== head
 struct HeadArgs {
   const float2 *cot;   // [B] cotangents of log rho
@@ -168,6 +231,7 @@ struct HeadArgs {
   size_t g_stride;
   long long off_wh, off_bh;
   int D;
+  JacOut jac;
 };
 
 __global__ void k_head_bwd(HeadArgs a) {
@@ -185,16 +249,26 @@ __global__ void k_head_bwd(HeadArgs a) {
       const float cvr = c.x * pv.x - c.y * pv.y, cvi = c.x * pv.y + c.y * pv.x;
       d0 = cwr; d1 = -cwi; d2 = cvr; d3 = cvi;
       const float *hA = a.H + (2 * b) * a.D, *hB = hA + a.D;
-      for (int k = 0; k < a.D; ++k) {
-        atomicAdd(&acc[2 * k], hA[k] * d0 + hB[k] * d2);
-        atomicAdd(&acc[2 * k + 1], hA[k] * d1 + hB[k] * d3);
+      if (a.jac.nvirt) {   // this configuration's own head gradient
+        for (int k = 0; k < a.D; ++k) {
+          jac_put1(a.jac, b, a.off_wh + 2 * k, hA[k] * d0 + hB[k] * d2);
+          jac_put1(a.jac, b, a.off_wh + 2 * k + 1, hA[k] * d1 + hB[k] * d3);
+        }
+        jac_put1(a.jac, b, a.off_bh, d0 + d2);
+        jac_put1(a.jac, b, a.off_bh + 1, d1 + d3);
+      } else {
+        for (int k = 0; k < a.D; ++k) {
+          atomicAdd(&acc[2 * k], hA[k] * d0 + hB[k] * d2);
+          atomicAdd(&acc[2 * k + 1], hA[k] * d1 + hB[k] * d3);
+        }
+        atomicAdd(&acc[2 * a.D], d0 + d2);
+        atomicAdd(&acc[2 * a.D + 1], d1 + d3);
       }
-      atomicAdd(&acc[2 * a.D], d0 + d2);
-      atomicAdd(&acc[2 * a.D + 1], d1 + d3);
     }
     reinterpret_cast<float4 *>(a.dF)[b] = make_float4(d0, d1, d2, d3);
   }
   __syncthreads();
+  if (a.jac.nvirt) return;
   float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
   for (int i = threadIdx.x; i < nacc; i += blockDim.x) {
     const long long k = i < 2 * a.D ? a.off_wh + i : a.off_bh + (i - 2 * a.D);
@@ -241,6 +315,7 @@ struct MlpGeo {
   static constexpr int BYTES = M_OFF + 64 + 4 * D;
   // TMEM columns (C_B1: db1 = dU^T 1, every one of its 16 columns holds the same sums)
   static constexpr int C_U = 0, C_DG = 128, C_DX = 256, C_W1 = 320, C_W2 = 384, C_B1 = 448;
+  static constexpr int C_JB1 = 320;   // per-configuration mode: 4 x 16 db1 columns (dW1/dW2 blocks in [0, 256))
 };
 
 struct MlpArgs {
@@ -256,6 +331,7 @@ struct MlpArgs {
   long long off_w1, off_b1, off_w2, off_b2;   // flat offsets (off_w1 / off_b1 / off_w2 already at this half)
   int F;
   int *err;
+  JacOut jac;
 };
 
 // 512 threads: thread (row, cg) owns a quarter of the hidden chunk's and of dX's columns; 16 warps hide
@@ -307,11 +383,14 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       }
 #pragma unroll
       for (int j = 0; j < QD; j += 8) st_row8(sm + G::DX_OFF, row, cg * QD + j, D, dxo + j);
-      if (a.do_db2) {
+      if (a.do_db2) {   // the warp's 32 rows are one virtual configuration in the per-configuration mode
 #pragma unroll
         for (int j = 0; j < QD; ++j) {
           const float t = warp_sum_f(dxo[j]);
-          if (lane == 0) atomicAdd(&db2[cg * QD + j], t);
+          if (lane == 0) {
+            if (!a.jac.nvirt) atomicAdd(&db2[cg * QD + j], t);
+            else if (tile * 4 + (warp & 3) < a.jac.nvirt) jac_put1(a.jac, tile * 4 + (warp & 3), a.off_b2 + cg * QD + j, t);
+          }
         }
       }
       ok = wait_ld(s);   // this tile's Xmid image
@@ -350,13 +429,45 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       if (threadIdx.x == 0) {
         tc_fence_after();
         mma_kk(s, dus, w1, G::HC, D, G::C_DX, false);              // dX' part = dU W1_c^T
-        mma_mm(s, dus, G::HC, xs, D, D, G::C_W1, !first);          // dW1_c^T += dU^T Xmid
-        mma_mm(s, gs, G::HC, dxs, D, D, G::C_W2, !first);          // dW2_c   += G^T dX
-        mma_mm(s, dus, G::HC, ones, 16, 16, G::C_B1, !first);       // db1_c   += dU^T 1
+        if (!a.jac.nvirt) {
+          mma_mm(s, dus, G::HC, xs, D, D, G::C_W1, !first);          // dW1_c^T += dU^T Xmid
+          mma_mm(s, gs, G::HC, dxs, D, D, G::C_W2, !first);          // dW2_c   += G^T dX
+          mma_mm(s, dus, G::HC, ones, 16, 16, G::C_B1, !first);       // db1_c   += dU^T 1
+        } else {   // per configuration: dW1_c^T into columns [64 c, 64 c + 64) (U and dG are consumed)
+          for (int c = 0; c < 4; ++c) {
+            mma_mm_rows(s, dus, G::HC, xs, D, D, 64 * c, 32 * c, 2);
+            mma_mm_rows(s, dus, G::HC, ones, 16, 16, G::C_JB1 + 16 * c, 32 * c, 2);
+          }
+        }
         mma_commit(s.bar_mma);
       }
       ok = wait_mma(s);
       if (!sync_ok(s, ok)) break;
+      if (a.jac.nvirt) {
+        const int F = a.F;
+        auto i1 = [&](int m, int nn) -> long long { return a.off_w1 + (long long)nn * F + m; };
+        jac_flush<decltype(i1), NQ>(s, a.jac, tile, 0, D, i1);
+        {   // db1 per configuration: column 0 of each 16-column block, lane m = hidden unit
+          float re[16], im[16];
+          for (int pr = 0; pr < 2; ++pr) {
+            tmem_ld16(s.tmem + lane_addr + G::C_JB1 + 16 * (2 * pr), re);
+            tmem_ld16(s.tmem + lane_addr + G::C_JB1 + 16 * (2 * pr + 1), im);
+            const size_t v0 = tile * 4 + 2 * pr;
+            if (cg == 0 && v0 + 1 < a.jac.nvirt) jac_put2(a.jac, v0 >> 1, a.off_b1 + row, re[0], im[0]);
+          }
+        }
+        tc_fence_before();
+        if (!sync_ok(s, true)) break;
+        if (threadIdx.x == 0) {
+          tc_fence_after();
+          for (int c = 0; c < 4; ++c) mma_mm_rows(s, gs, G::HC, dxs, D, D, 64 * c, 32 * c, 2);   // dW2_c per config
+          mma_commit(s.bar_mma);
+        }
+        ok = wait_mma(s);
+        if (!sync_ok(s, ok)) break;
+        auto i2 = [&](int m, int nn) -> long long { return a.off_w2 + (long long)m * D + nn; };
+        jac_flush<decltype(i2), NQ>(s, a.jac, tile, 0, D, i2);
+      }
 #pragma unroll
       for (int j = 0; j < QD; j += 16) {
         float v[16];
@@ -372,7 +483,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       __syncthreads();
     }
   }
-  if (!s.bad && !first) {
+  if (!s.bad && !first && !a.jac.nvirt) {
     float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
     const int F = a.F;
     // dW1_c^T block: lane m = hidden unit (of this half), column n = input feature i
@@ -406,6 +517,7 @@ struct A1Geo {
   static constexpr int M_OFF = F_OFF + 4 * kRows * KS * 4;
   static constexpr int BYTES = M_OFF + 64;
   static constexpr int C_QKV = 0, C_DH = 3 * D, C_WO = 256;
+  static constexpr int C_JWO = 256;   // per-configuration mode: 4 x D dWo columns
   static_assert(3 * kRows * 8 * 4 <= W_BYTES, "stats fit the weight region");
 };
 
@@ -420,6 +532,7 @@ struct A1Args {
   size_t g_stride;
   long long off_wo;
   int *err;
+  JacOut jac;
 };
 
 template <int D, int HD>
@@ -609,15 +722,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
     if (!sync_ok(s, true)) break;
     if (threadIdx.x == 0) {
       tc_fence_after();
-      mma_mm(s, hs, 128, dxs, D, D, G::C_WO, !first);   // dWo += H^T dX'   (rows of H beyond D are zero)
+      if (!a.jac.nvirt) {
+        mma_mm(s, hs, 128, dxs, D, D, G::C_WO, !first);   // dWo += H^T dX'   (rows of H beyond D are zero)
+      } else {
+        for (int c = 0; c < 4; ++c) mma_mm_rows(s, hs, 128, dxs, D, D, G::C_JWO + 64 * c, 32 * c, 2);
+      }
       mma_commit(s.bar_mma);
     }
     ok = wait_mma(s);
     first = false;
+    if (a.jac.nvirt) {
+      if (!sync_ok(s, ok)) break;
+      auto iwo = [&](int m, int nn) -> long long { return m < D ? a.off_wo + (long long)m * D + nn : -1; };
+      jac_flush<decltype(iwo), 2>(s, a.jac, tile, G::C_JWO, D, iwo);
+    }
     tc_fence_before();
     if (!sync_ok(s, ok)) break;
   }
-  if (!s.bad && !first) {
+  if (!s.bad && !first && !a.jac.nvirt) {
     float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
     flush_block(s, G::C_WO, D, g, [&](int m, int nn) -> long long {
       return m < D ? a.off_wo + (long long)m * D + nn : -1;
@@ -636,8 +758,8 @@ struct A2Geo {
   static constexpr int XR_OFF = W_OFF + W_BYTES;        // X image as stored [128][D]
   static constexpr int XP_OFF = XR_OFF + IMG;           // X padded [128][128] (columns >= D zero)
   static constexpr int DQ_OFF = XP_OFF + kRows * 128 * 2;   // [dQ dK dV] image [128][3D]
-  static constexpr int M_OFF = DQ_OFF + QIMG;           // misc: bars, holder, dE [4][D]
-  static constexpr int BYTES = M_OFF + 64 + 4 * 4 * D;
+  static constexpr int M_OFF = DQ_OFF + QIMG;           // misc: bars, holder, dE [4][4][D]
+  static constexpr int BYTES = M_OFF + 64 + 4 * 4 * 4 * D;
   static constexpr int C_W = 0, C_DX = 256;
 };
 
@@ -654,6 +776,7 @@ struct A2Args {
   size_t g_stride;
   long long off_wq, off_wk, off_wv, off_e;
   int *err;
+  JacOut jac;
 };
 
 template <int D>
@@ -663,8 +786,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
   constexpr int HALF = D / 2;
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
-  float *dE = reinterpret_cast<float *>(sm + G::M_OFF + 64);
-  for (int i = threadIdx.x; i < 4 * D; i += kThreads) dE[i] = 0.f;
+  float *dE = reinterpret_cast<float *>(sm + G::M_OFF + 64);   // [4][D], or [4 configurations][4][D]
+  for (int i = threadIdx.x; i < 4 * 4 * D; i += kThreads) dE[i] = 0.f;
   for (int i = threadIdx.x; i < kRows * 128 * 2 / 16; i += kThreads)
     reinterpret_cast<uint4 *>(sm + G::XP_OFF)[i] = make_uint4(0, 0, 0, 0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -701,12 +824,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
       if (!sync_ok(s, true)) break;
       if (threadIdx.x == 0) {
         tc_fence_after();
-        mma_mm(s, xp, 128, dq, 3 * D, 3 * D, G::C_W, !first);   // dWqkv += X^T [dQ dK dV]
+        if (!a.jac.nvirt) mma_mm(s, xp, 128, dq, 3 * D, 3 * D, G::C_W, !first);   // dWqkv += X^T [dQ dK dV]
         mma_kk(s, dq, wq, 3 * D, D, G::C_DX, false);            // [dQ dK dV] Wqkv^T
         mma_commit(s.bar_mma);
       }
       ok = wait_mma(s);
       if (!sync_ok(s, ok)) break;
+      if (a.jac.nvirt) {   // dWq, dWk, dWv per configuration, one 4 x D column block at a time
+        bool fine = true;
+        for (int part = 0; part < 3 && fine; ++part) {
+          if (threadIdx.x == 0) {
+            tc_fence_after();
+            // columns [D part, D part + D) of the [dQ dK dV] image start (D / 8) MN groups (128 B each) in
+            for (int c = 0; c < 4; ++c)
+              mma_mm_rows(s, xp, 128, dq + part * (D / 8) * 128, 3 * D, D, 64 * c, 32 * c, 2);
+            mma_commit(s.bar_mma);
+          }
+          fine = wait_mma(s);
+          if (!sync_ok(s, fine)) break;
+          const long long off = part == 0 ? a.off_wq : part == 1 ? a.off_wk : a.off_wv;
+          auto iw = [&](int m, int nn) -> long long { return m < D ? off + (long long)m * D + nn : -1; };
+          jac_flush<decltype(iw), 2>(s, a.jac, tile, 0, D, iw);
+          tc_fence_before();
+          if (!sync_ok(s, true)) break;
+        }
+        if (s.bad) break;
+      }
       float out[HALF];
 #pragma unroll
       for (int j = 0; j < HALF; j += 16) {
@@ -725,16 +868,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
           const uint32_t w1 = (sqn & 1) ? a.sigp[b] : a.sig[b];
           const uint32_t w2 = (sqn & 1) ? a.sig[b] : a.sigp[b];
           const int pat = embed_pattern(0, w1, w2, i, n);
+          // per-configuration mode: one [4][D] block per virtual configuration (sqn >> 1) of the tile
+          float *dst = a.jac.nvirt ? dE + (sqn >> 1) * 4 * D : dE;
 #pragma unroll
-          for (int j = 0; j < HALF; ++j) atomicAdd(&dE[pat * D + half * HALF + j], out[j]);
+          for (int j = 0; j < HALF; ++j) atomicAdd(&dst[pat * D + half * HALF + j], out[j]);
         }
+      }
+      if (a.jac.nvirt && a.embed_grad) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * 4 * D; i += kThreads) {
+          const size_t v = tile * 4 + i / (4 * D);
+          if (v < a.jac.nvirt) jac_put1(a.jac, v, a.off_e + i % (4 * D), dE[i]);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * 4 * D; i += kThreads) dE[i] = 0.f;
       }
       first = false;
       tc_fence_before();
       __syncthreads();
     }
   }
-  if (!s.bad && !first) {
+  if (!s.bad && !first && !a.jac.nvirt) {
     float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
     flush_block(s, G::C_W, 3 * D, g, [&](int m, int nn) -> long long {
       if (m >= D) return -1;
@@ -819,11 +973,46 @@ struct BwdTcBuffers {
   size_t tiles;
 };
 
-// The whole tensor-core VJP given the forward's parked activations and the row cotangents.
+// Output of the per-configuration mode (log-derivatives); nvirt = 0 selects the VJP.
+struct BwdTcJac {
+  float *o32;
+  uint16_t *o16;
+  const float2 *oref;
+  size_t ldo, nvirt;
+};
+
+bool bwdtc_jac_supported(const DevModel &m) { return bwdtc_supported(m) && m.n_sites == 16; }
+
+// Virtual configurations of the per-configuration mode: v = 2 b + seed, cotangent (1, 0) or (0, -1).
+namespace tdo {
+namespace bwdtc {
+__global__ void k_jac_virtual(const uint32_t *__restrict__ sig, const uint32_t *__restrict__ sigp, size_t Ns,
+                              uint32_t *__restrict__ vs, uint32_t *__restrict__ vp, float2 *__restrict__ vc) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 2 * Ns; i += gridDim.x * (size_t)blockDim.x) {
+    vs[i] = sig[i >> 1];
+    vp[i] = sigp[i >> 1];
+    vc[i] = (i & 1) ? make_float2(0.f, -1.f) : make_float2(1.f, 0.f);
+  }
+}
+}  // namespace bwdtc
+}  // namespace tdo
+
+cudaError_t launch_jac_virtual(const uint32_t *sig, const uint32_t *sigp, size_t Ns, uint32_t *vs, uint32_t *vp,
+                               float2 *vc, cudaStream_t st) {
+  const unsigned grid = (unsigned)((2 * Ns + 255) / 256 < 4096 ? (2 * Ns + 255) / 256 : 4096);
+  tdo::bwdtc::k_jac_virtual<<<grid ? grid : 1, 256, 0, st>>>(sig, sigp, Ns, vs, vp, vc);
+  return cudaGetLastError();
+}
+
+// The whole tensor-core VJP given the forward's parked activations and the row cotangents; with jac
+// (nvirt > 0) the per-configuration log-derivatives of the virtual configurations instead (gacc unused).
 cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcLayer *views, const BwdTcBuffers &bf,
                          const uint32_t *sig, const uint32_t *sigp, size_t B, const float2 *cot, float *gacc,
-                         size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st) {
+                         size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st,
+                         const BwdTcJac *jac) {
   using namespace tdo::bwdtc;
+  JacOut jo{nullptr, nullptr, nullptr, 0, 0};
+  if (jac) jo = JacOut{jac->o32, jac->o16, jac->oref, jac->ldo, jac->nvirt};
   constexpr int D = 64;
   const int n = m.n_sites, ts = tdo::seqs_per_tile(n), tc = ts / 2;
   const size_t tiles = bf.tiles, Bpad = tiles * tc;
@@ -833,7 +1022,7 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
   const long long off_e = fo[0], off_wh = fo[1 + 8 * TDO_MAX_LAYERS], off_bh = fo[2 + 8 * TDO_MAX_LAYERS];
   cudaError_t e;
   {
-    HeadArgs h{cot, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, gacc, g_stride, off_wh, off_bh, D};
+    HeadArgs h{cot, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, gacc, g_stride, off_wh, off_bh, D, jo};
     const unsigned grid = (unsigned)((Bpad + 255) / 256 < 1024 ? (Bpad + 255) / 256 : 1024);
     k_head_bwd<<<grid ? grid : 1, 256, (2 * D + 2) * sizeof(float), st>>>(h);
     k_head_dx<<<(unsigned)(tiles * kRows * D / 256 < 65535 * 8 ? (tiles * kRows * D + 255) / 256 : 65535 * 8), 256, 0,
@@ -875,6 +1064,7 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
         ma.off_b2 = b2[l];
         ma.F = m.ffn;
         ma.err = err;
+        ma.jac = jo;
         k_bwd_mlp<D><<<grid, kMlpThreads, MlpGeo<D>::BYTES, st>>>(ma);
       }
       dxmid = bf.dxb;
@@ -893,6 +1083,7 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
     a1.g_stride = g_stride;
     a1.off_wo = Wo[l];
     a1.err = err;
+    a1.jac = jo;
     if (m.dh == 8) k_bwd_attn1<D, 8><<<grid, kThreads, A1Geo<D>::BYTES, st>>>(a1);
     else k_bwd_attn1<D, 16><<<grid, kThreads, A1Geo<D>::BYTES, st>>>(a1);
     A2Args a2;
@@ -915,6 +1106,7 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
     a2.off_wv = Wv[l];
     a2.off_e = off_e;
     a2.err = err;
+    a2.jac = jo;
     k_bwd_attn2<D><<<grid, kThreads, A2Geo<D>::BYTES, st>>>(a2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

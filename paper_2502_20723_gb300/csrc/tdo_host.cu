@@ -53,9 +53,19 @@ struct BwdTcBuffers {
 size_t bwdtc_packed_bytes(const DevModel &m);
 bool bwdtc_supported(const DevModel &m);
 cudaError_t launch_pack_bwdtc(const DevModel &m, uint8_t *dst, BwdTcLayer *views, cudaStream_t st);
+struct BwdTcJac {
+  float *o32;
+  uint16_t *o16;
+  const float2 *oref;
+  size_t ldo, nvirt;
+};
+bool bwdtc_jac_supported(const DevModel &m);
+cudaError_t launch_jac_virtual(const uint32_t *sig, const uint32_t *sigp, size_t Ns, uint32_t *vs, uint32_t *vp,
+                               float2 *vc, cudaStream_t st);
 cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcLayer *views, const BwdTcBuffers &bf,
                          const uint32_t *sig, const uint32_t *sigp, size_t B, const float2 *cot, float *gacc,
-                         size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st);
+                         size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st,
+                         const BwdTcJac *jac = nullptr);
 cudaError_t launch_fwd_bf16_store(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                                   const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
                                   cudaStream_t st, uint8_t *x_img, uint8_t *xmid_img, float *h, float *f,
@@ -109,6 +119,7 @@ struct tdo_ctx {
   DBuf theta64, theta32, etab, tensor_tab, wbf16, errflag, wbwd;
   DBuf dtab;   // conv embedding: per-pattern table gradients
   DBuf oref, oref_scratch;   // BF16-stored O for SR: per-parameter shift and its FP32 sample
+  DBuf jac_vs, jac_vp, jac_vc, jac_lr;   // tensor-core log-derivatives: virtual configurations
   DevModel dm{};
   DevModelBF16 dmb{};
   bool tc_bwd = false;                 // tensor-core gradient (BF16 contexts whose shape it supports)
@@ -525,7 +536,7 @@ extern "C" tdo_status tdo_destroy(tdo_ctx *c) {
                   &c->l2, &c->stats, &c->nonfinite, &c->cot, &c->gacc, &c->scratch, &c->grad, &c->Obuf,
                   &c->srwork, &c->delta, &c->acc_u64, &c->wbf16, &c->errflag, &c->wbwd, &c->act_x, &c->act_xmid,
                   &c->act_h, &c->act_f, &c->act_dF, &c->act_dxa, &c->act_dxb, &c->act_dqkv, &c->dtab,
-                  &c->oref, &c->oref_scratch};
+                  &c->oref, &c->oref_scratch, &c->jac_vs, &c->jac_vp, &c->jac_vc, &c->jac_lr};
   for (DBuf *b : bufs) b->release();
   for (auto &r : c->trec) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : c->epool) cudaEventDestroy(e);
@@ -741,11 +752,16 @@ static tdo_status vjp_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, si
   return TDO_OK;
 }
 
+static tdo_status jacobian_tc(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t Ns, float *O32,
+                              uint16_t *O16, const float2 *oref, size_t ldo);
+
 // Log-derivatives of B configurations: FP32 into O, or (O16 non-null) BF16 of O - oref; rows of ldo
-// elements (0: P).
+// elements (0: P).  BF16 contexts whose tensor-core backward covers the model take the tensor-core
+// path (per-configuration MMAs); the rest the FP32 backward.
 static tdo_status jacobian_dev(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t B, float *O,
                                uint16_t *O16 = nullptr, const float2 *oref = nullptr, size_t ldo = 0) {
   if (!ldo) ldo = c->P;
+  if (c->tc_bwd && bwdtc_jac_supported(c->dm)) return jacobian_tc(c, ds, dp, B, O, O16, oref, ldo);
   const bool conv = c->model.embed == TDO_EMBED_CONV;
   const int grid = bwd32_grid(c->dm, B, 1, c->n_sm);
   CU(c, c->scratch.ensure(sizeof(float) * bwd32_scratch_floats(c->dm, grid)));
@@ -861,6 +877,43 @@ static tdo_status vjp_tc(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, siz
                      c->errflag.as<int>(), c->n_sm, c->stream));
   CU(c, launch_reduce_copies(c->gacc.as<float>(), copies, stride, c->P, grad, 0, c->stream));
   tm.done(2 + (long long)c->dm.layers * (2 + (c->dm.ffn > 0 ? c->dm.ffn / 128 : 0)) + 1);
+  return TDO_OK;
+}
+
+// Tensor-core log-derivatives: the Ns samples become 2 Ns virtual configurations (one per real cotangent
+// seed), the BF16 forward parks their activations, and the backward writes each configuration's weight
+// gradients (per-configuration MMAs over its 32 rows) to O[b][k] = (seed 0, seed 1).
+static tdo_status jacobian_tc(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, size_t Ns, float *O32,
+                              uint16_t *O16, const float2 *oref, size_t ldo) {
+  const size_t nv = 2 * Ns;
+  const size_t tiles = tc_tiles(c, nv);
+  const int ts = 2 * (128 / (2 * c->n)) < 2 ? 2 : 2 * (128 / (2 * c->n));
+  const size_t D = c->dm.d, img = (size_t)128 * D * 2, L = c->dm.layers;
+  CU(c, c->jac_vs.ensure(4 * nv));
+  CU(c, c->jac_vp.ensure(4 * nv));
+  CU(c, c->jac_vc.ensure(sizeof(float2) * nv));
+  CU(c, c->jac_lr.ensure(sizeof(float2) * nv));
+  CU(c, c->act_x.ensure(L * tiles * img));
+  CU(c, c->act_xmid.ensure(c->dm.ffn > 0 ? L * tiles * img : 16));
+  CU(c, c->act_h.ensure(sizeof(float) * tiles * ts * D));
+  CU(c, c->act_f.ensure(sizeof(float) * tiles * ts * 2));
+  CU(c, c->act_dF.ensure(sizeof(float) * tiles * ts * 2));
+  CU(c, c->act_dxa.ensure(sizeof(float) * tiles * 128 * D));
+  CU(c, c->act_dxb.ensure(sizeof(float) * tiles * 128 * D));
+  CU(c, c->act_dqkv.ensure(tiles * 128 * 3 * D * 2));
+  uint32_t *vs = c->jac_vs.as<uint32_t>(), *vp = c->jac_vp.as<uint32_t>();
+  Timed tm(c, G_BWD_JAC);
+  CU(c, launch_jac_virtual(ds, dp, Ns, vs, vp, c->jac_vc.as<float2>(), c->stream));
+  CU(c, launch_fwd_bf16_store(c->dm, c->dmb, vs, vp, nv, c->jac_lr.as<float2>(), c->errflag.as<int>(), c->n_sm,
+                              c->stream, c->act_x.as<uint8_t>(), c->dm.ffn > 0 ? c->act_xmid.as<uint8_t>() : nullptr,
+                              c->act_h.as<float>(), c->act_f.as<float>(), tiles));
+  BwdTcBuffers bf{c->act_x.as<uint8_t>(), c->act_xmid.as<uint8_t>(), c->act_dqkv.as<uint8_t>(), c->act_h.as<float>(),
+                  c->act_f.as<float>(), c->act_dF.as<float>(), c->act_dxa.as<float>(), c->act_dxb.as<float>(), tiles};
+  BwdTcJac jac{O32, O16, oref, ldo, nv};
+  CU(c, launch_bwdtc(c->dm, c->dmb, c->bwl, bf, vs, vp, nv, c->jac_vc.as<float2>(), nullptr, 0, c->flat_offsets,
+                     c->errflag.as<int>(), c->n_sm, c->stream, &jac));
+  tm.done(4 + (long long)c->dm.layers * (2 + (c->dm.ffn > 0 ? c->dm.ffn / 128 : 0)));
+  TRY(check_err_flag(c));
   return TDO_OK;
 }
 
