@@ -11,6 +11,8 @@
 // m16n8k8 uses a0, a1 and b0 only.  The C fragments of the two key halves of a score block are,
 // packed pairwise, the A fragment of the same block, and movmatrix transposes an 8 x 8 piece.
 #pragma once
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "tcgen05.cuh"
@@ -200,6 +202,74 @@ __device__ __forceinline__ void attn_fwd_bwd(const float *Q, const float *K, con
       if (g < n) emit(3, g, 8 * c + 2 * t, y[c][0], y[c][1]);
       if (g + 8 < n) emit(3, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
     }
+  }
+}
+
+// Forward only, operands already FP16 in shared memory (the forward kernel's layout):
+//   Qh, Kh: [rows][ldh] halves, this sequence's rows from 0 (Q pre-scaled by 1/sqrt(HD) log2 e),
+//   Vt:     [features][ldt] halves, V transposed, this sequence's keys at columns 0..15 (keys >= n zero),
+// all with 4-byte-aligned pairs.  emit(row, col, v0, v1) for the attention output O, row < n.
+template <int HD, typename EMIT>
+__device__ __forceinline__ void attn_fwd_h(const __half *Qh, const __half *Kh, const __half *Vt, int ldh, int ldt,
+                                           int n, EMIT emit) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  auto ld2 = [&](const __half *M, int r, int c) -> uint32_t {
+    return r < n ? *reinterpret_cast<const uint32_t *>(M + r * ldh + c) : 0u;
+  };
+  float s[2][4];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) zero4(s[j]);
+  if (HD == 8) {
+    const uint32_t a0 = ld2(Qh, g, 2 * t), a1 = ld2(Qh, g + 8, 2 * t);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) mma1688(s[j], a0, a1, ld2(Kh, 8 * j + g, 2 * t));
+  } else {
+    const uint32_t a[4] = {ld2(Qh, g, 2 * t), ld2(Qh, g + 8, 2 * t), ld2(Qh, g, 8 + 2 * t), ld2(Qh, g + 8, 8 + 2 * t)};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) mma16816(s[j], a, ld2(Kh, 8 * j + g, 2 * t), ld2(Kh, 8 * j + g, 8 + 2 * t));
+  }
+  float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const bool ok = 8 * j + 2 * t + e < n;
+      s[j][e] = ok ? s[j][e] : -INFINITY;
+      s[j][2 + e] = ok ? s[j][2 + e] : -INFINITY;
+      m0 = fmaxf(m0, s[j][e]);
+      m1 = fmaxf(m1, s[j][2 + e]);
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      s[j][e] = tc::ex2_fast(s[j][e] - m0);
+      s[j][2 + e] = tc::ex2_fast(s[j][2 + e] - m1);
+      l0 += s[j][e];
+      l1 += s[j][2 + e];
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+  }
+  const float i0 = 1.f / l0, i1 = 1.f / l1;
+  const uint32_t pa[4] = {h2(s[0][0] * i0, s[0][1] * i0), h2(s[0][2] * i1, s[0][3] * i1),
+                          h2(s[1][0] * i0, s[1][1] * i0), h2(s[1][2] * i1, s[1][3] * i1)};
+#pragma unroll
+  for (int c = 0; c < HD / 8; ++c) {
+    float o[4];
+    zero4(o);
+    const __half *vr = Vt + (8 * c + g) * ldt;
+    mma16816(o, pa, *reinterpret_cast<const uint32_t *>(vr + 2 * t), *reinterpret_cast<const uint32_t *>(vr + 8 + 2 * t));
+    if (g < n) emit(g, 8 * c + 2 * t, o[0], o[1]);
+    if (g + 8 < n) emit(g + 8, 8 * c + 2 * t, o[2], o[3]);
   }
 }
 

@@ -755,10 +755,10 @@ struct A2Geo {
   static constexpr int QIMG = kRows * 3 * D * 2;
   static constexpr int W_OFF = 0;                       // Wqkv rows [D][3D]
   static constexpr int W_BYTES = 3 * D * D * 2;
-  static constexpr int XR_OFF = W_OFF + W_BYTES;        // X image as stored [128][D]
-  static constexpr int XP_OFF = XR_OFF + IMG;           // X padded [128][128] (columns >= D zero)
-  static constexpr int DQ_OFF = XP_OFF + kRows * 128 * 2;   // [dQ dK dV] image [128][3D]
-  static constexpr int M_OFF = DQ_OFF + QIMG;           // misc: bars, holder, dE [4][4][D]
+  static constexpr int XR_OFF = W_OFF + W_BYTES;        // X images as stored [2][128][D] (next tile early)
+  static constexpr int XP_OFF = XR_OFF + 2 * IMG;       // X padded [128][128] (columns >= D zero)
+  static constexpr int DQ_OFF = XP_OFF + kRows * 128 * 2;   // [dQ dK dV] images [2][128][3D]
+  static constexpr int M_OFF = DQ_OFF + 2 * QIMG;       // misc: bars, holder, dE [4][4][D]
   static constexpr int BYTES = M_OFF + 64 + 4 * 4 * 4 * D;
   static constexpr int C_W = 0, C_DX = 256;
 };
@@ -793,8 +793,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (warp & 3) + lane, half = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
-  const uint32_t wq = smem_u32(sm + G::W_OFF), xr = smem_u32(sm + G::XR_OFF), xp = smem_u32(sm + G::XP_OFF),
-                 dq = smem_u32(sm + G::DQ_OFF);
+  const uint32_t wq = smem_u32(sm + G::W_OFF), xr0 = smem_u32(sm + G::XR_OFF), xp = smem_u32(sm + G::XP_OFF),
+                 dq0 = smem_u32(sm + G::DQ_OFF);
   if (threadIdx.x == 0) {
     mbar_expect_tx(s.bar_ld, G::W_BYTES);
     bulk_g2s(wq, a.wqkv, G::W_BYTES, s.bar_ld);
@@ -803,8 +803,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
   const int n = a.n, nvalid = a.ts * n, tc = a.ts / 2;
   bool first = true;
   if (sync_ok(s, ok)) {
-    for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
-      load2(s, xr, a.x + tile * (size_t)G::IMG, G::IMG, dq, a.dqkv + tile * (size_t)G::QIMG, G::QIMG);
+    if ((size_t)blockIdx.x < a.tiles)
+      load2(s, xr0, a.x + blockIdx.x * (size_t)G::IMG, G::IMG, dq0, a.dqkv + blockIdx.x * (size_t)G::QIMG, G::QIMG);
+    int buf = 0;
+    for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, buf ^= 1) {
+      const uint32_t dq = dq0 + buf * G::QIMG;
+      const uint8_t *xr_ptr = sm + G::XR_OFF + buf * G::IMG;
       const size_t rg = (tile * kRows + row) * (size_t)D + half * HALF;
       float base[HALF];
 #pragma unroll
@@ -812,13 +816,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
         const float4 q = *reinterpret_cast<const float4 *>(a.dxm + rg + j);
         base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
       }
-      ok = wait_ld(s);
+      ok = wait_ld(s);   // this tile's X and [dQ dK dV] images
       if (!sync_ok(s, ok)) break;
+      {   // the other buffers were last read by the previous tile's MMAs, which have completed
+        const size_t nxt = tile + gridDim.x;
+        if (nxt < a.tiles)
+          load2(s, xr0 + (buf ^ 1) * G::IMG, a.x + nxt * (size_t)G::IMG, G::IMG, dq0 + (buf ^ 1) * G::QIMG,
+                a.dqkv + nxt * (size_t)G::QIMG, G::QIMG);
+      }
       // X padded to 128 columns: each 8-row group of the stored image (16D bytes) -> first half of 2048
       for (int i = threadIdx.x; i < kRows / 8 * (D * 16 / 16); i += kThreads) {
         const int grp = i / (D * 16 / 16), c = i % (D * 16 / 16);
         reinterpret_cast<uint4 *>(sm + G::XP_OFF + grp * 2048)[c] =
-            reinterpret_cast<const uint4 *>(sm + G::XR_OFF + grp * D * 16)[c];
+            reinterpret_cast<const uint4 *>(xr_ptr + grp * D * 16)[c];
       }
       fence_proxy_async();
       if (!sync_ok(s, true)) break;

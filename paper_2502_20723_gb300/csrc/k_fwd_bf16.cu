@@ -18,6 +18,7 @@
 // Every mbarrier wait is bounded; on timeout the kernel sets *err, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
+#include "attn_mma.cuh"
 #include "tdo_device.cuh"
 #include "tcgen05.cuh"
 
@@ -43,6 +44,12 @@ struct Geo {
   // F [128][2] floats, results [64] float2
   static constexpr int BYTES = M_OFF + 16 + 8 + 512 + 1024 + 512;
   static_assert(2 * HC * D <= KV_BYTES, "hidden chunk fits the K/V region");
+  // warp-MMA attention (N <= 16): FP16 Q, K [128][LDH] and V transposed [D][LDT] in the K/V region,
+  // sequence s's keys at columns 16 s .. 16 s + 15 of V^T
+  static constexpr int LDH = D + 8;                              // halves; conflict-free fragment rows
+  static constexpr int QH_OFF = KV_OFF, KH_OFF = QH_OFF + kRows * LDH * 2, VT_OFF = KH_OFF + kRows * LDH * 2;
+  static constexpr int LDT = ((KV_BYTES - 2 * kRows * LDH * 2) / (D * 2)) & ~7;
+  __host__ __device__ static constexpr bool mma_attention(int n, int ts) { return n <= 16 && ts * 16 + 8 <= LDT; }
 };
 
 using namespace tdo::tc;
@@ -167,6 +174,52 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
     ok = wait_mma(c);
     if (sync_fail(c, ok)) return false;
     stage_w(c, w_addr, mb.Wo[l], D * D * 2);   // W is free: the QKV MMAs have completed
+    if (G::mma_attention(n, ts)) {
+      // ---------------- attention by warp-level MMAs, one warp per (sequence, head): FP16 Q (scaled), K
+      // and V^T to shared memory, output -> A (BF16)
+      __half *Qh = reinterpret_cast<__half *>(sm + G::QH_OFF), *Kh = reinterpret_cast<__half *>(sm + G::KH_OFF);
+      __half *Vt = reinterpret_cast<__half *>(sm + G::VT_OFF);
+      {   // TMEM loads are warp-collective: every lane loads, valid rows store
+        const int sq = valid ? row / n : 0, i = valid ? row % n : 0;
+#pragma unroll
+        for (int j = 0; j < DH; j += 16) {
+          float v[16];
+          tmem_ld16(c.tmem + lane_addr + half * DH + j, v);
+          if (valid) {
+#pragma unroll
+            for (int e = 0; e < 16; e += 2)
+              *reinterpret_cast<uint32_t *>(Qh + row * G::LDH + half * DH + j + e) =
+                  amma::h2(v[e] * qscale, v[e + 1] * qscale);
+          }
+          tmem_ld16(c.tmem + lane_addr + D + half * DH + j, v);
+          if (valid) {
+#pragma unroll
+            for (int e = 0; e < 16; e += 2)
+              *reinterpret_cast<uint32_t *>(Kh + row * G::LDH + half * DH + j + e) = amma::h2(v[e], v[e + 1]);
+          }
+          tmem_ld16(c.tmem + lane_addr + 2 * D + half * DH + j, v);
+          if (valid) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) Vt[(half * DH + j + e) * G::LDT + 16 * sq + i] = __float2half_rn(v[e]);
+          }
+        }
+      }
+      if (n < 16)   // keys n .. 15 of every sequence: zero (their probabilities are zero, V must be finite)
+        for (int idx = threadIdx.x; idx < D * ts * (16 - n); idx += kThreads) {
+          const int f = idx / (ts * (16 - n)), r = idx % (ts * (16 - n));
+          Vt[f * G::LDT + 16 * (r / (16 - n)) + n + r % (16 - n)] = __float2half_rn(0.f);
+        }
+      for (int idx = threadIdx.x; idx < (kRows - ts * n) * (D / 8); idx += kThreads)   // padding rows: O = 0
+        *reinterpret_cast<uint4 *>(A + canon(ts * n + idx / (D / 8), 8 * (idx % (D / 8)), D)) = make_uint4(0, 0, 0, 0);
+      __syncthreads();
+      for (int u = warp; u < ts * heads; u += kThreads / 32) {
+        const int sq = u / heads, h = u % heads, rb = sq * n;
+        amma::attn_fwd_h<HD>(Qh + rb * G::LDH + h * HD, Kh + rb * G::LDH + h * HD, Vt + h * HD * G::LDT + 16 * sq,
+                             G::LDH, G::LDT, n, [&](int r, int cc, float v0, float v1) {
+                               *reinterpret_cast<uint32_t *>(A + canon(rb + r, h * HD + cc, D)) = pack_bf16(v0, v1);
+                             });
+      }
+    } else {
     // K, V (FP32) to shared memory, this thread's column half
 #pragma unroll
     for (int j = 0; j < DH; j += 16) {
@@ -224,6 +277,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
 #pragma unroll
         for (int e8 = 0; e8 < HD; e8 += 8) st_row8(A, row, h * HD + e8, D, o + e8);
       }
+    }
     }
     tc_fence_before();
     fence_proxy_async();
