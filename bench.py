@@ -369,7 +369,7 @@ def run_reference(args) -> dict | None:
 def run_kernel_case(args) -> None:
     """One call of one kind on the workload's model with a reduced sample count (for ncu captures):
     fwd (log rho of all connected rows), grad (gradient backward), jac (log-derivatives), sample (one
-    sweep), sr (CG solve on the log-derivatives).  Runs the call twice (first warms up)."""
+    sweep), sr (one SR step: gradient, log-derivatives in the step's own layout, CG solve, update).  Runs the call twice (first warms up)."""
     import torch
 
     from paper_2502_20723_gb300 import build, tdo
@@ -394,9 +394,7 @@ def run_kernel_case(args) -> None:
         elif args.kernel_case == "sample":
             ctx.sample(sig, sigp, 1, 1, 0)
         elif args.kernel_case == "sr":
-            g, _ = ctx.grad(sig, sigp)
-            O = ctx.jacobian(sig, sigp)
-            ctx.sr_solve(O, g, SHIFT, tol=1e-8, max_iter=50)
+            ctx.sr_step(sig, sigp, LR, SHIFT)   # the step's own O layout (BF16 pairs in BF16 contexts)
     torch.cuda.synchronize()
     print(json.dumps({"kernel_case": args.kernel_case, "samples": args.case_samples, "rows": int(len(rows_s))}))
 

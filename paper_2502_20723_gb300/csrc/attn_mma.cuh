@@ -273,5 +273,207 @@ __device__ __forceinline__ void attn_fwd_h(const __half *Qh, const __half *Kh, c
   }
 }
 
+// ---- shared-memory fragments by ldmatrix (FP16 row-major blocks, 16-byte-aligned rows)
+__device__ __forceinline__ void ldsm2(uint32_t addr, uint32_t &r0, uint32_t &r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm2t(uint32_t addr, uint32_t &r0, uint32_t &r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+
+// A fragment of the [16][HD] block at M (row stride ldh halves): HD = 8 fills a[0..1], HD = 16 a[0..3].
+template <int HD>
+__device__ __forceinline__ void frag_a(uint32_t M, int ldh, uint32_t (&a)[4]) {
+  const int lane = threadIdx.x & 31;
+  const int r = (lane & 7) + 8 * ((lane >> 3) & 1);
+  if (HD == 8) {
+    ldsm2(M + (uint32_t)(r * ldh) * 2, a[0], a[1]);
+    a[2] = a[3] = 0u;
+  } else {
+    ldsm4(M + (uint32_t)(r * ldh + 8 * (lane >> 4)) * 2, a[0], a[1], a[2], a[3]);
+  }
+}
+// B fragments of X^T for a [16 rows = n][HD cols = k] block X: b[j][kh] = n-tile j (rows 8j..8j+7), k half kh.
+template <int HD>
+__device__ __forceinline__ void frag_bn(uint32_t M, int ldh, uint32_t (&b)[2][2]) {
+  const int lane = threadIdx.x & 31, j = lane >> 3;
+  if (HD == 8) {
+    ldsm2(M + (uint32_t)(((lane & 7) + 8 * (j & 1)) * ldh) * 2, b[0][0], b[1][0]);
+    b[0][1] = b[1][1] = 0u;
+  } else {
+    ldsm4(M + (uint32_t)(((lane & 7) + 8 * (j >> 1)) * ldh + 8 * (j & 1)) * 2, b[0][0], b[0][1], b[1][0], b[1][1]);
+  }
+}
+// B fragments of a [16 rows = k][HD cols = n] block (transposing load): b[c][kh] = n-tile c, k half kh.
+template <int HD>
+__device__ __forceinline__ void frag_bk(uint32_t M, int ldh, uint32_t (&b)[HD / 8][2]) {
+  const int lane = threadIdx.x & 31, j = lane >> 3;
+  if (HD == 8) {
+    ldsm2t(M + (uint32_t)(((lane & 7) + 8 * (j & 1)) * ldh) * 2, b[0][0], b[0][1]);
+  } else {
+    uint32_t r0, r1, r2, r3;
+    ldsm4t(M + (uint32_t)(((lane & 7) + 8 * (j & 1)) * ldh + 8 * (j >> 1)) * 2, r0, r1, r2, r3);
+    b[0][0] = r0; b[0][1] = r1; b[HD / 8 - 1][0] = r2; b[HD / 8 - 1][1] = r3;
+  }
+}
+
+// S[16][16] = A B^T over HD features (A, B: [16][HD] blocks as fragments).
+template <int HD>
+__device__ __forceinline__ void mma_s(const uint32_t (&a)[4], const uint32_t (&b)[2][2], float (&s)[2][4]) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    zero4(s[j]);
+    if (HD == 8) mma1688(s[j], a[0], a[1], b[j][0]);
+    else mma16816(s[j], a, b[j][0], b[j][1]);
+  }
+}
+// Y[16][HD] = X[16][16] M[16][HD] with X as an A fragment and M's B fragments.
+template <int HD>
+__device__ __forceinline__ void mma_y(const uint32_t (&x)[4], const uint32_t (&b)[HD / 8][2], float (&y)[HD / 8][4]) {
+#pragma unroll
+  for (int c = 0; c < HD / 8; ++c) {
+    zero4(y[c]);
+    mma16816(y[c], x, b[c][0], b[c][1]);
+  }
+}
+
+// Forward and backward of softmax attention for one (sequence, head) on one warp, FP16 operands in
+// shared memory: Qh, Kh, Vh, dHh are u32 shared addresses of this sequence's first row and this head's
+// first feature in [rows][ldh] row-major FP16 arrays (Q unscaled), readable 16 rows down (rows >= n
+// hold finite values: the next sequence or zero padding).  Keys >= n are masked; query rows >= n get
+// zero probabilities, so they add nothing to dK and dV.  emit as in attn_fwd_bwd.
+template <int HD, typename EMIT>
+__device__ __forceinline__ void attn_fwd_bwd_h(uint32_t Qh, uint32_t Kh, uint32_t Vh, uint32_t dHh, int ldh, int n,
+                                               float qscale, float scale, EMIT emit) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t qa[4], kb[2][2];
+  frag_a<HD>(Qh, ldh, qa);
+  frag_bn<HD>(Kh, ldh, kb);
+  float s[2][4];
+  mma_s<HD>(qa, kb, s);
+  const bool q0 = g < n, q1 = g + 8 < n;
+  float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const bool ok = 8 * j + 2 * t + e < n;
+      s[j][e] = ok ? s[j][e] * qscale : -INFINITY;
+      s[j][2 + e] = ok ? s[j][2 + e] * qscale : -INFINITY;
+      m0 = fmaxf(m0, s[j][e]);
+      m1 = fmaxf(m1, s[j][2 + e]);
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      s[j][e] = tc::ex2_fast(s[j][e] - m0);
+      s[j][2 + e] = tc::ex2_fast(s[j][2 + e] - m1);
+      l0 += s[j][e];
+      l1 += s[j][2 + e];
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+  }
+  const float i0 = q0 ? 1.f / l0 : 0.f, i1 = q1 ? 1.f / l1 : 0.f;   // invalid query rows: P = 0
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    s[j][0] *= i0; s[j][1] *= i0;
+    s[j][2] *= i1; s[j][3] *= i1;
+  }
+  const uint32_t pa[4] = {h2(s[0][0], s[0][1]), h2(s[0][2], s[0][3]), h2(s[1][0], s[1][1]), h2(s[1][2], s[1][3])};
+  {   // O = P V
+    uint32_t vb[HD / 8][2];
+    frag_bk<HD>(Vh, ldh, vb);
+    float o[HD / 8][4];
+    mma_y<HD>(pa, vb, o);
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      if (q0) emit(0, g, 8 * c + 2 * t, o[c][0], o[c][1]);
+      if (q1) emit(0, g + 8, 8 * c + 2 * t, o[c][2], o[c][3]);
+    }
+  }
+  // dA = dH V^T; delta_i = sum_j P_ij dA_ij; dS = scale P (dA - delta)
+  float da[2][4];
+  {
+    uint32_t ha[4], vn[2][2];
+    frag_a<HD>(dHh, ldh, ha);
+    frag_bn<HD>(Vh, ldh, vn);
+    mma_s<HD>(ha, vn, da);
+  }
+  float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    d0 = fmaf(s[j][0], da[j][0], fmaf(s[j][1], da[j][1], d0));
+    d1 = fmaf(s[j][2], da[j][2], fmaf(s[j][3], da[j][3], d1));
+  }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    da[j][0] = scale * s[j][0] * (da[j][0] - d0);
+    da[j][1] = scale * s[j][1] * (da[j][1] - d0);
+    da[j][2] = scale * s[j][2] * (da[j][2] - d1);
+    da[j][3] = scale * s[j][3] * (da[j][3] - d1);
+  }
+  const uint32_t x00 = h2(da[0][0], da[0][1]), x10 = h2(da[0][2], da[0][3]), x01 = h2(da[1][0], da[1][1]),
+                 x11 = h2(da[1][2], da[1][3]);
+  {   // dQ = dS K
+    const uint32_t dsa[4] = {x00, x10, x01, x11};
+    uint32_t b[HD / 8][2];
+    frag_bk<HD>(Kh, ldh, b);
+    float y[HD / 8][4];
+    mma_y<HD>(dsa, b, y);
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      if (q0) emit(1, g, 8 * c + 2 * t, y[c][0], y[c][1]);
+      if (q1) emit(1, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
+    }
+  }
+  {   // dK = dS^T Q
+    const uint32_t dst[4] = {trans8(x00), trans8(x01), trans8(x10), trans8(x11)};
+    uint32_t b[HD / 8][2];
+    frag_bk<HD>(Qh, ldh, b);
+    float y[HD / 8][4];
+    mma_y<HD>(dst, b, y);
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      if (q0) emit(2, g, 8 * c + 2 * t, y[c][0], y[c][1]);
+      if (q1) emit(2, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
+    }
+  }
+  {   // dV = P^T dH
+    const uint32_t pt[4] = {trans8(pa[0]), trans8(pa[2]), trans8(pa[1]), trans8(pa[3])};
+    uint32_t b[HD / 8][2];
+    frag_bk<HD>(dHh, ldh, b);
+    float y[HD / 8][4];
+    mma_y<HD>(pt, b, y);
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      if (q0) emit(3, g, 8 * c + 2 * t, y[c][0], y[c][1]);
+      if (q1) emit(3, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
+    }
+  }
+}
+
 }  // namespace amma
 }  // namespace tdo

@@ -12,7 +12,8 @@
 //                U = Xmid W1, dG = dX W2^T (MMA), dU = dG gelu'(U) (CUDA cores),
 //                dX' = dX + dU W1^T, dW1^T += dU^T Xmid, dW2 += G^T dX (MMA, MN-major operands)
 //              k_bwd_attn1: QKV = X Wqkv, dH = dX' Wo^T (MMA); softmax attention forward and backward
-//                per (sequence, head) on the CUDA cores -> dQ, dK, dV (BF16 images); dWo += H^T dX'
+//                per (sequence, head) by warp-level MMAs on FP16 copies -> dQ, dK, dV (BF16 images);
+//                dWo += H^T dX'  (sequences of at most 16 tokens)
 //              k_bwd_attn2: dWqkv += X^T [dQ dK dV], dX = dX' + [dQ dK dV] Wqkv^T (MMA); embedding
 //                gradient at the first layer
 // Weight-gradient MMAs read the row-major activation images as MN-major operands: M or N = the
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       for (int j = 0; j < QD; j += 4) {
         const float4 v = *reinterpret_cast<const float4 *>(a.dxo + rg + j);
         dxo[j] = v.x; dxo[j + 1] = v.y; dxo[j + 2] = v.z; dxo[j + 3] = v.w;
-        const float4 q = *reinterpret_cast<const float4 *>(a.base + rg + j);
+        const float4 q = a.base == a.dxo ? v : *reinterpret_cast<const float4 *>(a.base + rg + j);
         base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
       }
 #pragma unroll
@@ -504,21 +505,26 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
 }
 
 // ====================================================================================== attention pass 1
+// Sequences of N <= 16 tokens: one warp per (sequence, head) does the softmax attention forward and
+// backward with warp-level MMAs on FP16 copies of Q, K, V, dH (row stride D + 8 halves: ldmatrix rows
+// on distinct banks; 16 zero rows after the tile so the last sequence's 16-row blocks stay in bounds).
 template <int D>
 struct A1Geo {
-  static constexpr int KS = D + 1;
   static constexpr int IMG = kRows * D * 2;
-  static constexpr int W_OFF = 0;                      // Wqkv^T [3D][D], later Wo rows [D][D], then stats
+  static constexpr int LDH = D + 8;
+  static constexpr int HROWS = kRows + 16;
+  static constexpr int W_OFF = 0;                      // Wqkv^T [3D][D] (the forward's image), kept
   static constexpr int W_BYTES = 3 * D * D * 2;
-  static constexpr int X_OFF = W_OFF + W_BYTES;        // X image
-  static constexpr int DX_OFF = X_OFF + IMG;           // dX' BF16 image
+  static constexpr int WO_OFF = W_OFF + W_BYTES;       // Wo rows [D][D], kept
+  static constexpr int X_OFF = WO_OFF + D * D * 2;     // X images [2][128][D] (the next tile's early)
+  static constexpr int DX_OFF = X_OFF + 2 * IMG;       // dX' BF16 image
   static constexpr int H_OFF = DX_OFF + IMG;           // head outputs [128][128] BF16 (upper half zero)
-  static constexpr int F_OFF = H_OFF + kRows * 128 * 2;   // Q, K, V, dH FP32 [128][KS] each
-  static constexpr int M_OFF = F_OFF + 4 * kRows * KS * 4;
+  static constexpr int F_OFF = H_OFF + kRows * 128 * 2;   // Q, K, V, dH FP16 [HROWS][LDH] each
+  static constexpr int F_BYTES = HROWS * LDH * 2;
+  static constexpr int M_OFF = F_OFF + 4 * F_BYTES;
   static constexpr int BYTES = M_OFF + 64;
   static constexpr int C_QKV = 0, C_DH = 3 * D, C_WO = 256;
   static constexpr int C_JWO = 256;   // per-configuration mode: 4 x D dWo columns
-  static_assert(3 * kRows * 8 * 4 <= W_BYTES, "stats fit the weight region");
 };
 
 struct A1Args {
@@ -539,205 +545,123 @@ template <int D, int HD>
 __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
   using G = A1Geo<D>;
   extern __shared__ __align__(1024) uint8_t sm[];
-  constexpr int HALF = D / 2, KS = G::KS;
+  constexpr int HALF = D / 2, LDH = G::LDH;
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (warp & 3) + lane, half = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
-  const uint32_t wr = smem_u32(sm + G::W_OFF), xs = smem_u32(sm + G::X_OFF), dxs = smem_u32(sm + G::DX_OFF),
-                 hs = smem_u32(sm + G::H_OFF);
-  float *Qs = reinterpret_cast<float *>(sm + G::F_OFF), *Ks = Qs + kRows * KS, *Vs = Ks + kRows * KS,
-        *dHs = Vs + kRows * KS;
-  float *st_m = reinterpret_cast<float *>(sm + G::W_OFF), *st_l = st_m + kRows * 8, *st_d = st_l + kRows * 8;
+  const uint32_t wr = smem_u32(sm + G::W_OFF), wo = smem_u32(sm + G::WO_OFF), xs0 = smem_u32(sm + G::X_OFF),
+                 dxs = smem_u32(sm + G::DX_OFF), hs = smem_u32(sm + G::H_OFF), f16 = smem_u32(sm + G::F_OFF);
+  __half *Fh = reinterpret_cast<__half *>(sm + G::F_OFF);   // Q, K, V, dH at multiples of HROWS * LDH
   for (int i = threadIdx.x; i < kRows * 128 * 2 / 16; i += kThreads)
     reinterpret_cast<uint4 *>(sm + G::H_OFF)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < 4 * 16 * LDH / 8; i += kThreads) {   // the 16 rows after each tile block
+    const int arr = i / (16 * LDH / 8), k = i % (16 * LDH / 8);
+    reinterpret_cast<uint4 *>(Fh + arr * G::HROWS * LDH + kRows * LDH)[k] = make_uint4(0, 0, 0, 0);
+  }
   const int n = a.n, heads = a.heads, nvalid = a.ts * n;
   const bool valid = row < nvalid;
-  const int sq = valid ? row / n : 0;
   const float qscale = rsqrtf((float)HD) * 1.4426950408889634f;   // scores in base 2
   const float scale = rsqrtf((float)HD);
+  if (threadIdx.x == 0) {   // both weight images once per kernel
+    mbar_expect_tx(s.bar_ld, G::W_BYTES + D * D * 2);
+    bulk_g2s(wr, a.wqkvT, G::W_BYTES, s.bar_ld);
+    bulk_g2s(wo, a.wo, D * D * 2, s.bar_ld);
+  }
+  bool ok = wait_ld(s);
   bool first = true;
-  for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
-    load2(s, xs, a.x + tile * (size_t)G::IMG, G::IMG, wr, a.wqkvT, G::W_BYTES);
-    const size_t rg = (tile * kRows + row) * (size_t)D + half * HALF;
-    {
-      float v[HALF];
+  if (sync_ok(s, ok)) {
+    if ((size_t)blockIdx.x < a.tiles) load2(s, xs0, a.x + blockIdx.x * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+    int buf = 0;
+    for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, buf ^= 1) {
+      const uint32_t xs = xs0 + buf * G::IMG;
+      const size_t rg = (tile * kRows + row) * (size_t)D + half * HALF;
+      {
+        float v[HALF];
 #pragma unroll
-      for (int j = 0; j < HALF; j += 4) {
-        const float4 q = *reinterpret_cast<const float4 *>(a.dxm + rg + j);
-        v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
+        for (int j = 0; j < HALF; j += 4) {
+          const float4 q = *reinterpret_cast<const float4 *>(a.dxm + rg + j);
+          v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
+        }
+#pragma unroll
+        for (int j = 0; j < HALF; j += 8) st_row8(sm + G::DX_OFF, row, half * HALF + j, D, v + j);
       }
+      ok = wait_ld(s);   // this tile's X image
+      fence_proxy_async();
+      if (!sync_ok(s, ok)) break;
+      {   // the other X buffer was last read by the previous tile's MMAs, which have completed
+        const size_t nxt = tile + gridDim.x;
+        if (nxt < a.tiles) load2(s, xs0 + (buf ^ 1) * G::IMG, a.x + nxt * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+      }
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        mma_kk(s, xs, wr, D, 3 * D, G::C_QKV, false);   // Q, K, V
+        mma_kk(s, dxs, wo, D, D, G::C_DH, false);       // dH = dX' Wo^T
+        mma_commit(s.bar_mma);
+      }
+      ok = wait_mma(s);
+      if (!sync_ok(s, ok)) break;
+      // Q, K, V, dH -> FP16 rows (TMEM loads are warp-collective; rows past the tile's sequences stay)
 #pragma unroll
-      for (int j = 0; j < HALF; j += 8) st_row8(sm + G::DX_OFF, row, half * HALF + j, D, v + j);
-    }
-    bool ok = wait_ld(s);
-    fence_proxy_async();
-    if (!sync_ok(s, ok)) break;
-    if (threadIdx.x == 0) {
-      tc_fence_after();
-      mma_kk(s, xs, wr, D, 3 * D, G::C_QKV, false);   // Q, K, V
-      mma_commit(s.bar_mma);
-    }
-    ok = wait_mma(s);
-    if (!sync_ok(s, ok)) break;
-    load2(s, wr, a.wo, D * D * 2, 0, nullptr, 0);    // W is free: the QKV MMA has completed
+      for (int part = 0; part < 4; ++part) {
+        const int col0 = part < 3 ? G::C_QKV + part * D : G::C_DH;
+        __half *dst = Fh + part * G::HROWS * LDH + row * LDH + half * HALF;
 #pragma unroll
-    for (int j = 0; j < HALF; j += 16) {
-      float v[16];
-      tmem_ld16(s.tmem + lane_addr + G::C_QKV + half * HALF + j, v);
-#pragma unroll
-      for (int e = 0; e < 16; ++e) Qs[row * KS + half * HALF + j + e] = v[e];
-      tmem_ld16(s.tmem + lane_addr + G::C_QKV + D + half * HALF + j, v);
-#pragma unroll
-      for (int e = 0; e < 16; ++e) Ks[row * KS + half * HALF + j + e] = v[e];
-      tmem_ld16(s.tmem + lane_addr + G::C_QKV + 2 * D + half * HALF + j, v);
-#pragma unroll
-      for (int e = 0; e < 16; ++e) Vs[row * KS + half * HALF + j + e] = v[e];
-    }
-    ok = wait_ld(s);
-    if (!sync_ok(s, ok)) break;
-    if (threadIdx.x == 0) {
-      tc_fence_after();
-      mma_kk(s, dxs, wr, D, D, G::C_DH, false);       // dH = dX' Wo^T
-      mma_commit(s.bar_mma);
-    }
-    ok = wait_mma(s);
-    if (!sync_ok(s, ok)) break;
-#pragma unroll
-    for (int j = 0; j < HALF; j += 16) {
-      float v[16];
-      tmem_ld16(s.tmem + lane_addr + G::C_DH + half * HALF + j, v);
-#pragma unroll
-      for (int e = 0; e < 16; ++e) dHs[row * KS + half * HALF + j + e] = v[e];
-    }
-    __syncthreads();   // Q, K, V, dH of every row visible; Wo no longer read (stats reuse the region)
-    uint8_t *dq_img = a.dqkv + tile * (size_t)(kRows * 3 * D * 2);
-    if (n <= 16) {
-      // ---- one warp per (sequence, head): warp-level MMAs (the 16 x 16 blocks stay in registers)
+        for (int j = 0; j < HALF; j += 16) {
+          float v[16];
+          tmem_ld16(s.tmem + lane_addr + col0 + half * HALF + j, v);
+          uint4 q0, q1;
+          q0.x = amma::h2(v[0], v[1]);   q0.y = amma::h2(v[2], v[3]);
+          q0.z = amma::h2(v[4], v[5]);   q0.w = amma::h2(v[6], v[7]);
+          q1.x = amma::h2(v[8], v[9]);   q1.y = amma::h2(v[10], v[11]);
+          q1.z = amma::h2(v[12], v[13]); q1.w = amma::h2(v[14], v[15]);
+          reinterpret_cast<uint4 *>(dst + j)[0] = q0;
+          reinterpret_cast<uint4 *>(dst + j)[1] = q1;
+        }
+      }
+      (void)valid;
+      __syncthreads();   // every row's Q, K, V, dH visible
+      uint8_t *dq_img = a.dqkv + tile * (size_t)(kRows * 3 * D * 2);
       for (int i = threadIdx.x; i < (kRows - nvalid) * (3 * D / 8); i += kThreads) {   // padding rows: dQKV = 0
         const int r = nvalid + i / (3 * D / 8), c8 = i % (3 * D / 8);
         *reinterpret_cast<uint4 *>(dq_img + canon(r, 8 * c8, 3 * D)) = make_uint4(0, 0, 0, 0);
       }
       for (int u = warp; u < a.ts * heads; u += kThreads / 32) {
-        const int sq = u / heads, h = u % heads, rb = sq * n, off = rb * KS + h * HD;
-        amma::attn_fwd_bwd<HD>(Qs + off, Ks + off, Vs + off, dHs + off, KS, n, qscale, scale,
-                               [&](int kind, int r, int c, float v0, float v1) {
-                                 const int row = rb + r, col = h * HD + c;
-                                 if (kind == 0)
-                                   *reinterpret_cast<uint32_t *>(sm + G::H_OFF + canon(row, col, 128)) = pack_bf16(v0, v1);
-                                 else
-                                   *reinterpret_cast<uint32_t *>(dq_img + canon(row, (kind - 1) * D + col, 3 * D)) =
-                                       pack_bf16(v0, v1);
-                               });
+        const int sq = u / heads, h = u % heads, rb = sq * n;
+        const uint32_t off = (uint32_t)(rb * LDH + h * HD) * 2;
+        amma::attn_fwd_bwd_h<HD>(f16 + off, f16 + G::F_BYTES + off, f16 + 2 * G::F_BYTES + off,
+                                 f16 + 3 * G::F_BYTES + off, LDH, n, qscale, scale,
+                                 [&](int kind, int r, int c, float v0, float v1) {
+                                   const int rr = rb + r, col = h * HD + c;
+                                   if (kind == 0)
+                                     *reinterpret_cast<uint32_t *>(sm + G::H_OFF + canon(rr, col, 128)) = pack_bf16(v0, v1);
+                                   else
+                                     *reinterpret_cast<uint32_t *>(dq_img + canon(rr, (kind - 1) * D + col, 3 * D)) =
+                                         pack_bf16(v0, v1);
+                                 });
       }
-    } else {
-    // ---- pass 1: this thread = query row; forward output (-> H image) and dQ
-    const int h0 = half * (heads / 2), h1 = h0 + heads / 2;
-    for (int h = h0; h < h1; ++h) {
-      float o[HD], dq[HD];
-#pragma unroll
-      for (int e = 0; e < HD; ++e) { o[e] = 0.f; dq[e] = 0.f; }
-      float mx = -INFINITY, l = 0.f, delta = 0.f;
-      if (valid) {
-        const float *qr = Qs + row * KS + h * HD, *gr = dHs + row * KS + h * HD;
-        const float *kb = Ks + sq * n * KS + h * HD, *vb = Vs + sq * n * KS + h * HD;
-        float q[HD], gg[HD];
-#pragma unroll
-        for (int e = 0; e < HD; ++e) { q[e] = qr[e] * qscale; gg[e] = gr[e]; }
-        // online softmax with dA_ij = dH_i . v_j accumulated alongside: delta = sum_j p_j dA_j / l
-        for (int j = 0; j < n; ++j) {
-          const float *kr = kb + j * KS, *vr = vb + j * KS;
-          float sc = 0.f, da = 0.f;
-#pragma unroll
-          for (int e = 0; e < HD; ++e) { sc = fmaf(q[e], kr[e], sc); da = fmaf(gg[e], vr[e], da); }
-          if (sc > mx) {
-            const float cr = ex2_fast(mx - sc);
-            l *= cr;
-            delta *= cr;
-#pragma unroll
-            for (int e = 0; e < HD; ++e) o[e] *= cr;
-            mx = sc;
-          }
-          const float p = ex2_fast(sc - mx);
-          l += p;
-          delta = fmaf(p, da, delta);
-#pragma unroll
-          for (int e = 0; e < HD; ++e) o[e] = fmaf(p, vr[e], o[e]);
+      fence_proxy_async();
+      if (!sync_ok(s, true)) break;
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        if (!a.jac.nvirt) {
+          mma_mm(s, hs, 128, dxs, D, D, G::C_WO, !first);   // dWo += H^T dX'   (rows of H beyond D are zero)
+        } else {
+          for (int c = 0; c < 4; ++c) mma_mm_rows(s, hs, 128, dxs, D, D, G::C_JWO + 64 * c, 32 * c, 2);
         }
-        const float inv = 1.0f / l;
-        delta *= inv;
-#pragma unroll
-        for (int e = 0; e < HD; ++e) o[e] *= inv;
-        // dQ_i = scale sum_j a_ij (dA_ij - delta_i) k_j
-        for (int j = 0; j < n; ++j) {
-          const float *kr = kb + j * KS, *vr = vb + j * KS;
-          float sc = 0.f, da = 0.f;
-#pragma unroll
-          for (int e = 0; e < HD; ++e) { sc = fmaf(q[e], kr[e], sc); da = fmaf(gg[e], vr[e], da); }
-          const float w = scale * ex2_fast(sc - mx) * inv * (da - delta);
-#pragma unroll
-          for (int e = 0; e < HD; ++e) dq[e] = fmaf(w, kr[e], dq[e]);
-        }
+        mma_commit(s.bar_mma);
       }
-      st_m[row * 8 + h] = mx;
-      st_l[row * 8 + h] = l;
-      st_d[row * 8 + h] = delta;
-#pragma unroll
-      for (int e8 = 0; e8 < HD; e8 += 8) {
-        st_row8(sm + G::H_OFF, row, h * HD + e8, 128, o + e8);
-        st_row8(dq_img, row, h * HD + e8, 3 * D, dq + e8);
+      ok = wait_mma(s);
+      first = false;
+      if (a.jac.nvirt) {
+        if (!sync_ok(s, ok)) break;
+        auto iwo = [&](int m, int nn) -> long long { return m < D ? a.off_wo + (long long)m * D + nn : -1; };
+        jac_flush<decltype(iwo), 2>(s, a.jac, tile, G::C_JWO, D, iwo);
       }
-    }
-    __syncthreads();
-    // ---- pass 2: this thread = key row j; dK_j, dV_j
-    for (int h = h0; h < h1; ++h) {
-      float dk[HD], dv[HD];
-#pragma unroll
-      for (int e = 0; e < HD; ++e) { dk[e] = 0.f; dv[e] = 0.f; }
-      if (valid) {
-        float kj[HD], vj[HD];
-#pragma unroll
-        for (int e = 0; e < HD; ++e) { kj[e] = Ks[row * KS + h * HD + e]; vj[e] = Vs[row * KS + h * HD + e]; }
-        for (int i = 0; i < n; ++i) {
-          const int ri = sq * n + i;
-          const float *qr = Qs + ri * KS + h * HD, *gr = dHs + ri * KS + h * HD;
-          float sc = 0.f, da = 0.f;
-#pragma unroll
-          for (int e = 0; e < HD; ++e) { sc = fmaf(qr[e], kj[e], sc); da = fmaf(gr[e], vj[e], da); }
-          const float aij = ex2_fast(sc * qscale - st_m[ri * 8 + h]) / st_l[ri * 8 + h];
-          const float w = scale * aij * (da - st_d[ri * 8 + h]);
-#pragma unroll
-          for (int e = 0; e < HD; ++e) { dv[e] = fmaf(aij, gr[e], dv[e]); dk[e] = fmaf(w, qr[e], dk[e]); }
-        }
-      }
-#pragma unroll
-      for (int e8 = 0; e8 < HD; e8 += 8) {
-        st_row8(dq_img, row, D + h * HD + e8, 3 * D, dk + e8);
-        st_row8(dq_img, row, 2 * D + h * HD + e8, 3 * D, dv + e8);
-      }
-    }
-    }
-    fence_proxy_async();
-    if (!sync_ok(s, true)) break;
-    if (threadIdx.x == 0) {
-      tc_fence_after();
-      if (!a.jac.nvirt) {
-        mma_mm(s, hs, 128, dxs, D, D, G::C_WO, !first);   // dWo += H^T dX'   (rows of H beyond D are zero)
-      } else {
-        for (int c = 0; c < 4; ++c) mma_mm_rows(s, hs, 128, dxs, D, D, G::C_JWO + 64 * c, 32 * c, 2);
-      }
-      mma_commit(s.bar_mma);
-    }
-    ok = wait_mma(s);
-    first = false;
-    if (a.jac.nvirt) {
+      tc_fence_before();
       if (!sync_ok(s, ok)) break;
-      auto iwo = [&](int m, int nn) -> long long { return m < D ? a.off_wo + (long long)m * D + nn : -1; };
-      jac_flush<decltype(iwo), 2>(s, a.jac, tile, G::C_JWO, D, iwo);
     }
-    tc_fence_before();
-    if (!sync_ok(s, ok)) break;
   }
   if (!s.bad && !first && !a.jac.nvirt) {
     float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
@@ -871,15 +795,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
 #pragma unroll
       for (int j = 0; j < HALF; j += 4)
         *reinterpret_cast<float4 *>(a.dxo + rg + j) = make_float4(out[j], out[j + 1], out[j + 2], out[j + 3]);
-      if (a.embed_grad && row < nvalid) {
+      if (a.embed_grad && a.jac.nvirt && row < nvalid) {   // VJP mode: k_embed_grad after the launch
         const int sqn = row / n, i = row % n;
         const size_t b = tile * tc + (sqn >> 1);
         if (b < a.B) {
           const uint32_t w1 = (sqn & 1) ? a.sigp[b] : a.sig[b];
           const uint32_t w2 = (sqn & 1) ? a.sig[b] : a.sigp[b];
           const int pat = embed_pattern(0, w1, w2, i, n);
-          // per-configuration mode: one [4][D] block per virtual configuration (sqn >> 1) of the tile
-          float *dst = a.jac.nvirt ? dE + (sqn >> 1) * 4 * D : dE;
+          // one [4][D] block per virtual configuration (sqn >> 1) of the tile
+          float *dst = dE + (sqn >> 1) * 4 * D;
 #pragma unroll
           for (int j = 0; j < HALF; ++j) atomicAdd(&dst[pat * D + half * HALF + j], out[j]);
         }
@@ -906,9 +830,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
       if (nn < 2 * D) return a.off_wk + (long long)m * D + (nn - D);
       return a.off_wv + (long long)m * D + (nn - 2 * D);
     });
-    __syncthreads();
-    if (a.embed_grad)
-      for (int i = threadIdx.x; i < 4 * D; i += kThreads) atomicAdd(g + a.off_e + i, dE[i]);
   }
   sync_finish(s);
 }
@@ -974,7 +895,7 @@ cudaError_t launch_pack_bwdtc(const DevModel &m, uint8_t *dst, BwdTcLayer *views
 
 bool bwdtc_supported(const DevModel &m) {
   return m.d == 64 && (m.dh == 8 || m.dh == 16) && m.heads % 2 == 0 && m.heads <= 16 &&
-         (m.ffn == 0 || m.ffn == 128 || m.ffn == 256) && m.embed == 0;
+         (m.ffn == 0 || m.ffn == 128 || m.ffn == 256) && m.embed == 0 && m.n_sites <= 16;
 }
 
 struct BwdTcBuffers {
@@ -982,6 +903,57 @@ struct BwdTcBuffers {
   float *h, *f, *dF, *dxa, *dxb;
   size_t tiles;
 };
+
+// Token-embedding gradient of the VJP: dE[p][c] = sum over the rows whose token is p of dX[row][c], dX the
+// gradient at the first layer's input ([tiles * 128][D] FP32, tile-major rows).  Thread = (row slot,
+// 4 columns); 4 x 4 register sums per thread (no shared-memory atomics on the 4 hot rows of dE), one
+// block reduction, then float atomics into the block's gradient copy.
+namespace tdo {
+namespace bwdtc {
+__global__ void __launch_bounds__(256) k_embed_grad(const float *__restrict__ dX, const uint32_t *__restrict__ sig,
+                                                    const uint32_t *__restrict__ sigp, size_t B, int n, int ts,
+                                                    size_t tiles, float *__restrict__ g, size_t g_stride,
+                                                    long long off_e) {
+  constexpr int D = 64, CG = D / 4, SLOTS = 256 / CG;
+  __shared__ float4 red[SLOTS][4][CG];
+  const int cg = threadIdx.x % CG, slot = threadIdx.x / CG, tc = ts / 2, nvalid = ts * n;
+  float4 acc[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const size_t rows = tiles * kRows;
+  for (size_t r = (size_t)blockIdx.x * SLOTS + slot; r < rows; r += (size_t)gridDim.x * SLOTS) {
+    const int rt = (int)(r % kRows);
+    if (rt >= nvalid) continue;
+    const int sq = rt / n, i = rt % n;
+    const size_t b = (r / kRows) * tc + (sq >> 1);
+    if (b >= B) continue;
+    const uint32_t w1 = (sq & 1) ? sigp[b] : sig[b];
+    const uint32_t w2 = (sq & 1) ? sig[b] : sigp[b];
+    const int pat = embed_pattern(0, w1, w2, i, n);
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(dX + r * D) + cg);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float m = p == pat ? 1.f : 0.f;
+      acc[p].x = fmaf(m, v.x, acc[p].x); acc[p].y = fmaf(m, v.y, acc[p].y);
+      acc[p].z = fmaf(m, v.z, acc[p].z); acc[p].w = fmaf(m, v.w, acc[p].w);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) red[slot][p][cg] = acc[p];
+  __syncthreads();
+  if (threadIdx.x < 4 * CG) {
+    const int p = threadIdx.x / CG, c = threadIdx.x % CG;
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < SLOTS; ++q) {
+      const float4 u = red[q][p][c];
+      t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+    }
+    float *dst = g + (size_t)(blockIdx.x % kCopiesMax) * g_stride + off_e + p * D + 4 * c;
+    atomicAdd(dst, t.x); atomicAdd(dst + 1, t.y); atomicAdd(dst + 2, t.z); atomicAdd(dst + 3, t.w);
+  }
+}
+}  // namespace bwdtc
+}  // namespace tdo
 
 // Output of the per-configuration mode (log-derivatives); nvirt = 0 selects the VJP.
 struct BwdTcJac {
@@ -1118,6 +1090,8 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
     a2.err = err;
     a2.jac = jo;
     k_bwd_attn2<D><<<grid, kThreads, A2Geo<D>::BYTES, st>>>(a2);
+    if (l == 0 && !jo.nvirt)
+      k_embed_grad<<<(unsigned)(2 * n_sm), 256, 0, st>>>(bf.dxa, sig, sigp, B, n, ts, tiles, gacc, g_stride, off_e);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -876,7 +876,7 @@ static tdo_status vjp_tc(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, siz
   CU(c, launch_bwdtc(c->dm, c->dmb, c->bwl, bf, ds, dp, B, cot, c->gacc.as<float>(), stride, c->flat_offsets,
                      c->errflag.as<int>(), c->n_sm, c->stream));
   CU(c, launch_reduce_copies(c->gacc.as<float>(), copies, stride, c->P, grad, 0, c->stream));
-  tm.done(2 + (long long)c->dm.layers * (2 + (c->dm.ffn > 0 ? c->dm.ffn / 128 : 0)) + 1);
+  tm.done(2 + (long long)c->dm.layers * (2 + (c->dm.ffn > 0 ? c->dm.ffn / 128 : 0)) + 2);
   return TDO_OK;
 }
 

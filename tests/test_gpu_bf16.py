@@ -91,8 +91,8 @@ def test_bf16_unsupported_shapes():
 @pytest.mark.parametrize("kind,n,h,L,r,Ns", [("ising", 16, 8, 4, 4, 96), ("xyz", 13, 4, 2, 2, 64), ("ising", 8, 8, 2, 0, 128),
                                               ("ising", 20, 8, 1, 2, 24), ("xyz", 5, 4, 1, 4, 40)])
 def test_cost_gradient_bf16_tensor_core(kind, n, h, L, r, Ns):
-    """tdo_grad on a BF16 context runs the tensor-core backward (BF16 activations, FP32 accumulation;
-    softmax attention by warp-level FP16 MMAs for N <= 16, on the CUDA cores above): the gradient is
+    """tdo_grad on a BF16 context runs the tensor-core backward (BF16 activations, FP32 accumulation,
+    softmax attention by warp-level FP16 MMAs) for N <= 16 and the FP32 backward above: the gradient is
     within 5e-2 of the oracle's in norm (measured values are reported)."""
     prob = problem(kind, n)
     spec = synth.model_spec(64, h, L, r)
