@@ -30,7 +30,7 @@ from paper_2502_20723_gb300 import synth  # noqa: E402
 
 N_SITES, D, HEADS, LAYERS, MLP = 16, 64, 8, 4, 4
 N_SAMPLES = 16384
-LR, SHIFT = 0.0061, 1e-3
+LR, SHIFT = 0.0061, 0.004   # eta_0 and lambda_0 of the paper's learning-rate and SR-shift schedules
 METRIC = "VMC steps/s and log rho evals/s (N=16, d=64, 4 layers)"
 WORKLOAD = "ising_n16_d64_l4_h8_mlp4_ns16384"
 

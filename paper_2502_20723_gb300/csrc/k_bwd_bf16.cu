@@ -370,6 +370,14 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   bool first = true;
   if (sync_ok(s, ok)) {
     if ((size_t)blockIdx.x < a.tiles) load2(s, xs0, a.xmid + blockIdx.x * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+    const bool base_is_dxo = a.base == a.dxo;
+    float4 nx[QD / 4];   // this thread's incoming dX of the next tile, loaded one tile early
+    auto load_nx = [&](size_t t) {
+      const float4 *src = reinterpret_cast<const float4 *>(a.dxo + (t * kRows + row) * (size_t)D + cg * QD);
+#pragma unroll
+      for (int j = 0; j < QD / 4; ++j) nx[j] = src[j];
+    };
+    if ((size_t)blockIdx.x < a.tiles) load_nx(blockIdx.x);
     int buf = 0;
     for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, buf ^= 1) {
       const uint32_t xs = xs0 + buf * G::IMG;
@@ -377,10 +385,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       float dxo[QD], base[QD];
 #pragma unroll
       for (int j = 0; j < QD; j += 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(a.dxo + rg + j);
+        const float4 v = nx[j / 4];
         dxo[j] = v.x; dxo[j + 1] = v.y; dxo[j + 2] = v.z; dxo[j + 3] = v.w;
-        const float4 q = a.base == a.dxo ? v : *reinterpret_cast<const float4 *>(a.base + rg + j);
-        base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
+        base[j] = v.x; base[j + 1] = v.y; base[j + 2] = v.z; base[j + 3] = v.w;   // pass 0: base = dX
       }
 #pragma unroll
       for (int j = 0; j < QD; j += 8) st_row8(sm + G::DX_OFF, row, cg * QD + j, D, dxo + j);
@@ -442,6 +449,13 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
         }
         mma_commit(s.bar_mma);
       }
+      if (!base_is_dxo) {   // second pass: the residual base, loaded while the MMAs run
+#pragma unroll
+        for (int j = 0; j < QD; j += 4) {
+          const float4 q = *reinterpret_cast<const float4 *>(a.base + rg + j);
+          base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
+        }
+      }
       ok = wait_mma(s);
       if (!sync_ok(s, ok)) break;
       if (a.jac.nvirt) {
@@ -479,6 +493,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
               make_float4(base[j + e] + v[e], base[j + e + 1] + v[e + 1], base[j + e + 2] + v[e + 2],
                           base[j + e + 3] + v[e + 3]);
       }
+      if (tile + gridDim.x < a.tiles) load_nx(tile + gridDim.x);
       first = false;
       tc_fence_before();
       __syncthreads();

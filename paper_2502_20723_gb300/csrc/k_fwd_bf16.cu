@@ -1,6 +1,7 @@
 // BF16 tensor-core forward of the ansatz (architecture appendix) on sm_103a: tcgen05.mma with FP32
 // accumulators in tensor memory, weights streamed into shared memory by cp.async.bulk (TMA engine),
-// attention / softmax / GELU / residual on the CUDA cores in FP32.
+// softmax attention by warp-level MMAs (N <= 16; CUDA cores otherwise), the MLP's GELU in packed FP16
+// arithmetic feeding an FP16 GEMM, residual stream and head in FP32.
 //
 // Tile: 128 token rows (TS sequences of N tokens, TS*N <= 128), one CTA of 256 threads.  TMEM lane r
 // holds row r; warps w and w+4 share lane quarter w%4 and split the columns in two halves, so thread
@@ -74,10 +75,10 @@ struct Ctl {
 
 // Issue the MMAs of one GEMM: D[tmem + col] (+)= A[128 x K] * B^T, B stored [N][K]; commit to bar_mma.
 __device__ __forceinline__ void gemm(Ctl &c, uint32_t a_addr, uint32_t b_addr, int K, int N, uint32_t col,
-                                     bool accumulate) {
+                                     bool accumulate, bool f16 = false) {
   if (c.mma_thread) {
     tc_fence_after();
-    const uint32_t id = idesc_bf16(kRows, N);
+    const uint32_t id = f16 ? idesc_f16(kRows, N) : idesc_bf16(kRows, N);
     for (int kk = 0; kk < K / 16; ++kk) {
       const uint64_t ad = sdesc(a_addr + kk * 256, 128, K * 16);
       const uint64_t bd = sdesc(b_addr + kk * 256, 128, K * 16);
@@ -105,6 +106,21 @@ __device__ __forceinline__ bool wait_w(Ctl &c) {
   const bool ok = mbar_wait(c.bar_w, c.ph_w);
   c.ph_w ^= 1u;
   return ok;
+}
+
+// GELU (tanh form) of a pair of FP16 values, in packed half2 arithmetic: 0.5 u (1 + tanh(k0 (u + k1 u^3))).
+// Two results per instruction; the MLP's hidden activations feed an FP16 GEMM, so they never pass
+// through FP32 after the bias add.
+__device__ __forceinline__ uint32_t gelu_h2(uint32_t x) {
+  const __half2 k1 = __float2half2_rn(0.044715f), k0 = __float2half2_rn(0.7978845608028654f);
+  const __half2 one = __float2half2_rn(1.0f), hf = __float2half2_rn(0.5f);
+  const __half2 h = *reinterpret_cast<const __half2 *>(&x);
+  const __half2 s = __hmul2(__hmul2(h, __hfma2(__hmul2(h, h), k1, one)), k0);
+  uint32_t sb = *reinterpret_cast<const uint32_t *>(&s), tb;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(tb) : "r"(sb));
+  const __half2 hh = __hmul2(h, hf);
+  const __half2 g = __hfma2(hh, *reinterpret_cast<const __half2 *>(&tb), hh);
+  return *reinterpret_cast<const uint32_t *>(&g);
 }
 
 // Agree across the CTA on failure; returns true if any thread saw a timeout.
@@ -312,23 +328,28 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
         ok = wait_mma(c);
         if (sync_fail(c, ok)) return false;
         stage_w(c, w_addr, mb.W2[l] + (size_t)ch * G::HC * D, G::HC * D * 2);
-        // GELU(U + b1) -> G (BF16), this thread's half of the chunk columns
+        // GELU(U + b1) -> G (FP16, packed half2 arithmetic), this thread's half of the chunk columns
         constexpr int HH = G::HC / 2;
 #pragma unroll
         for (int j = 0; j < HH; j += 16) {
           float v[16];
           tmem_ld16(c.tmem + lane_addr + half * HH + j, v);
           const int c0 = ch * G::HC + half * HH + j;
+          const float4 *b4 = reinterpret_cast<const float4 *>(m.L[l].b1 + c0);
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] = gelu_fast(v[e] + __ldg(m.L[l].b1 + c0 + e));
-          st_row8(Gs, row, half * HH + j, G::HC, v);
-          st_row8(Gs, row, half * HH + j + 8, G::HC, v + 8);
+          for (int e8 = 0; e8 < 2; ++e8) {   // 8 columns (one 16-byte row segment of the image) at a time
+            const float4 ba = __ldg(b4 + 2 * e8), bb = __ldg(b4 + 2 * e8 + 1);
+            const float *w = v + 8 * e8;
+            *reinterpret_cast<uint4 *>(Gs + canon(row, half * HH + j + 8 * e8, G::HC)) =
+                make_uint4(gelu_h2(amma::h2(w[0] + ba.x, w[1] + ba.y)), gelu_h2(amma::h2(w[2] + ba.z, w[3] + ba.w)),
+                           gelu_h2(amma::h2(w[4] + bb.x, w[5] + bb.y)), gelu_h2(amma::h2(w[6] + bb.z, w[7] + bb.w)));
+          }
         }
         tc_fence_before();
         fence_proxy_async();
         ok = wait_w(c);
         if (sync_fail(c, ok)) return false;
-        gemm(c, g_addr, w_addr, G::HC, D, G::HC, ch > 0);            // out -> cols [HC, HC + D)
+        gemm(c, g_addr, w_addr, G::HC, D, G::HC, ch > 0, true);      // out -> cols [HC, HC + D), FP16
         ok = wait_mma(c);
         if (sync_fail(c, ok)) return false;
         if (ch + 1 < nch) stage_w(c, w_addr, mb.W1[l] + (size_t)(ch + 1) * G::HC * D, G::HC * D * 2);
@@ -521,12 +542,14 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 // ------------------------------------------------------------------ packing of BF16 weights
 // dst element (n, k) of W^T ([N][K] canonical) = W[k][n] for an FP32 W [K][N] (row stride ldw, col off).
-__global__ void k_pack(const float *__restrict__ W, int ldw, int col0, int K, int N, uint8_t *__restrict__ dst) {
+__global__ void k_pack(const float *__restrict__ W, int ldw, int col0, int K, int N, uint8_t *__restrict__ dst,
+                       int f16) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N * K) return;
   const int n = i / K, k = i % K;
-  const __nv_bfloat16 v = __float2bfloat16_rn(W[(size_t)k * ldw + col0 + n]);
-  *reinterpret_cast<__nv_bfloat16 *>(dst + canon(n, k, K)) = v;
+  const float w = W[(size_t)k * ldw + col0 + n];
+  if (f16) *reinterpret_cast<__half *>(dst + canon(n, k, K)) = __float2half_rn(w);
+  else *reinterpret_cast<__nv_bfloat16 *>(dst + canon(n, k, K)) = __float2bfloat16_rn(w);
 }
 
 }  // namespace bf16
@@ -549,8 +572,8 @@ cudaError_t launch_pack_bf16(const DevModel &m, uint16_t *dst16, DevModelBF16 *v
   const int D = m.d, F = m.ffn;
   const int HC = (4 * D < 128) ? 4 * D : 128;
   size_t off = 0;
-  auto pack = [&](const float *W, int ldw, int col0, int K, int N, uint8_t *out) {
-    k_pack<<<(N * K + 255) / 256, 256, 0, st>>>(W, ldw, col0, K, N, out);
+  auto pack = [&](const float *W, int ldw, int col0, int K, int N, uint8_t *out, int f16 = 0) {
+    k_pack<<<(N * K + 255) / 256, 256, 0, st>>>(W, ldw, col0, K, N, out, f16);
   };
   for (int l = 0; l < m.layers; ++l) {
     const DevLayer &L = m.L[l];
@@ -569,9 +592,10 @@ cudaError_t launch_pack_bf16(const DevModel &m, uint16_t *dst16, DevModelBF16 *v
       views->W1[l] = reinterpret_cast<const uint16_t *>(dst + off);
       for (int c = 0; c < F / HC; ++c) pack(L.W1, F, c * HC, D, HC, dst + off + (size_t)c * HC * D * 2);
       off += (size_t)F * D * 2;
-      // W2^T chunks: [D][HC] each (K = hidden units c*HC..c*HC+HC-1)
+      // W2^T chunks: [D][HC] each (K = hidden units c*HC..c*HC+HC-1), FP16 (the GEMM with the FP16 GELU output)
       views->W2[l] = reinterpret_cast<const uint16_t *>(dst + off);
-      for (int c = 0; c < F / HC; ++c) pack(L.W2 + (size_t)c * HC * D, D, 0, HC, D, dst + off + (size_t)c * HC * D * 2);
+      for (int c = 0; c < F / HC; ++c)
+        pack(L.W2 + (size_t)c * HC * D, D, 0, HC, D, dst + off + (size_t)c * HC * D * 2, 1);
       off += (size_t)F * D * 2;
     } else {
       views->W1[l] = views->W2[l] = nullptr;

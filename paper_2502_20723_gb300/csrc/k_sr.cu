@@ -230,6 +230,22 @@ __global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const OT *__restrict__ O,
       float f[4] = {0.f, 0.f, 0.f, 0.f};
       if (VEC && kn == 4) {
         int r = r0;
+        if constexpr (sizeof(OT) == 4) {   // BF16 pairs: 8 rows (8 x 16 bytes) in flight per thread
+          for (; r + 8 <= r1; r += 8) {
+            uint4 q[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) q[u] = __ldcs(reinterpret_cast<const uint4 *>(O + (g0 + r + u) * ldo + k));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const float2 tv = ts[r + u];
+              const float2 c0 = cplx(q[u].x), c1 = cplx(q[u].y), c2 = cplx(q[u].z), c3 = cplx(q[u].w);
+              f[0] = fmaf(c0.x, tv.x, fmaf(c0.y, tv.y, f[0]));
+              f[1] = fmaf(c1.x, tv.x, fmaf(c1.y, tv.y, f[1]));
+              f[2] = fmaf(c2.x, tv.x, fmaf(c2.y, tv.y, f[2]));
+              f[3] = fmaf(c3.x, tv.x, fmaf(c3.y, tv.y, f[3]));
+            }
+          }
+        }
         for (; r + 4 <= r1; r += 4) {
           float2 c[4][4];
 #pragma unroll
