@@ -220,6 +220,47 @@ __device__ __forceinline__ void jac_flush(const Sync &s, const JacOut &j, size_t
   }
 }
 
+// The same for blocks whose output index is contiguous along the columns (k = off + m * ld + n, rows
+// m < mlim) when O is stored in BF16: each warp stages 32 rows x 8 columns of (seed 0, seed 1) pairs in
+// shared memory (2 KB per warp at stage + 512 floats * warp) and writes them back 4 rows x 8 columns per
+// instruction, so a warp store covers 4 contiguous 32-byte pieces instead of 32 scattered elements.
+template <int NQ>
+__device__ __noinline__ void jac_flush_rows(const Sync &s, const JacOut &j, size_t tile, uint32_t col0, int N,
+                                               long long off, int ld, int mlim, float *stage) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cg = warp >> 2, mb = 32 * (warp & 3);
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  float2 *st = reinterpret_cast<float2 *>(stage) + warp * 256;   // [32 rows][8 columns]
+  for (int pr = 0; pr < 2; ++pr) {
+    const size_t v0 = tile * 4 + 2 * pr;
+    const bool ok = v0 + 1 < j.nvirt;
+    const size_t b = v0 >> 1;
+    for (int jj = 0; jj < N / NQ; jj += 16) {
+      float re[16], im[16];
+      tmem_ld16(s.tmem + lane_addr + col0 + (2 * pr) * N + cg * (N / NQ) + jj, re);
+      tmem_ld16(s.tmem + lane_addr + col0 + (2 * pr + 1) * N + cg * (N / NQ) + jj, im);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) st[lane * 8 + e] = make_float2(re[8 * h + e], im[8 * h + e]);
+        __syncwarp();
+        if (ok) {
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int r = 4 * it + (lane >> 3), c = lane & 7, m = mb + r;
+            if (m < mlim) {
+              const long long k = off + (long long)m * ld + cg * (N / NQ) + jj + 8 * h + c;
+              const float2 v = st[r * 8 + c], rf = j.oref[k];
+              reinterpret_cast<uint32_t *>(j.o16)[b * j.ldo + (size_t)k] = pack_bf16(v.x - rf.x, v.y - rf.y);
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
 // ====================================================================================== head
 struct HeadArgs {
   const float2 *cot;   // [B] cotangents of log rho
@@ -480,8 +521,12 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
         }
         ok = wait_mma(s);
         if (!sync_ok(s, ok)) break;
-        auto i2 = [&](int m, int nn) -> long long { return a.off_w2 + (long long)m * D + nn; };
-        jac_flush<decltype(i2), NQ>(s, a.jac, tile, 0, D, i2);
+        if (a.jac.o16) {   // dU image region (32 KB): free, its MMAs have completed
+          jac_flush_rows<NQ>(s, a.jac, tile, 0, D, a.off_w2, D, G::HC, reinterpret_cast<float *>(sm + G::DU_OFF));
+        } else {
+          auto i2 = [&](int m, int nn) -> long long { return a.off_w2 + (long long)m * D + nn; };
+          jac_flush<decltype(i2), NQ>(s, a.jac, tile, 0, D, i2);
+        }
       }
 #pragma unroll
       for (int j = 0; j < QD; j += 16) {
@@ -671,8 +716,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
       first = false;
       if (a.jac.nvirt) {
         if (!sync_ok(s, ok)) break;
-        auto iwo = [&](int m, int nn) -> long long { return m < D ? a.off_wo + (long long)m * D + nn : -1; };
-        jac_flush<decltype(iwo), 2>(s, a.jac, tile, G::C_JWO, D, iwo);
+        if (a.jac.o16) {   // FP16 attention copies (free after the attention)
+          jac_flush_rows<2>(s, a.jac, tile, G::C_JWO, D, a.off_wo, D, D, reinterpret_cast<float *>(sm + G::F_OFF));
+        } else {
+          auto iwo = [&](int m, int nn) -> long long { return m < D ? a.off_wo + (long long)m * D + nn : -1; };
+          jac_flush<decltype(iwo), 2>(s, a.jac, tile, G::C_JWO, D, iwo);
+        }
       }
       tc_fence_before();
       if (!sync_ok(s, ok)) break;
@@ -792,8 +841,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
           fine = wait_mma(s);
           if (!sync_ok(s, fine)) break;
           const long long off = part == 0 ? a.off_wq : part == 1 ? a.off_wk : a.off_wv;
-          auto iw = [&](int m, int nn) -> long long { return m < D ? off + (long long)m * D + nn : -1; };
-          jac_flush<decltype(iw), 2>(s, a.jac, tile, 0, D, iw);
+          if (a.jac.o16) {   // this tile's stored X image: already copied into the padded one
+            jac_flush_rows<2>(s, a.jac, tile, 0, D, off, D, D, reinterpret_cast<float *>(const_cast<uint8_t *>(xr_ptr)));
+          } else {
+            auto iw = [&](int m, int nn) -> long long { return m < D ? off + (long long)m * D + nn : -1; };
+            jac_flush<decltype(iw), 2>(s, a.jac, tile, 0, D, iw);
+          }
           tc_fence_before();
           if (!sync_ok(s, true)) break;
         }

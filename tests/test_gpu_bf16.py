@@ -142,3 +142,28 @@ def test_jacobian_tensor_core(kind, n, h, L, r, B, std):
     rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
     print(f"tensor-core log-derivatives: relative error per sample max {rel.max():.3e}")
     assert rel.max() <= 3e-2
+
+
+@pytest.mark.parametrize("Ns", [70, 37])
+def test_sr_step_bf16_log_derivative_storage(Ns):
+    """At N = 16 a BF16 context's SR step stores the tensor-core log-derivatives as BF16 pairs of O - ō
+    (written by the staged per-configuration flushes).  Its update must equal, within 2e-3 in norm, the
+    solve of the same system from the FP32 log-derivatives of tdo_jacobian (same gradient, shift and CG
+    tolerance): the only difference is the BF16 rounding of the centred values."""
+    n = 16
+    prob = problem("ising", n)
+    spec = synth.model_spec(64, 8, 2, 4)
+    th = synth.init_params(spec, 4, std=0.05)
+    sig, sigp = synth.random_configs(n, Ns, seed=12)
+    lr, shift = 0.01, 0.004
+    ref_ctx = ctx_for(prob, spec, th)
+    g, _ = ref_ctx.grad(dev(sig), dev(sigp))
+    O = ref_ctx.jacobian(dev(sig), dev(sigp))
+    x, it, res = ref_ctx.sr_solve(O, g, shift, tol=1e-6, max_iter=100)
+    ctx = ctx_for(prob, spec, th)
+    ctx.sr_step(dev(sig), dev(sigp), lr, shift)
+    delta = (th - ctx.get_params()) / lr
+    x = x.cpu().numpy()
+    rel = np.linalg.norm(delta - x) / np.linalg.norm(x)
+    print(f"SR update from BF16-stored log-derivatives: relative difference {rel:.3e} ({it} CG iterations)")
+    assert rel <= 2e-3
