@@ -353,8 +353,8 @@ struct MlpGeo {
   static constexpr int G_OFF = DX_OFF + IMG;           // G  [128][HC]
   static constexpr int DU_OFF = G_OFF + kRows * HC * 2;  // dU [128][HC]
   static constexpr int ONE_OFF = DU_OFF + kRows * HC * 2;  // all-ones [128][16] (row sums by MMA)
-  static constexpr int M_OFF = ONE_OFF + kRows * 16 * 2;    // misc: bars, holder, db2[D]
-  static constexpr int BYTES = M_OFF + 64 + 4 * D;
+  static constexpr int M_OFF = ONE_OFF + kRows * 16 * 2;    // misc: bars, holder, db2[D], b1 of the chunk [HC]
+  static constexpr int BYTES = M_OFF + 64 + 4 * D + 4 * HC;
   // TMEM columns (C_B1: db1 = dU^T 1, every one of its 16 columns holds the same sums)
   static constexpr int C_U = 0, C_DG = 128, C_DX = 256, C_W1 = 320, C_W2 = 384, C_B1 = 448;
   static constexpr int C_JB1 = 320;   // per-configuration mode: 4 x 16 db1 columns (dW1/dW2 blocks in [0, 256))
@@ -390,7 +390,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
   float *db2 = reinterpret_cast<float *>(sm + G::M_OFF + 64);
+  float *b1s = db2 + D;
   for (int i = threadIdx.x; i < D; i += kMlpThreads) db2[i] = 0.f;
+  for (int i = threadIdx.x; i < G::HC; i += kMlpThreads) b1s[i] = a.b1[i];
   for (int i = threadIdx.x; i < kRows * 16 / 8; i += kMlpThreads)   // bf16 1.0 = 0x3F80
     reinterpret_cast<uint4 *>(sm + G::ONE_OFF)[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -464,7 +466,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
         tmem_ld16(s.tmem + lane_addr + G::C_DG + cg * QH + j, dg);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const float uu = u[e] + __ldg(a.b1 + cg * QH + j + e);
+          const float uu = u[e] + b1s[cg * QH + j + e];
           du[e] = dg[e] * gelu_grad_fast(uu, &gl[e]);
         }
         st_row8(sm + G::G_OFF, row, cg * QH + j, G::HC, gl);

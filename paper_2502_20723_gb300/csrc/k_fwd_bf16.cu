@@ -201,17 +201,19 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
         for (int j = 0; j < DH; j += 16) {
           float v[16];
           tmem_ld16(c.tmem + lane_addr + half * DH + j, v);
-          if (valid) {
-#pragma unroll
-            for (int e = 0; e < 16; e += 2)
-              *reinterpret_cast<uint32_t *>(Qh + row * G::LDH + half * DH + j + e) =
-                  amma::h2(v[e] * qscale, v[e + 1] * qscale);
+          if (valid) {   // 16-byte stores: rows 144 bytes apart land on distinct bank groups
+            uint4 *dst = reinterpret_cast<uint4 *>(Qh + row * G::LDH + half * DH + j);
+            dst[0] = make_uint4(amma::h2(v[0] * qscale, v[1] * qscale), amma::h2(v[2] * qscale, v[3] * qscale),
+                                amma::h2(v[4] * qscale, v[5] * qscale), amma::h2(v[6] * qscale, v[7] * qscale));
+            dst[1] = make_uint4(amma::h2(v[8] * qscale, v[9] * qscale), amma::h2(v[10] * qscale, v[11] * qscale),
+                                amma::h2(v[12] * qscale, v[13] * qscale), amma::h2(v[14] * qscale, v[15] * qscale));
           }
           tmem_ld16(c.tmem + lane_addr + D + half * DH + j, v);
           if (valid) {
-#pragma unroll
-            for (int e = 0; e < 16; e += 2)
-              *reinterpret_cast<uint32_t *>(Kh + row * G::LDH + half * DH + j + e) = amma::h2(v[e], v[e + 1]);
+            uint4 *dst = reinterpret_cast<uint4 *>(Kh + row * G::LDH + half * DH + j);
+            dst[0] = make_uint4(amma::h2(v[0], v[1]), amma::h2(v[2], v[3]), amma::h2(v[4], v[5]), amma::h2(v[6], v[7]));
+            dst[1] = make_uint4(amma::h2(v[8], v[9]), amma::h2(v[10], v[11]), amma::h2(v[12], v[13]),
+                                amma::h2(v[14], v[15]));
           }
           tmem_ld16(c.tmem + lane_addr + 2 * D + half * DH + j, v);
           if (valid) {
