@@ -348,9 +348,9 @@ struct MlpGeo {
   static constexpr int W1T_OFF = 0;                    // [HC][D]  (U = Xmid W1_c)
   static constexpr int W2_OFF = W1T_OFF + HC * D * 2;  // [HC][D]  (dG = dX W2_c^T)
   static constexpr int W1_OFF = W2_OFF + HC * D * 2;   // [D][HC]  (dX' = dU W1_c^T)
-  static constexpr int X_OFF = W1_OFF + HC * D * 2;    // Xmid images [2][128][D] (the next tile's loads early)
-  static constexpr int DX_OFF = X_OFF + 2 * IMG;       // dX (BF16) [128][D]
-  static constexpr int G_OFF = DX_OFF + IMG;           // G  [128][HC]
+  static constexpr int X_OFF = W1_OFF + HC * D * 2;    // Xmid images [2][128][D] (tile t and t + 1)
+  static constexpr int DX_OFF = X_OFF + 2 * IMG;       // dX (BF16) images [2][128][D] (tile t and t + 1)
+  static constexpr int G_OFF = DX_OFF + 2 * IMG;       // G  [128][HC]
   static constexpr int DU_OFF = G_OFF + kRows * HC * 2;  // dU [128][HC]
   static constexpr int ONE_OFF = DU_OFF + kRows * HC * 2;  // all-ones [128][16] (row sums by MMA)
   static constexpr int M_OFF = ONE_OFF + kRows * 16 * 2;    // misc: bars, holder, db2[D], b1 of the chunk [HC]
@@ -377,7 +377,11 @@ struct MlpArgs {
 };
 
 // 512 threads: thread (row, cg) owns a quarter of the hidden chunk's and of dX's columns; 16 warps hide
-// the latency of the CUDA-core phases.  The next tile's Xmid image is loaded during this tile.
+// the latency of the CUDA-core phases.  Two tiles are in flight: the products U, dG of tile t + 1 (MMA1,
+// barrier bar_mma) are issued while the backward products of tile t (MMA2, barrier bar2) run and its dX'
+// is written out; the Xmid and dX images are double-buffered and the incoming dX is read one tile early.
+// In the per-configuration mode MMA2 also fills TMEM columns [0, 256), so MMA1 of the next tile waits
+// for the end of the tile.
 constexpr int kMlpThreads = 512;
 
 template <int D>
@@ -387,6 +391,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   constexpr int NQ = kMlpThreads / 128;
   constexpr int QD = D / NQ, QH = G::HC / NQ;   // dX columns and hidden columns per thread
   static_assert(QD % 16 == 0 && QH % 16 == 0, "column groups of 16");
+  const uint32_t bar2 = smem_u32(sm + G::M_OFF + 24);
+  uint32_t ph2 = 0;
+  if (threadIdx.x == 0) mbar_init(bar2, 1);   // made visible by the fence and barrier in sync_init
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
   float *db2 = reinterpret_cast<float *>(sm + G::M_OFF + 64);
@@ -399,8 +406,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   const int row = 32 * (warp & 3) + lane, cg = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
   const uint32_t w1t = smem_u32(sm + G::W1T_OFF), w2 = smem_u32(sm + G::W2_OFF), w1 = smem_u32(sm + G::W1_OFF);
-  const uint32_t xs0 = smem_u32(sm + G::X_OFF), dxs = smem_u32(sm + G::DX_OFF), gs = smem_u32(sm + G::G_OFF),
+  const uint32_t xs0 = smem_u32(sm + G::X_OFF), dxs0 = smem_u32(sm + G::DX_OFF), gs = smem_u32(sm + G::G_OFF),
                  dus = smem_u32(sm + G::DU_OFF), ones = smem_u32(sm + G::ONE_OFF);
+  const bool jac = a.jac.nvirt != 0;
   fence_proxy_async();   // the ones image is read by the tensor cores
   // weights once per kernel
   if (threadIdx.x == 0) {
@@ -411,59 +419,69 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   }
   bool ok = wait_ld(s);
   bool first = true;
-  if (sync_ok(s, ok)) {
-    if ((size_t)blockIdx.x < a.tiles) load2(s, xs0, a.xmid + blockIdx.x * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
-    const bool base_is_dxo = a.base == a.dxo;
-    float4 nx[QD / 4];   // this thread's incoming dX of the next tile, loaded one tile early
+  const size_t t0 = blockIdx.x, step = gridDim.x;
+  if (sync_ok(s, ok) && t0 < a.tiles) {
+    float4 nx[QD / 4];   // this thread's incoming dX of a coming tile
     auto load_nx = [&](size_t t) {
       const float4 *src = reinterpret_cast<const float4 *>(a.dxo + (t * kRows + row) * (size_t)D + cg * QD);
 #pragma unroll
       for (int j = 0; j < QD / 4; ++j) nx[j] = src[j];
     };
-    if ((size_t)blockIdx.x < a.tiles) load_nx(blockIdx.x);
-    int buf = 0;
-    for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, buf ^= 1) {
-      const uint32_t xs = xs0 + buf * G::IMG;
-      const size_t rg = (tile * kRows + row) * (size_t)D + cg * QD;
-      float dxo[QD], base[QD];
+    // dX image of tile t (BF16, buffer b) from nx, and its db2 share (per configuration: the warp's 32 rows
+    // are one virtual configuration)
+    auto put_dx = [&](size_t t, int b) {
+      float dxo[QD];
 #pragma unroll
       for (int j = 0; j < QD; j += 4) {
         const float4 v = nx[j / 4];
         dxo[j] = v.x; dxo[j + 1] = v.y; dxo[j + 2] = v.z; dxo[j + 3] = v.w;
-        base[j] = v.x; base[j + 1] = v.y; base[j + 2] = v.z; base[j + 3] = v.w;   // pass 0: base = dX
       }
 #pragma unroll
-      for (int j = 0; j < QD; j += 8) st_row8(sm + G::DX_OFF, row, cg * QD + j, D, dxo + j);
-      if (a.do_db2) {   // the warp's 32 rows are one virtual configuration in the per-configuration mode
+      for (int j = 0; j < QD; j += 8) st_row8(sm + G::DX_OFF + b * G::IMG, row, cg * QD + j, D, dxo + j);
+      if (a.do_db2) {
 #pragma unroll
         for (int j = 0; j < QD; ++j) {
-          const float t = warp_sum_f(dxo[j]);
+          const float sum = warp_sum_f(dxo[j]);
           if (lane == 0) {
-            if (!a.jac.nvirt) atomicAdd(&db2[cg * QD + j], t);
-            else if (tile * 4 + (warp & 3) < a.jac.nvirt) jac_put1(a.jac, tile * 4 + (warp & 3), a.off_b2 + cg * QD + j, t);
+            if (!jac) atomicAdd(&db2[cg * QD + j], sum);
+            else if (t * 4 + (warp & 3) < a.jac.nvirt) jac_put1(a.jac, t * 4 + (warp & 3), a.off_b2 + cg * QD + j, sum);
           }
         }
       }
-      ok = wait_ld(s);   // this tile's Xmid image
+    };
+    // MMA1 of tile t from buffer b, once its Xmid image has landed and its dX image is written
+    auto issue_mma1 = [&](int b) -> bool {
+      const bool okl = wait_ld(s);
       fence_proxy_async();
-      if (!sync_ok(s, ok)) break;
-      // the other buffer was last read by the previous tile's MMAs, which have completed
-      const size_t nxt = tile + gridDim.x;
-      if (nxt < a.tiles) load2(s, xs0 + (buf ^ 1) * G::IMG, a.xmid + nxt * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+      tc_fence_before();
+      if (!sync_ok(s, okl)) return false;
       if (threadIdx.x == 0) {
         tc_fence_after();
-        mma_kk(s, xs, w1t, D, G::HC, G::C_U, false);    // U  = Xmid W1_c
-        mma_kk(s, dxs, w2, D, G::HC, G::C_DG, false);   // dG = dX W2_c^T
+        mma_kk(s, xs0 + b * G::IMG, w1t, D, G::HC, G::C_U, false);    // U  = Xmid W1_c
+        mma_kk(s, dxs0 + b * G::IMG, w2, D, G::HC, G::C_DG, false);   // dG = dX W2_c^T
         mma_commit(s.bar_mma);
       }
-      ok = wait_mma(s);
+      return true;
+    };
+    // prologue: tile t0 in buffer 0, then the Xmid image of t0 + step into buffer 1
+    load2(s, xs0, a.xmid + t0 * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+    load_nx(t0);
+    put_dx(t0, 0);
+    if (t0 + step < a.tiles) load_nx(t0 + step);
+    bool live = issue_mma1(0);
+    if (live && t0 + step < a.tiles) load2(s, xs0 + G::IMG, a.xmid + (t0 + step) * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+    int buf = 0;
+    for (size_t tile = t0; live && tile < a.tiles; tile += step, buf ^= 1) {
+      const uint32_t xs = xs0 + buf * G::IMG, dxs = dxs0 + buf * G::IMG;
+      const size_t rg = (tile * kRows + row) * (size_t)D + cg * QD;
+      const bool has_next = tile + step < a.tiles;
+      ok = wait_mma(s);   // U, dG of this tile; also MMA2 of the previous tile (G, dU images free)
       if (!sync_ok(s, ok)) break;
       // dU = dG gelu'(U + b1), G = gelu(U + b1) -> shared images
 #pragma unroll
       for (int j = 0; j < QH; j += 16) {
         float u[16], dg[16], gl[16], du[16];
-        tmem_ld16(s.tmem + lane_addr + G::C_U + cg * QH + j, u);
-        tmem_ld16(s.tmem + lane_addr + G::C_DG + cg * QH + j, dg);
+        tmem_ld16x2(s.tmem + lane_addr + G::C_U + cg * QH + j, u, s.tmem + lane_addr + G::C_DG + cg * QH + j, dg);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const float uu = u[e] + b1s[cg * QH + j + e];
@@ -480,7 +498,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       if (threadIdx.x == 0) {
         tc_fence_after();
         mma_kk(s, dus, w1, G::HC, D, G::C_DX, false);              // dX' part = dU W1_c^T
-        if (!a.jac.nvirt) {
+        if (!jac) {
           mma_mm(s, dus, G::HC, xs, D, D, G::C_W1, !first);          // dW1_c^T += dU^T Xmid
           mma_mm(s, gs, G::HC, dxs, D, D, G::C_W2, !first);          // dW2_c   += G^T dX
           mma_mm(s, dus, G::HC, ones, 16, 16, G::C_B1, !first);       // db1_c   += dU^T 1
@@ -490,18 +508,30 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
             mma_mm_rows(s, dus, G::HC, ones, 16, 16, G::C_JB1 + 16 * c, 32 * c, 2);
           }
         }
-        mma_commit(s.bar_mma);
+        mma_commit(bar2);
       }
-      if (!base_is_dxo) {   // second pass: the residual base, loaded while the MMAs run
+      // while MMA2 runs: this tile's residual base, the next tile's dX image (the other buffer, last read
+      // by the previous tile's MMA2) and, in VJP mode, the next tile's MMA1
+      float base[QD];
 #pragma unroll
-        for (int j = 0; j < QD; j += 4) {
-          const float4 q = *reinterpret_cast<const float4 *>(a.base + rg + j);
-          base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
-        }
+      for (int j = 0; j < QD; j += 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(a.base + rg + j);
+        base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
       }
-      ok = wait_mma(s);
+      if (has_next) {
+        put_dx(tile + step, buf ^ 1);
+        if (tile + 2 * step < a.tiles) load_nx(tile + 2 * step);
+        if (!jac && !issue_mma1(buf ^ 1)) break;
+      }
+      ok = mbar_wait(bar2, ph2);
+      ph2 ^= 1u;
+      tc_fence_after();
       if (!sync_ok(s, ok)) break;
-      if (a.jac.nvirt) {
+      // MMA2 has read this tile's Xmid buffer: the Xmid image two tiles ahead goes there (in the
+      // per-configuration mode after the next tile's image has been waited for)
+      if (!jac && tile + 2 * step < a.tiles)
+        load2(s, xs, a.xmid + (tile + 2 * step) * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+      if (jac) {
         const int F = a.F;
         auto i1 = [&](int m, int nn) -> long long { return a.off_w1 + (long long)nn * F + m; };
         jac_flush<decltype(i1), NQ>(s, a.jac, tile, 0, D, i1);
@@ -519,9 +549,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
         if (threadIdx.x == 0) {
           tc_fence_after();
           for (int c = 0; c < 4; ++c) mma_mm_rows(s, gs, G::HC, dxs, D, D, 64 * c, 32 * c, 2);   // dW2_c per config
-          mma_commit(s.bar_mma);
+          mma_commit(bar2);
         }
-        ok = wait_mma(s);
+        ok = mbar_wait(bar2, ph2);
+        ph2 ^= 1u;
+        tc_fence_after();
         if (!sync_ok(s, ok)) break;
         if (a.jac.o16) {   // dU image region (32 KB): free, its MMAs have completed
           jac_flush_rows<NQ>(s, a.jac, tile, 0, D, a.off_w2, D, G::HC, reinterpret_cast<float *>(sm + G::DU_OFF));
@@ -540,13 +572,16 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
               make_float4(base[j + e] + v[e], base[j + e + 1] + v[e + 1], base[j + e + 2] + v[e + 2],
                           base[j + e + 3] + v[e + 3]);
       }
-      if (tile + gridDim.x < a.tiles) load_nx(tile + gridDim.x);
       first = false;
+      if (jac && has_next) {   // TMEM [0, 256) read out: the next tile's MMA1, then its successor's Xmid load
+        if (!issue_mma1(buf ^ 1)) break;
+        if (tile + 2 * step < a.tiles) load2(s, xs, a.xmid + (tile + 2 * step) * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+      }
       tc_fence_before();
       __syncthreads();
     }
   }
-  if (!s.bad && !first && !a.jac.nvirt) {
+  if (!s.bad && !first && !jac) {
     float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
     const int F = a.F;
     // dW1_c^T block: lane m = hidden unit (of this half), column n = input feature i
@@ -563,6 +598,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
     if (a.do_db2)
       for (int i = threadIdx.x; i < D; i += kMlpThreads) atomicAdd(g + a.off_b2 + i, db2[i]);
   }
+  if (s.bad) mbar_wait(bar2, ph2);   // bounded: the error path waits out a product still in flight
   sync_finish(s);
 }
 
@@ -603,22 +639,27 @@ struct A1Args {
   JacOut jac;
 };
 
+// 512 threads: thread (row, quarter) stages a quarter of the columns; 16 warps share the tile's
+// (sequence, head) attention units.
+constexpr int kA1Threads = 512;
+
 template <int D, int HD>
-__global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
+__global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
   using G = A1Geo<D>;
   extern __shared__ __align__(1024) uint8_t sm[];
-  constexpr int HALF = D / 2, LDH = G::LDH;
+  constexpr int NQ = kA1Threads / 128, QC = D / NQ, LDH = G::LDH;
+  static_assert(QC % 16 == 0, "column groups of 16");
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+  const int row = 32 * (warp & 3) + lane, quarter = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
   const uint32_t wr = smem_u32(sm + G::W_OFF), wo = smem_u32(sm + G::WO_OFF), xs0 = smem_u32(sm + G::X_OFF),
                  dxs = smem_u32(sm + G::DX_OFF), hs = smem_u32(sm + G::H_OFF), f16 = smem_u32(sm + G::F_OFF);
   __half *Fh = reinterpret_cast<__half *>(sm + G::F_OFF);   // Q, K, V, dH at multiples of HROWS * LDH
-  for (int i = threadIdx.x; i < kRows * 128 * 2 / 16; i += kThreads)
+  for (int i = threadIdx.x; i < kRows * 128 * 2 / 16; i += kA1Threads)
     reinterpret_cast<uint4 *>(sm + G::H_OFF)[i] = make_uint4(0, 0, 0, 0);
-  for (int i = threadIdx.x; i < 4 * 16 * LDH / 8; i += kThreads) {   // the 16 rows after each tile block
+  for (int i = threadIdx.x; i < 4 * 16 * LDH / 8; i += kA1Threads) {   // the 16 rows after each tile block
     const int arr = i / (16 * LDH / 8), k = i % (16 * LDH / 8);
     reinterpret_cast<uint4 *>(Fh + arr * G::HROWS * LDH + kRows * LDH)[k] = make_uint4(0, 0, 0, 0);
   }
@@ -638,16 +679,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
     int buf = 0;
     for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, buf ^= 1) {
       const uint32_t xs = xs0 + buf * G::IMG;
-      const size_t rg = (tile * kRows + row) * (size_t)D + half * HALF;
+      const size_t rg = (tile * kRows + row) * (size_t)D + quarter * QC;
       {
-        float v[HALF];
+        float v[QC];
 #pragma unroll
-        for (int j = 0; j < HALF; j += 4) {
+        for (int j = 0; j < QC; j += 4) {
           const float4 q = *reinterpret_cast<const float4 *>(a.dxm + rg + j);
           v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
         }
 #pragma unroll
-        for (int j = 0; j < HALF; j += 8) st_row8(sm + G::DX_OFF, row, half * HALF + j, D, v + j);
+        for (int j = 0; j < QC; j += 8) st_row8(sm + G::DX_OFF, row, quarter * QC + j, D, v + j);
       }
       ok = wait_ld(s);   // this tile's X image
       fence_proxy_async();
@@ -668,11 +709,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
 #pragma unroll
       for (int part = 0; part < 4; ++part) {
         const int col0 = part < 3 ? G::C_QKV + part * D : G::C_DH;
-        __half *dst = Fh + part * G::HROWS * LDH + row * LDH + half * HALF;
+        __half *dst = Fh + part * G::HROWS * LDH + row * LDH + quarter * QC;
 #pragma unroll
-        for (int j = 0; j < HALF; j += 16) {
+        for (int j = 0; j < QC; j += 16) {
           float v[16];
-          tmem_ld16(s.tmem + lane_addr + col0 + half * HALF + j, v);
+          tmem_ld16(s.tmem + lane_addr + col0 + quarter * QC + j, v);
           uint4 q0, q1;
           q0.x = amma::h2(v[0], v[1]);   q0.y = amma::h2(v[2], v[3]);
           q0.z = amma::h2(v[4], v[5]);   q0.w = amma::h2(v[6], v[7]);
@@ -685,11 +726,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
       (void)valid;
       __syncthreads();   // every row's Q, K, V, dH visible
       uint8_t *dq_img = a.dqkv + tile * (size_t)(kRows * 3 * D * 2);
-      for (int i = threadIdx.x; i < (kRows - nvalid) * (3 * D / 8); i += kThreads) {   // padding rows: dQKV = 0
+      for (int i = threadIdx.x; i < (kRows - nvalid) * (3 * D / 8); i += kA1Threads) {   // padding rows: dQKV = 0
         const int r = nvalid + i / (3 * D / 8), c8 = i % (3 * D / 8);
         *reinterpret_cast<uint4 *>(dq_img + canon(r, 8 * c8, 3 * D)) = make_uint4(0, 0, 0, 0);
       }
-      for (int u = warp; u < a.ts * heads; u += kThreads / 32) {
+      for (int u = warp; u < a.ts * heads; u += kA1Threads / 32) {
         const int sq = u / heads, h = u % heads, rb = sq * n;
         const uint32_t off = (uint32_t)(rb * LDH + h * HD) * 2;
         amma::attn_fwd_bwd_h<HD>(f16 + off, f16 + G::F_BYTES + off, f16 + 2 * G::F_BYTES + off,
@@ -719,10 +760,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
       if (a.jac.nvirt) {
         if (!sync_ok(s, ok)) break;
         if (a.jac.o16) {   // FP16 attention copies (free after the attention)
-          jac_flush_rows<2>(s, a.jac, tile, G::C_JWO, D, a.off_wo, D, D, reinterpret_cast<float *>(sm + G::F_OFF));
+          jac_flush_rows<NQ>(s, a.jac, tile, G::C_JWO, D, a.off_wo, D, D, reinterpret_cast<float *>(sm + G::F_OFF));
         } else {
           auto iwo = [&](int m, int nn) -> long long { return m < D ? a.off_wo + (long long)m * D + nn : -1; };
-          jac_flush<decltype(iwo), 2>(s, a.jac, tile, G::C_JWO, D, iwo);
+          jac_flush<decltype(iwo), NQ>(s, a.jac, tile, G::C_JWO, D, iwo);
         }
       }
       tc_fence_before();
@@ -731,9 +772,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn1(A1Args a) {
   }
   if (!s.bad && !first && !a.jac.nvirt) {
     float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
-    flush_block(s, G::C_WO, D, g, [&](int m, int nn) -> long long {
-      return m < D ? a.off_wo + (long long)m * D + nn : -1;
-    });
+    auto iwo = [&](int m, int nn) -> long long { return m < D ? a.off_wo + (long long)m * D + nn : -1; };
+    flush_block<decltype(iwo), NQ>(s, G::C_WO, D, g, iwo);
   }
   sync_finish(s);
 }
@@ -1136,8 +1176,8 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
     a1.off_wo = Wo[l];
     a1.err = err;
     a1.jac = jo;
-    if (m.dh == 8) k_bwd_attn1<D, 8><<<grid, kThreads, A1Geo<D>::BYTES, st>>>(a1);
-    else k_bwd_attn1<D, 16><<<grid, kThreads, A1Geo<D>::BYTES, st>>>(a1);
+    if (m.dh == 8) k_bwd_attn1<D, 8><<<grid, kA1Threads, A1Geo<D>::BYTES, st>>>(a1);
+    else k_bwd_attn1<D, 16><<<grid, kA1Threads, A1Geo<D>::BYTES, st>>>(a1);
     A2Args a2;
     a2.wqkv = v.wqkvr;
     a2.x = bf.x + (size_t)l * tiles * img;
