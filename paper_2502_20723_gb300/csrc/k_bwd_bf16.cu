@@ -353,11 +353,12 @@ struct MlpGeo {
   static constexpr int G_OFF = DX_OFF + 2 * IMG;       // G  [128][HC]
   static constexpr int DU_OFF = G_OFF + kRows * HC * 2;  // dU [128][HC]
   static constexpr int ONE_OFF = DU_OFF + kRows * HC * 2;  // all-ones [128][16] (row sums by MMA)
-  static constexpr int M_OFF = ONE_OFF + kRows * 16 * 2;    // misc: bars, holder, db2[D], b1 of the chunk [HC]
-  static constexpr int BYTES = M_OFF + 64 + 4 * D + 4 * HC;
-  // TMEM columns (C_B1: db1 = dU^T 1, every one of its 16 columns holds the same sums)
-  static constexpr int C_U = 0, C_DG = 128, C_DX = 256, C_W1 = 320, C_W2 = 384, C_B1 = 448;
-  static constexpr int C_JB1 = 320;   // per-configuration mode: 4 x 16 db1 columns (dW1/dW2 blocks in [0, 256))
+  static constexpr int M_OFF = ONE_OFF + kRows * 16 * 2;    // misc: bars, holder, b1 of the chunk [HC]
+  static constexpr int BYTES = M_OFF + 64 + 4 * HC;
+  // TMEM columns (C_B1: db1 = dU^T 1, C_B2: db2 = dX^T 1; every one of their 16 columns holds the same sums)
+  static constexpr int C_U = 0, C_DG = 128, C_DX = 256, C_W1 = 320, C_W2 = 384, C_B1 = 448, C_B2 = 464;
+  // per-configuration mode: 4 x 16 db1 and 4 x 16 db2 columns (dW1/dW2 blocks in [0, 256))
+  static constexpr int C_JB1 = 320, C_JB2 = 384;
 };
 
 struct MlpArgs {
@@ -384,7 +385,9 @@ struct MlpArgs {
 // for the end of the tile.
 constexpr int kMlpThreads = 512;
 
-template <int D>
+// ADD: the dX' part is added onto dxm (the first pass's output, a.base == a.dxm) by one vector reduction
+// per element, with no read of the base here.
+template <int D, bool ADD>
 __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   using G = MlpGeo<D>;
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -396,9 +399,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   if (threadIdx.x == 0) mbar_init(bar2, 1);   // made visible by the fence and barrier in sync_init
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
-  float *db2 = reinterpret_cast<float *>(sm + G::M_OFF + 64);
-  float *b1s = db2 + D;
-  for (int i = threadIdx.x; i < D; i += kMlpThreads) db2[i] = 0.f;
+  float *b1s = reinterpret_cast<float *>(sm + G::M_OFF + 64);
   for (int i = threadIdx.x; i < G::HC; i += kMlpThreads) b1s[i] = a.b1[i];
   for (int i = threadIdx.x; i < kRows * 16 / 8; i += kMlpThreads)   // bf16 1.0 = 0x3F80
     reinterpret_cast<uint4 *>(sm + G::ONE_OFF)[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
@@ -427,9 +428,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
 #pragma unroll
       for (int j = 0; j < QD / 4; ++j) nx[j] = src[j];
     };
-    // dX image of tile t (BF16, buffer b) from nx, and its db2 share (per configuration: the warp's 32 rows
-    // are one virtual configuration)
-    auto put_dx = [&](size_t t, int b) {
+    // dX image of tile t (BF16, buffer b) from nx
+    auto put_dx = [&](int b) {
       float dxo[QD];
 #pragma unroll
       for (int j = 0; j < QD; j += 4) {
@@ -438,16 +438,6 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       }
 #pragma unroll
       for (int j = 0; j < QD; j += 8) st_row8(sm + G::DX_OFF + b * G::IMG, row, cg * QD + j, D, dxo + j);
-      if (a.do_db2) {
-#pragma unroll
-        for (int j = 0; j < QD; ++j) {
-          const float sum = warp_sum_f(dxo[j]);
-          if (lane == 0) {
-            if (!jac) atomicAdd(&db2[cg * QD + j], sum);
-            else if (t * 4 + (warp & 3) < a.jac.nvirt) jac_put1(a.jac, t * 4 + (warp & 3), a.off_b2 + cg * QD + j, sum);
-          }
-        }
-      }
     };
     // MMA1 of tile t from buffer b, once its Xmid image has landed and its dX image is written
     auto issue_mma1 = [&](int b) -> bool {
@@ -466,7 +456,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
     // prologue: tile t0 in buffer 0, then the Xmid image of t0 + step into buffer 1
     load2(s, xs0, a.xmid + t0 * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
     load_nx(t0);
-    put_dx(t0, 0);
+    put_dx(0);
     if (t0 + step < a.tiles) load_nx(t0 + step);
     bool live = issue_mma1(0);
     if (live && t0 + step < a.tiles) load2(s, xs0 + G::IMG, a.xmid + (t0 + step) * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
@@ -502,24 +492,29 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
           mma_mm(s, dus, G::HC, xs, D, D, G::C_W1, !first);          // dW1_c^T += dU^T Xmid
           mma_mm(s, gs, G::HC, dxs, D, D, G::C_W2, !first);          // dW2_c   += G^T dX
           mma_mm(s, dus, G::HC, ones, 16, 16, G::C_B1, !first);       // db1_c   += dU^T 1
+          // db2 += dX^T 1: M = 128 reads the D-wide image as 128 features; lanes >= D hold unused sums
+          if (a.do_db2) mma_mm(s, dxs, D, ones, 16, 16, G::C_B2, !first);
         } else {   // per configuration: dW1_c^T into columns [64 c, 64 c + 64) (U and dG are consumed)
           for (int c = 0; c < 4; ++c) {
             mma_mm_rows(s, dus, G::HC, xs, D, D, 64 * c, 32 * c, 2);
             mma_mm_rows(s, dus, G::HC, ones, 16, 16, G::C_JB1 + 16 * c, 32 * c, 2);
+            if (a.do_db2) mma_mm_rows(s, dxs, D, ones, 16, 16, G::C_JB2 + 16 * c, 32 * c, 2);
           }
         }
         mma_commit(bar2);
       }
-      // while MMA2 runs: this tile's residual base, the next tile's dX image (the other buffer, last read
-      // by the previous tile's MMA2) and, in VJP mode, the next tile's MMA1
+      // while MMA2 runs: this tile's residual base (unless dX' is added in place), the next tile's dX image
+      // (the other buffer, last read by the previous tile's MMA2) and, in VJP mode, the next tile's MMA1
       float base[QD];
+      if (!ADD) {
 #pragma unroll
-      for (int j = 0; j < QD; j += 4) {
-        const float4 q = *reinterpret_cast<const float4 *>(a.base + rg + j);
-        base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
+        for (int j = 0; j < QD; j += 4) {
+          const float4 q = *reinterpret_cast<const float4 *>(a.base + rg + j);
+          base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
+        }
       }
       if (has_next) {
-        put_dx(tile + step, buf ^ 1);
+        put_dx(buf ^ 1);
         if (tile + 2 * step < a.tiles) load_nx(tile + 2 * step);
         if (!jac && !issue_mma1(buf ^ 1)) break;
       }
@@ -535,13 +530,19 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
         const int F = a.F;
         auto i1 = [&](int m, int nn) -> long long { return a.off_w1 + (long long)nn * F + m; };
         jac_flush<decltype(i1), NQ>(s, a.jac, tile, 0, D, i1);
-        {   // db1 per configuration: column 0 of each 16-column block, lane m = hidden unit
+        if (cg == 0) {   // db1 (lane m = hidden unit) and db2 (lane m < D = feature) per configuration:
+                         // column 0 of each 16-column block
           float re[16], im[16];
           for (int pr = 0; pr < 2; ++pr) {
-            tmem_ld16(s.tmem + lane_addr + G::C_JB1 + 16 * (2 * pr), re);
-            tmem_ld16(s.tmem + lane_addr + G::C_JB1 + 16 * (2 * pr + 1), im);
             const size_t v0 = tile * 4 + 2 * pr;
-            if (cg == 0 && v0 + 1 < a.jac.nvirt) jac_put2(a.jac, v0 >> 1, a.off_b1 + row, re[0], im[0]);
+            tmem_ld16x2(s.tmem + lane_addr + G::C_JB1 + 16 * (2 * pr), re,
+                        s.tmem + lane_addr + G::C_JB1 + 16 * (2 * pr + 1), im);
+            if (v0 + 1 < a.jac.nvirt) jac_put2(a.jac, v0 >> 1, a.off_b1 + row, re[0], im[0]);
+            if (a.do_db2) {
+              tmem_ld16x2(s.tmem + lane_addr + G::C_JB2 + 16 * (2 * pr), re,
+                          s.tmem + lane_addr + G::C_JB2 + 16 * (2 * pr + 1), im);
+              if (row < D && v0 + 1 < a.jac.nvirt) jac_put2(a.jac, v0 >> 1, a.off_b2 + row, re[0], im[0]);
+            }
           }
         }
         tc_fence_before();
@@ -567,10 +568,14 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
         float v[16];
         tmem_ld16(s.tmem + lane_addr + G::C_DX + cg * QD + j, v);
 #pragma unroll
-        for (int e = 0; e < 16; e += 4)
-          *reinterpret_cast<float4 *>(a.dxm + rg + j + e) =
-              make_float4(base[j + e] + v[e], base[j + e + 1] + v[e + 1], base[j + e + 2] + v[e + 2],
-                          base[j + e + 3] + v[e + 3]);
+        for (int e = 0; e < 16; e += 4) {
+          float4 *dst = reinterpret_cast<float4 *>(a.dxm + rg + j + e);
+          if (ADD)
+            atomicAdd(dst, make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]));
+          else
+            *dst = make_float4(base[j + e] + v[e], base[j + e + 1] + v[e + 1], base[j + e + 2] + v[e + 2],
+                               base[j + e + 3] + v[e + 3]);
+        }
       }
       first = false;
       if (jac && has_next) {   // TMEM [0, 256) read out: the next tile's MMA1, then its successor's Xmid load
@@ -589,14 +594,12 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
     auto i2 = [&](int m, int n) -> long long { return a.off_w2 + (long long)m * D + n; };
     flush_block<decltype(i1), NQ>(s, G::C_W1, D, g, i1);
     flush_block<decltype(i2), NQ>(s, G::C_W2, D, g, i2);
-    if (cg == 0) {   // lane m of the db1 accumulator = hidden unit m of this half
-      float v[16];
-      tmem_ld16(s.tmem + lane_addr + G::C_B1, v);
+    if (cg == 0) {   // lane m of the db1 accumulator = hidden unit m of this half; of db2 = feature m < D
+      float v[16], w[16];
+      tmem_ld16x2(s.tmem + lane_addr + G::C_B1, v, s.tmem + lane_addr + G::C_B2, w);
       atomicAdd(g + a.off_b1 + row, v[0]);
+      if (a.do_db2 && row < D) atomicAdd(g + a.off_b2 + row, w[0]);
     }
-    __syncthreads();
-    if (a.do_db2)
-      for (int i = threadIdx.x; i < D; i += kMlpThreads) atomicAdd(g + a.off_b2 + i, db2[i]);
   }
   if (s.bad) mbar_wait(bar2, ph2);   // bounded: the error path waits out a product still in flight
   sync_finish(s);
@@ -615,8 +618,8 @@ struct A1Geo {
   static constexpr int W_BYTES = 3 * D * D * 2;
   static constexpr int WO_OFF = W_OFF + W_BYTES;       // Wo rows [D][D], kept
   static constexpr int X_OFF = WO_OFF + D * D * 2;     // X images [2][128][D] (the next tile's early)
-  static constexpr int DX_OFF = X_OFF + 2 * IMG;       // dX' BF16 image
-  static constexpr int H_OFF = DX_OFF + IMG;           // head outputs [128][128] BF16 (upper half zero)
+  static constexpr int DX_OFF = X_OFF + 2 * IMG;       // dX' BF16 images [2][128][D] (read by dWo of the tile)
+  static constexpr int H_OFF = DX_OFF + 2 * IMG;       // head outputs [128][128] BF16 (upper half zero)
   static constexpr int F_OFF = H_OFF + kRows * 128 * 2;   // Q, K, V, dH FP16 [HROWS][LDH] each
   static constexpr int F_BYTES = HROWS * LDH * 2;
   static constexpr int M_OFF = F_OFF + 4 * F_BYTES;
@@ -640,7 +643,8 @@ struct A1Args {
 };
 
 // 512 threads: thread (row, quarter) stages a quarter of the columns; 16 warps share the tile's
-// (sequence, head) attention units.
+// (sequence, head) attention units.  The next tile's dX' rows are read during this tile; in VJP mode the
+// dWo product of a tile (barrier bar2) completes behind the next tile's loads and products.
 constexpr int kA1Threads = 512;
 
 template <int D, int HD>
@@ -649,13 +653,17 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   constexpr int NQ = kA1Threads / 128, QC = D / NQ, LDH = G::LDH;
   static_assert(QC % 16 == 0, "column groups of 16");
+  const uint32_t bar2 = smem_u32(sm + G::M_OFF + 24);
+  uint32_t ph2 = 0;
+  bool pend2 = false;
+  if (threadIdx.x == 0) mbar_init(bar2, 1);   // made visible by the fence and barrier in sync_init
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (warp & 3) + lane, quarter = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
   const uint32_t wr = smem_u32(sm + G::W_OFF), wo = smem_u32(sm + G::WO_OFF), xs0 = smem_u32(sm + G::X_OFF),
-                 dxs = smem_u32(sm + G::DX_OFF), hs = smem_u32(sm + G::H_OFF), f16 = smem_u32(sm + G::F_OFF);
+                 dxs0 = smem_u32(sm + G::DX_OFF), hs = smem_u32(sm + G::H_OFF), f16 = smem_u32(sm + G::F_OFF);
   __half *Fh = reinterpret_cast<__half *>(sm + G::F_OFF);   // Q, K, V, dH at multiples of HROWS * LDH
   for (int i = threadIdx.x; i < kRows * 128 * 2 / 16; i += kA1Threads)
     reinterpret_cast<uint4 *>(sm + G::H_OFF)[i] = make_uint4(0, 0, 0, 0);
@@ -676,20 +684,27 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
   bool first = true;
   if (sync_ok(s, ok)) {
     if ((size_t)blockIdx.x < a.tiles) load2(s, xs0, a.x + blockIdx.x * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+    float4 nx[QC / 4];   // this thread's dX' of the coming tile
+    auto load_nx = [&](size_t t) {
+      const float4 *src = reinterpret_cast<const float4 *>(a.dxm + (t * kRows + row) * (size_t)D + quarter * QC);
+#pragma unroll
+      for (int j = 0; j < QC / 4; ++j) nx[j] = src[j];
+    };
+    if ((size_t)blockIdx.x < a.tiles) load_nx(blockIdx.x);
     int buf = 0;
     for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, buf ^= 1) {
-      const uint32_t xs = xs0 + buf * G::IMG;
-      const size_t rg = (tile * kRows + row) * (size_t)D + quarter * QC;
-      {
+      const uint32_t xs = xs0 + buf * G::IMG, dxs = dxs0 + buf * G::IMG;
+      {   // this buffer was last read by the dWo product two tiles back, waited for in the previous tile
         float v[QC];
 #pragma unroll
         for (int j = 0; j < QC; j += 4) {
-          const float4 q = *reinterpret_cast<const float4 *>(a.dxm + rg + j);
+          const float4 q = nx[j / 4];
           v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
         }
 #pragma unroll
-        for (int j = 0; j < QC; j += 8) st_row8(sm + G::DX_OFF, row, quarter * QC + j, D, v + j);
+        for (int j = 0; j < QC; j += 8) st_row8(sm + G::DX_OFF + buf * G::IMG, row, quarter * QC + j, D, v + j);
       }
+      if (tile + gridDim.x < a.tiles) load_nx(tile + gridDim.x);
       ok = wait_ld(s);   // this tile's X image
       fence_proxy_async();
       if (!sync_ok(s, ok)) break;
@@ -704,6 +719,11 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
         mma_commit(s.bar_mma);
       }
       ok = wait_mma(s);
+      if (pend2) {   // the previous tile's dWo product: complete, the products just waited for came after it
+        ok = mbar_wait(bar2, ph2) && ok;
+        ph2 ^= 1u;
+        pend2 = false;
+      }
       if (!sync_ok(s, ok)) break;
       // Q, K, V, dH -> FP16 rows (TMEM loads are warp-collective; rows past the tile's sequences stay)
 #pragma unroll
@@ -750,14 +770,18 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
         tc_fence_after();
         if (!a.jac.nvirt) {
           mma_mm(s, hs, 128, dxs, D, D, G::C_WO, !first);   // dWo += H^T dX'   (rows of H beyond D are zero)
+          mma_commit(bar2);
         } else {
           for (int c = 0; c < 4; ++c) mma_mm_rows(s, hs, 128, dxs, D, D, G::C_JWO + 64 * c, 32 * c, 2);
+          mma_commit(s.bar_mma);
         }
-        mma_commit(s.bar_mma);
       }
-      ok = wait_mma(s);
       first = false;
-      if (a.jac.nvirt) {
+      ok = true;
+      if (!a.jac.nvirt) {
+        pend2 = true;
+      } else {
+        ok = wait_mma(s);
         if (!sync_ok(s, ok)) break;
         if (a.jac.o16) {   // FP16 attention copies (free after the attention)
           jac_flush_rows<NQ>(s, a.jac, tile, G::C_JWO, D, a.off_wo, D, D, reinterpret_cast<float *>(sm + G::F_OFF));
@@ -769,6 +793,12 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
       tc_fence_before();
       if (!sync_ok(s, ok)) break;
     }
+  }
+  if (pend2) {   // the last tile's dWo product (bounded wait, also on the error path)
+    const bool okw = mbar_wait(bar2, ph2);
+    ph2 ^= 1u;
+    tc_fence_after();
+    sync_ok(s, okw);
   }
   if (!s.bad && !first && !a.jac.nvirt) {
     float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
@@ -1126,7 +1156,8 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
 #define TDO_COMMA ,
 #define TDO_SET_SMEM(K, BYTES)                                                                 \
   if ((e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES)) != cudaSuccess) return e;
-  TDO_SET_SMEM(k_bwd_mlp<D>, MlpGeo<D>::BYTES);
+  TDO_SET_SMEM(k_bwd_mlp<D TDO_COMMA false>, MlpGeo<D>::BYTES);
+  TDO_SET_SMEM(k_bwd_mlp<D TDO_COMMA true>, MlpGeo<D>::BYTES);
   TDO_SET_SMEM(k_bwd_attn2<D>, A2Geo<D>::BYTES);
   TDO_SET_SMEM(k_bwd_attn1<D TDO_COMMA 8>, A1Geo<D>::BYTES);
   TDO_SET_SMEM(k_bwd_attn1<D TDO_COMMA 16>, A1Geo<D>::BYTES);
@@ -1157,7 +1188,8 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
         ma.F = m.ffn;
         ma.err = err;
         ma.jac = jo;
-        k_bwd_mlp<D><<<grid, kMlpThreads, MlpGeo<D>::BYTES, st>>>(ma);
+        if (hb == 0) k_bwd_mlp<D, false><<<grid, kMlpThreads, MlpGeo<D>::BYTES, st>>>(ma);
+        else k_bwd_mlp<D, true><<<grid, kMlpThreads, MlpGeo<D>::BYTES, st>>>(ma);
       }
       dxmid = bf.dxb;
     }
