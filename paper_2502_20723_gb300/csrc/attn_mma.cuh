@@ -209,12 +209,13 @@ __device__ __forceinline__ void attn_fwd_bwd(const float *Q, const float *K, con
 //   Qh, Kh: [rows][ldh] halves, this sequence's rows from 0 (Q pre-scaled by 1/sqrt(HD) log2 e),
 //   Vt:     [features][ldt] halves, V transposed, this sequence's keys at columns 0..15 (keys >= n zero),
 // all with 4-byte-aligned pairs.  emit(row, col, v0, v1) for the attention output O, row < n.
-template <int HD, typename EMIT>
+// FULL: n = 16 at compile time (no masks).
+template <int HD, bool FULL = false, typename EMIT>
 __device__ __forceinline__ void attn_fwd_h(const __half *Qh, const __half *Kh, const __half *Vt, int ldh, int ldt,
                                            int n, EMIT emit) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   auto ld2 = [&](const __half *M, int r, int c) -> uint32_t {
-    return r < n ? *reinterpret_cast<const uint32_t *>(M + r * ldh + c) : 0u;
+    return (FULL || r < n) ? *reinterpret_cast<const uint32_t *>(M + r * ldh + c) : 0u;
   };
   float s[2][4];
 #pragma unroll
@@ -233,7 +234,7 @@ __device__ __forceinline__ void attn_fwd_h(const __half *Qh, const __half *Kh, c
   for (int j = 0; j < 2; ++j)
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      const bool ok = 8 * j + 2 * t + e < n;
+      const bool ok = FULL || 8 * j + 2 * t + e < n;
       s[j][e] = ok ? s[j][e] : -INFINITY;
       s[j][2 + e] = ok ? s[j][2 + e] : -INFINITY;
       m0 = fmaxf(m0, s[j][e]);
@@ -268,8 +269,8 @@ __device__ __forceinline__ void attn_fwd_h(const __half *Qh, const __half *Kh, c
     zero4(o);
     const __half *vr = Vt + (8 * c + g) * ldt;
     mma16816(o, pa, *reinterpret_cast<const uint32_t *>(vr + 2 * t), *reinterpret_cast<const uint32_t *>(vr + 8 + 2 * t));
-    if (g < n) emit(g, 8 * c + 2 * t, o[0], o[1]);
-    if (g + 8 < n) emit(g + 8, 8 * c + 2 * t, o[2], o[3]);
+    if (FULL || g < n) emit(g, 8 * c + 2 * t, o[0], o[1]);
+    if (FULL || g + 8 < n) emit(g + 8, 8 * c + 2 * t, o[2], o[3]);
   }
 }
 
@@ -349,8 +350,9 @@ __device__ __forceinline__ void mma_y(const uint32_t (&x)[4], const uint32_t (&b
 // shared memory: Qh, Kh, Vh, dHh are u32 shared addresses of this sequence's first row and this head's
 // first feature in [rows][ldh] row-major FP16 arrays (Q unscaled), readable 16 rows down (rows >= n
 // hold finite values: the next sequence or zero padding).  Keys >= n are masked; query rows >= n get
-// zero probabilities, so they add nothing to dK and dV.  emit as in attn_fwd_bwd.
-template <int HD, typename EMIT>
+// zero probabilities, so they add nothing to dK and dV.  emit as in attn_fwd_bwd.  FULL: n = 16 at
+// compile time (no masks).
+template <int HD, bool FULL = false, typename EMIT>
 __device__ __forceinline__ void attn_fwd_bwd_h(uint32_t Qh, uint32_t Kh, uint32_t Vh, uint32_t dHh, int ldh, int n,
                                                float qscale, float scale, EMIT emit) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -359,13 +361,13 @@ __device__ __forceinline__ void attn_fwd_bwd_h(uint32_t Qh, uint32_t Kh, uint32_
   frag_bn<HD>(Kh, ldh, kb);
   float s[2][4];
   mma_s<HD>(qa, kb, s);
-  const bool q0 = g < n, q1 = g + 8 < n;
+  const bool q0 = FULL || g < n, q1 = FULL || g + 8 < n;
   float m0 = -INFINITY, m1 = -INFINITY;
 #pragma unroll
   for (int j = 0; j < 2; ++j)
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      const bool ok = 8 * j + 2 * t + e < n;
+      const bool ok = FULL || 8 * j + 2 * t + e < n;
       s[j][e] = ok ? s[j][e] * qscale : -INFINITY;
       s[j][2 + e] = ok ? s[j][2 + e] * qscale : -INFINITY;
       m0 = fmaxf(m0, s[j][e]);

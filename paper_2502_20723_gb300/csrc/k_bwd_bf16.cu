@@ -20,6 +20,8 @@
 // image's feature dimension, K = the 128 rows of the tile.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "attn_mma.cuh"
 #include "tcgen05.cuh"
 #include "tdo_device.cuh"
@@ -365,8 +367,8 @@ struct MlpArgs {
   const uint8_t *w1t, *w2, *w1;   // packed images of this half: W1^T [HC][D], W2 rows [HC][D], W1 rows [D][HC]
   const float *b1;                // b1 of this half
   const uint8_t *xmid;            // [tiles] images
-  const float *dxo, *base;        // FP32 [tiles*128][D]
-  float *dxm;                     // FP32 out
+  const float *dxo;               // FP32 [tiles*128][D]: dX at the MLP output
+  float *dxm;                     // FP32 out: dX' (first pass: dxo + its part; second pass: += its part)
   size_t tiles;
   int do_db2;
   float *g;
@@ -385,8 +387,8 @@ struct MlpArgs {
 // for the end of the tile.
 constexpr int kMlpThreads = 512;
 
-// ADD: the dX' part is added onto dxm (the first pass's output, a.base == a.dxm) by one vector reduction
-// per element, with no read of the base here.
+// ADD: the dX' part is added onto dxm (the first pass's output) by one vector reduction per element, with
+// no read of it here.
 template <int D, bool ADD>
 __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   using G = MlpGeo<D>;
@@ -503,15 +505,13 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
         }
         mma_commit(bar2);
       }
-      // while MMA2 runs: this tile's residual base (unless dX' is added in place), the next tile's dX image
-      // (the other buffer, last read by the previous tile's MMA2) and, in VJP mode, the next tile's MMA1
-      float base[QD];
-      if (!ADD) {
+      // while MMA2 runs: this tile's residual base (first pass: dX again, from L2; the loads are pinned
+      // here), the next tile's dX image (the other buffer, last read by the previous tile's MMA2) and, in
+      // VJP mode, the next tile's MMA1
+      float4 base[ADD ? 1 : QD / 4];
+      if constexpr (!ADD) {
 #pragma unroll
-        for (int j = 0; j < QD; j += 4) {
-          const float4 q = *reinterpret_cast<const float4 *>(a.base + rg + j);
-          base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
-        }
+        for (int j = 0; j < QD / 4; ++j) base[j] = ld_pinned_f4(a.dxo + rg + 4 * j);
       }
       if (has_next) {
         put_dx(buf ^ 1);
@@ -570,11 +570,12 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
 #pragma unroll
         for (int e = 0; e < 16; e += 4) {
           float4 *dst = reinterpret_cast<float4 *>(a.dxm + rg + j + e);
-          if (ADD)
+          if constexpr (ADD) {
             atomicAdd(dst, make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]));
-          else
-            *dst = make_float4(base[j + e] + v[e], base[j + e + 1] + v[e + 1], base[j + e + 2] + v[e + 2],
-                               base[j + e + 3] + v[e + 3]);
+          } else {
+            const float4 b = base[(j + e) / 4];
+            *dst = make_float4(b.x + v[e], b.y + v[e + 1], b.z + v[e + 2], b.w + v[e + 3]);
+          }
         }
       }
       first = false;
@@ -726,21 +727,20 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
       }
       if (!sync_ok(s, ok)) break;
       // Q, K, V, dH -> FP16 rows (TMEM loads are warp-collective; rows past the tile's sequences stay)
+      static_assert(QC == 16, "one 16-column group per part");
 #pragma unroll
-      for (int part = 0; part < 4; ++part) {
-        const int col0 = part < 3 ? G::C_QKV + part * D : G::C_DH;
-        __half *dst = Fh + part * G::HROWS * LDH + row * LDH + quarter * QC;
+      for (int pp = 0; pp < 2; ++pp) {   // parts (Q, K) then (V, dH): two TMEM loads per wait
+        float v[2][16];
+        tmem_ld16x2(s.tmem + lane_addr + G::C_QKV + (2 * pp) * D + quarter * QC, v[0],
+                    s.tmem + lane_addr + (pp == 0 ? G::C_QKV + D : G::C_DH) + quarter * QC, v[1]);
 #pragma unroll
-        for (int j = 0; j < QC; j += 16) {
-          float v[16];
-          tmem_ld16(s.tmem + lane_addr + col0 + quarter * QC + j, v);
-          uint4 q0, q1;
-          q0.x = amma::h2(v[0], v[1]);   q0.y = amma::h2(v[2], v[3]);
-          q0.z = amma::h2(v[4], v[5]);   q0.w = amma::h2(v[6], v[7]);
-          q1.x = amma::h2(v[8], v[9]);   q1.y = amma::h2(v[10], v[11]);
-          q1.z = amma::h2(v[12], v[13]); q1.w = amma::h2(v[14], v[15]);
-          reinterpret_cast<uint4 *>(dst + j)[0] = q0;
-          reinterpret_cast<uint4 *>(dst + j)[1] = q1;
+        for (int h = 0; h < 2; ++h) {
+          __half *dst = Fh + (2 * pp + h) * G::HROWS * LDH + row * LDH + quarter * QC;
+          const float *w = v[h];
+          reinterpret_cast<uint4 *>(dst)[0] = make_uint4(amma::h2(w[0], w[1]), amma::h2(w[2], w[3]),
+                                                         amma::h2(w[4], w[5]), amma::h2(w[6], w[7]));
+          reinterpret_cast<uint4 *>(dst)[1] = make_uint4(amma::h2(w[8], w[9]), amma::h2(w[10], w[11]),
+                                                         amma::h2(w[12], w[13]), amma::h2(w[14], w[15]));
         }
       }
       (void)valid;
@@ -750,20 +750,23 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
         const int r = nvalid + i / (3 * D / 8), c8 = i % (3 * D / 8);
         *reinterpret_cast<uint4 *>(dq_img + canon(r, 8 * c8, 3 * D)) = make_uint4(0, 0, 0, 0);
       }
-      for (int u = warp; u < a.ts * heads; u += kA1Threads / 32) {
-        const int sq = u / heads, h = u % heads, rb = sq * n;
-        const uint32_t off = (uint32_t)(rb * LDH + h * HD) * 2;
-        amma::attn_fwd_bwd_h<HD>(f16 + off, f16 + G::F_BYTES + off, f16 + 2 * G::F_BYTES + off,
-                                 f16 + 3 * G::F_BYTES + off, LDH, n, qscale, scale,
-                                 [&](int kind, int r, int c, float v0, float v1) {
-                                   const int rr = rb + r, col = h * HD + c;
-                                   if (kind == 0)
-                                     *reinterpret_cast<uint32_t *>(sm + G::H_OFF + canon(rr, col, 128)) = pack_bf16(v0, v1);
-                                   else
-                                     *reinterpret_cast<uint32_t *>(dq_img + canon(rr, (kind - 1) * D + col, 3 * D)) =
-                                         pack_bf16(v0, v1);
-                                 });
-      }
+      auto units = [&](auto full) {
+        for (int u = warp; u < a.ts * heads; u += kA1Threads / 32) {
+          const int sq = u / heads, h = u % heads, rb = sq * n;
+          const uint32_t off = (uint32_t)(rb * LDH + h * HD) * 2;
+          amma::attn_fwd_bwd_h<HD, decltype(full)::value>(
+              f16 + off, f16 + G::F_BYTES + off, f16 + 2 * G::F_BYTES + off, f16 + 3 * G::F_BYTES + off, LDH, n,
+              qscale, scale, [&](int kind, int r, int c, float v0, float v1) {
+                const int rr = rb + r, col = h * HD + c;
+                if (kind == 0)
+                  *reinterpret_cast<uint32_t *>(sm + G::H_OFF + canon(rr, col, 128)) = pack_bf16(v0, v1);
+                else
+                  *reinterpret_cast<uint32_t *>(dq_img + canon(rr, (kind - 1) * D + col, 3 * D)) = pack_bf16(v0, v1);
+              });
+        }
+      };
+      if (n == 16) units(std::true_type{});
+      else units(std::false_type{});
       fence_proxy_async();
       if (!sync_ok(s, true)) break;
       if (threadIdx.x == 0) {
@@ -816,8 +819,8 @@ struct A2Geo {
   static constexpr int W_OFF = 0;                       // Wqkv rows [D][3D]
   static constexpr int W_BYTES = 3 * D * D * 2;
   static constexpr int XR_OFF = W_OFF + W_BYTES;        // X images as stored [2][128][D] (next tile early)
-  static constexpr int XP_OFF = XR_OFF + 2 * IMG;       // X padded [128][128] (columns >= D zero)
-  static constexpr int DQ_OFF = XP_OFF + kRows * 128 * 2;   // [dQ dK dV] images [2][128][3D]
+  static constexpr int ST_OFF = XR_OFF + 2 * IMG;       // per-configuration mode: flush staging, 2 KB per warp
+  static constexpr int DQ_OFF = ST_OFF + 16 * 2048;     // [dQ dK dV] images [2][128][3D]
   static constexpr int M_OFF = DQ_OFF + 2 * QIMG;       // misc: bars, holder, dE [4][4][D]
   static constexpr int BYTES = M_OFF + 64 + 4 * 4 * 4 * D;
   static constexpr int C_W = 0, C_DX = 256;
@@ -839,22 +842,25 @@ struct A2Args {
   JacOut jac;
 };
 
+// 512 threads: thread (row, quarter) owns a quarter of dX's columns; the next tile's dX' rows are read
+// during this tile.  The weight-gradient MMAs read the stored X image MN-major with M = 128: TMEM lanes
+// >= D then hold sums of unrelated image bytes and are never read.
+constexpr int kA2Threads = 512;
+
 template <int D>
-__global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
+__global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
   using G = A2Geo<D>;
   extern __shared__ __align__(1024) uint8_t sm[];
-  constexpr int HALF = D / 2;
+  constexpr int NQ = kA2Threads / 128, QC = D / NQ;
+  static_assert(QC % 16 == 0, "column groups of 16");
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
   float *dE = reinterpret_cast<float *>(sm + G::M_OFF + 64);   // [4][D], or [4 configurations][4][D]
-  for (int i = threadIdx.x; i < 4 * 4 * D; i += kThreads) dE[i] = 0.f;
-  for (int i = threadIdx.x; i < kRows * 128 * 2 / 16; i += kThreads)
-    reinterpret_cast<uint4 *>(sm + G::XP_OFF)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < 4 * 4 * D; i += kA2Threads) dE[i] = 0.f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+  const int row = 32 * (warp & 3) + lane, quarter = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
-  const uint32_t wq = smem_u32(sm + G::W_OFF), xr0 = smem_u32(sm + G::XR_OFF), xp = smem_u32(sm + G::XP_OFF),
-                 dq0 = smem_u32(sm + G::DQ_OFF);
+  const uint32_t wq = smem_u32(sm + G::W_OFF), xr0 = smem_u32(sm + G::XR_OFF), dq0 = smem_u32(sm + G::DQ_OFF);
   if (threadIdx.x == 0) {
     mbar_expect_tx(s.bar_ld, G::W_BYTES);
     bulk_g2s(wq, a.wqkv, G::W_BYTES, s.bar_ld);
@@ -865,17 +871,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
   if (sync_ok(s, ok)) {
     if ((size_t)blockIdx.x < a.tiles)
       load2(s, xr0, a.x + blockIdx.x * (size_t)G::IMG, G::IMG, dq0, a.dqkv + blockIdx.x * (size_t)G::QIMG, G::QIMG);
+    float4 nx[QC / 4];   // this thread's dX' of the coming tile
+    auto load_nx = [&](size_t t) {
+      const float4 *src = reinterpret_cast<const float4 *>(a.dxm + (t * kRows + row) * (size_t)D + quarter * QC);
+#pragma unroll
+      for (int j = 0; j < QC / 4; ++j) nx[j] = src[j];
+    };
+    if ((size_t)blockIdx.x < a.tiles) load_nx(blockIdx.x);
     int buf = 0;
     for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, buf ^= 1) {
-      const uint32_t dq = dq0 + buf * G::QIMG;
-      const uint8_t *xr_ptr = sm + G::XR_OFF + buf * G::IMG;
-      const size_t rg = (tile * kRows + row) * (size_t)D + half * HALF;
-      float base[HALF];
+      const uint32_t dq = dq0 + buf * G::QIMG, xr = xr0 + buf * G::IMG;
+      const size_t rg = (tile * kRows + row) * (size_t)D + quarter * QC;
+      float base[QC];
 #pragma unroll
-      for (int j = 0; j < HALF; j += 4) {
-        const float4 q = *reinterpret_cast<const float4 *>(a.dxm + rg + j);
+      for (int j = 0; j < QC; j += 4) {
+        const float4 q = nx[j / 4];
         base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
       }
+      if (tile + gridDim.x < a.tiles) load_nx(tile + gridDim.x);
       ok = wait_ld(s);   // this tile's X and [dQ dK dV] images
       if (!sync_ok(s, ok)) break;
       {   // the other buffers were last read by the previous tile's MMAs, which have completed
@@ -884,17 +897,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
           load2(s, xr0 + (buf ^ 1) * G::IMG, a.x + nxt * (size_t)G::IMG, G::IMG, dq0 + (buf ^ 1) * G::QIMG,
                 a.dqkv + nxt * (size_t)G::QIMG, G::QIMG);
       }
-      // X padded to 128 columns: each 8-row group of the stored image (16D bytes) -> first half of 2048
-      for (int i = threadIdx.x; i < kRows / 8 * (D * 16 / 16); i += kThreads) {
-        const int grp = i / (D * 16 / 16), c = i % (D * 16 / 16);
-        reinterpret_cast<uint4 *>(sm + G::XP_OFF + grp * 2048)[c] =
-            reinterpret_cast<const uint4 *>(xr_ptr + grp * D * 16)[c];
-      }
-      fence_proxy_async();
-      if (!sync_ok(s, true)) break;
       if (threadIdx.x == 0) {
         tc_fence_after();
-        if (!a.jac.nvirt) mma_mm(s, xp, 128, dq, 3 * D, 3 * D, G::C_W, !first);   // dWqkv += X^T [dQ dK dV]
+        if (!a.jac.nvirt) mma_mm(s, xr, D, dq, 3 * D, 3 * D, G::C_W, !first);   // dWqkv += X^T [dQ dK dV]
         mma_kk(s, dq, wq, 3 * D, D, G::C_DX, false);            // [dQ dK dV] Wqkv^T
         mma_commit(s.bar_mma);
       }
@@ -907,33 +912,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
             tc_fence_after();
             // columns [D part, D part + D) of the [dQ dK dV] image start (D / 8) MN groups (128 B each) in
             for (int c = 0; c < 4; ++c)
-              mma_mm_rows(s, xp, 128, dq + part * (D / 8) * 128, 3 * D, D, 64 * c, 32 * c, 2);
+              mma_mm_rows(s, xr, D, dq + part * (D / 8) * 128, 3 * D, D, 64 * c, 32 * c, 2);
             mma_commit(s.bar_mma);
           }
           fine = wait_mma(s);
           if (!sync_ok(s, fine)) break;
           const long long off = part == 0 ? a.off_wq : part == 1 ? a.off_wk : a.off_wv;
-          if (a.jac.o16) {   // this tile's stored X image: already copied into the padded one
-            jac_flush_rows<2>(s, a.jac, tile, 0, D, off, D, D, reinterpret_cast<float *>(const_cast<uint8_t *>(xr_ptr)));
+          if (a.jac.o16) {
+            jac_flush_rows<NQ>(s, a.jac, tile, 0, D, off, D, D, reinterpret_cast<float *>(sm + G::ST_OFF));
           } else {
             auto iw = [&](int m, int nn) -> long long { return m < D ? off + (long long)m * D + nn : -1; };
-            jac_flush<decltype(iw), 2>(s, a.jac, tile, 0, D, iw);
+            jac_flush<decltype(iw), NQ>(s, a.jac, tile, 0, D, iw);
           }
           tc_fence_before();
           if (!sync_ok(s, true)) break;
         }
         if (s.bad) break;
       }
-      float out[HALF];
+      float out[QC];
 #pragma unroll
-      for (int j = 0; j < HALF; j += 16) {
+      for (int j = 0; j < QC; j += 16) {
         float v[16];
-        tmem_ld16(s.tmem + lane_addr + G::C_DX + half * HALF + j, v);
+        tmem_ld16(s.tmem + lane_addr + G::C_DX + quarter * QC + j, v);
 #pragma unroll
         for (int e = 0; e < 16; ++e) out[j + e] = base[j + e] + v[e];
       }
 #pragma unroll
-      for (int j = 0; j < HALF; j += 4)
+      for (int j = 0; j < QC; j += 4)
         *reinterpret_cast<float4 *>(a.dxo + rg + j) = make_float4(out[j], out[j + 1], out[j + 2], out[j + 3]);
       if (a.embed_grad && a.jac.nvirt && row < nvalid) {   // VJP mode: k_embed_grad after the launch
         const int sqn = row / n, i = row % n;
@@ -945,17 +950,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
           // one [4][D] block per virtual configuration (sqn >> 1) of the tile
           float *dst = dE + (sqn >> 1) * 4 * D;
 #pragma unroll
-          for (int j = 0; j < HALF; ++j) atomicAdd(&dst[pat * D + half * HALF + j], out[j]);
+          for (int j = 0; j < QC; ++j) atomicAdd(&dst[pat * D + quarter * QC + j], out[j]);
         }
       }
       if (a.jac.nvirt && a.embed_grad) {
         __syncthreads();
-        for (int i = threadIdx.x; i < 4 * 4 * D; i += kThreads) {
+        for (int i = threadIdx.x; i < 4 * 4 * D; i += kA2Threads) {
           const size_t v = tile * 4 + i / (4 * D);
           if (v < a.jac.nvirt) jac_put1(a.jac, v, a.off_e + i % (4 * D), dE[i]);
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < 4 * 4 * D; i += kThreads) dE[i] = 0.f;
+        for (int i = threadIdx.x; i < 4 * 4 * D; i += kA2Threads) dE[i] = 0.f;
       }
       first = false;
       tc_fence_before();
@@ -964,12 +969,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_bwd_attn2(A2Args a) {
   }
   if (!s.bad && !first && !a.jac.nvirt) {
     float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
-    flush_block(s, G::C_W, 3 * D, g, [&](int m, int nn) -> long long {
+    auto iw = [&](int m, int nn) -> long long {
       if (m >= D) return -1;
       if (nn < D) return a.off_wq + (long long)m * D + nn;
       if (nn < 2 * D) return a.off_wk + (long long)m * D + (nn - D);
       return a.off_wv + (long long)m * D + (nn - 2 * D);
-    });
+    };
+    flush_block<decltype(iw), NQ>(s, G::C_W, 3 * D, g, iw);
   }
   sync_finish(s);
 }
@@ -1175,7 +1181,6 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
         ma.b1 = m.L[l].b1 + hb * 128;
         ma.xmid = bf.xmid + (size_t)l * tiles * img;
         ma.dxo = bf.dxa;
-        ma.base = hb == 0 ? bf.dxa : bf.dxb;
         ma.dxm = bf.dxb;
         ma.tiles = tiles;
         ma.do_db2 = hb == 0;
@@ -1231,7 +1236,7 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
     a2.off_e = off_e;
     a2.err = err;
     a2.jac = jo;
-    k_bwd_attn2<D><<<grid, kThreads, A2Geo<D>::BYTES, st>>>(a2);
+    k_bwd_attn2<D><<<grid, kA2Threads, A2Geo<D>::BYTES, st>>>(a2);
     if (l == 0 && !jo.nvirt)
       k_embed_grad<<<(unsigned)(2 * n_sm), 256, 0, st>>>(bf.dxa, sig, sigp, B, n, ts, tiles, gacc, g_stride, off_e);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -19,6 +19,8 @@
 // Every mbarrier wait is bounded; on timeout the kernel sets *err, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "attn_mma.cuh"
 #include "tdo_device.cuh"
 #include "tcgen05.cuh"
@@ -230,13 +232,18 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
       for (int idx = threadIdx.x; idx < (kRows - ts * n) * (D / 8); idx += kThreads)   // padding rows: O = 0
         *reinterpret_cast<uint4 *>(A + canon(ts * n + idx / (D / 8), 8 * (idx % (D / 8)), D)) = make_uint4(0, 0, 0, 0);
       __syncthreads();
-      for (int u = warp; u < ts * heads; u += kThreads / 32) {
-        const int sq = u / heads, h = u % heads, rb = sq * n;
-        amma::attn_fwd_h<HD>(Qh + rb * G::LDH + h * HD, Kh + rb * G::LDH + h * HD, Vt + h * HD * G::LDT + 16 * sq,
-                             G::LDH, G::LDT, n, [&](int r, int cc, float v0, float v1) {
-                               *reinterpret_cast<uint32_t *>(A + canon(rb + r, h * HD + cc, D)) = pack_bf16(v0, v1);
-                             });
-      }
+      auto units = [&](auto full) {
+        for (int u = warp; u < ts * heads; u += kThreads / 32) {
+          const int sq = u / heads, h = u % heads, rb = sq * n;
+          amma::attn_fwd_h<HD, decltype(full)::value>(
+              Qh + rb * G::LDH + h * HD, Kh + rb * G::LDH + h * HD, Vt + h * HD * G::LDT + 16 * sq, G::LDH, G::LDT, n,
+              [&](int r, int cc, float v0, float v1) {
+                *reinterpret_cast<uint32_t *>(A + canon(rb + r, h * HD + cc, D)) = pack_bf16(v0, v1);
+              });
+        }
+      };
+      if (n == 16) units(std::true_type{});
+      else units(std::false_type{});
     } else {
     // K, V (FP32) to shared memory, this thread's column half
 #pragma unroll

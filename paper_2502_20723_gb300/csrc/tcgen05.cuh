@@ -105,6 +105,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16-byte global load issued where it stands: a volatile asm statement keeps its place among the other
+// asm statements (barrier waits, MMA issue), so the compiler does not sink it towards its first use.
+__device__ __forceinline__ float4 ld_pinned_f4(const float *p) {
+  float4 v;
+  asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+
 // Two 16-column loads (addresses ta, tb) completed by one wait.
 __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, float (&va)[16], uint32_t tb, float (&vb)[16]) {
   uint32_t r[32];
