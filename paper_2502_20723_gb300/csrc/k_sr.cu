@@ -125,22 +125,32 @@ __global__ void k_sr_cfin(const double *__restrict__ part, const double *__restr
   if (threadIdx.x == 0) { sc[S_CR] = a; sc[S_CI] = b; }
 }
 
-// Partial dot products of the rows of O with v over one chunk of kChunk parameters: block (chunk, sg)
-// streams the chunk of every sample row of sample group sg (8 KB of FP32 O or 4 KB of BF16 O,
-// contiguous), one warp per row at a time, 16-byte loads per lane when every row starts on a 16-byte
-// boundary, with the chunk of v in shared memory.  part[chunk][s] = sum_{k in chunk} O[s][k] v[k].
-constexpr int kChunk = 1024;
+// Partial dot products of the rows of O with v over one chunk of parameters: block (chunk, sg) streams
+// the chunk of every sample row of sample group sg (8 KB contiguous), one warp per row at a time,
+// 16-byte loads per lane when every row starts on a 16-byte boundary, with the chunk of v in shared
+// memory.  part[chunk][s] = sum_{k in chunk} O[s][k] v[k].
+constexpr int kChunk = 1024;   // the smaller chunk (the most chunks: buffer sizes)
 constexpr int kSampleGroups = 8;
+// Parameters per chunk: 1024 for FP32 pairs, 2048 for BF16 pairs, so that a block reads 8 KB contiguous
+// runs of a row either way (4 KB runs left BF16 passes at 71-83 % of the copy bandwidth); chunk / 4
+// threads per block.
+template <typename OT>
+struct SrChunk {
+  static constexpr int value = sizeof(OT) == 4 ? 2 * kChunk : kChunk;
+};
 
 template <typename OT, bool VEC>
-__global__ void k_sr_tpart(const OT *__restrict__ O, size_t Ns, size_t P, size_t ldo, const float *__restrict__ vf,
-                           double2 *__restrict__ part, const double *__restrict__ sc) {
-  __shared__ float4 vs4[kChunk / 4];
+__global__ void __launch_bounds__(SrChunk<OT>::value / 4) k_sr_tpart(const OT *__restrict__ O, size_t Ns, size_t P,
+                                                                      size_t ldo, const float *__restrict__ vf,
+                                                                      double2 *__restrict__ part,
+                                                                      const double *__restrict__ sc) {
+  constexpr int CH = SrChunk<OT>::value;
+  __shared__ float4 vs4[CH / 4];
   float *vs = reinterpret_cast<float *>(vs4);
   if (sc[S_DONE] != 0.0) return;
-  const size_t k0 = (size_t)blockIdx.x * kChunk;
-  const int kn = (int)((P - k0) < (size_t)kChunk ? (P - k0) : (size_t)kChunk);
-  for (int i = threadIdx.x; i < kChunk; i += blockDim.x) vs[i] = i < kn ? vf[k0 + i] : 0.f;
+  const size_t k0 = (size_t)blockIdx.x * CH;
+  const int kn = (int)((P - k0) < (size_t)CH ? (P - k0) : (size_t)CH);
+  for (int i = threadIdx.x; i < CH; i += blockDim.x) vs[i] = i < kn ? vf[k0 + i] : 0.f;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const size_t per = (Ns + kSampleGroups - 1) / kSampleGroups;
@@ -201,19 +211,20 @@ __global__ void k_sr_tsum(const float2 *__restrict__ t, size_t Ns, double *__res
   if (threadIdx.x == 0) { sc[S_TR] = a; sc[S_TI] = b; }
 }
 
-// Partial products w = Re(O^H t) over one chunk of kChunk parameters and one sample group: block
-// (chunk, sg) streams the chunk (8 KB of FP32 O, 4 KB of BF16 O, contiguous) of every sample row of its
+// Partial products w = Re(O^H t) over one chunk of parameters and one sample group: block
+// (chunk, sg) streams the chunk (8 KB contiguous) of every sample row of its
 // group, each thread owning 4 consecutive parameters (16-byte loads when every row starts on a 16-byte
 // boundary), with the group's t in shared memory.  FP32 runs of kRun rows, FP64 across runs.
 // wpart[sg][k] = sum_{s in group sg} Re(conj(O[s][k]) t[s]).
 constexpr int kWRows = 2048;   // t values of a sample group staged at a time (16 KB)
 template <typename OT, bool VEC>
-__global__ void __launch_bounds__(kSrBlock) k_sr_wpart(const OT *__restrict__ O, size_t Ns, size_t P, size_t ldo,
-                                                       const float2 *__restrict__ t, double *__restrict__ wpart,
-                                                       const double *__restrict__ sc) {
+__global__ void __launch_bounds__(SrChunk<OT>::value / 4) k_sr_wpart(const OT *__restrict__ O, size_t Ns, size_t P,
+                                                                      size_t ldo, const float2 *__restrict__ t,
+                                                                      double *__restrict__ wpart,
+                                                                      const double *__restrict__ sc) {
   __shared__ float2 ts[kWRows];
   if (sc[S_DONE] != 0.0) return;
-  const size_t k = (size_t)blockIdx.x * kChunk + 4 * threadIdx.x;
+  const size_t k = (size_t)blockIdx.x * SrChunk<OT>::value + 4 * threadIdx.x;
   const int kn = k < P ? (int)(P - k < 4 ? P - k : 4) : 0;
   const size_t per = (Ns + kSampleGroups - 1) / kSampleGroups;
   const size_t s_begin = (size_t)blockIdx.y * per;
@@ -446,21 +457,22 @@ static SrPtrs sr_carve(double *work, size_t Ns, size_t P) {
 template <typename OT>
 static void matvec(const OT *O, size_t Ns, size_t P, size_t ldo, const double *v, double shift, SrPtrs &q,
                    int nb, cudaStream_t st) {
-  const int nchunks = (int)((P + kChunk - 1) / kChunk);
+  constexpr int CH = SrChunk<OT>::value, TB = CH / 4;
+  const int nchunks = (int)((P + CH - 1) / CH);
   constexpr size_t align = 16 / sizeof(OT);   // elements per 16 bytes
   k_sr_vprep<<<nb, kSrBlock, 0, st>>>(P, v, q.mean, q.vf, q.part, q.part2, q.sc);
   k_sr_cfin<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
   const bool vec = ldo % align == 0 && reinterpret_cast<uintptr_t>(O) % 16 == 0;   // 16-byte-aligned rows
   if (vec)
-    k_sr_tpart<OT, true><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, ldo, q.vf, q.tpart, q.sc);
+    k_sr_tpart<OT, true><<<dim3(nchunks, kSampleGroups), TB, 0, st>>>(O, Ns, P, ldo, q.vf, q.tpart, q.sc);
   else
-    k_sr_tpart<OT, false><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, ldo, q.vf, q.tpart, q.sc);
+    k_sr_tpart<OT, false><<<dim3(nchunks, kSampleGroups), TB, 0, st>>>(O, Ns, P, ldo, q.vf, q.tpart, q.sc);
   k_sr_tred<<<(unsigned)((Ns + 255) / 256), 256, 0, st>>>(q.tpart, nchunks, Ns, q.t, q.sc);
   k_sr_tsum<<<1, 1024, 0, st>>>(q.t, Ns, q.sc);
   if (vec)
-    k_sr_wpart<OT, true><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, ldo, q.t, q.wpart, q.sc);
+    k_sr_wpart<OT, true><<<dim3(nchunks, kSampleGroups), TB, 0, st>>>(O, Ns, P, ldo, q.t, q.wpart, q.sc);
   else
-    k_sr_wpart<OT, false><<<dim3(nchunks, kSampleGroups), kSrBlock, 0, st>>>(O, Ns, P, ldo, q.t, q.wpart, q.sc);
+    k_sr_wpart<OT, false><<<dim3(nchunks, kSampleGroups), TB, 0, st>>>(O, Ns, P, ldo, q.t, q.wpart, q.sc);
   k_sr_wfin<<<nb, kSrBlock, 0, st>>>(Ns, P, q.mean, q.wpart, v, shift, q.Ap, q.part, q.sc);
 }
 
