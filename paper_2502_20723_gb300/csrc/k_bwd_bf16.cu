@@ -355,8 +355,8 @@ struct MlpGeo {
   static constexpr int G_OFF = DX_OFF + 2 * IMG;       // G  [128][HC]
   static constexpr int DU_OFF = G_OFF + kRows * HC * 2;  // dU [128][HC]
   static constexpr int ONE_OFF = DU_OFF + kRows * HC * 2;  // all-ones [128][16] (row sums by MMA)
-  static constexpr int M_OFF = ONE_OFF + kRows * 16 * 2;    // misc: bars, holder, b1 of the chunk [HC]
-  static constexpr int BYTES = M_OFF + 64 + 4 * HC;
+  static constexpr int M_OFF = ONE_OFF + kRows * 16 * 2;    // misc: bars, holder, b1 of the chunk [HC], Wh [D][2]
+  static constexpr int BYTES = M_OFF + 64 + 4 * HC + 8 * D;
   // TMEM columns (C_B1: db1 = dU^T 1, C_B2: db2 = dX^T 1; every one of their 16 columns holds the same sums)
   static constexpr int C_U = 0, C_DG = 128, C_DX = 256, C_W1 = 320, C_W2 = 384, C_B1 = 448, C_B2 = 464;
   // per-configuration mode: 4 x 16 db1 and 4 x 16 db2 columns (dW1/dW2 blocks in [0, 256))
@@ -369,6 +369,10 @@ struct MlpArgs {
   const uint8_t *xmid;            // [tiles] images
   const float *dxo;               // FP32 [tiles*128][D]: dX at the MLP output
   float *dxm;                     // FP32 out: dX' (first pass: dxo + its part; second pass: += its part)
+  // last layer: dX at the MLP output formed from the head instead of read from dxo (dF non-null):
+  // dX[row][c] = (1/N) sum_o Wh[c][o] dF[seq(row)][o] for valid rows, 0 for padding rows
+  const float *dF, *Wh;
+  int n, ts;
   size_t tiles;
   int do_db2;
   float *g;
@@ -402,7 +406,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   Sync s;
   sync_init(s, sm + G::M_OFF, a.err);
   float *b1s = reinterpret_cast<float *>(sm + G::M_OFF + 64);
+  float *whs = b1s + G::HC;
+  const bool head = a.dF != nullptr;
   for (int i = threadIdx.x; i < G::HC; i += kMlpThreads) b1s[i] = a.b1[i];
+  if (head)
+    for (int i = threadIdx.x; i < 2 * D; i += kMlpThreads) whs[i] = a.Wh[i];
   for (int i = threadIdx.x; i < kRows * 16 / 8; i += kMlpThreads)   // bf16 1.0 = 0x3F80
     reinterpret_cast<uint4 *>(sm + G::ONE_OFF)[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -424,8 +432,29 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   bool first = true;
   const size_t t0 = blockIdx.x, step = gridDim.x;
   if (sync_ok(s, ok) && t0 < a.tiles) {
-    float4 nx[QD / 4];   // this thread's incoming dX of a coming tile
+    // head mode: this row's (dF0, dF1) / N of tile t, zero for padding rows
+    const bool hvalid = head && row < a.ts * a.n;
+    const float inv_n = head ? 1.0f / (float)a.n : 0.f;
+    auto head_f = [&](size_t t) -> float2 {
+      if (!hvalid) return make_float2(0.f, 0.f);
+      const int sq = row / a.n;
+      const float2 f = *reinterpret_cast<const float2 *>(a.dF + 4 * (t * (a.ts / 2) + (sq >> 1)) + 2 * (sq & 1));
+      return make_float2(f.x * inv_n, f.y * inv_n);
+    };
+    auto head_dx = [&](float2 f, float (&v)[QD]) {
+#pragma unroll
+      for (int j = 0; j < QD; ++j) {
+        const float2 w = *reinterpret_cast<const float2 *>(whs + 2 * (cg * QD + j));
+        v[j] = fmaf(w.x, f.x, w.y * f.y);
+      }
+    };
+    float4 nx[QD / 4];   // this thread's incoming dX of a coming tile (head mode: its (dF0, dF1) / N in nx[0])
     auto load_nx = [&](size_t t) {
+      if (head) {
+        const float2 f = head_f(t);
+        nx[0] = make_float4(f.x, f.y, 0.f, 0.f);
+        return;
+      }
       const float4 *src = reinterpret_cast<const float4 *>(a.dxo + (t * kRows + row) * (size_t)D + cg * QD);
 #pragma unroll
       for (int j = 0; j < QD / 4; ++j) nx[j] = src[j];
@@ -433,10 +462,14 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
     // dX image of tile t (BF16, buffer b) from nx
     auto put_dx = [&](int b) {
       float dxo[QD];
+      if (head) {
+        head_dx(make_float2(nx[0].x, nx[0].y), dxo);
+      } else {
 #pragma unroll
-      for (int j = 0; j < QD; j += 4) {
-        const float4 v = nx[j / 4];
-        dxo[j] = v.x; dxo[j + 1] = v.y; dxo[j + 2] = v.z; dxo[j + 3] = v.w;
+        for (int j = 0; j < QD; j += 4) {
+          const float4 v = nx[j / 4];
+          dxo[j] = v.x; dxo[j + 1] = v.y; dxo[j + 2] = v.z; dxo[j + 3] = v.w;
+        }
       }
 #pragma unroll
       for (int j = 0; j < QD; j += 8) st_row8(sm + G::DX_OFF + b * G::IMG, row, cg * QD + j, D, dxo + j);
@@ -510,8 +543,15 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       // VJP mode, the next tile's MMA1
       float4 base[ADD ? 1 : QD / 4];
       if constexpr (!ADD) {
+        if (head) {
+          float v[QD];
+          head_dx(head_f(tile), v);
 #pragma unroll
-        for (int j = 0; j < QD / 4; ++j) base[j] = ld_pinned_f4(a.dxo + rg + 4 * j);
+          for (int j = 0; j < QD / 4; ++j) base[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < QD / 4; ++j) base[j] = ld_pinned_f4(a.dxo + rg + 4 * j);
+        }
       }
       if (has_next) {
         put_dx(buf ^ 1);
@@ -1153,8 +1193,9 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
     HeadArgs h{cot, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, gacc, g_stride, off_wh, off_bh, D, jo};
     const unsigned grid = (unsigned)((Bpad + 255) / 256 < 1024 ? (Bpad + 255) / 256 : 1024);
     k_head_bwd<<<grid ? grid : 1, 256, (2 * D + 2) * sizeof(float), st>>>(h);
-    k_head_dx<<<(unsigned)(tiles * kRows * D / 256 < 65535 * 8 ? (tiles * kRows * D + 255) / 256 : 65535 * 8), 256, 0,
-                st>>>(bf.dF, m.Wh, D, n, ts, tiles, bf.dxa);
+    if (m.ffn == 0)   // with an MLP the last layer's MLP passes form this dX from dF themselves
+      k_head_dx<<<(unsigned)(tiles * kRows * D / 256 < 65535 * 8 ? (tiles * kRows * D + 255) / 256 : 65535 * 8), 256,
+                  0, st>>>(bf.dF, m.Wh, D, n, ts, tiles, bf.dxa);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const int grid = (int)(tiles < (size_t)n_sm ? tiles : (size_t)n_sm);
@@ -1193,6 +1234,11 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
         ma.F = m.ffn;
         ma.err = err;
         ma.jac = jo;
+        const bool last = l == m.layers - 1;
+        ma.dF = last ? bf.dF : nullptr;
+        ma.Wh = last ? m.Wh : nullptr;
+        ma.n = n;
+        ma.ts = ts;
         if (hb == 0) k_bwd_mlp<D, false><<<grid, kMlpThreads, MlpGeo<D>::BYTES, st>>>(ma);
         else k_bwd_mlp<D, true><<<grid, kMlpThreads, MlpGeo<D>::BYTES, st>>>(ma);
       }
