@@ -613,6 +613,23 @@ cudaError_t launch_pack_bf16(const DevModel &m, uint16_t *dst16, DevModelBF16 *v
   return cudaGetLastError();
 }
 
+// CTAs of the forward / sampler resident per SM: two (2 x 256 TMEM columns, 2 x 128 registers x 256
+// threads = the register file, 2 x 110.7 KB of the 228 KB shared memory) unless the kernel's attributes
+// say that one does not fit.  Every CTA runs its own tiles, so a launch of two per SM is correct however
+// many are resident.
+template <typename K>
+static int ctas_per_sm(K kernel, int bytes) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) { cudaGetLastError(); return 1; }
+  int dev = 0, regs = 0, smem = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const long long per_cta_regs = (long long)fa.numRegs * tdo::bf16::kThreads;
+  const long long per_cta_smem = (long long)bytes + (long long)fa.sharedSizeBytes + 1024;
+  return (2 * per_cta_regs <= regs && 2 * per_cta_smem <= smem) ? 2 : 1;
+}
+
 template <int D, int HD>
 static cudaError_t fwd_bf16_impl(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                                  const uint32_t *sigp, size_t B, float2 *out, int *err, int n_sm, cudaStream_t st,
@@ -623,11 +640,7 @@ static cudaError_t fwd_bf16_impl(const DevModel &m, const DevModelBF16 &mb, cons
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fwd_bf16<D, HD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_bf16<D, HD>, kThreads, bytes);
-  if (e != cudaSuccess) return e;
-  if (per_sm > 2) per_sm = 2;   // TMEM: 2 x 256 columns per SM
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = ctas_per_sm(k_fwd_bf16<D, HD>, bytes);
   const int tc = tdo::seqs_per_tile(m.n_sites) / 2;
   const size_t ntiles = (B + tc - 1) / tc;
   size_t grid = (size_t)n_sm * per_sm;
@@ -665,11 +678,7 @@ static cudaError_t sample_bf16_impl(const DevModel &m, const DevModelBF16 &mb, s
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_sample_bf16<D, HD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_bf16<D, HD>, kThreads, bytes);
-  if (e != cudaSuccess) return e;
-  if (per_sm > 2) per_sm = 2;
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = ctas_per_sm(k_sample_bf16<D, HD>, bytes);
   const int tc = tdo::seqs_per_tile(m.n_sites) / 2;
   const size_t ntiles = (n_chains + tc - 1) / tc;
   size_t grid = (size_t)n_sm * per_sm;
