@@ -131,7 +131,7 @@ __device__ __forceinline__ void attn_fwd_bwd(const float *Q, const float *K, con
     l0 += __shfl_xor_sync(0xffffffffu, l0, o);
     l1 += __shfl_xor_sync(0xffffffffu, l1, o);
   }
-  const float i0 = 1.f / l0, i1 = 1.f / l1;
+  const float i0 = tc::rcp_fast(l0), i1 = tc::rcp_fast(l1);
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     s[j][0] *= i0; s[j][1] *= i0;
@@ -260,7 +260,7 @@ __device__ __forceinline__ void attn_fwd_h(const __half *Qh, const __half *Kh, c
     l0 += __shfl_xor_sync(0xffffffffu, l0, o);
     l1 += __shfl_xor_sync(0xffffffffu, l1, o);
   }
-  const float i0 = 1.f / l0, i1 = 1.f / l1;
+  const float i0 = tc::rcp_fast(l0), i1 = tc::rcp_fast(l1);
   const uint32_t pa[4] = {h2(s[0][0] * i0, s[0][1] * i0), h2(s[0][2] * i1, s[0][3] * i1),
                           h2(s[1][0] * i0, s[1][1] * i0), h2(s[1][2] * i1, s[1][3] * i1)};
 #pragma unroll
@@ -393,7 +393,7 @@ __device__ __forceinline__ void attn_fwd_bwd_h(uint32_t Qh, uint32_t Kh, uint32_
     l0 += __shfl_xor_sync(0xffffffffu, l0, o);
     l1 += __shfl_xor_sync(0xffffffffu, l1, o);
   }
-  const float i0 = q0 ? 1.f / l0 : 0.f, i1 = q1 ? 1.f / l1 : 0.f;   // invalid query rows: P = 0
+  const float i0 = q0 ? tc::rcp_fast(l0) : 0.f, i1 = q1 ? tc::rcp_fast(l1) : 0.f;   // invalid query rows: P = 0
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     s[j][0] *= i0; s[j][1] *= i0;

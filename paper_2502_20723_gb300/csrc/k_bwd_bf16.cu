@@ -36,6 +36,8 @@ constexpr int kRows = 128;
 constexpr int kCopiesMax = 16;
 
 // Descriptors. K-major image [rows][K]: LBO 128 B (next 8 k), SBO 16K B (next 8 rows), 256 B per 16 k.
+// The start address sits in the low 14 bits as addr >> 4 and shared addresses stay below 256 KB, so the
+// descriptor of addr + delta is the descriptor of addr plus delta >> 4.
 // The same image read MN-major (the stored K is the MMA's M or N, the rows are the MMA's K):
 // 8-element MN groups 128 B apart, 8-row K groups 16K B apart, 32K B per 16 rows.
 __device__ __forceinline__ uint64_t dk(uint32_t addr, int K) { return sdesc(addr, 128, K * 16); }
@@ -69,15 +71,17 @@ __device__ __forceinline__ bool wait_ld(Sync &s) {
 // K-major x K-major: D[tmem + col] (+)= A[128 x K] B[N x K]^T
 __device__ __forceinline__ void mma_kk(const Sync &s, uint32_t a, uint32_t b, int K, int N, uint32_t col, bool acc) {
   const uint32_t id = idesc_bf16(kRows, N);
+  const uint64_t da = dk(a, K), db = dk(b, K);
   for (int kk = 0; kk < K / 16; ++kk)
-    mma_bf16(s.tmem + col, dk(a + kk * 256, K), dk(b + kk * 256, K), id, (acc || kk > 0) ? 1u : 0u);
+    mma_bf16(s.tmem + col, da + kk * 16, db + kk * 16, id, (acc || kk > 0) ? 1u : 0u);
 }
 // MN-major x MN-major over the 128 rows: D[tmem + col][M = Ka][N = Kb] (+)= A_img^T B_img
 __device__ __forceinline__ void mma_mm(const Sync &s, uint32_t a, int Ka, uint32_t b, int Kb, int N, uint32_t col,
                                        bool acc) {
   const uint32_t id = idesc_bf16_major(kRows, N, 1, 1);
+  const uint64_t da = dmn(a, Ka), db = dmn(b, Kb);
   for (int kk = 0; kk < kRows / 16; ++kk)
-    mma_bf16(s.tmem + col, dmn(a + kk * Ka * 32, Ka), dmn(b + kk * Kb * 32, Kb), id, (acc || kk > 0) ? 1u : 0u);
+    mma_bf16(s.tmem + col, da + kk * Ka * 2, db + kk * Kb * 2, id, (acc || kk > 0) ? 1u : 0u);
 }
 
 __device__ __forceinline__ void sync_init(Sync &s, uint8_t *misc, int *err) {
@@ -191,9 +195,10 @@ __device__ __forceinline__ void jac_put1(const JacOut &j, size_t v, long long k,
 __device__ __forceinline__ void mma_mm_rows(const Sync &s, uint32_t a, int Ka, uint32_t b, int Kb, int N,
                                             uint32_t col, int r0, int nsteps) {
   const uint32_t id = idesc_bf16_major(kRows, N, 1, 1);
+  const uint64_t da = dmn(a, Ka), db = dmn(b, Kb);
   for (int kk = 0; kk < nsteps; ++kk) {
     const int r = r0 / 16 + kk;
-    mma_bf16(s.tmem + col, dmn(a + r * Ka * 32, Ka), dmn(b + r * Kb * 32, Kb), id, kk > 0 ? 1u : 0u);
+    mma_bf16(s.tmem + col, da + r * Ka * 2, db + r * Kb * 2, id, kk > 0 ? 1u : 0u);
   }
 }
 

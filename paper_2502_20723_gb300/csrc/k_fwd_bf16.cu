@@ -81,11 +81,10 @@ __device__ __forceinline__ void gemm(Ctl &c, uint32_t a_addr, uint32_t b_addr, i
   if (c.mma_thread) {
     tc_fence_after();
     const uint32_t id = f16 ? idesc_f16(kRows, N) : idesc_bf16(kRows, N);
-    for (int kk = 0; kk < K / 16; ++kk) {
-      const uint64_t ad = sdesc(a_addr + kk * 256, 128, K * 16);
-      const uint64_t bd = sdesc(b_addr + kk * 256, 128, K * 16);
-      mma_bf16(c.tmem + col, ad, bd, id, (accumulate || kk > 0) ? 1u : 0u);
-    }
+    // descriptor of addr + 256 kk = descriptor of addr + 16 kk (address field addr >> 4, below 256 KB)
+    const uint64_t ad = sdesc(a_addr, 128, K * 16), bd = sdesc(b_addr, 128, K * 16);
+    for (int kk = 0; kk < K / 16; ++kk)
+      mma_bf16(c.tmem + col, ad + 16 * kk, bd + 16 * kk, id, (accumulate || kk > 0) ? 1u : 0u);
     mma_commit(c.bar_mma);
   }
 }
@@ -172,8 +171,12 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
       const uint32_t w2 = (s & 1) ? cfg_s[cfg] : cfg_p[cfg];
       pat = embed_pattern(m.embed, w1, w2, i, n);
     }
+    const float4 *e4 = reinterpret_cast<const float4 *>(m.etab + pat * D + half * DH);
 #pragma unroll
-    for (int j = 0; j < DH; ++j) X[j] = valid ? __ldg(m.etab + pat * D + half * DH + j) : 0.f;
+    for (int j = 0; j < DH; j += 4) {
+      const float4 q = valid ? __ldg(e4 + j / 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      X[j] = q.x; X[j + 1] = q.y; X[j + 2] = q.z; X[j + 3] = q.w;
+    }
   }
   stage_w(c, w_addr, mb.Wqkv[0], 3 * D * D * 2);
 #pragma unroll
@@ -364,12 +367,19 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
         if (ch + 1 < nch) stage_w(c, w_addr, mb.W1[l] + (size_t)(ch + 1) * G::HC * D, G::HC * D * 2);
         else if (l + 1 < m.layers) stage_w(c, w_addr, mb.Wqkv[l + 1], 3 * D * D * 2);
       }
+      const float4 *b2 = reinterpret_cast<const float4 *>(m.L[l].b2 + half * DH);
 #pragma unroll
       for (int j = 0; j < DH; j += 16) {
         float v[16];
         tmem_ld16(c.tmem + lane_addr + G::HC + half * DH + j, v);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) X[j + e] += v[e] + __ldg(m.L[l].b2 + half * DH + j + e);
+        for (int e = 0; e < 16; e += 4) {
+          const float4 bq = __ldg(b2 + (j + e) / 4);
+          X[j + e] += v[e] + bq.x;
+          X[j + e + 1] += v[e + 1] + bq.y;
+          X[j + e + 2] += v[e + 2] + bq.z;
+          X[j + e + 3] += v[e + 3] + bq.w;
+        }
       }
 #pragma unroll
       for (int j = 0; j < DH; j += 8) st_row8(A, row, half * DH + j, D, X + j);
