@@ -31,7 +31,6 @@ namespace bwdtc {
 
 using namespace tdo::tc;
 
-constexpr int kThreads = 256;
 constexpr int kRows = 128;
 constexpr int kCopiesMax = 16;
 
@@ -717,7 +716,7 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
     const int arr = i / (16 * LDH / 8), k = i % (16 * LDH / 8);
     reinterpret_cast<uint4 *>(Fh + arr * G::HROWS * LDH + kRows * LDH)[k] = make_uint4(0, 0, 0, 0);
   }
-  const int n = a.n, heads = a.heads, nvalid = a.ts * n;
+  const int n = a.n, nvalid = a.ts * n;
   const bool valid = row < nvalid;
   const float qscale = rsqrtf((float)HD) * 1.4426950408889634f;   // scores in base 2
   const float scale = rsqrtf((float)HD);
@@ -796,8 +795,9 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
         *reinterpret_cast<uint4 *>(dq_img + canon(r, 8 * c8, 3 * D)) = make_uint4(0, 0, 0, 0);
       }
       auto units = [&](auto full) {
-        for (int u = warp; u < a.ts * heads; u += kA1Threads / 32) {
-          const int sq = u / heads, h = u % heads, rb = sq * n;
+        constexpr int H = D / HD;   // heads (d_model = heads x head dimension)
+        for (int u = warp; u < a.ts * H; u += kA1Threads / 32) {
+          const int sq = u / H, h = u % H, rb = sq * (decltype(full)::value ? 16 : n);
           const uint32_t off = (uint32_t)(rb * LDH + h * HD) * 2;
           amma::attn_fwd_bwd_h<HD, decltype(full)::value>(
               f16 + off, f16 + G::F_BYTES + off, f16 + 2 * G::F_BYTES + off, f16 + 3 * G::F_BYTES + off, LDH, n,

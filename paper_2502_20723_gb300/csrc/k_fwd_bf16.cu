@@ -236,8 +236,9 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
         *reinterpret_cast<uint4 *>(A + canon(ts * n + idx / (D / 8), 8 * (idx % (D / 8)), D)) = make_uint4(0, 0, 0, 0);
       __syncthreads();
       auto units = [&](auto full) {
-        for (int u = warp; u < ts * heads; u += kThreads / 32) {
-          const int sq = u / heads, h = u % heads, rb = sq * n;
+        constexpr int H = D / HD;   // heads (d_model = heads x head dimension)
+        for (int u = warp; u < ts * H; u += kThreads / 32) {
+          const int sq = u / H, h = u % H, rb = sq * (decltype(full)::value ? 16 : n);
           amma::attn_fwd_h<HD, decltype(full)::value>(
               Qh + rb * G::LDH + h * HD, Kh + rb * G::LDH + h * HD, Vt + h * HD * G::LDT + 16 * sq, G::LDH, G::LDT, n,
               [&](int r, int cc, float v0, float v1) {
