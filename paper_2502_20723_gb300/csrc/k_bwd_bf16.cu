@@ -282,6 +282,55 @@ struct HeadArgs {
   JacOut jac;
 };
 
+// dF of one configuration: (Re, Im) cotangent times the symmetrisation's weights of both orders.
+__device__ __forceinline__ float4 head_df(const HeadArgs &a, size_t b) {
+  float2 pw, pv;
+  symmetrise(a.F[4 * b], a.F[4 * b + 1], a.F[4 * b + 2], a.F[4 * b + 3], &pw, &pv);
+  const float2 c = a.cot[b];
+  const float cwr = c.x * pw.x - c.y * pw.y, cwi = c.x * pw.y + c.y * pw.x;
+  const float cvr = c.x * pv.x - c.y * pv.y, cvi = c.x * pv.y + c.y * pv.x;
+  return make_float4(cwr, -cwi, cvr, cvi);
+}
+
+// VJP mode (D = 64): one warp per configuration at a time, lane k owns features k and k + 32 of dWh in
+// registers (coalesced reads of the pooled vectors, no shared-memory atomics in the loop); one block
+// reduction and one set of global atomics per block at the end.
+__global__ void __launch_bounds__(256) k_head_bwd_vjp(HeadArgs a) {
+  __shared__ float red[8][130];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float w0[2] = {0.f, 0.f}, w1[2] = {0.f, 0.f}, bb0 = 0.f, bb1 = 0.f;
+  for (size_t b = blockIdx.x * (size_t)8 + warp; b < a.Bpad; b += gridDim.x * (size_t)8) {
+    float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (b < a.B) {
+      d = head_df(a, b);
+      const float *hA = a.H + (2 * b) * 64, *hB = hA + 64;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float xa = hA[lane + 32 * h], xb = hB[lane + 32 * h];
+        w0[h] = fmaf(xa, d.x, fmaf(xb, d.z, w0[h]));
+        w1[h] = fmaf(xa, d.y, fmaf(xb, d.w, w1[h]));
+      }
+      bb0 += d.x + d.z;
+      bb1 += d.y + d.w;
+    }
+    if (lane == 0) reinterpret_cast<float4 *>(a.dF)[b] = d;
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    red[warp][2 * (lane + 32 * h)] = w0[h];
+    red[warp][2 * (lane + 32 * h) + 1] = w1[h];
+  }
+  if (lane == 0) { red[warp][128] = bb0; red[warp][129] = bb1; }
+  __syncthreads();
+  float *g = a.g + (size_t)(blockIdx.x % kCopiesMax) * a.g_stride;
+  for (int i = threadIdx.x; i < 130; i += blockDim.x) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += red[w][i];
+    atomicAdd(g + (i < 128 ? a.off_wh + i : a.off_bh + (i - 128)), v);
+  }
+}
+
 __global__ void k_head_bwd(HeadArgs a) {
   extern __shared__ float acc[];   // [2D + 2]
   const int nacc = 2 * a.D + 2;
@@ -1111,23 +1160,36 @@ __global__ void __launch_bounds__(256) k_embed_grad(const float *__restrict__ dX
   float4 acc[4];
 #pragma unroll
   for (int p = 0; p < 4; ++p) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const size_t rows = tiles * kRows;
-  for (size_t r = (size_t)blockIdx.x * SLOTS + slot; r < rows; r += (size_t)gridDim.x * SLOTS) {
-    const int rt = (int)(r % kRows);
-    if (rt >= nvalid) continue;
-    const int sq = rt / n, i = rt % n;
-    const size_t b = (r / kRows) * tc + (sq >> 1);
-    if (b >= B) continue;
-    const uint32_t w1 = (sq & 1) ? sigp[b] : sig[b];
-    const uint32_t w2 = (sq & 1) ? sig[b] : sigp[b];
-    const int pat = embed_pattern(0, w1, w2, i, n);
-    const float4 v = __ldcs(reinterpret_cast<const float4 *>(dX + r * D) + cg);
+  const size_t rows = tiles * kRows, stride = (size_t)gridDim.x * SLOTS;
+  // UNR rows per thread and iteration, all loads first: enough bytes in flight to stream dX
+  constexpr int UNR = 4;
+  for (size_t r0 = (size_t)blockIdx.x * SLOTS + slot; r0 < rows; r0 += UNR * stride) {
+    float4 v[UNR];
+    int pat[UNR];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const float m = p == pat ? 1.f : 0.f;
-      acc[p].x = fmaf(m, v.x, acc[p].x); acc[p].y = fmaf(m, v.y, acc[p].y);
-      acc[p].z = fmaf(m, v.z, acc[p].z); acc[p].w = fmaf(m, v.w, acc[p].w);
+    for (int u = 0; u < UNR; ++u) {
+      const size_t r = r0 + u * stride;
+      pat[u] = -1;
+      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r >= rows) continue;
+      const int rt = (int)(r % kRows);
+      if (rt >= nvalid) continue;
+      const int sq = rt / n, i = rt % n;
+      const size_t b = (r / kRows) * tc + (sq >> 1);
+      if (b >= B) continue;
+      const uint32_t w1 = (sq & 1) ? sigp[b] : sig[b];
+      const uint32_t w2 = (sq & 1) ? sig[b] : sigp[b];
+      pat[u] = embed_pattern(0, w1, w2, i, n);
+      v[u] = __ldcs(reinterpret_cast<const float4 *>(dX + r * D) + cg);
     }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const float m = p == pat[u] ? 1.f : 0.f;
+        acc[p].x = fmaf(m, v[u].x, acc[p].x); acc[p].y = fmaf(m, v[u].y, acc[p].y);
+        acc[p].z = fmaf(m, v[u].z, acc[p].z); acc[p].w = fmaf(m, v[u].w, acc[p].w);
+      }
   }
 #pragma unroll
   for (int p = 0; p < 4; ++p) red[slot][p][cg] = acc[p];
@@ -1196,8 +1258,13 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
   cudaError_t e;
   {
     HeadArgs h{cot, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, gacc, g_stride, off_wh, off_bh, D, jo};
-    const unsigned grid = (unsigned)((Bpad + 255) / 256 < 1024 ? (Bpad + 255) / 256 : 1024);
-    k_head_bwd<<<grid ? grid : 1, 256, (2 * D + 2) * sizeof(float), st>>>(h);
+    if (jac) {
+      const unsigned grid = (unsigned)((Bpad + 255) / 256 < 1024 ? (Bpad + 255) / 256 : 1024);
+      k_head_bwd<<<grid ? grid : 1, 256, (2 * D + 2) * sizeof(float), st>>>(h);
+    } else {
+      const unsigned grid = (unsigned)((Bpad + 7) / 8 < (size_t)4 * n_sm ? (Bpad + 7) / 8 : (size_t)4 * n_sm);
+      k_head_bwd_vjp<<<grid ? grid : 1, 256, 0, st>>>(h);
+    }
     if (m.ffn == 0)   // with an MLP the last layer's MLP passes form this dX from dF themselves
       k_head_dx<<<(unsigned)(tiles * kRows * D / 256 < 65535 * 8 ? (tiles * kRows * D + 255) / 256 : 65535 * 8), 256,
                   0, st>>>(bf.dF, m.Wh, D, n, ts, tiles, bf.dxa);
