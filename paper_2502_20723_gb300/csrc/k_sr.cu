@@ -58,46 +58,6 @@ __device__ __forceinline__ double sum_parts(const double *part, int n, double *s
   return block_sum_d(a, sh);
 }
 
-// mean[k] = (1/Ns) sum_s O[s][k] and the Jacobi preconditioner diag[k] = (1/Ns) sum_s |O[s][k]|^2 -
-// |mean[k]|^2 + shift (the variance of O_k floored at 0; 1 where that sum is 0), in one pass over O: thread per k, 4
-// independent loads in flight, FP32 runs of kRun samples accumulated in FP64.  The preconditioner only
-// sets the CG's convergence rate, so the one-pass variance formula is accurate enough for it.
-template <typename OT>
-__global__ void k_sr_moments(const OT *__restrict__ O, size_t Ns, size_t P, size_t ldo, double shift,
-                             double2 *__restrict__ mean, double *__restrict__ diag) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
-    double ar = 0.0, ai = 0.0, aa = 0.0;
-    for (size_t s0 = 0; s0 < Ns; s0 += kRun) {
-      const size_t s1 = s0 + kRun < Ns ? s0 + kRun : Ns;
-      float fr[4] = {0, 0, 0, 0}, fi[4] = {0, 0, 0, 0}, fa[4] = {0, 0, 0, 0};
-      size_t s = s0;
-      for (; s + 4 <= s1; s += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float2 o = cplx(__ldg(O + (s + u) * ldo + k));
-          fr[u] += o.x;
-          fi[u] += o.y;
-          fa[u] = fmaf(o.x, o.x, fmaf(o.y, o.y, fa[u]));
-        }
-      }
-      for (; s < s1; ++s) {
-        const float2 o = cplx(__ldg(O + s * ldo + k));
-        fr[0] += o.x;
-        fi[0] += o.y;
-        fa[0] = fmaf(o.x, o.x, fmaf(o.y, o.y, fa[0]));
-      }
-      ar += (double)((fr[0] + fr[1]) + (fr[2] + fr[3]));
-      ai += (double)((fi[0] + fi[1]) + (fi[2] + fi[3]));
-      aa += (double)((fa[0] + fa[1]) + (fa[2] + fa[3]));
-    }
-    const double mr = ar / (double)Ns, mi = ai / (double)Ns;
-    mean[k] = make_double2(mr, mi);
-    const double var = aa / (double)Ns - (mr * mr + mi * mi);
-    const double dk = (var > 0.0 ? var : 0.0) + shift;
-    diag[k] = dk > 0.0 ? dk : 1.0;   // a constant O_k with no shift: leave that coordinate unscaled
-  }
-}
-
 // vf = (float) v; block partials of mean . v (re, im)
 __global__ void k_sr_vprep(size_t P, const double *__restrict__ v, const double2 *__restrict__ mean,
                            float *__restrict__ vf, double *__restrict__ part, double *__restrict__ part2,
@@ -294,6 +254,104 @@ __global__ void __launch_bounds__(SrChunk<OT>::value / 4) k_sr_wpart(const OT *_
   for (int e = 0; e < kn; ++e) wpart[(size_t)blockIdx.y * P + k + e] = w[e];
 }
 
+// Moments of O in one pass, with the w-pass's access shape (a block owns one chunk of parameters, 8 KB
+// contiguous per row, of one of kSampleGroups sample groups; each thread 4 consecutive parameters):
+// mpart[q][sg][k] = sum over group sg of Re O[s][k] (q = 0), Im O[s][k] (q = 1), |O[s][k]|^2 (q = 2), in
+// FP32 runs of kRun samples accumulated in FP64.
+template <typename OT, bool VEC>
+__global__ void __launch_bounds__(SrChunk<OT>::value / 4) k_sr_mpart(const OT *__restrict__ O, size_t Ns, size_t P,
+                                                                      size_t ldo, double *__restrict__ mpart) {
+  const size_t k = (size_t)blockIdx.x * SrChunk<OT>::value + 4 * threadIdx.x;
+  const int kn = k < P ? (int)(P - k < 4 ? P - k : 4) : 0;
+  if (kn == 0) return;
+  const size_t per = (Ns + kSampleGroups - 1) / kSampleGroups;
+  const size_t s_begin = (size_t)blockIdx.y * per;
+  const size_t s_end = s_begin + per < Ns ? s_begin + per : Ns;
+  double ar[4] = {0.0, 0.0, 0.0, 0.0}, ai[4] = {0.0, 0.0, 0.0, 0.0}, aa[4] = {0.0, 0.0, 0.0, 0.0};
+  auto acc = [](float2 o, float &fr, float &fi, float &fa) {
+    fr += o.x;
+    fi += o.y;
+    fa = fmaf(o.x, o.x, fmaf(o.y, o.y, fa));
+  };
+  for (size_t r0 = s_begin; r0 < s_end; r0 += kRun) {
+    const size_t r1 = r0 + kRun < s_end ? r0 + kRun : s_end;
+    float fr[4] = {0.f, 0.f, 0.f, 0.f}, fi[4] = {0.f, 0.f, 0.f, 0.f}, fa[4] = {0.f, 0.f, 0.f, 0.f};
+    size_t r = r0;
+    if (VEC && kn == 4) {
+      if constexpr (sizeof(OT) == 4) {   // BF16 pairs: 8 rows (8 x 16 bytes) in flight per thread
+        for (; r + 8 <= r1; r += 8) {
+          uint4 q[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) q[u] = __ldcs(reinterpret_cast<const uint4 *>(O + (r + u) * ldo + k));
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            acc(cplx(q[u].x), fr[0], fi[0], fa[0]);
+            acc(cplx(q[u].y), fr[1], fi[1], fa[1]);
+            acc(cplx(q[u].z), fr[2], fi[2], fa[2]);
+            acc(cplx(q[u].w), fr[3], fi[3], fa[3]);
+          }
+        }
+      }
+      for (; r + 4 <= r1; r += 4) {
+        float2 c[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) load4(O + (r + u) * ldo + k, c[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc(c[u][e], fr[e], fi[e], fa[e]);
+      }
+      for (; r < r1; ++r) {
+        float2 c[4];
+        load4(O + r * ldo + k, c);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc(c[e], fr[e], fi[e], fa[e]);
+      }
+    } else {
+      for (; r < r1; ++r) {
+        const OT *row = O + r * ldo + k;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (e < kn) acc(cplx(__ldcs(row + e)), fr[e], fi[e], fa[e]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ar[e] += (double)fr[e];
+      ai[e] += (double)fi[e];
+      aa[e] += (double)fa[e];
+    }
+  }
+  const size_t g = (size_t)blockIdx.y * P;
+  for (int e = 0; e < kn; ++e) {
+    mpart[g + k + e] = ar[e];
+    mpart[(size_t)kSampleGroups * P + g + k + e] = ai[e];
+    mpart[2 * (size_t)kSampleGroups * P + g + k + e] = aa[e];
+  }
+}
+
+// mean[k] = (1/Ns) sum_s O[s][k] and the Jacobi preconditioner diag[k] = (1/Ns) sum_s |O[s][k]|^2 -
+// |mean[k]|^2 + shift (the variance of O_k floored at 0; 1 where that sum is 0), from the group sums.
+// The preconditioner only sets the CG's convergence rate, so the one-pass variance formula is accurate
+// enough for it.
+__global__ void k_sr_mfin(size_t Ns, size_t P, double shift, const double *__restrict__ mpart,
+                          double2 *__restrict__ mean, double *__restrict__ diag) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
+    double ar = 0.0, ai = 0.0, aa = 0.0;
+#pragma unroll
+    for (int g = 0; g < kSampleGroups; ++g) {
+      ar += mpart[(size_t)g * P + k];
+      ai += mpart[(size_t)(kSampleGroups + g) * P + k];
+      aa += mpart[(size_t)(2 * kSampleGroups + g) * P + k];
+    }
+    const double mr = ar / (double)Ns, mi = ai / (double)Ns;
+    mean[k] = make_double2(mr, mi);
+    const double var = aa / (double)Ns - (mr * mr + mi * mi);
+    const double dk = (var > 0.0 ? var : 0.0) + shift;
+    diag[k] = dk > 0.0 ? dk : 1.0;   // a constant O_k with no shift: leave that coordinate unscaled
+  }
+}
+
 // Ap[k] = (1/Ns) [sum_sg wpart[sg][k] - Re(conj(mean[k]) T)] + shift p[k]; partials of p . Ap.
 __global__ void k_sr_wfin(size_t Ns, size_t P, const double2 *__restrict__ mean, const double *__restrict__ wpart,
                           const double *__restrict__ p, double shift, double *__restrict__ Ap,
@@ -427,6 +485,7 @@ struct SrPtrs {
   float2 *t;
   double2 *tpart;
   double *wpart;
+  double *mpart;   // [3][kSampleGroups][P] group sums of the moments pass
 };
 
 // Carves the workspace; every region starts on a 16-byte boundary (double2 / float2 / float4 access).
@@ -449,10 +508,10 @@ static SrPtrs sr_carve(double *work, size_t Ns, size_t P) {
   q.t = reinterpret_cast<float2 *>(take(8 * Ns));
   q.tpart = reinterpret_cast<double2 *>(take(16 * ((P + kChunk - 1) / kChunk) * Ns));
   q.wpart = reinterpret_cast<double *>(take(8 * kSampleGroups * P));
+  q.mpart = reinterpret_cast<double *>(take(3 * 8 * kSampleGroups * P));
   return q;
 }
 
-// S' v -> Ap (and the partials of v . Ap in q.part), all on the device.
 // S' v -> Ap (and the partials of v . Ap in q.part), all on the device: 7 launches, O streamed twice.
 template <typename OT>
 static void matvec(const OT *O, size_t Ns, size_t P, size_t ldo, const double *v, double shift, SrPtrs &q,
@@ -482,7 +541,8 @@ size_t sr_work_doubles(size_t Ns, size_t P) {
   // the regions carved by sr_carve, each rounded up to 16 bytes, plus slack
   const size_t nchunks = (P + tdo::kChunk - 1) / tdo::kChunk;
   const size_t bytes = 16 * P + 5 * (8 * P + 16) + 3 * 8 * 1024 + 8 * 32 + (4 * P + 16) + (8 * Ns + 16) +
-                       16 * nchunks * Ns + 16 + 8 * tdo::kSampleGroups * P + 16 + 64;
+                       16 * nchunks * Ns + 16 + 8 * tdo::kSampleGroups * P + 16 + 3 * 8 * tdo::kSampleGroups * P + 16 +
+                       64;
   return (bytes + 7) / 8;
 }
 
@@ -511,9 +571,18 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const 
     }
     return cudaSuccess;
   };
-  k_sr_moments<OT><<<nb, kSrBlock, 0, st>>>(O2, Ns, P, ldo, shift, q.mean, q.diag);
+  {
+    constexpr int CH = SrChunk<OT>::value;
+    const int nchunks = (int)((P + CH - 1) / CH);
+    const bool vec = ldo % (16 / sizeof(OT)) == 0 && reinterpret_cast<uintptr_t>(O2) % 16 == 0;
+    if (vec)
+      k_sr_mpart<OT, true><<<dim3(nchunks, kSampleGroups), CH / 4, 0, st>>>(O2, Ns, P, ldo, q.mpart);
+    else
+      k_sr_mpart<OT, false><<<dim3(nchunks, kSampleGroups), CH / 4, 0, st>>>(O2, Ns, P, ldo, q.mpart);
+    k_sr_mfin<<<nb, kSrBlock, 0, st>>>(Ns, P, shift, q.mpart, q.mean, q.diag);
+  }
   k_sr_clear<<<1, 32, 0, st>>>(q.sc);
-  nl += 2;
+  nl += 3;
   cudaError_t e;
   if (x0 && (e = mv(x0)) != cudaSuccess) return e;
   k_sr_init<<<nb, kSrBlock, 0, st>>>(P, rhs, x0, q.Ap, x, q.r, q.z, q.p, q.diag, q.part, q.part2, q.part3);
