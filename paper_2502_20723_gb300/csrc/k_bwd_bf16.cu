@@ -7,15 +7,18 @@
 // outputs.  The backward then runs sub-layer by sub-layer over all tiles, so that the weight
 // gradients of one sub-layer stay in tensor memory for all the tiles a CTA processes and leave it once
 // per CTA (float atomics into 16 accumulator copies), instead of once per tile:
-//   head:      k_head_bwd (dF, dWh, dbh), k_head_dx (dX at the last layer output, FP32 per row)
+//   head:      k_head_bwd (dF, dWh, dbh); the dX at the last layer output, (1/N) Wh dF per row, is formed
+//              inside that layer's MLP passes (k_head_dx writes it out only for models without an MLP)
 //   per layer: k_bwd_mlp  x2 (one pass per 128-wide half of the hidden layer):
 //                U = Xmid W1, dG = dX W2^T (MMA), dU = dG gelu'(U) (CUDA cores),
-//                dX' = dX + dU W1^T, dW1^T += dU^T Xmid, dW2 += G^T dX (MMA, MN-major operands)
+//                dX' = dX + dU W1^T, dW1^T += dU^T Xmid, dW2 += G^T dX, db1 += dU^T 1, db2 += dX^T 1
+//                (MMA, MN-major operands); the second pass adds its dX' part onto the first's output
 //              k_bwd_attn1: QKV = X Wqkv, dH = dX' Wo^T (MMA); softmax attention forward and backward
 //                per (sequence, head) by warp-level MMAs on FP16 copies -> dQ, dK, dV (BF16 images);
 //                dWo += H^T dX'  (sequences of at most 16 tokens)
-//              k_bwd_attn2: dWqkv += X^T [dQ dK dV], dX = dX' + [dQ dK dV] Wqkv^T (MMA); embedding
-//                gradient at the first layer
+//              k_bwd_attn2: dWqkv += X^T [dQ dK dV], dX = dX' + [dQ dK dV] Wqkv^T (MMA)
+//   then:      k_embed_grad, the token-embedding gradient from dX at the first layer's input (in the
+//              per-configuration mode attention pass 2 of the first layer sums it per configuration)
 // Weight-gradient MMAs read the row-major activation images as MN-major operands: M or N = the
 // image's feature dimension, K = the 128 rows of the tile.
 #include <cuda_bf16.h>
