@@ -212,17 +212,28 @@ __device__ __forceinline__ void jac_flush(const Sync &s, const JacOut &j, size_t
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = 32 * (warp & 3) + lane, cg = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
-  for (int pr = 0; pr < 2; ++pr) {   // sample tile * 2 + pr: configurations 2 pr (seed 0) and 2 pr + 1
-    const size_t v0 = tile * 4 + 2 * pr;
-    for (int jj = 0; jj < N / NQ; jj += 16) {
+  for (int jj = 0; jj < N / NQ; jj += 16) {
+    // the reference values of this thread's 16 columns, shared by both samples of the tile
+    float2 rf[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const long long k = idx(m, cg * (N / NQ) + jj + e);
+      rf[e] = (j.o16 && k >= 0) ? j.oref[k] : make_float2(0.f, 0.f);
+    }
+    for (int pr = 0; pr < 2; ++pr) {   // sample tile * 2 + pr: configurations 2 pr (seed 0) and 2 pr + 1
+      const size_t v0 = tile * 4 + 2 * pr;
       float re[16], im[16];
-      tmem_ld16(s.tmem + lane_addr + col0 + (2 * pr) * N + cg * (N / NQ) + jj, re);
-      tmem_ld16(s.tmem + lane_addr + col0 + (2 * pr + 1) * N + cg * (N / NQ) + jj, im);
+      tmem_ld16x2(s.tmem + lane_addr + col0 + (2 * pr) * N + cg * (N / NQ) + jj, re,
+                  s.tmem + lane_addr + col0 + (2 * pr + 1) * N + cg * (N / NQ) + jj, im);
       if (v0 + 1 < j.nvirt) {
+        const size_t b = v0 >> 1;
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const long long k = idx(m, cg * (N / NQ) + jj + e);
-          if (k >= 0) jac_put2(j, v0 >> 1, k, re[e], im[e]);
+          if (k < 0) continue;
+          const size_t i = b * j.ldo + (size_t)k;
+          if (j.o16) reinterpret_cast<uint32_t *>(j.o16)[i] = pack_bf16(re[e] - rf[e].x, im[e] - rf[e].y);
+          else reinterpret_cast<float2 *>(j.o32)[i] = make_float2(re[e], im[e]);
         }
       }
     }
@@ -240,14 +251,24 @@ __device__ __noinline__ void jac_flush_rows(const Sync &s, const JacOut &j, size
   const int cg = warp >> 2, mb = 32 * (warp & 3);
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
   float2 *st = reinterpret_cast<float2 *>(stage) + warp * 256;   // [32 rows][8 columns]
-  for (int pr = 0; pr < 2; ++pr) {
-    const size_t v0 = tile * 4 + 2 * pr;
-    const bool ok = v0 + 1 < j.nvirt;
-    const size_t b = v0 >> 1;
-    for (int jj = 0; jj < N / NQ; jj += 16) {
+  for (int jj = 0; jj < N / NQ; jj += 16) {
+    // reference values of the 16 elements this lane writes back, shared by both samples of the tile
+    float2 rf[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int m = mb + 4 * it + (lane >> 3);
+        rf[h][it] = m < mlim ? j.oref[off + (long long)m * ld + cg * (N / NQ) + jj + 8 * h + (lane & 7)]
+                             : make_float2(0.f, 0.f);
+      }
+    for (int pr = 0; pr < 2; ++pr) {
+      const size_t v0 = tile * 4 + 2 * pr;
+      const bool ok = v0 + 1 < j.nvirt;
+      const size_t b = v0 >> 1;
       float re[16], im[16];
-      tmem_ld16(s.tmem + lane_addr + col0 + (2 * pr) * N + cg * (N / NQ) + jj, re);
-      tmem_ld16(s.tmem + lane_addr + col0 + (2 * pr + 1) * N + cg * (N / NQ) + jj, im);
+      tmem_ld16x2(s.tmem + lane_addr + col0 + (2 * pr) * N + cg * (N / NQ) + jj, re,
+                  s.tmem + lane_addr + col0 + (2 * pr + 1) * N + cg * (N / NQ) + jj, im);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
 #pragma unroll
@@ -259,8 +280,9 @@ __device__ __noinline__ void jac_flush_rows(const Sync &s, const JacOut &j, size
             const int r = 4 * it + (lane >> 3), c = lane & 7, m = mb + r;
             if (m < mlim) {
               const long long k = off + (long long)m * ld + cg * (N / NQ) + jj + 8 * h + c;
-              const float2 v = st[r * 8 + c], rf = j.oref[k];
-              reinterpret_cast<uint32_t *>(j.o16)[b * j.ldo + (size_t)k] = pack_bf16(v.x - rf.x, v.y - rf.y);
+              const float2 v = st[r * 8 + c];
+              reinterpret_cast<uint32_t *>(j.o16)[b * j.ldo + (size_t)k] =
+                  pack_bf16(v.x - rf[h][it].x, v.y - rf[h][it].y);
             }
           }
         }
@@ -1002,37 +1024,45 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
       }
       ok = wait_mma(s);
       if (!sync_ok(s, ok)) break;
-      if (a.jac.nvirt) {   // dWq, dWk, dWv per configuration, one 4 x D column block at a time
-        bool fine = true;
-        for (int part = 0; part < 3 && fine; ++part) {
-          if (threadIdx.x == 0) {
-            tc_fence_after();
-            // columns [D part, D part + D) of the [dQ dK dV] image start (D / 8) MN groups (128 B each) in
-            for (int c = 0; c < 4; ++c)
-              mma_mm_rows(s, xr, D, dq + part * (D / 8) * 128, 3 * D, D, 64 * c, 32 * c, 2);
-            mma_commit(s.bar_mma);
-          }
-          fine = wait_mma(s);
-          if (!sync_ok(s, fine)) break;
-          const long long off = part == 0 ? a.off_wq : part == 1 ? a.off_wk : a.off_wv;
-          if (a.jac.o16) {
-            jac_flush_rows<NQ>(s, a.jac, tile, 0, D, off, D, D, reinterpret_cast<float *>(sm + G::ST_OFF));
-          } else {
-            auto iw = [&](int m, int nn) -> long long { return m < D ? off + (long long)m * D + nn : -1; };
-            jac_flush<decltype(iw), NQ>(s, a.jac, tile, 0, D, iw);
-          }
-          tc_fence_before();
-          if (!sync_ok(s, true)) break;
-        }
-        if (s.bad) break;
-      }
-      float out[QC];
+      float out[QC];   // dX = dX' + [dQ dK dV] Wqkv^T, read out first (its TMEM columns are reused below)
 #pragma unroll
       for (int j = 0; j < QC; j += 16) {
         float v[16];
         tmem_ld16(s.tmem + lane_addr + G::C_DX + quarter * QC + j, v);
 #pragma unroll
         for (int e = 0; e < 16; ++e) out[j + e] = base[j + e] + v[e];
+      }
+      if (a.jac.nvirt) {   // dWq, dWk, dWv per configuration: 4 x D column blocks, alternately at TMEM
+                           // columns 0 and 256, the next part's MMAs running under this part's flush
+        tc_fence_before();
+        if (!sync_ok(s, true)) break;
+        auto issue_part = [&](int part) {
+          if (threadIdx.x == 0) {
+            tc_fence_after();
+            // columns [D part, D part + D) of the [dQ dK dV] image start (D / 8) MN groups (128 B each) in
+            for (int c = 0; c < 4; ++c)
+              mma_mm_rows(s, xr, D, dq + part * (D / 8) * 128, 3 * D, D, 256 * (part & 1) + 64 * c, 32 * c, 2);
+            mma_commit(s.bar_mma);
+          }
+        };
+        issue_part(0);
+        bool fine = true;
+        for (int part = 0; part < 3 && fine; ++part) {
+          fine = wait_mma(s);
+          if (!sync_ok(s, fine)) break;
+          if (part + 1 < 3) issue_part(part + 1);   // into the other column half, free since part - 1's flush
+          const long long off = part == 0 ? a.off_wq : part == 1 ? a.off_wk : a.off_wv;
+          const uint32_t col0 = 256 * (part & 1);
+          if (a.jac.o16) {
+            jac_flush_rows<NQ>(s, a.jac, tile, col0, D, off, D, D, reinterpret_cast<float *>(sm + G::ST_OFF));
+          } else {
+            auto iw = [&](int m, int nn) -> long long { return m < D ? off + (long long)m * D + nn : -1; };
+            jac_flush<decltype(iw), NQ>(s, a.jac, tile, col0, D, iw);
+          }
+          tc_fence_before();
+          if (!sync_ok(s, true)) break;
+        }
+        if (s.bad) break;
       }
 #pragma unroll
       for (int j = 0; j < QC; j += 4)
