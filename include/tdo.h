@@ -144,6 +144,36 @@ tdo_status tdo_sample(tdo_ctx *ctx, size_t n_chains, size_t n_sweeps, uint64_t s
                       uint32_t *sig, uint32_t *sigp, uint32_t *samples_sig, uint32_t *samples_sigp,
                       uint64_t *accepted);
 
+/* Metropolis-Hastings on the diagonal of rho, P(alpha) proportional to |rho(alpha, alpha)| (supplement,
+ * "Mixed-State Observables"; the sampler of the local estimator below).  Chains alpha [n_chains] in/out
+ * (bit i = site i).  Same random stream as tdo_sample with N choices per draw: proposal t of chain c
+ * takes Philox4x32-10(key = (seed lo, seed hi), counter = (c, t lo, t hi, 0)) -> (x0, x1, ...), flips
+ * site k = ((x0 >> 8) * N) >> 24 of alpha (in both entries of the pair (alpha, alpha)), u = (x1 >> 8) 2^-24,
+ * and accepts iff u < exp(min(0, Re(log rho(alpha', alpha') - log rho(alpha, alpha)))).  A sweep is N
+ * proposals: t = counter .. counter + n_sweeps*N - 1.  samples [sweep][n_chains] (may be NULL) get the
+ * states after each sweep; accepted (may be NULL) the number of accepted moves. */
+tdo_status tdo_sample_diag(tdo_ctx *ctx, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
+                           uint32_t *alpha, uint32_t *samples, uint64_t *accepted);
+
+/* Site-averaged magnetisations <sigma^a> = Tr(rho A) / Tr(rho), A = (1/N) sum_i sigma^a_i (supplement,
+ * "Mixed-State Observables") from Ns samples alpha of |rho(alpha, alpha)| (tdo_sample_diag):
+ * local estimator A~(alpha) = sum_beta rho(alpha, beta) / rho(alpha, alpha) <beta|A|alpha> over beta =
+ * alpha and its N single flips (<alpha ^ e_i|sigma^x_i|alpha> = 1, <alpha ^ e_i|sigma^y_i|alpha> =
+ * i (1 - 2 alpha_i), <alpha|sigma^z_i|alpha> = 1 - 2 alpha_i; bit 0 = |0>), reweighted by the sign s of
+ * rho(alpha, alpha) (the ansatz does not force it positive): <A> = sum s A~ / sum s.
+ * mag[3] = (<sigma^x>, <sigma^y>, <sigma^z>) (real parts); sign_mean (may be NULL) = mean of s;
+ * local (may be NULL) = [Ns][4] complex doubles (s, A~x, A~y, A~z), each as (re, im).
+ * TDO_EINVAL when the signs sum to zero. */
+tdo_status tdo_magnetisation(tdo_ctx *ctx, const uint32_t *alpha, size_t Ns, double *mag, double *sign_mean,
+                             double *local);
+
+/* Purity Tr(rho^2) / Tr(rho)^2 from Ns samples (sigma, sigma') of |rho|^2 (tdo_sample):
+ * Tr(rho)^2 / Tr(rho^2) = E[rho(sigma, sigma) rho(sigma', sigma') / |rho(sigma, sigma')|^2], estimated by
+ * the sample mean m; purity = 1 / m, stderr_ (may be NULL) its standard error by the delta method.
+ * TDO_EINVAL when m <= 0. */
+tdo_status tdo_purity(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t Ns, double *purity,
+                      double *stderr_);
+
 /* Cost gradient for real parameters from Ns samples (derivative of Eq. lossnetk):
  * grad_k = 2 Re (1/Ns) sum_x [ conj(L_loc(x)) sum_y Lhat_xy (rho_y/rho_x) O_k(y) - Cost O_k(x) ],
  * grad FP64 [P] (overwritten); cost (may be NULL) = mean |L_loc|^2; O (may be NULL) receives the

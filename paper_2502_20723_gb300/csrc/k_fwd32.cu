@@ -34,6 +34,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd32(DevModel m, const uint32_t *
 
 // Each CTA owns tiles of ts/2 chains and runs every proposal of those chains: draw (bit, u), evaluate
 // the proposed configurations as one tile, accept iff u < exp(min(0, 2 Re(log rho' - log rho))).
+// diag: chains on |rho(alpha, alpha)| (sig = sigp = alpha): N proposals per sweep, each flipping one site
+// in both entries, accepted iff u < exp(min(0, Re(log rho' - log rho))).
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_sample32(DevModel m, size_t n_chains, size_t n_sweeps,
                                                         uint64_t seed, uint64_t counter,
@@ -41,7 +43,7 @@ __global__ void __launch_bounds__(kThreads) k_sample32(DevModel m, size_t n_chai
                                                         uint32_t *__restrict__ sigp,
                                                         uint32_t *__restrict__ ssig,
                                                         uint32_t *__restrict__ ssigp,
-                                                        unsigned long long *accepted) {
+                                                        unsigned long long *accepted, int diag) {
   extern __shared__ float4 smem4[];
   float *sm = reinterpret_cast<float *>(smem4);
   using G = F32Geom<D>;
@@ -62,15 +64,18 @@ __global__ void __launch_bounds__(kThreads) k_sample32(DevModel m, size_t n_chai
     __syncthreads();
     eval_tile_f32<D>(m, sm, ts);
     if (threadIdx.x < tc) lcur = res[threadIdx.x].x;
+    const int per = diag ? n : 2 * n;   // proposals per sweep
     for (size_t sw = 0; sw < n_sweeps; ++sw) {
-      for (int j = 0; j < 2 * n; ++j) {
-        const uint64_t t = counter + (uint64_t)sw * (uint64_t)(2 * n) + (uint64_t)j;
+      for (int j = 0; j < per; ++j) {
+        const uint64_t t = counter + (uint64_t)sw * (uint64_t)per + (uint64_t)j;
         if (threadIdx.x < tc) {
           int bit;
-          metropolis_draw(seed, (uint32_t)c, t, n, &bit, &u);
+          metropolis_draw(seed, (uint32_t)c, t, per, &bit, &u);
           ps = cs;
           pp = cp;
-          if (bit < n) ps ^= 1u << bit; else pp ^= 1u << (bit - n);
+          if (diag) { ps ^= 1u << bit; pp ^= 1u << bit; }
+          else if (bit < n) ps ^= 1u << bit;
+          else pp ^= 1u << (bit - n);
           csig[threadIdx.x] = ps;
           csigp[threadIdx.x] = pp;
         }
@@ -78,7 +83,7 @@ __global__ void __launch_bounds__(kThreads) k_sample32(DevModel m, size_t n_chai
         eval_tile_f32<D>(m, sm, ts);
         if (threadIdx.x < tc) {
           const float lnew = res[threadIdx.x].x;
-          const float d = 2.0f * (lnew - lcur);
+          const float d = (diag ? 1.0f : 2.0f) * (lnew - lcur);
           if (u < expf(fminf(0.0f, d))) {
             cs = ps; cp = pp; lcur = lnew;
             if (mine) ++acc_count;
@@ -118,7 +123,8 @@ static cudaError_t fwd_impl(const DevModel &m, const uint32_t *sig, const uint32
 template <int D>
 static cudaError_t sample_impl(const DevModel &m, size_t n_chains, size_t n_sweeps, uint64_t seed,
                                uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
-                               uint32_t *ssigp, unsigned long long *accepted, int n_sm, cudaStream_t st) {
+                               uint32_t *ssigp, unsigned long long *accepted, int diag, int n_sm,
+                               cudaStream_t st) {
   const size_t bytes = F32Geom<D>::BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_sample32<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
@@ -130,7 +136,7 @@ static cudaError_t sample_impl(const DevModel &m, size_t n_chains, size_t n_swee
   size_t grid = (size_t)n_sm * (per_sm > 0 ? per_sm : 1);
   if (grid > ntiles) grid = ntiles;
   k_sample32<D><<<(unsigned)grid, kThreads, bytes, st>>>(m, n_chains, n_sweeps, seed, counter, sig, sigp,
-                                                         ssig, ssigp, accepted);
+                                                         ssig, ssigp, accepted, diag);
   return cudaGetLastError();
 }
 
@@ -149,12 +155,12 @@ cudaError_t launch_fwd32(const DevModel &m, const uint32_t *sig, const uint32_t 
 
 cudaError_t launch_sample32(const DevModel &m, size_t n_chains, size_t n_sweeps, uint64_t seed,
                             uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
-                            uint32_t *ssigp, unsigned long long *accepted, int n_sm, cudaStream_t st) {
+                            uint32_t *ssigp, unsigned long long *accepted, int diag, int n_sm, cudaStream_t st) {
   if (n_chains == 0) return cudaSuccess;
   switch (m.d) {
-    case 16: return tdo::sample_impl<16>(m, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted, n_sm, st);
-    case 32: return tdo::sample_impl<32>(m, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted, n_sm, st);
-    case 64: return tdo::sample_impl<64>(m, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted, n_sm, st);
+    case 16: return tdo::sample_impl<16>(m, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted, diag, n_sm, st);
+    case 32: return tdo::sample_impl<32>(m, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted, diag, n_sm, st);
+    case 64: return tdo::sample_impl<64>(m, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted, diag, n_sm, st);
     default: return cudaErrorInvalidValue;
   }
 }

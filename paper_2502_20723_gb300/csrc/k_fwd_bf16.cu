@@ -495,12 +495,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_bf16(DevModel m, DevModelBF
   ctl_finish(c);
 }
 
-// Metropolis chains on the BF16 forward (same proposal stream and acceptance rule as the FP32 sampler).
+// Metropolis chains on the BF16 forward (same proposal stream and acceptance rule as the FP32 sampler,
+// including its diagonal mode).
 template <int D, int HD>
 __global__ void __launch_bounds__(kThreads, 2)
     k_sample_bf16(DevModel m, DevModelBF16 mb, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
                   uint32_t *__restrict__ sig, uint32_t *__restrict__ sigp, uint32_t *__restrict__ ssig,
-                  uint32_t *__restrict__ ssigp, unsigned long long *accepted, int *err) {
+                  uint32_t *__restrict__ ssigp, unsigned long long *accepted, int *err, int diag) {
   extern __shared__ __align__(1024) uint8_t sm[];
   using G = Geo<D>;
   Ctl c;
@@ -523,15 +524,18 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (!eval_tile<D, HD>(m, mb, sm, c, ts, cs, cp, res)) break;
     if (threadIdx.x < tc) lcur = res[threadIdx.x].x;
     bool stop = false;
+    const int per = diag ? n : 2 * n;   // proposals per sweep
     for (size_t sw = 0; sw < n_sweeps && !stop; ++sw) {
-      for (int j = 0; j < 2 * n; ++j) {
-        const uint64_t t = counter + (uint64_t)sw * (uint64_t)(2 * n) + (uint64_t)j;
+      for (int j = 0; j < per; ++j) {
+        const uint64_t t = counter + (uint64_t)sw * (uint64_t)per + (uint64_t)j;
         if (threadIdx.x < tc) {
           int bit;
-          metropolis_draw(seed, (uint32_t)ch, t, n, &bit, &u);
+          metropolis_draw(seed, (uint32_t)ch, t, per, &bit, &u);
           p0 = s0;
           p1 = s1;
-          if (bit < n) p0 ^= 1u << bit; else p1 ^= 1u << (bit - n);
+          if (diag) { p0 ^= 1u << bit; p1 ^= 1u << bit; }
+          else if (bit < n) p0 ^= 1u << bit;
+          else p1 ^= 1u << (bit - n);
           cs[threadIdx.x] = p0;
           cp[threadIdx.x] = p1;
         }
@@ -539,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (!eval_tile<D, HD>(m, mb, sm, c, ts, cs, cp, res)) { stop = true; break; }
         if (threadIdx.x < tc) {
           const float lnew = res[threadIdx.x].x;
-          if (u < expf(fminf(0.0f, 2.0f * (lnew - lcur)))) {
+          if (u < expf(fminf(0.0f, (diag ? 1.0f : 2.0f) * (lnew - lcur)))) {
             s0 = p0; s1 = p1; lcur = lnew;
             if (mine) ++acc_count;
           }
@@ -681,7 +685,7 @@ cudaError_t launch_fwd_bf16(const DevModel &m, const DevModelBF16 &mb, const uin
 template <int D, int HD>
 static cudaError_t sample_bf16_impl(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
                                     uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
-                                    uint32_t *ssigp, unsigned long long *accepted, int *err, int n_sm,
+                                    uint32_t *ssigp, unsigned long long *accepted, int *err, int diag, int n_sm,
                                     cudaStream_t st) {
   using namespace tdo::bf16;
   const int bytes = Geo<D>::BYTES;
@@ -695,19 +699,19 @@ static cudaError_t sample_bf16_impl(const DevModel &m, const DevModelBF16 &mb, s
   size_t grid = (size_t)n_sm * per_sm;
   if (grid > ntiles) grid = ntiles;
   k_sample_bf16<D, HD><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp,
-                                                               ssig, ssigp, accepted, err);
+                                                               ssig, ssigp, accepted, err, diag);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sample_bf16(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
                                uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
-                               uint32_t *ssigp, unsigned long long *accepted, int *err_flag, int n_sm,
+                               uint32_t *ssigp, unsigned long long *accepted, int *err_flag, int diag, int n_sm,
                                cudaStream_t st) {
   if (n_chains == 0) return cudaSuccess;
 #define TDO_SAMPLE_BF16(DD, HH)                                                                                   \
   if (m.d == DD && m.dh == HH)                                                                                     \
     return sample_bf16_impl<DD, HH>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted,     \
-                                    err_flag, n_sm, st);
+                                    err_flag, diag, n_sm, st);
   TDO_SAMPLE_BF16(64, 8)
   TDO_SAMPLE_BF16(64, 16)
   TDO_SAMPLE_BF16(32, 8)

@@ -23,11 +23,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // Proposal of Metropolis step t of chain c: which of the 2N bits to flip, and the uniform u.
-__device__ __forceinline__ void metropolis_draw(uint64_t seed, uint32_t chain, uint64_t t, int n,
+// choices = 2N for the |rho|^2 chains (bit k < N flips sigma_k, else sigma'_{k-N}), N for the chains on
+// the diagonal |rho(alpha, alpha)| (bit k flips site k of alpha).
+__device__ __forceinline__ void metropolis_draw(uint64_t seed, uint32_t chain, uint64_t t, int choices,
                                                 int *bit, float *u) {
   const uint4 x = philox4x32_10(make_uint4(chain, (uint32_t)t, (uint32_t)(t >> 32), 0u),
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-  *bit = (int)(((uint64_t)(x.x >> 8) * (uint64_t)(2 * n)) >> 24);
+  *bit = (int)(((uint64_t)(x.x >> 8) * (uint64_t)choices) >> 24);
   *u = (float)(x.y >> 8) * (1.0f / 16777216.0f);
 }
 

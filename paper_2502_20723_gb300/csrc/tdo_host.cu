@@ -120,6 +120,7 @@ struct tdo_ctx {
   DBuf dtab;   // conv embedding: per-pattern table gradients
   DBuf oref, oref_scratch;   // BF16-stored O for SR: per-parameter shift and its FP32 sample
   DBuf jac_vs, jac_vp, jac_vc, jac_lr;   // tensor-core log-derivatives: virtual configurations
+  DBuf obs_rs, obs_rp, obs_lr, obs_part, obs_out, obs_local;   // observables and purity
   DevModel dm{};
   DevModelBF16 dmb{};
   bool tc_bwd = false;                 // tensor-core gradient (BF16 contexts whose shape it supports)
@@ -536,7 +537,8 @@ extern "C" tdo_status tdo_destroy(tdo_ctx *c) {
                   &c->l2, &c->stats, &c->nonfinite, &c->cot, &c->gacc, &c->scratch, &c->grad, &c->Obuf,
                   &c->srwork, &c->delta, &c->acc_u64, &c->wbf16, &c->errflag, &c->wbwd, &c->act_x, &c->act_xmid,
                   &c->act_h, &c->act_f, &c->act_dF, &c->act_dxa, &c->act_dxb, &c->act_dqkv, &c->dtab,
-                  &c->oref, &c->oref_scratch, &c->jac_vs, &c->jac_vp, &c->jac_vc, &c->jac_lr};
+                  &c->oref, &c->oref_scratch, &c->jac_vs, &c->jac_vp, &c->jac_vc, &c->jac_lr, &c->obs_rs,
+                  &c->obs_rp, &c->obs_lr, &c->obs_part, &c->obs_out, &c->obs_local};
   for (DBuf *b : bufs) b->release();
   for (auto &r : c->trec) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : c->epool) cudaEventDestroy(e);
@@ -1058,9 +1060,9 @@ extern "C" tdo_status tdo_sr_step(tdo_ctx *c, const uint32_t *sig, const uint32_
   return TDO_OK;
 }
 
-extern "C" tdo_status tdo_sample(tdo_ctx *c, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
-                                 uint32_t *sig, uint32_t *sigp, uint32_t *samples_sig, uint32_t *samples_sigp,
-                                 uint64_t *accepted) {
+static tdo_status sample_impl(tdo_ctx *c, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
+                              uint32_t *sig, uint32_t *sigp, uint32_t *samples_sig, uint32_t *samples_sigp,
+                              uint64_t *accepted, int diag) {
   if (!c) return TDO_EINVAL;
   if (n_chains == 0) return TDO_OK;
   if (!sig || !sigp) return fail(c, TDO_EINVAL, "NULL buffer");
@@ -1082,10 +1084,10 @@ extern "C" tdo_status tdo_sample(tdo_ctx *c, size_t n_chains, size_t n_sweeps, u
   Timed tm(c, G_SAMPLE);
   if (c->model.precision == TDO_BF16)
     CU(c, launch_sample_bf16(c->dm, c->dmb, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
-                             c->acc_u64.as<unsigned long long>(), c->errflag.as<int>(), c->n_sm, c->stream));
+                             c->acc_u64.as<unsigned long long>(), c->errflag.as<int>(), diag, c->n_sm, c->stream));
   else
     CU(c, launch_sample32(c->dm, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
-                          c->acc_u64.as<unsigned long long>(), c->n_sm, c->stream));
+                          c->acc_u64.as<unsigned long long>(), diag, c->n_sm, c->stream));
   tm.done(1);
   if (hs) CU(c, cudaMemcpyAsync(sig, dsig, 4 * n_chains, cudaMemcpyDeviceToHost, c->stream));
   if (hp) CU(c, cudaMemcpyAsync(sigp, dsigp, 4 * n_chains, cudaMemcpyDeviceToHost, c->stream));
@@ -1104,6 +1106,87 @@ extern "C" tdo_status tdo_sample(tdo_ctx *c, size_t n_chains, size_t n_sweeps, u
   if (hs || hp || hss || hsp || accepted) {
     CU(c, cudaStreamSynchronize(c->stream));
     TRY(check_err_flag(c));
+  }
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_sample(tdo_ctx *c, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
+                                 uint32_t *sig, uint32_t *sigp, uint32_t *samples_sig, uint32_t *samples_sigp,
+                                 uint64_t *accepted) {
+  return sample_impl(c, n_chains, n_sweeps, seed, counter, sig, sigp, samples_sig, samples_sigp, accepted, 0);
+}
+
+// The chain state alpha serves as both words of the pair (the kernels flip the same site in both).
+extern "C" tdo_status tdo_sample_diag(tdo_ctx *c, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
+                                      uint32_t *alpha, uint32_t *samples, uint64_t *accepted) {
+  return sample_impl(c, n_chains, n_sweeps, seed, counter, alpha, alpha, samples, samples, accepted, 1);
+}
+
+extern "C" tdo_status tdo_magnetisation(tdo_ctx *c, const uint32_t *alpha, size_t Ns, double *mag,
+                                        double *sign_mean, double *local) {
+  if (!c) return TDO_EINVAL;
+  if (Ns == 0) return fail(c, TDO_EINVAL, "no samples");
+  if (!alpha || !mag) return fail(c, TDO_EINVAL, "NULL buffer");
+  const int n = c->n;
+  const size_t rows = Ns * (size_t)(n + 1);
+  const void *da;
+  bool h1;
+  TRY(stage_in(c, 0, alpha, 4 * Ns, &da, &h1));
+  CU(c, c->obs_rs.ensure(4 * rows));
+  CU(c, c->obs_rp.ensure(4 * rows));
+  CU(c, c->obs_lr.ensure(8 * rows));
+  CU(c, c->obs_part.ensure(8 * 7 * 256));
+  CU(c, c->obs_out.ensure(8 * 8));
+  double *dlocal = nullptr;
+  if (local) {
+    if (is_device_ptr(local)) dlocal = local;
+    else { CU(c, c->obs_local.ensure(8 * 8 * Ns)); dlocal = c->obs_local.as<double>(); }
+  }
+  CU(c, launch_obs_rows((const uint32_t *)da, Ns, n, c->obs_rs.as<uint32_t>(), c->obs_rp.as<uint32_t>(), c->stream));
+  TRY(forward_dev(c, c->obs_rs.as<uint32_t>(), c->obs_rp.as<uint32_t>(), rows, c->obs_lr.as<float2>()));
+  CU(c, launch_obs_reduce((const uint32_t *)da, Ns, n, c->obs_lr.as<float2>(), dlocal, c->obs_part.as<double>(),
+                          c->obs_out.as<double>(), c->stream));
+  double h[7];
+  CU(c, cudaMemcpyAsync(h, c->obs_out.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  if (local && dlocal != local) CU(c, cudaMemcpyAsync(local, dlocal, 8 * 8 * Ns, cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  TRY(check_err_flag(c));
+  if (h[0] == 0.0) return fail(c, TDO_EINVAL, "the sample signs sum to zero");
+  mag[0] = h[1] / h[0];
+  mag[1] = h[3] / h[0];
+  mag[2] = h[5] / h[0];
+  if (sign_mean) *sign_mean = h[0] / (double)Ns;
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_purity(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t Ns, double *purity,
+                                 double *stderr_) {
+  if (!c) return TDO_EINVAL;
+  if (Ns == 0) return fail(c, TDO_EINVAL, "no samples");
+  if (!sig || !sigp || !purity) return fail(c, TDO_EINVAL, "NULL buffer");
+  const void *ds, *dp;
+  bool h1, h2;
+  TRY(stage_in(c, 0, sig, 4 * Ns, &ds, &h1));
+  TRY(stage_in(c, 1, sigp, 4 * Ns, &dp, &h2));
+  CU(c, c->obs_rs.ensure(4 * 3 * Ns));
+  CU(c, c->obs_rp.ensure(4 * 3 * Ns));
+  CU(c, c->obs_lr.ensure(8 * 3 * Ns));
+  CU(c, c->obs_part.ensure(8 * 7 * 256));
+  CU(c, c->obs_out.ensure(8 * 8));
+  CU(c, launch_pur_rows((const uint32_t *)ds, (const uint32_t *)dp, Ns, c->obs_rs.as<uint32_t>(),
+                        c->obs_rp.as<uint32_t>(), c->stream));
+  TRY(forward_dev(c, c->obs_rs.as<uint32_t>(), c->obs_rp.as<uint32_t>(), 3 * Ns, c->obs_lr.as<float2>()));
+  CU(c, launch_pur_reduce(c->obs_lr.as<float2>(), Ns, c->obs_part.as<double>(), c->obs_out.as<double>(), c->stream));
+  double h[2];
+  CU(c, cudaMemcpyAsync(h, c->obs_out.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  TRY(check_err_flag(c));
+  const double mean = h[0] / (double)Ns;
+  if (!(mean > 0.0)) return fail(c, TDO_EINVAL, "non-positive estimate of Tr(rho)^2 / Tr(rho^2)");
+  *purity = 1.0 / mean;
+  if (stderr_) {   // delta method: se(1/m) = se(m) / m^2
+    const double var = Ns > 1 ? (h[1] / (double)Ns - mean * mean) * (double)Ns / (double)(Ns - 1) : 0.0;
+    *stderr_ = sqrt(var > 0.0 ? var / (double)Ns : 0.0) / (mean * mean);
   }
   return TDO_OK;
 }

@@ -52,10 +52,11 @@ struct ConnPattern {
 // FP32 forward over explicit configurations.
 cudaError_t launch_fwd32(const DevModel &m, const uint32_t *sig, const uint32_t *sigp, size_t B,
                          float2 *logrho, int n_sm, cudaStream_t st);
-// Metropolis on FP32 forward: n_chains chains in/out, samples optional, accepted counter (device u64).
+// Metropolis on FP32 forward: n_chains chains in/out, samples optional, accepted counter (device u64);
+// diag != 0: chains on |rho(alpha, alpha)| (sig = sigp = alpha, N proposals per sweep).
 cudaError_t launch_sample32(const DevModel &m, size_t n_chains, size_t n_sweeps, uint64_t seed,
                             uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
-                            uint32_t *ssigp, unsigned long long *accepted, int n_sm, cudaStream_t st);
+                            uint32_t *ssigp, unsigned long long *accepted, int diag, int n_sm, cudaStream_t st);
 // BF16 tensor-core forward.
 cudaError_t launch_fwd_bf16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                             const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
@@ -64,7 +65,20 @@ bool bf16_supported(const DevModel &m);
 cudaError_t launch_sample_bf16(const DevModel &m, const DevModelBF16 &mb, size_t n_chains,
                                size_t n_sweeps, uint64_t seed, uint64_t counter, uint32_t *sig,
                                uint32_t *sigp, uint32_t *ssig, uint32_t *ssigp,
-                               unsigned long long *accepted, int *err_flag, int n_sm, cudaStream_t st);
+                               unsigned long long *accepted, int *err_flag, int diag, int n_sm, cudaStream_t st);
+
+// Mixed-state observables.  Rows of the magnetisation estimator: sample s -> (alpha, alpha), then
+// (alpha, alpha ^ e_i) for i < N, at rows s (N + 1) + j.
+cudaError_t launch_obs_rows(const uint32_t *alpha, size_t Ns, int n, uint32_t *rs, uint32_t *rp, cudaStream_t st);
+// From log rho of those rows: local[s] = (s, A~x, A~y, A~z) as complex pairs (may be NULL), and
+// out[0..6] = sum s, Re/Im sum s A~x, s A~y, s A~z (FP64, fixed order; part: nb = 256 blocks x 7 doubles).
+cudaError_t launch_obs_reduce(const uint32_t *alpha, size_t Ns, int n, const float2 *lr, double *local,
+                              double *part, double *out, cudaStream_t st);
+// Rows of the purity estimator: sample s -> (sigma, sigma'), (sigma, sigma), (sigma', sigma') at 3 s + j.
+cudaError_t launch_pur_rows(const uint32_t *sig, const uint32_t *sigp, size_t Ns, uint32_t *rs, uint32_t *rp,
+                            cudaStream_t st);
+// out[0] = sum_s Re rho(s,s) rho(s',s') / |rho(s,s')|^2, out[1] = sum of squares (FP64, fixed order).
+cudaError_t launch_pur_reduce(const float2 *lr, size_t Ns, double *part, double *out, cudaStream_t st);
 
 // Connections: count[s], entries [s*M + j].
 cudaError_t launch_connections(const ConnPattern *pat, int n_pat, const ConnContrib *con,

@@ -22,7 +22,8 @@ STATUS = {0: "TDO_OK", -1: "TDO_EINVAL", -2: "TDO_ENOMEM", -3: "TDO_ECUDA", -4: 
 EXPORTS = ["tdo_model_num_params", "tdo_create", "tdo_destroy", "tdo_num_params", "tdo_max_connections",
            "tdo_set_params", "tdo_get_params", "tdo_log_rho", "tdo_log_rho_vjp", "tdo_jacobian",
            "tdo_connections", "tdo_local_estimator", "tdo_local_estimator_noalloc", "tdo_sample", "tdo_grad", "tdo_sr_solve", "tdo_set_sr_options", "tdo_sr_step",
-           "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_last_error"]
+           "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_last_error", "tdo_sample_diag", "tdo_magnetisation",
+           "tdo_purity"]
 
 
 class TdoError(RuntimeError):
@@ -73,6 +74,9 @@ def lib() -> C.CDLL:
         L.tdo_local_estimator.argtypes = [vp, vp, vp, sz, vp, dp, dp]
         L.tdo_local_estimator_noalloc.argtypes = [vp, vp, vp, sz, vp, dp, dp]
         L.tdo_sample.argtypes = [vp, sz, sz, u64, u64, vp, vp, vp, vp, C.POINTER(u64)]
+        L.tdo_sample_diag.argtypes = [vp, sz, sz, u64, u64, vp, vp, C.POINTER(u64)]
+        L.tdo_magnetisation.argtypes = [vp, vp, sz, vp, dp, vp]
+        L.tdo_purity.argtypes = [vp, vp, vp, sz, dp, dp]
         L.tdo_grad.argtypes = [vp, vp, vp, sz, vp, dp, vp]
         L.tdo_sr_solve.argtypes = [vp, vp, sz, vp, C.c_double, C.c_double, i32, vp, C.POINTER(i32), dp]
         L.tdo_sr_step.argtypes = [vp, vp, vp, sz, C.c_double, C.c_double, dp]
@@ -239,6 +243,30 @@ class Context:
         self._chk(lib().tdo_sample(self.h, nc, n_sweeps, seed, counter, _ptr(sig), _ptr(sigp), _ptr(ss), _ptr(sp),
                                    C.byref(acc)))
         return acc.value, ((ss, sp) if samples else None)
+
+    def sample_diag(self, alpha, n_sweeps: int, seed: int, counter: int, samples=False):
+        """Metropolis sweeps on |rho(alpha, alpha)| in place on the chains alpha; returns (accepted, samples
+        [n_sweeps][chains] or None)."""
+        nc = len(alpha)
+        ss = self._like(alpha, (n_sweeps, nc), np.uint32) if samples else None
+        acc = C.c_uint64()
+        self._chk(lib().tdo_sample_diag(self.h, nc, n_sweeps, seed, counter, _ptr(alpha), _ptr(ss), C.byref(acc)))
+        return acc.value, ss
+
+    def magnetisation(self, alpha, local: bool = False):
+        """(<sigma^x>, <sigma^y>, <sigma^z>) from samples alpha of |rho(alpha, alpha)|; returns (mag [3],
+        mean sign, per-sample (s, A~x, A~y, A~z) as complex [Ns, 4] or None)."""
+        mag = np.zeros(3)
+        sm = C.c_double()
+        loc = np.zeros((len(alpha), 8)) if local else None
+        self._chk(lib().tdo_magnetisation(self.h, _ptr(alpha), len(alpha), mag.ctypes.data, C.byref(sm), _ptr(loc)))
+        return mag, sm.value, (loc.view(np.complex128) if local else None)
+
+    def purity(self, sig, sigp):
+        """Tr(rho^2) / Tr(rho)^2 from samples of |rho|^2; returns (purity, standard error)."""
+        pu, se = C.c_double(), C.c_double()
+        self._chk(lib().tdo_purity(self.h, _ptr(sig), _ptr(sigp), len(sig), C.byref(pu), C.byref(se)))
+        return pu.value, se.value
 
     def grad(self, sig, sigp, grad=None, O=None):
         Ns = len(sig)
