@@ -199,6 +199,28 @@ tdo_status tdo_set_sr_options(tdo_ctx *ctx, double tol, int max_iter);
 tdo_status tdo_sr_step(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t Ns, double lr,
                        double diag_shift, double *cost);
 
+/* Learning-rate and SR-shift schedules (supplement, "Learning Rate Scheduling"): value(step) = v0 for
+ * step < i_switch, else v0 (1 + cos(pi (step - i_switch) / i_decay)) / 2 + alpha v0.  Host arithmetic. */
+double tdo_schedule_value(long long step, double v0, long long i_switch, long long i_decay, double alpha);
+
+/* The two schedules of one optimisation run.  The paper's values: eta0 0.0061, i_switch 30000,
+ * i_decay 40000, alpha 0.001; lambda0 0.004, i_switch_sr 30000, i_decay_sr 40000, alpha_sr 0.01. */
+typedef struct {
+  double eta0;
+  long long i_switch, i_decay;
+  double alpha;
+  double lambda0;
+  long long i_switch_sr, i_decay_sr;
+  double alpha_sr;
+} tdo_schedule;
+
+/* One step of the optimisation workflow (supplement, optimisation procedure) with the schedules:
+ * n_sweeps Metropolis sweeps of the chains (sig, sigp) [n_chains] (tdo_sample with *counter, which
+ * advances by n_sweeps * 2N), then tdo_sr_step on the chain states with lr = eta(step) and diag_shift =
+ * lambda(step) of sched (NULL: the paper's values).  cost (may be NULL) as in tdo_sr_step. */
+tdo_status tdo_vmc_step(tdo_ctx *ctx, uint32_t *sig, uint32_t *sigp, size_t n_chains, size_t n_sweeps,
+                        uint64_t seed, uint64_t *counter, long long step, const tdo_schedule *sched, double *cost);
+
 /* Device timing of this context's kernels: with enable != 0, every kernel launch of the calls above is
  * bracketed by CUDA events on the context's stream (records from before are dropped).  Used by the
  * benchmark to time kernels inside a real step. */

@@ -1222,6 +1222,29 @@ extern "C" tdo_status tdo_timing_read(tdo_ctx *c, const char *group, double *ms,
   return TDO_OK;
 }
 
+extern "C" double tdo_schedule_value(long long step, double v0, long long i_switch, long long i_decay, double alpha) {
+  if (step < i_switch) return v0;
+  const double pi = 3.14159265358979323846;
+  return v0 * (1.0 + cos(pi * (double)(step - i_switch) / (double)i_decay)) / 2.0 + alpha * v0;
+}
+
+extern "C" tdo_status tdo_vmc_step(tdo_ctx *c, uint32_t *sig, uint32_t *sigp, size_t n_chains, size_t n_sweeps,
+                                   uint64_t seed, uint64_t *counter, long long step, const tdo_schedule *sched,
+                                   double *cost) {
+  if (!c) return TDO_EINVAL;
+  if (!counter) return fail(c, TDO_EINVAL, "NULL counter");
+  const tdo_schedule paper = {0.0061, 30000, 40000, 0.001, 0.004, 30000, 40000, 0.01};
+  const tdo_schedule &sc = sched ? *sched : paper;
+  if (sc.i_decay <= 0 || sc.i_decay_sr <= 0) return fail(c, TDO_EINVAL, "decay periods must be > 0");
+  if (n_sweeps > 0) {
+    TRY(tdo_sample(c, n_chains, n_sweeps, seed, *counter, sig, sigp, nullptr, nullptr, nullptr));
+    *counter += (uint64_t)n_sweeps * (uint64_t)(2 * c->n);
+  }
+  const double lr = tdo_schedule_value(step, sc.eta0, sc.i_switch, sc.i_decay, sc.alpha);
+  const double shift = tdo_schedule_value(step, sc.lambda0, sc.i_switch_sr, sc.i_decay_sr, sc.alpha_sr);
+  return tdo_sr_step(c, sig, sigp, n_chains, lr, shift, cost);
+}
+
 extern "C" tdo_status tdo_set_sr_options(tdo_ctx *c, double tol, int max_iter) {
   if (!c) return TDO_EINVAL;
   if (!(tol >= 0.0) || max_iter < 0) return fail(c, TDO_EINVAL, "tol must be >= 0 and max_iter >= 0");

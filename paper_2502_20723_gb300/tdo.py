@@ -23,7 +23,7 @@ EXPORTS = ["tdo_model_num_params", "tdo_create", "tdo_destroy", "tdo_num_params"
            "tdo_set_params", "tdo_get_params", "tdo_log_rho", "tdo_log_rho_vjp", "tdo_jacobian",
            "tdo_connections", "tdo_local_estimator", "tdo_local_estimator_noalloc", "tdo_sample", "tdo_grad", "tdo_sr_solve", "tdo_set_sr_options", "tdo_sr_step",
            "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_last_error", "tdo_sample_diag", "tdo_magnetisation",
-           "tdo_purity"]
+           "tdo_purity", "tdo_schedule_value", "tdo_vmc_step"]
 
 
 class TdoError(RuntimeError):
@@ -42,6 +42,22 @@ class Problem(C.Structure):
 class Model(C.Structure):
     _fields_ = [("embed", C.c_int), ("conv_channels", C.c_int), ("d_model", C.c_int), ("n_heads", C.c_int),
                 ("n_layers", C.c_int), ("mlp_ratio", C.c_int), ("precision", C.c_int)]
+
+
+class Schedule(C.Structure):
+    """tdo_schedule: learning-rate and SR-shift schedules (defaults: the paper's values)."""
+    _fields_ = [("eta0", C.c_double), ("i_switch", C.c_longlong), ("i_decay", C.c_longlong), ("alpha", C.c_double),
+                ("lambda0", C.c_double), ("i_switch_sr", C.c_longlong), ("i_decay_sr", C.c_longlong),
+                ("alpha_sr", C.c_double)]
+
+    def __init__(self, eta0=0.0061, i_switch=30000, i_decay=40000, alpha=0.001, lambda0=0.004, i_switch_sr=30000,
+                 i_decay_sr=40000, alpha_sr=0.01):
+        super().__init__(eta0, i_switch, i_decay, alpha, lambda0, i_switch_sr, i_decay_sr, alpha_sr)
+
+
+def schedule_value(step: int, v0: float, i_switch: int, i_decay: int, alpha: float) -> float:
+    """tdo_schedule_value: v0 before i_switch, then cosine decay to a floor alpha v0."""
+    return lib().tdo_schedule_value(step, v0, i_switch, i_decay, alpha)
 
 
 _lib = None
@@ -77,6 +93,9 @@ def lib() -> C.CDLL:
         L.tdo_sample_diag.argtypes = [vp, sz, sz, u64, u64, vp, vp, C.POINTER(u64)]
         L.tdo_magnetisation.argtypes = [vp, vp, sz, vp, dp, vp]
         L.tdo_purity.argtypes = [vp, vp, vp, sz, dp, dp]
+        L.tdo_schedule_value.argtypes = [C.c_longlong, C.c_double, C.c_longlong, C.c_longlong, C.c_double]
+        L.tdo_schedule_value.restype = C.c_double
+        L.tdo_vmc_step.argtypes = [vp, vp, vp, sz, sz, u64, C.POINTER(u64), C.c_longlong, C.POINTER(Schedule), dp]
         L.tdo_grad.argtypes = [vp, vp, vp, sz, vp, dp, vp]
         L.tdo_sr_solve.argtypes = [vp, vp, sz, vp, C.c_double, C.c_double, i32, vp, C.POINTER(i32), dp]
         L.tdo_sr_step.argtypes = [vp, vp, vp, sz, C.c_double, C.c_double, dp]
@@ -87,7 +106,8 @@ def lib() -> C.CDLL:
         L.tdo_last_error.argtypes = [vp]
         L.tdo_last_error.restype = C.c_char_p
         for name in EXPORTS:
-            if name not in ("tdo_model_num_params", "tdo_num_params", "tdo_max_connections", "tdo_last_error"):
+            if name not in ("tdo_model_num_params", "tdo_num_params", "tdo_max_connections", "tdo_last_error",
+                            "tdo_schedule_value"):
                 getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -267,6 +287,15 @@ class Context:
         pu, se = C.c_double(), C.c_double()
         self._chk(lib().tdo_purity(self.h, _ptr(sig), _ptr(sigp), len(sig), C.byref(pu), C.byref(se)))
         return pu.value, se.value
+
+    def vmc_step(self, sig, sigp, n_sweeps: int, seed: int, counter: int, step: int, schedule=None):
+        """Sweeps of the chains, then an SR step with the scheduled rate and shift; returns (cost, counter)."""
+        ctr = C.c_uint64(counter)
+        cost = C.c_double()
+        sched = C.byref(schedule) if schedule is not None else None
+        self._chk(lib().tdo_vmc_step(self.h, _ptr(sig), _ptr(sigp), len(sig), n_sweeps, seed, C.byref(ctr), step,
+                                     sched, C.byref(cost)))
+        return cost.value, ctr.value
 
     def grad(self, sig, sigp, grad=None, O=None):
         Ns = len(sig)

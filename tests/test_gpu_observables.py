@@ -123,3 +123,34 @@ def test_purity_matches_oracle(precision, d, h, n, tol):
     z = ctx_for(problem("ising", n), spec, np.zeros_like(th), precision)
     p1, se1 = z.purity(dev(s0), dev(s1))
     assert p1 == pytest.approx(1.0, abs=1e-6) and se1 == pytest.approx(0.0, abs=1e-6)
+
+
+def test_vmc_step_is_sample_then_scheduled_sr_step():
+    """tdo_vmc_step = tdo_sample (counter advanced by sweeps * 2N) + tdo_sr_step with the scheduled rate
+    and shift: identical chains and cost, and parameters equal to the rounding of the gradient's float
+    atomics (within 1e-5); each step starts both contexts from the same parameters."""
+    from paper_2502_20723_gb300 import tdo
+    n = 4
+    spec = synth.model_spec(16, 2, 1, 0)
+    th = synth.init_params(spec, 0, std=0.2)
+    s0, s1 = synth.random_configs(n, 256, seed=1)
+    sched = tdo.Schedule(eta0=0.01, i_switch=2, i_decay=10, alpha=0.001, lambda0=0.05, i_switch_sr=1, i_decay_sr=8,
+                         alpha_sr=0.01)
+    a = ctx_for(problem("ising", n), spec, th)
+    b = ctx_for(problem("ising", n), spec, th)
+    sa, pa, sb, pb = dev(s0), dev(s1), dev(s0), dev(s1)
+    ctr = 5
+    for k, step in enumerate((0, 6)):   # before the switch, and on the cosine part of both schedules
+        cost_a, ctr_new = a.vmc_step(sa, pa, 2, 99, ctr, step, sched)
+        b.sample(sb, pb, 2, 99, ctr)
+        cost_b = b.sr_step(sb, pb, tdo.schedule_value(step, 0.01, 2, 10, 0.001),
+                           tdo.schedule_value(step, 0.05, 1, 8, 0.01))
+        assert ctr_new == ctr + 2 * 2 * n
+        ctr = ctr_new
+        assert np.array_equal(host(sa), host(sb)) and np.array_equal(host(pa), host(pb))
+        assert cost_a == pytest.approx(cost_b, rel=1e-12)
+        pa_, pb_ = a.get_params(), b.get_params()
+        assert np.abs(pa_ - pb_).max() <= 1e-5 * max(1.0, np.abs(pb_).max())
+        # the next step from one shared state (set_params also drops both warm starts)
+        a.set_params(pa_)
+        b.set_params(pa_)

@@ -115,6 +115,7 @@ def test_set_params_roundtrip_and_autograd():
 @pytest.mark.parametrize("kind,n,kw", [
     ("ising", 4, {}), ("ising", 16, dict(g=0.5)), ("xyz", 8, dict(Jx=0.9)), ("xyz", 8, dict(Jx=1.0)),
     ("xyz", 5, dict(Jx=1.4, Jy=2.0, Jz=1.0, Bx=-1.0, By=0.7, Bz=0.1)), ("ising", 32, {}), ("ising", 1, {}),
+    ("heis", 10, {}), ("ising2d", 4, {}), ("ising2d", 6, {}),
 ])
 def test_connections_match_oracle_rows(kind, n, kw):
     prob = problem(kind, n, **kw)
@@ -143,7 +144,8 @@ def test_connections_match_oracle_rows(kind, n, kw):
 # ------------------------------------------------------------------ L_loc, cost
 @pytest.mark.parametrize("kind,n,d,h,L,r,Ns", [
     ("ising", 4, 16, 2, 1, 0, 256), ("ising", 8, 32, 4, 2, 0, 300), ("xyz", 8, 32, 4, 2, 0, 300),
-    ("ising", 16, 64, 8, 4, 4, 64),
+    ("ising", 16, 64, 8, 4, 4, 64), ("heis", 5, 32, 4, 2, 0, 300), ("heis", 10, 32, 4, 2, 0, 200),
+    ("ising2d", 6, 32, 4, 2, 0, 300),
 ])
 def test_local_estimator_and_cost(kind, n, d, h, L, r, Ns):
     prob = problem(kind, n)
@@ -217,7 +219,8 @@ def test_vjp_random_cotangents(n, d, h, L, r, B):
 
 
 @pytest.mark.parametrize("kind,n,d,h,L,r,Ns", [("ising", 8, 32, 4, 2, 0, 256), ("xyz", 8, 32, 4, 2, 0, 256),
-                                               ("ising", 16, 64, 8, 4, 4, 48)])
+                                               ("ising", 16, 64, 8, 4, 4, 48), ("heis", 5, 32, 4, 2, 0, 200),
+                                               ("ising2d", 6, 32, 4, 2, 0, 200)])
 def test_cost_gradient(kind, n, d, h, L, r, Ns):
     prob = problem(kind, n)
     spec = synth.model_spec(d, h, L, r)
