@@ -237,11 +237,17 @@ def run_ours(args) -> dict | None:
         # BF16 contexts, FP32 pairs otherwise) from HBM twice
         mv = main["sr_mv"]
         byts = 2 * N_SAMPLES * P * (4 if args.precision == "bf16" else 8)
+        # DRAM bytes of one product from ncu (dram__bytes_read.sum + dram__bytes_write.sum of k_sr_tpart and
+        # k_sr_wpart on the 2048-sample case, profiles/k_sr_tpart_wpart_ising_n16_d64_l4.md), scaled by the
+        # samples (the passes stream every row once); for the BF16 layout at this P only
+        traffic = None
+        if args.precision == "bf16" and P == 198274:
+            traffic = (1.627103e9 + 4.585984e6 + 1.624482e9 + 6.067968e6) / 2048 * N_SAMPLES
         achieved = byts * mv["launches"] / (mv["ms"] * 1e-3) / 1e9 if mv["ms"] else 0.0
         peak = float(peaks.get("hbm_gbs", 6781.4))
         roof = {"bound": "hbm", "kernel": "S' v product (k_sr_tpart + k_sr_wpart, group sr_mv)",
                 "o_element_bytes": 4 if args.precision == "bf16" else 8,
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)", "algorithmic_per_launch": byts,
                 "products_per_step": mv["launches"], "ms_per_product": mv["ms"] / max(1e-9, mv["launches"])}
     fwd_tflops = fwd_evals * F_EVAL / (groups["fwd"]["ms"] * 1e-3) / 1e12 if groups["fwd"]["ms"] else None
