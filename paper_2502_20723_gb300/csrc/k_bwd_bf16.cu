@@ -1193,18 +1193,21 @@ __global__ void __launch_bounds__(256) k_embed_grad(const float *__restrict__ dX
   float4 acc[4];
 #pragma unroll
   for (int p = 0; p < 4; ++p) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const size_t rows = tiles * kRows, stride = (size_t)gridDim.x * SLOTS;
-  // UNR rows per thread and iteration, all loads first: enough bytes in flight to stream dX
+  const size_t rows = tiles * kRows;
+  // each block streams one contiguous range of rows (UNR * SLOTS rows = 16 KB per iteration); UNR rows per
+  // thread and iteration, all loads first: enough bytes in flight to stream dX
   constexpr int UNR = 4;
-  for (size_t r0 = (size_t)blockIdx.x * SLOTS + slot; r0 < rows; r0 += UNR * stride) {
+  const size_t per = (rows + gridDim.x - 1) / gridDim.x;
+  const size_t r_begin = (size_t)blockIdx.x * per, r_end = r_begin + per < rows ? r_begin + per : rows;
+  for (size_t r0 = r_begin + slot; r0 < r_end; r0 += UNR * SLOTS) {
     float4 v[UNR];
     int pat[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
-      const size_t r = r0 + u * stride;
+      const size_t r = r0 + u * SLOTS;
       pat[u] = -1;
       v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r >= rows) continue;
+      if (r >= r_end) continue;
       const int rt = (int)(r % kRows);
       if (rt >= nvalid) continue;
       const int sq = rt / n, i = rt % n;
