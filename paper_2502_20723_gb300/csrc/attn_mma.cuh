@@ -205,75 +205,6 @@ __device__ __forceinline__ void attn_fwd_bwd(const float *Q, const float *K, con
   }
 }
 
-// Forward only, operands already FP16 in shared memory (the forward kernel's layout):
-//   Qh, Kh: [rows][ldh] halves, this sequence's rows from 0 (Q pre-scaled by 1/sqrt(HD) log2 e),
-//   Vt:     [features][ldt] halves, V transposed, this sequence's keys at columns 0..15 (keys >= n zero),
-// all with 4-byte-aligned pairs.  emit(row, col, v0, v1) for the attention output O, row < n.
-// FULL: n = 16 at compile time (no masks).
-template <int HD, bool FULL = false, typename EMIT>
-__device__ __forceinline__ void attn_fwd_h(const __half *Qh, const __half *Kh, const __half *Vt, int ldh, int ldt,
-                                           int n, EMIT emit) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  auto ld2 = [&](const __half *M, int r, int c) -> uint32_t {
-    return (FULL || r < n) ? *reinterpret_cast<const uint32_t *>(M + r * ldh + c) : 0u;
-  };
-  float s[2][4];
-#pragma unroll
-  for (int j = 0; j < 2; ++j) zero4(s[j]);
-  if (HD == 8) {
-    const uint32_t a0 = ld2(Qh, g, 2 * t), a1 = ld2(Qh, g + 8, 2 * t);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) mma1688(s[j], a0, a1, ld2(Kh, 8 * j + g, 2 * t));
-  } else {
-    const uint32_t a[4] = {ld2(Qh, g, 2 * t), ld2(Qh, g + 8, 2 * t), ld2(Qh, g, 8 + 2 * t), ld2(Qh, g + 8, 8 + 2 * t)};
-#pragma unroll
-    for (int j = 0; j < 2; ++j) mma16816(s[j], a, ld2(Kh, 8 * j + g, 2 * t), ld2(Kh, 8 * j + g, 8 + 2 * t));
-  }
-  float m0 = -INFINITY, m1 = -INFINITY;
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const bool ok = FULL || 8 * j + 2 * t + e < n;
-      s[j][e] = ok ? s[j][e] : -INFINITY;
-      s[j][2 + e] = ok ? s[j][2 + e] : -INFINITY;
-      m0 = fmaxf(m0, s[j][e]);
-      m1 = fmaxf(m1, s[j][2 + e]);
-    }
-#pragma unroll
-  for (int o = 1; o <= 2; o <<= 1) {
-    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-  }
-  float l0 = 0.f, l1 = 0.f;
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      s[j][e] = tc::ex2_fast(s[j][e] - m0);
-      s[j][2 + e] = tc::ex2_fast(s[j][2 + e] - m1);
-      l0 += s[j][e];
-      l1 += s[j][2 + e];
-    }
-#pragma unroll
-  for (int o = 1; o <= 2; o <<= 1) {
-    l0 += __shfl_xor_sync(0xffffffffu, l0, o);
-    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-  }
-  const float i0 = tc::rcp_fast(l0), i1 = tc::rcp_fast(l1);
-  const uint32_t pa[4] = {h2(s[0][0] * i0, s[0][1] * i0), h2(s[0][2] * i1, s[0][3] * i1),
-                          h2(s[1][0] * i0, s[1][1] * i0), h2(s[1][2] * i1, s[1][3] * i1)};
-#pragma unroll
-  for (int c = 0; c < HD / 8; ++c) {
-    float o[4];
-    zero4(o);
-    const __half *vr = Vt + (8 * c + g) * ldt;
-    mma16816(o, pa, *reinterpret_cast<const uint32_t *>(vr + 2 * t), *reinterpret_cast<const uint32_t *>(vr + 8 + 2 * t));
-    if (FULL || g < n) emit(g, 8 * c + 2 * t, o[0], o[1]);
-    if (FULL || g + 8 < n) emit(g + 8, 8 * c + 2 * t, o[2], o[3]);
-  }
-}
-
 // ---- shared-memory fragments by ldmatrix (FP16 row-major blocks, 16-byte-aligned rows)
 __device__ __forceinline__ void ldsm2(uint32_t addr, uint32_t &r0, uint32_t &r1) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
@@ -343,6 +274,90 @@ __device__ __forceinline__ void mma_y(const uint32_t (&x)[4], const uint32_t (&b
   for (int c = 0; c < HD / 8; ++c) {
     zero4(y[c]);
     mma16816(y[c], x, b[c][0], b[c][1]);
+  }
+}
+
+// Forward only, operands already FP16 in shared memory (the forward kernel's layout):
+//   Qh, Kh: [rows][ldh] halves, this sequence's rows from 0 (Q pre-scaled by 1/sqrt(HD) log2 e),
+//   V:      FULL: [rows][ldh] halves like K (16-byte-aligned rows: fragments by ldmatrix.trans);
+//           otherwise V transposed, [features][ldv] halves, this sequence's keys at columns 0..15
+//           (keys >= n zero),
+// all with 4-byte-aligned pairs.  emit(row, col, v0, v1) for the attention output O, row < n.
+// FULL: n = 16 at compile time (no masks).
+template <int HD, bool FULL = false, typename EMIT>
+__device__ __forceinline__ void attn_fwd_h(const __half *Qh, const __half *Kh, const __half *V, int ldh, int ldv,
+                                           int n, EMIT emit) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  auto ld2 = [&](const __half *M, int r, int c) -> uint32_t {
+    return (FULL || r < n) ? *reinterpret_cast<const uint32_t *>(M + r * ldh + c) : 0u;
+  };
+  float s[2][4];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) zero4(s[j]);
+  if (HD == 8) {
+    const uint32_t a0 = ld2(Qh, g, 2 * t), a1 = ld2(Qh, g + 8, 2 * t);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) mma1688(s[j], a0, a1, ld2(Kh, 8 * j + g, 2 * t));
+  } else {
+    const uint32_t a[4] = {ld2(Qh, g, 2 * t), ld2(Qh, g + 8, 2 * t), ld2(Qh, g, 8 + 2 * t), ld2(Qh, g + 8, 8 + 2 * t)};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) mma16816(s[j], a, ld2(Kh, 8 * j + g, 2 * t), ld2(Kh, 8 * j + g, 8 + 2 * t));
+  }
+  float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const bool ok = FULL || 8 * j + 2 * t + e < n;
+      s[j][e] = ok ? s[j][e] : -INFINITY;
+      s[j][2 + e] = ok ? s[j][2 + e] : -INFINITY;
+      m0 = fmaxf(m0, s[j][e]);
+      m1 = fmaxf(m1, s[j][2 + e]);
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      s[j][e] = tc::ex2_fast(s[j][e] - m0);
+      s[j][2 + e] = tc::ex2_fast(s[j][2 + e] - m1);
+      l0 += s[j][e];
+      l1 += s[j][2 + e];
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+  }
+  const float i0 = tc::rcp_fast(l0), i1 = tc::rcp_fast(l1);
+  const uint32_t pa[4] = {h2(s[0][0] * i0, s[0][1] * i0), h2(s[0][2] * i1, s[0][3] * i1),
+                          h2(s[1][0] * i0, s[1][1] * i0), h2(s[1][2] * i1, s[1][3] * i1)};
+  if constexpr (FULL) {   // O = P V with V's B fragments by transposing ldmatrix
+    uint32_t vb[HD / 8][2];
+    frag_bk<HD>((uint32_t)__cvta_generic_to_shared(V), ldh, vb);
+    float o[HD / 8][4];
+    mma_y<HD>(pa, vb, o);
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      emit(g, 8 * c + 2 * t, o[c][0], o[c][1]);
+      emit(g + 8, 8 * c + 2 * t, o[c][2], o[c][3]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      float o[4];
+      zero4(o);
+      const __half *vr = V + (8 * c + g) * ldv;
+      mma16816(o, pa, *reinterpret_cast<const uint32_t *>(vr + 2 * t),
+               *reinterpret_cast<const uint32_t *>(vr + 8 + 2 * t));
+      if (g < n) emit(g, 8 * c + 2 * t, o[0], o[1]);
+      if (g + 8 < n) emit(g + 8, 8 * c + 2 * t, o[2], o[3]);
+    }
   }
 }
 

@@ -221,7 +221,12 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
                                 amma::h2(v[14], v[15]));
           }
           tmem_ld16(c.tmem + lane_addr + 2 * D + half * DH + j, v);
-          if (valid) {
+          if (n == 16) {   // full sequences: V row-major like K (the attention reads it by ldmatrix.trans)
+            uint4 *dst = reinterpret_cast<uint4 *>(Vt + row * G::LDH + half * DH + j);
+            dst[0] = make_uint4(amma::h2(v[0], v[1]), amma::h2(v[2], v[3]), amma::h2(v[4], v[5]), amma::h2(v[6], v[7]));
+            dst[1] = make_uint4(amma::h2(v[8], v[9]), amma::h2(v[10], v[11]), amma::h2(v[12], v[13]),
+                                amma::h2(v[14], v[15]));
+          } else if (valid) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) Vt[(half * DH + j + e) * G::LDT + 16 * sq + i] = __float2half_rn(v[e]);
           }
@@ -239,8 +244,10 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
         constexpr int H = D / HD;   // heads (d_model = heads x head dimension)
         for (int u = warp; u < ts * H; u += kThreads / 32) {
           const int sq = u / H, h = u % H, rb = sq * (decltype(full)::value ? 16 : n);
-          amma::attn_fwd_h<HD, decltype(full)::value>(
-              Qh + rb * G::LDH + h * HD, Kh + rb * G::LDH + h * HD, Vt + h * HD * G::LDT + 16 * sq, G::LDH, G::LDT, n,
+          constexpr bool FULL = decltype(full)::value;
+          amma::attn_fwd_h<HD, FULL>(
+              Qh + rb * G::LDH + h * HD, Kh + rb * G::LDH + h * HD,
+              FULL ? Vt + rb * G::LDH + h * HD : Vt + h * HD * G::LDT + 16 * sq, G::LDH, FULL ? G::LDH : G::LDT, n,
               [&](int r, int cc, float v0, float v1) {
                 *reinterpret_cast<uint32_t *>(A + canon(rb + r, h * HD + cc, D)) = pack_bf16(v0, v1);
               });
