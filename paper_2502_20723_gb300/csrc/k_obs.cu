@@ -43,11 +43,11 @@ __global__ void k_obs_rows(const uint32_t *__restrict__ alpha, size_t Ns, int n,
   }
 }
 
-// Thread per sample; part[q * gridDim.x + block] for the 7 sums.
+// Thread per sample; part[q * gridDim.x + block] for the 6 sums: s, Re/Im s A~x, Re/Im s A~y, s A~z.
 __global__ void k_obs_local(const uint32_t *__restrict__ alpha, size_t Ns, int n, const float2 *__restrict__ lr,
                             double *__restrict__ local, double *__restrict__ part) {
   __shared__ double sh[32];
-  double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Ns; s += gridDim.x * (size_t)blockDim.x) {
     const float2 *row = lr + s * (size_t)(n + 1);
     const double r0 = row[0].x, i0 = row[0].y;
@@ -73,10 +73,10 @@ __global__ void k_obs_local(const uint32_t *__restrict__ alpha, size_t Ns, int n
     acc[0] += sg;
     acc[1] += sg * xr; acc[2] += sg * xi;
     acc[3] += sg * yr; acc[4] += sg * yi;
-    acc[5] += sg * z;  acc[6] += 0.0;
+    acc[5] += sg * z;
   }
 #pragma unroll
-  for (int q = 0; q < 7; ++q) {
+  for (int q = 0; q < 6; ++q) {
     const double t = block_sum(acc[q], sh);
     if (threadIdx.x == 0) part[q * gridDim.x + blockIdx.x] = t;
   }
@@ -133,7 +133,7 @@ cudaError_t launch_obs_reduce(const uint32_t *alpha, size_t Ns, int n, const flo
                               double *part, double *out, cudaStream_t st) {
   using namespace tdo::obs;
   k_obs_local<<<kBlocks, kThreads, 0, st>>>(alpha, Ns, n, lr, local, part);
-  k_sum_parts<<<1, 256, 0, st>>>(part, kBlocks, 7, out);
+  k_sum_parts<<<1, 256, 0, st>>>(part, kBlocks, 6, out);
   return cudaGetLastError();
 }
 

@@ -1146,7 +1146,7 @@ extern "C" tdo_status tdo_magnetisation(tdo_ctx *c, const uint32_t *alpha, size_
   TRY(forward_dev(c, c->obs_rs.as<uint32_t>(), c->obs_rp.as<uint32_t>(), rows, c->obs_lr.as<float2>()));
   CU(c, launch_obs_reduce((const uint32_t *)da, Ns, n, c->obs_lr.as<float2>(), dlocal, c->obs_part.as<double>(),
                           c->obs_out.as<double>(), c->stream));
-  double h[7];
+  double h[6];
   CU(c, cudaMemcpyAsync(h, c->obs_out.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   if (local && dlocal != local) CU(c, cudaMemcpyAsync(local, dlocal, 8 * 8 * Ns, cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaStreamSynchronize(c->stream));

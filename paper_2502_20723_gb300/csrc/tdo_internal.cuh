@@ -71,7 +71,8 @@ cudaError_t launch_sample_bf16(const DevModel &m, const DevModelBF16 &mb, size_t
 // (alpha, alpha ^ e_i) for i < N, at rows s (N + 1) + j.
 cudaError_t launch_obs_rows(const uint32_t *alpha, size_t Ns, int n, uint32_t *rs, uint32_t *rp, cudaStream_t st);
 // From log rho of those rows: local[s] = (s, A~x, A~y, A~z) as complex pairs (may be NULL), and
-// out[0..6] = sum s, Re/Im sum s A~x, s A~y, s A~z (FP64, fixed order; part: nb = 256 blocks x 7 doubles).
+// out[0..5] = sum s, Re/Im sum s A~x, Re/Im sum s A~y, sum s A~z (A~z is real; FP64, fixed order;
+// part: 256 blocks x 6 doubles).
 cudaError_t launch_obs_reduce(const uint32_t *alpha, size_t Ns, int n, const float2 *lr, double *local,
                               double *part, double *out, cudaStream_t st);
 // Rows of the purity estimator: sample s -> (sigma, sigma'), (sigma, sigma), (sigma', sigma') at 3 s + j.
