@@ -1,5 +1,6 @@
-"""Writes tests/golden/ed_observables.json: exact steady-state observables of the workloads' problems,
-computed by the oracle only (dense LU for N <= 6, RK4 propagation of Eq. VecLin for N = 8).
+"""Writes tests/golden/ed_observables.json: exact steady-state observables of the workloads' problems
+(Ising and XYZ chains, the Heisenberg chain with fields, the 2D Ising torus), computed by the oracle only
+(dense LU for N <= 6, RK4 propagation of Eq. VecLin for N = 8).
 
     python tests/golden/make_golden.py
 """
@@ -33,6 +34,10 @@ CASES = {
     "ising_n8_V2_g1": (synth.ising_chain, dict(n=8, V=2.0, g=1.0, gamma=1.0)),
     "xyz_n4_Jx0.9": (synth.xyz_chain, dict(n=4, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0)),
     "xyz_n8_Jx0.9": (synth.xyz_chain, dict(n=8, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0)),
+    # Heisenberg chain with fields (J = (1.4, 2.0, 1.0), B = (-1.0, B_y, 0.1)) and the 2D Ising torus
+    "heis_n5_By0.5": (synth.xyz_chain, dict(n=5, Jx=1.4, Jy=2.0, Jz=1.0, Bx=-1.0, By=0.5, Bz=0.1, gamma=1.0)),
+    "ising2d_2x2_V2_g1": (synth.ising_2d, dict(mx=2, ny=2, V=2.0, g=1.0, gamma=1.0)),
+    "ising2d_2x3_V2_g1": (synth.ising_2d, dict(mx=2, ny=3, V=2.0, g=1.0, gamma=1.0)),
 }
 
 

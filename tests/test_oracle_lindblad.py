@@ -129,3 +129,23 @@ def test_propagation_matches_dense():
     a = lindblad.steady_state_dense(p)
     b = lindblad.steady_state_propagate(p, tol=1e-12)
     assert np.abs(a - b).max() < 1e-10
+
+
+def test_golden_ed_observables_are_consistent():
+    """The stored exact steady states (tests/golden/ed_observables.json, written by
+    tests/golden/make_golden.py from the oracle): every Ising entry, chain or 2D torus, obeys the
+    site-averaged sum rule g <sigma^y> = gamma (1 + <sigma^z>) (the sigma^z sigma^z bonds commute with
+    sigma^z_i, so the rule holds on any lattice); the 2 x 2 torus is the 4-site ring; purities lie in
+    [2^-N, 1]."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ed_observables.json")))
+    assert {"heis_n5_By0.5", "ising2d_2x2_V2_g1", "ising2d_2x3_V2_g1"} <= set(gold)
+    for name, e in gold.items():
+        pr = e["problem"]
+        n = pr["n"] if "n" in pr else pr["mx"] * pr["ny"]
+        assert 2.0 ** -n - 1e-9 <= e["purity"] <= 1.0 + 1e-9, name
+        if name.startswith("ising"):
+            assert pr["g"] * e["sy"] == pytest.approx(pr["gamma"] * (1.0 + e["sz"]), abs=1e-8), name
+    for q in ("sx", "sy", "sz", "purity"):
+        assert gold["ising2d_2x2_V2_g1"][q] == pytest.approx(gold["ising_n4_V2_g1"][q], abs=1e-10)
