@@ -44,6 +44,26 @@ def flops_per_sequence(n=N_SITES, d=D, layers=LAYERS, r=MLP) -> float:
 F_EVAL = 2.0 * flops_per_sequence()   # one log rho = both orders of the doubled configuration
 
 
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """Largest per-rank value (every rank times its own replica); the run's only collective."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job rate of `world` replicas that each finished `units_per_rank` within `seconds`."""
+    return world * units_per_rank / seconds
+
+
+def replica_seeds(rank: int) -> tuple[int, int]:
+    """(initial-configuration seed, Metropolis seed) of a replica: every rank runs its own chains."""
+    return 1000 + rank, 12345 + rank
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -127,10 +147,10 @@ def run_ours(args) -> dict | None:
 
     def measure(precision: str, steps: int, warmup: int, e2e: bool):
         ctx = tdo.Context(prob, spec, theta, precision, stream=stream.cuda_stream)
-        s0, s1 = synth.random_configs(N_SITES, N_SAMPLES, seed=1000 + rank)
+        cfg_seed, seed = replica_seeds(rank)
+        s0, s1 = synth.random_configs(N_SITES, N_SAMPLES, seed=cfg_seed)
         sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
         sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
-        seed = 12345 + rank
         counter = [0]
         ctx.sample(sig, sigp, args.burn_in, seed, counter[0])     # burn-in (untimed)
         counter[0] += args.burn_in * 2 * N_SITES
@@ -170,10 +190,7 @@ def run_ours(args) -> dict | None:
         sr_mv = {"ms": ms / steps, "launches": n / steps}
         ctx.timing(False)
         lloc_rows = int(ctx.connections(sig, sigp)[0].sum().item())
-        t_max = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        out = {"t_ms": float(t_max.item()), "groups": groups, "sr_mv": sr_mv, "launches": launches,
+        out = {"t_ms": max_over_ranks(t_ms, world), "groups": groups, "sr_mv": sr_mv, "launches": launches,
                "lloc_rows": lloc_rows,
                "costs": costs, "sr_iters": sr_iters, "clocks": clk.summary(), "P": ctx.P}
         if e2e:
@@ -191,10 +208,7 @@ def run_ours(args) -> dict | None:
                 counter[0] += 2 * N_SITES
                 ctx.sr_step(hs_np, hp_np, LR, SHIFT)                   # H2D samples, D2H cost
             torch.cuda.synchronize()
-            e2e_t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-            if world > 1:
-                dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-            out["e2e_steps_per_s"] = world * n_e2e / float(e2e_t.item())
+            out["e2e_steps_per_s"] = replicas_rate(world, n_e2e, max_over_ranks(time.perf_counter() - t0, world))
         ctx.close()
         return out
 
@@ -253,7 +267,7 @@ def run_ours(args) -> dict | None:
     fwd_tflops = fwd_evals * F_EVAL / (groups["fwd"]["ms"] * 1e-3) / 1e12 if groups["fwd"]["ms"] else None
     res = {
         "metric": METRIC,
-        "value": world * args.steps / (t_max * 1e-3),
+        "value": replicas_rate(world, args.steps, t_max * 1e-3),
         "unit": "VMC steps/s",
         "n_gpus": world,
         "steps": args.steps,
