@@ -56,3 +56,19 @@ def test_create_without_device_fails_cleanly(libtdo):
     spec = synth.model_spec(16, 2, 1, 0)
     with pytest.raises(tdo.TdoError):
         tdo.Context(synth.ising_chain(4), spec, synth.init_params(spec))
+
+
+def test_null_context_is_rejected_without_a_device(libtdo):
+    """Entry points given no context return TDO_EINVAL before touching CUDA (pure host checks)."""
+    from paper_2502_20723_gb300 import tdo
+    einval = -1
+    assert [k for k, v in tdo.STATUS.items() if v == "TDO_EINVAL"] == [einval]
+    u64 = ctypes.c_uint64(0)
+    d = ctypes.c_double(0.0)
+    mag = (ctypes.c_double * 3)()
+    assert libtdo.tdo_sample(None, 4, 1, 0, 0, None, None, None, None, None) == einval
+    assert libtdo.tdo_sample_diag(None, 4, 1, 0, 0, None, None, None) == einval
+    assert libtdo.tdo_magnetisation(None, None, 4, mag, None, None) == einval
+    assert libtdo.tdo_purity(None, None, None, 4, ctypes.byref(d), None) == einval
+    assert libtdo.tdo_vmc_step(None, None, None, 4, 1, 0, ctypes.byref(u64), 0, None, None) == einval
+    assert libtdo.tdo_sr_step(None, None, None, 4, 0.1, 0.1, None) == einval
