@@ -48,7 +48,9 @@ typedef enum {
 } tdo_status;
 
 enum { TDO_EMBED_TOKEN = 0, TDO_EMBED_CONV = 1 };
-enum { TDO_FP32 = 0, TDO_BF16 = 1 };
+/* Precision of a context: TDO_FP32 = FP32 CUDA-core path; TDO_BF16 and TDO_FP16 = tensor-core path
+ * (tcgen05 GEMMs with FP32 accumulation) whose GEMM operands are BF16 or FP16 respectively. */
+enum { TDO_FP32 = 0, TDO_BF16 = 1, TDO_FP16 = 2 };
 
 /* Problem statement: a chain of N spins, a Hamiltonian given as a sum of real multiples of Pauli strings
  * on at most two sites, and single-site jump operators with rates (Eq. Lindblad / Eq. VecLin). */
@@ -72,7 +74,7 @@ typedef struct {
   int n_heads;                /* divides d_model; head dim <= 16 */
   int n_layers;               /* 1..8 */
   int mlp_ratio;              /* 0 (the paper's block: no MLP) or 1..4 */
-  int precision;              /* TDO_FP32 or TDO_BF16 (GEMMs of the forward on tcgen05 tensor cores) */
+  int precision;              /* TDO_FP32, TDO_BF16 or TDO_FP16 (tensor-core GEMM operand type) */
 } tdo_model;
 
 /* Number of real parameters of a model (the length of theta). 0 for an invalid model. */
@@ -124,7 +126,7 @@ tdo_status tdo_local_estimator(tdo_ctx *ctx, const uint32_t *sig, const uint32_t
  * cudaMalloc / cudaFree may imply.  The paper has no counterpart; this is an interface convenience.
  * Same outputs as tdo_local_estimator, but sig, sigp and lloc must be device pointers (lloc 16-byte
  * aligned), and the call
- * allocates nothing: its scratch is one fixed device array (about 8.7 MB) that every GPU which loads
+ * allocates nothing: its scratch is one fixed device array (10,813,952 bytes, about 10.8 MB) that every GPU which loads
  * the library holds until the process exits.  Limits: Ns <= 16384 and Ns * tdo_max_connections()
  * <= 262144, else TDO_EINVAL.  The first call on a device looks up the array's device address (once
  * per device, with that device current); make that first call before any stream capture.  All calls
@@ -189,13 +191,25 @@ tdo_status tdo_grad(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, siz
 tdo_status tdo_sr_solve(tdo_ctx *ctx, const float *O, size_t Ns, const double *rhs, double diag_shift,
                         double tol, int max_iter, double *x, int *iters, double *resid);
 
+/* Optimiser applied to the SR direction delta = (Re S + diag_shift I)^-1 grad by tdo_sr_step and tdo_vmc_step
+ * (optimisation-procedure section: "Stochastic Gradient Descent or Adam" combined with stochastic
+ * reconfiguration as the gradient preconditioner).  TDO_OPT_SGD (default): theta <- theta - lr delta.
+ * TDO_OPT_ADAM (Kingma and Ba, Algorithm 1, delta in the role of the gradient): with t the steps taken
+ * since this call, m <- beta1 m + (1 - beta1) delta, v <- beta2 v + (1 - beta2) delta^2,
+ * theta <- theta - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps); the moments are FP64 [P]
+ * in the context.  Every call resets the moments and t (TDO_EINVAL on an unknown kind or beta outside
+ * [0, 1), eps <= 0).  The paper uses Adam for its Heisenberg example with no values printed; the
+ * usual 0.9, 0.999, 1e-8 are suggested. */
+enum { TDO_OPT_SGD = 0, TDO_OPT_ADAM = 1 };
+tdo_status tdo_set_optimizer(tdo_ctx *ctx, int kind, double beta1, double beta2, double eps);
+
 /* Stopping rule of the CG solve inside tdo_sr_step (defaults: tol 1e-6, max_iter 100).  The solve
  * starts from the previous step's solution when there is one (reset by tdo_set_params). */
 tdo_status tdo_set_sr_options(tdo_ctx *ctx, double tol, int max_iter);
 
 /* One optimisation-workflow step on a given sample set: cost and gradient, log-derivatives,
- * SR solve with diag_shift, theta <- theta - lr * delta.  cost (may be NULL) gets the cost before the
- * update. */
+ * SR solve with diag_shift, then the optimiser's update with the direction delta (tdo_set_optimizer;
+ * default theta <- theta - lr * delta).  cost (may be NULL) gets the cost before the update. */
 tdo_status tdo_sr_step(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t Ns, double lr,
                        double diag_shift, double *cost);
 
@@ -234,6 +248,28 @@ tdo_status tdo_timing_read(tdo_ctx *ctx, const char *group, double *ms, long lon
 
 /* Iterations and final relative residual of the last tdo_sr_step's CG solve. */
 tdo_status tdo_sr_info(const tdo_ctx *ctx, int *iters, double *resid);
+
+/* How the last tdo_sr_step's CG solve ended (each pointer may be NULL): outcome 0 = stopped at the
+ * iteration limit, 1 = converged, 2 = breakdown (p . (S + shift I) p not positive), 3 = a non-finite
+ * value (the step then returned TDO_ENUMERIC); last_pap = the last p . (S + shift I) p, formed as
+ * (1/Ns) sum_s |t_s - tbar|^2 + shift |p|^2 with t = O p (never negative); restarts = 1 when the
+ * warm-started solve failed and was solved again from x = 0. */
+tdo_status tdo_sr_report(const tdo_ctx *ctx, int *outcome, double *last_pap, int *restarts);
+
+/* Arithmetic peak of the current device measured by the library (no counterpart in the paper):
+ * kind 0 = FP32 fused multiply-add on the CUDA cores, 1 = FP64 FMA; *tflops = the best of three timed
+ * launches (CUDA events on `stream`, a cudaStream_t or NULL) of a kernel of independent FMA chains,
+ * 2 FLOP per FMA.  Allocates and frees a few bytes of device memory; synchronises the stream.  Used as
+ * the denominator of the FP32 path's roofline fraction. */
+tdo_status tdo_measure_peak(int kind, void *stream, double *tflops);
+
+/* Self-test of the bounded device waits (no counterpart in the paper): launches one CTA that sets up the
+ * tensor-core control block of the forward (two mbarriers, a TMEM allocation) and waits, at most
+ * spin_limit polls (1 .. 2^20), for an MMA completion that nothing signals; no copy and no MMA is in
+ * flight.  The wait gives up, the kernel raises the context's error flag, frees its TMEM and returns, and
+ * the call reports TDO_ETIMEOUT exactly as a timed-out production kernel does.  The context stays
+ * usable.  BF16 contexts only (TDO_EUNSUPPORTED otherwise). */
+tdo_status tdo_wait_selftest(tdo_ctx *ctx, long long spin_limit);
 
 /* Message of the last failing call on this context (or of the last failed tdo_create when ctx is NULL). */
 const char *tdo_last_error(const tdo_ctx *ctx);

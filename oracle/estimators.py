@@ -158,6 +158,17 @@ def sr_step(problem: dict, spec: dict, theta, sig, sigp, lr_eta: float, diag_shi
     return np.asarray(theta) - lr_eta * delta, cost, g, delta
 
 
+def adam_step(theta, delta, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """One Adam step (Kingma and Ba 2014, Algorithm 1) with the SR direction delta as the gradient, as the
+    optimisation-procedure section combines Adam with stochastic reconfiguration; t = this step's number
+    (1 for the first).  Returns (theta, m, v)."""
+    m = b1 * np.asarray(m) + (1.0 - b1) * np.asarray(delta)
+    v = b2 * np.asarray(v) + (1.0 - b2) * np.asarray(delta) ** 2
+    m_hat = m / (1.0 - b1 ** t)
+    v_hat = v / (1.0 - b2 ** t)
+    return np.asarray(theta) - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
 def lr_schedule(i: int, eta0: float = 0.0061, i_switch: int = 30000, i_decay: int = 40000, alpha: float = 0.001):
     """Learning-rate schedule of the scheduling section: constant, then cosine decay plus a floor."""
     if i < i_switch:

@@ -29,10 +29,24 @@
 #include "tcgen05.cuh"
 #include "tdo_device.cuh"
 
+// TDO_F16 = 1 compiles the same kernels with FP16 operand images and weights (k_bwd_f16.cu), in their own
+// namespace and with launcher names ending in _f16; the default build uses BF16 operands.
+#ifndef TDO_F16
+#define TDO_F16 0
+#endif
+#if TDO_F16
+#define TDO_BWNS bwdtc16
+#define TDO_OPFN(name) name##_f16
+#else
+#define TDO_BWNS bwdtc
+#define TDO_OPFN(name) name
+#endif
+
 namespace tdo {
-namespace bwdtc {
+namespace TDO_BWNS {
 
 using namespace tdo::tc;
+constexpr bool kF16 = TDO_F16 != 0;   // operand type of every tensor-core GEMM image and weight
 
 constexpr int kRows = 128;
 constexpr int kCopiesMax = 16;
@@ -72,7 +86,7 @@ __device__ __forceinline__ bool wait_ld(Sync &s) {
 
 // K-major x K-major: D[tmem + col] (+)= A[128 x K] B[N x K]^T
 __device__ __forceinline__ void mma_kk(const Sync &s, uint32_t a, uint32_t b, int K, int N, uint32_t col, bool acc) {
-  const uint32_t id = idesc_bf16(kRows, N);
+  const uint32_t id = idesc16<kF16>(kRows, N);
   const uint64_t da = dk(a, K), db = dk(b, K);
   for (int kk = 0; kk < K / 16; ++kk)
     mma_bf16(s.tmem + col, da + kk * 16, db + kk * 16, id, (acc || kk > 0) ? 1u : 0u);
@@ -80,7 +94,7 @@ __device__ __forceinline__ void mma_kk(const Sync &s, uint32_t a, uint32_t b, in
 // MN-major x MN-major over the 128 rows: D[tmem + col][M = Ka][N = Kb] (+)= A_img^T B_img
 __device__ __forceinline__ void mma_mm(const Sync &s, uint32_t a, int Ka, uint32_t b, int Kb, int N, uint32_t col,
                                        bool acc) {
-  const uint32_t id = idesc_bf16_major(kRows, N, 1, 1);
+  const uint32_t id = idesc16_major<kF16>(kRows, N, 1, 1);
   const uint64_t da = dmn(a, Ka), db = dmn(b, Kb);
   for (int kk = 0; kk < kRows / 16; ++kk)
     mma_bf16(s.tmem + col, da + kk * Ka * 2, db + kk * Kb * 2, id, (acc || kk > 0) ? 1u : 0u);
@@ -196,7 +210,7 @@ __device__ __forceinline__ void jac_put1(const JacOut &j, size_t v, long long k,
 // MN-major x MN-major over rows [r0, r0 + 16 nsteps) of the images: D[tmem + col] = A_img^T B_img
 __device__ __forceinline__ void mma_mm_rows(const Sync &s, uint32_t a, int Ka, uint32_t b, int Kb, int N,
                                             uint32_t col, int r0, int nsteps) {
-  const uint32_t id = idesc_bf16_major(kRows, N, 1, 1);
+  const uint32_t id = idesc16_major<kF16>(kRows, N, 1, 1);
   const uint64_t da = dmn(a, Ka), db = dmn(b, Kb);
   for (int kk = 0; kk < nsteps; ++kk) {
     const int r = r0 / 16 + kk;
@@ -295,6 +309,7 @@ __device__ __noinline__ void jac_flush_rows(const Sync &s, const JacOut &j, size
 // ====================================================================================== head
 struct HeadArgs {
   const float2 *cot;   // [B] cotangents of log rho
+  const float *cscale; // power-of-two factor applied to every cotangent (null: 1)
   const float *F;      // [B][4] head outputs (F0, F1 of both orders)
   const float *H;      // [2B][D] pooled vectors
   const float *Wh;     // [D][2]
@@ -311,7 +326,12 @@ struct HeadArgs {
 __device__ __forceinline__ float4 head_df(const HeadArgs &a, size_t b) {
   float2 pw, pv;
   symmetrise(a.F[4 * b], a.F[4 * b + 1], a.F[4 * b + 2], a.F[4 * b + 3], &pw, &pv);
-  const float2 c = a.cot[b];
+  float2 c = a.cot[b];
+  if (a.cscale) {
+    const float k = *a.cscale;
+    c.x *= k;
+    c.y *= k;
+  }
   const float cwr = c.x * pw.x - c.y * pw.y, cwi = c.x * pw.y + c.y * pw.x;
   const float cvr = c.x * pv.x - c.y * pv.y, cvi = c.x * pv.y + c.y * pv.x;
   return make_float4(cwr, -cwi, cvr, cvi);
@@ -366,10 +386,8 @@ __global__ void k_head_bwd(HeadArgs a) {
     if (b < a.B) {
       float2 pw, pv;
       symmetrise(a.F[4 * b], a.F[4 * b + 1], a.F[4 * b + 2], a.F[4 * b + 3], &pw, &pv);
-      const float2 c = a.cot[b];
-      const float cwr = c.x * pw.x - c.y * pw.y, cwi = c.x * pw.y + c.y * pw.x;
-      const float cvr = c.x * pv.x - c.y * pv.y, cvi = c.x * pv.y + c.y * pv.x;
-      d0 = cwr; d1 = -cwi; d2 = cvr; d3 = cvi;
+      const float4 d = head_df(a, b);
+      d0 = d.x; d1 = d.y; d2 = d.z; d3 = d.w;
       const float *hA = a.H + (2 * b) * a.D, *hB = hA + a.D;
       if (a.jac.nvirt) {   // this configuration's own head gradient
         for (int k = 0; k < a.D; ++k) {
@@ -489,8 +507,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   for (int i = threadIdx.x; i < G::HC; i += kMlpThreads) b1s[i] = a.b1[i];
   if (head)
     for (int i = threadIdx.x; i < 2 * D; i += kMlpThreads) whs[i] = a.Wh[i];
-  for (int i = threadIdx.x; i < kRows * 16 / 8; i += kMlpThreads)   // bf16 1.0 = 0x3F80
-    reinterpret_cast<uint4 *>(sm + G::ONE_OFF)[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+  for (int i = threadIdx.x; i < kRows * 16 / 8; i += kMlpThreads)   // 1.0 in the operand type
+    reinterpret_cast<uint4 *>(sm + G::ONE_OFF)[i] = make_uint4(kOnePair<kF16>, kOnePair<kF16>, kOnePair<kF16>, kOnePair<kF16>);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (warp & 3) + lane, cg = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
@@ -550,7 +568,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
         }
       }
 #pragma unroll
-      for (int j = 0; j < QD; j += 8) st_row8(sm + G::DX_OFF + b * G::IMG, row, cg * QD + j, D, dxo + j);
+      for (int j = 0; j < QD; j += 8) st_row8<kF16>(sm + G::DX_OFF + b * G::IMG, row, cg * QD + j, D, dxo + j);
     };
     // MMA1 of tile t from buffer b, once its Xmid image has landed and its dX image is written
     auto issue_mma1 = [&](int b) -> bool {
@@ -590,10 +608,10 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
           const float uu = u[e] + b1s[cg * QH + j + e];
           du[e] = dg[e] * gelu_grad_fast(uu, &gl[e]);
         }
-        st_row8(sm + G::G_OFF, row, cg * QH + j, G::HC, gl);
-        st_row8(sm + G::G_OFF, row, cg * QH + j + 8, G::HC, gl + 8);
-        st_row8(sm + G::DU_OFF, row, cg * QH + j, G::HC, du);
-        st_row8(sm + G::DU_OFF, row, cg * QH + j + 8, G::HC, du + 8);
+        st_row8<kF16>(sm + G::G_OFF, row, cg * QH + j, G::HC, gl);
+        st_row8<kF16>(sm + G::G_OFF, row, cg * QH + j + 8, G::HC, gl + 8);
+        st_row8<kF16>(sm + G::DU_OFF, row, cg * QH + j, G::HC, du);
+        st_row8<kF16>(sm + G::DU_OFF, row, cg * QH + j + 8, G::HC, du + 8);
       }
       tc_fence_before();
       fence_proxy_async();
@@ -821,7 +839,7 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
           v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
         }
 #pragma unroll
-        for (int j = 0; j < QC; j += 8) st_row8(sm + G::DX_OFF + buf * G::IMG, row, quarter * QC + j, D, v + j);
+        for (int j = 0; j < QC; j += 8) st_row8<kF16>(sm + G::DX_OFF + buf * G::IMG, row, quarter * QC + j, D, v + j);
       }
       if (tile + gridDim.x < a.tiles) load_nx(tile + gridDim.x);
       ok = wait_ld(s);   // this tile's X image
@@ -878,9 +896,9 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
               qscale, scale, [&](int kind, int r, int c, float v0, float v1) {
                 const int rr = rb + r, col = h * HD + c;
                 if (kind == 0)
-                  *reinterpret_cast<uint32_t *>(sm + G::H_OFF + canon(rr, col, 128)) = pack_bf16(v0, v1);
+                  *reinterpret_cast<uint32_t *>(sm + G::H_OFF + canon(rr, col, 128)) = pack16<kF16>(v0, v1);
                 else
-                  *reinterpret_cast<uint32_t *>(dq_img + canon(rr, (kind - 1) * D + col, 3 * D)) = pack_bf16(v0, v1);
+                  *reinterpret_cast<uint32_t *>(dq_img + canon(rr, (kind - 1) * D + col, 3 * D)) = pack16<kF16>(v0, v1);
               });
         }
       };
@@ -1107,17 +1125,49 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
   sync_finish(s);
 }
 
-// Non-transposed BF16 packing: dst canonical [N][Ktot], element (n, koff + k) = W[n * ldw + col0 + k].
+// Non-transposed 16-bit packing: dst canonical [N][Ktot], element (n, koff + k) = W[n * ldw + col0 + k].
 __global__ void k_pack_nt(const float *__restrict__ W, int ldw, int col0, int K, int N, int Ktot, int koff,
                           uint8_t *__restrict__ dst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N * K) return;
   const int nn = i / K, k = i % K;
-  const __nv_bfloat16 v = __float2bfloat16_rn(W[(size_t)nn * ldw + col0 + k]);
-  *reinterpret_cast<__nv_bfloat16 *>(dst + canon(nn, koff + k, Ktot)) = v;
+  const float w = W[(size_t)nn * ldw + col0 + k];
+  if (kF16) *reinterpret_cast<__half *>(dst + canon(nn, koff + k, Ktot)) = __float2half_rn(w);
+  else *reinterpret_cast<__nv_bfloat16 *>(dst + canon(nn, koff + k, Ktot)) = __float2bfloat16_rn(w);
 }
 
-}  // namespace bwdtc
+// Power-of-two scale of the VJP's cotangents: scale[0] = 2^-e with max_b max(|Re c_b|, |Im c_b|) = m 2^e,
+// m in [0.5, 1) (1 when every cotangent is zero or one is not finite), scale[1] = 1 / scale[0].  Scaled
+// by it, the backward's gradient images sit near the top of the 16-bit range instead of among FP16's
+// subnormals (|c| carries the 2 / Ns of the sample mean); the exact power of two is undone on the sums.
+__global__ void __launch_bounds__(1024) k_cot_scale(const float2 *__restrict__ cot, size_t B, float *__restrict__ scale) {
+  __shared__ float red[32];
+  float m = 0.f;
+  for (size_t b = threadIdx.x; b < B; b += blockDim.x) {
+    const float2 c = cot[b];
+    m = fmaxf(m, fmaxf(fabsf(c.x), fabsf(c.y)));   // a NaN operand is dropped by fmaxf; caught downstream
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      int e = 0;
+      if (m > 0.f && isfinite(m)) {
+        frexpf(m, &e);
+        e = e < -100 ? -100 : (e > 100 ? 100 : e);
+      }
+      scale[0] = ldexpf(1.0f, -e);
+      scale[1] = ldexpf(1.0f, e);
+    }
+  }
+}
+
+}  // namespace TDO_BWNS
 }  // namespace tdo
 
 // ------------------------------------------------------------------------------------- host side
@@ -1128,14 +1178,16 @@ struct BwdTcLayer {
   const uint8_t *wqkvT, *wor, *wqkvr;
 };
 
+#if !TDO_F16   // operand-independent
 size_t bwdtc_packed_bytes(const DevModel &m) {
   const size_t D = m.d, F = m.ffn;
   return (size_t)m.layers * (2 * F * D + D * D + 3 * D * D) * 2;
 }
+#endif
 
-// Row-major (non-transposed) BF16 images for the backward; views per layer into dst.
-cudaError_t launch_pack_bwdtc(const DevModel &m, uint8_t *dst, BwdTcLayer *views, cudaStream_t st) {
-  using namespace tdo::bwdtc;
+// Row-major (non-transposed) 16-bit images for the backward; views per layer into dst.
+cudaError_t TDO_OPFN(launch_pack_bwdtc)(const DevModel &m, uint8_t *dst, BwdTcLayer *views, cudaStream_t st) {
+  using namespace tdo::TDO_BWNS;
   const int D = m.d, F = m.ffn;
   size_t off = 0;
   auto pack = [&](const float *W, int ldw, int col0, int K, int N, int Ktot, int koff, uint8_t *out) {
@@ -1166,15 +1218,18 @@ cudaError_t launch_pack_bwdtc(const DevModel &m, uint8_t *dst, BwdTcLayer *views
   return cudaGetLastError();
 }
 
+#if !TDO_F16
 bool bwdtc_supported(const DevModel &m) {
   return m.d == 64 && (m.dh == 8 || m.dh == 16) && m.heads % 2 == 0 && m.heads <= 16 &&
          (m.ffn == 0 || m.ffn == 128 || m.ffn == 256) && m.embed == 0 && m.n_sites <= 16;
 }
+#endif
 
 struct BwdTcBuffers {
   uint8_t *x, *xmid, *dqkv;
   float *h, *f, *dF, *dxa, *dxb;
   size_t tiles;
+  float *cscale;   // [2]: cotangent scale and its inverse (VJP mode)
 };
 
 // Token-embedding gradient of the VJP: dE[p][c] = sum over the rows whose token is p of dX[row][c], dX the
@@ -1182,7 +1237,7 @@ struct BwdTcBuffers {
 // 4 columns); 4 x 4 register sums per thread (no shared-memory atomics on the 4 hot rows of dE), one
 // block reduction, then float atomics into the block's gradient copy.
 namespace tdo {
-namespace bwdtc {
+namespace TDO_BWNS {
 __global__ void __launch_bounds__(256) k_embed_grad(const float *__restrict__ dX, const uint32_t *__restrict__ sig,
                                                     const uint32_t *__restrict__ sigp, size_t B, int n, int ts,
                                                     size_t tiles, float *__restrict__ g, size_t g_stride,
@@ -1241,7 +1296,7 @@ __global__ void __launch_bounds__(256) k_embed_grad(const float *__restrict__ dX
     atomicAdd(dst, t.x); atomicAdd(dst + 1, t.y); atomicAdd(dst + 2, t.z); atomicAdd(dst + 3, t.w);
   }
 }
-}  // namespace bwdtc
+}  // namespace TDO_BWNS
 }  // namespace tdo
 
 // Output of the per-configuration mode (log-derivatives); nvirt = 0 selects the VJP.
@@ -1252,11 +1307,13 @@ struct BwdTcJac {
   size_t ldo, nvirt;
 };
 
+#if !TDO_F16
 bool bwdtc_jac_supported(const DevModel &m) { return bwdtc_supported(m) && m.n_sites == 16; }
+#endif
 
 // Virtual configurations of the per-configuration mode: v = 2 b + seed, cotangent (1, 0) or (0, -1).
 namespace tdo {
-namespace bwdtc {
+namespace TDO_BWNS {
 __global__ void k_jac_virtual(const uint32_t *__restrict__ sig, const uint32_t *__restrict__ sigp, size_t Ns,
                               uint32_t *__restrict__ vs, uint32_t *__restrict__ vp, float2 *__restrict__ vc) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 2 * Ns; i += gridDim.x * (size_t)blockDim.x) {
@@ -1265,23 +1322,25 @@ __global__ void k_jac_virtual(const uint32_t *__restrict__ sig, const uint32_t *
     vc[i] = (i & 1) ? make_float2(0.f, -1.f) : make_float2(1.f, 0.f);
   }
 }
-}  // namespace bwdtc
+}  // namespace TDO_BWNS
 }  // namespace tdo
 
+#if !TDO_F16
 cudaError_t launch_jac_virtual(const uint32_t *sig, const uint32_t *sigp, size_t Ns, uint32_t *vs, uint32_t *vp,
                                float2 *vc, cudaStream_t st) {
   const unsigned grid = (unsigned)((2 * Ns + 255) / 256 < 4096 ? (2 * Ns + 255) / 256 : 4096);
-  tdo::bwdtc::k_jac_virtual<<<grid ? grid : 1, 256, 0, st>>>(sig, sigp, Ns, vs, vp, vc);
+  tdo::TDO_BWNS::k_jac_virtual<<<grid ? grid : 1, 256, 0, st>>>(sig, sigp, Ns, vs, vp, vc);
   return cudaGetLastError();
 }
+#endif
 
 // The whole tensor-core VJP given the forward's parked activations and the row cotangents; with jac
 // (nvirt > 0) the per-configuration log-derivatives of the virtual configurations instead (gacc unused).
-cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcLayer *views, const BwdTcBuffers &bf,
+cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, const BwdTcLayer *views, const BwdTcBuffers &bf,
                          const uint32_t *sig, const uint32_t *sigp, size_t B, const float2 *cot, float *gacc,
                          size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st,
                          const BwdTcJac *jac) {
-  using namespace tdo::bwdtc;
+  using namespace tdo::TDO_BWNS;
   JacOut jo{nullptr, nullptr, nullptr, 0, 0};
   if (jac) jo = JacOut{jac->o32, jac->o16, jac->oref, jac->ldo, jac->nvirt};
   constexpr int D = 64;
@@ -1293,7 +1352,11 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
   const long long off_e = fo[0], off_wh = fo[1 + 8 * TDO_MAX_LAYERS], off_bh = fo[2 + 8 * TDO_MAX_LAYERS];
   cudaError_t e;
   {
-    HeadArgs h{cot, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, gacc, g_stride, off_wh, off_bh, D, jo};
+    if (!jac) {
+      k_cot_scale<<<1, 1024, 0, st>>>(cot, B, bf.cscale);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    HeadArgs h{cot, jac ? nullptr : bf.cscale, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, gacc, g_stride, off_wh, off_bh, D, jo};
     if (jac) {
       const unsigned grid = (unsigned)((Bpad + 255) / 256 < 1024 ? (Bpad + 255) / 256 : 1024);
       k_head_bwd<<<grid ? grid : 1, 256, (2 * D + 2) * sizeof(float), st>>>(h);

@@ -25,8 +25,23 @@
 #include "tdo_device.cuh"
 #include "tcgen05.cuh"
 
+// TDO_F16 = 1 compiles the same kernels with FP16 operand images and weights (k_fwd_f16.cu), in their own
+// namespace and with launcher names ending in _f16; the default build uses BF16 operands.
+#ifndef TDO_F16
+#define TDO_F16 0
+#endif
+#if TDO_F16
+#define TDO_OPNS f16op
+#define TDO_OPFN(name) name##_f16
+#else
+#define TDO_OPNS bf16
+#define TDO_OPFN(name) name
+#endif
+
 namespace tdo {
-namespace bf16 {
+namespace TDO_OPNS {
+
+constexpr bool kF16 = TDO_F16 != 0;   // operand type of every tensor-core GEMM image and weight
 
 constexpr int kThreads = 256;
 constexpr int kRows = 128;
@@ -73,6 +88,7 @@ struct Ctl {
   bool mma_thread;
   int *err;
   bool bad;
+  long long spin;            // polls of every mbarrier wait before it gives up (kSpinLimit)
 };
 
 // Issue the MMAs of one GEMM: D[tmem + col] (+)= A[128 x K] * B^T, B stored [N][K]; commit to bar_mma.
@@ -80,7 +96,7 @@ __device__ __forceinline__ void gemm(Ctl &c, uint32_t a_addr, uint32_t b_addr, i
                                      bool accumulate, bool f16 = false) {
   if (c.mma_thread) {
     tc_fence_after();
-    const uint32_t id = f16 ? idesc_f16(kRows, N) : idesc_bf16(kRows, N);
+    const uint32_t id = f16 ? idesc_f16(kRows, N) : idesc16<kF16>(kRows, N);
     // descriptor of addr + 256 kk = descriptor of addr + 16 kk (address field addr >> 4, below 256 KB)
     const uint64_t ad = sdesc(a_addr, 128, K * 16), bd = sdesc(b_addr, 128, K * 16);
     for (int kk = 0; kk < K / 16; ++kk)
@@ -90,7 +106,7 @@ __device__ __forceinline__ void gemm(Ctl &c, uint32_t a_addr, uint32_t b_addr, i
 }
 
 __device__ __forceinline__ bool wait_mma(Ctl &c) {
-  const bool ok = mbar_wait(c.bar_mma, c.ph_mma);
+  const bool ok = mbar_wait(c.bar_mma, c.ph_mma, c.spin);
   c.ph_mma ^= 1u;
   tc_fence_after();
   return ok;
@@ -104,7 +120,7 @@ __device__ __forceinline__ void stage_w(Ctl &c, uint32_t w_addr, const void *src
   }
 }
 __device__ __forceinline__ bool wait_w(Ctl &c) {
-  const bool ok = mbar_wait(c.bar_w, c.ph_w);
+  const bool ok = mbar_wait(c.bar_w, c.ph_w, c.spin);
   c.ph_w ^= 1u;
   return ok;
 }
@@ -180,7 +196,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
   }
   stage_w(c, w_addr, mb.Wqkv[0], 3 * D * D * 2);
 #pragma unroll
-  for (int j = 0; j < DH; j += 8) st_row8(A, row, half * DH + j, D, X + j);
+  for (int j = 0; j < DH; j += 8) st_row8<kF16>(A, row, half * DH + j, D, X + j);
 
   const int heads = m.heads;
   const float qscale = rsqrtf((float)HD) * 1.4426950408889634f;   // softmax in base 2
@@ -249,7 +265,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
               Qh + rb * G::LDH + h * HD, Kh + rb * G::LDH + h * HD,
               FULL ? Vt + rb * G::LDH + h * HD : Vt + h * HD * G::LDT + 16 * sq, G::LDH, FULL ? G::LDH : G::LDT, n,
               [&](int r, int cc, float v0, float v1) {
-                *reinterpret_cast<uint32_t *>(A + canon(rb + r, h * HD + cc, D)) = pack_bf16(v0, v1);
+                *reinterpret_cast<uint32_t *>(A + canon(rb + r, h * HD + cc, D)) = pack16<kF16>(v0, v1);
               });
         }
       };
@@ -311,7 +327,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
           for (int e = 0; e < HD; ++e) o[e] *= inv;
         }
 #pragma unroll
-        for (int e8 = 0; e8 < HD; e8 += 8) st_row8(A, row, h * HD + e8, D, o + e8);
+        for (int e8 = 0; e8 < HD; e8 += 8) st_row8<kF16>(A, row, h * HD + e8, D, o + e8);
       }
     }
     }
@@ -334,7 +350,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
       for (int e = 0; e < 16; ++e) X[j + e] += v[e];
     }
 #pragma unroll
-    for (int j = 0; j < DH; j += 8) st_row8(A, row, half * DH + j, D, X + j);
+    for (int j = 0; j < DH; j += 8) st_row8<kF16>(A, row, half * DH + j, D, X + j);
     if (mlp) {
       const int nch = m.ffn / G::HC;
       for (int ch = 0; ch < nch; ++ch) {
@@ -390,7 +406,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
         }
       }
 #pragma unroll
-      for (int j = 0; j < DH; j += 8) st_row8(A, row, half * DH + j, D, X + j);
+      for (int j = 0; j < DH; j += 8) st_row8<kF16>(A, row, half * DH + j, D, X + j);
     }
   }
   // ---------------- pooling, head, symmetrisation (FP32)
@@ -429,10 +445,8 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
   return true;
 }
 
-template <int D>
-__device__ __forceinline__ void ctl_init(Ctl &c, uint8_t *sm, int *err) {
-  using G = Geo<D>;
-  uint8_t *misc = sm + G::M_OFF;
+// Barriers at misc[0, 16), the TMEM address at misc[16, 20); TMEM allocated by warp 0.
+__device__ __forceinline__ void ctl_init_misc(Ctl &c, uint8_t *misc, int *err) {
   c.bar_mma = smem_u32(misc);
   c.bar_w = smem_u32(misc + 8);
   c.ph_mma = 0;
@@ -440,6 +454,7 @@ __device__ __forceinline__ void ctl_init(Ctl &c, uint8_t *sm, int *err) {
   c.mma_thread = threadIdx.x == 0;
   c.err = err;
   c.bad = false;
+  c.spin = kSpinLimit;
   if (threadIdx.x == 0) {
     mbar_init(c.bar_mma, 1);
     mbar_init(c.bar_w, 1);
@@ -456,13 +471,18 @@ __device__ __forceinline__ void ctl_init(Ctl &c, uint8_t *sm, int *err) {
   c.tmem = *reinterpret_cast<volatile uint32_t *>(misc + 16);
 }
 
+template <int D>
+__device__ __forceinline__ void ctl_init(Ctl &c, uint8_t *sm, int *err) {
+  ctl_init_misc(c, sm + Geo<D>::M_OFF, err);
+}
+
 // Free TMEM; after a timeout, first give in-flight MMAs / copies a bounded chance to finish.
 __device__ __forceinline__ void ctl_finish(Ctl &c) {
   if (c.bad) {
     if (threadIdx.x == 0) atomicExch(c.err, 1);
     // bounded drain of whatever the barriers still expect
-    mbar_wait(c.bar_mma, c.ph_mma);
-    mbar_wait(c.bar_w, c.ph_w);
+    mbar_wait(c.bar_mma, c.ph_mma, c.spin);
+    mbar_wait(c.bar_w, c.ph_w, c.spin);
   }
   tc_fence_before();
   __syncthreads();
@@ -471,6 +491,22 @@ __device__ __forceinline__ void ctl_finish(Ctl &c) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem), "r"(kTmemCols));
   }
 }
+
+#if !TDO_F16
+// Self-test of the bounded waits: the control block of the forward (its two mbarriers and its TMEM
+// allocation) with a spin limit given by the caller; the kernel waits for an MMA completion that nothing
+// will signal (no copy and no MMA is ever issued), so the wait gives up after `spin` polls, and the
+// teardown sets *err, drains the barriers (bounded) and frees the TMEM, as after a real timeout.
+__global__ void __launch_bounds__(128) k_wait_probe(int *err, long long spin) {
+  __shared__ __align__(16) uint8_t misc[32];
+  Ctl c;
+  ctl_init_misc(c, misc, err);
+  c.spin = spin;
+  if (!wait_mma(c)) c.bad = true;
+  c.bad = __syncthreads_or(c.bad ? 1 : 0) != 0;
+  ctl_finish(c);
+}
+#endif
 
 template <int D, int HD>
 __global__ void __launch_bounds__(kThreads, 2) k_fwd_bf16(DevModel m, DevModelBF16 mb, const uint32_t *__restrict__ sig,
@@ -583,9 +619,10 @@ __global__ void k_pack(const float *__restrict__ W, int ldw, int col0, int K, in
   else *reinterpret_cast<__nv_bfloat16 *>(dst + canon(n, k, K)) = __float2bfloat16_rn(w);
 }
 
-}  // namespace bf16
+}  // namespace TDO_OPNS
 }  // namespace tdo
 
+#if !TDO_F16   // operand-independent
 bool bf16_supported(const DevModel &m) {
   return (m.d == 64 || m.d == 32) && (m.dh == 8 || m.dh == 16) && m.heads % 2 == 0 && (m.ffn == 0 || m.ffn % (m.d * 4 < 128 ? m.d * 4 : 128) == 0) &&
          m.embed == 0;
@@ -595,15 +632,16 @@ size_t bf16_packed_bytes(const DevModel &m) {
   const size_t D = m.d, F = m.ffn;
   return (size_t)m.layers * (3 * D * D + D * D + 2 * F * D) * 2;
 }
+#endif
 
 // Packs every layer's weights into dst and fills the device views.
-cudaError_t launch_pack_bf16(const DevModel &m, uint16_t *dst16, DevModelBF16 *views, cudaStream_t st) {
-  using namespace tdo::bf16;
+cudaError_t TDO_OPFN(launch_pack_bf16)(const DevModel &m, uint16_t *dst16, DevModelBF16 *views, cudaStream_t st) {
+  using namespace tdo::TDO_OPNS;
   uint8_t *dst = reinterpret_cast<uint8_t *>(dst16);
   const int D = m.d, F = m.ffn;
   const int HC = (4 * D < 128) ? 4 * D : 128;
   size_t off = 0;
-  auto pack = [&](const float *W, int ldw, int col0, int K, int N, uint8_t *out, int f16 = 0) {
+  auto pack = [&](const float *W, int ldw, int col0, int K, int N, uint8_t *out, int f16 = kF16 ? 1 : 0) {
     k_pack<<<(N * K + 255) / 256, 256, 0, st>>>(W, ldw, col0, K, N, out, f16);
   };
   for (int l = 0; l < m.layers; ++l) {
@@ -647,7 +685,7 @@ static int ctas_per_sm(K kernel, int bytes) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  const long long per_cta_regs = (long long)fa.numRegs * tdo::bf16::kThreads;
+  const long long per_cta_regs = (long long)fa.numRegs * tdo::TDO_OPNS::kThreads;
   const long long per_cta_smem = (long long)bytes + (long long)fa.sharedSizeBytes + 1024;
   return (2 * per_cta_regs <= regs && 2 * per_cta_smem <= smem) ? 2 : 1;
 }
@@ -655,8 +693,8 @@ static int ctas_per_sm(K kernel, int bytes) {
 template <int D, int HD>
 static cudaError_t fwd_bf16_impl(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                                  const uint32_t *sigp, size_t B, float2 *out, int *err, int n_sm, cudaStream_t st,
-                                 const tdo::bf16::FwdStore &store) {
-  using namespace tdo::bf16;
+                                 const tdo::TDO_OPNS::FwdStore &store) {
+  using namespace tdo::TDO_OPNS;
   const int bytes = Geo<D>::BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_fwd_bf16<D, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -671,12 +709,12 @@ static cudaError_t fwd_bf16_impl(const DevModel &m, const DevModelBF16 &mb, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_bf16_store(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
+cudaError_t TDO_OPFN(launch_fwd_bf16_store)(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                                   const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
                                   cudaStream_t st, uint8_t *x_img, uint8_t *xmid_img, float *h, float *f,
                                   size_t tiles) {
   if (B == 0) return cudaSuccess;
-  tdo::bf16::FwdStore fs{x_img, xmid_img, h, f, tiles};
+  tdo::TDO_OPNS::FwdStore fs{x_img, xmid_img, h, f, tiles};
   if (m.d == 64 && m.dh == 8) return fwd_bf16_impl<64, 8>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, fs);
   if (m.d == 64 && m.dh == 16) return fwd_bf16_impl<64, 16>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, fs);
   if (m.d == 32 && m.dh == 8) return fwd_bf16_impl<32, 8>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, fs);
@@ -684,9 +722,17 @@ cudaError_t launch_fwd_bf16_store(const DevModel &m, const DevModelBF16 &mb, con
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_fwd_bf16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig, const uint32_t *sigp,
+#if !TDO_F16
+cudaError_t launch_wait_probe(int *err_flag, long long spin, cudaStream_t st) {
+  tdo::bf16::k_wait_probe<<<1, 128, 0, st>>>(err_flag, spin);
+  return cudaGetLastError();
+}
+#endif
+
+cudaError_t TDO_OPFN(launch_fwd_bf16)(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig, const uint32_t *sigp,
                             size_t B, float2 *logrho, int *err_flag, int n_sm, cudaStream_t st) {
-  return launch_fwd_bf16_store(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, nullptr, nullptr, nullptr, nullptr, 0);
+  return TDO_OPFN(launch_fwd_bf16_store)(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, nullptr, nullptr, nullptr,
+                                         nullptr, 0);
 }
 
 template <int D, int HD>
@@ -694,7 +740,7 @@ static cudaError_t sample_bf16_impl(const DevModel &m, const DevModelBF16 &mb, s
                                     uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
                                     uint32_t *ssigp, unsigned long long *accepted, int *err, int diag, int n_sm,
                                     cudaStream_t st) {
-  using namespace tdo::bf16;
+  using namespace tdo::TDO_OPNS;
   const int bytes = Geo<D>::BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_sample_bf16<D, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -710,7 +756,7 @@ static cudaError_t sample_bf16_impl(const DevModel &m, const DevModelBF16 &mb, s
   return cudaGetLastError();
 }
 
-cudaError_t launch_sample_bf16(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
+cudaError_t TDO_OPFN(launch_sample_bf16)(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
                                uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
                                uint32_t *ssigp, unsigned long long *accepted, int *err_flag, int diag, int n_sm,
                                cudaStream_t st) {

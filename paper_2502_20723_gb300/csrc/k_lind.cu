@@ -164,11 +164,12 @@ __global__ void k_cotangent(const int64_t *__restrict__ offs, size_t Ns, const f
 }
 
 __global__ void k_reduce_copies(const float *__restrict__ acc, int n_copies, size_t stride, size_t P,
-                                double *__restrict__ out, int accumulate) {
+                                double *__restrict__ out, int accumulate, const float *__restrict__ scale) {
+  const double f = scale ? (double)*scale : 1.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
-    double a = accumulate ? out[k] : 0.0;
+    double a = 0.0;
     for (int c = 0; c < n_copies; ++c) a += (double)acc[(size_t)c * stride + k];
-    out[k] = a;
+    out[k] = (accumulate ? out[k] : 0.0) + f * a;
   }
 }
 
@@ -215,6 +216,22 @@ __global__ void k_params_f32(const double *__restrict__ theta, size_t P, const l
 __global__ void k_axpy(double *__restrict__ theta, const double *__restrict__ delta, double lr, size_t P) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x)
     theta[k] -= lr * delta[k];
+}
+
+// Adam (Kingma and Ba, Algorithm 1) on the SR direction delta, the optimiser's "gradient": with t the
+// step count after this step, m = b1 m + (1 - b1) delta, v = b2 v + (1 - b2) delta^2,
+// theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).  FP64 throughout.
+__global__ void k_adam(double *__restrict__ theta, const double *__restrict__ delta, double *__restrict__ m,
+                       double *__restrict__ v, size_t P, double lr, double b1, double b2, double eps, double c1,
+                       double c2) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
+    const double d = delta[k];
+    const double mk = b1 * m[k] + (1.0 - b1) * d;
+    const double vk = b2 * v[k] + (1.0 - b2) * d * d;
+    m[k] = mk;
+    v[k] = vk;
+    theta[k] -= lr * (mk / c1) / (sqrt(vk / c2) + eps);
+  }
 }
 
 }  // namespace tdo
@@ -264,8 +281,8 @@ cudaError_t launch_cotangent(const int64_t *offs, size_t Ns, const float2 *fcoef
 }
 
 cudaError_t launch_reduce_copies(const float *acc, int n_copies, size_t stride, size_t P, double *out,
-                                 int accumulate, cudaStream_t st) {
-  tdo::k_reduce_copies<<<grid_for(P, 256), 256, 0, st>>>(acc, n_copies, stride, P, out, accumulate);
+                                 int accumulate, cudaStream_t st, const float *scale) {
+  tdo::k_reduce_copies<<<grid_for(P, 256), 256, 0, st>>>(acc, n_copies, stride, P, out, accumulate, scale);
   return cudaGetLastError();
 }
 
@@ -288,5 +305,12 @@ cudaError_t launch_params_f32(const double *theta, size_t P, const long long *ta
 
 cudaError_t launch_axpy_update(double *theta, const double *delta, double lr, size_t P, cudaStream_t st) {
   tdo::k_axpy<<<grid_for(P, 256), 256, 0, st>>>(theta, delta, lr, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam_update(double *theta, const double *delta, double *m, double *v, size_t P, long long t,
+                               double lr, double b1, double b2, double eps, cudaStream_t st) {
+  const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+  tdo::k_adam<<<grid_for(P, 256), 256, 0, st>>>(theta, delta, m, v, P, lr, b1, b2, eps, c1, c2);
   return cudaGetLastError();
 }

@@ -34,9 +34,11 @@ __device__ __forceinline__ void load4(const uint32_t *p, float2 (&c)[4]) {
 }
 
 enum {
-  S_RZ = 0, S_BN, S_AL, S_RN, S_DONE, S_IT, S_TOL, S_PAP, S_CR, S_CI, S_TR, S_TI, S_COUNT
+  S_RZ = 0, S_BN, S_AL, S_RN, S_DONE, S_IT, S_TOL, S_PAP, S_CR, S_CI, S_TR, S_TI, S_TT, S_COUNT
 };
-// S_DONE: 1 converged, 2 breakdown (S' not positive definite)
+// S_DONE: 1 converged, 2 breakdown (p . S' p not positive: p = 0 before convergence), 3 a non-finite value
+// (in the right-hand side, the log-derivatives' moments or a product)
+enum { SR_CONVERGED = 1, SR_BREAKDOWN = 2, SR_NONFINITE = 3 };
 
 __device__ __forceinline__ double block_sum_d(double v, double *sh) {
   v = warp_sum_d(v);
@@ -58,7 +60,8 @@ __device__ __forceinline__ double sum_parts(const double *part, int n, double *s
   return block_sum_d(a, sh);
 }
 
-// vf = (float) v; block partials of mean . v (re, im)
+// vf = (float) v; block partials of mean . vf (re, im).  The centring term takes the same rounded copy
+// as the t-pass, so t = (O - mean) vf holds up to the products' rounding.
 __global__ void k_sr_vprep(size_t P, const double *__restrict__ v, const double2 *__restrict__ mean,
                            float *__restrict__ vf, double *__restrict__ part, double *__restrict__ part2,
                            const double *__restrict__ sc) {
@@ -66,10 +69,10 @@ __global__ void k_sr_vprep(size_t P, const double *__restrict__ v, const double2
   if (sc[S_DONE] != 0.0) return;
   double cr = 0.0, ci = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
-    const double x = v[k];
-    vf[k] = (float)x;
-    cr += mean[k].x * x;
-    ci += mean[k].y * x;
+    const float xf = (float)v[k];
+    vf[k] = xf;
+    cr += mean[k].x * (double)xf;
+    ci += mean[k].y * (double)xf;
   }
   const double a = block_sum_d(cr, sh);
   const double b = block_sum_d(ci, sh);
@@ -160,15 +163,23 @@ __global__ void k_sr_tred(const double2 *__restrict__ part, int nchunks, size_t 
   }
 }
 
-// T = sum_s t[s]  (zero in exact arithmetic; subtracted explicitly below)
+// T = sum_s t[s] (zero in exact arithmetic; subtracted explicitly below) and sum_s |t[s]|^2, from which
+// p . S' p = (1/Ns) sum_s |t_s - T/Ns|^2 + shift |p|^2 is formed: non-negative by construction, where
+// the dot product of p with the rounded S' p is not once |O| is large against the shift.
 __global__ void k_sr_tsum(const float2 *__restrict__ t, size_t Ns, double *__restrict__ sc) {
   __shared__ double sh[32];
   if (sc[S_DONE] != 0.0) return;
-  double a = 0.0, b = 0.0;
-  for (size_t s = threadIdx.x; s < Ns; s += blockDim.x) { a += t[s].x; b += t[s].y; }
+  double a = 0.0, b = 0.0, q = 0.0;
+  for (size_t s = threadIdx.x; s < Ns; s += blockDim.x) {
+    const double x = t[s].x, y = t[s].y;
+    a += x;
+    b += y;
+    q += x * x + y * y;
+  }
   a = block_sum_d(a, sh);
   b = block_sum_d(b, sh);
-  if (threadIdx.x == 0) { sc[S_TR] = a; sc[S_TI] = b; }
+  q = block_sum_d(q, sh);
+  if (threadIdx.x == 0) { sc[S_TR] = a; sc[S_TI] = b; sc[S_TT] = q; }
 }
 
 // Partial products w = Re(O^H t) over one chunk of parameters and one sample group: block
@@ -352,7 +363,7 @@ __global__ void k_sr_mfin(size_t Ns, size_t P, double shift, const double *__res
   }
 }
 
-// Ap[k] = (1/Ns) [sum_sg wpart[sg][k] - Re(conj(mean[k]) T)] + shift p[k]; partials of p . Ap.
+// Ap[k] = (1/Ns) [sum_sg wpart[sg][k] - Re(conj(mean[k]) T)] + shift p[k]; partials of p . p.
 __global__ void k_sr_wfin(size_t Ns, size_t P, const double2 *__restrict__ mean, const double *__restrict__ wpart,
                           const double *__restrict__ p, double shift, double *__restrict__ Ap,
                           double *__restrict__ part, const double *__restrict__ sc) {
@@ -367,20 +378,31 @@ __global__ void k_sr_wfin(size_t Ns, size_t P, const double2 *__restrict__ mean,
     const double2 m = mean[k];
     const double v = (a - (m.x * Tr + m.y * Ti)) / (double)Ns + shift * p[k];
     Ap[k] = v;
-    loc += v * p[k];
+    loc += p[k] * p[k];
   }
   const double b = block_sum_d(loc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = b;
 }
 
-__global__ void k_sr_alpha(const double *__restrict__ part, int nb, double *__restrict__ sc) {
+// alpha = r.z / p.S'p with p.S'p = (1/Ns) sum_s |t_s - tbar|^2 + shift p.p (the partials hold p.p)
+__global__ void k_sr_alpha(const double *__restrict__ part, int nb, size_t Ns, double shift, double *__restrict__ sc) {
   __shared__ double sh[32];
   if (sc[S_DONE] != 0.0) return;
-  const double pap = sum_parts(part, nb, sh);
+  const double pp = sum_parts(part, nb, sh);
   if (threadIdx.x == 0) {
+    const double n = (double)Ns, Tr = sc[S_TR], Ti = sc[S_TI];
+    const double var = sc[S_TT] - (Tr * Tr + Ti * Ti) / n;   // sum_s |t_s - tbar|^2
+    const double pap = (var > 0.0 ? var : 0.0) / n + shift * pp;
     sc[S_PAP] = pap;
-    sc[S_AL] = (pap > 0.0) ? sc[S_RZ] / pap : 0.0;
-    if (!(pap > 0.0)) sc[S_DONE] = 2.0;   // breakdown (S' must be positive definite)
+    if (!isfinite(pap) || !isfinite(sc[S_RZ])) {
+      sc[S_AL] = 0.0;
+      sc[S_DONE] = SR_NONFINITE;
+    } else if (!(pap > 0.0)) {
+      sc[S_AL] = 0.0;
+      sc[S_DONE] = SR_BREAKDOWN;
+    } else {
+      sc[S_AL] = sc[S_RZ] / pap;
+    }
   }
 }
 
@@ -418,7 +440,8 @@ __global__ void k_sr_beta(const double *__restrict__ part, const double *__restr
     sc[S_RN] = rr;
     sc[S_AL] = (sc[S_RZ] != 0.0) ? rz / sc[S_RZ] : 0.0;   // beta (alpha slot reused)
     sc[S_RZ] = rz;
-    if (rr <= sc[S_TOL] * sc[S_BN]) sc[S_DONE] = 1.0;
+    if (!isfinite(rr) || !isfinite(rz)) sc[S_DONE] = SR_NONFINITE;
+    else if (rr <= sc[S_TOL] * sc[S_BN]) sc[S_DONE] = SR_CONVERGED;
   }
 }
 
@@ -469,7 +492,8 @@ __global__ void k_sr_init_scalars(const double *__restrict__ part, const double 
     sc[S_IT] = 0.0;
     sc[S_TOL] = tol * tol;
     sc[S_PAP] = 0.0;
-    sc[S_DONE] = (rr <= tol * tol * bb) ? 1.0 : 0.0;
+    if (!isfinite(rr) || !isfinite(rz) || !isfinite(bb)) sc[S_DONE] = SR_NONFINITE;
+    else sc[S_DONE] = (rr <= tol * tol * bb) ? SR_CONVERGED : 0.0;
   }
 }
 
@@ -551,6 +575,7 @@ template <typename OT>
 static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const double *rhs, const double *x0,
                            double shift,
                            double tol, int max_iter, double *x, double *work, int *iters, double *resid,
+                           int *outcome, double *last_pap,
                            long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used, cudaStream_t st) {
   SrPtrs q = sr_carve(work, Ns, P);
   int nb = (int)((P + kSrBlock - 1) / kSrBlock);
@@ -599,7 +624,7 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const 
     const int end = it + group < max_iter ? it + group : max_iter;
     for (; it < end; ++it) {
       if ((e = mv(q.p)) != cudaSuccess) return e;
-      k_sr_alpha<<<1, 1024, 0, st>>>(q.part, nb, q.sc);
+      k_sr_alpha<<<1, 1024, 0, st>>>(q.part, nb, Ns, shift, q.sc);
       k_sr_xr<<<nb, kSrBlock, 0, st>>>(P, x, q.r, q.z, q.p, q.Ap, q.diag, q.part, q.part2, q.sc);
       k_sr_beta<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
       k_sr_p<<<nb, kSrBlock, 0, st>>>(P, q.p, q.z, q.sc);
@@ -621,26 +646,29 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const 
   }
   if (iters) *iters = (int)h[S_IT];
   if (mv_used) {   // launches after convergence returned at once: keep the pairs of real products only
-    const int real = (x0 ? 1 : 0) + (int)h[S_IT] + (h[S_DONE] == 1.0 ? 0 : 1);
+    const int real = (x0 ? 1 : 0) + (int)h[S_IT] + (h[S_DONE] == (double)SR_CONVERGED ? 0 : 1);
     if (*mv_used > real) *mv_used = real;
   }
   if (resid) *resid = h[S_BN] > 0 ? sqrt(h[S_RN] / h[S_BN]) : 0.0;
   if (launches) *launches = nl;
-  if (h[S_DONE] == 2.0) return cudaErrorInvalidValue;   // not positive definite
+  if (outcome) *outcome = (int)h[S_DONE];
+  if (last_pap) *last_pap = h[S_PAP];
   return cudaSuccess;
 }
 }  // namespace tdo
 
 // mv_ev (optional): mv_cap event pairs recorded around the S' v launches; *mv_used = pairs recorded.
 // o_bf16: O holds BF16 pairs (uint32 per element) instead of FP32 (re, im); ldo >= P: elements per row.
+// *outcome: 0 stopped at max_iter, 1 converged, 2 breakdown (p . S'p not positive), 3 a non-finite value;
+// *last_pap: the last p . S'p.  The return value reports CUDA errors only.
 cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, size_t ldo, const double *rhs, const double *x0,
                        double shift, double tol, int max_iter, double *x, double *work, int n_sm, int *iters,
-                       double *resid, long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used,
-                       cudaStream_t st) {
+                       double *resid, int *outcome, double *last_pap, long long *launches, cudaEvent_t *mv_ev,
+                       int mv_cap, int *mv_used, cudaStream_t st) {
   (void)n_sm;
   if (o_bf16)
     return tdo::sr_cg_t(reinterpret_cast<const uint32_t *>(O), Ns, P, ldo, rhs, x0, shift, tol, max_iter, x, work, iters,
-                        resid, launches, mv_ev, mv_cap, mv_used, st);
+                        resid, outcome, last_pap, launches, mv_ev, mv_cap, mv_used, st);
   return tdo::sr_cg_t(reinterpret_cast<const float2 *>(O), Ns, P, ldo, rhs, x0, shift, tol, max_iter, x, work, iters,
-                      resid, launches, mv_ev, mv_cap, mv_used, st);
+                      resid, outcome, last_pap, launches, mv_ev, mv_cap, mv_used, st);
 }

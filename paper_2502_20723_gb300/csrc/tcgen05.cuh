@@ -31,9 +31,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t phase) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with parity `phase` to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t phase) {
-  for (long long i = 0; i < kSpinLimit; ++i) {
+// Bounded wait for the phase with parity `phase` to complete; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t phase, long long limit = kSpinLimit) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try(a, phase)) return true;
     if (i > 64) __nanosleep(32);
   }
@@ -177,13 +177,33 @@ __host__ __device__ __forceinline__ uint32_t canon(int row, int k, int K) {
   return (uint32_t)((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// Store 8 consecutive k values (k0 % 8 == 0) of one row as BF16 (one 16-byte store).
+__device__ __forceinline__ uint32_t pack_f16(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+// The 16-bit operand type of the tensor-core GEMM images: FP16 (F16) or BF16.  Both keep FP32
+// accumulation; FP16 has three more mantissa bits, BF16 the FP32 exponent range.
+template <bool F16>
+__device__ __forceinline__ uint32_t pack16(float a, float b) {
+  return F16 ? pack_f16(a, b) : pack_bf16(a, b);
+}
+template <bool F16>
+__host__ __device__ constexpr uint32_t idesc16(int M, int N) {
+  return F16 ? idesc_f16(M, N) : idesc_bf16(M, N);
+}
+template <bool F16>
+constexpr uint32_t kOnePair = F16 ? 0x3C003C00u : 0x3F803F80u;   // two 1.0 values
+
+// Store 8 consecutive k values (k0 % 8 == 0) of one row as 16-bit operands (one 16-byte store).
+template <bool F16>
 __device__ __forceinline__ void st_row8(uint8_t *base, int row, int k0, int K, const float *v) {
   uint4 q;
-  q.x = pack_bf16(v[0], v[1]);
-  q.y = pack_bf16(v[2], v[3]);
-  q.z = pack_bf16(v[4], v[5]);
-  q.w = pack_bf16(v[6], v[7]);
+  q.x = pack16<F16>(v[0], v[1]);
+  q.y = pack16<F16>(v[2], v[3]);
+  q.z = pack16<F16>(v[4], v[5]);
+  q.w = pack16<F16>(v[6], v[7]);
   *reinterpret_cast<uint4 *>(base + canon(row, k0, K)) = q;
 }
 
@@ -192,6 +212,10 @@ __device__ __forceinline__ void st_row8(uint8_t *base, int row, int k0, int K, c
 // bit 16: B MN-major).
 __host__ __device__ constexpr uint32_t idesc_bf16_major(int M, int N, int a_mn, int b_mn) {
   return idesc_bf16(M, N) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16);
+}
+template <bool F16>
+__host__ __device__ constexpr uint32_t idesc16_major(int M, int N, int a_mn, int b_mn) {
+  return idesc16<F16>(M, N) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16);
 }
 
 }  // namespace tc

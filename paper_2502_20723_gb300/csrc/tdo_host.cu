@@ -34,10 +34,11 @@ cudaError_t launch_conv_vjp(int d, int c1, const float *Wc1, const float *bc1, c
                             const float2 *oref, size_t ldo, long long o_wc1, long long o_bc1, long long o_wc2,
                             long long o_bc2, cudaStream_t st);
 size_t sr_work_doubles(size_t Ns, size_t P);
+cudaError_t measure_fma_peak(int fp64, int n_sm, cudaStream_t st, double *tflops);
 cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, size_t ldo, const double *rhs, const double *x0,
                        double shift, double tol, int max_iter, double *x, double *work, int n_sm, int *iters,
-                       double *resid, long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used,
-                       cudaStream_t st);
+                       double *resid, int *outcome, double *last_pap, long long *launches, cudaEvent_t *mv_ev,
+                       int mv_cap, int *mv_used, cudaStream_t st);
 cudaError_t launch_params_f32(const double *theta, size_t P, const long long *tab, int n_tensors,
                               float *dst, cudaStream_t st);
 size_t bf16_packed_bytes(const DevModel &m);
@@ -49,10 +50,12 @@ struct BwdTcBuffers {
   uint8_t *x, *xmid, *dqkv;
   float *h, *f, *dF, *dxa, *dxb;
   size_t tiles;
+  float *cscale;   // [2]: cotangent scale and its inverse (VJP mode)
 };
 size_t bwdtc_packed_bytes(const DevModel &m);
 bool bwdtc_supported(const DevModel &m);
 cudaError_t launch_pack_bwdtc(const DevModel &m, uint8_t *dst, BwdTcLayer *views, cudaStream_t st);
+cudaError_t launch_pack_bwdtc_f16(const DevModel &m, uint8_t *dst, BwdTcLayer *views, cudaStream_t st);
 struct BwdTcJac {
   float *o32;
   uint16_t *o16;
@@ -66,10 +69,20 @@ cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcL
                          const uint32_t *sig, const uint32_t *sigp, size_t B, const float2 *cot, float *gacc,
                          size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st,
                          const BwdTcJac *jac = nullptr);
+cudaError_t launch_bwdtc_f16(const DevModel &m, const DevModelBF16 &mb, const BwdTcLayer *views,
+                             const BwdTcBuffers &bf, const uint32_t *sig, const uint32_t *sigp, size_t B,
+                             const float2 *cot, float *gacc, size_t g_stride, const long long *fo, int *err, int n_sm,
+                             cudaStream_t st, const BwdTcJac *jac = nullptr);
 cudaError_t launch_fwd_bf16_store(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                                   const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
                                   cudaStream_t st, uint8_t *x_img, uint8_t *xmid_img, float *h, float *f,
                                   size_t tiles);
+cudaError_t launch_fwd_bf16_store_f16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
+                                      const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
+                                      cudaStream_t st, uint8_t *x_img, uint8_t *xmid_img, float *h, float *f,
+                                      size_t tiles);
+// A tensor-core launcher of the context's operand type: fn (BF16) or fn_f16 (FP16).
+#define TC_LAUNCH(c, fn, ...) ((c)->f16 ? fn##_f16(__VA_ARGS__) : fn(__VA_ARGS__))
 
 namespace {
 
@@ -123,19 +136,29 @@ struct tdo_ctx {
   DBuf obs_rs, obs_rp, obs_lr, obs_part, obs_out, obs_local;   // observables and purity
   DevModel dm{};
   DevModelBF16 dmb{};
-  bool tc_bwd = false;                 // tensor-core gradient (BF16 contexts whose shape it supports)
+  bool tc = false;                     // tensor-core path (TDO_BF16 or TDO_FP16 contexts)
+  bool f16 = false;                    // its operands are FP16 (TDO_FP16) rather than BF16
+  bool tc_bwd = false;                 // tensor-core gradient (tensor-core contexts whose shape it supports)
   BwdTcLayer bwl[TDO_MAX_LAYERS];
   DBuf act_x, act_xmid, act_h, act_f, act_dF, act_dxa, act_dxb, act_dqkv;
   // workspace
   DBuf stage_in[4], stage_out;
   DBuf conn_cnt, conn_sig, conn_sigp, conn_coef, offs, fsig, fsigp, fcoef, flr, lloc, l2, stats,
-      nonfinite, cot, gacc, scratch, grad, Obuf, srwork, delta, acc_u64;
+      nonfinite, cot, gacc, scratch, grad, Obuf, srwork, delta, acc_u64, cscale;
   std::string err;
   double sr_tol = 1e-6;
   int sr_max_iter = 100;
+  // optimiser applied to the SR direction: TDO_OPT_SGD (theta -= lr delta) or TDO_OPT_ADAM
+  int opt = TDO_OPT_SGD;
+  double adam_b1 = 0.9, adam_b2 = 0.999, adam_eps = 1e-8;
+  long long adam_t = 0;
+  DBuf adam_m, adam_v;
   bool have_delta = false;
   int last_sr_iters = 0;
   double last_sr_resid = 0;
+  int last_sr_outcome = 0;      // 0 max_iter reached, 1 converged, 2 breakdown, 3 non-finite
+  double last_sr_pap = 0;       // last p . S'p of the solve
+  int last_sr_restarts = 0;     // 1 when the warm-started solve failed and was rerun from x = 0
   // kernel timing (tdo_timing)
   bool timing = false;
   std::vector<TimingRec> trec;
@@ -199,7 +222,10 @@ static bool model_valid(const tdo_model *m, std::string *why) {
   if (m->mlp_ratio < 0 || m->mlp_ratio > 4) { *why = "mlp_ratio must be 0..4"; return false; }
   if (m->embed != TDO_EMBED_TOKEN && m->embed != TDO_EMBED_CONV) { *why = "unknown embedding"; return false; }
   if (m->embed == TDO_EMBED_CONV && (m->conv_channels < 1 || m->conv_channels > 256)) { *why = "conv_channels must be 1..256"; return false; }
-  if (m->precision != TDO_FP32 && m->precision != TDO_BF16) { *why = "unknown precision"; return false; }
+  if (m->precision != TDO_FP32 && m->precision != TDO_BF16 && m->precision != TDO_FP16) {
+    *why = "unknown precision";
+    return false;
+  }
   return true;
 }
 
@@ -398,14 +424,14 @@ static tdo_status refresh_params(tdo_ctx *c) {
     CU(c, launch_conv_table_k(m->d_model, m->conv_channels, b + c->tensors[0].pad, b + c->tensors[1].pad,
                               b + c->tensors[2].pad, b + c->tensors[3].pad, c->etab.as<float>(), c->stream));
   }
-  if (m->precision == TDO_BF16) CU(c, launch_pack_bf16(c->dm, c->wbf16.as<uint16_t>(), &c->dmb, c->stream));
-  if (c->tc_bwd) CU(c, launch_pack_bwdtc(c->dm, c->wbwd.as<uint8_t>(), c->bwl, c->stream));
+  if (c->tc) CU(c, TC_LAUNCH(c, launch_pack_bf16, c->dm, c->wbf16.as<uint16_t>(), &c->dmb, c->stream));
+  if (c->tc_bwd) CU(c, TC_LAUNCH(c, launch_pack_bwdtc, c->dm, c->wbwd.as<uint8_t>(), c->bwl, c->stream));
   return TDO_OK;
 }
 
-// Reports (and clears) a timeout flagged by a BF16 kernel's bounded waits.
+// Reports (and clears) a timeout flagged by a tensor-core kernel's bounded waits.
 static tdo_status check_err_flag(tdo_ctx *c) {
-  if (c->model.precision != TDO_BF16) return TDO_OK;
+  if (!c->tc) return TDO_OK;
   int f = 0;
   CU(c, cudaMemcpyAsync(&f, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaStreamSynchronize(c->stream));
@@ -466,13 +492,15 @@ extern "C" tdo_status tdo_create(const tdo_problem *problem, const tdo_model *mo
   if ((problem->n_terms > 0 && (!problem->term_sites || !problem->term_paulis || !problem->term_coef)) ||
       (problem->n_jumps > 0 && (!problem->jump_site || !problem->jump_op || !problem->jump_rate)))
     return fail(nullptr, TDO_EINVAL, "problem arrays are NULL");
-  if (model->precision == TDO_BF16 && model->embed != TDO_EMBED_TOKEN)
-    return fail(nullptr, TDO_EUNSUPPORTED, "the BF16 path supports the token embedding");
+  if (model->precision != TDO_FP32 && model->embed != TDO_EMBED_TOKEN)
+    return fail(nullptr, TDO_EUNSUPPORTED, "the tensor-core (BF16 / FP16) path supports the token embedding");
   const size_t P = tdo_model_num_params(model);
   if (!theta || n_theta != P) return fail(nullptr, TDO_EINVAL, "theta must hold %zu values (got %zu)", P, n_theta);
 
   tdo_ctx *c = new tdo_ctx();
   c->model = *model;
+  c->tc = model->precision == TDO_BF16 || model->precision == TDO_FP16;
+  c->f16 = model->precision == TDO_FP16;
   c->n = problem->n_sites;
   c->stream = (cudaStream_t)stream;
   auto bail = [&](tdo_status s) {
@@ -504,13 +532,14 @@ extern "C" tdo_status tdo_create(const tdo_problem *problem, const tdo_model *mo
     return bail(TDO_ECUDA);
   }
   build_devmodel(c);
-  if (model->precision == TDO_BF16) {
+  if (c->tc) {
     if (!bf16_supported(c->dm)) {
-      fail(c, TDO_EUNSUPPORTED, "BF16 path: d_model 32 or 64, head dim a multiple of 8, an even head count, "
-                                 "MLP width a multiple of min(4 d_model, 128)");
+      fail(c, TDO_EUNSUPPORTED, "tensor-core path: d_model 32 or 64, head dim a multiple of 8, an even head "
+                                 "count, MLP width a multiple of min(4 d_model, 128)");
       return bail(TDO_EUNSUPPORTED);
     }
     if ((e = c->wbf16.ensure(bf16_packed_bytes(c->dm))) != cudaSuccess ||
+        (e = c->cscale.ensure(2 * sizeof(float))) != cudaSuccess ||
         (e = c->errflag.ensure(sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(c->errflag.p, 0, sizeof(int))) != cudaSuccess) {
       fail(c, TDO_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
@@ -573,8 +602,8 @@ extern "C" tdo_status tdo_get_params(tdo_ctx *c, double *theta) {
 static tdo_status forward_dev(tdo_ctx *c, const uint32_t *sig, const uint32_t *sigp, size_t B, float2 *out) {
   if (B == 0) return TDO_OK;
   Timed tm(c, G_FWD);
-  if (c->model.precision == TDO_BF16)
-    CU(c, launch_fwd_bf16(c->dm, c->dmb, sig, sigp, B, out, c->errflag.as<int>(), c->n_sm, c->stream));
+  if (c->tc)
+    CU(c, TC_LAUNCH(c, launch_fwd_bf16, c->dm, c->dmb, sig, sigp, B, out, c->errflag.as<int>(), c->n_sm, c->stream));
   else
     CU(c, launch_fwd32(c->dm, sig, sigp, B, out, c->n_sm, c->stream));
   return TDO_OK;
@@ -852,7 +881,7 @@ static tdo_status forward_park(tdo_ctx *c, const uint32_t *sig, const uint32_t *
   CU(c, c->act_h.ensure(sizeof(float) * tiles * ts * c->dm.d));
   CU(c, c->act_f.ensure(sizeof(float) * tiles * ts * 2));
   Timed tm(c, G_FWD);
-  CU(c, launch_fwd_bf16_store(c->dm, c->dmb, sig, sigp, B, out, c->errflag.as<int>(), c->n_sm, c->stream,
+  CU(c, TC_LAUNCH(c, launch_fwd_bf16_store, c->dm, c->dmb, sig, sigp, B, out, c->errflag.as<int>(), c->n_sm, c->stream,
                               c->act_x.as<uint8_t>(), c->dm.ffn > 0 ? c->act_xmid.as<uint8_t>() : nullptr,
                               c->act_h.as<float>(), c->act_f.as<float>(), tiles));
   return TDO_OK;
@@ -873,11 +902,12 @@ static tdo_status vjp_tc(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp, siz
   CU(c, c->gacc.ensure(sizeof(float) * copies * stride));
   CU(c, cudaMemsetAsync(c->gacc.p, 0, sizeof(float) * copies * stride, c->stream));
   BwdTcBuffers bf{c->act_x.as<uint8_t>(), c->act_xmid.as<uint8_t>(), c->act_dqkv.as<uint8_t>(), c->act_h.as<float>(),
-                  c->act_f.as<float>(), c->act_dF.as<float>(), c->act_dxa.as<float>(), c->act_dxb.as<float>(), tiles};
+                  c->act_f.as<float>(), c->act_dF.as<float>(), c->act_dxa.as<float>(), c->act_dxb.as<float>(), tiles,
+                  c->cscale.as<float>()};
   Timed tm(c, G_BWD_VJP);
-  CU(c, launch_bwdtc(c->dm, c->dmb, c->bwl, bf, ds, dp, B, cot, c->gacc.as<float>(), stride, c->flat_offsets,
+  CU(c, TC_LAUNCH(c, launch_bwdtc, c->dm, c->dmb, c->bwl, bf, ds, dp, B, cot, c->gacc.as<float>(), stride, c->flat_offsets,
                      c->errflag.as<int>(), c->n_sm, c->stream));
-  CU(c, launch_reduce_copies(c->gacc.as<float>(), copies, stride, c->P, grad, 0, c->stream));
+  CU(c, launch_reduce_copies(c->gacc.as<float>(), copies, stride, c->P, grad, 0, c->stream, c->cscale.as<float>() + 1));
   tm.done(2 + (long long)c->dm.layers * (2 + (c->dm.ffn > 0 ? c->dm.ffn / 128 : 0)) + 2);
   return TDO_OK;
 }
@@ -906,13 +936,14 @@ static tdo_status jacobian_tc(tdo_ctx *c, const uint32_t *ds, const uint32_t *dp
   uint32_t *vs = c->jac_vs.as<uint32_t>(), *vp = c->jac_vp.as<uint32_t>();
   Timed tm(c, G_BWD_JAC);
   CU(c, launch_jac_virtual(ds, dp, Ns, vs, vp, c->jac_vc.as<float2>(), c->stream));
-  CU(c, launch_fwd_bf16_store(c->dm, c->dmb, vs, vp, nv, c->jac_lr.as<float2>(), c->errflag.as<int>(), c->n_sm,
+  CU(c, TC_LAUNCH(c, launch_fwd_bf16_store, c->dm, c->dmb, vs, vp, nv, c->jac_lr.as<float2>(), c->errflag.as<int>(), c->n_sm,
                               c->stream, c->act_x.as<uint8_t>(), c->dm.ffn > 0 ? c->act_xmid.as<uint8_t>() : nullptr,
                               c->act_h.as<float>(), c->act_f.as<float>(), tiles));
   BwdTcBuffers bf{c->act_x.as<uint8_t>(), c->act_xmid.as<uint8_t>(), c->act_dqkv.as<uint8_t>(), c->act_h.as<float>(),
-                  c->act_f.as<float>(), c->act_dF.as<float>(), c->act_dxa.as<float>(), c->act_dxb.as<float>(), tiles};
+                  c->act_f.as<float>(), c->act_dF.as<float>(), c->act_dxa.as<float>(), c->act_dxb.as<float>(), tiles,
+                  c->cscale.as<float>()};
   BwdTcJac jac{O32, O16, oref, ldo, nv};
-  CU(c, launch_bwdtc(c->dm, c->dmb, c->bwl, bf, vs, vp, nv, c->jac_vc.as<float2>(), nullptr, 0, c->flat_offsets,
+  CU(c, TC_LAUNCH(c, launch_bwdtc, c->dm, c->dmb, c->bwl, bf, vs, vp, nv, c->jac_vc.as<float2>(), nullptr, 0, c->flat_offsets,
                      c->errflag.as<int>(), c->n_sm, c->stream, &jac));
   tm.done(4 + (long long)c->dm.layers * (2 + (c->dm.ffn > 0 ? c->dm.ffn / 128 : 0)));
   TRY(check_err_flag(c));
@@ -966,7 +997,7 @@ extern "C" tdo_status tdo_grad(tdo_ctx *c, const uint32_t *sig, const uint32_t *
 static cudaError_t sr_cg_timed(tdo_ctx *c, const void *O, int o_bf16, size_t ldo, size_t Ns, const double *rhs,
                                const double *x0,
                                double shift, double tol, int max_iter, double *x, int *iters, double *resid,
-                               long long *launches) {
+                               int *outcome, double *last_pap, long long *launches) {
   std::vector<cudaEvent_t> ev;
   if (c->timing) {
     const int n = 2 * (max_iter + 1);
@@ -979,13 +1010,23 @@ static cudaError_t sr_cg_timed(tdo_ctx *c, const void *O, int o_bf16, size_t ldo
   }
   int used = 0;
   const cudaError_t err = sr_cg_impl(O, o_bf16, Ns, c->P, ldo, rhs, x0, shift, tol, max_iter, x, c->srwork.as<double>(), c->n_sm,
-                                     iters, resid, launches, ev.empty() ? nullptr : ev.data(), (int)ev.size() / 2,
-                                     &used, c->stream);
+                                     iters, resid, outcome, last_pap, launches, ev.empty() ? nullptr : ev.data(),
+                                     (int)ev.size() / 2, &used, c->stream);
   for (int i = 0; i < (int)ev.size(); ++i) {
     if (i / 2 < used && i % 2 == 0) c->trec.push_back({G_SR_MV, ev[i], ev[i + 1], 1});
     else if (i / 2 >= used) c->epool.push_back(ev[i]);
   }
   return err;
+}
+
+// Status of a finished CG solve: a breakdown (p . S'p not positive before convergence, only possible
+// for p = 0) or a non-finite value (gradient, log-derivatives, or a product) are TDO_ENUMERIC, each with
+// its own message; stopping at max_iter is not an error (tdo_sr_info reports it).
+static tdo_status sr_outcome_status(tdo_ctx *c, int outcome) {
+  if (outcome == 3)
+    return fail(c, TDO_ENUMERIC, "SR solve: non-finite value (NaN or Inf in the gradient, the log-derivatives or a product)");
+  if (outcome == 2) return fail(c, TDO_ENUMERIC, "SR solve: CG breakdown (p . (S + shift I) p not positive)");
+  return TDO_OK;
 }
 
 extern "C" tdo_status tdo_sr_solve(tdo_ctx *c, const float *O, size_t Ns, const double *rhs, double diag_shift,
@@ -1002,14 +1043,15 @@ extern "C" tdo_status tdo_sr_solve(tdo_ctx *c, const float *O, size_t Ns, const 
   if (!is_device_ptr(x)) { CU(c, c->delta.ensure(sizeof(double) * c->P)); dx = c->delta.as<double>(); }
   CU(c, c->srwork.ensure(sizeof(double) * sr_work_doubles(Ns, c->P)));
   Timed tm(c, G_SR);
-  int it_local = 0;
+  int it_local = 0, outcome = 0;
   long long nl = 0;
+  double pap = 0;
   cudaError_t e = sr_cg_timed(c, dO, 0, c->P, Ns, (const double *)dr, nullptr, diag_shift, tol, max_iter, dx,
-                              &it_local, resid, &nl);
+                              &it_local, resid, &outcome, &pap, &nl);
   if (iters) *iters = it_local;
   tm.done(nl);
-  if (e == cudaErrorInvalidValue) return fail(c, TDO_ENUMERIC, "CG breakdown: S + shift I is not positive definite");
   CU(c, e);
+  TRY(sr_outcome_status(c, outcome));
   TRY(deliver(c, x, dx, sizeof(double) * c->P, &h3));
   CU(c, cudaStreamSynchronize(c->stream));
   return TDO_OK;
@@ -1027,32 +1069,49 @@ extern "C" tdo_status tdo_sr_step(tdo_ctx *c, const uint32_t *sig, const uint32_
   TRY(stage_in(c, 1, sigp, 4 * Ns, &dp, &h2));
   CU(c, c->grad.ensure(sizeof(double) * c->P));
   CU(c, c->delta.ensure(sizeof(double) * c->P));
-  const int o_bf16 = c->model.precision == TDO_BF16 ? 1 : 0;   // SR's O in BF16 for BF16 contexts
+  const int o_bf16 = c->tc ? 1 : 0;   // SR's O in BF16 for tensor-core contexts
   const size_t ldo = o_bf16 ? (c->P + 3) / 4 * 4 : (c->P + 1) / 2 * 2;   // rows on 16-byte boundaries
   CU(c, c->Obuf.ensure((o_bf16 ? sizeof(uint16_t) : sizeof(float)) * 2 * ldo * Ns));
   TRY(grad_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, c->grad.as<double>(), cost));
   if (o_bf16) TRY(jacobian_bf16_for_sr(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, ldo));
   else TRY(jacobian_dev(c, (const uint32_t *)ds, (const uint32_t *)dp, Ns, c->Obuf.as<float>(), nullptr, nullptr, ldo));
   CU(c, c->srwork.ensure(sizeof(double) * sr_work_doubles(Ns, c->P)));
-  int iters = 0;
-  double resid = 0;
+  int iters = 0, outcome = 0, restarts = 0;
+  double resid = 0, pap = 0;
   cudaError_t e;
   {
-    // warm start from the previous step's solution (same parameter layout)
+    // warm start from the previous step's solution (same parameter layout); if that solve breaks down or
+    // meets a non-finite value, solve once more from x = 0 before reporting the failure
     Timed tm(c, G_SR);
-    long long nl = 0;
-    e = sr_cg_timed(c, c->Obuf.p, o_bf16, ldo, Ns, c->grad.as<double>(), c->have_delta ? c->delta.as<double>() : nullptr,
-                    diag_shift, c->sr_tol, c->sr_max_iter, c->delta.as<double>(), &iters, &resid, &nl);
-    tm.done(nl);
+    long long nl = 0, nl2 = 0;
+    const bool warm = c->have_delta;
+    e = sr_cg_timed(c, c->Obuf.p, o_bf16, ldo, Ns, c->grad.as<double>(), warm ? c->delta.as<double>() : nullptr,
+                    diag_shift, c->sr_tol, c->sr_max_iter, c->delta.as<double>(), &iters, &resid, &outcome, &pap, &nl);
+    if (e == cudaSuccess && warm && (outcome == 2 || outcome == 3)) {
+      restarts = 1;
+      e = sr_cg_timed(c, c->Obuf.p, o_bf16, ldo, Ns, c->grad.as<double>(), nullptr, diag_shift, c->sr_tol,
+                      c->sr_max_iter, c->delta.as<double>(), &iters, &resid, &outcome, &pap, &nl2);
+    }
+    tm.done(nl + nl2);
   }
-  c->have_delta = (e == cudaSuccess);
+  c->have_delta = (e == cudaSuccess && (outcome == 0 || outcome == 1));
   c->last_sr_iters = iters;
   c->last_sr_resid = resid;
-  if (e == cudaErrorInvalidValue) return fail(c, TDO_ENUMERIC, "CG breakdown: S + shift I is not positive definite");
+  c->last_sr_outcome = outcome;
+  c->last_sr_pap = pap;
+  c->last_sr_restarts = restarts;
   CU(c, e);
+  TRY(sr_outcome_status(c, outcome));
   {
     Timed tm(c, G_UPDATE);
-    CU(c, launch_axpy_update(c->theta64.as<double>(), c->delta.as<double>(), lr, c->P, c->stream));
+    if (c->opt == TDO_OPT_ADAM) {
+      c->adam_t += 1;
+      CU(c, launch_adam_update(c->theta64.as<double>(), c->delta.as<double>(), c->adam_m.as<double>(),
+                               c->adam_v.as<double>(), c->P, c->adam_t, lr, c->adam_b1, c->adam_b2, c->adam_eps,
+                               c->stream));
+    } else {
+      CU(c, launch_axpy_update(c->theta64.as<double>(), c->delta.as<double>(), lr, c->P, c->stream));
+    }
     TRY(refresh_params(c));
     tm.done(c->model.embed == TDO_EMBED_CONV ? 3 : 2);
   }
@@ -1082,9 +1141,9 @@ static tdo_status sample_impl(tdo_ctx *c, size_t n_chains, size_t n_sweeps, uint
   CU(c, c->acc_u64.ensure(sizeof(unsigned long long)));
   CU(c, cudaMemsetAsync(c->acc_u64.p, 0, sizeof(unsigned long long), c->stream));
   Timed tm(c, G_SAMPLE);
-  if (c->model.precision == TDO_BF16)
-    CU(c, launch_sample_bf16(c->dm, c->dmb, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
-                             c->acc_u64.as<unsigned long long>(), c->errflag.as<int>(), diag, c->n_sm, c->stream));
+  if (c->tc)
+    CU(c, TC_LAUNCH(c, launch_sample_bf16, c->dm, c->dmb, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
+                    c->acc_u64.as<unsigned long long>(), c->errflag.as<int>(), diag, c->n_sm, c->stream));
   else
     CU(c, launch_sample32(c->dm, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
                           c->acc_u64.as<unsigned long long>(), diag, c->n_sm, c->stream));
@@ -1245,6 +1304,25 @@ extern "C" tdo_status tdo_vmc_step(tdo_ctx *c, uint32_t *sig, uint32_t *sigp, si
   return tdo_sr_step(c, sig, sigp, n_chains, lr, shift, cost);
 }
 
+extern "C" tdo_status tdo_set_optimizer(tdo_ctx *c, int kind, double beta1, double beta2, double eps) {
+  if (!c) return TDO_EINVAL;
+  if (kind != TDO_OPT_SGD && kind != TDO_OPT_ADAM) return fail(c, TDO_EINVAL, "unknown optimiser %d", kind);
+  if (kind == TDO_OPT_ADAM) {
+    if (!(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+      return fail(c, TDO_EINVAL, "Adam needs 0 <= beta1, beta2 < 1 and eps > 0");
+    CU(c, c->adam_m.ensure(sizeof(double) * c->P));
+    CU(c, c->adam_v.ensure(sizeof(double) * c->P));
+    CU(c, cudaMemsetAsync(c->adam_m.p, 0, sizeof(double) * c->P, c->stream));
+    CU(c, cudaMemsetAsync(c->adam_v.p, 0, sizeof(double) * c->P, c->stream));
+    c->adam_b1 = beta1;
+    c->adam_b2 = beta2;
+    c->adam_eps = eps;
+  }
+  c->adam_t = 0;
+  c->opt = kind;
+  return TDO_OK;
+}
+
 extern "C" tdo_status tdo_set_sr_options(tdo_ctx *c, double tol, int max_iter) {
   if (!c) return TDO_EINVAL;
   if (!(tol >= 0.0) || max_iter < 0) return fail(c, TDO_EINVAL, "tol must be >= 0 and max_iter >= 0");
@@ -1257,6 +1335,40 @@ extern "C" tdo_status tdo_sr_info(const tdo_ctx *c, int *iters, double *resid) {
   if (!c) return TDO_EINVAL;
   if (iters) *iters = c->last_sr_iters;
   if (resid) *resid = c->last_sr_resid;
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_measure_peak(int kind, void *stream, double *tflops) {
+  if ((kind != 0 && kind != 1) || !tflops) return TDO_EINVAL;
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TDO_ECUDA;
+  }
+  const cudaError_t e = measure_fma_peak(kind, n_sm, static_cast<cudaStream_t>(stream), tflops);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TDO_ECUDA;
+  }
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_wait_selftest(tdo_ctx *c, long long spin_limit) {
+  if (!c) return TDO_EINVAL;
+  if (!c->tc) return fail(c, TDO_EUNSUPPORTED, "tdo_wait_selftest needs a tensor-core (BF16 / FP16) context");
+  if (spin_limit < 1 || spin_limit > (1ll << 20))
+    return fail(c, TDO_EINVAL, "tdo_wait_selftest: spin_limit must be in [1, 2^20]");
+  CU(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->stream));
+  CU(c, launch_wait_probe(c->errflag.as<int>(), spin_limit, c->stream));
+  return check_err_flag(c);
+}
+
+extern "C" tdo_status tdo_sr_report(const tdo_ctx *c, int *outcome, double *last_pap, int *restarts) {
+  if (!c) return TDO_EINVAL;
+  if (outcome) *outcome = c->last_sr_outcome;
+  if (last_pap) *last_pap = c->last_sr_pap;
+  if (restarts) *restarts = c->last_sr_restarts;
   return TDO_OK;
 }
 
@@ -1283,8 +1395,9 @@ constexpr size_t kNaFsig = kNaCcoef + 8ull * TDO_NOALLOC_MAX_ENTRIES;
 constexpr size_t kNaFsigp = kNaFsig + 4ull * TDO_NOALLOC_MAX_ENTRIES;
 constexpr size_t kNaFcoef = kNaFsigp + 4ull * TDO_NOALLOC_MAX_ENTRIES;        // float2
 constexpr size_t kNaFlr = kNaFcoef + 8ull * TDO_NOALLOC_MAX_ENTRIES;          // float2
-constexpr size_t kNaBytes = kNaFlr + 8ull * TDO_NOALLOC_MAX_ENTRIES;          // about 8.7 MB
+constexpr size_t kNaBytes = kNaFlr + 8ull * TDO_NOALLOC_MAX_ENTRIES;          // 10,813,952 bytes (about 10.8 MB)
 static_assert(kNaCsig % 256 == 0 && kNaFlr % 16 == 0, "scratch alignment");
+static_assert(kNaBytes == 10813952ull, "the documented size of the fixed scratch array");
 
 void *g_noalloc_ptr[64];   // device address of g_noalloc_scratch per device (set up on first use)
 }  // namespace
@@ -1308,8 +1421,11 @@ extern "C" tdo_status tdo_local_estimator_noalloc(tdo_ctx *c, const uint32_t *si
                 Ns, M, TDO_NOALLOC_MAX_SAMPLES, TDO_NOALLOC_MAX_ENTRIES);
   int dev = 0;
   CU(c, cudaGetDevice(&dev));
+  if (dev != c->device)
+    return fail(c, TDO_EINVAL, "tdo_local_estimator_noalloc: the current device (%d) is not the context's device (%d)",
+                dev, c->device);
   if (dev < 0 || dev >= 64) return fail(c, TDO_EUNSUPPORTED, "device index %d out of range", dev);
-  if (!g_noalloc_ptr[dev]) {   // one-time set-up on this device (device current)
+  if (!g_noalloc_ptr[dev]) {   // one-time set-up on the context's device (current, checked above)
     void *p = nullptr;
     CU(c, cudaGetSymbolAddress(&p, g_noalloc_scratch));
     g_noalloc_ptr[dev] = p;
@@ -1333,8 +1449,9 @@ extern "C" tdo_status tdo_local_estimator_noalloc(tdo_ctx *c, const uint32_t *si
   CU(c, cudaMemcpyAsync(&total, offs + Ns, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaStreamSynchronize(c->stream));
   CU(c, launch_compact(cnt, offs, Ns, M, csig, csigp, ccoef, fsig, fsigp, fcoef, c->stream));
-  if (c->model.precision == TDO_BF16)
-    CU(c, launch_fwd_bf16(c->dm, c->dmb, fsig, fsigp, (size_t)total, flr, c->errflag.as<int>(), c->n_sm, c->stream));
+  if (c->tc)
+    CU(c, TC_LAUNCH(c, launch_fwd_bf16, c->dm, c->dmb, fsig, fsigp, (size_t)total, flr, c->errflag.as<int>(), c->n_sm,
+                    c->stream));
   else
     CU(c, launch_fwd32(c->dm, fsig, fsigp, (size_t)total, flr, c->n_sm, c->stream));
   CU(c, launch_lloc(offs, Ns, fcoef, flr, reinterpret_cast<double2 *>(lloc), l2, stats, flag, c->stream));
@@ -1343,14 +1460,7 @@ extern "C" tdo_status tdo_local_estimator_noalloc(tdo_ctx *c, const uint32_t *si
   CU(c, cudaMemcpyAsync(st, stats, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaMemcpyAsync(&nf, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaStreamSynchronize(c->stream));
-  if (c->model.precision == TDO_BF16) {
-    int f = 0;
-    CU(c, cudaMemcpy(&f, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (f) {
-      CU(c, cudaMemset(c->errflag.p, 0, sizeof(int)));
-      return fail(c, TDO_ETIMEOUT, "a tensor-core kernel's bounded wait gave up (results of that launch are invalid)");
-    }
-  }
+  TRY(check_err_flag(c));
   if (nf) return fail(c, TDO_ENUMERIC, "non-finite log rho or L_loc (rho = 0 exactly, or non-finite parameters)");
   const double mean = st[0] / (double)Ns;
   const double var = st[1] / (double)Ns - mean * mean;

@@ -57,15 +57,23 @@ cudaError_t launch_fwd32(const DevModel &m, const uint32_t *sig, const uint32_t 
 cudaError_t launch_sample32(const DevModel &m, size_t n_chains, size_t n_sweeps, uint64_t seed,
                             uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
                             uint32_t *ssigp, unsigned long long *accepted, int diag, int n_sm, cudaStream_t st);
-// BF16 tensor-core forward.
+// Tensor-core forward and sampler, BF16 operands (the _f16 variants: FP16 operands).
+cudaError_t launch_wait_probe(int *err_flag, long long spin, cudaStream_t st);
 cudaError_t launch_fwd_bf16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                             const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
                             cudaStream_t st);
+cudaError_t launch_fwd_bf16_f16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
+                                const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
+                                cudaStream_t st);
 bool bf16_supported(const DevModel &m);
 cudaError_t launch_sample_bf16(const DevModel &m, const DevModelBF16 &mb, size_t n_chains,
                                size_t n_sweeps, uint64_t seed, uint64_t counter, uint32_t *sig,
                                uint32_t *sigp, uint32_t *ssig, uint32_t *ssigp,
                                unsigned long long *accepted, int *err_flag, int diag, int n_sm, cudaStream_t st);
+cudaError_t launch_sample_bf16_f16(const DevModel &m, const DevModelBF16 &mb, size_t n_chains,
+                                   size_t n_sweeps, uint64_t seed, uint64_t counter, uint32_t *sig,
+                                   uint32_t *sigp, uint32_t *ssig, uint32_t *ssigp,
+                                   unsigned long long *accepted, int *err_flag, int diag, int n_sm, cudaStream_t st);
 
 // Mixed-state observables.  Rows of the magnetisation estimator: sample s -> (alpha, alpha), then
 // (alpha, alpha ^ e_i) for i < N, at rows s (N + 1) + j.
@@ -96,11 +104,16 @@ cudaError_t launch_cotangent(const int64_t *offs, size_t Ns, const float2 *fcoef
                              const double2 *lloc, const double *cost_stats, float2 *cot,
                              cudaStream_t st);
 // FP64 reductions.
+// scale (device pointer, may be NULL): every sum is multiplied by *scale (an exact power of two).
 cudaError_t launch_reduce_copies(const float *acc, int n_copies, size_t stride, size_t P, double *out,
-                                 int accumulate, cudaStream_t st);
+                                 int accumulate, cudaStream_t st, const float *scale = nullptr);
 cudaError_t launch_f64_to_f32(const double *src, float *dst, size_t n, cudaStream_t st);
-// BF16 weight packing.
+// 16-bit weight packing (BF16 operands; the _f16 variant packs FP16 operands).
 cudaError_t launch_pack_bf16(const DevModel &m, uint16_t *dst, DevModelBF16 *views, cudaStream_t st);
+cudaError_t launch_pack_bf16_f16(const DevModel &m, uint16_t *dst, DevModelBF16 *views, cudaStream_t st);
 
 cudaError_t launch_axpy_update(double *theta, const double *delta, double lr, size_t P, cudaStream_t st);
+// Adam step t (>= 1) on the direction delta with first and second moments m, v (FP64 [P], updated).
+cudaError_t launch_adam_update(double *theta, const double *delta, double *m, double *v, size_t P, long long t,
+                               double lr, double b1, double b2, double eps, cudaStream_t st);
 

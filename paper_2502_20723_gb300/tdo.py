@@ -15,14 +15,15 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtdo.so")
 
 TDO_EMBED_TOKEN, TDO_EMBED_CONV = 0, 1
-TDO_FP32, TDO_BF16 = 0, 1
+TDO_FP32, TDO_BF16, TDO_FP16 = 0, 1, 2
+PRECISIONS = {"fp32": TDO_FP32, "bf16": TDO_BF16, "fp16": TDO_FP16}
 STATUS = {0: "TDO_OK", -1: "TDO_EINVAL", -2: "TDO_ENOMEM", -3: "TDO_ECUDA", -4: "TDO_ENUMERIC",
           -5: "TDO_ETIMEOUT", -6: "TDO_EUNSUPPORTED"}
 
 EXPORTS = ["tdo_model_num_params", "tdo_create", "tdo_destroy", "tdo_num_params", "tdo_max_connections",
            "tdo_set_params", "tdo_get_params", "tdo_log_rho", "tdo_log_rho_vjp", "tdo_jacobian",
            "tdo_connections", "tdo_local_estimator", "tdo_local_estimator_noalloc", "tdo_sample", "tdo_grad", "tdo_sr_solve", "tdo_set_sr_options", "tdo_sr_step",
-           "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_last_error", "tdo_sample_diag", "tdo_magnetisation",
+           "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_sr_report", "tdo_wait_selftest", "tdo_set_optimizer", "tdo_measure_peak", "tdo_last_error", "tdo_sample_diag", "tdo_magnetisation",
            "tdo_purity", "tdo_schedule_value", "tdo_vmc_step"]
 
 
@@ -53,6 +54,15 @@ class Schedule(C.Structure):
     def __init__(self, eta0=0.0061, i_switch=30000, i_decay=40000, alpha=0.001, lambda0=0.004, i_switch_sr=30000,
                  i_decay_sr=40000, alpha_sr=0.01):
         super().__init__(eta0, i_switch, i_decay, alpha, lambda0, i_switch_sr, i_decay_sr, alpha_sr)
+
+
+def measure_peak(kind: str = "fp32", stream=None) -> float:
+    """tdo_measure_peak: measured FMA peak of the current device in TFLOP/s ("fp32" or "fp64")."""
+    t = C.c_double()
+    rc = lib().tdo_measure_peak(0 if kind == "fp32" else 1, stream, C.byref(t))
+    if rc != 0:
+        raise TdoError(rc, "tdo_measure_peak failed")
+    return t.value
 
 
 def schedule_value(step: int, v0: float, i_switch: int, i_decay: int, alpha: float) -> float:
@@ -100,9 +110,13 @@ def lib() -> C.CDLL:
         L.tdo_sr_solve.argtypes = [vp, vp, sz, vp, C.c_double, C.c_double, i32, vp, C.POINTER(i32), dp]
         L.tdo_sr_step.argtypes = [vp, vp, vp, sz, C.c_double, C.c_double, dp]
         L.tdo_set_sr_options.argtypes = [vp, C.c_double, i32]
+        L.tdo_set_optimizer.argtypes = [vp, i32, C.c_double, C.c_double, C.c_double]
         L.tdo_timing.argtypes = [vp, i32]
         L.tdo_timing_read.argtypes = [vp, C.c_char_p, dp, C.POINTER(C.c_longlong)]
         L.tdo_sr_info.argtypes = [vp, C.POINTER(i32), dp]
+        L.tdo_sr_report.argtypes = [vp, C.POINTER(i32), dp, C.POINTER(i32)]
+        L.tdo_wait_selftest.argtypes = [vp, C.c_longlong]
+        L.tdo_measure_peak.argtypes = [i32, vp, dp]
         L.tdo_last_error.argtypes = [vp]
         L.tdo_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -128,7 +142,7 @@ def make_model(spec: dict, precision: str = "fp32") -> Model:
     return Model(TDO_EMBED_TOKEN if spec.get("embed", "token") == "token" else TDO_EMBED_CONV,
                  int(spec.get("conv_channels", 0)), int(spec["d_model"]), int(spec["n_heads"]),
                  int(spec["n_layers"]), int(spec.get("mlp_ratio", 0)),
-                 TDO_BF16 if precision == "bf16" else TDO_FP32)
+                 PRECISIONS[precision])
 
 
 def model_num_params(spec: dict) -> int:
@@ -324,6 +338,20 @@ class Context:
         it, res = C.c_int(), C.c_double()
         self._chk(lib().tdo_sr_info(self.h, C.byref(it), C.byref(res)))
         return it.value, res.value
+
+    def sr_report(self):
+        """(outcome, last p.S'p, restarts) of the last SR step's CG solve (tdo_sr_report)."""
+        o, pap, r = C.c_int(), C.c_double(), C.c_int()
+        self._chk(lib().tdo_sr_report(self.h, C.byref(o), C.byref(pap), C.byref(r)))
+        return o.value, pap.value, r.value
+
+    def wait_selftest(self, spin_limit: int) -> int:
+        """tdo_wait_selftest: status of a bounded device wait that nothing completes (TDO_ETIMEOUT = -5)."""
+        return lib().tdo_wait_selftest(self.h, int(spin_limit))
+
+    def set_optimizer(self, kind: str = "sgd", beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        """tdo_set_optimizer: "sgd" or "adam" on the SR direction (resets Adam's moments)."""
+        self._chk(lib().tdo_set_optimizer(self.h, {"sgd": 0, "adam": 1}[kind], float(beta1), float(beta2), float(eps)))
 
     def set_sr_options(self, tol: float, max_iter: int):
         self._chk(lib().tdo_set_sr_options(self.h, float(tol), int(max_iter)))

@@ -27,3 +27,16 @@ def logrho_err(gpu_f2: np.ndarray, ref: np.ndarray) -> np.ndarray:
     dr = gpu_f2[:, 0].astype(np.float64) - ref.real
     di = wrap_phase(gpu_f2[:, 1].astype(np.float64) - ref.imag)
     return np.hypot(dr, di)
+
+
+def block_errors(spec: dict, g: np.ndarray, ref: np.ndarray) -> dict:
+    """Per named parameter block (synth.param_shapes order): max |g - ref| / max |ref| over the block, so
+    that a wrong small block (the head, the embedding table, one bias) shows even when the gradient's
+    norm is dominated by the large weight matrices."""
+    out, off = {}, 0
+    for name, shape in synth.param_shapes(spec):
+        n = int(np.prod(shape))
+        gb, rb = np.asarray(g[off:off + n]), np.asarray(ref[off:off + n])
+        out[name] = float(np.abs(gb - rb).max() / max(np.abs(rb).max(), 1e-300))
+        off += n
+    return out

@@ -72,3 +72,9 @@ def test_null_context_is_rejected_without_a_device(libtdo):
     assert libtdo.tdo_purity(None, None, None, 4, ctypes.byref(d), None) == einval
     assert libtdo.tdo_vmc_step(None, None, None, 4, 1, 0, ctypes.byref(u64), 0, None, None) == einval
     assert libtdo.tdo_sr_step(None, None, None, 4, 0.1, 0.1, None) == einval
+    assert libtdo.tdo_local_estimator_noalloc(None, None, None, 4, None, None, None) == einval
+    assert libtdo.tdo_sr_report(None, None, None, None) == einval
+    assert libtdo.tdo_wait_selftest(None, 16) == einval
+    assert libtdo.tdo_set_optimizer(None, 1, 0.9, 0.999, 1e-8) == einval
+    assert libtdo.tdo_measure_peak(2, None, ctypes.byref(d)) == einval
+    assert libtdo.tdo_measure_peak(0, None, None) == einval

@@ -303,6 +303,30 @@ def test_sr_step_matches_oracle():
     assert np.linalg.norm((new - th) - (ref_new - th)) <= 1e-3 * np.linalg.norm(ref_new - th)
 
 
+def test_sr_step_adam_three_steps_match_oracle():
+    """Adam on the SR direction (tdo_set_optimizer): three steps on the same samples, each compared element by
+    element with the oracle's Cholesky SR direction fed to its Adam (Kingma and Ba); the CG runs to 1e-12 so
+    that the two directions agree to FP32 rounding of the log-derivatives.  eps = 1e-3 keeps the update a
+    smooth function of the direction, so the bound is the FP32 error of delta times lr / eps."""
+    prob = problem("ising", 4)
+    spec = synth.model_spec(16, 2, 1, 0)
+    th = synth.init_params(spec, 3, std=0.1)
+    sig, sigp = synth.random_configs(4, 200, seed=5)
+    ctx = ctx_for(prob, spec, th)
+    ctx.set_sr_options(1e-12, 4000)
+    ctx.set_optimizer("adam", 0.9, 0.999, 1e-3)
+    lr, shift = 0.01, 0.01
+    ref, m, v = th.copy(), np.zeros_like(th), np.zeros_like(th)
+    for t in range(1, 4):
+        ctx.sr_step(dev(sig), dev(sigp), lr, shift)
+        _, _, _, delta = E.sr_step(prob, spec, ref, sig, sigp, lr, shift)
+        ref, m, v = E.adam_step(ref, delta, m, v, t, lr, 0.9, 0.999, 1e-3)
+        got = ctx.get_params()
+        err = np.abs(got - ref).max()
+        assert err <= 2e-4 * lr, (t, err)
+        assert np.abs(got - th).max() > 0.5 * lr   # the steps moved the parameters by order lr
+
+
 # ------------------------------------------------------------------ Metropolis
 def test_metropolis_replays_oracle_chains():
     """Same Philox stream on both sides: every chain whose accept decisions are all decided by more than

@@ -152,3 +152,24 @@ def test_lr_schedule():
     assert E.lr_schedule(0) == 0.0061
     assert abs(E.lr_schedule(30000) - 0.0061 * (1 + 0.001)) < 1e-15
     assert abs(E.lr_schedule(70000) - 0.0061 * 0.001) < 1e-15
+
+
+def test_adam_step_matches_torch_and_first_step_closed_form():
+    """The oracle's Adam (Kingma and Ba, Algorithm 1) against torch.optim.Adam fed the same directions, and
+    its first step: m_hat = delta, v_hat = delta^2, so theta moves by lr delta / (|delta| + eps)."""
+    import torch
+    rng = np.random.default_rng(4)
+    th0 = rng.standard_normal(7)
+    deltas = [rng.standard_normal(7) * s for s in (1.0, 0.1, 3.0, 1e-4)]
+    lr, b1, b2, eps = 0.02, 0.85, 0.995, 1e-6
+    th, m, v = th0.copy(), np.zeros(7), np.zeros(7)
+    p = torch.nn.Parameter(torch.as_tensor(th0.copy()))
+    opt = torch.optim.Adam([p], lr=lr, betas=(b1, b2), eps=eps)
+    for t, d in enumerate(deltas, start=1):
+        th, m, v = E.adam_step(th, d, m, v, t, lr, b1, b2, eps)
+        opt.zero_grad()
+        p.grad = torch.as_tensor(d)
+        opt.step()
+        assert np.abs(th - p.detach().numpy()).max() < 1e-13
+    th1, _, _ = E.adam_step(th0, deltas[0], np.zeros(7), np.zeros(7), 1, lr, b1, b2, eps)
+    assert np.allclose(th0 - th1, lr * deltas[0] / (np.abs(deltas[0]) + eps), rtol=0, atol=1e-15)
