@@ -9,7 +9,15 @@ One step = one VMC step through the C ABI: one Metropolis sweep (2N proposals pe
 then tdo_sr_step on the chain states (connections, log rho of every connected configuration, L_loc and
 cost, cost gradient, log-derivatives, SR conjugate-gradient solve, parameter update).
 
+The timed arm is the FP16 tensor-core context (tcgen05 GEMMs with FP16 operands, FP32 accumulation);
+shorter comparison runs time the BF16 tensor-core and the FP32 CUDA-core contexts.  A BF16 backward's
+rounding, amplified by the SR solve's 1 / diag_shift, makes the BF16 optimisation leave the FP32
+trajectory after a few steps; the FP16 one follows it.
+
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded sample of the same step.
+The cpu_baseline leg runs that oracle on a fixed subset of the run's final samples: its local estimator there
+is also the reference of the "at set error" figures (L_loc and cost of the FP16, BF16 and FP32 contexts
+at the run's final parameters against it).
 """
 from __future__ import annotations
 
@@ -70,11 +78,6 @@ def measured_peaks() -> dict:
             return json.load(f)
     except OSError:
         return {}
-
-
-def fp32_alu_peak_tflops(sm_mhz: float = 2070.0) -> float:
-    """CUDA-core FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -191,8 +194,10 @@ def run_ours(args) -> dict | None:
         ctx.timing(False)
         lloc_rows = int(ctx.connections(sig, sigp)[0].sum().item())
         out = {"t_ms": max_over_ranks(t_ms, world), "groups": groups, "sr_mv": sr_mv, "launches": launches,
-               "lloc_rows": lloc_rows,
-               "costs": costs, "sr_iters": sr_iters, "clocks": clk.summary(), "P": ctx.P}
+               "lloc_rows": lloc_rows, "costs": costs, "sr_iters": sr_iters, "clocks": clk.summary(), "P": ctx.P,
+               "theta": ctx.get_params(),
+               "subset": ((sig[:SET_ERROR_SAMPLES].cpu().numpy().astype(np.int64) & 0xFFFFFFFF).astype(np.uint32),
+                          (sigp[:SET_ERROR_SAMPLES].cpu().numpy().astype(np.int64) & 0xFFFFFFFF).astype(np.uint32))}
         if e2e:
             # end to end through the public API with host buffers (copies inside the timed region)
             hs = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
@@ -212,59 +217,75 @@ def run_ours(args) -> dict | None:
         ctx.close()
         return out
 
+    peak_fp32 = tdo.measure_peak("fp32", stream.cuda_stream)
+    peak_fp64 = tdo.measure_peak("fp64", stream.cuda_stream)
     main = measure(args.precision, args.steps, args.warmup, True)
-    other = None
+    others = {}
     if not args.no_compare:
-        other = measure("fp32" if args.precision == "bf16" else "bf16", max(2, min(args.steps, 3)), 3, False)
+        for prec in ("fp16", "bf16", "fp32"):
+            if prec != args.precision:
+                others[prec] = measure(prec, max(2, min(args.steps, 3)), 3, False)
     t_max, groups, launches, lloc_rows = main["t_ms"], main["groups"], main["launches"], main["lloc_rows"]
     fwd_evals = lloc_rows
     sample_evals = N_SAMPLES * (1 + 2 * N_SITES)
     clk_summary = main["clocks"]
+
+    # at set error: L_loc and cost of both precisions on a fixed subset of the final samples, at the final
+    # parameters of the timed run (compared below with the oracle's values from the cpu_baseline leg)
+    sub_s, sub_p = main["subset"]
+    set_err_gpu = {}
+    for prec in ("fp16", "bf16", "fp32"):
+        c2 = tdo.Context(prob, spec, main["theta"], prec, stream=stream.cuda_stream)
+        ll, cost, _ = c2.local_estimator(sub_s.astype(np.uint32), sub_p.astype(np.uint32))
+        set_err_gpu[prec] = (np.asarray(ll[:, 0] + 1j * ll[:, 1]), cost)
+        c2.close()
 
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
         return None
 
-    # ---- roofline of the dominant kernel group
     peaks = measured_peaks()
-    dom = max(groups, key=lambda g: groups[g]["ms"])
-    clocks = clk_summary
     P = main["P"]
-    if dom in ("fwd", "sample", "bwd_vjp", "bwd_jac"):
-        units = {"fwd": fwd_evals, "sample": sample_evals, "bwd_vjp": lloc_rows, "bwd_jac": N_SAMPLES}[dom]
-        per_unit = {"fwd": F_EVAL, "sample": F_EVAL, "bwd_vjp": 2 * F_EVAL, "bwd_jac": 4 * F_EVAL}[dom]
-        flops = units * per_unit
-        achieved = flops / (groups[dom]["ms"] * 1e-3) / 1e12
-        tensor = args.precision == "bf16" and dom in ("fwd", "sample", "bwd_vjp")
-        if tensor:
-            peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-            roof = {"bound": "tensor", "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
-        else:
-            peak = fp32_alu_peak_tflops()
-            roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
-        roof.update({"kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "algorithmic_per_launch": flops / max(1, groups[dom]["launches"])})
+    tensor = args.precision in ("bf16", "fp16")
+    if tensor:
+        # FP16 and BF16 dense MMA share one nominal rate (2.25 PFLOP/s), so the measured BF16 figure serves both
+        peak_t = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        t_src = ("MEASURED_PEAKS bf16_tflops_sustained (of measured; FP16 at the same nominal rate)"
+                 if "bf16_tflops_sustained" in peaks else "fallback 1700 TFLOP/s sustained")
     else:
-        # SR: the dominant work is the S' v product of each CG iteration (k_sr_tpart + k_sr_wpart and their
-        # small reductions, timed product by product): it streams O (Ns x P complex elements, BF16 pairs in
-        # BF16 contexts, FP32 pairs otherwise) from HBM twice
-        mv = main["sr_mv"]
-        byts = 2 * N_SAMPLES * P * (4 if args.precision == "bf16" else 8)
-        # DRAM bytes of one product from ncu (dram__bytes_read.sum + dram__bytes_write.sum of k_sr_tpart and
-        # k_sr_wpart on the 2048-sample case, profiles/k_sr_tpart_wpart_ising_n16_d64_l4.md), scaled by the
-        # samples (the passes stream every row once); for the BF16 layout at this P only
-        traffic = None
-        if args.precision == "bf16" and P == 198274:
-            traffic = (1.627103e9 + 4.585984e6 + 1.624482e9 + 6.067968e6) / 2048 * N_SAMPLES
-        achieved = byts * mv["launches"] / (mv["ms"] * 1e-3) / 1e9 if mv["ms"] else 0.0
-        peak = float(peaks.get("hbm_gbs", 6781.4))
-        roof = {"bound": "hbm", "kernel": "S' v product (k_sr_tpart + k_sr_wpart, group sr_mv)",
-                "o_element_bytes": 4 if args.precision == "bf16" else 8,
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)", "algorithmic_per_launch": byts,
-                "products_per_step": mv["launches"], "ms_per_product": mv["ms"] / max(1e-9, mv["launches"])}
-    fwd_tflops = fwd_evals * F_EVAL / (groups["fwd"]["ms"] * 1e-3) / 1e12 if groups["fwd"]["ms"] else None
+        peak_t, t_src = peak_fp32, "tdo_measure_peak FP32 FFMA, this run (of measured)"
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "MEASURED_PEAKS hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
+
+    def compute_roof(group, units, per_unit, desc):
+        ms, n = groups[group]["ms"], groups[group]["launches"]
+        flops = units * per_unit
+        ach = flops / (ms * 1e-3) / 1e12 if ms else 0.0
+        return {"bound": "tensor" if tensor else "alu", "kernel": desc, "group": group, "achieved": ach,
+                "peak": peak_t, "unit": "TFLOP/s", "frac": ach / peak_t, "traffic": None,
+                "algorithmic_per_step": flops, "units_per_step": units, "per_unit": per_unit,
+                "ms_per_step": ms, "launches_per_step": n, "peak_source": t_src}
+
+    rooflines = {
+        "fwd": compute_roof("fwd", fwd_evals, F_EVAL, "forward of every connected row (log rho evals)"),
+        "bwd_vjp": compute_roof("bwd_vjp", lloc_rows, 2 * F_EVAL, "gradient backward (VJP of every connected row)"),
+        "sample": compute_roof("sample", sample_evals, F_EVAL, "Metropolis sweep (one log rho per proposal)"),
+    }
+    mv = main["sr_mv"]
+    ob = 8 if args.precision == "fp32" else 4   # tensor-core contexts store O - obar as BF16 pairs
+    byts = 2 * N_SAMPLES * P * ob
+    ach = byts * mv["launches"] / (mv["ms"] * 1e-3) / 1e9 if mv["ms"] else 0.0
+    rooflines["sr_mv"] = {"bound": "hbm", "kernel": "S' v product (k_sr_tpart + k_sr_wpart and reductions)",
+                          "group": "sr_mv", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                          "traffic": None, "algorithmic_per_launch": byts, "o_element_bytes": ob,
+                          "products_per_step": mv["launches"], "ms_per_step": mv["ms"], "peak_source": hbm_src}
+    # the headline roofline: the dominant kernel group of the timed steps
+    dom_ms = {"fwd": groups["fwd"]["ms"], "bwd_vjp": groups["bwd_vjp"]["ms"], "sample": groups["sample"]["ms"],
+              "sr_mv": mv["ms"]}
+    dom = max(dom_ms, key=dom_ms.get)
+    roof = dict(rooflines[dom])
+    fwd_tflops = rooflines["fwd"]["achieved"]
     res = {
         "metric": METRIC,
         "value": replicas_rate(world, args.steps, t_max * 1e-3),
@@ -276,42 +297,70 @@ def run_ours(args) -> dict | None:
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "bf16",
+        "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.precision],
         "data": "synthetic (seeded random initial chains, Metropolis-sampled; random-init N(0,0.02) weights)",
         "config": {"workload": WORKLOAD, "n_sites": N_SITES, "d_model": D, "heads": HEADS, "layers": LAYERS,
                    "mlp_ratio": MLP, "samples_per_gpu": N_SAMPLES, "params": P, "precision": args.precision,
-                   "sweeps_per_step": 1, "l2": "256 MB buffer written between timed steps",
+                   "sweeps_per_step": 1, "lr": LR, "diag_shift": SHIFT,
+                   "l2": "256 MB buffer written between timed steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "logrho_evals_per_s": (fwd_evals + sample_evals) * world * args.steps / (t_max * 1e-3),
         "logrho_evals_per_s_fwd_kernel": fwd_evals / (groups["fwd"]["ms"] * 1e-3) if groups["fwd"]["ms"] else None,
         "rows_per_step": {"lloc_rows": lloc_rows, "sample_evals": sample_evals},
         "breakdown_ms_per_step": {g: round(v["ms"], 3) for g, v in groups.items()},
-        "cost_last": main["costs"][-1],
+        "costs": [round(c, 6) for c in main["costs"]],
         "sr_cg_iterations": main["sr_iters"],
         "fwd_kernel_tflops": fwd_tflops,
         "roofline": roof,
-        "clocks": clocks,
+        "rooflines": rooflines,
+        "peaks_measured_here": {"fp32_fma_tflops": peak_fp32, "fp64_fma_tflops": peak_fp64},
+        "clocks": clk_summary,
         "e2e": {"value": main["e2e_steps_per_s"], "unit": "VMC steps/s",
                 "h2d_bytes_per_step": 4 * 4 * N_SAMPLES, "d2h_bytes_per_step": 2 * 4 * N_SAMPLES + 8},
         "gpu_launches": launches,
     }
-    if other is not None:
+    res["compare"] = {}
+    for prec, other in others.items():
         og = other["groups"]
-        res["compare"] = {"precision": "fp32" if args.precision == "bf16" else "bf16",
-                          "value": world * len(other["costs"]) / (other["t_ms"] * 1e-3), "unit": "VMC steps/s",
-                          "ms_per_step": other["t_ms"] / len(other["costs"]),
-                          "logrho_evals_per_s_fwd_kernel": fwd_evals / (og["fwd"]["ms"] * 1e-3) if og["fwd"]["ms"] else None,
-                          "breakdown_ms_per_step": {g: round(v["ms"], 3) for g, v in og.items()},
-                          "cost_last": other["costs"][-1]}
+        res["compare"][prec] = {
+            "value": world * len(other["costs"]) / (other["t_ms"] * 1e-3), "unit": "VMC steps/s",
+            "steps": len(other["costs"]), "warmup": 3, "ms_per_step": other["t_ms"] / len(other["costs"]),
+            "logrho_evals_per_s_fwd_kernel": fwd_evals / (og["fwd"]["ms"] * 1e-3) if og["fwd"]["ms"] else None,
+            "breakdown_ms_per_step": {g: round(v["ms"], 3) for g, v in og.items()},
+            "costs": [round(c, 6) for c in other["costs"]], "sr_cg_iterations": other["sr_iters"]}
     if world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+        base = cpu_baseline(args.cpu_budget, main["theta"], sub_s, sub_p)
+        ref_l, ref_c = base.pop("lloc_ref"), base.pop("cost_ref")
+        res["cpu_baseline"] = base
+        res["at_set_error"] = set_error_report(set_err_gpu, ref_l, ref_c)
     return res
 
 
 # ---------------------------------------------------------------------------------- oracle on the CPU
+SET_ERROR_SAMPLES = 256
+TOL_COST_REL_BF16 = 1e-3
+
+
+def set_error_report(gpu: dict, ref_l: np.ndarray, ref_c: float) -> dict:
+    """L_loc and cost of each precision against the oracle on the same samples and parameters:
+    lloc_max_rel = max_s |L_gpu - L_ref| / max_s |L_ref|, lloc_rms_rel = ||L_gpu - L_ref|| / ||L_ref||,
+    cost_rel = |cost_gpu - cost_ref| / cost_ref."""
+    out = {"samples": int(len(ref_l)), "parameters": "final parameters of the timed run", "cost_oracle": ref_c,
+           "cost_tolerance_bf16": TOL_COST_REL_BF16}
+    for prec, (l, c) in gpu.items():
+        d = np.abs(l - ref_l)
+        out[prec] = {"lloc_max_rel": float(d.max() / np.abs(ref_l).max()),
+                     "lloc_rms_rel": float(np.linalg.norm(l - ref_l) / np.linalg.norm(ref_l)),
+                     "cost": c, "cost_rel": float(abs(c - ref_c) / ref_c)}
+    for prec in gpu:
+        if prec != "fp32":
+            out[prec]["within_tolerance"] = out[prec]["cost_rel"] <= TOL_COST_REL_BF16
+    return out
+
+
 def _timed(fn, count: int, target_s: float, grow: int = 8):
     """Run fn(count); if it took well under target_s, rerun once with a count scaled to the target.
-    Returns (seconds per unit, count used)."""
+    Returns (seconds per unit, count used, seconds of the counted run)."""
     t0 = time.perf_counter()
     fn(count)
     dt = time.perf_counter() - t0
@@ -320,10 +369,10 @@ def _timed(fn, count: int, target_s: float, grow: int = 8):
         t0 = time.perf_counter()
         fn(count)
         dt = time.perf_counter() - t0
-    return dt / count, count
+    return dt / count, count, dt
 
 
-def oracle_step_estimate(budget_s: float) -> dict:
+def oracle_step_estimate(budget_s: float, theta=None) -> dict:
     """Time the FP64 oracle on a bounded sample of one VMC step of the workload and extrapolate.
     Parts: Metropolis proposals (one log rho each), the local estimator and gradient over each sample's
     connected configurations, the log-derivatives.  The SR solve is not included: the oracle's dense
@@ -334,7 +383,7 @@ def oracle_step_estimate(budget_s: float) -> dict:
 
     prob = synth.ising_chain(N_SITES, V=2.0, g=1.0, gamma=1.0)
     spec = synth.model_spec(D, HEADS, LAYERS, MLP)
-    th = synth.init_params(spec, seed=0)
+    th = synth.init_params(spec, seed=0) if theta is None else theta
 
     def ev(k):
         a, b = synth.random_configs(N_SITES, k, seed=1)
@@ -348,21 +397,47 @@ def oracle_step_estimate(budget_s: float) -> dict:
         a, b = synth.random_configs(N_SITES, k, seed=3)
         E.jacobian(spec, th, a, b, N_SITES)
 
-    t_eval, nf = _timed(ev, 128, 0.35 * budget_s)
-    t_grad, ng = _timed(gr, 4, 0.4 * budget_s)
-    t_jac, nj = _timed(jc, 2, 0.25 * budget_s)
+    t_eval, nf, s1 = _timed(ev, 128, 0.35 * budget_s)
+    t_grad, ng, s2 = _timed(gr, 4, 0.4 * budget_s)
+    t_jac, nj, s3 = _timed(jc, 2, 0.25 * budget_s)
     step_s = N_SAMPLES * (2 * N_SITES * t_eval + t_grad + t_jac)
-    return {"step_s": step_s, "cores": torch.get_num_threads(),
+    timed = s1 + s2 + s3
+    return {"step_s": step_s, "timed_s": timed, "extrapolation_factor": step_s / timed,
+            "cores": torch.get_num_threads(), "host_cpus": os.cpu_count(),
             "sample": (f"{nf} log rho evals, gradient estimator on {ng} samples (with their connected "
-                       f"configurations), log-derivatives of {nj} samples; extrapolated to 16384 samples x "
-                       f"(32 Metropolis proposals + estimator + gradient + log-derivatives); SR solve excluded "
-                       f"(oracle dense Cholesky infeasible at P=198,274)")}
+                       f"configurations), log-derivatives of {nj} samples, timed {timed:.1f} s; extrapolated to "
+                       f"16384 samples x (32 Metropolis proposals + estimator + gradient + log-derivatives) "
+                       f"= x{step_s / timed:.0f}; SR solve excluded (oracle dense Cholesky infeasible at "
+                       f"P=198,274)")}
 
 
-def cpu_baseline(budget_s: float) -> dict:
-    est = oracle_step_estimate(budget_s)
-    return {"value": 1.0 / est["step_s"], "unit": "VMC steps/s", "cores": est["cores"], "kind": "oracle",
-            "sample": est["sample"]}
+def cpu_baseline(budget_s: float, theta=None, sub_s=None, sub_p=None) -> dict:
+    """The oracle on the host cores: one VMC step extrapolated from a timed sample, plus its local
+    estimator on the given subset of samples (the reference of the at-set-error figures)."""
+    from oracle import estimators as E
+    est = oracle_step_estimate(budget_s, theta)
+    out = {"value": 1.0 / est["step_s"], "unit": "VMC steps/s", "cores": est["cores"], "kind": "oracle",
+           "sample": est["sample"], "timed_s": est["timed_s"], "extrapolation_factor": est["extrapolation_factor"],
+           "host_cpus": est["host_cpus"]}
+    if sub_s is not None:
+        prob = synth.ising_chain(N_SITES, V=2.0, g=1.0, gamma=1.0)
+        spec = synth.model_spec(D, HEADS, LAYERS, MLP)
+        t0 = time.perf_counter()
+        ll = E.local_estimator(prob, spec, theta, sub_s, sub_p)
+        out["lloc_ref"], out["cost_ref"] = ll, float(np.mean(np.abs(ll) ** 2))
+        out["set_error_oracle_s"] = time.perf_counter() - t0
+    return out
+
+
+def _single_thread_estimate(budget_s: float) -> dict:
+    """The same oracle sample with one thread (numpy/BLAS and torch), in a child process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(budget_s)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    for line in r.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    return {"error": (r.stderr or "no output")[-300:]}
 
 
 def run_reference(args) -> dict | None:
@@ -370,19 +445,26 @@ def run_reference(args) -> dict | None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    budget = max(3.0, 150.0 / max(1, args.steps + args.warmup))
+    budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_step_estimate(budget)
+        oracle_step_estimate(min(budget, 2.0))
     est_steps = [oracle_step_estimate(budget) for _ in range(args.steps)]
     step_s = statistics.mean(e["step_s"] for e in est_steps)
+    timed_s = statistics.mean(e["timed_s"] for e in est_steps)
     v = 1.0 / step_s
+    single = _single_thread_estimate(budget)
     return {"metric": METRIC, "value": v, "unit": "VMC steps/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "ms_per_step_kind": "extrapolated",
+            "timed_s_per_step": timed_s, "extrapolation_factor": step_s / timed_s,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "n_sites": N_SITES, "d_model": D, "heads": HEADS, "layers": LAYERS,
                        "mlp_ratio": MLP, "samples_per_gpu": N_SAMPLES, "parallelism": "CPU oracle"},
             "cpu_baseline": {"value": v, "unit": "VMC steps/s", "cores": est_steps[0]["cores"], "kind": "oracle",
-                             "sample": est_steps[0]["sample"]},
+                             "host_cpus": est_steps[0]["host_cpus"], "sample": est_steps[0]["sample"],
+                             "single_thread": {"value": 1.0 / single["step_s"] if "step_s" in single else None,
+                                               "timed_s": single.get("timed_s"), "cores": 1,
+                                               "note": single.get("error")}},
             "e2e": {"value": v, "unit": "VMC steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -422,18 +504,24 @@ def run_kernel_case(args) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
-    ap.add_argument("--no-compare", action="store_true", help="skip the other-precision comparison run")
+    ap.add_argument("--precision", default="fp16", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the other-precision comparison runs")
     ap.add_argument("--burn-in", type=int, default=4)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", default=None, choices=["fwd", "grad", "jac", "sample", "sr"],
                     help="run one call of one kind on a reduced sample count (profiling) and exit")
     ap.add_argument("--case-samples", type=int, default=1024)
+    ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sample is not None:   # child process of the reference arm (single-thread timing)
+        import torch
+        torch.set_num_threads(1)
+        print(json.dumps({k: v for k, v in oracle_step_estimate(args.oracle_sample).items() if k != "sample"}))
+        return
     if args.kernel_case:
         run_kernel_case(args)
         return

@@ -98,6 +98,23 @@ tdo_status tdo_get_params(tdo_ctx *ctx, double *theta);
  * logrho[b] = log rho(sig[b], sigp[b]) as (re, im) floats, b < B.  B may be 0. */
 tdo_status tdo_log_rho(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t B, float *logrho);
 
+/* The ansatz over chains of different lengths in one batch (architecture appendix: the token embedding,
+ * the attention and the mean pooling take a sequence of any length with the same theta, the
+ * translation-invariant form of the appendix's global mean pooling): logrho[b] = log rho(sig[b], sigp[b])
+ * for a chain of n_sites[b] sites, 1 <= n_sites[b] <= 32 (TDO_EUNSUPPORTED otherwise; the context's own
+ * n_sites plays no part).  The batch is sorted into buckets of equal N on the device; tensor-core contexts
+ * then run every bucket's tiles in one persistent launch whose shape (CTAs per SM, bucket order, static
+ * or dynamic tile schedule) is chosen by timing four candidates on the first call with a new mix of
+ * chain lengths and cached in the context (tdo_ragged_tuning reads it); FP32 contexts launch once per
+ * bucket.  Synchronises the stream.  B < 2^32. */
+tdo_status tdo_log_rho_ragged(tdo_ctx *ctx, const int32_t *n_sites, const uint32_t *sig, const uint32_t *sigp,
+                              size_t B, float *logrho);
+/* The launch shape the autotuner kept for a mix of chain lengths (bit N-1 of mix set for each N present):
+ * CTAs per SM (1 or 2), descending-N tile order (0/1), dynamic tile schedule (0/1).  TDO_EINVAL if that
+ * mix has not been seen. */
+tdo_status tdo_ragged_tuning(const tdo_ctx *ctx, uint32_t mix, int *ctas_per_sm, int *descending,
+                             int *dynamic_schedule);
+
 /* Vector-Jacobian product of tdo_log_rho: grad[k] += sum_b Re(c_b * d log rho_b / d theta_k) with the
  * complex cotangents c_b = (cot[2b], cot[2b+1]); grad is FP64 [P], accumulated into (not zeroed). */
 tdo_status tdo_log_rho_vjp(tdo_ctx *ctx, const uint32_t *sig, const uint32_t *sigp, size_t B,

@@ -49,160 +49,30 @@ __device__ __forceinline__ uint32_t trans8(uint32_t x) {
 
 __device__ __forceinline__ void zero4(float (&d)[4]) { d[0] = d[1] = d[2] = d[3] = 0.f; }
 
-// S = A B^T over the feature dimension for a [16 rows][HD] A block and a [16 keys][HD] B block, both
-// FP32 in shared memory (row stride ld, rows >= n read as 0).  Returns the two key halves s[0], s[1].
-template <int HD>
-__device__ __forceinline__ void scores(const float *A, const float *B, int ld, int n, float ascale, float (&s)[2][4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  auto ld2 = [&](const float *M, int r, int c, float sc) -> uint32_t {
-    return r < n ? h2(M[r * ld + c] * sc, M[r * ld + c + 1] * sc) : 0u;
-  };
-#pragma unroll
-  for (int j = 0; j < 2; ++j) zero4(s[j]);
-  if (HD == 8) {
-    const uint32_t a0 = ld2(A, g, 2 * t, ascale), a1 = ld2(A, g + 8, 2 * t, ascale);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) mma1688(s[j], a0, a1, ld2(B, 8 * j + g, 2 * t, 1.f));
-  } else {
-    const uint32_t a[4] = {ld2(A, g, 2 * t, ascale), ld2(A, g + 8, 2 * t, ascale), ld2(A, g, 8 + 2 * t, ascale),
-                           ld2(A, g + 8, 8 + 2 * t, ascale)};
-#pragma unroll
-    for (int j = 0; j < 2; ++j) mma16816(s[j], a, ld2(B, 8 * j + g, 2 * t, 1.f), ld2(B, 8 * j + g, 8 + 2 * t, 1.f));
-  }
-}
-
-// Y[16 rows][HD] = X[16][16 keys] M[16 keys][HD] with X given as an A fragment and M FP32 in shared
-// memory (row stride ld, rows >= n read as 0): out[c] holds features 8c .. 8c+7.
-template <int HD>
-__device__ __forceinline__ void times_rows(const uint32_t (&x)[4], const float *M, int ld, int n,
-                                           float (&out)[HD / 8][4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  auto col2 = [&](int r, int c) -> uint32_t {   // (M[r][c], M[r+1][c])
-    const float lo = r < n ? M[r * ld + c] : 0.f, hi = r + 1 < n ? M[(r + 1) * ld + c] : 0.f;
-    return h2(lo, hi);
-  };
-#pragma unroll
-  for (int c = 0; c < HD / 8; ++c) {
-    zero4(out[c]);
-    mma16816(out[c], x, col2(2 * t, 8 * c + g), col2(8 + 2 * t, 8 * c + g));
-  }
-}
-
-// Forward and backward of softmax attention for one (sequence, head) on one warp.
-//   Q, K, V, dH: FP32 [n][ld] blocks of this head (column 0 = the head's first feature), n <= 16.
-//   qscale: 1/sqrt(HD) * log2(e) (scores in base 2); scale: 1/sqrt(HD).
-//   emit(kind, row, col, v0, v1): kind 0 = attention output O, 1 = dQ, 2 = dK, 3 = dV, for
-//   (row, col..col+1) with row < n.
-template <int HD, typename EMIT>
-__device__ __forceinline__ void attn_fwd_bwd(const float *Q, const float *K, const float *V, const float *dH, int ld,
-                                             int n, float qscale, float scale, EMIT emit) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float s[2][4];
-  scores<HD>(Q, K, ld, n, qscale, s);
-  // softmax over the keys of rows g (s[.][0..1]) and g + 8 (s[.][2..3]); keys >= n masked
-  float m0 = -INFINITY, m1 = -INFINITY;
+// dS (FP32 C fragments of this warp's 16 x 16 block) to FP16 A fragments, after scaling the block by the
+// power of two that puts its largest magnitude in [2^13, 2^14).  dS = P (dA - delta) is a small difference
+// times probabilities; unscaled, much of it would fall among FP16's subnormals (below 6.1e-5) or to zero,
+// and the dQ, dK weight gradients built from it would be mostly rounding.  Returns the inverse factor,
+// applied exactly to the FP32 products dS K and dS^T Q.
+__device__ __forceinline__ float ds_pack_scaled(const float (&da)[2][4], uint32_t &x00, uint32_t &x10, uint32_t &x01,
+                                                uint32_t &x11) {
+  float m = 0.f;
 #pragma unroll
   for (int j = 0; j < 2; ++j)
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const bool ok = 8 * j + 2 * t + e < n;
-      s[j][e] = ok ? s[j][e] : -INFINITY;
-      s[j][2 + e] = ok ? s[j][2 + e] : -INFINITY;
-      m0 = fmaxf(m0, s[j][e]);
-      m1 = fmaxf(m1, s[j][2 + e]);
-    }
+    for (int e = 0; e < 4; ++e) m = fmaxf(m, fabsf(da[j][e]));
 #pragma unroll
-  for (int o = 1; o <= 2; o <<= 1) {
-    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-  }
-  float l0 = 0.f, l1 = 0.f;
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      s[j][e] = tc::ex2_fast(s[j][e] - m0);
-      s[j][2 + e] = tc::ex2_fast(s[j][2 + e] - m1);
-      l0 += s[j][e];
-      l1 += s[j][2 + e];
-    }
-#pragma unroll
-  for (int o = 1; o <= 2; o <<= 1) {
-    l0 += __shfl_xor_sync(0xffffffffu, l0, o);
-    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-  }
-  const float i0 = tc::rcp_fast(l0), i1 = tc::rcp_fast(l1);
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    s[j][0] *= i0; s[j][1] *= i0;
-    s[j][2] *= i1; s[j][3] *= i1;
-  }
-  const uint32_t pa[4] = {h2(s[0][0], s[0][1]), h2(s[0][2], s[0][3]), h2(s[1][0], s[1][1]), h2(s[1][2], s[1][3])};
-  // O = P V
-  {
-    float o[HD / 8][4];
-    times_rows<HD>(pa, V, ld, n, o);
-#pragma unroll
-    for (int c = 0; c < HD / 8; ++c) {
-      if (g < n) emit(0, g, 8 * c + 2 * t, o[c][0], o[c][1]);
-      if (g + 8 < n) emit(0, g + 8, 8 * c + 2 * t, o[c][2], o[c][3]);
-    }
-  }
-  // dA = dH V^T; delta_i = sum_j P_ij dA_ij; dS = scale P (dA - delta)
-  float da[2][4];
-  scores<HD>(dH, V, ld, n, 1.f, da);
-  float d0 = 0.f, d1 = 0.f;
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    d0 = fmaf(s[j][0], da[j][0], fmaf(s[j][1], da[j][1], d0));
-    d1 = fmaf(s[j][2], da[j][2], fmaf(s[j][3], da[j][3], d1));
-  }
-#pragma unroll
-  for (int o = 1; o <= 2; o <<= 1) {
-    d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-  }
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    da[j][0] = scale * s[j][0] * (da[j][0] - d0);
-    da[j][1] = scale * s[j][1] * (da[j][1] - d0);
-    da[j][2] = scale * s[j][2] * (da[j][2] - d1);
-    da[j][3] = scale * s[j][3] * (da[j][3] - d1);
-  }
-  const uint32_t x00 = h2(da[0][0], da[0][1]), x10 = h2(da[0][2], da[0][3]), x01 = h2(da[1][0], da[1][1]),
-                 x11 = h2(da[1][2], da[1][3]);
-  // dQ = dS K
-  {
-    const uint32_t dsa[4] = {x00, x10, x01, x11};
-    float y[HD / 8][4];
-    times_rows<HD>(dsa, K, ld, n, y);
-#pragma unroll
-    for (int c = 0; c < HD / 8; ++c) {
-      if (g < n) emit(1, g, 8 * c + 2 * t, y[c][0], y[c][1]);
-      if (g + 8 < n) emit(1, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
-    }
-  }
-  // dK = dS^T Q, dV = P^T dH (transposed A fragments: block (I, J) of X^T is block (J, I) of X transposed)
-  {
-    const uint32_t dst[4] = {trans8(x00), trans8(x01), trans8(x10), trans8(x11)};
-    float y[HD / 8][4];
-    times_rows<HD>(dst, Q, ld, n, y);
-#pragma unroll
-    for (int c = 0; c < HD / 8; ++c) {
-      if (g < n) emit(2, g, 8 * c + 2 * t, y[c][0], y[c][1]);
-      if (g + 8 < n) emit(2, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
-    }
-  }
-  {
-    const uint32_t pt[4] = {trans8(pa[0]), trans8(pa[2]), trans8(pa[1]), trans8(pa[3])};
-    float y[HD / 8][4];
-    times_rows<HD>(pt, dH, ld, n, y);
-#pragma unroll
-    for (int c = 0; c < HD / 8; ++c) {
-      if (g < n) emit(3, g, 8 * c + 2 * t, y[c][0], y[c][1]);
-      if (g + 8 < n) emit(3, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
-    }
-  }
+  for (int o = 1; o <= 16; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int ex = 0;
+  if (m > 0.f && isfinite(m)) frexpf(m, &ex);   // m = f 2^ex, f in [0.5, 1)
+  int k = 14 - ex;
+  k = k > 100 ? 100 : (k < -100 ? -100 : k);
+  const float up = ldexpf(1.0f, k);
+  x00 = h2(da[0][0] * up, da[0][1] * up);
+  x10 = h2(da[0][2] * up, da[0][3] * up);
+  x01 = h2(da[1][0] * up, da[1][1] * up);
+  x11 = h2(da[1][2] * up, da[1][3] * up);
+  return ldexpf(1.0f, -k);
 }
 
 // ---- shared-memory fragments by ldmatrix (FP16 row-major blocks, 16-byte-aligned rows)
@@ -365,7 +235,8 @@ __device__ __forceinline__ void attn_fwd_h(const __half *Qh, const __half *Kh, c
 // shared memory: Qh, Kh, Vh, dHh are u32 shared addresses of this sequence's first row and this head's
 // first feature in [rows][ldh] row-major FP16 arrays (Q unscaled), readable 16 rows down (rows >= n
 // hold finite values: the next sequence or zero padding).  Keys >= n are masked; query rows >= n get
-// zero probabilities, so they add nothing to dK and dV.  emit as in attn_fwd_bwd.  FULL: n = 16 at
+// zero probabilities, so they add nothing to dK and dV.  emit(kind, row, col, v0, v1): kind 0 = the
+// attention output O, 1 = dQ, 2 = dK, 3 = dV at (row, col..col+1), row < n.  FULL: n = 16 at
 // compile time (no masks).
 template <int HD, bool FULL = false, typename EMIT>
 __device__ __forceinline__ void attn_fwd_bwd_h(uint32_t Qh, uint32_t Kh, uint32_t Vh, uint32_t dHh, int ldh, int n,
@@ -452,8 +323,8 @@ __device__ __forceinline__ void attn_fwd_bwd_h(uint32_t Qh, uint32_t Kh, uint32_
     da[j][2] = scale * s[j][2] * (da[j][2] - d1);
     da[j][3] = scale * s[j][3] * (da[j][3] - d1);
   }
-  const uint32_t x00 = h2(da[0][0], da[0][1]), x10 = h2(da[0][2], da[0][3]), x01 = h2(da[1][0], da[1][1]),
-                 x11 = h2(da[1][2], da[1][3]);
+  uint32_t x00, x10, x01, x11;
+  const float ds_down = ds_pack_scaled(da, x00, x10, x01, x11);
   {   // dQ = dS K
     const uint32_t dsa[4] = {x00, x10, x01, x11};
     uint32_t b[HD / 8][2];
@@ -462,8 +333,8 @@ __device__ __forceinline__ void attn_fwd_bwd_h(uint32_t Qh, uint32_t Kh, uint32_
     mma_y<HD>(dsa, b, y);
 #pragma unroll
     for (int c = 0; c < HD / 8; ++c) {
-      if (q0) emit(1, g, 8 * c + 2 * t, y[c][0], y[c][1]);
-      if (q1) emit(1, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
+      if (q0) emit(1, g, 8 * c + 2 * t, y[c][0] * ds_down, y[c][1] * ds_down);
+      if (q1) emit(1, g + 8, 8 * c + 2 * t, y[c][2] * ds_down, y[c][3] * ds_down);
     }
   }
   {   // dK = dS^T Q
@@ -474,8 +345,8 @@ __device__ __forceinline__ void attn_fwd_bwd_h(uint32_t Qh, uint32_t Kh, uint32_
     mma_y<HD>(dst, b, y);
 #pragma unroll
     for (int c = 0; c < HD / 8; ++c) {
-      if (q0) emit(2, g, 8 * c + 2 * t, y[c][0], y[c][1]);
-      if (q1) emit(2, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
+      if (q0) emit(2, g, 8 * c + 2 * t, y[c][0] * ds_down, y[c][1] * ds_down);
+      if (q1) emit(2, g + 8, 8 * c + 2 * t, y[c][2] * ds_down, y[c][3] * ds_down);
     }
   }
   {   // dV = P^T dH

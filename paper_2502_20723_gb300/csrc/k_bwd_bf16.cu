@@ -100,6 +100,25 @@ __device__ __forceinline__ void mma_mm(const Sync &s, uint32_t a, int Ka, uint32
     mma_bf16(s.tmem + col, da + kk * Ka * 2, db + kk * Kb * 2, id, (acc || kk > 0) ? 1u : 0u);
 }
 
+// The same products with an explicit operand type (F16: FP16, else BF16) and, for mma_kk_range, a K range
+// [k0, k1) of both K-major images (multiples of 16).
+template <bool F16>
+__device__ __forceinline__ void mma_kk_range(const Sync &s, uint32_t a, uint32_t b, int K, int k0, int k1, int N,
+                                             uint32_t col, bool acc) {
+  const uint32_t id = idesc16<F16>(kRows, N);
+  const uint64_t da = dk(a, K), db = dk(b, K);
+  for (int kk = k0 / 16; kk < k1 / 16; ++kk)
+    mma_bf16(s.tmem + col, da + kk * 16, db + kk * 16, id, (acc || kk > k0 / 16) ? 1u : 0u);
+}
+template <bool F16>
+__device__ __forceinline__ void mma_mm_t(const Sync &s, uint32_t a, int Ka, uint32_t b, int Kb, int N, uint32_t col,
+                                         bool acc) {
+  const uint32_t id = idesc16_major<F16>(kRows, N, 1, 1);
+  const uint64_t da = dmn(a, Ka), db = dmn(b, Kb);
+  for (int kk = 0; kk < kRows / 16; ++kk)
+    mma_bf16(s.tmem + col, da + kk * Ka * 2, db + kk * Kb * 2, id, (acc || kk > 0) ? 1u : 0u);
+}
+
 __device__ __forceinline__ void sync_init(Sync &s, uint8_t *misc, int *err) {
   s.bar_mma = smem_u32(misc);
   s.bar_ld = smem_u32(misc + 8);
@@ -190,10 +209,16 @@ struct JacOut {
   const float2 *oref;
   size_t ldo;
   size_t nvirt;          // virtual configurations (0: the kernels run in VJP mode)
+  const float *iscale;   // inverse of the seeds' power-of-two scale (null: 1), applied to every output
 };
+
+__device__ __forceinline__ float jac_unscale(const JacOut &j) { return j.iscale ? *j.iscale : 1.0f; }
 
 __device__ __forceinline__ void jac_put2(const JacOut &j, size_t b, long long k, float re, float im) {
   const size_t i = b * j.ldo + (size_t)k;
+  const float u = jac_unscale(j);
+  re *= u;
+  im *= u;
   if (j.o16) {
     const float2 r = j.oref[k];
     reinterpret_cast<uint32_t *>(j.o16)[i] = pack_bf16(re - r.x, im - r.y);
@@ -203,14 +228,17 @@ __device__ __forceinline__ void jac_put2(const JacOut &j, size_t b, long long k,
 }
 __device__ __forceinline__ void jac_put1(const JacOut &j, size_t v, long long k, float x) {
   const size_t i = ((v >> 1) * j.ldo + (size_t)k) * 2 + (v & 1);
+  x *= jac_unscale(j);
   if (j.o16) j.o16[i] = __bfloat16_as_ushort(__float2bfloat16_rn(x - ((v & 1) ? j.oref[k].y : j.oref[k].x)));
   else j.o32[i] = x;
 }
 
 // MN-major x MN-major over rows [r0, r0 + 16 nsteps) of the images: D[tmem + col] = A_img^T B_img
+// (operand type F16: FP16, else BF16)
+template <bool F16 = kF16>
 __device__ __forceinline__ void mma_mm_rows(const Sync &s, uint32_t a, int Ka, uint32_t b, int Kb, int N,
                                             uint32_t col, int r0, int nsteps) {
-  const uint32_t id = idesc16_major<kF16>(kRows, N, 1, 1);
+  const uint32_t id = idesc16_major<F16>(kRows, N, 1, 1);
   const uint64_t da = dmn(a, Ka), db = dmn(b, Kb);
   for (int kk = 0; kk < nsteps; ++kk) {
     const int r = r0 / 16 + kk;
@@ -223,6 +251,7 @@ __device__ __forceinline__ void mma_mm_rows(const Sync &s, uint32_t a, int Ka, u
 // idx(m, n) < 0 skips an element.
 template <typename IDX, int NQ>
 __device__ __forceinline__ void jac_flush(const Sync &s, const JacOut &j, size_t tile, uint32_t col0, int N, IDX idx) {
+  const float u = jac_unscale(j);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = 32 * (warp & 3) + lane, cg = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
@@ -246,8 +275,8 @@ __device__ __forceinline__ void jac_flush(const Sync &s, const JacOut &j, size_t
           const long long k = idx(m, cg * (N / NQ) + jj + e);
           if (k < 0) continue;
           const size_t i = b * j.ldo + (size_t)k;
-          if (j.o16) reinterpret_cast<uint32_t *>(j.o16)[i] = pack_bf16(re[e] - rf[e].x, im[e] - rf[e].y);
-          else reinterpret_cast<float2 *>(j.o32)[i] = make_float2(re[e], im[e]);
+          if (j.o16) reinterpret_cast<uint32_t *>(j.o16)[i] = pack_bf16(u * re[e] - rf[e].x, u * im[e] - rf[e].y);
+          else reinterpret_cast<float2 *>(j.o32)[i] = make_float2(u * re[e], u * im[e]);
         }
       }
     }
@@ -261,6 +290,7 @@ __device__ __forceinline__ void jac_flush(const Sync &s, const JacOut &j, size_t
 template <int NQ>
 __device__ __noinline__ void jac_flush_rows(const Sync &s, const JacOut &j, size_t tile, uint32_t col0, int N,
                                                long long off, int ld, int mlim, float *stage) {
+  const float u = jac_unscale(j);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cg = warp >> 2, mb = 32 * (warp & 3);
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
@@ -296,7 +326,7 @@ __device__ __noinline__ void jac_flush_rows(const Sync &s, const JacOut &j, size
               const long long k = off + (long long)m * ld + cg * (N / NQ) + jj + 8 * h + c;
               const float2 v = st[r * 8 + c];
               reinterpret_cast<uint32_t *>(j.o16)[b * j.ldo + (size_t)k] =
-                  pack_bf16(v.x - rf[h][it].x, v.y - rf[h][it].y);
+                  pack_bf16(u * v.x - rf[h][it].x, u * v.y - rf[h][it].y);
             }
           }
         }
@@ -897,8 +927,9 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
                 const int rr = rb + r, col = h * HD + c;
                 if (kind == 0)
                   *reinterpret_cast<uint32_t *>(sm + G::H_OFF + canon(rr, col, 128)) = pack16<kF16>(v0, v1);
-                else
-                  *reinterpret_cast<uint32_t *>(dq_img + canon(rr, (kind - 1) * D + col, 3 * D)) = pack16<kF16>(v0, v1);
+                else   // dQ, dK: BF16 (FP32's exponent range; they sit decades below dV); dV: the operand type
+                  *reinterpret_cast<uint32_t *>(dq_img + canon(rr, (kind - 1) * D + col, 3 * D)) =
+                      kind < 3 ? pack_bf16(v0, v1) : pack16<kF16>(v0, v1);
               });
         }
       };
@@ -958,7 +989,8 @@ struct A2Geo {
   static constexpr int XR_OFF = W_OFF + W_BYTES;        // X images as stored [2][128][D] (next tile early)
   static constexpr int ST_OFF = XR_OFF + 2 * IMG;       // per-configuration mode: flush staging, 2 KB per warp
   static constexpr int DQ_OFF = ST_OFF + 16 * 2048;     // [dQ dK dV] images [2][128][3D]
-  static constexpr int M_OFF = DQ_OFF + 2 * QIMG;       // misc: bars, holder, dE [4][4][D]
+  static constexpr int XB_OFF = DQ_OFF + 2 * QIMG;      // FP16 operands: a BF16 copy of the tile's X image
+  static constexpr int M_OFF = XB_OFF + IMG;             // misc: bars, holder, dE [4][4][D]
   static constexpr int BYTES = M_OFF + 64 + 4 * 4 * 4 * D;
   static constexpr int C_W = 0, C_DX = 256;
 };
@@ -998,6 +1030,9 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
   const int row = 32 * (warp & 3) + lane, quarter = warp >> 2;
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
   const uint32_t wq = smem_u32(sm + G::W_OFF), xr0 = smem_u32(sm + G::XR_OFF), dq0 = smem_u32(sm + G::DQ_OFF);
+  // the dQ, dK block of the [dQ dK dV] image is BF16: with FP16 operands its products take a BF16 copy of X
+  // and BF16 rows of Wq, Wk (packed so); with BF16 operands everything is BF16 already
+  const uint32_t xb = kF16 ? smem_u32(sm + G::XB_OFF) : 0u;
   if (threadIdx.x == 0) {
     mbar_expect_tx(s.bar_ld, G::W_BYTES);
     bulk_g2s(wq, a.wqkv, G::W_BYTES, s.bar_ld);
@@ -1028,6 +1063,24 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
       if (tile + gridDim.x < a.tiles) load_nx(tile + gridDim.x);
       ok = wait_ld(s);   // this tile's X and [dQ dK dV] images
       if (!sync_ok(s, ok)) break;
+      if (kF16) {   // BF16 copy of the X image (same canonical layout); its last reader, the previous tile's
+                    // MMAs, has completed
+        const uint4 *src = reinterpret_cast<const uint4 *>(sm + G::XR_OFF + buf * G::IMG);
+        uint4 *dst = reinterpret_cast<uint4 *>(sm + G::XB_OFF);
+        for (int i = threadIdx.x; i < G::IMG / 16; i += kA2Threads) {
+          const uint4 q = src[i];
+          const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+          uint32_t o[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[e]));
+            o[e] = pack_bf16(f.x, f.y);
+          }
+          dst[i] = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+        fence_proxy_async();
+        __syncthreads();
+      }
       {   // the other buffers were last read by the previous tile's MMAs, which have completed
         const size_t nxt = tile + gridDim.x;
         if (nxt < a.tiles)
@@ -1036,8 +1089,17 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
       }
       if (threadIdx.x == 0) {
         tc_fence_after();
-        if (!a.jac.nvirt) mma_mm(s, xr, D, dq, 3 * D, 3 * D, G::C_W, !first);   // dWqkv += X^T [dQ dK dV]
-        mma_kk(s, dq, wq, 3 * D, D, G::C_DX, false);            // [dQ dK dV] Wqkv^T
+        if (kF16) {
+          if (!a.jac.nvirt) {   // dWq, dWk += X^T [dQ dK] (BF16); dWv += X^T dV (FP16)
+            mma_mm_t<false>(s, xb, D, dq, 3 * D, 2 * D, G::C_W, !first);
+            mma_mm_t<true>(s, xr, D, dq + (2 * D / 8) * 128, 3 * D, D, G::C_W + 2 * D, !first);
+          }
+          mma_kk_range<false>(s, dq, wq, 3 * D, 0, 2 * D, D, G::C_DX, false);   // [dQ dK] [Wq Wk]^T
+          mma_kk_range<true>(s, dq, wq, 3 * D, 2 * D, 3 * D, D, G::C_DX, true);  // + dV Wv^T
+        } else {
+          if (!a.jac.nvirt) mma_mm(s, xr, D, dq, 3 * D, 3 * D, G::C_W, !first);   // dWqkv += X^T [dQ dK dV]
+          mma_kk(s, dq, wq, 3 * D, D, G::C_DX, false);            // [dQ dK dV] Wqkv^T
+        }
         mma_commit(s.bar_mma);
       }
       ok = wait_mma(s);
@@ -1058,8 +1120,12 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
           if (threadIdx.x == 0) {
             tc_fence_after();
             // columns [D part, D part + D) of the [dQ dK dV] image start (D / 8) MN groups (128 B each) in
-            for (int c = 0; c < 4; ++c)
-              mma_mm_rows(s, xr, D, dq + part * (D / 8) * 128, 3 * D, D, 256 * (part & 1) + 64 * c, 32 * c, 2);
+            for (int c = 0; c < 4; ++c) {
+              if (kF16 && part < 2)   // dQ, dK parts: BF16
+                mma_mm_rows<false>(s, xb, D, dq + part * (D / 8) * 128, 3 * D, D, 256 * (part & 1) + 64 * c, 32 * c, 2);
+              else
+                mma_mm_rows(s, xr, D, dq + part * (D / 8) * 128, 3 * D, D, 256 * (part & 1) + 64 * c, 32 * c, 2);
+            }
             mma_commit(s.bar_mma);
           }
         };
@@ -1127,42 +1193,61 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
 
 // Non-transposed 16-bit packing: dst canonical [N][Ktot], element (n, koff + k) = W[n * ldw + col0 + k].
 __global__ void k_pack_nt(const float *__restrict__ W, int ldw, int col0, int K, int N, int Ktot, int koff,
-                          uint8_t *__restrict__ dst) {
+                          uint8_t *__restrict__ dst, int f16) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N * K) return;
   const int nn = i / K, k = i % K;
   const float w = W[(size_t)nn * ldw + col0 + k];
-  if (kF16) *reinterpret_cast<__half *>(dst + canon(nn, koff + k, Ktot)) = __float2half_rn(w);
+  if (f16) *reinterpret_cast<__half *>(dst + canon(nn, koff + k, Ktot)) = __float2half_rn(w);
   else *reinterpret_cast<__nv_bfloat16 *>(dst + canon(nn, koff + k, Ktot)) = __float2bfloat16_rn(w);
 }
 
-// Power-of-two scale of the VJP's cotangents: scale[0] = 2^-e with max_b max(|Re c_b|, |Im c_b|) = m 2^e,
-// m in [0.5, 1) (1 when every cotangent is zero or one is not finite), scale[1] = 1 / scale[0].  Scaled
-// by it, the backward's gradient images sit near the top of the 16-bit range instead of among FP16's
-// subnormals (|c| carries the 2 / Ns of the sample mean); the exact power of two is undone on the sums.
-__global__ void __launch_bounds__(1024) k_cot_scale(const float2 *__restrict__ cot, size_t B, float *__restrict__ scale) {
+// Power-of-two scale of the backward's cotangents (the VJP's, or the +-1 seeds of the log-derivatives):
+// with m = max_b max(|Re c_b|, |Im c_b|) and h = max_c (|Wh[c][0]| + |Wh[c][1]|), the last layer's dX is
+// at most B = 2 m h / N per element; scale[0] = 2^(11 - e) with B = f 2^e, f in [0.5, 1) (1 when B is zero
+// or not finite), scale[1] = 1 / scale[0].  It puts the largest gradient signal of the last layer near
+// 2^11, so that the backward's FP16 images hold the bulk of the signals (whose median sits three to five
+// decades below the largest) above FP16's subnormals, with 2^5 of headroom for their growth towards the
+// first layer; the exact power of two is undone on every output.
+__global__ void __launch_bounds__(1024) k_cot_scale(const float2 *__restrict__ cot, size_t B,
+                                                     const float *__restrict__ Wh, int D, int n,
+                                                     float *__restrict__ scale) {
   __shared__ float red[32];
-  float m = 0.f;
+  float m = 0.f, h = 0.f;
   for (size_t b = threadIdx.x; b < B; b += blockDim.x) {
     const float2 c = cot[b];
     m = fmaxf(m, fmaxf(fabsf(c.x), fabsf(c.y)));   // a NaN operand is dropped by fmaxf; caught downstream
   }
+  for (int c = threadIdx.x; c < D; c += blockDim.x) h = fmaxf(h, fabsf(Wh[2 * c]) + fabsf(Wh[2 * c + 1]));
+  m *= 2.0f;   // (both orders of the doubled configuration)
 #pragma unroll
-  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    h = fmaxf(h, __shfl_xor_sync(0xffffffffu, h, o));
+  }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
+  float mh = 0.f;
   if (threadIdx.x < 32) {
-    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    mh = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 16; o; o >>= 1) mh = fmaxf(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = h;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    h = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) h = fmaxf(h, __shfl_xor_sync(0xffffffffu, h, o));
     if (threadIdx.x == 0) {
+      const float bound = mh * h / (float)n;
       int e = 0;
-      if (m > 0.f && isfinite(m)) {
-        frexpf(m, &e);
-        e = e < -100 ? -100 : (e > 100 ? 100 : e);
-      }
-      scale[0] = ldexpf(1.0f, -e);
-      scale[1] = ldexpf(1.0f, e);
+      if (bound > 0.f && isfinite(bound)) frexpf(bound, &e);
+      int k = 11 - e;
+      k = k < -100 ? -100 : (k > 100 ? 100 : k);
+      scale[0] = ldexpf(1.0f, k);
+      scale[1] = ldexpf(1.0f, -k);
     }
   }
 }
@@ -1190,8 +1275,9 @@ cudaError_t TDO_OPFN(launch_pack_bwdtc)(const DevModel &m, uint8_t *dst, BwdTcLa
   using namespace tdo::TDO_BWNS;
   const int D = m.d, F = m.ffn;
   size_t off = 0;
-  auto pack = [&](const float *W, int ldw, int col0, int K, int N, int Ktot, int koff, uint8_t *out) {
-    k_pack_nt<<<(N * K + 255) / 256, 256, 0, st>>>(W, ldw, col0, K, N, Ktot, koff, out);
+  auto pack = [&](const float *W, int ldw, int col0, int K, int N, int Ktot, int koff, uint8_t *out,
+                  int f16 = kF16 ? 1 : 0) {
+    k_pack_nt<<<(N * K + 255) / 256, 256, 0, st>>>(W, ldw, col0, K, N, Ktot, koff, out, f16);
   };
   for (int l = 0; l < m.layers; ++l) {
     const DevLayer &L = m.L[l];
@@ -1210,8 +1296,8 @@ cudaError_t TDO_OPFN(launch_pack_bwdtc)(const DevModel &m, uint8_t *dst, BwdTcLa
     pack(L.Wo, D, 0, D, D, D, 0, dst + off);
     off += (size_t)D * D * 2;
     v.wqkvr = dst + off;
-    pack(L.Wq, D, 0, D, D, 3 * D, 0, dst + off);
-    pack(L.Wk, D, 0, D, D, 3 * D, D, dst + off);
+    pack(L.Wq, D, 0, D, D, 3 * D, 0, dst + off, 0);   // the rows multiplying the BF16 dQ, dK block
+    pack(L.Wk, D, 0, D, D, 3 * D, D, dst + off, 0);
     pack(L.Wv, D, 0, D, D, 3 * D, 2 * D, dst + off);
     off += (size_t)3 * D * D * 2;
   }
@@ -1341,8 +1427,8 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
                          size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st,
                          const BwdTcJac *jac) {
   using namespace tdo::TDO_BWNS;
-  JacOut jo{nullptr, nullptr, nullptr, 0, 0};
-  if (jac) jo = JacOut{jac->o32, jac->o16, jac->oref, jac->ldo, jac->nvirt};
+  JacOut jo{nullptr, nullptr, nullptr, 0, 0, nullptr};
+  if (jac) jo = JacOut{jac->o32, jac->o16, jac->oref, jac->ldo, jac->nvirt, bf.cscale + 1};
   constexpr int D = 64;
   const int n = m.n_sites, ts = tdo::seqs_per_tile(n), tc = ts / 2;
   const size_t tiles = bf.tiles, Bpad = tiles * tc;
@@ -1352,11 +1438,9 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
   const long long off_e = fo[0], off_wh = fo[1 + 8 * TDO_MAX_LAYERS], off_bh = fo[2 + 8 * TDO_MAX_LAYERS];
   cudaError_t e;
   {
-    if (!jac) {
-      k_cot_scale<<<1, 1024, 0, st>>>(cot, B, bf.cscale);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    HeadArgs h{cot, jac ? nullptr : bf.cscale, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, gacc, g_stride, off_wh, off_bh, D, jo};
+    k_cot_scale<<<1, 1024, 0, st>>>(cot, B, m.Wh, D, n, bf.cscale);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    HeadArgs h{cot, bf.cscale, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, gacc, g_stride, off_wh, off_bh, D, jo};
     if (jac) {
       const unsigned grid = (unsigned)((Bpad + 255) / 256 < 1024 ? (Bpad + 255) / 256 : 1024);
       k_head_bwd<<<grid ? grid : 1, 256, (2 * D + 2) * sizeof(float), st>>>(h);

@@ -157,14 +157,15 @@ __device__ __forceinline__ void park_image(const uint8_t *A, uint8_t *dst) {
     reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(A)[i];
 }
 
+// n_tile > 0: the tile's chain length (the ragged batch), else the model's.
 template <int D, int HD>
 __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm, Ctl &c, int ts,
                           const uint32_t *cfg_s, const uint32_t *cfg_p, float2 *res,
-                          const FwdStore *store = nullptr, size_t tile = 0) {
+                          const FwdStore *store = nullptr, size_t tile = 0, int n_tile = 0) {
   using G = Geo<D>;
   constexpr int DH = D / 2;   // columns per thread (half)
   constexpr int KS = G::KS;
-  const int n = m.n_sites;
+  const int n = n_tile > 0 ? n_tile : m.n_sites;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (warp & 3) + lane;
   const int half = warp >> 2;
@@ -538,6 +539,46 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_bf16(DevModel m, DevModelBF
   ctl_finish(c);
 }
 
+// Chains of different lengths in one persistent launch (the ansatz takes any N with the same theta):
+// configurations sorted by N into buckets, tiles of each bucket numbered consecutively in the bucket
+// order of tab; a CTA takes its next tile from the work counter `next` (dynamic), or tiles blockIdx.x +
+// k gridDim.x (next = null, static).  Results go back to the callers' positions through perm.
+template <int D, int HD>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_fwd_ragged(DevModel m, DevModelBF16 mb, const uint32_t *__restrict__ ssig, const uint32_t *__restrict__ ssigp,
+                 const uint32_t *__restrict__ perm, RaggedTab tab, unsigned long long *next, float2 *__restrict__ out,
+                 int *err) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  using G = Geo<D>;
+  __shared__ long long s_tile;
+  Ctl c;
+  ctl_init<D>(c, sm, err);
+  uint32_t *cs = reinterpret_cast<uint32_t *>(sm + G::M_OFF + 24);
+  uint32_t *cp = cs + 64;
+  float2 *res = reinterpret_cast<float2 *>(sm + G::M_OFF + 16 + 8 + 512 + 1024);
+  const long long total = tab.tile0[tab.nb];
+  for (long long it = 0;; ++it) {
+    if (threadIdx.x == 0) s_tile = next ? (long long)atomicAdd(next, 1ull) : blockIdx.x + it * (long long)gridDim.x;
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= total || c.bad) break;
+    int k = 0;
+    while (k + 1 < tab.nb && tile >= tab.tile0[k + 1]) ++k;
+    const int n = tab.n[k], ts = seqs_per_tile(n), tc = ts / 2;
+    const long long i0 = tab.base[k] + (tile - tab.tile0[k]) * tc, end = tab.base[k] + tab.count[k];
+    const long long idx = i0 + threadIdx.x;
+    if (threadIdx.x < tc) {
+      cs[threadIdx.x] = idx < end ? ssig[idx] : 0u;
+      cp[threadIdx.x] = idx < end ? ssigp[idx] : 0u;
+    }
+    __syncthreads();
+    if (!eval_tile<D, HD>(m, mb, sm, c, ts, cs, cp, res, nullptr, 0, n)) break;
+    if (threadIdx.x < tc && idx < end) out[perm[idx]] = res[threadIdx.x];
+    __syncthreads();
+  }
+  ctl_finish(c);
+}
+
 // Metropolis chains on the BF16 forward (same proposal stream and acceptance rule as the FP32 sampler,
 // including its diagonal mode).
 template <int D, int HD>
@@ -733,6 +774,39 @@ cudaError_t TDO_OPFN(launch_fwd_bf16)(const DevModel &m, const DevModelBF16 &mb,
                             size_t B, float2 *logrho, int *err_flag, int n_sm, cudaStream_t st) {
   return TDO_OPFN(launch_fwd_bf16_store)(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, nullptr, nullptr, nullptr,
                                          nullptr, 0);
+}
+
+template <int D, int HD>
+static cudaError_t fwd_ragged_impl(const DevModel &m, const DevModelBF16 &mb, const uint32_t *ssig,
+                                   const uint32_t *ssigp, const uint32_t *perm, const RaggedTab &tab,
+                                   unsigned long long *next, float2 *out, int *err, int n_sm, int ctas_per_sm_req,
+                                   cudaStream_t st) {
+  using namespace tdo::TDO_OPNS;
+  const int bytes = Geo<D>::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_ragged<D, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fwd_ragged<D, HD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  const int fit = ctas_per_sm(k_fwd_ragged<D, HD>, bytes);
+  const int per_sm = ctas_per_sm_req < fit ? ctas_per_sm_req : fit;
+  const long long total = tab.tile0[tab.nb];
+  long long grid = (long long)n_sm * (per_sm < 1 ? 1 : per_sm);
+  if (grid > total) grid = total;
+  if (grid < 1) return cudaSuccess;
+  if (next && (e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  k_fwd_ragged<D, HD><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, ssig, ssigp, perm, tab, next, out, err);
+  return cudaGetLastError();
+}
+
+cudaError_t TDO_OPFN(launch_fwd_ragged)(const DevModel &m, const DevModelBF16 &mb, const uint32_t *ssig,
+                                        const uint32_t *ssigp, const uint32_t *perm, const RaggedTab &tab,
+                                        unsigned long long *next, float2 *out, int *err_flag, int n_sm,
+                                        int ctas_per_sm_req, cudaStream_t st) {
+  if (m.d == 64 && m.dh == 8) return fwd_ragged_impl<64, 8>(m, mb, ssig, ssigp, perm, tab, next, out, err_flag, n_sm, ctas_per_sm_req, st);
+  if (m.d == 64 && m.dh == 16) return fwd_ragged_impl<64, 16>(m, mb, ssig, ssigp, perm, tab, next, out, err_flag, n_sm, ctas_per_sm_req, st);
+  if (m.d == 32 && m.dh == 8) return fwd_ragged_impl<32, 8>(m, mb, ssig, ssigp, perm, tab, next, out, err_flag, n_sm, ctas_per_sm_req, st);
+  if (m.d == 32 && m.dh == 16) return fwd_ragged_impl<32, 16>(m, mb, ssig, ssigp, perm, tab, next, out, err_flag, n_sm, ctas_per_sm_req, st);
+  return cudaErrorInvalidValue;
 }
 
 template <int D, int HD>

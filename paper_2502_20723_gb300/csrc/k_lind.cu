@@ -234,6 +234,38 @@ __global__ void k_adam(double *__restrict__ theta, const double *__restrict__ de
   }
 }
 
+// Ragged batches: counts of each chain length (shared-memory histogram per block, then global atomics).
+__global__ void k_ragged_hist(const int32_t *__restrict__ n_sites, size_t B, unsigned long long *__restrict__ counts) {
+  __shared__ unsigned int h[33];
+  if (threadIdx.x < 33) h[threadIdx.x] = 0u;
+  __syncthreads();
+  for (size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x; b < B; b += gridDim.x * (size_t)blockDim.x) {
+    const int n = n_sites[b];
+    atomicAdd(&h[(n >= 1 && n <= 32) ? n : 0], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 33 && h[threadIdx.x]) atomicAdd(counts + threadIdx.x, (unsigned long long)h[threadIdx.x]);
+}
+
+// Scatter into buckets: position cursor[N]++ (atomics; the order inside a bucket is arbitrary, the results
+// go back through perm), perm = source index.  Entries outside 1..32 were rejected by the caller.
+__global__ void k_ragged_scatter(const int32_t *__restrict__ n_sites, const uint32_t *__restrict__ sig,
+                                 const uint32_t *__restrict__ sigp, size_t B, unsigned long long *__restrict__ cursor,
+                                 uint32_t *__restrict__ ssig, uint32_t *__restrict__ ssigp, uint32_t *__restrict__ perm) {
+  for (size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x; b < B; b += gridDim.x * (size_t)blockDim.x) {
+    const unsigned long long pos = atomicAdd(cursor + n_sites[b], 1ull);
+    ssig[pos] = sig[b];
+    ssigp[pos] = sigp[b];
+    perm[pos] = (uint32_t)b;
+  }
+}
+
+__global__ void k_unpermute(const float2 *__restrict__ in, const uint32_t *__restrict__ perm, size_t B,
+                            float2 *__restrict__ out) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < B; j += gridDim.x * (size_t)blockDim.x)
+    out[perm[j]] = in[j];
+}
+
 }  // namespace tdo
 
 static unsigned grid_for(size_t n, int block) {
@@ -300,6 +332,27 @@ cudaError_t launch_conv_table_k(int d, int c1, const float *Wc1, const float *bc
 cudaError_t launch_params_f32(const double *theta, size_t P, const long long *tab, int n_tensors,
                               float *dst, cudaStream_t st) {
   tdo::k_params_f32<<<grid_for(P, 256), 256, 0, st>>>(theta, P, tab, n_tensors, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ragged_hist(const int32_t *n_sites, size_t B, unsigned long long *counts, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, 33 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess || B == 0) return e;
+  tdo::k_ragged_hist<<<grid_for(B, 256), 256, 0, st>>>(n_sites, B, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ragged_scatter(const int32_t *n_sites, const uint32_t *sig, const uint32_t *sigp, size_t B,
+                                  unsigned long long *cursor, uint32_t *ssig, uint32_t *ssigp, uint32_t *perm,
+                                  cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  tdo::k_ragged_scatter<<<grid_for(B, 256), 256, 0, st>>>(n_sites, sig, sigp, B, cursor, ssig, ssigp, perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute(const float2 *in, const uint32_t *perm, size_t B, float2 *out, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  tdo::k_unpermute<<<grid_for(B, 256), 256, 0, st>>>(in, perm, B, out);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 #include <string>
 #include <utility>
 #include <vector>
+#include <array>
 
 #include "../../include/tdo.h"
 #include "tdo_internal.cuh"
@@ -153,6 +154,11 @@ struct tdo_ctx {
   double adam_b1 = 0.9, adam_b2 = 0.999, adam_eps = 1e-8;
   long long adam_t = 0;
   DBuf adam_m, adam_v;
+  // ragged batches: bucket counts, cursors, sorted configurations, permutation, work counter, FP32 results
+  DBuf rg_counts, rg_cursor, rg_ssig, rg_ssigp, rg_perm, rg_next, rg_tmp, rg_n;
+  // autotuned launch shape of the ragged forward per mix of chain lengths (bit N-1 set for each N present):
+  // (CTAs per SM, descending-N tile order, dynamic work counter)
+  std::map<uint32_t, std::array<int, 3>> rg_tuned;
   bool have_delta = false;
   int last_sr_iters = 0;
   double last_sr_resid = 0;
@@ -638,6 +644,131 @@ extern "C" tdo_status tdo_log_rho(tdo_ctx *c, const uint32_t *sig, const uint32_
     CU(c, cudaStreamSynchronize(c->stream));
     TRY(check_err_flag(c));
   }
+  return TDO_OK;
+}
+
+// Ragged batch on the device: bucketing, then one persistent tensor-core launch (autotuned on the first call
+// with a new mix of chain lengths), or one FP32 launch per bucket.
+static tdo_status ragged_dev(tdo_ctx *c, const int32_t *dn, const uint32_t *ds, const uint32_t *dp, size_t B,
+                             float2 *out) {
+  CU(c, c->rg_counts.ensure(33 * sizeof(unsigned long long)));
+  CU(c, c->rg_cursor.ensure(33 * sizeof(unsigned long long)));
+  CU(c, c->rg_ssig.ensure(4 * B));
+  CU(c, c->rg_ssigp.ensure(4 * B));
+  CU(c, c->rg_perm.ensure(4 * B));
+  CU(c, c->rg_next.ensure(sizeof(unsigned long long)));
+  CU(c, launch_ragged_hist(dn, B, c->rg_counts.as<unsigned long long>(), c->stream));
+  unsigned long long cnt[33];
+  CU(c, cudaMemcpyAsync(cnt, c->rg_counts.p, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  if (cnt[0]) return fail(c, TDO_EUNSUPPORTED, "tdo_log_rho_ragged: %llu chain lengths outside 1..32", cnt[0]);
+  unsigned long long base[33] = {0};
+  uint32_t mix = 0;
+  for (int n = 1; n <= 32; ++n) {
+    base[n] = (n > 1 ? base[n - 1] + cnt[n - 1] : 0);
+    if (cnt[n]) mix |= 1u << (n - 1);
+  }
+  CU(c, cudaMemcpyAsync(c->rg_cursor.p, base, sizeof(base), cudaMemcpyHostToDevice, c->stream));
+  uint32_t *ss = c->rg_ssig.as<uint32_t>(), *sp = c->rg_ssigp.as<uint32_t>(), *perm = c->rg_perm.as<uint32_t>();
+  CU(c, launch_ragged_scatter(dn, ds, dp, B, c->rg_cursor.as<unsigned long long>(), ss, sp, perm, c->stream));
+  if (!c->tc) {   // FP32 path: one launch per bucket, the model's chain length set to the bucket's
+    CU(c, c->rg_tmp.ensure(8 * B));
+    Timed tm(c, G_FWD);
+    int nl = 0;
+    for (int n = 1; n <= 32; ++n) {
+      if (!cnt[n]) continue;
+      DevModel dm = c->dm;
+      dm.n_sites = n;
+      CU(c, launch_fwd32(dm, ss + base[n], sp + base[n], cnt[n], c->rg_tmp.as<float2>() + base[n], c->n_sm, c->stream));
+      ++nl;
+    }
+    CU(c, launch_unpermute(c->rg_tmp.as<float2>(), perm, B, out, c->stream));
+    tm.done(nl + 1);
+    return TDO_OK;
+  }
+  auto table = [&](bool desc) {
+    RaggedTab t{};
+    long long tile = 0;
+    for (int i = 0; i < 32; ++i) {
+      const int n = desc ? 32 - i : 1 + i;
+      if (!cnt[n]) continue;
+      const int k = t.nb++;
+      t.n[k] = n;
+      t.base[k] = (long long)base[n];
+      t.count[k] = (long long)cnt[n];
+      t.tile0[k] = tile;
+      const int ts = 2 * (128 / (2 * n)), tc = (ts < 2 ? 2 : ts) / 2;   // configurations per 128-row tile
+      tile += ((long long)cnt[n] + tc - 1) / tc;
+    }
+    t.tile0[t.nb] = tile;
+    return t;
+  };
+  auto launch = [&](const std::array<int, 3> &cfg) -> cudaError_t {
+    const RaggedTab t = table(cfg[1] != 0);
+    return TC_LAUNCH(c, launch_fwd_ragged, c->dm, c->dmb, ss, sp, perm, t,
+                     cfg[2] ? c->rg_next.as<unsigned long long>() : nullptr, out, c->errflag.as<int>(), c->n_sm,
+                     cfg[0], c->stream);
+  };
+  auto it = c->rg_tuned.find(mix);
+  if (it == c->rg_tuned.end()) {
+    // autotune: time each candidate once on this batch (identical outputs), keep the fastest
+    const std::array<int, 3> cand[4] = {{2, 1, 1}, {2, 0, 1}, {2, 0, 0}, {1, 1, 1}};
+    cudaEvent_t e0, e1;
+    CU(c, cudaEventCreate(&e0));
+    CU(c, cudaEventCreate(&e1));
+    float best = 0.f;
+    int bi = 0;
+    for (int i = 0; i < 4; ++i) {
+      CU(c, cudaEventRecord(e0, c->stream));
+      const cudaError_t e = launch(cand[i]);
+      CU(c, cudaEventRecord(e1, c->stream));
+      CU(c, e);
+      CU(c, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CU(c, cudaEventElapsedTime(&ms, e0, e1));
+      if (i == 0 || ms < best) { best = ms; bi = i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    it = c->rg_tuned.emplace(mix, cand[bi]).first;
+  }
+  Timed tm(c, G_FWD);
+  CU(c, launch(it->second));
+  tm.done(1);
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_log_rho_ragged(tdo_ctx *c, const int32_t *n_sites, const uint32_t *sig, const uint32_t *sigp,
+                                         size_t B, float *logrho) {
+  if (!c) return TDO_EINVAL;
+  if (B == 0) return TDO_OK;
+  if (!n_sites || !sig || !sigp || !logrho) return fail(c, TDO_EINVAL, "NULL buffer");
+  if (B > 0xFFFFFFFFull) return fail(c, TDO_EINVAL, "B must be below 2^32");
+  const void *dn, *ds, *dp;
+  bool h0, h1, h2, h3 = false;
+  TRY(stage_in(c, 2, n_sites, 4 * B, &dn, &h0));
+  TRY(stage_in(c, 0, sig, 4 * B, &ds, &h1));
+  TRY(stage_in(c, 1, sigp, 4 * B, &dp, &h2));
+  float2 *dout = reinterpret_cast<float2 *>(logrho);
+  if (!is_device_ptr(logrho)) {
+    CU(c, c->stage_out.ensure(8 * B));
+    dout = c->stage_out.as<float2>();
+  }
+  TRY(ragged_dev(c, (const int32_t *)dn, (const uint32_t *)ds, (const uint32_t *)dp, B, dout));
+  TRY(deliver(c, logrho, dout, 8 * B, &h3));
+  CU(c, cudaStreamSynchronize(c->stream));
+  TRY(check_err_flag(c));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_ragged_tuning(const tdo_ctx *c, uint32_t mix, int *ctas_per_sm, int *descending,
+                                        int *dynamic_schedule) {
+  if (!c) return TDO_EINVAL;
+  const auto it = c->rg_tuned.find(mix);
+  if (it == c->rg_tuned.end()) return TDO_EINVAL;
+  if (ctas_per_sm) *ctas_per_sm = it->second[0];
+  if (descending) *descending = it->second[1];
+  if (dynamic_schedule) *dynamic_schedule = it->second[2];
   return TDO_OK;
 }
 

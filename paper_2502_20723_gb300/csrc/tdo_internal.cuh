@@ -57,6 +57,17 @@ cudaError_t launch_fwd32(const DevModel &m, const uint32_t *sig, const uint32_t 
 cudaError_t launch_sample32(const DevModel &m, size_t n_chains, size_t n_sweeps, uint64_t seed,
                             uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
                             uint32_t *ssigp, unsigned long long *accepted, int diag, int n_sm, cudaStream_t st);
+// A batch of configurations of chains of different lengths, sorted into buckets of equal N: bucket k
+// (in tile order) holds count[k] configurations of N = n[k] from sorted position base[k], its tiles
+// numbered from tile0[k] (tile0[nb] = all tiles).
+struct RaggedTab {
+  int nb;
+  int n[32];
+  long long tile0[33];
+  long long base[32];
+  long long count[32];
+};
+
 // Tensor-core forward and sampler, BF16 operands (the _f16 variants: FP16 operands).
 cudaError_t launch_wait_probe(int *err_flag, long long spin, cudaStream_t st);
 cudaError_t launch_fwd_bf16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
@@ -66,6 +77,23 @@ cudaError_t launch_fwd_bf16_f16(const DevModel &m, const DevModelBF16 &mb, const
                                 const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
                                 cudaStream_t st);
 bool bf16_supported(const DevModel &m);
+// The ragged batch in one persistent launch (next: a device work counter, or null for a static schedule;
+// ctas_per_sm_req: 1 or 2, capped by what fits).
+cudaError_t launch_fwd_ragged(const DevModel &m, const DevModelBF16 &mb, const uint32_t *ssig, const uint32_t *ssigp,
+                              const uint32_t *perm, const RaggedTab &tab, unsigned long long *next, float2 *out,
+                              int *err_flag, int n_sm, int ctas_per_sm_req, cudaStream_t st);
+cudaError_t launch_fwd_ragged_f16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *ssig,
+                                  const uint32_t *ssigp, const uint32_t *perm, const RaggedTab &tab,
+                                  unsigned long long *next, float2 *out, int *err_flag, int n_sm, int ctas_per_sm_req,
+                                  cudaStream_t st);
+// Bucketing of a ragged batch: counts[N] for N in 1..32 (counts[0]: entries outside 1..32); then the
+// scatter of sig, sigp into ssig, ssigp at cursor[N]++ (cursor preset to each bucket's base), perm = the
+// source position; and out[perm[j]] = in[j] for the FP32 path's per-bucket results.
+cudaError_t launch_ragged_hist(const int32_t *n_sites, size_t B, unsigned long long *counts, cudaStream_t st);
+cudaError_t launch_ragged_scatter(const int32_t *n_sites, const uint32_t *sig, const uint32_t *sigp, size_t B,
+                                  unsigned long long *cursor, uint32_t *ssig, uint32_t *ssigp, uint32_t *perm,
+                                  cudaStream_t st);
+cudaError_t launch_unpermute(const float2 *in, const uint32_t *perm, size_t B, float2 *out, cudaStream_t st);
 cudaError_t launch_sample_bf16(const DevModel &m, const DevModelBF16 &mb, size_t n_chains,
                                size_t n_sweeps, uint64_t seed, uint64_t counter, uint32_t *sig,
                                uint32_t *sigp, uint32_t *ssig, uint32_t *ssigp,

@@ -23,7 +23,7 @@ STATUS = {0: "TDO_OK", -1: "TDO_EINVAL", -2: "TDO_ENOMEM", -3: "TDO_ECUDA", -4: 
 EXPORTS = ["tdo_model_num_params", "tdo_create", "tdo_destroy", "tdo_num_params", "tdo_max_connections",
            "tdo_set_params", "tdo_get_params", "tdo_log_rho", "tdo_log_rho_vjp", "tdo_jacobian",
            "tdo_connections", "tdo_local_estimator", "tdo_local_estimator_noalloc", "tdo_sample", "tdo_grad", "tdo_sr_solve", "tdo_set_sr_options", "tdo_sr_step",
-           "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_sr_report", "tdo_wait_selftest", "tdo_set_optimizer", "tdo_measure_peak", "tdo_last_error", "tdo_sample_diag", "tdo_magnetisation",
+           "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_sr_report", "tdo_wait_selftest", "tdo_set_optimizer", "tdo_log_rho_ragged", "tdo_ragged_tuning", "tdo_measure_peak", "tdo_last_error", "tdo_sample_diag", "tdo_magnetisation",
            "tdo_purity", "tdo_schedule_value", "tdo_vmc_step"]
 
 
@@ -94,6 +94,8 @@ def lib() -> C.CDLL:
         L.tdo_set_params.argtypes = [vp, vp]
         L.tdo_get_params.argtypes = [vp, vp]
         L.tdo_log_rho.argtypes = [vp, vp, vp, sz, vp]
+        L.tdo_log_rho_ragged.argtypes = [vp, vp, vp, vp, sz, vp]
+        L.tdo_ragged_tuning.argtypes = [vp, C.c_uint32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.tdo_log_rho_vjp.argtypes = [vp, vp, vp, sz, vp, vp]
         L.tdo_jacobian.argtypes = [vp, vp, vp, sz, vp]
         L.tdo_connections.argtypes = [vp, vp, vp, sz, vp, vp, vp, vp]
@@ -239,6 +241,19 @@ class Context:
         out = self._like(sig, (B, 2), np.float32) if out is None else out
         self._chk(lib().tdo_log_rho(self.h, _ptr(sig), _ptr(sigp), B, _ptr(out)))
         return out
+
+    def log_rho_ragged(self, n_sites, sig, sigp, out=None):
+        """tdo_log_rho_ragged: log rho of configurations of chains of lengths n_sites[b] (int32)."""
+        B = len(sig)
+        out = self._like(sig, (B, 2), np.float32) if out is None else out
+        self._chk(lib().tdo_log_rho_ragged(self.h, _ptr(n_sites), _ptr(sig), _ptr(sigp), B, _ptr(out)))
+        return out
+
+    def ragged_tuning(self, mix: int):
+        """(CTAs per SM, descending order, dynamic schedule) kept by the autotuner for a mix of lengths."""
+        a, b, d = C.c_int(), C.c_int(), C.c_int()
+        self._chk(lib().tdo_ragged_tuning(self.h, mix, C.byref(a), C.byref(b), C.byref(d)))
+        return a.value, b.value, d.value
 
     def log_rho_vjp(self, sig, sigp, cot, grad):
         self._chk(lib().tdo_log_rho_vjp(self.h, _ptr(sig), _ptr(sigp), len(sig), _ptr(cot), _ptr(grad)))

@@ -76,5 +76,7 @@ def test_null_context_is_rejected_without_a_device(libtdo):
     assert libtdo.tdo_sr_report(None, None, None, None) == einval
     assert libtdo.tdo_wait_selftest(None, 16) == einval
     assert libtdo.tdo_set_optimizer(None, 1, 0.9, 0.999, 1e-8) == einval
+    assert libtdo.tdo_log_rho_ragged(None, None, None, None, 4, None) == einval
+    assert libtdo.tdo_ragged_tuning(None, 1, None, None, None) == einval
     assert libtdo.tdo_measure_peak(2, None, ctypes.byref(d)) == einval
     assert libtdo.tdo_measure_peak(0, None, None) == einval

@@ -149,3 +149,23 @@ def test_golden_ed_observables_are_consistent():
             assert pr["g"] * e["sy"] == pytest.approx(pr["gamma"] * (1.0 + e["sz"]), abs=1e-8), name
     for q in ("sx", "sy", "sz", "purity"):
         assert gold["ising2d_2x2_V2_g1"][q] == pytest.approx(gold["ising_n4_V2_g1"][q], abs=1e-10)
+
+
+def test_golden_propagated_states_carry_their_certificates():
+    """Steady states too large for the dense LU (N = 8 and the 10-site Heisenberg chain with fields of the
+    Heisenberg section) come from RK4 propagation; each stores the certificate computed from the state
+    itself: ||Lhat rho|| / ||rho|| below 1e-10 (the steady-state equation), rho Hermitian and positive
+    semidefinite to 1e-10, unit trace."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ed_observables.json")))
+    assert "heis_n10_By0.5" in gold
+    for name, e in gold.items():
+        if e["method"].startswith("RK4"):
+            c = e["certificate"]
+            assert c["residual"] < 1e-10, name
+            assert c["herm_err"] < 1e-10, name
+            assert c["min_eig"] > -1e-10, name
+            assert abs(c["trace"] - 1.0) < 1e-12, name
+            for q in ("sx", "sy", "sz"):
+                assert -1.0 <= e[q] <= 1.0, name
