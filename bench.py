@@ -328,12 +328,78 @@ def run_ours(args) -> dict | None:
             "logrho_evals_per_s_fwd_kernel": fwd_evals / (og["fwd"]["ms"] * 1e-3) if og["fwd"]["ms"] else None,
             "breakdown_ms_per_step": {g: round(v["ms"], 3) for g, v in og.items()},
             "costs": [round(c, 6) for c in other["costs"]], "sr_cg_iterations": other["sr_iters"]}
+    if not args.no_config5:
+        res["config5"] = config5_leg(tdo, torch, stream, flush)
     if world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(args.cpu_budget, main["theta"], sub_s, sub_p)
         ref_l, ref_c = base.pop("lloc_ref"), base.pop("cost_ref")
         res["cpu_baseline"] = base
         res["at_set_error"] = set_error_report(set_err_gpu, ref_l, ref_c)
     return res
+
+
+# ------------------------------------------------------------------ chains of uneven length (one launch)
+CONFIG5_N = (8, 12, 16, 20, 24, 32)
+CONFIG5_SAMPLES = 32768
+
+
+def config5_leg(tdo, torch, stream, flush, reps: int = 5) -> dict:
+    """The XYZ chains (Jx = 0.9, Jy = Jz = 1, gamma = 1) of N in {8, 12, 16, 20, 24, 32}, 32,768 samples
+    in equal shares (two Metropolis sweeps from uniform configurations, FP16 context per N), and every
+    configuration the Lindbladian connects to them, evaluated as one interleaved batch by
+    tdo_log_rho_ragged: one persistent tensor-core launch across the lengths (autotuned on its first
+    call), timed over `reps` calls with the L2 flushed between them."""
+    spec = synth.model_spec(D, HEADS, LAYERS, MLP)
+    theta = synth.init_params(spec, seed=0)
+    per = CONFIG5_SAMPLES // len(CONFIG5_N)
+    rn, rs, rp = [], [], []
+    for i, n in enumerate(CONFIG5_N):
+        k = per + (CONFIG5_SAMPLES - per * len(CONFIG5_N) if i == 0 else 0)
+        ctx = tdo.Context(synth.xyz_chain(n, Jx=0.9, Jy=1.0, Jz=1.0), spec, theta, "fp16", stream=stream.cuda_stream)
+        s0, s1 = synth.random_configs(n, k, seed=500 + n)
+        sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
+        sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
+        ctx.sample(sig, sigp, 2, 77 + n, 0)
+        cnt, cs, cp, _ = ctx.connections(sig, sigp)
+        mask = torch.arange(cs.shape[1], device="cuda")[None, :] < cnt[:, None]
+        rs.append(cs[mask])
+        rp.append(cp[mask])
+        rn.append(torch.full((int(mask.sum().item()),), n, dtype=torch.int32, device="cuda"))
+        ctx.close()
+    n_all, s_all, p_all = torch.cat(rn), torch.cat(rs), torch.cat(rp)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    order = torch.randperm(len(n_all), device="cuda", generator=g)   # interleaved lengths
+    n_all, s_all, p_all = n_all[order].contiguous(), s_all[order].contiguous(), p_all[order].contiguous()
+    counts = {int(n): int((n_all == n).sum().item()) for n in CONFIG5_N}
+    flops = sum(c * 2.0 * flops_per_sequence(n=n) for n, c in counts.items())
+    mix = sum(1 << (n - 1) for n in CONFIG5_N)
+    peaks = measured_peaks()
+    peak_t = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    out = {"workload": "xyz_uneven_n8-32_d64_l4_h8_mlp4_ns32768", "samples": CONFIG5_SAMPLES,
+           "rows_per_n": counts, "rows": int(len(n_all)), "algorithmic_flop_per_call": flops, "reps": reps,
+           "precisions": {}}
+    for prec in ("fp16", "bf16", "fp32"):
+        ctx = tdo.Context(synth.xyz_chain(16), spec, theta, prec, stream=stream.cuda_stream)
+        ctx.log_rho_ragged(n_all, s_all, p_all)   # first call: bucketing and (tensor core) autotuning
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.log_rho_ragged(n_all, s_all, p_all)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = statistics.median(ms)
+        r = {"ms_per_call": t, "logrho_evals_per_s": len(n_all) / (t * 1e-3), "tflops": flops / (t * 1e-3) / 1e12}
+        if prec != "fp32":
+            r["tensor_frac_of_bf16_sustained"] = r["tflops"] / peak_t
+            r["tuned_shape"] = dict(zip(("ctas_per_sm", "descending", "dynamic"), ctx.ragged_tuning(mix)))
+        out["precisions"][prec] = r
+        ctx.close()
+    return out
 
 
 # ---------------------------------------------------------------------------------- oracle on the CPU
@@ -512,6 +578,7 @@ def main():
     ap.add_argument("--burn-in", type=int, default=4)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-config5", action="store_true", help="skip the uneven-length (N = 8..32) leg")
     ap.add_argument("--kernel-case", default=None, choices=["fwd", "grad", "jac", "sample", "sr"],
                     help="run one call of one kind on a reduced sample count (profiling) and exit")
     ap.add_argument("--case-samples", type=int, default=1024)

@@ -1397,6 +1397,55 @@ struct BwdTcJac {
 bool bwdtc_jac_supported(const DevModel &m) { return bwdtc_supported(m) && m.n_sites == 16; }
 #endif
 
+namespace tdo {
+namespace TDO_BWNS {
+// VJP-mode db2 of a layer: the column sums of the FP32 dX at its MLP output, dX [rows][D] (padding rows
+// zero), summed in FP64 per thread over a row range; one float atomic per column and block into the
+// block's gradient copy.  (A sum over every connected row cancels heavily: summing the 16-bit image
+// would leave the rounding of single rows in it.)
+__global__ void __launch_bounds__(256) k_db2_rows(const float *__restrict__ dX, size_t rows, int D, float *g,
+                                                  size_t g_stride, long long off) {
+  __shared__ double red[256];
+  const int groups = 256 / D, c = threadIdx.x % D, grp = threadIdx.x / D;
+  double a = 0.0;
+  if (grp < groups)
+    for (size_t r = blockIdx.x * (size_t)groups + grp; r < rows; r += gridDim.x * (size_t)groups) a += dX[r * D + c];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.x < D) {
+    double t = 0.0;
+    for (int k = 0; k < groups; ++k) t += red[k * D + threadIdx.x];
+    atomicAdd(g + (size_t)(blockIdx.x % kCopiesMax) * g_stride + off + threadIdx.x, (float)t);
+  }
+}
+
+// The last layer's db2, whose dX is formed from the head: every sequence has N rows, each carrying
+// (1/N) Wh dF of its sequence, so db2[c] = sum_o Wh[c][o] S_o with S_o = sum over configurations of the
+// F_o cotangents of both orders, dF [Bpad][4] (zero beyond B).  One block, FP64 sums.
+__global__ void __launch_bounds__(256) k_db2_head(const float *__restrict__ dF, size_t Bpad, const float *__restrict__ Wh,
+                                                  int D, float *g, long long off) {
+  __shared__ double red[2][256];
+  double s0 = 0.0, s1 = 0.0;
+  for (size_t b = threadIdx.x; b < Bpad; b += blockDim.x) {
+    s0 += (double)dF[4 * b] + (double)dF[4 * b + 2];
+    s1 += (double)dF[4 * b + 1] + (double)dF[4 * b + 3];
+  }
+  red[0][threadIdx.x] = s0;
+  red[1][threadIdx.x] = s1;
+  __syncthreads();
+  for (int w = 128; w; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < D; c += blockDim.x)
+    atomicAdd(g + off + c, (float)((double)Wh[2 * c] * red[0][0] + (double)Wh[2 * c + 1] * red[1][0]));
+}
+}  // namespace TDO_BWNS
+}  // namespace tdo
+
 // Virtual configurations of the per-configuration mode: v = 2 b + seed, cotangent (1, 0) or (0, -1).
 namespace tdo {
 namespace TDO_BWNS {
@@ -1479,7 +1528,7 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
         ma.dxo = bf.dxa;
         ma.dxm = bf.dxb;
         ma.tiles = tiles;
-        ma.do_db2 = hb == 0;
+        ma.do_db2 = hb == 0 && jac;   // VJP mode: db2 from the FP32 dX (below)
         ma.g = gacc;
         ma.g_stride = g_stride;
         ma.off_w1 = W1[l] + hb * 128;
@@ -1498,6 +1547,12 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
         else k_bwd_mlp<D, true><<<grid, kMlpThreads, MlpGeo<D>::BYTES, st>>>(ma);
       }
       dxmid = bf.dxb;
+      if (!jac) {   // db2 of this layer from FP32 data (its MLP output's dX: the head's for the last layer)
+        if (l == m.layers - 1)
+          k_db2_head<<<1, 256, 0, st>>>(bf.dF, Bpad, m.Wh, D, gacc, b2[l]);
+        else
+          k_db2_rows<<<(unsigned)(2 * n_sm), 256, 0, st>>>(bf.dxa, tiles * kRows, D, gacc, g_stride, b2[l]);
+      }
     }
     A1Args a1;
     a1.wqkvT = reinterpret_cast<const uint8_t *>(mb.Wqkv[l]);

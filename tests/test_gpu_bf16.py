@@ -1,4 +1,4 @@
-"""BF16 tensor-core path (tcgen05) vs the FP64 oracle, through the C ABI.
+"""Tensor-core path (tcgen05; BF16 contexts, and FP16 contexts where named) vs the FP64 oracle, through the C ABI.
 
 Tolerances: log rho within 2e-2 absolute (phase modulo 2 pi), cost within 1e-3 relative on the same
 samples, Metropolis decisions identical wherever the oracle's margin |2 Re dlogrho - log u| exceeds
@@ -8,7 +8,7 @@ import pytest
 
 from oracle import estimators as E, sampler as OS, transformer as T
 from paper_2502_20723_gb300 import synth
-from tests.gpu_common import logrho_err, problem
+from tests.gpu_common import block_errors, logrho_err, problem
 
 pytestmark = pytest.mark.gpu
 
@@ -88,23 +88,36 @@ def test_bf16_unsupported_shapes():
         ctx_for(problem("ising", 4), spec, synth.init_params(spec))
 
 
+# Bounds per named parameter block (max |g - ref| / max |ref| over the block) and in norm, about three times
+# the errors measured on GB300: FP16 operands at most 1.3e-2 (weights) and 1.7e-2 (biases), 5.3e-4 in norm;
+# BF16 operands 1.9e-2 (weights) and 0.16 (the hidden bias b1, a 16-bit ones-MMA sum over every row),
+# 3.6e-3 in norm.  N > 16 runs the FP32 backward.
+GRAD_BOUNDS = {"fp16": (4e-2, 5e-2, 2e-3), "bf16": (5e-2, 0.5, 1e-2)}
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("kind,n,h,L,r,Ns", [("ising", 16, 8, 4, 4, 96), ("xyz", 13, 4, 2, 2, 64), ("ising", 8, 8, 2, 0, 128),
                                               ("ising", 20, 8, 1, 2, 24), ("xyz", 5, 4, 1, 4, 40)])
-def test_cost_gradient_bf16_tensor_core(kind, n, h, L, r, Ns):
-    """tdo_grad on a BF16 context runs the tensor-core backward (BF16 activations, FP32 accumulation,
-    softmax attention by warp-level FP16 MMAs) for N <= 16 and the FP32 backward above: the gradient is
-    within 5e-2 of the oracle's in norm (measured values are reported)."""
+def test_cost_gradient_tensor_core(prec, kind, n, h, L, r, Ns):
+    """tdo_grad on a tensor-core context runs the tensor-core backward (16-bit activations, FP32
+    accumulation, softmax attention by warp-level FP16 MMAs) for N <= 16 and the FP32 backward above."""
+    from paper_2502_20723_gb300 import tdo
     prob = problem(kind, n)
     spec = synth.model_spec(64, h, L, r)
     th = synth.init_params(spec, seed=21, std=0.05)
     sig, sigp = synth.random_configs(n, Ns, seed=9)
-    g, cost = ctx_for(prob, spec, th).grad(dev(sig), dev(sigp))
+    g, cost = tdo.Context(prob, spec, th, prec).grad(dev(sig), dev(sigp))
     g = g.cpu().numpy()
     ref, c_ref, _, _ = E.grad_estimator(prob, spec, th, sig, sigp)
     rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
-    print(f"bf16 gradient relative error {rel:.3e}, cost {cost:.6f} vs {c_ref:.6f}")
+    blocks = block_errors(spec, g, ref)
+    print(f"{prec} gradient: relative error {rel:.3e}, worst block {max(blocks, key=blocks.get)} "
+          f"{max(blocks.values()):.2e}")
+    w_tol, b_tol, n_tol = GRAD_BOUNDS[prec]
     assert abs(cost - c_ref) <= 1e-3 * c_ref
-    assert rel <= 5e-2
+    bad = {k: v for k, v in blocks.items() if v > (b_tol if k.startswith("b") else w_tol)}
+    assert not bad, bad
+    assert rel <= n_tol
 
 
 @pytest.mark.parametrize("kind,n,d,h,L,r,Ns", [("xyz", 6, 32, 4, 1, 0, 256), ("ising", 8, 32, 4, 1, 0, 40)])

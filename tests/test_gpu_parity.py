@@ -8,7 +8,7 @@ import pytest
 
 from oracle import estimators as E, lindblad, sampler as OS, transformer as T
 from paper_2502_20723_gb300 import synth
-from tests.gpu_common import logrho_err, problem
+from tests.gpu_common import block_errors, logrho_err, problem
 
 pytestmark = pytest.mark.gpu
 
@@ -230,7 +230,12 @@ def test_cost_gradient(kind, n, d, h, L, r, Ns):
     g = g.cpu().numpy()
     ref, c_ref, _, _ = E.grad_estimator(prob, spec, th, sig, sigp)
     assert abs(cost - c_ref) <= 1e-5 * c_ref
-    assert np.linalg.norm(g - ref) <= 1e-4 * np.linalg.norm(ref), np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    # element by element per named block (a wrong small block shows even where the norm would hide it):
+    # measured at most 1.8e-4 of the block's largest entry (the MLP biases of the 4-layer case, sums over
+    # every connected row), 5e-6 in norm
+    worst = {k: v for k, v in block_errors(spec, g, ref).items() if v > 1e-3}
+    assert not worst, worst
+    assert np.linalg.norm(g - ref) <= 2e-5 * np.linalg.norm(ref), np.linalg.norm(g - ref) / np.linalg.norm(ref)
 
 
 # ------------------------------------------------------------------ SR
