@@ -220,7 +220,8 @@ tdo_status tdo_sr_solve(tdo_ctx *ctx, const float *O, size_t Ns, const double *r
 enum { TDO_OPT_SGD = 0, TDO_OPT_ADAM = 1 };
 tdo_status tdo_set_optimizer(tdo_ctx *ctx, int kind, double beta1, double beta2, double eps);
 
-/* Stopping rule of the CG solve inside tdo_sr_step (defaults: tol 1e-6, max_iter 100).  The solve
+/* Stopping rule of the CG solve inside tdo_sr_step: ||r|| <= tol ||rhs|| or max_iter iterations (defaults:
+ * tol 1e-5, max_iter 100).  The solve
  * starts from the previous step's solution when there is one (reset by tdo_set_params). */
 tdo_status tdo_set_sr_options(tdo_ctx *ctx, double tol, int max_iter);
 

@@ -1400,22 +1400,38 @@ bool bwdtc_jac_supported(const DevModel &m) { return bwdtc_supported(m) && m.n_s
 namespace tdo {
 namespace TDO_BWNS {
 // VJP-mode db2 of a layer: the column sums of the FP32 dX at its MLP output, dX [rows][D] (padding rows
-// zero), summed in FP64 per thread over a row range; one float atomic per column and block into the
-// block's gradient copy.  (A sum over every connected row cancels heavily: summing the 16-bit image
+// zero).  A thread owns 4 columns (float4 loads, D / 4 threads per row, coalesced rows) and sums its rows in
+// FP32 runs of 64, added in FP64 between runs (GB300 issues about two FP64 adds per SM and cycle: a
+// dependent FP64 chain over every row took 8 ms per launch); one float atomic per column and block into
+// the block's gradient copy.  (A sum over every connected row cancels heavily: summing the 16-bit image
 // would leave the rounding of single rows in it.)
 __global__ void __launch_bounds__(256) k_db2_rows(const float *__restrict__ dX, size_t rows, int D, float *g,
                                                   size_t g_stride, long long off) {
-  __shared__ double red[256];
-  const int groups = 256 / D, c = threadIdx.x % D, grp = threadIdx.x / D;
-  double a = 0.0;
-  if (grp < groups)
-    for (size_t r = blockIdx.x * (size_t)groups + grp; r < rows; r += gridDim.x * (size_t)groups) a += dX[r * D + c];
-  red[threadIdx.x] = a;
+  __shared__ double red[256][4];
+  const int tpr = D / 4, groups = 256 / tpr, c4 = threadIdx.x % tpr, grp = threadIdx.x / tpr;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  if (grp < groups) {
+    const size_t stride = gridDim.x * (size_t)groups;
+    size_t r = blockIdx.x * (size_t)groups + grp;
+    while (r < rows) {
+      float f[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int k = 0; k < 64 && r < rows; ++k, r += stride) {
+        const float4 v = __ldcs(reinterpret_cast<const float4 *>(dX + r * D) + c4);
+        f[0] += v.x; f[1] += v.y; f[2] += v.z; f[3] += v.w;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) a[e] += (double)f[e];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) red[threadIdx.x][e] = a[e];
   __syncthreads();
-  if (threadIdx.x < D) {
-    double t = 0.0;
-    for (int k = 0; k < groups; ++k) t += red[k * D + threadIdx.x];
-    atomicAdd(g + (size_t)(blockIdx.x % kCopiesMax) * g_stride + off + threadIdx.x, (float)t);
+  if (threadIdx.x < tpr) {
+    for (int e = 0; e < 4; ++e) {
+      double t = 0.0;
+      for (int k = 0; k < groups; ++k) t += red[k * tpr + threadIdx.x][e];
+      atomicAdd(g + (size_t)(blockIdx.x % kCopiesMax) * g_stride + off + 4 * threadIdx.x + e, (float)t);
+    }
   }
 }
 
@@ -1551,7 +1567,7 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
         if (l == m.layers - 1)
           k_db2_head<<<1, 256, 0, st>>>(bf.dF, Bpad, m.Wh, D, gacc, b2[l]);
         else
-          k_db2_rows<<<(unsigned)(2 * n_sm), 256, 0, st>>>(bf.dxa, tiles * kRows, D, gacc, g_stride, b2[l]);
+          k_db2_rows<<<(unsigned)(4 * n_sm), 256, 0, st>>>(bf.dxa, tiles * kRows, D, gacc, g_stride, b2[l]);
       }
     }
     A1Args a1;

@@ -147,7 +147,7 @@ struct tdo_ctx {
   DBuf conn_cnt, conn_sig, conn_sigp, conn_coef, offs, fsig, fsigp, fcoef, flr, lloc, l2, stats,
       nonfinite, cot, gacc, scratch, grad, Obuf, srwork, delta, acc_u64, cscale;
   std::string err;
-  double sr_tol = 1e-6;
+  double sr_tol = 1e-5;   // relative residual (the default of the CG that NetKet's SR preconditioner calls)
   int sr_max_iter = 100;
   // optimiser applied to the SR direction: TDO_OPT_SGD (theta -= lr delta) or TDO_OPT_ADAM
   int opt = TDO_OPT_SGD;
