@@ -60,7 +60,8 @@ def test_log_rho_fp32(n, d, h, L, r, B):
     ctx = ctx_for(prob, spec, th)
     out = ctx.log_rho(dev(sig), dev(sigp)).cpu().numpy()
     err = logrho_err(out, ref)
-    assert np.all(err <= 1e-6 * np.maximum(np.abs(ref), 1.0)), (err.max(), np.abs(ref).min())
+    # relative to each element's |log rho| (measured at most 2.6e-7; |log rho| >= 0.55 in these cases)
+    assert np.all(err <= 1e-6 * np.abs(ref)), ((err / np.abs(ref)).max(), np.abs(ref).min())
     # host pointers give the same bits
     host = ctx.log_rho(sig.astype(np.uint32), sigp.astype(np.uint32))
     assert np.array_equal(host, out)
