@@ -1437,14 +1437,23 @@ __global__ void __launch_bounds__(256) k_db2_rows(const float *__restrict__ dX, 
 
 // The last layer's db2, whose dX is formed from the head: every sequence has N rows, each carrying
 // (1/N) Wh dF of its sequence, so db2[c] = sum_o Wh[c][o] S_o with S_o = sum over configurations of the
-// F_o cotangents of both orders, dF [Bpad][4] (zero beyond B).  One block, FP64 sums.
+// F_o cotangents of both orders, dF [Bpad][4] (zero beyond B).  A grid of blocks, each summing its range
+// of configurations in FP32 runs of 64 added in FP64, then adding its own Wh S into copy blockIdx % 16.
 __global__ void __launch_bounds__(256) k_db2_head(const float *__restrict__ dF, size_t Bpad, const float *__restrict__ Wh,
-                                                  int D, float *g, long long off) {
+                                                  int D, float *g, size_t g_stride, long long off) {
   __shared__ double red[2][256];
   double s0 = 0.0, s1 = 0.0;
-  for (size_t b = threadIdx.x; b < Bpad; b += blockDim.x) {
-    s0 += (double)dF[4 * b] + (double)dF[4 * b + 2];
-    s1 += (double)dF[4 * b + 1] + (double)dF[4 * b + 3];
+  const size_t stride = gridDim.x * (size_t)blockDim.x;
+  size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  while (b < Bpad) {
+    float f0 = 0.f, f1 = 0.f;
+    for (int k = 0; k < 64 && b < Bpad; ++k, b += stride) {
+      const float4 q = __ldcs(reinterpret_cast<const float4 *>(dF) + b);
+      f0 += q.x + q.z;
+      f1 += q.y + q.w;
+    }
+    s0 += (double)f0;
+    s1 += (double)f1;
   }
   red[0][threadIdx.x] = s0;
   red[1][threadIdx.x] = s1;
@@ -1456,8 +1465,9 @@ __global__ void __launch_bounds__(256) k_db2_head(const float *__restrict__ dF, 
     }
     __syncthreads();
   }
+  float *gc = g + (size_t)(blockIdx.x % kCopiesMax) * g_stride;
   for (int c = threadIdx.x; c < D; c += blockDim.x)
-    atomicAdd(g + off + c, (float)((double)Wh[2 * c] * red[0][0] + (double)Wh[2 * c + 1] * red[1][0]));
+    atomicAdd(gc + off + c, (float)((double)Wh[2 * c] * red[0][0] + (double)Wh[2 * c + 1] * red[1][0]));
 }
 }  // namespace TDO_BWNS
 }  // namespace tdo
@@ -1565,7 +1575,7 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
       dxmid = bf.dxb;
       if (!jac) {   // db2 of this layer from FP32 data (its MLP output's dX: the head's for the last layer)
         if (l == m.layers - 1)
-          k_db2_head<<<1, 256, 0, st>>>(bf.dF, Bpad, m.Wh, D, gacc, b2[l]);
+          k_db2_head<<<(unsigned)(2 * n_sm), 256, 0, st>>>(bf.dF, Bpad, m.Wh, D, gacc, g_stride, b2[l]);
         else
           k_db2_rows<<<(unsigned)(4 * n_sm), 256, 0, st>>>(bf.dxa, tiles * kRows, D, gacc, g_stride, b2[l]);
       }
