@@ -231,6 +231,84 @@ __device__ __forceinline__ void attn_fwd_h(const __half *Qh, const __half *Kh, c
   }
 }
 
+// Forward only, for sequences of 17 to 32 tokens: one warp computes the 16 query rows q0 .. q0 + 15 of one
+// (sequence, head) against its 32 keys (keys >= n masked), FP16 operands in shared memory, all row-major
+// with row stride ldh halves and 16-byte-aligned rows: Qh (pre-scaled by 1/sqrt(HD) log2 e), Kh and Vh
+// point at the sequence's first row; rows up to 31 below them must hold finite values (the next sequence
+// or zeros).  Scores in four 16 x 8 key tiles, softmax in base 2 over the 32 keys, O = P V in two k-steps
+// of 16 keys with V's B fragments by transposing ldmatrix.  emit(row, col, v0, v1) for rows < n.
+template <int HD, typename EMIT>
+__device__ __forceinline__ void attn_fwd_h32(const __half *Qh, const __half *Kh, const __half *Vh, int ldh, int n,
+                                             int q0, EMIT emit) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  auto ld2 = [&](const __half *M, int r, int c) -> uint32_t {
+    return *reinterpret_cast<const uint32_t *>(M + r * ldh + c);
+  };
+  float s[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) zero4(s[j]);
+  if (HD == 8) {
+    const uint32_t a0 = ld2(Qh, q0 + g, 2 * t), a1 = ld2(Qh, q0 + g + 8, 2 * t);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mma1688(s[j], a0, a1, ld2(Kh, 8 * j + g, 2 * t));
+  } else {
+    const uint32_t a[4] = {ld2(Qh, q0 + g, 2 * t), ld2(Qh, q0 + g + 8, 2 * t), ld2(Qh, q0 + g, 8 + 2 * t),
+                           ld2(Qh, q0 + g + 8, 8 + 2 * t)};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mma16816(s[j], a, ld2(Kh, 8 * j + g, 2 * t), ld2(Kh, 8 * j + g, 8 + 2 * t));
+  }
+  float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const bool ok = 8 * j + 2 * t + e < n;
+      s[j][e] = ok ? s[j][e] : -INFINITY;
+      s[j][2 + e] = ok ? s[j][2 + e] : -INFINITY;
+      m0 = fmaxf(m0, s[j][e]);
+      m1 = fmaxf(m1, s[j][2 + e]);
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      s[j][e] = tc::ex2_fast(s[j][e] - m0);
+      s[j][2 + e] = tc::ex2_fast(s[j][2 + e] - m1);
+      l0 += s[j][e];
+      l1 += s[j][2 + e];
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+  }
+  const float i0 = tc::rcp_fast(l0), i1 = tc::rcp_fast(l1);
+  float o[HD / 8][4];
+#pragma unroll
+  for (int c = 0; c < HD / 8; ++c) zero4(o[c]);
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {   // keys 16 kk .. 16 kk + 15
+    const uint32_t pa[4] = {h2(s[2 * kk][0] * i0, s[2 * kk][1] * i0), h2(s[2 * kk][2] * i1, s[2 * kk][3] * i1),
+                            h2(s[2 * kk + 1][0] * i0, s[2 * kk + 1][1] * i0),
+                            h2(s[2 * kk + 1][2] * i1, s[2 * kk + 1][3] * i1)};
+    uint32_t vb[HD / 8][2];
+    frag_bk<HD>((uint32_t)__cvta_generic_to_shared(Vh + 16 * kk * ldh), ldh, vb);
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) mma16816(o[c], pa, vb[c][0], vb[c][1]);
+  }
+#pragma unroll
+  for (int c = 0; c < HD / 8; ++c) {
+    if (q0 + g < n) emit(q0 + g, 8 * c + 2 * t, o[c][0], o[c][1]);
+    if (q0 + g + 8 < n) emit(q0 + g + 8, 8 * c + 2 * t, o[c][2], o[c][3]);
+  }
+}
+
 // Forward and backward of softmax attention for one (sequence, head) on one warp, FP16 operands in
 // shared memory: Qh, Kh, Vh, dHh are u32 shared addresses of this sequence's first row and this head's
 // first feature in [rows][ldh] row-major FP16 arrays (Q unscaled), readable 16 rows down (rows >= n

@@ -68,6 +68,12 @@ struct Geo {
   static constexpr int QH_OFF = KV_OFF, KH_OFF = QH_OFF + kRows * LDH * 2, VT_OFF = KH_OFF + kRows * LDH * 2;
   static constexpr int LDT = ((KV_BYTES - 2 * kRows * LDH * 2) / (D * 2)) & ~7;
   __host__ __device__ static constexpr bool mma_attention(int n, int ts) { return n <= 16 && ts * 16 + 8 <= LDT; }
+  // warp-MMA attention for 17 <= N <= 32: FP16 Q, K, V row-major [LROWS][LDH] each in the K/V region; a
+  // unit reads 32 rows from its sequence's first row, at most row (ts - 1) N + 31 <= 136 of the tile
+  static constexpr int LROWS = 137;
+  static constexpr int QL_OFF = KV_OFF, KL_OFF = QL_OFF + LROWS * LDH * 2, VL_OFF = KL_OFF + LROWS * LDH * 2;
+  static_assert(3 * LROWS * LDH * 2 <= KV_BYTES, "long-sequence attention operands fit the K/V region");
+  static_assert((LROWS * LDH * 2) % 16 == 0, "16-byte-aligned regions");
 };
 
 using namespace tdo::tc;
@@ -272,6 +278,57 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
       };
       if (n == 16) units(std::true_type{});
       else units(std::false_type{});
+    } else if (n > 16) {
+      // ---------------- attention of 17 to 32 tokens by warp-level MMAs, one warp per (sequence, head,
+      // block of 16 queries): FP16 Q (scaled), K, V row-major to shared memory, output -> A
+      __half *Ql = reinterpret_cast<__half *>(sm + G::QL_OFF), *Kl = reinterpret_cast<__half *>(sm + G::KL_OFF);
+      __half *Vl = reinterpret_cast<__half *>(sm + G::VL_OFF);
+#pragma unroll
+      for (int j = 0; j < DH; j += 16) {   // TMEM loads are warp-collective: every lane loads, valid rows store
+        float v[16];
+        tmem_ld16(c.tmem + lane_addr + half * DH + j, v);
+        if (valid) {
+          uint4 *dst = reinterpret_cast<uint4 *>(Ql + row * G::LDH + half * DH + j);
+          dst[0] = make_uint4(amma::h2(v[0] * qscale, v[1] * qscale), amma::h2(v[2] * qscale, v[3] * qscale),
+                              amma::h2(v[4] * qscale, v[5] * qscale), amma::h2(v[6] * qscale, v[7] * qscale));
+          dst[1] = make_uint4(amma::h2(v[8] * qscale, v[9] * qscale), amma::h2(v[10] * qscale, v[11] * qscale),
+                              amma::h2(v[12] * qscale, v[13] * qscale), amma::h2(v[14] * qscale, v[15] * qscale));
+        }
+        tmem_ld16(c.tmem + lane_addr + D + half * DH + j, v);
+        if (valid) {
+          uint4 *dst = reinterpret_cast<uint4 *>(Kl + row * G::LDH + half * DH + j);
+          dst[0] = make_uint4(amma::h2(v[0], v[1]), amma::h2(v[2], v[3]), amma::h2(v[4], v[5]), amma::h2(v[6], v[7]));
+          dst[1] = make_uint4(amma::h2(v[8], v[9]), amma::h2(v[10], v[11]), amma::h2(v[12], v[13]),
+                              amma::h2(v[14], v[15]));
+        }
+        tmem_ld16(c.tmem + lane_addr + 2 * D + half * DH + j, v);
+        if (valid) {
+          uint4 *dst = reinterpret_cast<uint4 *>(Vl + row * G::LDH + half * DH + j);
+          dst[0] = make_uint4(amma::h2(v[0], v[1]), amma::h2(v[2], v[3]), amma::h2(v[4], v[5]), amma::h2(v[6], v[7]));
+          dst[1] = make_uint4(amma::h2(v[8], v[9]), amma::h2(v[10], v[11]), amma::h2(v[12], v[13]),
+                              amma::h2(v[14], v[15]));
+        }
+      }
+      {   // rows past the tile's sequences: zero (finite values for the masked keys' V and the unused queries)
+        const int zr = G::LROWS - ts * n, per = D / 8;
+        for (int idx = threadIdx.x; idx < 3 * zr * per; idx += kThreads) {
+          const int reg = idx / (zr * per), r = ts * n + (idx % (zr * per)) / per, c8 = idx % per;
+          __half *base = reg == 0 ? Ql : (reg == 1 ? Kl : Vl);
+          *reinterpret_cast<uint4 *>(base + r * G::LDH + 8 * c8) = make_uint4(0, 0, 0, 0);
+        }
+      }
+      for (int idx = threadIdx.x; idx < (kRows - ts * n) * (D / 8); idx += kThreads)   // padding rows: O = 0
+        *reinterpret_cast<uint4 *>(A + canon(ts * n + idx / (D / 8), 8 * (idx % (D / 8)), D)) = make_uint4(0, 0, 0, 0);
+      __syncthreads();
+      constexpr int H = D / HD;
+      for (int u = warp; u < ts * H * 2; u += kThreads / 32) {
+        const int sq = u / (2 * H), h = (u >> 1) % H, qb = u & 1, rb = sq * n;
+        amma::attn_fwd_h32<HD>(Ql + rb * G::LDH + h * HD, Kl + rb * G::LDH + h * HD, Vl + rb * G::LDH + h * HD,
+                               G::LDH, n, 16 * qb, [&](int r, int cc, float v0, float v1) {
+                                 *reinterpret_cast<uint32_t *>(A + canon(rb + r, h * HD + cc, D)) =
+                                     pack16<kF16>(v0, v1);
+                               });
+      }
     } else {
     // K, V (FP32) to shared memory, this thread's column half
 #pragma unroll

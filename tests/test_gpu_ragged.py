@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-MIX = (8, 12, 16, 20, 24, 32, 1, 5, 13)
+MIX = (8, 12, 16, 17, 20, 21, 24, 29, 32, 1, 5, 13)
 
 
 @pytest.fixture(scope="module", autouse=True)
