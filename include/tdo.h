@@ -274,6 +274,37 @@ tdo_status tdo_sr_info(const tdo_ctx *ctx, int *iters, double *resid);
  * warm-started solve failed and was solved again from x = 0. */
 tdo_status tdo_sr_report(const tdo_ctx *ctx, int *outcome, double *last_pap, int *restarts);
 
+/* How the CG solve forms each product (Re S + shift I) v (metric-tensor section; the S matrix is never
+ * formed).  TDO_SR_PRODUCT_TWO_PASS (default): two streaming passes over the log-derivatives, t = O v
+ * per sample, then w = Re(O^H t) per parameter (HBM-bound; on GB300 at about 0.94 of the measured copy
+ * bandwidth).  TDO_SR_PRODUCT_ONE_PASS: where the log-derivatives are stored as BF16 pairs (tensor-core
+ * contexts) with rows on 16-byte boundaries, one pass: thread-block clusters of up to 16 CTAs each own a
+ * range of samples and every CTA of a cluster one parameter slice; t_s is exchanged inside the cluster
+ * through distributed shared memory, and w is accumulated from the same copy of the row in shared
+ * memory.  It reads O once, but each row costs two block barriers and one cluster exchange, and on a
+ * GB300 it measured 1.3 times slower than two passes at the headline shape (198,274 parameters, 16,384
+ * samples); it is kept as an option.  Both give the same products up to the order of FP32 partial sums
+ * (each within 3e-7 of an FP64 evaluation of the definition). */
+enum { TDO_SR_PRODUCT_TWO_PASS = 0, TDO_SR_PRODUCT_ONE_PASS = 1 };
+tdo_status tdo_set_sr_product(tdo_ctx *ctx, int mode);
+
+/* One product of the CG solve outside it: Ap = (Re S + shift I) v, S_ij = <O_i^* O_j> - <O_i^*><O_j> over
+ * the Ns rows of O (metric-tensor and regularisation sections), S never formed.  O: log-derivatives as
+ * BF16 pairs, one uint32 per element (Re in the low 16 bits, Im in the high 16 bits), [Ns][ldo] with
+ * ldo >= the parameter count P, device memory owned by the caller; v, Ap: FP64 [P], device memory.  The
+ * product runs in the mode of tdo_set_sr_product for tensor-core contexts, and in two passes in FP32
+ * contexts; tdo_sr_product_shape reports it.  v is rounded to FP32 for the products with O, as in the
+ * solve.  TDO_EINVAL for NULL or host pointers, Ns = 0 or ldo < P; TDO_ETIMEOUT when a bounded wait of the
+ * one-pass product gave up.  Synchronises the context's stream. */
+tdo_status tdo_sr_apply(tdo_ctx *ctx, const uint32_t *O, size_t Ns, size_t ldo, const double *v, double shift,
+                        double *Ap);
+
+/* The last tdo_sr_step's (or tdo_sr_apply's) product shape (each pointer may be NULL): one_pass = 1 when
+ * the one-pass product ran, cluster = CTAs per cluster, clusters = clusters launched (0, 0 for two
+ * passes).  A bounded wait of
+ * the one-pass product that gives up makes tdo_sr_step return TDO_ETIMEOUT. */
+tdo_status tdo_sr_product_shape(const tdo_ctx *ctx, int *one_pass, int *cluster, int *clusters);
+
 /* Arithmetic peak of the current device measured by the library (no counterpart in the paper):
  * kind 0 = FP32 fused multiply-add on the CUDA cores, 1 = FP64 FMA; *tflops = the best of three timed
  * launches (CUDA events on `stream`, a cudaStream_t or NULL) of a kernel of independent FMA chains,

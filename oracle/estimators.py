@@ -142,6 +142,13 @@ def sr_matrix(O: np.ndarray) -> np.ndarray:
     return (Oc.conj().T @ Oc).real / O.shape[0]
 
 
+def sr_product(O: np.ndarray, v: np.ndarray, diag_shift: float) -> np.ndarray:
+    """(Re S + lambda I) v without forming S: (1/Ns) Re[Oc^H (Oc v)] + lambda v, Oc = O - mean(O) (the
+    metric-tensor section's S applied to a vector; v real)."""
+    Oc = O - O.mean(axis=0, keepdims=True)
+    return (Oc.conj().T @ (Oc @ v)).real / O.shape[0] + diag_shift * v
+
+
 def sr_solve(O: np.ndarray, grad: np.ndarray, diag_shift: float) -> np.ndarray:
     """delta = (Re S + lambda I)^{-1} grad by Cholesky (S' symmetric positive definite)."""
     S = sr_matrix(O) + diag_shift * np.eye(O.shape[1])

@@ -11,6 +11,7 @@
 // iteration, the host looks at it between groups of iterations only.
 #include "tdo_internal.cuh"
 #include "tdo_device.cuh"
+#include "tcgen05.cuh"
 
 namespace tdo {
 
@@ -363,9 +364,10 @@ __global__ void k_sr_mfin(size_t Ns, size_t P, double shift, const double *__res
   }
 }
 
-// Ap[k] = (1/Ns) [sum_sg wpart[sg][k] - Re(conj(mean[k]) T)] + shift p[k]; partials of p . p.
+// Ap[k] = (1/Ns) [sum_g wpart[g][k] - Re(conj(mean[k]) T)] + shift p[k] over ng partial rows; partials
+// of p . p.
 __global__ void k_sr_wfin(size_t Ns, size_t P, const double2 *__restrict__ mean, const double *__restrict__ wpart,
-                          const double *__restrict__ p, double shift, double *__restrict__ Ap,
+                          int ng, const double *__restrict__ p, double shift, double *__restrict__ Ap,
                           double *__restrict__ part, const double *__restrict__ sc) {
   __shared__ double sh[32];
   if (sc[S_DONE] != 0.0) return;
@@ -373,8 +375,330 @@ __global__ void k_sr_wfin(size_t Ns, size_t P, const double2 *__restrict__ mean,
   double loc = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
     double a = 0.0;
+    for (int g = 0; g < ng; ++g) a += wpart[(size_t)g * P + k];
+    const double2 m = mean[k];
+    const double v = (a - (m.x * Tr + m.y * Ti)) / (double)Ns + shift * p[k];
+    Ap[k] = v;
+    loc += p[k] * p[k];
+  }
+  const double b = block_sum_d(loc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+// ---------------------------------------------------------------- one-pass product (BF16 pairs)
+// S' v with O read from HBM once.  Thread-block clusters of C CTAs share a range of sample rows; CTA q of a
+// cluster owns the parameter slice [q SL, q SL + SL) of each of those rows.  Per row:
+//   - the slice arrives by one bulk copy into a ring of kFusedRing shared-memory buffers;
+//   - the CTA forms its partial of t_s = O_s . v over the slice and sends it to every other CTA of the
+//     cluster by an asynchronous store into the peer's shared memory that also counts its 16 bytes on the
+//     peer's mbarrier (st.async ... complete_tx); its own partial goes to its own slot by a plain store;
+//   - once all C partials of the row are in, warp 1 forms t_s (centred as in k_sr_tred) and publishes it
+//     in shared memory, and every thread adds Re(conj(O_sk) t_s) to its parameters' FP32 run sums from the
+//     same buffer.
+// The partials of rows s + 1 and s + 2 are sent before row s's are awaited, so the exchange overlaps the
+// stream; with a lookahead of kFusedLook rows, 2 kFusedLook + 2 exchange slots keep a CTA that runs ahead
+// from overwriting a slot (or counting bytes on a barrier phase) that a peer has not finished with.  A
+// slot's barrier is armed for (C - 1) x 16 bytes by its own CTA before any peer can send into that phase
+// (at the start, and after the slot's previous row was consumed), so its byte count never goes negative.
+// Arithmetic: GB300's FP64 rate is a small fraction of its FP32 rate, so no FP64 operation is on the
+// per-row path.  A CTA's partial is an FP32 sum (per thread, per warp, then a 16-lane tree over the warps:
+// one chunk sum, as in k_sr_tpart); the sum over the cluster's C partials is double-float (an FP32 pair
+// hi + lo combined by Knuth's TwoSum, about 48 significant bits, in the role of k_sr_tred's FP64 sum) in a
+// fixed xor-butterfly tree, so every CTA of a cluster gets the same bits of t_s.  Runs of kRun rows of
+// FP32 products per parameter are added into the cluster's double-float partial row wpart[cluster][P]
+// (L2-resident; each element has one owner thread, the first run writes instead of adding); k_sr_wfin_dd
+// sums the partial rows in FP64.  Every wait is bounded: on a timeout the CTA flags *err and goes on, so
+// that every CTA of the cluster still reaches each exchange and the final cluster barrier.
+constexpr int kFusedThreads = 512;
+constexpr int kFusedGroups = 8;   // 4-element groups per thread
+constexpr int kFusedRing = 4, kFusedLook = 2, kFusedSlots = 2 * kFusedLook + 2;
+constexpr int kFusedMaxSlice = 4 * kFusedGroups * kFusedThreads;
+constexpr int kFusedMaxClusters = 3 * kSampleGroups;   // partial rows kept in the moments' buffer
+
+struct FusedLayout {
+  int slots, wsum, tbuf, bars, bytes;   // byte offsets in dynamic shared memory (ring at 0) and the total
+};
+__host__ __device__ inline FusedLayout fused_layout(int SL, int C) {
+  FusedLayout L;
+  L.slots = kFusedRing * SL * 4;   // SL is a multiple of 4: every buffer starts on a 16-byte boundary
+  L.wsum = L.slots + kFusedSlots * C * 16;
+  L.tbuf = L.wsum + 2 * (kFusedThreads / 32) * 8;   // per-warp partials, double-buffered by row parity
+  L.bars = L.tbuf + 2 * 8;                          // t of the row, double-buffered by row parity
+  L.bytes = L.bars + (kFusedRing + kFusedSlots) * 8;
+  return L;
+}
+
+// Double-float value hi + lo (|lo| <= ulp(hi) / 2 after renormalisation).
+struct DF {
+  float hi, lo;
+};
+// (a + b) exactly as s + e (Knuth's TwoSum, symmetric in a and b)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  DF r;
+  r.hi = s + e;
+  r.lo = e - (r.hi - s);
+  return r;
+}
+// Sum over lanes 0-15 of a warp (the only lanes that call it) by an xor butterfly: each ends with the same
+// bits.
+__device__ __forceinline__ DF df_half_sum(DF v) {
 #pragma unroll
-    for (int g = 0; g < kSampleGroups; ++g) a += wpart[(size_t)g * P + k];
+  for (int o = 8; o; o >>= 1) {
+    DF w;
+    w.hi = __shfl_xor_sync(0x0000ffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0x0000ffffu, v.lo, o);
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint32_t cl_special(int which) {
+  uint32_t r;
+  if (which == 0) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  else if (which == 1) asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  else if (which == 2) asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  else asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// The shared::cluster address of local shared address a in the CTA of rank r.
+__device__ __forceinline__ uint32_t cl_map(uint32_t a, uint32_t r) {
+  uint32_t d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(r));
+  return d;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// 16 bytes into a peer's shared memory (cluster address a), counted on the peer's mbarrier (cluster
+// address bar) as completed transaction bytes.
+__device__ __forceinline__ void cl_put_async(uint32_t a, float4 v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(a),
+               "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+               : "memory");
+}
+// Bounded wait on a local mbarrier that peers of the cluster complete (acquire at cluster scope).
+__device__ __forceinline__ bool cl_wait(uint32_t a, uint32_t parity) {
+  for (long long i = 0; i < tc::kSpinLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (i > 64) __nanosleep(32);
+  }
+  return false;
+}
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    k_sr_fused(const uint32_t *__restrict__ O, size_t Ns, size_t P, size_t ldo, int SL, const float *__restrict__ vf,
+               float2 *__restrict__ t, float2 *__restrict__ wpart, const double *__restrict__ sc, int *err) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  if (sc[S_DONE] != 0.0) return;   // the same value for every CTA: all of them leave here together
+  const int C = (int)cl_special(1), q = (int)cl_special(0);
+  const size_t g = cl_special(2), G = cl_special(3);
+  const FusedLayout L = fused_layout(SL, C);
+  const uint32_t base = tc::smem_u32(sm);
+  const uint32_t full = base + L.bars, recv = full + 8 * kFusedRing, slots = base + L.slots;
+  const float4 *slot = reinterpret_cast<const float4 *>(sm + L.slots);
+  float2 *wsum = reinterpret_cast<float2 *>(sm + L.wsum);
+  float2 *tbuf = reinterpret_cast<float2 *>(sm + L.tbuf);
+  const size_t per = (Ns + G - 1) / G;
+  const size_t s0 = g * per < Ns ? g * per : Ns;
+  const int nr = (int)((s0 + per < Ns ? s0 + per : Ns) - s0);
+  const size_t k0 = (size_t)q * SL;
+  const int kn = k0 < P ? (int)(P - k0 < (size_t)SL ? P - k0 : (size_t)SL) : 0;
+  const int ngr = (kn + 3) / 4;
+  const uint32_t bytes = 16u * (uint32_t)ngr;   // inside the row: ldo and k0 are multiples of 4
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  DF ncr, nci;   // -(mean . v) as double-float pairs: the kernel's only FP64 arithmetic
+  {
+    const double cr = sc[S_CR], ci = sc[S_CI];
+    ncr.hi = (float)(-cr);
+    ncr.lo = (float)(-cr - (double)ncr.hi);
+    nci.hi = (float)(-ci);
+    nci.lo = (float)(-ci - (double)nci.hi);
+  }
+  float4 vr[kFusedGroups], f[kFusedGroups];
+#pragma unroll
+  for (int i = 0; i < kFusedGroups; ++i) {
+    const int k = 4 * (tid + kFusedThreads * i);
+    float x[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) x[e] = k + e < kn ? vf[k0 + k + e] : 0.f;
+    vr[i] = make_float4(x[0], x[1], x[2], x[3]);
+    f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (tid == 0) {
+    for (int b = 0; b < kFusedRing; ++b) tc::mbar_init(full + 8 * b, 1);
+    for (int b = 0; b < kFusedSlots; ++b) tc::mbar_init(recv + 8 * b, 1);
+    for (int b = 0; b < kFusedSlots; ++b) tc::mbar_expect_tx(recv + 8 * b, 16u * (uint32_t)(C - 1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cl_sync();   // every CTA's barriers exist and are armed before a peer stores into its slots
+  auto issue = [&](int r) {   // thread 0: row r's slice into buffer r % kFusedRing
+    const uint32_t bar = full + 8 * (r % kFusedRing);
+    tc::mbar_expect_tx(bar, bytes);
+    tc::bulk_g2s(base + (uint32_t)((r % kFusedRing) * SL * 4), O + (s0 + r) * ldo + k0, bytes, bar);
+  };
+  if (tid == 0 && ngr > 0)
+    for (int r = 0; r < kFusedRing && r < nr; ++r) issue(r);
+  bool ok = true;
+  // the four elements of group gi from a row buffer (zero past the slice: padding columns are never data)
+  auto elems = [&](const uint4 &u, int gi, float2 (&c)[4]) {
+    c[0] = cplx(u.x); c[1] = cplx(u.y); c[2] = cplx(u.z); c[3] = cplx(u.w);
+    if (4 * gi + 4 > kn)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (4 * gi + e >= kn) c[e] = make_float2(0.f, 0.f);
+  };
+  // row r: this CTA's partial of O_s . v to every CTA of the cluster
+  auto send = [&](int r) {
+    float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};   // independent chains per element slot
+    if (ngr > 0) {
+      ok = tc::mbar_wait(full + 8 * (r % kFusedRing), (uint32_t)((r / kFusedRing) & 1)) && ok;
+      const uint4 *buf = reinterpret_cast<const uint4 *>(sm + (size_t)(r % kFusedRing) * SL * 4);
+#pragma unroll
+      for (int i = 0; i < kFusedGroups; ++i) {
+        const int gi = tid + kFusedThreads * i;
+        if (gi < ngr) {
+          float2 c[4];
+          elems(buf[gi], gi, c);
+          const float vv[4] = {vr[i].x, vr[i].y, vr[i].z, vr[i].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            ar[e] = fmaf(c[e].x, vv[e], ar[e]);
+            ai[e] = fmaf(c[e].y, vv[e], ai[e]);
+          }
+        }
+      }
+    }
+    float pr = (ar[0] + ar[1]) + (ar[2] + ar[3]), pi = (ai[0] + ai[1]) + (ai[2] + ai[3]);
+    pr = warp_sum(pr);
+    pi = warp_sum(pi);
+    float2 *ws = wsum + (r & 1) * (kFusedThreads / 32);
+    if (lane == 0) ws[warp] = make_float2(pr, pi);
+    __syncthreads();
+    if (warp == 0 && lane < 16) {   // the CTA's partial: FP32 tree over the 16 warps (as one chunk sum)
+      float a = ws[lane].x, b = ws[lane].y;
+#pragma unroll
+      for (int o = 8; o; o >>= 1) {
+        a += __shfl_xor_sync(0x0000ffffu, a, o);
+        b += __shfl_xor_sync(0x0000ffffu, b, o);
+      }
+      if (lane < C) {   // lane p: the partial into slot q of CTA p
+        const int sl = r % kFusedSlots;
+        const float4 msg = make_float4(a, 0.f, b, 0.f);
+        if (lane == q)   // read by warp 1 after the block barriers between this send and the row's turn
+          *reinterpret_cast<float4 *>(sm + L.slots + (sl * C + q) * 16) = msg;
+        else
+          cl_put_async(cl_map(slots + (uint32_t)((sl * C + q) * 16), (uint32_t)lane), msg,
+                       cl_map(recv + 8 * sl, (uint32_t)lane));
+      }
+    }
+  };
+  // warp 1 (lanes 0-15), row r: t_s from the C partials, centred, to tbuf[r & 1] (and to t by the
+  // cluster's CTA 0)
+  auto form_t = [&](int r) {
+    const int sl = r % kFusedSlots;
+    ok = cl_wait(recv + 8 * sl, (uint32_t)((r / kFusedSlots) & 1)) && ok;
+    DF a = {0.f, 0.f}, b = {0.f, 0.f};
+    if (lane < C) {
+      const float4 m = slot[sl * C + lane];
+      a.hi = m.x; a.lo = m.y; b.hi = m.z; b.lo = m.w;
+    }
+    a = df_add(df_half_sum(a), ncr);
+    b = df_add(df_half_sum(b), nci);
+    if (lane == 0) {
+      const float2 tv = make_float2(a.hi + a.lo, b.hi + b.lo);
+      tbuf[r & 1] = tv;
+      if (q == 0) t[s0 + r] = tv;
+    }
+  };
+  for (int r = 0; r < kFusedLook && r < nr; ++r) send(r);
+  __syncthreads();   // own-slot stores of the first rows before warp 1 reads them
+  bool first = true;
+  for (int r = 0; r < nr; ++r) {
+    if (warp == 1 && lane < 16) form_t(r);
+    if (r + kFusedLook < nr) send(r + kFusedLook);   // its block barrier also publishes tbuf[r & 1]
+    else __syncthreads();
+    const float2 tv = tbuf[r & 1];
+    if (ngr > 0) {
+      const uint4 *buf = reinterpret_cast<const uint4 *>(sm + (size_t)(r % kFusedRing) * SL * 4);
+#pragma unroll
+      for (int i = 0; i < kFusedGroups; ++i) {
+        const int gi = tid + kFusedThreads * i;
+        if (gi < ngr) {
+          float2 c[4];
+          elems(buf[gi], gi, c);
+          f[i].x = fmaf(c[0].x, tv.x, fmaf(c[0].y, tv.y, f[i].x));
+          f[i].y = fmaf(c[1].x, tv.x, fmaf(c[1].y, tv.y, f[i].y));
+          f[i].z = fmaf(c[2].x, tv.x, fmaf(c[2].y, tv.y, f[i].z));
+          f[i].w = fmaf(c[3].x, tv.x, fmaf(c[3].y, tv.y, f[i].w));
+        }
+      }
+    }
+    if ((r + 1) % kRun == 0 || r + 1 == nr) {   // the run into the cluster's double-float partial row
+#pragma unroll
+      for (int i = 0; i < kFusedGroups; ++i) {
+        const int k = 4 * (tid + kFusedThreads * i);
+        const float fe[4] = {f[i].x, f[i].y, f[i].z, f[i].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (k + e < kn) {
+            float2 *w = wpart + g * P + k0 + k + e;
+            DF acc = {0.f, 0.f};
+            if (!first) { const float2 o = *w; acc.hi = o.x; acc.lo = o.y; }
+            acc = df_add(acc, DF{fe[e], 0.f});
+            *w = make_float2(acc.hi, acc.lo);
+          }
+        f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      first = false;
+    }
+    __syncthreads();   // buffer r % kFusedRing, slot r % kFusedSlots and tbuf are done with
+    if (tid == 0) {
+      tc::mbar_expect_tx(recv + 8 * (r % kFusedSlots), 16u * (uint32_t)(C - 1));   // for row r + kFusedSlots
+      if (ngr > 0 && r + kFusedRing < nr) {
+        tc::fence_proxy_async();
+        issue(r + kFusedRing);
+      }
+    }
+  }
+  if (nr == 0)
+    for (int k = tid; k < kn; k += kFusedThreads) wpart[g * P + k0 + k] = make_float2(0.f, 0.f);
+  const bool bad = __syncthreads_or(ok ? 0 : 1) != 0;
+  if (bad && tid == 0 && ngr > 0)   // copies still in flight after a timeout: wait for them (bounded)
+    for (int r = nr - kFusedRing > 0 ? nr - kFusedRing : 0; r < nr; ++r)
+      tc::mbar_wait(full + 8 * (r % kFusedRing), (uint32_t)((r / kFusedRing) & 1));
+  cl_sync();   // no CTA leaves while a peer may still store into its slots
+  if (bad && tid == 0 && err) atomicExch(err, 1);
+}
+
+// Ap[k] = (1/Ns) [sum_g (hi + lo)(wpart[g][k]) - Re(conj(mean[k]) T)] + shift p[k] over ng double-float
+// partial rows (FP64 sums); partials of p . p.
+__global__ void k_sr_wfin_dd(size_t Ns, size_t P, const double2 *__restrict__ mean, const float2 *__restrict__ wpart,
+                             int ng, const double *__restrict__ p, double shift, double *__restrict__ Ap,
+                             double *__restrict__ part, const double *__restrict__ sc) {
+  __shared__ double sh[32];
+  if (sc[S_DONE] != 0.0) return;
+  const double Tr = sc[S_TR], Ti = sc[S_TI];
+  double loc = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
+    double a = 0.0;
+    for (int g = 0; g < ng; ++g) {
+      const float2 w = wpart[(size_t)g * P + k];
+      a += (double)w.x + (double)w.y;
+    }
     const double2 m = mean[k];
     const double v = (a - (m.x * Tr + m.y * Ti)) / (double)Ns + shift * p[k];
     Ap[k] = v;
@@ -556,7 +880,79 @@ static void matvec(const OT *O, size_t Ns, size_t P, size_t ldo, const double *v
     k_sr_wpart<OT, true><<<dim3(nchunks, kSampleGroups), TB, 0, st>>>(O, Ns, P, ldo, q.t, q.wpart, q.sc);
   else
     k_sr_wpart<OT, false><<<dim3(nchunks, kSampleGroups), TB, 0, st>>>(O, Ns, P, ldo, q.t, q.wpart, q.sc);
-  k_sr_wfin<<<nb, kSrBlock, 0, st>>>(Ns, P, q.mean, q.wpart, v, shift, q.Ap, q.part, q.sc);
+  k_sr_wfin<<<nb, kSrBlock, 0, st>>>(Ns, P, q.mean, q.wpart, kSampleGroups, v, shift, q.Ap, q.part, q.sc);
+}
+
+// The one-pass product's shape for this O: the smallest cluster (so the most clusters) whose three row
+// slices fit in shared memory, and as many clusters as the device runs at once (at most
+// kFusedMaxClusters).  C = 0: not available (FP32 storage, unaligned rows, no cluster launch).
+struct FusedPlan {
+  int C = 0, G = 0, SL = 0, bytes = 0;
+};
+static FusedPlan fused_plan(const void *O, size_t Ns, size_t P, size_t ldo) {
+  FusedPlan pl;
+  if (ldo % 4 != 0 || reinterpret_cast<uintptr_t>(O) % 16 != 0 || Ns == 0) return pl;
+  int dev = 0, smax = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return pl;
+  for (int C = 1; C <= 16; C *= 2) {
+    const size_t sl = ((P + C - 1) / C + 3) / 4 * 4;
+    if (sl > (size_t)kFusedMaxSlice) continue;
+    const FusedLayout L = fused_layout((int)sl, C);
+    if (L.bytes > smax) continue;
+    if (cudaFuncSetAttribute(k_sr_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes) != cudaSuccess ||
+        (C > 8 && cudaFuncSetAttribute(k_sr_fused, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess))
+      break;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kFusedThreads);
+    cfg.dynamicSmemBytes = L.bytes;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int G = 0;
+    if (cudaOccupancyMaxActiveClusters(&G, k_sr_fused, &cfg) != cudaSuccess || G <= 0) break;
+    if (G > kFusedMaxClusters) G = kFusedMaxClusters;
+    if ((size_t)G > Ns) G = (int)Ns;
+    pl.C = C;
+    pl.G = G;
+    pl.SL = (int)sl;
+    pl.bytes = L.bytes;
+    break;
+  }
+  cudaGetLastError();   // a refused attribute or query leaves the two-pass product in use
+  return pl;
+}
+
+// S' v -> Ap by the one-pass product: 5 launches, O streamed once.
+static cudaError_t matvec_fused(const uint32_t *O, size_t Ns, size_t P, size_t ldo, const double *v, double shift,
+                                SrPtrs &q, int nb, const FusedPlan &pl, int *err, cudaStream_t st) {
+  k_sr_vprep<<<nb, kSrBlock, 0, st>>>(P, v, q.mean, q.vf, q.part, q.part2, q.sc);
+  k_sr_cfin<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = pl.C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(pl.C * pl.G);
+  cfg.blockDim = dim3(kFusedThreads);
+  cfg.dynamicSmemBytes = pl.bytes;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  float2 *wp = reinterpret_cast<float2 *>(q.mpart);   // G double-float rows of P in the moments' buffer
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_sr_fused, O, Ns, P, ldo, pl.SL, (const float *)q.vf, q.t, wp,
+                                           (const double *)q.sc, err);
+  if (e != cudaSuccess) return e;
+  k_sr_tsum<<<1, 1024, 0, st>>>(q.t, Ns, q.sc);
+  k_sr_wfin_dd<<<nb, kSrBlock, 0, st>>>(Ns, P, q.mean, wp, pl.G, v, shift, q.Ap, q.part, q.sc);
+  return cudaSuccess;
 }
 
 }  // namespace tdo
@@ -571,24 +967,77 @@ size_t sr_work_doubles(size_t Ns, size_t P) {
 }
 
 namespace tdo {
+// mean and Jacobi diagonal of O (one pass over O)
+template <typename OT>
+static void moments(const OT *O2, size_t Ns, size_t P, size_t ldo, double shift, SrPtrs &q, int nb, cudaStream_t st) {
+  constexpr int CH = SrChunk<OT>::value;
+  const int nchunks = (int)((P + CH - 1) / CH);
+  const bool vec = ldo % (16 / sizeof(OT)) == 0 && reinterpret_cast<uintptr_t>(O2) % 16 == 0;
+  if (vec)
+    k_sr_mpart<OT, true><<<dim3(nchunks, kSampleGroups), CH / 4, 0, st>>>(O2, Ns, P, ldo, q.mpart);
+  else
+    k_sr_mpart<OT, false><<<dim3(nchunks, kSampleGroups), CH / 4, 0, st>>>(O2, Ns, P, ldo, q.mpart);
+  k_sr_mfin<<<nb, kSrBlock, 0, st>>>(Ns, P, shift, q.mpart, q.mean, q.diag);
+}
+
+static int sr_blocks(size_t P) {
+  int nb = (int)((P + kSrBlock - 1) / kSrBlock);
+  return nb > 1024 ? 1024 : (nb < 1 ? 1 : nb);
+}
+
+// One product (Re S + shift I) v -> Ap outside the CG loop (BF16-pair storage).
+static cudaError_t sr_apply_t(const uint32_t *O2, size_t Ns, size_t P, size_t ldo, const double *v, double shift,
+                              double *Ap, double *work, int product_mode, int *err, int *shape, cudaStream_t st) {
+  SrPtrs q = sr_carve(work, Ns, P);
+  const int nb = sr_blocks(P);
+  FusedPlan pl;
+  if (product_mode == 1) pl = fused_plan(O2, Ns, P, ldo);
+  if (shape) { shape[0] = pl.C > 0 ? 1 : 0; shape[1] = pl.C; shape[2] = pl.G; }
+  moments(O2, Ns, P, ldo, shift, q, nb, st);
+  k_sr_clear<<<1, 32, 0, st>>>(q.sc);
+  if (pl.C > 0) {
+    const cudaError_t e = matvec_fused(O2, Ns, P, ldo, v, shift, q, nb, pl, err, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    matvec(O2, Ns, P, ldo, v, shift, q, nb, st);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(Ap, q.Ap, sizeof(double) * P, cudaMemcpyDeviceToDevice, st);
+}
+
 template <typename OT>
 static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const double *rhs, const double *x0,
                            double shift,
                            double tol, int max_iter, double *x, double *work, int *iters, double *resid,
                            int *outcome, double *last_pap,
-                           long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used, cudaStream_t st) {
+                           long long *launches, cudaEvent_t *mv_ev, int mv_cap, int *mv_used, int product_mode,
+                           int *err, int *shape, cudaStream_t st) {
   SrPtrs q = sr_carve(work, Ns, P);
-  int nb = (int)((P + kSrBlock - 1) / kSrBlock);
-  if (nb > 1024) nb = 1024;
-  if (nb < 1) nb = 1;
+  FusedPlan pl;
+  if constexpr (sizeof(OT) == 4)
+    if (product_mode == 1) pl = fused_plan(O2, Ns, P, ldo);
+  if (shape) { shape[0] = pl.C > 0 ? 1 : 0; shape[1] = pl.C; shape[2] = pl.G; }
+  const int nb = sr_blocks(P);
   long long nl = 0;
   int nmv = 0;
   if (mv_used) *mv_used = 0;
   auto mv = [&](const double *v) -> cudaError_t {
     const bool rec = mv_ev && nmv < mv_cap;
     if (rec) cudaEventRecord(mv_ev[2 * nmv], st);
-    matvec(O2, Ns, P, ldo, v, shift, q, nb, st);
-    nl += 7;
+    if constexpr (sizeof(OT) == 4) {
+      if (pl.C > 0) {
+        const cudaError_t e = matvec_fused(O2, Ns, P, ldo, v, shift, q, nb, pl, err, st);
+        if (e != cudaSuccess) return e;
+        nl += 5;
+      } else {
+        matvec(O2, Ns, P, ldo, v, shift, q, nb, st);
+        nl += 7;
+      }
+    } else {
+      matvec(O2, Ns, P, ldo, v, shift, q, nb, st);
+      nl += 7;
+    }
     if (rec) {
       cudaEventRecord(mv_ev[2 * nmv + 1], st);
       ++nmv;
@@ -596,16 +1045,7 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const 
     }
     return cudaSuccess;
   };
-  {
-    constexpr int CH = SrChunk<OT>::value;
-    const int nchunks = (int)((P + CH - 1) / CH);
-    const bool vec = ldo % (16 / sizeof(OT)) == 0 && reinterpret_cast<uintptr_t>(O2) % 16 == 0;
-    if (vec)
-      k_sr_mpart<OT, true><<<dim3(nchunks, kSampleGroups), CH / 4, 0, st>>>(O2, Ns, P, ldo, q.mpart);
-    else
-      k_sr_mpart<OT, false><<<dim3(nchunks, kSampleGroups), CH / 4, 0, st>>>(O2, Ns, P, ldo, q.mpart);
-    k_sr_mfin<<<nb, kSrBlock, 0, st>>>(Ns, P, shift, q.mpart, q.mean, q.diag);
-  }
+  moments(O2, Ns, P, ldo, shift, q, nb, st);
   k_sr_clear<<<1, 32, 0, st>>>(q.sc);
   nl += 3;
   cudaError_t e;
@@ -660,15 +1100,24 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const 
 // mv_ev (optional): mv_cap event pairs recorded around the S' v launches; *mv_used = pairs recorded.
 // o_bf16: O holds BF16 pairs (uint32 per element) instead of FP32 (re, im); ldo >= P: elements per row.
 // *outcome: 0 stopped at max_iter, 1 converged, 2 breakdown (p . S'p not positive), 3 a non-finite value;
-// *last_pap: the last p . S'p.  The return value reports CUDA errors only.
+// *last_pap: the last p . S'p.  product_mode 0: two passes; 1: the one-pass product where O's storage and
+// shape allow it (BF16 pairs), else two passes.  err (device int, may be NULL): set when a bounded wait of the
+// one-pass product gave up.  shape (may be NULL): {one pass used, cluster size, clusters}.  The return
+// value reports CUDA errors only.
 cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, size_t ldo, const double *rhs, const double *x0,
                        double shift, double tol, int max_iter, double *x, double *work, int n_sm, int *iters,
                        double *resid, int *outcome, double *last_pap, long long *launches, cudaEvent_t *mv_ev,
-                       int mv_cap, int *mv_used, cudaStream_t st) {
+                       int mv_cap, int *mv_used, int product_mode, int *err, int *shape, cudaStream_t st) {
   (void)n_sm;
   if (o_bf16)
     return tdo::sr_cg_t(reinterpret_cast<const uint32_t *>(O), Ns, P, ldo, rhs, x0, shift, tol, max_iter, x, work, iters,
-                        resid, outcome, last_pap, launches, mv_ev, mv_cap, mv_used, st);
+                        resid, outcome, last_pap, launches, mv_ev, mv_cap, mv_used, product_mode, err, shape, st);
   return tdo::sr_cg_t(reinterpret_cast<const float2 *>(O), Ns, P, ldo, rhs, x0, shift, tol, max_iter, x, work, iters,
-                      resid, outcome, last_pap, launches, mv_ev, mv_cap, mv_used, st);
+                      resid, outcome, last_pap, launches, mv_ev, mv_cap, mv_used, product_mode, err, shape, st);
+}
+
+// One product (Re S + shift I) v with O as BF16 pairs [Ns][ldo] (ldo >= P), v and Ap FP64 [P] on the device.
+cudaError_t sr_apply_impl(const uint32_t *O, size_t Ns, size_t P, size_t ldo, const double *v, double shift, double *Ap,
+                          double *work, int product_mode, int *err, int *shape, cudaStream_t st) {
+  return tdo::sr_apply_t(O, Ns, P, ldo, v, shift, Ap, work, product_mode, err, shape, st);
 }

@@ -35,11 +35,13 @@ cudaError_t launch_conv_vjp(int d, int c1, const float *Wc1, const float *bc1, c
                             const float2 *oref, size_t ldo, long long o_wc1, long long o_bc1, long long o_wc2,
                             long long o_bc2, cudaStream_t st);
 size_t sr_work_doubles(size_t Ns, size_t P);
+cudaError_t sr_apply_impl(const uint32_t *O, size_t Ns, size_t P, size_t ldo, const double *v, double shift, double *Ap,
+                          double *work, int product_mode, int *err, int *shape, cudaStream_t st);
 cudaError_t measure_fma_peak(int fp64, int n_sm, cudaStream_t st, double *tflops);
 cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, size_t ldo, const double *rhs, const double *x0,
                        double shift, double tol, int max_iter, double *x, double *work, int n_sm, int *iters,
                        double *resid, int *outcome, double *last_pap, long long *launches, cudaEvent_t *mv_ev,
-                       int mv_cap, int *mv_used, cudaStream_t st);
+                       int mv_cap, int *mv_used, int product_mode, int *err, int *shape, cudaStream_t st);
 cudaError_t launch_params_f32(const double *theta, size_t P, const long long *tab, int n_tensors,
                               float *dst, cudaStream_t st);
 size_t bf16_packed_bytes(const DevModel &m);
@@ -165,6 +167,8 @@ struct tdo_ctx {
   int last_sr_outcome = 0;      // 0 max_iter reached, 1 converged, 2 breakdown, 3 non-finite
   double last_sr_pap = 0;       // last p . S'p of the solve
   int last_sr_restarts = 0;     // 1 when the warm-started solve failed and was rerun from x = 0
+  int sr_product = TDO_SR_PRODUCT_TWO_PASS;   // or TDO_SR_PRODUCT_ONE_PASS (where the storage allows it)
+  int last_sr_shape[3] = {0, 0, 0};   // one pass used, cluster size, clusters (last solve)
   // kernel timing (tdo_timing)
   bool timing = false;
   std::vector<TimingRec> trec;
@@ -1142,7 +1146,8 @@ static cudaError_t sr_cg_timed(tdo_ctx *c, const void *O, int o_bf16, size_t ldo
   int used = 0;
   const cudaError_t err = sr_cg_impl(O, o_bf16, Ns, c->P, ldo, rhs, x0, shift, tol, max_iter, x, c->srwork.as<double>(), c->n_sm,
                                      iters, resid, outcome, last_pap, launches, ev.empty() ? nullptr : ev.data(),
-                                     (int)ev.size() / 2, &used, c->stream);
+                                     (int)ev.size() / 2, &used, c->sr_product, c->tc ? c->errflag.as<int>() : nullptr,
+                                     c->last_sr_shape, c->stream);
   for (int i = 0; i < (int)ev.size(); ++i) {
     if (i / 2 < used && i % 2 == 0) c->trec.push_back({G_SR_MV, ev[i], ev[i + 1], 1});
     else if (i / 2 >= used) c->epool.push_back(ev[i]);
@@ -1232,6 +1237,7 @@ extern "C" tdo_status tdo_sr_step(tdo_ctx *c, const uint32_t *sig, const uint32_
   c->last_sr_pap = pap;
   c->last_sr_restarts = restarts;
   CU(c, e);
+  TRY(check_err_flag(c));
   TRY(sr_outcome_status(c, outcome));
   {
     Timed tm(c, G_UPDATE);
@@ -1493,6 +1499,38 @@ extern "C" tdo_status tdo_wait_selftest(tdo_ctx *c, long long spin_limit) {
   CU(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->stream));
   CU(c, launch_wait_probe(c->errflag.as<int>(), spin_limit, c->stream));
   return check_err_flag(c);
+}
+
+extern "C" tdo_status tdo_set_sr_product(tdo_ctx *c, int mode) {
+  if (!c) return TDO_EINVAL;
+  if (mode != TDO_SR_PRODUCT_TWO_PASS && mode != TDO_SR_PRODUCT_ONE_PASS)
+    return fail(c, TDO_EINVAL, "tdo_set_sr_product: mode must be TDO_SR_PRODUCT_TWO_PASS or TDO_SR_PRODUCT_ONE_PASS");
+  c->sr_product = mode;
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_sr_apply(tdo_ctx *c, const uint32_t *O, size_t Ns, size_t ldo, const double *v, double shift,
+                                   double *Ap) {
+  if (!c) return TDO_EINVAL;
+  if (Ns == 0) return fail(c, TDO_EINVAL, "Ns must be > 0");
+  if (!O || !v || !Ap) return fail(c, TDO_EINVAL, "NULL buffer");
+  if (ldo < c->P) return fail(c, TDO_EINVAL, "tdo_sr_apply: ldo must be >= the parameter count");
+  if (!is_device_ptr(O) || !is_device_ptr(v) || !is_device_ptr(Ap))
+    return fail(c, TDO_EINVAL, "tdo_sr_apply: O, v and Ap must be device memory");
+  CU(c, c->srwork.ensure(sizeof(double) * sr_work_doubles(Ns, c->P)));
+  CU(c, sr_apply_impl(O, Ns, c->P, ldo, v, shift, Ap, c->srwork.as<double>(), c->tc ? c->sr_product : TDO_SR_PRODUCT_TWO_PASS,
+                      c->tc ? c->errflag.as<int>() : nullptr, c->last_sr_shape, c->stream));
+  TRY(check_err_flag(c));
+  CU(c, cudaStreamSynchronize(c->stream));
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_sr_product_shape(const tdo_ctx *c, int *one_pass, int *cluster, int *clusters) {
+  if (!c) return TDO_EINVAL;
+  if (one_pass) *one_pass = c->last_sr_shape[0];
+  if (cluster) *cluster = c->last_sr_shape[1];
+  if (clusters) *clusters = c->last_sr_shape[2];
+  return TDO_OK;
 }
 
 extern "C" tdo_status tdo_sr_report(const tdo_ctx *c, int *outcome, double *last_pap, int *restarts) {

@@ -23,7 +23,7 @@ STATUS = {0: "TDO_OK", -1: "TDO_EINVAL", -2: "TDO_ENOMEM", -3: "TDO_ECUDA", -4: 
 EXPORTS = ["tdo_model_num_params", "tdo_create", "tdo_destroy", "tdo_num_params", "tdo_max_connections",
            "tdo_set_params", "tdo_get_params", "tdo_log_rho", "tdo_log_rho_vjp", "tdo_jacobian",
            "tdo_connections", "tdo_local_estimator", "tdo_local_estimator_noalloc", "tdo_sample", "tdo_grad", "tdo_sr_solve", "tdo_set_sr_options", "tdo_sr_step",
-           "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_sr_report", "tdo_wait_selftest", "tdo_set_optimizer", "tdo_log_rho_ragged", "tdo_ragged_tuning", "tdo_measure_peak", "tdo_last_error", "tdo_sample_diag", "tdo_magnetisation",
+           "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_sr_report", "tdo_set_sr_product", "tdo_sr_product_shape", "tdo_sr_apply", "tdo_wait_selftest", "tdo_set_optimizer", "tdo_log_rho_ragged", "tdo_ragged_tuning", "tdo_measure_peak", "tdo_last_error", "tdo_sample_diag", "tdo_magnetisation",
            "tdo_purity", "tdo_schedule_value", "tdo_vmc_step"]
 
 
@@ -117,6 +117,9 @@ def lib() -> C.CDLL:
         L.tdo_timing_read.argtypes = [vp, C.c_char_p, dp, C.POINTER(C.c_longlong)]
         L.tdo_sr_info.argtypes = [vp, C.POINTER(i32), dp]
         L.tdo_sr_report.argtypes = [vp, C.POINTER(i32), dp, C.POINTER(i32)]
+        L.tdo_set_sr_product.argtypes = [vp, i32]
+        L.tdo_sr_product_shape.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.tdo_sr_apply.argtypes = [vp, vp, sz, sz, vp, C.c_double, vp]
         L.tdo_wait_selftest.argtypes = [vp, C.c_longlong]
         L.tdo_measure_peak.argtypes = [i32, vp, dp]
         L.tdo_last_error.argtypes = [vp]
@@ -359,6 +362,25 @@ class Context:
         o, pap, r = C.c_int(), C.c_double(), C.c_int()
         self._chk(lib().tdo_sr_report(self.h, C.byref(o), C.byref(pap), C.byref(r)))
         return o.value, pap.value, r.value
+
+    def set_sr_product(self, mode: str):
+        """tdo_set_sr_product: "two_pass" (default) or "one_pass" (thread-block clusters, where the
+        log-derivatives' storage allows it)."""
+        self._chk(lib().tdo_set_sr_product(self.h, {"two_pass": 0, "one_pass": 1}[mode]))
+
+    def sr_apply(self, O_pairs, v, shift: float, out=None):
+        """tdo_sr_apply: (Re S + shift I) v for log-derivatives O given as BF16 pairs (a device int32 / uint32
+        tensor [Ns][ldo], ldo >= P), v FP64 [P] on the device."""
+        Ns, ldo = O_pairs.shape
+        out = self._like(v, (self.P,), np.float64) if out is None else out
+        self._chk(lib().tdo_sr_apply(self.h, _ptr(O_pairs), Ns, ldo, _ptr(v), float(shift), _ptr(out)))
+        return out
+
+    def sr_product_shape(self):
+        """(one pass used, CTAs per cluster, clusters) of the last SR step's products (tdo_sr_product_shape)."""
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        self._chk(lib().tdo_sr_product_shape(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
 
     def wait_selftest(self, spin_limit: int) -> int:
         """tdo_wait_selftest: status of a bounded device wait that nothing completes (TDO_ETIMEOUT = -5)."""

@@ -74,6 +74,9 @@ def test_null_context_is_rejected_without_a_device(libtdo):
     assert libtdo.tdo_sr_step(None, None, None, 4, 0.1, 0.1, None) == einval
     assert libtdo.tdo_local_estimator_noalloc(None, None, None, 4, None, None, None) == einval
     assert libtdo.tdo_sr_report(None, None, None, None) == einval
+    assert libtdo.tdo_set_sr_product(None, 0) == einval
+    assert libtdo.tdo_sr_product_shape(None, None, None, None) == einval
+    assert libtdo.tdo_sr_apply(None, None, 4, 4, None, ctypes.c_double(0.1), None) == einval
     assert libtdo.tdo_wait_selftest(None, 16) == einval
     assert libtdo.tdo_set_optimizer(None, 1, 0.9, 0.999, 1e-8) == einval
     assert libtdo.tdo_log_rho_ragged(None, None, None, None, 4, None) == einval

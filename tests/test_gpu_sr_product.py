@@ -1,0 +1,103 @@
+"""The one-pass S'v product against the two-pass product (metric-tensor section: S v = (1/Ns) Re[Obar^H
+(Obar v)] + shift v, S never formed).
+
+The one-pass product has thread-block clusters exchange t_s = O_s v in distributed shared memory and
+accumulate Re(O^H t) from the same copy of each row.  Both products run on the same tensor-core context,
+samples and parameters, and differ only in the order of the FP32 partial sums.  Checks:
+  - two CG iterations (one full product enters the update) agree to 1e-5 relative (measured 1e-6 to
+    2.3e-6: the residual update r - alpha S'p cancels, which amplifies the summation order);
+  - CG to 1e-10 agrees to 1e-4 relative (the summation order, amplified by the condition number of
+    S + shift I).
+The parameter counts give clusters of 1, 2, 4, 8 and 16 CTAs.  The sample counts leave clusters with
+uneven row counts, and with none (37 samples).  tdo_sr_apply, one product on its own, is compared element
+by element with the oracle's matrix-free product of the same BF16-rounded O in FP64, in both modes."""
+import numpy as np
+import pytest
+
+from oracle import estimators as E
+from paper_2502_20723_gb300 import synth
+from tests.gpu_common import problem
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+LR, SHIFT = 0.0061, 0.004
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_20723_gb300 import build
+    build.build()
+
+
+def dev(a):
+    return torch.as_tensor(np.asarray(a).astype(np.int64)).to(torch.int32).cuda()
+
+
+def update(ctx, th, sig, sigp, mode, tol, iters):
+    ctx.set_params(th)
+    ctx.set_sr_product(mode)
+    ctx.set_sr_options(tol, iters)
+    ctx.sr_step(sig, sigp, LR, SHIFT)
+    return (th - ctx.get_params()) / LR, ctx.sr_product_shape(), ctx.sr_info()[0]
+
+
+@pytest.mark.parametrize("d,h,L,r,Ns,C", [
+    (32, 4, 1, 0, 64, 1), (64, 8, 1, 0, 96, 2), (64, 8, 1, 4, 300, 4), (64, 8, 2, 4, 37, 8),
+    (64, 8, 4, 4, 512, 16),
+])
+def test_one_pass_product_matches_two_pass(d, h, L, r, Ns, C):
+    from paper_2502_20723_gb300 import tdo
+    n = 16
+    spec = synth.model_spec(d, h, L, r)
+    th = synth.init_params(spec, seed=5)
+    s0, s1 = synth.random_configs(n, Ns, seed=23)
+    sig, sigp = dev(s0), dev(s1)
+    ctx = tdo.Context(problem("ising", n), spec, th, "fp16")
+    for tol, iters, bound in ((0.0, 2, 1e-5), (1e-10, 500, 1e-4)):
+        d2, shape2, it2 = update(ctx, th, sig, sigp, "two_pass", tol, iters)
+        d1, shape1, it1 = update(ctx, th, sig, sigp, "one_pass", tol, iters)
+        assert shape2 == (0, 0, 0)
+        assert shape1[0] == 1 and shape1[1] == C and 1 <= shape1[2] <= 24, shape1
+        rel = np.linalg.norm(d1 - d2) / np.linalg.norm(d2)
+        print(f"P={th.size} C={C} clusters={shape1[2]} Ns={Ns} iterations {it1}/{it2}: "
+              f"relative difference {rel:.3e}")
+        assert np.all(np.isfinite(d1)) and rel <= bound
+
+
+NAN_PAIR = 0x7FC07FC0   # padding columns: a product that reads them as data turns non-finite
+
+
+@pytest.mark.parametrize("d,h,L,r,Ns,C", [
+    (32, 4, 1, 0, 64, 1), (64, 8, 1, 0, 96, 2), (64, 8, 1, 4, 300, 4), (64, 8, 2, 4, 37, 8),
+    (64, 8, 4, 4, 256, 16),
+])
+def test_sr_apply_matches_oracle_product(d, h, L, r, Ns, C):
+    from paper_2502_20723_gb300 import tdo
+    spec = synth.model_spec(d, h, L, r)
+    th = synth.init_params(spec, seed=5)
+    P = th.size
+    ldo = (P + 3) // 4 * 4 + 4
+    ctx = tdo.Context(problem("ising", 16), spec, th, "fp16")
+    rng = np.random.default_rng(P)
+    bre = torch.from_numpy((0.5 + rng.standard_normal((Ns, P))).astype(np.float32)).to(torch.bfloat16)
+    bim = torch.from_numpy((rng.standard_normal((Ns, P)) - 0.3).astype(np.float32)).to(torch.bfloat16)
+    O = bre.float().numpy().astype(np.float64) + 1j * bim.float().numpy().astype(np.float64)
+    pairs = torch.full((Ns, ldo), NAN_PAIR, dtype=torch.int32)
+    pairs[:, :P] = (bre.view(torch.int16).to(torch.int32) & 0xFFFF) | (bim.view(torch.int16).to(torch.int32) << 16)
+    pairs = pairs.cuda()
+    v = rng.standard_normal(P)
+    ref = E.sr_product(O, v, SHIFT)
+    got = {}
+    for mode in ("two_pass", "one_pass"):
+        ctx.set_sr_product(mode)
+        got[mode] = ctx.sr_apply(pairs, torch.from_numpy(v).cuda(), SHIFT).cpu().numpy()
+        shape = ctx.sr_product_shape()
+        assert shape[0] == (mode == "one_pass") and (mode != "one_pass" or shape[1] == C), shape
+        rel = np.linalg.norm(got[mode] - ref) / np.linalg.norm(ref)
+        elem = np.abs(got[mode] - ref).max() / np.abs(ref).max()
+        print(f"P={P} Ns={Ns} {mode} shape {shape}: relative error {rel:.3e}, max element error {elem:.3e}")
+        assert np.all(np.isfinite(got[mode])) and rel <= 1e-5 and elem <= 1e-5

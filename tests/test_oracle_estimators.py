@@ -137,6 +137,19 @@ def test_sr_matrix_brute_force_and_solve_residual():
     assert np.linalg.norm((S + 1e-3 * np.eye(5)) @ d - g) < 1e-10 * np.linalg.norm(g) / 1e-3
 
 
+def test_sr_product_is_the_brute_force_matrix_times_v():
+    """The matrix-free product against the double-sum S of the metric-tensor section times v, with a
+    mean far from zero (the centring must cancel it) and a shift."""
+    rng = np.random.default_rng(4)
+    O = 3.0 + rng.standard_normal((13, 6)) + 1j * (rng.standard_normal((13, 6)) - 2.0)
+    S = np.zeros((6, 6))
+    for i in range(6):
+        for j in range(6):
+            S[i, j] = (np.mean(np.conj(O[:, i]) * O[:, j]) - np.mean(np.conj(O[:, i])) * np.mean(O[:, j])).real
+    v = rng.standard_normal(6)
+    assert np.abs(E.sr_product(O, v, 0.25) - (S @ v + 0.25 * v)).max() < 1e-12
+
+
 def test_connections_structure_ising():
     """Ising row: diagonal + N sigma flips + N sigma' flips + one jump per site with both bits = 1."""
     p = synth.ising_chain(6, g=1.0)
