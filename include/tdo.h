@@ -49,8 +49,14 @@ typedef enum {
 
 enum { TDO_EMBED_TOKEN = 0, TDO_EMBED_CONV = 1 };
 /* Precision of a context: TDO_FP32 = FP32 CUDA-core path; TDO_BF16 and TDO_FP16 = tensor-core path
- * (tcgen05 GEMMs with FP32 accumulation) whose GEMM operands are BF16 or FP16 respectively. */
-enum { TDO_FP32 = 0, TDO_BF16 = 1, TDO_FP16 = 2 };
+ * (tcgen05 GEMMs with FP32 accumulation) whose GEMM operands are BF16 or FP16 respectively.  TDO_FP8 =
+ * the tensor-core path whose evaluations of log rho (tdo_log_rho, tdo_log_rho_ragged, the local
+ * estimator's connected rows, tdo_sample and the observables) run on E4M3 operands (kind::f8f6f4, FP32
+ * accumulation; one power-of-two scale per weight matrix, one per tile for each activation image, set
+ * from the largest magnitude so that scaled values stay below 256); its gradient, log-derivatives and SR
+ * step use the FP16 kernels.  E4M3 keeps 4 significant bits: its log rho error is stated beside its
+ * throughput, not bounded like the 16-bit paths'. */
+enum { TDO_FP32 = 0, TDO_BF16 = 1, TDO_FP16 = 2, TDO_FP8 = 3 };
 
 /* Problem statement: a chain of N spins, a Hamiltonian given as a sum of real multiples of Pauli strings
  * on at most two sites, and single-site jump operators with rates (Eq. Lindblad / Eq. VecLin). */
@@ -74,7 +80,7 @@ typedef struct {
   int n_heads;                /* divides d_model; head dim <= 16 */
   int n_layers;               /* 1..8 */
   int mlp_ratio;              /* 0 (the paper's block: no MLP) or 1..4 */
-  int precision;              /* TDO_FP32, TDO_BF16 or TDO_FP16 (tensor-core GEMM operand type) */
+  int precision;              /* TDO_FP32, TDO_BF16, TDO_FP16 or TDO_FP8 (tensor-core GEMM operand type) */
 } tdo_model;
 
 /* Number of real parameters of a model (the length of theta). 0 for an invalid model. */

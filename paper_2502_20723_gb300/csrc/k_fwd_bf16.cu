@@ -26,11 +26,21 @@
 #include "tcgen05.cuh"
 
 // TDO_F16 = 1 compiles the same kernels with FP16 operand images and weights (k_fwd_f16.cu), in their own
-// namespace and with launcher names ending in _f16; the default build uses BF16 operands.
+// namespace and with launcher names ending in _f16; the default build uses BF16 operands.  TDO_F8 = 1
+// (k_fwd_f8.cu) compiles them with E4M3 GEMM operands (tcgen05.mma kind::f8f6f4, FP32 accumulation):
+// 8-bit canonical images, one power-of-two scale per weight matrix, one per tile for each activation
+// image (from the tile's largest magnitude), dequantised in the epilogue; used for evaluation only
+// (no parked activations).
 #ifndef TDO_F16
 #define TDO_F16 0
 #endif
-#if TDO_F16
+#ifndef TDO_F8
+#define TDO_F8 0
+#endif
+#if TDO_F8
+#define TDO_OPNS f8op
+#define TDO_OPFN(name) name##_f8
+#elif TDO_F16
 #define TDO_OPNS f16op
 #define TDO_OPFN(name) name##_f16
 #else
@@ -42,6 +52,8 @@ namespace tdo {
 namespace TDO_OPNS {
 
 constexpr bool kF16 = TDO_F16 != 0;   // operand type of every tensor-core GEMM image and weight
+constexpr bool kF8 = TDO_F8 != 0;     // E4M3 images and weights instead
+constexpr int kEB = kF8 ? 1 : 2;      // bytes per GEMM operand element
 
 constexpr int kThreads = 256;
 constexpr int kRows = 128;
@@ -50,18 +62,19 @@ constexpr int kTmemCols = 256;
 template <int D>
 struct Geo {
   static constexpr int HC = (4 * D < 128) ? 4 * D : 128;        // hidden chunk (max mlp_ratio 4)
-  static constexpr int A_OFF = 0;                                // BF16 [128][D]
-  static constexpr int A_BYTES = kRows * D * 2;
+  static constexpr int A_OFF = 0;                                // BF16 / FP16 / E4M3 [128][D]
+  static constexpr int A_BYTES = kRows * D * kEB;
   static constexpr int KS = D + 1;                               // K/V/pool row stride (floats): no bank conflicts
   static constexpr int KV_OFF = A_OFF + A_BYTES;                 // FP32 K [128][KS], V [128][KS]
   static constexpr int KV_BYTES = 2 * kRows * KS * 4;            // (G [128][HC] BF16, pool [128][KS] alias)
   static constexpr int W_OFF = KV_OFF + KV_BYTES;                // weights of the current GEMM
-  static constexpr int W_BYTES = (3 * D * D * 2 > 2 * HC * D) ? 3 * D * D * 2 : 2 * HC * D;
+  static constexpr int W_BYTES = ((3 * D * D > HC * D) ? 3 * D * D : HC * D) * kEB;
   static constexpr int M_OFF = W_OFF + W_BYTES;                  // misc
   // misc layout (bytes from M_OFF): mbar_mma 8, mbar_w 8, tmem holder 4, flag 4, configs 2x64x4,
-  // F [128][2] floats, results [64] float2
-  static constexpr int BYTES = M_OFF + 16 + 8 + 512 + 1024 + 512;
-  static_assert(2 * HC * D <= KV_BYTES, "hidden chunk fits the K/V region");
+  // F [128][2] floats, results [64] float2, scale reductions [2][8] floats
+  static constexpr int RED_OFF = M_OFF + 16 + 8 + 512 + 1024 + 512;
+  static constexpr int BYTES = RED_OFF + 64;
+  static_assert(kRows * HC * kEB <= KV_BYTES, "hidden chunk fits the K/V region");
   // warp-MMA attention (N <= 16): FP16 Q, K [128][LDH] and V transposed [D][LDT] in the K/V region,
   // sequence s's keys at columns 16 s .. 16 s + 15 of V^T
   static constexpr int LDH = D + 8;                              // halves; conflict-free fragment rows
@@ -98,16 +111,70 @@ struct Ctl {
 };
 
 // Issue the MMAs of one GEMM: D[tmem + col] (+)= A[128 x K] * B^T, B stored [N][K]; commit to bar_mma.
+// Every MMA covers 32 bytes of K (16 16-bit or 32 E4M3 elements): the next one starts 256 B later.
 __device__ __forceinline__ void gemm(Ctl &c, uint32_t a_addr, uint32_t b_addr, int K, int N, uint32_t col,
                                      bool accumulate, bool f16 = false) {
   if (c.mma_thread) {
     tc_fence_after();
-    const uint32_t id = f16 ? idesc_f16(kRows, N) : idesc16<kF16>(kRows, N);
     // descriptor of addr + 256 kk = descriptor of addr + 16 kk (address field addr >> 4, below 256 KB)
-    const uint64_t ad = sdesc(a_addr, 128, K * 16), bd = sdesc(b_addr, 128, K * 16);
-    for (int kk = 0; kk < K / 16; ++kk)
-      mma_bf16(c.tmem + col, ad + 16 * kk, bd + 16 * kk, id, (accumulate || kk > 0) ? 1u : 0u);
+    if constexpr (kF8) {
+      const uint32_t id = idesc_e4m3(kRows, N);
+      const uint64_t ad = sdesc(a_addr, 128, K * 8), bd = sdesc(b_addr, 128, K * 8);
+      for (int kk = 0; kk < K / 32; ++kk)
+        mma_e4m3(c.tmem + col, ad + 16 * kk, bd + 16 * kk, id, (accumulate || kk > 0) ? 1u : 0u);
+    } else {
+      const uint32_t id = f16 ? idesc_f16(kRows, N) : idesc16<kF16>(kRows, N);
+      const uint64_t ad = sdesc(a_addr, 128, K * 16), bd = sdesc(b_addr, 128, K * 16);
+      for (int kk = 0; kk < K / 16; ++kk)
+        mma_bf16(c.tmem + col, ad + 16 * kk, bd + 16 * kk, id, (accumulate || kk > 0) ? 1u : 0u);
+    }
     mma_commit(c.bar_mma);
+  }
+}
+
+// Image element addressing and stores for the build's operand type.
+__device__ __forceinline__ uint32_t canonE(int row, int k, int K) {
+  if constexpr (kF8) return canon8(row, k, K);
+  else return canon(row, k, K);
+}
+// 8 consecutive k values (k0 % 8 == 0) of one row, times s (E4M3 only; the 16-bit images are unscaled).
+__device__ __forceinline__ void put_row8(uint8_t *base, int row, int k0, int K, const float *v, float s) {
+  if constexpr (kF8) {
+    uint2 q;
+    q.x = (uint32_t)pack_e4m3(v[0] * s, v[1] * s) | ((uint32_t)pack_e4m3(v[2] * s, v[3] * s) << 16);
+    q.y = (uint32_t)pack_e4m3(v[4] * s, v[5] * s) | ((uint32_t)pack_e4m3(v[6] * s, v[7] * s) << 16);
+    *reinterpret_cast<uint2 *>(base + canon8(row, k0, K)) = q;
+  } else {
+    st_row8<kF16>(base, row, k0, K, v);
+  }
+}
+// Two consecutive k values (k even) of one row, times s (E4M3 only).
+__device__ __forceinline__ void put_pair(uint8_t *base, int row, int k, int K, float v0, float v1, float s) {
+  if constexpr (kF8) *reinterpret_cast<uint16_t *>(base + canon8(row, k, K)) = pack_e4m3(v0 * s, v1 * s);
+  else *reinterpret_cast<uint32_t *>(base + canon(row, k, K)) = pack16<kF16>(v0, v1);
+}
+
+// Power-of-two scale for an E4M3 image of the tile: every thread passes the largest magnitude it will
+// store; the CTA's largest m in [2^e, 2^(e+1)) gives 2^(7 - e), so scaled magnitudes stay below 256 (E4M3
+// saturates at 448).  1 for an all-zero image.  A block barrier; red alternates between two 8-float halves
+// so that consecutive calls need no second barrier.  Returns 1 without a barrier in the 16-bit builds.
+__device__ __forceinline__ float tile_scale(float amax, float *red, int &par) {
+  if constexpr (!kF8) {
+    return 1.0f;
+  } else {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    float *r = red + 8 * par;
+    par ^= 1;
+    if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    float m = r[0];
+#pragma unroll
+    for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, r[w]);
+    if (!(m >= 1.17549435e-38f)) return 1.0f;                   // zero (or subnormal) image
+    int f = 127 + 7 - ((int)((__float_as_uint(m) >> 23) & 0xffu) - 127);
+    f = f < 1 ? 1 : (f > 254 ? 254 : f);                        // a normal power of two
+    return __uint_as_float((uint32_t)f << 23);
   }
 }
 
@@ -146,6 +213,23 @@ __device__ __forceinline__ uint32_t gelu_h2(uint32_t x) {
   return *reinterpret_cast<const uint32_t *>(&g);
 }
 
+// v *= f (E4M3 dequantisation; nothing in the 16-bit builds)
+__device__ __forceinline__ void scale16(float (&v)[16], float f) {
+  if constexpr (kF8) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] *= f;
+  }
+}
+// Zero 8 consecutive k values (k0 % 8 == 0) of one image row.
+__device__ __forceinline__ void zero_row8(uint8_t *base, int row, int k0, int K) {
+  if constexpr (kF8) *reinterpret_cast<uint2 *>(base + canon8(row, k0, K)) = make_uint2(0u, 0u);
+  else *reinterpret_cast<uint4 *>(base + canon(row, k0, K)) = make_uint4(0u, 0u, 0u, 0u);
+}
+// Packed weights `elems` elements past p (p points at the build's operand type).
+__device__ __forceinline__ const uint8_t *wchunk(const uint16_t *p, size_t elems) {
+  return reinterpret_cast<const uint8_t *>(p) + elems * kEB;
+}
+
 // Agree across the CTA on failure; returns true if any thread saw a timeout.
 __device__ __forceinline__ bool sync_fail(Ctl &c, bool ok) {
   const int any = __syncthreads_or(ok ? 0 : 1);
@@ -158,7 +242,7 @@ __device__ __forceinline__ bool sync_fail(Ctl &c, bool ok) {
 // Copy the A image (BF16 [128][D], complete: callers are past a barrier) to global memory.
 template <int D>
 __device__ __forceinline__ void park_image(const uint8_t *A, uint8_t *dst) {
-  constexpr int N16 = 128 * D * 2 / 16;
+  constexpr int N16 = Geo<D>::A_BYTES / 16;
   for (int i = threadIdx.x; i < N16; i += kThreads)
     reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(A)[i];
 }
@@ -201,9 +285,22 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
       X[j] = q.x; X[j + 1] = q.y; X[j + 2] = q.z; X[j + 3] = q.w;
     }
   }
-  stage_w(c, w_addr, mb.Wqkv[0], 3 * D * D * 2);
+  stage_w(c, w_addr, mb.Wqkv[0], 3 * D * D * kEB);
+  float *red = reinterpret_cast<float *>(sm + G::RED_OFF);
+  int rpar = 0;
+  float ia = 1.f;   // 1 / the scale of the A image's E4M3 values (1 in the 16-bit builds)
+  auto put_x = [&]() {   // X -> the A image
+    float amx = 0.f;
+    if constexpr (kF8) {
 #pragma unroll
-  for (int j = 0; j < DH; j += 8) st_row8<kF16>(A, row, half * DH + j, D, X + j);
+      for (int j = 0; j < DH; ++j) amx = fmaxf(amx, fabsf(X[j]));
+    }
+    const float sx = tile_scale(amx, red, rpar);
+#pragma unroll
+    for (int j = 0; j < DH; j += 8) put_row8(A, row, half * DH + j, D, X + j, sx);
+    ia = 1.f / sx;
+  };
+  put_x();
 
   const int heads = m.heads;
   const float qscale = rsqrtf((float)HD) * 1.4426950408889634f;   // softmax in base 2
@@ -217,7 +314,25 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
     if (store) park_image<D>(A, store->X + ((size_t)l * store->tiles + tile) * (size_t)G::A_BYTES);
     ok = wait_mma(c);
     if (sync_fail(c, ok)) return false;
-    stage_w(c, w_addr, mb.Wo[l], D * D * 2);   // W is free: the QKV MMAs have completed
+    stage_w(c, w_addr, mb.Wo[l], D * D * kEB);   // W is free: the QKV MMAs have completed
+    // E4M3: dequantisation of Q, K, V (the image's scale times each weight matrix's), and the scale of the
+    // attention output's image from max |V| (each output row is a convex combination of V rows)
+    const float *wsc = kF8 ? mb.wscale + 6 * l : nullptr;
+    const float fq = kF8 ? ia * __ldg(wsc + 0) : 1.f, fk = kF8 ? ia * __ldg(wsc + 1) : 1.f,
+                fv = kF8 ? ia * __ldg(wsc + 2) : 1.f;
+    const float qs = qscale * fq;
+    float so = 1.f;
+    if constexpr (kF8) {
+      float amx = 0.f;
+#pragma unroll
+      for (int j = 0; j < DH; j += 16) {
+        float vv[16];
+        tmem_ld16(c.tmem + lane_addr + 2 * D + half * DH + j, vv);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) amx = fmaxf(amx, fabsf(vv[e]));
+      }
+      so = tile_scale(amx * fv, red, rpar);
+    }
     if (G::mma_attention(n, ts)) {
       // ---------------- attention by warp-level MMAs, one warp per (sequence, head): FP16 Q (scaled), K
       // and V^T to shared memory, output -> A (BF16)
@@ -231,12 +346,13 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
           tmem_ld16(c.tmem + lane_addr + half * DH + j, v);
           if (valid) {   // 16-byte stores: rows 144 bytes apart land on distinct bank groups
             uint4 *dst = reinterpret_cast<uint4 *>(Qh + row * G::LDH + half * DH + j);
-            dst[0] = make_uint4(amma::h2(v[0] * qscale, v[1] * qscale), amma::h2(v[2] * qscale, v[3] * qscale),
-                                amma::h2(v[4] * qscale, v[5] * qscale), amma::h2(v[6] * qscale, v[7] * qscale));
-            dst[1] = make_uint4(amma::h2(v[8] * qscale, v[9] * qscale), amma::h2(v[10] * qscale, v[11] * qscale),
-                                amma::h2(v[12] * qscale, v[13] * qscale), amma::h2(v[14] * qscale, v[15] * qscale));
+            dst[0] = make_uint4(amma::h2(v[0] * qs, v[1] * qs), amma::h2(v[2] * qs, v[3] * qs),
+                                amma::h2(v[4] * qs, v[5] * qs), amma::h2(v[6] * qs, v[7] * qs));
+            dst[1] = make_uint4(amma::h2(v[8] * qs, v[9] * qs), amma::h2(v[10] * qs, v[11] * qs),
+                                amma::h2(v[12] * qs, v[13] * qs), amma::h2(v[14] * qs, v[15] * qs));
           }
           tmem_ld16(c.tmem + lane_addr + D + half * DH + j, v);
+          scale16(v, fk);
           if (valid) {
             uint4 *dst = reinterpret_cast<uint4 *>(Kh + row * G::LDH + half * DH + j);
             dst[0] = make_uint4(amma::h2(v[0], v[1]), amma::h2(v[2], v[3]), amma::h2(v[4], v[5]), amma::h2(v[6], v[7]));
@@ -244,6 +360,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
                                 amma::h2(v[14], v[15]));
           }
           tmem_ld16(c.tmem + lane_addr + 2 * D + half * DH + j, v);
+          scale16(v, fv);
           if (n == 16) {   // full sequences: V row-major like K (the attention reads it by ldmatrix.trans)
             uint4 *dst = reinterpret_cast<uint4 *>(Vt + row * G::LDH + half * DH + j);
             dst[0] = make_uint4(amma::h2(v[0], v[1]), amma::h2(v[2], v[3]), amma::h2(v[4], v[5]), amma::h2(v[6], v[7]));
@@ -261,7 +378,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
           Vt[f * G::LDT + 16 * (r / (16 - n)) + n + r % (16 - n)] = __float2half_rn(0.f);
         }
       for (int idx = threadIdx.x; idx < (kRows - ts * n) * (D / 8); idx += kThreads)   // padding rows: O = 0
-        *reinterpret_cast<uint4 *>(A + canon(ts * n + idx / (D / 8), 8 * (idx % (D / 8)), D)) = make_uint4(0, 0, 0, 0);
+        zero_row8(A, ts * n + idx / (D / 8), 8 * (idx % (D / 8)), D);
       __syncthreads();
       auto units = [&](auto full) {
         constexpr int H = D / HD;   // heads (d_model = heads x head dimension)
@@ -271,9 +388,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
           amma::attn_fwd_h<HD, FULL>(
               Qh + rb * G::LDH + h * HD, Kh + rb * G::LDH + h * HD,
               FULL ? Vt + rb * G::LDH + h * HD : Vt + h * HD * G::LDT + 16 * sq, G::LDH, FULL ? G::LDH : G::LDT, n,
-              [&](int r, int cc, float v0, float v1) {
-                *reinterpret_cast<uint32_t *>(A + canon(rb + r, h * HD + cc, D)) = pack16<kF16>(v0, v1);
-              });
+              [&](int r, int cc, float v0, float v1) { put_pair(A, rb + r, h * HD + cc, D, v0, v1, so); });
         }
       };
       if (n == 16) units(std::true_type{});
@@ -289,12 +404,13 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
         tmem_ld16(c.tmem + lane_addr + half * DH + j, v);
         if (valid) {
           uint4 *dst = reinterpret_cast<uint4 *>(Ql + row * G::LDH + half * DH + j);
-          dst[0] = make_uint4(amma::h2(v[0] * qscale, v[1] * qscale), amma::h2(v[2] * qscale, v[3] * qscale),
-                              amma::h2(v[4] * qscale, v[5] * qscale), amma::h2(v[6] * qscale, v[7] * qscale));
-          dst[1] = make_uint4(amma::h2(v[8] * qscale, v[9] * qscale), amma::h2(v[10] * qscale, v[11] * qscale),
-                              amma::h2(v[12] * qscale, v[13] * qscale), amma::h2(v[14] * qscale, v[15] * qscale));
+          dst[0] = make_uint4(amma::h2(v[0] * qs, v[1] * qs), amma::h2(v[2] * qs, v[3] * qs),
+                              amma::h2(v[4] * qs, v[5] * qs), amma::h2(v[6] * qs, v[7] * qs));
+          dst[1] = make_uint4(amma::h2(v[8] * qs, v[9] * qs), amma::h2(v[10] * qs, v[11] * qs),
+                              amma::h2(v[12] * qs, v[13] * qs), amma::h2(v[14] * qs, v[15] * qs));
         }
         tmem_ld16(c.tmem + lane_addr + D + half * DH + j, v);
+        scale16(v, fk);
         if (valid) {
           uint4 *dst = reinterpret_cast<uint4 *>(Kl + row * G::LDH + half * DH + j);
           dst[0] = make_uint4(amma::h2(v[0], v[1]), amma::h2(v[2], v[3]), amma::h2(v[4], v[5]), amma::h2(v[6], v[7]));
@@ -302,6 +418,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
                               amma::h2(v[14], v[15]));
         }
         tmem_ld16(c.tmem + lane_addr + 2 * D + half * DH + j, v);
+        scale16(v, fv);
         if (valid) {
           uint4 *dst = reinterpret_cast<uint4 *>(Vl + row * G::LDH + half * DH + j);
           dst[0] = make_uint4(amma::h2(v[0], v[1]), amma::h2(v[2], v[3]), amma::h2(v[4], v[5]), amma::h2(v[6], v[7]));
@@ -318,15 +435,14 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
         }
       }
       for (int idx = threadIdx.x; idx < (kRows - ts * n) * (D / 8); idx += kThreads)   // padding rows: O = 0
-        *reinterpret_cast<uint4 *>(A + canon(ts * n + idx / (D / 8), 8 * (idx % (D / 8)), D)) = make_uint4(0, 0, 0, 0);
+        zero_row8(A, ts * n + idx / (D / 8), 8 * (idx % (D / 8)), D);
       __syncthreads();
       constexpr int H = D / HD;
       for (int u = warp; u < ts * H * 2; u += kThreads / 32) {
         const int sq = u / (2 * H), h = (u >> 1) % H, qb = u & 1, rb = sq * n;
         amma::attn_fwd_h32<HD>(Ql + rb * G::LDH + h * HD, Kl + rb * G::LDH + h * HD, Vl + rb * G::LDH + h * HD,
                                G::LDH, n, 16 * qb, [&](int r, int cc, float v0, float v1) {
-                                 *reinterpret_cast<uint32_t *>(A + canon(rb + r, h * HD + cc, D)) =
-                                     pack16<kF16>(v0, v1);
+                                 put_pair(A, rb + r, h * HD + cc, D, v0, v1, so);
                                });
       }
     } else {
@@ -335,9 +451,11 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
     for (int j = 0; j < DH; j += 16) {
       float v[16];
       tmem_ld16(c.tmem + lane_addr + D + half * DH + j, v);
+      scale16(v, fk);
 #pragma unroll
       for (int e = 0; e < 16; ++e) Ks[row * KS + half * DH + j + e] = v[e];
       tmem_ld16(c.tmem + lane_addr + 2 * D + half * DH + j, v);
+      scale16(v, fv);
 #pragma unroll
       for (int e = 0; e < 16; ++e) Vs[row * KS + half * DH + j + e] = v[e];
     }
@@ -354,7 +472,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
           for (int e8 = 0; e8 < HD; e8 += 8) {
             tmem_ld8(c.tmem + lane_addr + h * HD + e8, t8);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) q[e8 + e] = t8[e] * qscale;
+            for (int e = 0; e < 8; ++e) q[e8 + e] = t8[e] * qs;
           }
         }
 #pragma unroll
@@ -385,7 +503,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
           for (int e = 0; e < HD; ++e) o[e] *= inv;
         }
 #pragma unroll
-        for (int e8 = 0; e8 < HD; e8 += 8) st_row8<kF16>(A, row, h * HD + e8, D, o + e8);
+        for (int e8 = 0; e8 < HD; e8 += 8) put_row8(A, row, h * HD + e8, D, o + e8, so);
       }
     }
     }
@@ -397,20 +515,25 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
     ok = wait_mma(c);
     if (sync_fail(c, ok)) return false;
     const bool mlp = m.ffn > 0;
-    if (mlp) stage_w(c, w_addr, mb.W1[l], G::HC * D * 2);
-    else if (l + 1 < m.layers) stage_w(c, w_addr, mb.Wqkv[l + 1], 3 * D * D * 2);
+    if (mlp) stage_w(c, w_addr, mb.W1[l], G::HC * D * kEB);
+    else if (l + 1 < m.layers) stage_w(c, w_addr, mb.Wqkv[l + 1], 3 * D * D * kEB);
     // X += attention block output
+    const float fo = kF8 ? __ldg(wsc + 3) / so : 1.f;
 #pragma unroll
     for (int j = 0; j < DH; j += 16) {
       float v[16];
       tmem_ld16(c.tmem + lane_addr + half * DH + j, v);
+      scale16(v, fo);
 #pragma unroll
       for (int e = 0; e < 16; ++e) X[j + e] += v[e];
     }
-#pragma unroll
-    for (int j = 0; j < DH; j += 8) st_row8<kF16>(A, row, half * DH + j, D, X + j);
+    put_x();
     if (mlp) {
       const int nch = m.ffn / G::HC;
+      // E4M3: U's dequantisation, and 1 / the scale of each hidden chunk's image (at most two chunks: the
+      // chunks' W2 products sit in their own TMEM columns HC + ch D, so that no sum mixes scales)
+      const float f1 = kF8 ? ia * __ldg(wsc + 4) : 1.f;
+      float ig0 = 1.f, ig1 = 1.f;
       for (int ch = 0; ch < nch; ++ch) {
         tc_fence_before();
         fence_proxy_async();
@@ -421,9 +544,33 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
           park_image<D>(A, store->Xmid + ((size_t)l * store->tiles + tile) * (size_t)G::A_BYTES);
         ok = wait_mma(c);
         if (sync_fail(c, ok)) return false;
-        stage_w(c, w_addr, mb.W2[l] + (size_t)ch * G::HC * D, G::HC * D * 2);
-        // GELU(U + b1) -> G (FP16, packed half2 arithmetic), this thread's half of the chunk columns
+        stage_w(c, w_addr, wchunk(mb.W2[l], (size_t)ch * G::HC * D), G::HC * D * kEB);
         constexpr int HH = G::HC / 2;
+        if constexpr (kF8) {   // GELU(U + b1) in FP32 -> G (E4M3), scaled from max |U + b1| (|GELU(u)| <= max(|u|, 0.17))
+          float amx = 0.f;
+#pragma unroll
+          for (int j = 0; j < HH; j += 16) {
+            float v[16];
+            tmem_ld16(c.tmem + lane_addr + half * HH + j, v);
+            const float *b1 = m.L[l].b1 + ch * G::HC + half * HH + j;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) amx = fmaxf(amx, fabsf(fmaf(v[e], f1, __ldg(b1 + e))));
+          }
+          const float sg = tile_scale(fmaxf(amx, 0.17f), red, rpar);
+          if (ch == 0) ig0 = 1.f / sg;
+          else ig1 = 1.f / sg;
+#pragma unroll
+          for (int j = 0; j < HH; j += 16) {
+            float v[16];
+            tmem_ld16(c.tmem + lane_addr + half * HH + j, v);
+            const float *b1 = m.L[l].b1 + ch * G::HC + half * HH + j;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = gelu_fast(fmaf(v[e], f1, __ldg(b1 + e)));
+            put_row8(Gs, row, half * HH + j, G::HC, v, sg);
+            put_row8(Gs, row, half * HH + j + 8, G::HC, v + 8, sg);
+          }
+        } else {
+        // GELU(U + b1) -> G (FP16, packed half2 arithmetic), this thread's half of the chunk columns
 #pragma unroll
         for (int j = 0; j < HH; j += 16) {
           float v[16];
@@ -439,21 +586,33 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
                            gelu_h2(amma::h2(w[4] + bb.x, w[5] + bb.y)), gelu_h2(amma::h2(w[6] + bb.z, w[7] + bb.w)));
           }
         }
+        }
         tc_fence_before();
         fence_proxy_async();
         ok = wait_w(c);
         if (sync_fail(c, ok)) return false;
-        gemm(c, g_addr, w_addr, G::HC, D, G::HC, ch > 0, true);      // out -> cols [HC, HC + D), FP16
+        if constexpr (kF8) gemm(c, g_addr, w_addr, G::HC, D, G::HC + ch * D, false);   // chunk ch's own columns
+        else gemm(c, g_addr, w_addr, G::HC, D, G::HC, ch > 0, true);      // out -> cols [HC, HC + D), FP16
         ok = wait_mma(c);
         if (sync_fail(c, ok)) return false;
-        if (ch + 1 < nch) stage_w(c, w_addr, mb.W1[l] + (size_t)(ch + 1) * G::HC * D, G::HC * D * 2);
-        else if (l + 1 < m.layers) stage_w(c, w_addr, mb.Wqkv[l + 1], 3 * D * D * 2);
+        if (ch + 1 < nch) stage_w(c, w_addr, wchunk(mb.W1[l], (size_t)(ch + 1) * G::HC * D), G::HC * D * kEB);
+        else if (l + 1 < m.layers) stage_w(c, w_addr, mb.Wqkv[l + 1], 3 * D * D * kEB);
       }
+      const float f2a = kF8 ? ig0 * __ldg(wsc + 5) : 1.f, f2b = kF8 ? ig1 * __ldg(wsc + 5) : 1.f;
       const float4 *b2 = reinterpret_cast<const float4 *>(m.L[l].b2 + half * DH);
 #pragma unroll
       for (int j = 0; j < DH; j += 16) {
         float v[16];
         tmem_ld16(c.tmem + lane_addr + G::HC + half * DH + j, v);
+        if constexpr (kF8) {
+          scale16(v, f2a);
+          if (nch > 1) {
+            float v2[16];
+            tmem_ld16(c.tmem + lane_addr + G::HC + D + half * DH + j, v2);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = fmaf(v2[e], f2b, v[e]);
+          }
+        }
 #pragma unroll
         for (int e = 0; e < 16; e += 4) {
           const float4 bq = __ldg(b2 + (j + e) / 4);
@@ -463,8 +622,7 @@ __device__ bool eval_tile(const DevModel &m, const DevModelBF16 &mb, uint8_t *sm
           X[j + e + 3] += v[e + 3] + bq.w;
         }
       }
-#pragma unroll
-      for (int j = 0; j < DH; j += 8) st_row8<kF16>(A, row, half * DH + j, D, X + j);
+      put_x();
     }
   }
   // ---------------- pooling, head, symmetrisation (FP32)
@@ -550,7 +708,7 @@ __device__ __forceinline__ void ctl_finish(Ctl &c) {
   }
 }
 
-#if !TDO_F16
+#if !TDO_F16 && !TDO_F8
 // Self-test of the bounded waits: the control block of the forward (its two mbarriers and its TMEM
 // allocation) with a spin limit given by the caller; the kernel waits for an MMA completion that nothing
 // will signal (no copy and no MMA is ever issued), so the wait gives up after `spin` polls, and the
@@ -717,10 +875,45 @@ __global__ void k_pack(const float *__restrict__ W, int ldw, int col0, int K, in
   else *reinterpret_cast<__nv_bfloat16 *>(dst + canon(n, k, K)) = __float2bfloat16_rn(w);
 }
 
+#if TDO_F8
+// Scale of one weight matrix (the K x N block W[k][col0 + n], row stride ldw) for E4M3: its largest
+// magnitude in [2^e, 2^(e+1)) gives s = 2^(7 - e); sc[0] = s, sinv[0] = 1 / s (1 for an all-zero block).
+__global__ void __launch_bounds__(256) k_wscale(const float *__restrict__ W, int ldw, int col0, int K, int N,
+                                                float *__restrict__ sc, float *__restrict__ sinv) {
+  __shared__ float red[8];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < K * N; i += 256) m = fmaxf(m, fabsf(W[(size_t)(i / N) * ldw + col0 + i % N]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+    float s = 1.f;
+    if (m >= 1.17549435e-38f) {
+      int f = 127 + 7 - ((int)((__float_as_uint(m) >> 23) & 0xffu) - 127);
+      f = f < 1 ? 1 : (f > 254 ? 254 : f);
+      s = __uint_as_float((uint32_t)f << 23);
+    }
+    sc[0] = s;
+    sinv[0] = 1.f / s;
+  }
+}
+// dst element (n, k) of the 8-bit canonical image of W^T ([N][K]) = E4M3(W[k][col0 + n] * sc[0]).
+__global__ void k_pack8(const float *__restrict__ W, int ldw, int col0, int K, int N, uint8_t *__restrict__ dst,
+                        const float *__restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * K) return;
+  const int n = i / K, k = i % K;
+  const uint16_t two = pack_e4m3(W[(size_t)k * ldw + col0 + n] * sc[0], 0.f);
+  dst[canon8(n, k, K)] = (uint8_t)(two & 0xffu);
+}
+#endif
+
 }  // namespace TDO_OPNS
 }  // namespace tdo
 
-#if !TDO_F16   // operand-independent
+#if !TDO_F16 && !TDO_F8   // operand-independent
 bool bf16_supported(const DevModel &m) {
   return (m.d == 64 || m.d == 32) && (m.dh == 8 || m.dh == 16) && m.heads % 2 == 0 && (m.ffn == 0 || m.ffn % (m.d * 4 < 128 ? m.d * 4 : 128) == 0) &&
          m.embed == 0;
@@ -730,11 +923,63 @@ size_t bf16_packed_bytes(const DevModel &m) {
   const size_t D = m.d, F = m.ffn;
   return (size_t)m.layers * (3 * D * D + D * D + 2 * F * D) * 2;
 }
+
+// E4M3 images (1 byte per weight), then per layer the six scales (q, k, v, o, w1, w2) and their inverses.
+size_t f8_packed_bytes(const DevModel &m) {
+  const size_t D = m.d, F = m.ffn;
+  return (size_t)m.layers * (3 * D * D + D * D + 2 * F * D) + (size_t)m.layers * 12 * sizeof(float) + 16;
+}
 #endif
 
 // Packs every layer's weights into dst and fills the device views.
 cudaError_t TDO_OPFN(launch_pack_bf16)(const DevModel &m, uint16_t *dst16, DevModelBF16 *views, cudaStream_t st) {
   using namespace tdo::TDO_OPNS;
+#if TDO_F8
+  {   // E4M3: every weight matrix with its own power-of-two scale (kernel k_wscale), then its image
+    uint8_t *dst = reinterpret_cast<uint8_t *>(dst16);
+    const int D = m.d, F = m.ffn;
+    const int HC = (4 * D < 128) ? 4 * D : 128;
+    size_t off = 0;
+    for (int l = 0; l < m.layers; ++l) off += (size_t)(3 * D * D + D * D + 2 * F * D);
+    off = (off + 15) / 16 * 16;
+    float *sc = reinterpret_cast<float *>(dst + off), *sinv = sc + 6 * m.layers;
+    views->wscale = sinv;
+    off = 0;
+    for (int l = 0; l < m.layers; ++l) {
+      const DevLayer &L = m.L[l];
+      float *s6 = sc + 6 * l, *i6 = sinv + 6 * l;
+      k_wscale<<<1, 256, 0, st>>>(L.Wq, D, 0, D, D, s6 + 0, i6 + 0);
+      k_wscale<<<1, 256, 0, st>>>(L.Wk, D, 0, D, D, s6 + 1, i6 + 1);
+      k_wscale<<<1, 256, 0, st>>>(L.Wv, D, 0, D, D, s6 + 2, i6 + 2);
+      k_wscale<<<1, 256, 0, st>>>(L.Wo, D, 0, D, D, s6 + 3, i6 + 3);
+      uint8_t *q = dst + off;
+      views->Wqkv[l] = reinterpret_cast<const uint16_t *>(q);
+      k_pack8<<<(D * D + 255) / 256, 256, 0, st>>>(L.Wq, D, 0, D, D, q, s6 + 0);
+      k_pack8<<<(D * D + 255) / 256, 256, 0, st>>>(L.Wk, D, 0, D, D, q + (size_t)D * D, s6 + 1);
+      k_pack8<<<(D * D + 255) / 256, 256, 0, st>>>(L.Wv, D, 0, D, D, q + (size_t)2 * D * D, s6 + 2);
+      off += (size_t)3 * D * D;
+      views->Wo[l] = reinterpret_cast<const uint16_t *>(dst + off);
+      k_pack8<<<(D * D + 255) / 256, 256, 0, st>>>(L.Wo, D, 0, D, D, dst + off, s6 + 3);
+      off += (size_t)D * D;
+      if (F > 0) {
+        k_wscale<<<1, 256, 0, st>>>(L.W1, F, 0, D, F, s6 + 4, i6 + 4);
+        k_wscale<<<1, 256, 0, st>>>(L.W2, D, 0, F, D, s6 + 5, i6 + 5);
+        views->W1[l] = reinterpret_cast<const uint16_t *>(dst + off);
+        for (int c = 0; c < F / HC; ++c)
+          k_pack8<<<(HC * D + 255) / 256, 256, 0, st>>>(L.W1, F, c * HC, D, HC, dst + off + (size_t)c * HC * D, s6 + 4);
+        off += (size_t)F * D;
+        views->W2[l] = reinterpret_cast<const uint16_t *>(dst + off);
+        for (int c = 0; c < F / HC; ++c)
+          k_pack8<<<(HC * D + 255) / 256, 256, 0, st>>>(L.W2 + (size_t)c * HC * D, D, 0, HC, D,
+                                                        dst + off + (size_t)c * HC * D, s6 + 5);
+        off += (size_t)F * D;
+      } else {
+        views->W1[l] = views->W2[l] = nullptr;
+      }
+    }
+    return cudaGetLastError();
+  }
+#endif
   uint8_t *dst = reinterpret_cast<uint8_t *>(dst16);
   const int D = m.d, F = m.ffn;
   const int HC = (4 * D < 128) ? 4 * D : 128;
@@ -820,7 +1065,7 @@ cudaError_t TDO_OPFN(launch_fwd_bf16_store)(const DevModel &m, const DevModelBF1
   return cudaErrorInvalidValue;
 }
 
-#if !TDO_F16
+#if !TDO_F16 && !TDO_F8
 cudaError_t launch_wait_probe(int *err_flag, long long spin, cudaStream_t st) {
   tdo::bf16::k_wait_probe<<<1, 128, 0, st>>>(err_flag, spin);
   return cudaGetLastError();

@@ -87,6 +87,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       : "memory");
 }
 
+// kind::f8f6f4 with A = B = E4M3 (format fields 0, the same bit pattern as idesc_f16), D = F32; one
+// instruction covers K = 32 (32 bytes of each operand row).
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) { return idesc_f16(M, N); }
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -175,6 +186,19 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // Byte offset of element (row, k) in a canonical K-major tile with K columns.
 __host__ __device__ __forceinline__ uint32_t canon(int row, int k, int K) {
   return (uint32_t)((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Byte offset of element (row, k) in a canonical K-major tile of 8-bit elements with K columns: core
+// matrices of 8 rows x 16 bytes (16 elements), 128 B apart along K, 8-row groups K * 8 bytes apart.
+__host__ __device__ __forceinline__ uint32_t canon8(int row, int k, int K) {
+  return (uint32_t)((row >> 3) * (K * 8) + (k >> 4) * 128 + (row & 7) * 16 + (k & 15));
+}
+
+// Two E4M3 values (round to nearest even, saturating to +-448): a at the lower address.
+__device__ __forceinline__ uint16_t pack_e4m3(float a, float b) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %2, %1;" : "=h"(r) : "f"(a), "f"(b));
+  return r;
 }
 
 __device__ __forceinline__ uint32_t pack_f16(float a, float b) {

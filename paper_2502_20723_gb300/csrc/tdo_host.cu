@@ -86,6 +86,9 @@ cudaError_t launch_fwd_bf16_store_f16(const DevModel &m, const DevModelBF16 &mb,
                                       size_t tiles);
 // A tensor-core launcher of the context's operand type: fn (BF16) or fn_f16 (FP16).
 #define TC_LAUNCH(c, fn, ...) ((c)->f16 ? fn##_f16(__VA_ARGS__) : fn(__VA_ARGS__))
+// Evaluation-only launches (no parked activations): the E4M3 kernels and weights in FP8 contexts.
+#define EVAL_LAUNCH(c, fn, ...) \
+  ((c)->f8 ? fn##_f8((c)->dm, (c)->dmb8, __VA_ARGS__) : TC_LAUNCH(c, fn, (c)->dm, (c)->dmb, __VA_ARGS__))
 
 namespace {
 
@@ -132,15 +135,17 @@ struct tdo_ctx {
   int n_pat = 0;
   DBuf d_pat, d_con;
   // parameters
-  DBuf theta64, theta32, etab, tensor_tab, wbf16, errflag, wbwd;
+  DBuf theta64, theta32, etab, tensor_tab, wbf16, errflag, wbwd, wf8;
   DBuf dtab;   // conv embedding: per-pattern table gradients
   DBuf oref, oref_scratch;   // BF16-stored O for SR: per-parameter shift and its FP32 sample
   DBuf jac_vs, jac_vp, jac_vc, jac_lr;   // tensor-core log-derivatives: virtual configurations
   DBuf obs_rs, obs_rp, obs_lr, obs_part, obs_out, obs_local;   // observables and purity
   DevModel dm{};
   DevModelBF16 dmb{};
-  bool tc = false;                     // tensor-core path (TDO_BF16 or TDO_FP16 contexts)
-  bool f16 = false;                    // its operands are FP16 (TDO_FP16) rather than BF16
+  DevModelBF16 dmb8{};                 // views of the E4M3 weights (TDO_FP8)
+  bool tc = false;                     // tensor-core path (TDO_BF16, TDO_FP16 or TDO_FP8 contexts)
+  bool f16 = false;                    // its operands are FP16 (TDO_FP16; TDO_FP8's gradient) rather than BF16
+  bool f8 = false;                     // TDO_FP8: evaluation on E4M3 operands (wf8, dmb8)
   bool tc_bwd = false;                 // tensor-core gradient (tensor-core contexts whose shape it supports)
   BwdTcLayer bwl[TDO_MAX_LAYERS];
   DBuf act_x, act_xmid, act_h, act_f, act_dF, act_dxa, act_dxb, act_dqkv;
@@ -232,7 +237,7 @@ static bool model_valid(const tdo_model *m, std::string *why) {
   if (m->mlp_ratio < 0 || m->mlp_ratio > 4) { *why = "mlp_ratio must be 0..4"; return false; }
   if (m->embed != TDO_EMBED_TOKEN && m->embed != TDO_EMBED_CONV) { *why = "unknown embedding"; return false; }
   if (m->embed == TDO_EMBED_CONV && (m->conv_channels < 1 || m->conv_channels > 256)) { *why = "conv_channels must be 1..256"; return false; }
-  if (m->precision != TDO_FP32 && m->precision != TDO_BF16 && m->precision != TDO_FP16) {
+  if (m->precision != TDO_FP32 && m->precision != TDO_BF16 && m->precision != TDO_FP16 && m->precision != TDO_FP8) {
     *why = "unknown precision";
     return false;
   }
@@ -435,6 +440,7 @@ static tdo_status refresh_params(tdo_ctx *c) {
                               b + c->tensors[2].pad, b + c->tensors[3].pad, c->etab.as<float>(), c->stream));
   }
   if (c->tc) CU(c, TC_LAUNCH(c, launch_pack_bf16, c->dm, c->wbf16.as<uint16_t>(), &c->dmb, c->stream));
+  if (c->f8) CU(c, launch_pack_bf16_f8(c->dm, c->wf8.as<uint16_t>(), &c->dmb8, c->stream));
   if (c->tc_bwd) CU(c, TC_LAUNCH(c, launch_pack_bwdtc, c->dm, c->wbwd.as<uint8_t>(), c->bwl, c->stream));
   return TDO_OK;
 }
@@ -509,8 +515,9 @@ extern "C" tdo_status tdo_create(const tdo_problem *problem, const tdo_model *mo
 
   tdo_ctx *c = new tdo_ctx();
   c->model = *model;
-  c->tc = model->precision == TDO_BF16 || model->precision == TDO_FP16;
-  c->f16 = model->precision == TDO_FP16;
+  c->tc = model->precision == TDO_BF16 || model->precision == TDO_FP16 || model->precision == TDO_FP8;
+  c->f16 = model->precision == TDO_FP16 || model->precision == TDO_FP8;
+  c->f8 = model->precision == TDO_FP8;
   c->n = problem->n_sites;
   c->stream = (cudaStream_t)stream;
   auto bail = [&](tdo_status s) {
@@ -549,6 +556,7 @@ extern "C" tdo_status tdo_create(const tdo_problem *problem, const tdo_model *mo
       return bail(TDO_EUNSUPPORTED);
     }
     if ((e = c->wbf16.ensure(bf16_packed_bytes(c->dm))) != cudaSuccess ||
+        (c->f8 && (e = c->wf8.ensure(f8_packed_bytes(c->dm))) != cudaSuccess) ||
         (e = c->cscale.ensure(2 * sizeof(float))) != cudaSuccess ||
         (e = c->errflag.ensure(sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(c->errflag.p, 0, sizeof(int))) != cudaSuccess) {
@@ -574,7 +582,7 @@ extern "C" tdo_status tdo_destroy(tdo_ctx *c) {
                   &c->stage_in[1], &c->stage_in[2], &c->stage_in[3], &c->stage_out, &c->conn_cnt, &c->conn_sig,
                   &c->conn_sigp, &c->conn_coef, &c->offs, &c->fsig, &c->fsigp, &c->fcoef, &c->flr, &c->lloc,
                   &c->l2, &c->stats, &c->nonfinite, &c->cot, &c->gacc, &c->scratch, &c->grad, &c->Obuf,
-                  &c->srwork, &c->delta, &c->acc_u64, &c->wbf16, &c->errflag, &c->wbwd, &c->act_x, &c->act_xmid,
+                  &c->srwork, &c->delta, &c->acc_u64, &c->wbf16, &c->wf8, &c->errflag, &c->wbwd, &c->act_x, &c->act_xmid,
                   &c->act_h, &c->act_f, &c->act_dF, &c->act_dxa, &c->act_dxb, &c->act_dqkv, &c->dtab,
                   &c->oref, &c->oref_scratch, &c->jac_vs, &c->jac_vp, &c->jac_vc, &c->jac_lr, &c->obs_rs,
                   &c->obs_rp, &c->obs_lr, &c->obs_part, &c->obs_out, &c->obs_local};
@@ -613,7 +621,7 @@ static tdo_status forward_dev(tdo_ctx *c, const uint32_t *sig, const uint32_t *s
   if (B == 0) return TDO_OK;
   Timed tm(c, G_FWD);
   if (c->tc)
-    CU(c, TC_LAUNCH(c, launch_fwd_bf16, c->dm, c->dmb, sig, sigp, B, out, c->errflag.as<int>(), c->n_sm, c->stream));
+    CU(c, EVAL_LAUNCH(c, launch_fwd_bf16, sig, sigp, B, out, c->errflag.as<int>(), c->n_sm, c->stream));
   else
     CU(c, launch_fwd32(c->dm, sig, sigp, B, out, c->n_sm, c->stream));
   return TDO_OK;
@@ -709,7 +717,7 @@ static tdo_status ragged_dev(tdo_ctx *c, const int32_t *dn, const uint32_t *ds, 
   };
   auto launch = [&](const std::array<int, 3> &cfg) -> cudaError_t {
     const RaggedTab t = table(cfg[1] != 0);
-    return TC_LAUNCH(c, launch_fwd_ragged, c->dm, c->dmb, ss, sp, perm, t,
+    return EVAL_LAUNCH(c, launch_fwd_ragged, ss, sp, perm, t,
                      cfg[2] ? c->rg_next.as<unsigned long long>() : nullptr, out, c->errflag.as<int>(), c->n_sm,
                      cfg[0], c->stream);
   };
@@ -1279,7 +1287,7 @@ static tdo_status sample_impl(tdo_ctx *c, size_t n_chains, size_t n_sweeps, uint
   CU(c, cudaMemsetAsync(c->acc_u64.p, 0, sizeof(unsigned long long), c->stream));
   Timed tm(c, G_SAMPLE);
   if (c->tc)
-    CU(c, TC_LAUNCH(c, launch_sample_bf16, c->dm, c->dmb, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
+    CU(c, EVAL_LAUNCH(c, launch_sample_bf16, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
                     c->acc_u64.as<unsigned long long>(), c->errflag.as<int>(), diag, c->n_sm, c->stream));
   else
     CU(c, launch_sample32(c->dm, n_chains, n_sweeps, seed, counter, dsig, dsigp, dss, dsp,
@@ -1619,7 +1627,7 @@ extern "C" tdo_status tdo_local_estimator_noalloc(tdo_ctx *c, const uint32_t *si
   CU(c, cudaStreamSynchronize(c->stream));
   CU(c, launch_compact(cnt, offs, Ns, M, csig, csigp, ccoef, fsig, fsigp, fcoef, c->stream));
   if (c->tc)
-    CU(c, TC_LAUNCH(c, launch_fwd_bf16, c->dm, c->dmb, fsig, fsigp, (size_t)total, flr, c->errflag.as<int>(), c->n_sm,
+    CU(c, EVAL_LAUNCH(c, launch_fwd_bf16, fsig, fsigp, (size_t)total, flr, c->errflag.as<int>(), c->n_sm,
                     c->stream));
   else
     CU(c, launch_fwd32(c->dm, fsig, fsigp, (size_t)total, flr, c->n_sm, c->stream));

@@ -33,6 +33,7 @@ struct DevModelBF16 {
   const uint16_t *Wo[TDO_MAX_LAYERS];     // d x d
   const uint16_t *W1[TDO_MAX_LAYERS];     // f x d
   const uint16_t *W2[TDO_MAX_LAYERS];     // d x f
+  const float *wscale;                    // E4M3 images only: [layers][6] inverse scales (q, k, v, o, w1, w2)
 };
 
 // One contribution to an element of a row of Lhat: for the row (s, s') and the connected configuration
@@ -139,6 +140,21 @@ cudaError_t launch_f64_to_f32(const double *src, float *dst, size_t n, cudaStrea
 // 16-bit weight packing (BF16 operands; the _f16 variant packs FP16 operands).
 cudaError_t launch_pack_bf16(const DevModel &m, uint16_t *dst, DevModelBF16 *views, cudaStream_t st);
 cudaError_t launch_pack_bf16_f16(const DevModel &m, uint16_t *dst, DevModelBF16 *views, cudaStream_t st);
+
+// E4M3 (FP8) forward for evaluation: the same kernels with 8-bit operand images, per-matrix weight scales and
+// per-tile activation scales; dst of the packing holds f8_packed_bytes(m) bytes.
+size_t f8_packed_bytes(const DevModel &m);
+cudaError_t launch_pack_bf16_f8(const DevModel &m, uint16_t *dst, DevModelBF16 *views, cudaStream_t st);
+cudaError_t launch_fwd_bf16_f8(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig, const uint32_t *sigp,
+                               size_t B, float2 *logrho, int *err_flag, int n_sm, cudaStream_t st);
+cudaError_t launch_fwd_ragged_f8(const DevModel &m, const DevModelBF16 &mb, const uint32_t *ssig,
+                                 const uint32_t *ssigp, const uint32_t *perm, const RaggedTab &tab,
+                                 unsigned long long *next, float2 *out, int *err_flag, int n_sm, int ctas_per_sm_req,
+                                 cudaStream_t st);
+cudaError_t launch_sample_bf16_f8(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
+                                  uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
+                                  uint32_t *ssigp, unsigned long long *accepted, int *err_flag, int diag, int n_sm,
+                                  cudaStream_t st);
 
 cudaError_t launch_axpy_update(double *theta, const double *delta, double lr, size_t P, cudaStream_t st);
 // Adam step t (>= 1) on the direction delta with first and second moments m, v (FP64 [P], updated).

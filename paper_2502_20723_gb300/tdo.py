@@ -15,8 +15,8 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtdo.so")
 
 TDO_EMBED_TOKEN, TDO_EMBED_CONV = 0, 1
-TDO_FP32, TDO_BF16, TDO_FP16 = 0, 1, 2
-PRECISIONS = {"fp32": TDO_FP32, "bf16": TDO_BF16, "fp16": TDO_FP16}
+TDO_FP32, TDO_BF16, TDO_FP16, TDO_FP8 = 0, 1, 2, 3
+PRECISIONS = {"fp32": TDO_FP32, "bf16": TDO_BF16, "fp16": TDO_FP16, "fp8": TDO_FP8}
 STATUS = {0: "TDO_OK", -1: "TDO_EINVAL", -2: "TDO_ENOMEM", -3: "TDO_ECUDA", -4: "TDO_ENUMERIC",
           -5: "TDO_ETIMEOUT", -6: "TDO_EUNSUPPORTED"}
 

@@ -1,6 +1,7 @@
 // Test-only kernel: one tcgen05.mma chain D[128 x N] = A[128 x 128] . B[N x 128]^T on operands whose
 // shared-memory byte images are prepared by the host, to pin the descriptor fields of K-major and
-// MN-major operands.  All reads stay inside zero-filled 96 KB regions (any LBO/SBO reading of the
+// MN-major operands: kind::f16 with BF16 operands (8 MMAs of K = 16), or, with f8 set, kind::f8f6f4
+// with E4M3 operands in 8-bit K-major images (4 MMAs of K = 32).  All reads stay inside zero-filled 96 KB regions (any LBO/SBO reading of the
 // fields keeps the MMA's addresses below 62 KB from the region start).
 #include <stdint.h>
 
@@ -13,7 +14,7 @@ constexpr int kRegion = 96 * 1024;
 extern "C" __global__ void __launch_bounds__(128, 1)
     umma_probe(const uint8_t *a_img, int a_bytes, const uint8_t *b_img, int b_bytes, int N, int a_mn, int b_mn,
                uint32_t a_lbo, uint32_t a_sbo, uint32_t a_step, uint32_t b_lbo, uint32_t b_sbo, uint32_t b_step,
-               float *D, int *err) {
+               int f8, float *D, int *err) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t holder;
@@ -38,12 +39,13 @@ extern "C" __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = holder;
   if (threadIdx.x == 0) {
-    const uint32_t id = idesc_bf16_major(128, N, a_mn, b_mn);
+    const uint32_t id = f8 ? idesc_e4m3(128, N) : idesc_bf16_major(128, N, a_mn, b_mn);
     const uint32_t a0 = smem_u32(sm), b0 = smem_u32(sm + kRegion);
-    for (int kk = 0; kk < 8; ++kk) {
+    for (int kk = 0; kk < (f8 ? 4 : 8); ++kk) {
       const uint64_t ad = sdesc(a0 + kk * a_step, a_lbo, a_sbo);
       const uint64_t bd = sdesc(b0 + kk * b_step, b_lbo, b_sbo);
-      mma_bf16(tmem, ad, bd, id, kk > 0 ? 1u : 0u);
+      if (f8) mma_e4m3(tmem, ad, bd, id, kk > 0 ? 1u : 0u);
+      else mma_bf16(tmem, ad, bd, id, kk > 0 ? 1u : 0u);
     }
     mma_commit(bar_a);
   }
@@ -70,12 +72,12 @@ extern "C" __global__ void __launch_bounds__(128, 1)
 // Host launcher (C ABI) for the test: device buffers in, D [128 x N] device out.
 extern "C" int umma_probe_run(const uint8_t *a_img, int a_bytes, const uint8_t *b_img, int b_bytes, int N, int a_mn,
                               int b_mn, uint32_t a_lbo, uint32_t a_sbo, uint32_t a_step, uint32_t b_lbo,
-                              uint32_t b_sbo, uint32_t b_step, float *D, int *err) {
+                              uint32_t b_sbo, uint32_t b_step, int f8, float *D, int *err) {
   const int bytes = 2 * kRegion;
   cudaError_t e = cudaFuncSetAttribute(umma_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return (int)e;
   umma_probe<<<1, 128, bytes>>>(a_img, a_bytes, b_img, b_bytes, N, a_mn, b_mn, a_lbo, a_sbo, a_step, b_lbo, b_sbo,
-                                b_step, D, err);
+                                b_step, f8, D, err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
   return (int)cudaDeviceSynchronize();
