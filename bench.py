@@ -199,21 +199,35 @@ def run_ours(args) -> dict | None:
                "subset": ((sig[:SET_ERROR_SAMPLES].cpu().numpy().astype(np.int64) & 0xFFFFFFFF).astype(np.uint32),
                           (sigp[:SET_ERROR_SAMPLES].cpu().numpy().astype(np.int64) & 0xFFFFFFFF).astype(np.uint32))}
         if e2e:
-            # end to end through the public API with host buffers (copies inside the timed region)
+            # end to end through the public API with host buffers (copies inside the timed region), on the
+            # same trajectory as the timed steps: a fresh context from the same parameters and chains, the
+            # same burn-in and warm-up, then the same `steps` steps with the chains in pinned host memory
+            ctx.close()
+            ctx = tdo.Context(prob, spec, theta, precision, stream=stream.cuda_stream)
+            sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
+            sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
+            counter[0] = 0
+            ctx.sample(sig, sigp, args.burn_in, seed, counter[0])
+            counter[0] += args.burn_in * 2 * N_SITES
+            for _ in range(warmup):
+                step()
             hs = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
             hp = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
             hs.copy_(sig.cpu())
             hp.copy_(sigp.cpu())
             hs_np, hp_np = hs.numpy(), hp.numpy()
             torch.cuda.synchronize()
-            n_e2e = max(1, min(steps, 5))
+            e2e_costs = []
             t0 = time.perf_counter()
-            for _ in range(n_e2e):
+            for _ in range(steps):
+                flush.zero_()
                 ctx.sample(hs_np, hp_np, 1, seed, counter[0])          # H2D chains, D2H chains
                 counter[0] += 2 * N_SITES
-                ctx.sr_step(hs_np, hp_np, LR, SHIFT)                   # H2D samples, D2H cost
+                e2e_costs.append(ctx.sr_step(hs_np, hp_np, LR, SHIFT))  # H2D samples, D2H cost
             torch.cuda.synchronize()
-            out["e2e_steps_per_s"] = replicas_rate(world, n_e2e, max_over_ranks(time.perf_counter() - t0, world))
+            out["e2e_steps_per_s"] = replicas_rate(world, steps, max_over_ranks(time.perf_counter() - t0, world))
+            # the same steps up to the order of float atomics in the gradient sums
+            out["e2e_cost_max_rel_diff"] = float(np.max(np.abs(np.array(e2e_costs) - np.array(costs)) / np.abs(costs)))
         ctx.close()
         return out
 
@@ -316,7 +330,9 @@ def run_ours(args) -> dict | None:
         "peaks_measured_here": {"fp32_fma_tflops": peak_fp32, "fp64_fma_tflops": peak_fp64},
         "clocks": clk_summary,
         "e2e": {"value": main["e2e_steps_per_s"], "unit": "VMC steps/s",
-                "h2d_bytes_per_step": 4 * 4 * N_SAMPLES, "d2h_bytes_per_step": 2 * 4 * N_SAMPLES + 8},
+                "h2d_bytes_per_step": 4 * 4 * N_SAMPLES, "d2h_bytes_per_step": 2 * 4 * N_SAMPLES + 8,
+                "steps": args.steps, "trajectory": "the timed steps replayed from the same parameters and chains",
+                "cost_max_rel_diff_vs_timed_steps": main["e2e_cost_max_rel_diff"]},
         "gpu_launches": launches,
     }
     res["compare"] = {}

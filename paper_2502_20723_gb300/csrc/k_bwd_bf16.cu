@@ -173,6 +173,27 @@ __device__ __forceinline__ float gelu_grad_fast(float u, float *g) {
   return 0.5f * (1.0f + t) + 0.5f * u * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * u * u);
 }
 
+// GELU (tanh form) and its derivative for a pair of FP16 values, in packed half2 arithmetic (two results
+// per instruction): g = (u / 2)(1 + t), g' = (1 + t) / 2 + (u / 2)(1 - t^2) k0 (1 + 3 k1 u^2), with
+// t = tanh(k0 (u + k1 u^3)).  The polynomial terms take u clamped to [-10, 10] (beyond it t = +-1 in FP16,
+// so g' is 0 or 1 and g is u or 0 from the unclamped u / 2), which keeps u^2 finite.  Returns g; *gp = g'.
+__device__ __forceinline__ __half2 gelu_grad_h2(__half2 u, __half2 *gp) {
+  const __half2 k0 = __float2half2_rn(0.7978845608028654f), k1 = __float2half2_rn(0.044715f);
+  const __half2 k13 = __float2half2_rn(3.0f * 0.044715f), one = __float2half2_rn(1.0f), hf = __float2half2_rn(0.5f);
+  const __half2 lim = __float2half2_rn(10.0f), nlim = __float2half2_rn(-10.0f);
+  const __half2 uc = __hmin2(__hmax2(u, nlim), lim);
+  const __half2 u2 = __hmul2(uc, uc);
+  const __half2 arg = __hmul2(__hmul2(uc, __hfma2(u2, k1, one)), k0);
+  uint32_t tb;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(tb) : "r"(*reinterpret_cast<const uint32_t *>(&arg)));
+  const __half2 t = *reinterpret_cast<const __half2 *>(&tb);
+  const __half2 opt = __hadd2(one, t);
+  const __half2 omt2 = __hfma2(__hneg2(t), t, one);
+  const __half2 q = __hmul2(__hmul2(__hmul2(uc, hf), omt2), __hmul2(__hfma2(u2, k13, one), k0));
+  *gp = __hfma2(hf, opt, q);
+  return __hmul2(__hmul2(u, hf), opt);
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -631,17 +652,35 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       // dU = dG gelu'(U + b1), G = gelu(U + b1) -> shared images
 #pragma unroll
       for (int j = 0; j < QH; j += 16) {
-        float u[16], dg[16], gl[16], du[16];
+        float u[16], dg[16];
         tmem_ld16x2(s.tmem + lane_addr + G::C_U + cg * QH + j, u, s.tmem + lane_addr + G::C_DG + cg * QH + j, dg);
+        if constexpr (kF16) {   // FP16 images: GELU, GELU' and dU in packed half2 arithmetic
+          uint32_t gh[8], dh[8];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const float uu = u[e] + b1s[cg * QH + j + e];
-          du[e] = dg[e] * gelu_grad_fast(uu, &gl[e]);
+          for (int e = 0; e < 16; e += 2) {
+            const __half2 uu = __floats2half2_rn(u[e] + b1s[cg * QH + j + e], u[e + 1] + b1s[cg * QH + j + e + 1]);
+            __half2 gp;
+            const __half2 g = gelu_grad_h2(uu, &gp);
+            const __half2 d = __hmul2(__floats2half2_rn(dg[e], dg[e + 1]), gp);
+            gh[e / 2] = *reinterpret_cast<const uint32_t *>(&g);
+            dh[e / 2] = *reinterpret_cast<const uint32_t *>(&d);
+          }
+          *reinterpret_cast<uint4 *>(sm + G::G_OFF + canon(row, cg * QH + j, G::HC)) = make_uint4(gh[0], gh[1], gh[2], gh[3]);
+          *reinterpret_cast<uint4 *>(sm + G::G_OFF + canon(row, cg * QH + j + 8, G::HC)) = make_uint4(gh[4], gh[5], gh[6], gh[7]);
+          *reinterpret_cast<uint4 *>(sm + G::DU_OFF + canon(row, cg * QH + j, G::HC)) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
+          *reinterpret_cast<uint4 *>(sm + G::DU_OFF + canon(row, cg * QH + j + 8, G::HC)) = make_uint4(dh[4], dh[5], dh[6], dh[7]);
+        } else {
+          float gl[16], du[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float uu = u[e] + b1s[cg * QH + j + e];
+            du[e] = dg[e] * gelu_grad_fast(uu, &gl[e]);
+          }
+          st_row8<kF16>(sm + G::G_OFF, row, cg * QH + j, G::HC, gl);
+          st_row8<kF16>(sm + G::G_OFF, row, cg * QH + j + 8, G::HC, gl + 8);
+          st_row8<kF16>(sm + G::DU_OFF, row, cg * QH + j, G::HC, du);
+          st_row8<kF16>(sm + G::DU_OFF, row, cg * QH + j + 8, G::HC, du + 8);
         }
-        st_row8<kF16>(sm + G::G_OFF, row, cg * QH + j, G::HC, gl);
-        st_row8<kF16>(sm + G::G_OFF, row, cg * QH + j + 8, G::HC, gl + 8);
-        st_row8<kF16>(sm + G::DU_OFF, row, cg * QH + j, G::HC, du);
-        st_row8<kF16>(sm + G::DU_OFF, row, cg * QH + j + 8, G::HC, du + 8);
       }
       tc_fence_before();
       fence_proxy_async();
