@@ -22,6 +22,8 @@ at the run's final parameters against it).
 from __future__ import annotations
 
 import argparse
+import re
+import hashlib
 import json
 import os
 import statistics
@@ -290,9 +292,14 @@ def run_ours(args) -> dict | None:
     ob = 8 if args.precision == "fp32" else 4   # tensor-core contexts store O - obar as BF16 pairs
     byts = 2 * N_SAMPLES * P * ob
     ach = byts * mv["launches"] / (mv["ms"] * 1e-3) / 1e9 if mv["ms"] else 0.0
+    traffic, traffic_src = None, None
+    if args.precision != "fp32":   # the capture is of the BF16-pair passes
+        per_row, traffic_src = sr_traffic_per_row()
+        traffic = per_row * N_SAMPLES if per_row else None
     rooflines["sr_mv"] = {"bound": "hbm", "kernel": "S' v product (k_sr_tpart + k_sr_wpart and reductions)",
                           "group": "sr_mv", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                          "traffic": None, "algorithmic_per_launch": byts, "o_element_bytes": ob,
+                          "traffic": traffic, "traffic_source": traffic_src,
+                          "algorithmic_per_launch": byts, "o_element_bytes": ob,
                           "products_per_step": mv["launches"], "ms_per_step": mv["ms"], "peak_source": hbm_src}
     # the headline roofline: the dominant kernel group of the timed steps
     dom_ms = {"fwd": groups["fwd"]["ms"], "bwd_vjp": groups["bwd_vjp"]["ms"], "sample": groups["sample"]["ms"],
@@ -451,6 +458,25 @@ def config5_leg(tdo, torch, stream, flush, reps: int = 5) -> dict:
 # ---------------------------------------------------------------------------------- oracle on the CPU
 SET_ERROR_SAMPLES = 256
 TOL_COST_REL_BF16 = 1e-3
+
+
+def sr_traffic_per_row():
+    """DRAM bytes per sample row of one S' v product from the committed ncu summary of the two passes,
+    valid only while the SR source has the SHA-1 recorded with that capture: (bytes or None, source)."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    prof = os.path.join(here, "profiles", "k_sr_tpart_wpart_ising_n16_d64_l4.md")
+    src = os.path.join(here, "paper_2502_20723_gb300", "csrc", "k_sr.cu")
+    try:
+        m = re.search(r"bench-traffic sr_mv: k_sr\.cu sha1=([0-9a-f]{40}) bytes_per_sample_row=(\d+)", open(prof).read())
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None, None
+    if not m:
+        return None, None
+    if m.group(1) != sha:
+        return None, "k_sr.cu changed since the ncu capture in profiles/: traffic not known"
+    return int(m.group(2)), ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_sr_tpart + k_sr_wpart on "
+                             "1024 samples, scaled by the samples (profiles/k_sr_tpart_wpart_ising_n16_d64_l4.md)")
 
 
 def set_error_report(gpu: dict, ref_l: np.ndarray, ref_c: float) -> dict:
