@@ -452,12 +452,63 @@ def config5_leg(tdo, torch, stream, flush, reps: int = 5) -> dict:
                         **{p: float(np.abs(ll[p] - ref).max() / np.abs(ref).max()) for p in ("fp16", "bf16", "fp8")}}
         err[f"weights N(0,{std})"] = per_n
     out["lloc_max_rel_vs_fp32"] = err
+    out["vmc"] = config5_vmc(tdo, torch, stream, spec, theta)
     return out
 
 
 # ---------------------------------------------------------------------------------- oracle on the CPU
 SET_ERROR_SAMPLES = 256
 TOL_COST_REL_BF16 = 1e-3
+
+
+def config5_vmc(tdo, torch, stream, spec, theta, steps: dict = None) -> dict:
+    """VMC steps of the N in {8, ..., 32} workload: each chain length is its own Lindbladian, so one step
+    is, for every N, one Metropolis sweep and one SR step (connections, L_loc, cost, gradient,
+    log-derivatives, CG solve, update) on that length's share of the 32,768 chains, in a context per N
+    with the same initial parameters.  Timed with CUDA events around the whole multi-length step after
+    warm-up steps, FP16 against FP32."""
+    steps = steps or {"fp16": (2, 3), "fp32": (1, 2)}   # (warm-up, timed)
+    per = CONFIG5_SAMPLES // len(CONFIG5_N)
+    out = {"definition": "one sweep + one SR step of every chain length N in {8,12,16,20,24,32}, "
+                         f"{per}-{per + CONFIG5_SAMPLES - per * len(CONFIG5_N)} chains each (32,768 in all)",
+           "lr": LR, "diag_shift": SHIFT}
+    for prec, (warm, timed) in steps.items():
+        ctxs, chains = [], []
+        for i, n in enumerate(CONFIG5_N):
+            k = per + (CONFIG5_SAMPLES - per * len(CONFIG5_N) if i == 0 else 0)
+            ctx = tdo.Context(synth.xyz_chain(n, Jx=0.9, Jy=1.0, Jz=1.0), spec, theta, prec, stream=stream.cuda_stream)
+            s0, s1 = synth.random_configs(n, k, seed=700 + n)
+            sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
+            sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
+            ctx.sample(sig, sigp, 2, 91 + n, 0)
+            ctxs.append(ctx)
+            chains.append([sig, sigp, 2 * 2 * n])
+        costs = []
+
+        def one_step():
+            c = []
+            for (ctx, ch), n in zip(zip(ctxs, chains), CONFIG5_N):
+                ctx.sample(ch[0], ch[1], 1, 91 + n, ch[2])
+                ch[2] += 2 * n
+                c.append(ctx.sr_step(ch[0], ch[1], LR, SHIFT))
+            return c
+
+        for _ in range(warm):
+            one_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(timed):
+            costs.append(one_step())
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / timed
+        out[prec] = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "warmup": warm, "steps": timed,
+                     "costs_last_step": dict(zip((str(n) for n in CONFIG5_N), (round(x, 5) for x in costs[-1])))}
+        for ctx in ctxs:
+            ctx.close()
+    out["speedup_fp16_over_fp32"] = out["fp16"]["steps_per_s"] / out["fp32"]["steps_per_s"]
+    return out
 
 
 def sr_traffic_per_row():

@@ -1,6 +1,6 @@
 // Softmax attention of one (sequence, head) pair on one warp with warp-level tensor-core MMAs
-// (mma.sync m16n8k16 / m16n8k8, FP16 operands, FP32 accumulation), for sequences of at most 16
-// tokens and head dimension HD in {8, 16} (Eq. attn-head-appendix and its derivative).
+// (mma.sync m16n8k16 / m16n8k8, FP16 operands, FP32 accumulation), for sequences of at most 32
+// tokens (16-query blocks) and head dimension HD in {8, 16} (Eq. attn-head-appendix and its derivative).
 //
 // A 16 x 16 score block is 1/8 of one tcgen05 tile and lives in registers across the whole
 // forward-and-backward of the pair, so these blocks use the warp-synchronous MMA, while the
@@ -439,6 +439,198 @@ __device__ __forceinline__ void attn_fwd_bwd_h(uint32_t Qh, uint32_t Kh, uint32_
       if (q1) emit(3, g + 8, 8 * c + 2 * t, y[c][2], y[c][3]);
     }
   }
+}
+
+
+// Forward and backward of softmax attention for one (sequence, head) of 17 to 32 tokens on one warp, with
+// the operands of attn_fwd_bwd_h, readable 32 rows down from the sequence's first row (rows past the
+// sequence hold finite values).  The two 16-query blocks run one after the other; for each, the 16 x 32
+// score block is a row of four 8-key C fragments, and its softmax, dA = dH V^T, delta and dS follow as
+// for 16 tokens.  dQ of the block is emitted at once; dK and dV sum over both query blocks in FP32
+// registers and are emitted at the end.  Each block scales its dS by its own power of two
+// (ds_pack_scaled) and its dQ, dK products are unscaled before any sum.  emit(kind, row, col, v0, v1)
+// as in attn_fwd_bwd_h, row < n.
+template <int HD, typename EMIT>
+__device__ __forceinline__ void attn_fwd_bwd_h32(uint32_t Qh, uint32_t Kh, uint32_t Vh, uint32_t dHh, int ldh, int n,
+                                                 float qscale, float scale, EMIT emit) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const uint32_t blk = (uint32_t)(16 * ldh * 2);   // bytes from one 16-row block to the next
+  uint32_t kb[2][2][2], vn[2][2][2];                // K and V rows as B fragments (key blocks 0-15, 16-31)
+  frag_bn<HD>(Kh, ldh, kb[0]);
+  frag_bn<HD>(Kh + blk, ldh, kb[1]);
+  frag_bn<HD>(Vh, ldh, vn[0]);
+  frag_bn<HD>(Vh + blk, ldh, vn[1]);
+  uint32_t kk[2][HD / 8][2], vk[2][HD / 8][2];      // K and V rows as k-major B fragments (for dQ, O)
+  frag_bk<HD>(Kh, ldh, kk[0]);
+  frag_bk<HD>(Kh + blk, ldh, kk[1]);
+  frag_bk<HD>(Vh, ldh, vk[0]);
+  frag_bk<HD>(Vh + blk, ldh, vk[1]);
+  float dk[2][HD / 8][4], dv[2][HD / 8][4];
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) { zero4(dk[b][c]); zero4(dv[b][c]); }
+#pragma unroll
+  for (int qb = 0; qb < 2; ++qb) {
+    const uint32_t qo = (uint32_t)qb * blk;
+    const bool q0 = 16 * qb + g < n, q1 = 16 * qb + g + 8 < n;
+    uint32_t qa[4];
+    frag_a<HD>(Qh + qo, ldh, qa);
+    float s[4][4];   // s[j]: keys 8 j .. 8 j + 7
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      zero4(s[j]);
+      if (HD == 8) mma1688(s[j], qa[0], qa[1], kb[j >> 1][j & 1][0]);
+      else mma16816(s[j], qa, kb[j >> 1][j & 1][0], kb[j >> 1][j & 1][1]);
+    }
+    float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const bool ok = 8 * j + 2 * t + e < n;
+        s[j][e] = ok ? s[j][e] * qscale : -INFINITY;
+        s[j][2 + e] = ok ? s[j][2 + e] * qscale : -INFINITY;
+        m0 = fmaxf(m0, s[j][e]);
+        m1 = fmaxf(m1, s[j][2 + e]);
+      }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+      m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    }
+    float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        s[j][e] = tc::ex2_fast(s[j][e] - m0);
+        s[j][2 + e] = tc::ex2_fast(s[j][2 + e] - m1);
+        l0 += s[j][e];
+        l1 += s[j][2 + e];
+      }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+      l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+    }
+    const float i0 = q0 ? tc::rcp_fast(l0) : 0.f, i1 = q1 ? tc::rcp_fast(l1) : 0.f;   // invalid query rows: P = 0
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      s[j][0] *= i0; s[j][1] *= i0;
+      s[j][2] *= i1; s[j][3] *= i1;
+    }
+    uint32_t pa[2][4];   // P of key block kb as an A fragment
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      pa[b][0] = h2(s[2 * b][0], s[2 * b][1]);
+      pa[b][1] = h2(s[2 * b][2], s[2 * b][3]);
+      pa[b][2] = h2(s[2 * b + 1][0], s[2 * b + 1][1]);
+      pa[b][3] = h2(s[2 * b + 1][2], s[2 * b + 1][3]);
+    }
+    {   // O = P V over both key blocks
+      float o[HD / 8][4];
+#pragma unroll
+      for (int c = 0; c < HD / 8; ++c) {
+        zero4(o[c]);
+        mma16816(o[c], pa[0], vk[0][c][0], vk[0][c][1]);
+        mma16816(o[c], pa[1], vk[1][c][0], vk[1][c][1]);
+        if (q0) emit(0, 16 * qb + g, 8 * c + 2 * t, o[c][0], o[c][1]);
+        if (q1) emit(0, 16 * qb + g + 8, 8 * c + 2 * t, o[c][2], o[c][3]);
+      }
+    }
+    // dA = dH V^T; delta_i = sum_j P_ij dA_ij; dS = scale P (dA - delta)
+    float da[4][4];
+    uint32_t ha[4];
+    frag_a<HD>(dHh + qo, ldh, ha);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      zero4(da[j]);
+      if (HD == 8) mma1688(da[j], ha[0], ha[1], vn[j >> 1][j & 1][0]);
+      else mma16816(da[j], ha, vn[j >> 1][j & 1][0], vn[j >> 1][j & 1][1]);
+    }
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      d0 = fmaf(s[j][0], da[j][0], fmaf(s[j][1], da[j][1], d0));
+      d1 = fmaf(s[j][2], da[j][2], fmaf(s[j][3], da[j][3], d1));
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+    }
+    float mx = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      da[j][0] = scale * s[j][0] * (da[j][0] - d0);
+      da[j][1] = scale * s[j][1] * (da[j][1] - d0);
+      da[j][2] = scale * s[j][2] * (da[j][2] - d1);
+      da[j][3] = scale * s[j][3] * (da[j][3] - d1);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(da[j][e]));
+    }
+    // one power of two for the whole 16 x 32 block (ds_pack_scaled's rule), so that both key blocks'
+    // fragments share it
+#pragma unroll
+    for (int o = 1; o <= 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int ex = 0;
+    if (mx > 0.f && isfinite(mx)) frexpf(mx, &ex);
+    int kx = 14 - ex;
+    kx = kx > 100 ? 100 : (kx < -100 ? -100 : kx);
+    const float up = ldexpf(1.0f, kx), down = ldexpf(1.0f, -kx);
+    uint32_t x[2][4];   // dS of key block b as an A fragment (scaled)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      x[b][0] = h2(da[2 * b][0] * up, da[2 * b][1] * up);
+      x[b][1] = h2(da[2 * b][2] * up, da[2 * b][3] * up);
+      x[b][2] = h2(da[2 * b + 1][0] * up, da[2 * b + 1][1] * up);
+      x[b][3] = h2(da[2 * b + 1][2] * up, da[2 * b + 1][3] * up);
+    }
+    {   // dQ = dS K over both key blocks
+      float y[HD / 8][4];
+#pragma unroll
+      for (int c = 0; c < HD / 8; ++c) {
+        zero4(y[c]);
+        mma16816(y[c], x[0], kk[0][c][0], kk[0][c][1]);
+        mma16816(y[c], x[1], kk[1][c][0], kk[1][c][1]);
+        if (q0) emit(1, 16 * qb + g, 8 * c + 2 * t, y[c][0] * down, y[c][1] * down);
+        if (q1) emit(1, 16 * qb + g + 8, 8 * c + 2 * t, y[c][2] * down, y[c][3] * down);
+      }
+    }
+    uint32_t qk[HD / 8][2], hk[HD / 8][2];   // this block's Q and dH rows as k-major B fragments
+    frag_bk<HD>(Qh + qo, ldh, qk);
+    frag_bk<HD>(dHh + qo, ldh, hk);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      // dK[key block b] += dS^T Q, dV[key block b] += P^T dH (this query block's 16 rows as K = 16)
+      const uint32_t dst[4] = {trans8(x[b][0]), trans8(x[b][2]), trans8(x[b][1]), trans8(x[b][3])};
+      const uint32_t pt[4] = {trans8(pa[b][0]), trans8(pa[b][2]), trans8(pa[b][1]), trans8(pa[b][3])};
+#pragma unroll
+      for (int c = 0; c < HD / 8; ++c) {
+        float y[4];
+        zero4(y);
+        mma16816(y, dst, qk[c][0], qk[c][1]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dk[b][c][e] = fmaf(y[e], down, dk[b][c][e]);
+        mma16816(dv[b][c], pt, hk[c][0], hk[c][1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int c = 0; c < HD / 8; ++c) {
+      const int r0 = 16 * b + g, r1 = r0 + 8;
+      if (r0 < n) {
+        emit(2, r0, 8 * c + 2 * t, dk[b][c][0], dk[b][c][1]);
+        emit(3, r0, 8 * c + 2 * t, dv[b][c][0], dv[b][c][1]);
+      }
+      if (r1 < n) {
+        emit(2, r1, 8 * c + 2 * t, dk[b][c][2], dk[b][c][3]);
+        emit(3, r1, 8 * c + 2 * t, dv[b][c][2], dv[b][c][3]);
+      }
+    }
 }
 
 }  // namespace amma

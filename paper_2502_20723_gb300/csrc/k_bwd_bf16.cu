@@ -15,7 +15,7 @@
 //                (MMA, MN-major operands); the second pass adds its dX' part onto the first's output
 //              k_bwd_attn1: QKV = X Wqkv, dH = dX' Wo^T (MMA); softmax attention forward and backward
 //                per (sequence, head) by warp-level MMAs on FP16 copies -> dQ, dK, dV (BF16 images);
-//                dWo += H^T dX'  (sequences of at most 16 tokens)
+//                dWo += H^T dX'  (sequences of up to 32 tokens)
 //              k_bwd_attn2: dWqkv += X^T [dQ dK dV], dX = dX' + [dQ dK dV] Wqkv^T (MMA)
 //   then:      k_embed_grad, the token-embedding gradient from dX at the first layer's input (in the
 //              per-configuration mode attention pass 2 of the first layer sums it per configuration)
@@ -171,27 +171,6 @@ __device__ __forceinline__ float gelu_grad_fast(float u, float *g) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(k0 * fmaf(k1 * u, u * u, u)));
   *g = 0.5f * u * (1.0f + t);
   return 0.5f * (1.0f + t) + 0.5f * u * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * u * u);
-}
-
-// GELU (tanh form) and its derivative for a pair of FP16 values, in packed half2 arithmetic (two results
-// per instruction): g = (u / 2)(1 + t), g' = (1 + t) / 2 + (u / 2)(1 - t^2) k0 (1 + 3 k1 u^2), with
-// t = tanh(k0 (u + k1 u^3)).  The polynomial terms take u clamped to [-10, 10] (beyond it t = +-1 in FP16,
-// so g' is 0 or 1 and g is u or 0 from the unclamped u / 2), which keeps u^2 finite.  Returns g; *gp = g'.
-__device__ __forceinline__ __half2 gelu_grad_h2(__half2 u, __half2 *gp) {
-  const __half2 k0 = __float2half2_rn(0.7978845608028654f), k1 = __float2half2_rn(0.044715f);
-  const __half2 k13 = __float2half2_rn(3.0f * 0.044715f), one = __float2half2_rn(1.0f), hf = __float2half2_rn(0.5f);
-  const __half2 lim = __float2half2_rn(10.0f), nlim = __float2half2_rn(-10.0f);
-  const __half2 uc = __hmin2(__hmax2(u, nlim), lim);
-  const __half2 u2 = __hmul2(uc, uc);
-  const __half2 arg = __hmul2(__hmul2(uc, __hfma2(u2, k1, one)), k0);
-  uint32_t tb;
-  asm("tanh.approx.f16x2 %0, %1;" : "=r"(tb) : "r"(*reinterpret_cast<const uint32_t *>(&arg)));
-  const __half2 t = *reinterpret_cast<const __half2 *>(&tb);
-  const __half2 opt = __hadd2(one, t);
-  const __half2 omt2 = __hfma2(__hneg2(t), t, one);
-  const __half2 q = __hmul2(__hmul2(__hmul2(uc, hf), omt2), __hmul2(__hfma2(u2, k13, one), k0));
-  *gp = __hfma2(hf, opt, q);
-  return __hmul2(__hmul2(u, hf), opt);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -654,33 +633,16 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       for (int j = 0; j < QH; j += 16) {
         float u[16], dg[16];
         tmem_ld16x2(s.tmem + lane_addr + G::C_U + cg * QH + j, u, s.tmem + lane_addr + G::C_DG + cg * QH + j, dg);
-        if constexpr (kF16) {   // FP16 images: GELU, GELU' and dU in packed half2 arithmetic
-          uint32_t gh[8], dh[8];
+        float gl[16], du[16];
 #pragma unroll
-          for (int e = 0; e < 16; e += 2) {
-            const __half2 uu = __floats2half2_rn(u[e] + b1s[cg * QH + j + e], u[e + 1] + b1s[cg * QH + j + e + 1]);
-            __half2 gp;
-            const __half2 g = gelu_grad_h2(uu, &gp);
-            const __half2 d = __hmul2(__floats2half2_rn(dg[e], dg[e + 1]), gp);
-            gh[e / 2] = *reinterpret_cast<const uint32_t *>(&g);
-            dh[e / 2] = *reinterpret_cast<const uint32_t *>(&d);
-          }
-          *reinterpret_cast<uint4 *>(sm + G::G_OFF + canon(row, cg * QH + j, G::HC)) = make_uint4(gh[0], gh[1], gh[2], gh[3]);
-          *reinterpret_cast<uint4 *>(sm + G::G_OFF + canon(row, cg * QH + j + 8, G::HC)) = make_uint4(gh[4], gh[5], gh[6], gh[7]);
-          *reinterpret_cast<uint4 *>(sm + G::DU_OFF + canon(row, cg * QH + j, G::HC)) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
-          *reinterpret_cast<uint4 *>(sm + G::DU_OFF + canon(row, cg * QH + j + 8, G::HC)) = make_uint4(dh[4], dh[5], dh[6], dh[7]);
-        } else {
-          float gl[16], du[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const float uu = u[e] + b1s[cg * QH + j + e];
-            du[e] = dg[e] * gelu_grad_fast(uu, &gl[e]);
-          }
-          st_row8<kF16>(sm + G::G_OFF, row, cg * QH + j, G::HC, gl);
-          st_row8<kF16>(sm + G::G_OFF, row, cg * QH + j + 8, G::HC, gl + 8);
-          st_row8<kF16>(sm + G::DU_OFF, row, cg * QH + j, G::HC, du);
-          st_row8<kF16>(sm + G::DU_OFF, row, cg * QH + j + 8, G::HC, du + 8);
+        for (int e = 0; e < 16; ++e) {
+          const float uu = u[e] + b1s[cg * QH + j + e];
+          du[e] = dg[e] * gelu_grad_fast(uu, &gl[e]);
         }
+        st_row8<kF16>(sm + G::G_OFF, row, cg * QH + j, G::HC, gl);
+        st_row8<kF16>(sm + G::G_OFF, row, cg * QH + j + 8, G::HC, gl + 8);
+        st_row8<kF16>(sm + G::DU_OFF, row, cg * QH + j, G::HC, du);
+        st_row8<kF16>(sm + G::DU_OFF, row, cg * QH + j + 8, G::HC, du + 8);
       }
       tc_fence_before();
       fence_proxy_async();
@@ -812,9 +774,10 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
 }
 
 // ====================================================================================== attention pass 1
-// Sequences of N <= 16 tokens: one warp per (sequence, head) does the softmax attention forward and
-// backward with warp-level MMAs on FP16 copies of Q, K, V, dH (row stride D + 8 halves: ldmatrix rows
-// on distinct banks; 16 zero rows after the tile so the last sequence's 16-row blocks stay in bounds).
+// One warp per (sequence, head) does the softmax attention forward and backward with warp-level MMAs on
+// FP16 copies of Q, K, V, dH (row stride D + 8 halves: ldmatrix rows on distinct banks): one 16-row block
+// for N <= 16, two query and two key blocks for 17 <= N <= 32.  The 16 zero rows after the tile keep every
+// block in bounds: a sequence's blocks reach row (ts - 1) N + 31 <= 136 for N >= 17.
 template <int D>
 struct A1Geo {
   static constexpr int IMG = kRows * D * 2;
@@ -972,8 +935,27 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
               });
         }
       };
-      if (n == 16) units(std::true_type{});
-      else units(std::false_type{});
+      if (n == 16) {
+        units(std::true_type{});
+      } else if (n <= 16) {
+        units(std::false_type{});
+      } else {   // 17 to 32 tokens: one warp per (sequence, head), both 16-query blocks
+        constexpr int H = D / HD;
+        for (int u = warp; u < a.ts * H; u += kA1Threads / 32) {
+          const int sq = u / H, h = u % H, rb = sq * n;
+          const uint32_t off = (uint32_t)(rb * LDH + h * HD) * 2;
+          amma::attn_fwd_bwd_h32<HD>(
+              f16 + off, f16 + G::F_BYTES + off, f16 + 2 * G::F_BYTES + off, f16 + 3 * G::F_BYTES + off, LDH, n,
+              qscale, scale, [&](int kind, int r, int c, float v0, float v1) {
+                const int rr = rb + r, col = h * HD + c;
+                if (kind == 0)
+                  *reinterpret_cast<uint32_t *>(sm + G::H_OFF + canon(rr, col, 128)) = pack16<kF16>(v0, v1);
+                else
+                  *reinterpret_cast<uint32_t *>(dq_img + canon(rr, (kind - 1) * D + col, 3 * D)) =
+                      kind < 3 ? pack_bf16(v0, v1) : pack16<kF16>(v0, v1);
+              });
+        }
+      }
       fence_proxy_async();
       if (!sync_ok(s, true)) break;
       if (threadIdx.x == 0) {
@@ -1346,7 +1328,7 @@ cudaError_t TDO_OPFN(launch_pack_bwdtc)(const DevModel &m, uint8_t *dst, BwdTcLa
 #if !TDO_F16
 bool bwdtc_supported(const DevModel &m) {
   return m.d == 64 && (m.dh == 8 || m.dh == 16) && m.heads % 2 == 0 && m.heads <= 16 &&
-         (m.ffn == 0 || m.ffn == 128 || m.ffn == 256) && m.embed == 0 && m.n_sites <= 16;
+         (m.ffn == 0 || m.ffn == 128 || m.ffn == 256) && m.embed == 0 && m.n_sites <= 32;
 }
 #endif
 
