@@ -511,12 +511,12 @@ def config5_vmc(tdo, torch, stream, spec, theta, steps: dict = None) -> dict:
     return out
 
 
-def sr_traffic_per_row():
+def sr_traffic_per_row(prof: str = None, src: str = None):
     """DRAM bytes per sample row of one S' v product from the committed ncu summary of the two passes,
     valid only while the SR source has the SHA-1 recorded with that capture: (bytes or None, source)."""
     here = os.path.dirname(os.path.abspath(__file__))
-    prof = os.path.join(here, "profiles", "k_sr_tpart_wpart_ising_n16_d64_l4.md")
-    src = os.path.join(here, "paper_2502_20723_gb300", "csrc", "k_sr.cu")
+    prof = prof or os.path.join(here, "profiles", "k_sr_tpart_wpart_ising_n16_d64_l4.md")
+    src = src or os.path.join(here, "paper_2502_20723_gb300", "csrc", "k_sr.cu")
     try:
         m = re.search(r"bench-traffic sr_mv: k_sr\.cu sha1=([0-9a-f]{40}) bytes_per_sample_row=(\d+)", open(prof).read())
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
