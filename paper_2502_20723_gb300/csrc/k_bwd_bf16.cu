@@ -199,10 +199,11 @@ __device__ __forceinline__ void flush_block(const Sync &s, uint32_t col, int N, 
 }
 
 // ---- per-configuration (log-derivative) mode.  The rows are virtual configurations v = 2 b + seed
-// (sample b, cotangent (1, 0) for seed 0 and (0, -1) for seed 1), 32 rows (two sequences of N = 16)
-// each, so a tile holds the two seeds of two samples.  Weight gradients are then MMAs over each
-// configuration's 32 rows (two K steps) into their own TMEM columns, written to O[b][k] as the pair
-// (seed 0, seed 1) = (d Re log rho, d Im log rho): FP32, or BF16 of O - oref.
+// (sample b, cotangent (1, 0) for seed 0 and (0, -1) for seed 1), 2N rows (two sequences of N tokens)
+// each: a tile holds cpt = ts / 2 of them, the two seeds of cpt / 2 samples (4 at N = 16, 2 at N = 24
+// or 32; the N this mode takes make 2N a multiple of the MMAs' 16-row K step).  Weight gradients are then
+// MMAs over each configuration's 2N rows (2N / 16 K steps) into their own TMEM columns, written to O[b][k]
+// as the pair (seed 0, seed 1) = (d Re log rho, d Im log rho): FP32, or BF16 of O - oref.
 struct JacOut {
   float *o32;            // [nvirt / 2][ldo] float2, or
   uint16_t *o16;         // [nvirt / 2][ldo] BF16 pairs of O - oref
@@ -210,6 +211,8 @@ struct JacOut {
   size_t ldo;
   size_t nvirt;          // virtual configurations (0: the kernels run in VJP mode)
   const float *iscale;   // inverse of the seeds' power-of-two scale (null: 1), applied to every output
+  int cpt;               // virtual configurations per tile (even)
+  int rpc;               // rows per virtual configuration (2N, a multiple of 16)
 };
 
 __device__ __forceinline__ float jac_unscale(const JacOut &j) { return j.iscale ? *j.iscale : 1.0f; }
@@ -246,7 +249,7 @@ __device__ __forceinline__ void mma_mm_rows(const Sync &s, uint32_t a, int Ka, u
   }
 }
 
-// Flush per-configuration TMEM blocks [lanes M][N cols] at columns col0 + c * N for the tile's 4 virtual
+// Flush per-configuration TMEM blocks [lanes M][N cols] at columns col0 + c * N for the tile's cpt virtual
 // configurations: each thread (lane quarter, column group of NQ) pairs the two seeds of a sample.
 // idx(m, n) < 0 skips an element.
 template <typename IDX, int NQ>
@@ -263,8 +266,8 @@ __device__ __forceinline__ void jac_flush(const Sync &s, const JacOut &j, size_t
       const long long k = idx(m, cg * (N / NQ) + jj + e);
       rf[e] = (j.o16 && k >= 0) ? j.oref[k] : make_float2(0.f, 0.f);
     }
-    for (int pr = 0; pr < 2; ++pr) {   // sample tile * 2 + pr: configurations 2 pr (seed 0) and 2 pr + 1
-      const size_t v0 = tile * 4 + 2 * pr;
+    for (int pr = 0; pr < 2 && pr < j.cpt / 2; ++pr) {   // configurations 2 pr (seed 0) and 2 pr + 1 of the tile
+      const size_t v0 = tile * j.cpt + 2 * pr;
       float re[16], im[16];
       tmem_ld16x2(s.tmem + lane_addr + col0 + (2 * pr) * N + cg * (N / NQ) + jj, re,
                   s.tmem + lane_addr + col0 + (2 * pr + 1) * N + cg * (N / NQ) + jj, im);
@@ -287,8 +290,9 @@ __device__ __forceinline__ void jac_flush(const Sync &s, const JacOut &j, size_t
 // m < mlim) when O is stored in BF16: each warp stages 32 rows x 8 columns of (seed 0, seed 1) pairs in
 // shared memory (2 KB per warp at stage + 512 floats * warp) and writes them back 4 rows x 8 columns per
 // instruction, so a warp store covers 4 contiguous 32-byte pieces instead of 32 scattered elements.
-template <int NQ>
-__device__ __noinline__ void jac_flush_rows(const Sync &s, const JacOut &j, size_t tile, uint32_t col0, int N,
+// NPR = cpt / 2 samples per tile.
+template <int NQ, int NPR>
+__device__ __noinline__ void jac_flush_rows_n(const Sync &s, const JacOut &j, size_t tile, uint32_t col0, int N,
                                                long long off, int ld, int mlim, float *stage) {
   const float u = jac_unscale(j);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -306,8 +310,8 @@ __device__ __noinline__ void jac_flush_rows(const Sync &s, const JacOut &j, size
         rf[h][it] = m < mlim ? j.oref[off + (long long)m * ld + cg * (N / NQ) + jj + 8 * h + (lane & 7)]
                              : make_float2(0.f, 0.f);
       }
-    for (int pr = 0; pr < 2; ++pr) {
-      const size_t v0 = tile * 4 + 2 * pr;
+    for (int pr = 0; pr < NPR; ++pr) {
+      const size_t v0 = tile * (2 * NPR) + 2 * pr;
       const bool ok = v0 + 1 < j.nvirt;
       const size_t b = v0 >> 1;
       float re[16], im[16];
@@ -334,6 +338,13 @@ __device__ __noinline__ void jac_flush_rows(const Sync &s, const JacOut &j, size
       }
     }
   }
+}
+
+template <int NQ>
+__device__ __forceinline__ void jac_flush_rows(const Sync &s, const JacOut &j, size_t tile, uint32_t col0, int N,
+                                               long long off, int ld, int mlim, float *stage) {
+  if (j.cpt == 4) jac_flush_rows_n<NQ, 2>(s, j, tile, col0, N, off, ld, mlim, stage);
+  else jac_flush_rows_n<NQ, 1>(s, j, tile, col0, N, off, ld, mlim, stage);
 }
 
 // ====================================================================================== head
@@ -657,10 +668,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
           // db2 += dX^T 1: M = 128 reads the D-wide image as 128 features; lanes >= D hold unused sums
           if (a.do_db2) mma_mm(s, dxs, D, ones, 16, 16, G::C_B2, !first);
         } else {   // per configuration: dW1_c^T into columns [64 c, 64 c + 64) (U and dG are consumed)
-          for (int c = 0; c < 4; ++c) {
-            mma_mm_rows(s, dus, G::HC, xs, D, D, 64 * c, 32 * c, 2);
-            mma_mm_rows(s, dus, G::HC, ones, 16, 16, G::C_JB1 + 16 * c, 32 * c, 2);
-            if (a.do_db2) mma_mm_rows(s, dxs, D, ones, 16, 16, G::C_JB2 + 16 * c, 32 * c, 2);
+          const int rpc = a.jac.rpc, ks = rpc / 16;
+          for (int c = 0; c < 4 && c < a.jac.cpt; ++c) {
+            mma_mm_rows(s, dus, G::HC, xs, D, D, 64 * c, rpc * c, ks);
+            mma_mm_rows(s, dus, G::HC, ones, 16, 16, G::C_JB1 + 16 * c, rpc * c, ks);
+            if (a.do_db2) mma_mm_rows(s, dxs, D, ones, 16, 16, G::C_JB2 + 16 * c, rpc * c, ks);
           }
         }
         mma_commit(bar2);
@@ -700,8 +712,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
         if (cg == 0) {   // db1 (lane m = hidden unit) and db2 (lane m < D = feature) per configuration:
                          // column 0 of each 16-column block
           float re[16], im[16];
-          for (int pr = 0; pr < 2; ++pr) {
-            const size_t v0 = tile * 4 + 2 * pr;
+          for (int pr = 0; pr < 2 && pr < a.jac.cpt / 2; ++pr) {
+            const size_t v0 = tile * a.jac.cpt + 2 * pr;
             tmem_ld16x2(s.tmem + lane_addr + G::C_JB1 + 16 * (2 * pr), re,
                         s.tmem + lane_addr + G::C_JB1 + 16 * (2 * pr + 1), im);
             if (v0 + 1 < a.jac.nvirt) jac_put2(a.jac, v0 >> 1, a.off_b1 + row, re[0], im[0]);
@@ -716,7 +728,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
         if (!sync_ok(s, true)) break;
         if (threadIdx.x == 0) {
           tc_fence_after();
-          for (int c = 0; c < 4; ++c) mma_mm_rows(s, gs, G::HC, dxs, D, D, 64 * c, 32 * c, 2);   // dW2_c per config
+          for (int c = 0; c < 4 && c < a.jac.cpt; ++c)   // dW2_c per config
+            mma_mm_rows(s, gs, G::HC, dxs, D, D, 64 * c, a.jac.rpc * c, a.jac.rpc / 16);
           mma_commit(bar2);
         }
         ok = mbar_wait(bar2, ph2);
@@ -964,7 +977,8 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
           mma_mm(s, hs, 128, dxs, D, D, G::C_WO, !first);   // dWo += H^T dX'   (rows of H beyond D are zero)
           mma_commit(bar2);
         } else {
-          for (int c = 0; c < 4; ++c) mma_mm_rows(s, hs, 128, dxs, D, D, G::C_JWO + 64 * c, 32 * c, 2);
+          for (int c = 0; c < 4 && c < a.jac.cpt; ++c)
+            mma_mm_rows(s, hs, 128, dxs, D, D, G::C_JWO + 64 * c, a.jac.rpc * c, a.jac.rpc / 16);
           mma_commit(s.bar_mma);
         }
       }
@@ -1141,11 +1155,12 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
           if (threadIdx.x == 0) {
             tc_fence_after();
             // columns [D part, D part + D) of the [dQ dK dV] image start (D / 8) MN groups (128 B each) in
-            for (int c = 0; c < 4; ++c) {
+            const int rpc = a.jac.rpc, ks = rpc / 16;
+            for (int c = 0; c < 4 && c < a.jac.cpt; ++c) {
               if (kF16 && part < 2)   // dQ, dK parts: BF16
-                mma_mm_rows<false>(s, xb, D, dq + part * (D / 8) * 128, 3 * D, D, 256 * (part & 1) + 64 * c, 32 * c, 2);
+                mma_mm_rows<false>(s, xb, D, dq + part * (D / 8) * 128, 3 * D, D, 256 * (part & 1) + 64 * c, rpc * c, ks);
               else
-                mma_mm_rows(s, xr, D, dq + part * (D / 8) * 128, 3 * D, D, 256 * (part & 1) + 64 * c, 32 * c, 2);
+                mma_mm_rows(s, xr, D, dq + part * (D / 8) * 128, 3 * D, D, 256 * (part & 1) + 64 * c, rpc * c, ks);
             }
             mma_commit(s.bar_mma);
           }
@@ -1187,12 +1202,12 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
       }
       if (a.jac.nvirt && a.embed_grad) {
         __syncthreads();
-        for (int i = threadIdx.x; i < 4 * 4 * D; i += kA2Threads) {
-          const size_t v = tile * 4 + i / (4 * D);
+        for (int i = threadIdx.x; i < a.jac.cpt * 4 * D; i += kA2Threads) {
+          const size_t v = tile * a.jac.cpt + i / (4 * D);
           if (v < a.jac.nvirt) jac_put1(a.jac, v, a.off_e + i % (4 * D), dE[i]);
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < 4 * 4 * D; i += kA2Threads) dE[i] = 0.f;
+        for (int i = threadIdx.x; i < a.jac.cpt * 4 * D; i += kA2Threads) dE[i] = 0.f;
       }
       first = false;
       tc_fence_before();
@@ -1415,7 +1430,11 @@ struct BwdTcJac {
 };
 
 #if !TDO_F16
-bool bwdtc_jac_supported(const DevModel &m) { return bwdtc_supported(m) && m.n_sites == 16; }
+// The per-configuration mode needs 2N rows per configuration in whole 16-row K steps and at most 4
+// configurations per tile (their TMEM column blocks): N = 16, 24 or 32.
+bool bwdtc_jac_supported(const DevModel &m) {
+  return bwdtc_supported(m) && (m.n_sites == 16 || m.n_sites == 24 || m.n_sites == 32);
+}
 #endif
 
 namespace tdo {
@@ -1523,8 +1542,9 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
                          size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st,
                          const BwdTcJac *jac) {
   using namespace tdo::TDO_BWNS;
-  JacOut jo{nullptr, nullptr, nullptr, 0, 0, nullptr};
-  if (jac) jo = JacOut{jac->o32, jac->o16, jac->oref, jac->ldo, jac->nvirt, bf.cscale + 1};
+  const int n_ = m.n_sites, tc_ = tdo::seqs_per_tile(n_) / 2;
+  JacOut jo{nullptr, nullptr, nullptr, 0, 0, nullptr, tc_, 2 * n_};
+  if (jac) jo = JacOut{jac->o32, jac->o16, jac->oref, jac->ldo, jac->nvirt, bf.cscale + 1, tc_, 2 * n_};
   constexpr int D = 64;
   const int n = m.n_sites, ts = tdo::seqs_per_tile(n), tc = ts / 2;
   const size_t tiles = bf.tiles, Bpad = tiles * tc;

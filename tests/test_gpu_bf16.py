@@ -149,12 +149,16 @@ def test_sr_step_bf16(prec, tol, kind, n, d, h, L, r, Ns):
 
 @pytest.mark.parametrize("prec,tol", [("bf16", 3e-2), ("fp16", 3e-3)])
 @pytest.mark.parametrize("kind,n,h,L,r,B,std", [("ising", 16, 8, 2, 4, 7, 0.05), ("xyz", 16, 4, 1, 2, 10, 0.05),
-                                                 ("ising", 16, 8, 4, 4, 3, 0.02)])
+                                                 ("ising", 16, 8, 4, 4, 3, 0.02), ("ising", 24, 8, 2, 4, 5, 0.05),
+                                                 ("xyz", 24, 4, 1, 2, 6, 0.05), ("ising", 32, 8, 2, 4, 5, 0.05),
+                                                 ("xyz", 32, 8, 4, 4, 3, 0.02)])
 def test_jacobian_tensor_core(prec, tol, kind, n, h, L, r, B, std):
-    """tdo_jacobian on a BF16 context at N = 16: two virtual configurations per sample (one per real
-    cotangent seed) through the BF16 forward and the tensor-core backward with per-configuration
-    weight-gradient MMAs (an odd sample count leaves a half-empty last tile).  Within 3e-2 of the
-    oracle's log-derivatives in norm, per sample (measured values are reported)."""
+    """tdo_jacobian on a 16-bit context at N = 16, 24 and 32: two virtual configurations per sample (one
+    per real cotangent seed) through the tensor-core forward and backward with per-configuration
+    weight-gradient MMAs over each configuration's 2N rows (N = 16: four configurations per tile, so an
+    odd sample count leaves a half-empty last tile; N = 24: two, 96 of the tile's 128 rows; N = 32: two,
+    all 128 rows).  Within the bound of the oracle's log-derivatives in norm, per sample (measured
+    values are reported)."""
     spec = synth.model_spec(64, h, L, r)
     th = synth.init_params(spec, seed=13, std=std)
     sig, sigp = synth.random_configs(n, B, seed=3)
@@ -167,13 +171,12 @@ def test_jacobian_tensor_core(prec, tol, kind, n, h, L, r, B, std):
     assert rel.max() <= tol
 
 
-@pytest.mark.parametrize("Ns", [70, 37])
-def test_sr_step_bf16_log_derivative_storage(Ns):
-    """At N = 16 a BF16 context's SR step stores the tensor-core log-derivatives as BF16 pairs of O - ō
-    (written by the staged per-configuration flushes).  Its update must equal, within 2e-3 in norm, the
-    solve of the same system from the FP32 log-derivatives of tdo_jacobian (same gradient, shift and CG
-    tolerance): the only difference is the BF16 rounding of the centred values."""
-    n = 16
+@pytest.mark.parametrize("n,Ns", [(16, 70), (16, 37), (24, 41), (32, 33)])
+def test_sr_step_bf16_log_derivative_storage(n, Ns):
+    """At N = 16, 24 and 32 a BF16 context's SR step stores the tensor-core log-derivatives as BF16 pairs
+    of O - ō (written by the staged per-configuration flushes).  Its update must equal, within 2e-3 in
+    norm, the solve of the same system from the FP32 log-derivatives of tdo_jacobian (same gradient,
+    shift and CG tolerance): the only difference is the BF16 rounding of the centred values."""
     prob = problem("ising", n)
     spec = synth.model_spec(64, 8, 2, 4)
     th = synth.init_params(spec, 4, std=0.05)
