@@ -259,6 +259,28 @@ typedef struct {
 tdo_status tdo_vmc_step(tdo_ctx *ctx, uint32_t *sig, uint32_t *sigp, size_t n_chains, size_t n_sweeps,
                         uint64_t seed, uint64_t *counter, long long step, const tdo_schedule *sched, double *cost);
 
+/* Whole-step CUDA graph for tdo_vmc_step (the optimisation workflow's step: sweeps, connections, L_loc
+ * and cost, gradient, log-derivatives, SR solve, update).  With enable != 0, tdo_vmc_step records its
+ * step into a CUDA graph on first use and then launches that graph, with one host synchronisation per
+ * step (to return the cost and the outcome) instead of one per host decision.  Results are those of the
+ * call-by-call step, up to the order of floating-point atomics:
+ *   - the connected-row count stays on the device: buffers and grids are sized for n_chains x
+ *     tdo_max_connections rows, and the kernels read the count the connection scan left on the device;
+ *   - the CG's iterations are a conditional while node; a failed warm-started solve is rerun from x = 0
+ *     inside the same launch, and the update is skipped on the device when the solve fails, L_loc is not
+ *     finite or a bounded wait gave up; the status is then reported as tdo_sr_step reports it;
+ *   - the sampler's counter and Adam's bias corrections are read from device memory, written before each
+ *     launch, so advancing *counter and Adam's step count needs no new recording.
+ * The step is recorded again when anything it depends on changes: n_chains, n_sweeps, seed, lr and
+ * diag_shift (the schedules' values), the SR options and product mode, the optimiser, the chain
+ * buffers' addresses, or a reallocation of the context's device workspace.  Host chain buffers are
+ * staged (copied in before and out after each launch).  Graph mode records no per-group timing
+ * (tdo_timing).  Needs a tensor-core context whose gradient runs on the tensor cores (token embedding,
+ * d = 64, N <= 32): TDO_EUNSUPPORTED otherwise.  enable = 0 frees the recorded graph. */
+tdo_status tdo_set_step_graph(tdo_ctx *ctx, int enable);
+/* How many times the step graph has been recorded and launched (each pointer may be NULL). */
+tdo_status tdo_step_graph_stats(const tdo_ctx *ctx, long long *recordings, long long *launches);
+
 /* Device timing of this context's kernels: with enable != 0, every kernel launch of the calls above is
  * bracketed by CUDA events on the context's stream (records from before are dropped).  Used by the
  * benchmark to time kernels inside a real step. */

@@ -217,6 +217,15 @@ struct JacOut {
 
 __device__ __forceinline__ float jac_unscale(const JacOut &j) { return j.iscale ? *j.iscale : 1.0f; }
 
+// A replayed step graph keeps its row count in device memory (dB): a launch's B, Bpad and tiles are then
+// bounds (buffers and grids sized for the most rows the step can have) and each kernel reads the count.
+__device__ __forceinline__ size_t rows_now(const int64_t *dB, size_t B) {
+  return dB ? min(B, (size_t)*dB) : B;
+}
+__device__ __forceinline__ size_t tiles_now(const int64_t *dB, size_t tiles, int tc) {
+  return dB ? min(tiles, ((size_t)*dB + tc - 1) / tc) : tiles;
+}
+
 __device__ __forceinline__ void jac_put2(const JacOut &j, size_t b, long long k, float re, float im) {
   const size_t i = b * j.ldo + (size_t)k;
   const float u = jac_unscale(j);
@@ -356,6 +365,8 @@ struct HeadArgs {
   const float *Wh;     // [D][2]
   float *dF;           // [Bpad][4]
   size_t B, Bpad;
+  const int64_t *dB;   // device row count (null: B); Bpad then shrinks to its tiles
+  int tc;              // configurations per tile
   float *g;            // gradient accumulator copies
   size_t g_stride;
   long long off_wh, off_bh;
@@ -385,9 +396,10 @@ __global__ void __launch_bounds__(256) k_head_bwd_vjp(HeadArgs a) {
   __shared__ float red[8][130];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float w0[2] = {0.f, 0.f}, w1[2] = {0.f, 0.f}, bb0 = 0.f, bb1 = 0.f;
-  for (size_t b = blockIdx.x * (size_t)8 + warp; b < a.Bpad; b += gridDim.x * (size_t)8) {
+  const size_t B = rows_now(a.dB, a.B), Bpad = tiles_now(a.dB, a.Bpad / a.tc, a.tc) * a.tc;
+  for (size_t b = blockIdx.x * (size_t)8 + warp; b < Bpad; b += gridDim.x * (size_t)8) {
     float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (b < a.B) {
+    if (b < B) {
       d = head_df(a, b);
       const float *hA = a.H + (2 * b) * 64, *hB = hA + 64;
 #pragma unroll
@@ -459,9 +471,9 @@ __global__ void k_head_bwd(HeadArgs a) {
 
 // dX at the last layer output: (1/N) sum_o Wh[c][o] dF[seq(r)][o] for valid rows, 0 for padding.
 __global__ void k_head_dx(const float *__restrict__ dF, const float *__restrict__ Wh, int D, int n, int ts,
-                          size_t tiles, float *__restrict__ dX) {
+                          size_t tiles, float *__restrict__ dX, const int64_t *dB) {
   const int tc = ts / 2;
-  const size_t total = tiles * kRows * (size_t)D;
+  const size_t total = tiles_now(dB, tiles, tc) * kRows * (size_t)D;
   const float inv_n = 1.0f / (float)n;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += gridDim.x * (size_t)blockDim.x) {
     const size_t rowg = i / D;
@@ -511,6 +523,7 @@ struct MlpArgs {
   const float *dF, *Wh;
   int n, ts;
   size_t tiles;
+  const int64_t *dB;              // device row count (null: every tile); tiles is then a bound
   int do_db2;
   float *g;
   size_t g_stride;
@@ -567,8 +580,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
   }
   bool ok = wait_ld(s);
   bool first = true;
-  const size_t t0 = blockIdx.x, step = gridDim.x;
-  if (sync_ok(s, ok) && t0 < a.tiles) {
+  const size_t t0 = blockIdx.x, step = gridDim.x, ntl = tiles_now(a.dB, a.tiles, a.ts / 2);
+  if (sync_ok(s, ok) && t0 < ntl) {
     // head mode: this row's (dF0, dF1) / N of tile t, zero for padding rows
     const bool hvalid = head && row < a.ts * a.n;
     const float inv_n = head ? 1.0f / (float)a.n : 0.f;
@@ -629,14 +642,14 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
     load2(s, xs0, a.xmid + t0 * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
     load_nx(t0);
     put_dx(0);
-    if (t0 + step < a.tiles) load_nx(t0 + step);
+    if (t0 + step < ntl) load_nx(t0 + step);
     bool live = issue_mma1(0);
-    if (live && t0 + step < a.tiles) load2(s, xs0 + G::IMG, a.xmid + (t0 + step) * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+    if (live && t0 + step < ntl) load2(s, xs0 + G::IMG, a.xmid + (t0 + step) * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
     int buf = 0;
-    for (size_t tile = t0; live && tile < a.tiles; tile += step, buf ^= 1) {
+    for (size_t tile = t0; live && tile < ntl; tile += step, buf ^= 1) {
       const uint32_t xs = xs0 + buf * G::IMG, dxs = dxs0 + buf * G::IMG;
       const size_t rg = (tile * kRows + row) * (size_t)D + cg * QD;
-      const bool has_next = tile + step < a.tiles;
+      const bool has_next = tile + step < ntl;
       ok = wait_mma(s);   // U, dG of this tile; also MMA2 of the previous tile (G, dU images free)
       if (!sync_ok(s, ok)) break;
       // dU = dG gelu'(U + b1), G = gelu(U + b1) -> shared images
@@ -694,7 +707,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       }
       if (has_next) {
         put_dx(buf ^ 1);
-        if (tile + 2 * step < a.tiles) load_nx(tile + 2 * step);
+        if (tile + 2 * step < ntl) load_nx(tile + 2 * step);
         if (!jac && !issue_mma1(buf ^ 1)) break;
       }
       ok = mbar_wait(bar2, ph2);
@@ -703,7 +716,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       if (!sync_ok(s, ok)) break;
       // MMA2 has read this tile's Xmid buffer: the Xmid image two tiles ahead goes there (in the
       // per-configuration mode after the next tile's image has been waited for)
-      if (!jac && tile + 2 * step < a.tiles)
+      if (!jac && tile + 2 * step < ntl)
         load2(s, xs, a.xmid + (tile + 2 * step) * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
       if (jac) {
         const int F = a.F;
@@ -761,7 +774,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_bwd_mlp(MlpArgs a) {
       first = false;
       if (jac && has_next) {   // TMEM [0, 256) read out: the next tile's MMA1, then its successor's Xmid load
         if (!issue_mma1(buf ^ 1)) break;
-        if (tile + 2 * step < a.tiles) load2(s, xs, a.xmid + (tile + 2 * step) * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+        if (tile + 2 * step < ntl) load2(s, xs, a.xmid + (tile + 2 * step) * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
       }
       tc_fence_before();
       __syncthreads();
@@ -816,6 +829,7 @@ struct A1Args {
   const float *dxm;               // FP32 [tiles*128][D]
   uint8_t *dqkv;                  // out [tiles] images [128][3D]
   size_t tiles;
+  const int64_t *dB;              // device row count (null: every tile); tiles is then a bound
   int n, ts, heads;
   float *g;
   size_t g_stride;
@@ -864,17 +878,18 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
   }
   bool ok = wait_ld(s);
   bool first = true;
+  const size_t ntl = tiles_now(a.dB, a.tiles, a.ts / 2);
   if (sync_ok(s, ok)) {
-    if ((size_t)blockIdx.x < a.tiles) load2(s, xs0, a.x + blockIdx.x * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+    if ((size_t)blockIdx.x < ntl) load2(s, xs0, a.x + blockIdx.x * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
     float4 nx[QC / 4];   // this thread's dX' of the coming tile
     auto load_nx = [&](size_t t) {
       const float4 *src = reinterpret_cast<const float4 *>(a.dxm + (t * kRows + row) * (size_t)D + quarter * QC);
 #pragma unroll
       for (int j = 0; j < QC / 4; ++j) nx[j] = src[j];
     };
-    if ((size_t)blockIdx.x < a.tiles) load_nx(blockIdx.x);
+    if ((size_t)blockIdx.x < ntl) load_nx(blockIdx.x);
     int buf = 0;
-    for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, buf ^= 1) {
+    for (size_t tile = blockIdx.x; tile < ntl; tile += gridDim.x, buf ^= 1) {
       const uint32_t xs = xs0 + buf * G::IMG, dxs = dxs0 + buf * G::IMG;
       {   // this buffer was last read by the dWo product two tiles back, waited for in the previous tile
         float v[QC];
@@ -886,13 +901,13 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_bwd_attn1(A1Args a) {
 #pragma unroll
         for (int j = 0; j < QC; j += 8) st_row8<kF16>(sm + G::DX_OFF + buf * G::IMG, row, quarter * QC + j, D, v + j);
       }
-      if (tile + gridDim.x < a.tiles) load_nx(tile + gridDim.x);
+      if (tile + gridDim.x < ntl) load_nx(tile + gridDim.x);
       ok = wait_ld(s);   // this tile's X image
       fence_proxy_async();
       if (!sync_ok(s, ok)) break;
       {   // the other X buffer was last read by the previous tile's MMAs, which have completed
         const size_t nxt = tile + gridDim.x;
-        if (nxt < a.tiles) load2(s, xs0 + (buf ^ 1) * G::IMG, a.x + nxt * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
+        if (nxt < ntl) load2(s, xs0 + (buf ^ 1) * G::IMG, a.x + nxt * (size_t)G::IMG, G::IMG, 0, nullptr, 0);
       }
       if (threadIdx.x == 0) {
         tc_fence_after();
@@ -1036,6 +1051,7 @@ struct A2Args {
   const float *dxm;               // FP32 [tiles*128][D] (dX')
   float *dxo;                     // FP32 out: dX at the layer input
   size_t tiles;
+  const int64_t *dB;              // device row count (null: B and every tile); B and tiles are then bounds
   int n, ts, embed_grad;
   const uint32_t *sig, *sigp;     // configurations (for the embedding gradient)
   size_t B;
@@ -1074,9 +1090,10 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
   }
   bool ok = wait_ld(s);
   const int n = a.n, nvalid = a.ts * n, tc = a.ts / 2;
+  const size_t ntl = tiles_now(a.dB, a.tiles, tc), Bn = rows_now(a.dB, a.B);
   bool first = true;
   if (sync_ok(s, ok)) {
-    if ((size_t)blockIdx.x < a.tiles)
+    if ((size_t)blockIdx.x < ntl)
       load2(s, xr0, a.x + blockIdx.x * (size_t)G::IMG, G::IMG, dq0, a.dqkv + blockIdx.x * (size_t)G::QIMG, G::QIMG);
     float4 nx[QC / 4];   // this thread's dX' of the coming tile
     auto load_nx = [&](size_t t) {
@@ -1084,9 +1101,9 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
 #pragma unroll
       for (int j = 0; j < QC / 4; ++j) nx[j] = src[j];
     };
-    if ((size_t)blockIdx.x < a.tiles) load_nx(blockIdx.x);
+    if ((size_t)blockIdx.x < ntl) load_nx(blockIdx.x);
     int buf = 0;
-    for (size_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, buf ^= 1) {
+    for (size_t tile = blockIdx.x; tile < ntl; tile += gridDim.x, buf ^= 1) {
       const uint32_t dq = dq0 + buf * G::QIMG, xr = xr0 + buf * G::IMG;
       const size_t rg = (tile * kRows + row) * (size_t)D + quarter * QC;
       float base[QC];
@@ -1095,7 +1112,7 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
         const float4 q = nx[j / 4];
         base[j] = q.x; base[j + 1] = q.y; base[j + 2] = q.z; base[j + 3] = q.w;
       }
-      if (tile + gridDim.x < a.tiles) load_nx(tile + gridDim.x);
+      if (tile + gridDim.x < ntl) load_nx(tile + gridDim.x);
       ok = wait_ld(s);   // this tile's X and [dQ dK dV] images
       if (!sync_ok(s, ok)) break;
       if (kF16) {   // BF16 copy of the X image (same canonical layout); its last reader, the previous tile's
@@ -1118,7 +1135,7 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
       }
       {   // the other buffers were last read by the previous tile's MMAs, which have completed
         const size_t nxt = tile + gridDim.x;
-        if (nxt < a.tiles)
+        if (nxt < ntl)
           load2(s, xr0 + (buf ^ 1) * G::IMG, a.x + nxt * (size_t)G::IMG, G::IMG, dq0 + (buf ^ 1) * G::QIMG,
                 a.dqkv + nxt * (size_t)G::QIMG, G::QIMG);
       }
@@ -1190,7 +1207,7 @@ __global__ void __launch_bounds__(kA2Threads, 1) k_bwd_attn2(A2Args a) {
       if (a.embed_grad && a.jac.nvirt && row < nvalid) {   // VJP mode: k_embed_grad after the launch
         const int sqn = row / n, i = row % n;
         const size_t b = tile * tc + (sqn >> 1);
-        if (b < a.B) {
+        if (b < Bn) {
           const uint32_t w1 = (sqn & 1) ? a.sigp[b] : a.sig[b];
           const uint32_t w2 = (sqn & 1) ? a.sig[b] : a.sigp[b];
           const int pat = embed_pattern(0, w1, w2, i, n);
@@ -1247,9 +1264,10 @@ __global__ void k_pack_nt(const float *__restrict__ W, int ldw, int col0, int K,
 // first layer; the exact power of two is undone on every output.
 __global__ void __launch_bounds__(1024) k_cot_scale(const float2 *__restrict__ cot, size_t B,
                                                      const float *__restrict__ Wh, int D, int n,
-                                                     float *__restrict__ scale) {
+                                                     float *__restrict__ scale, const int64_t *dB) {
   __shared__ float red[32];
   float m = 0.f, h = 0.f;
+  B = rows_now(dB, B);
   for (size_t b = threadIdx.x; b < B; b += blockDim.x) {
     const float2 c = cot[b];
     m = fmaxf(m, fmaxf(fabsf(c.x), fabsf(c.y)));   // a NaN operand is dropped by fmaxf; caught downstream
@@ -1363,14 +1381,15 @@ namespace TDO_BWNS {
 __global__ void __launch_bounds__(256) k_embed_grad(const float *__restrict__ dX, const uint32_t *__restrict__ sig,
                                                     const uint32_t *__restrict__ sigp, size_t B, int n, int ts,
                                                     size_t tiles, float *__restrict__ g, size_t g_stride,
-                                                    long long off_e) {
+                                                    long long off_e, const int64_t *dB) {
   constexpr int D = 64, CG = D / 4, SLOTS = 256 / CG;
   __shared__ float4 red[SLOTS][4][CG];
   const int cg = threadIdx.x % CG, slot = threadIdx.x / CG, tc = ts / 2, nvalid = ts * n;
   float4 acc[4];
 #pragma unroll
   for (int p = 0; p < 4; ++p) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const size_t rows = tiles * kRows;
+  const size_t rows = tiles_now(dB, tiles, tc) * kRows;
+  B = rows_now(dB, B);
   // each block streams one contiguous range of rows (UNR * SLOTS rows = 16 KB per iteration); UNR rows per
   // thread and iteration, all loads first: enough bytes in flight to stream dX
   constexpr int UNR = 4;
@@ -1446,8 +1465,9 @@ namespace TDO_BWNS {
 // the block's gradient copy.  (A sum over every connected row cancels heavily: summing the 16-bit image
 // would leave the rounding of single rows in it.)
 __global__ void __launch_bounds__(256) k_db2_rows(const float *__restrict__ dX, size_t rows, int D, float *g,
-                                                  size_t g_stride, long long off) {
+                                                  size_t g_stride, long long off, const int64_t *dB, int tc) {
   __shared__ double red[256][4];
+  rows = tiles_now(dB, rows / kRows, tc) * kRows;
   const int tpr = D / 4, groups = 256 / tpr, c4 = threadIdx.x % tpr, grp = threadIdx.x / tpr;
   double a[4] = {0.0, 0.0, 0.0, 0.0};
   if (grp < groups) {
@@ -1480,8 +1500,10 @@ __global__ void __launch_bounds__(256) k_db2_rows(const float *__restrict__ dX, 
 // F_o cotangents of both orders, dF [Bpad][4] (zero beyond B).  A grid of blocks, each summing its range
 // of configurations in FP32 runs of 64 added in FP64, then adding its own Wh S into copy blockIdx % 16.
 __global__ void __launch_bounds__(256) k_db2_head(const float *__restrict__ dF, size_t Bpad, const float *__restrict__ Wh,
-                                                  int D, float *g, size_t g_stride, long long off) {
+                                                  int D, float *g, size_t g_stride, long long off, const int64_t *dB,
+                                                  int tc) {
   __shared__ double red[2][256];
+  Bpad = tiles_now(dB, Bpad / tc, tc) * tc;
   double s0 = 0.0, s1 = 0.0;
   const size_t stride = gridDim.x * (size_t)blockDim.x;
   size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -1540,7 +1562,7 @@ cudaError_t launch_jac_virtual(const uint32_t *sig, const uint32_t *sigp, size_t
 cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, const BwdTcLayer *views, const BwdTcBuffers &bf,
                          const uint32_t *sig, const uint32_t *sigp, size_t B, const float2 *cot, float *gacc,
                          size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st,
-                         const BwdTcJac *jac) {
+                         const BwdTcJac *jac, const int64_t *dB) {
   using namespace tdo::TDO_BWNS;
   const int n_ = m.n_sites, tc_ = tdo::seqs_per_tile(n_) / 2;
   JacOut jo{nullptr, nullptr, nullptr, 0, 0, nullptr, tc_, 2 * n_};
@@ -1554,9 +1576,9 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
   const long long off_e = fo[0], off_wh = fo[1 + 8 * TDO_MAX_LAYERS], off_bh = fo[2 + 8 * TDO_MAX_LAYERS];
   cudaError_t e;
   {
-    k_cot_scale<<<1, 1024, 0, st>>>(cot, B, m.Wh, D, n, bf.cscale);
+    k_cot_scale<<<1, 1024, 0, st>>>(cot, B, m.Wh, D, n, bf.cscale, dB);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    HeadArgs h{cot, bf.cscale, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, gacc, g_stride, off_wh, off_bh, D, jo};
+    HeadArgs h{cot, bf.cscale, bf.f, bf.h, m.Wh, bf.dF, B, Bpad, dB, tc, gacc, g_stride, off_wh, off_bh, D, jo};
     if (jac) {
       const unsigned grid = (unsigned)((Bpad + 255) / 256 < 1024 ? (Bpad + 255) / 256 : 1024);
       k_head_bwd<<<grid ? grid : 1, 256, (2 * D + 2) * sizeof(float), st>>>(h);
@@ -1566,7 +1588,7 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
     }
     if (m.ffn == 0)   // with an MLP the last layer's MLP passes form this dX from dF themselves
       k_head_dx<<<(unsigned)(tiles * kRows * D / 256 < 65535 * 8 ? (tiles * kRows * D + 255) / 256 : 65535 * 8), 256,
-                  0, st>>>(bf.dF, m.Wh, D, n, ts, tiles, bf.dxa);
+                  0, st>>>(bf.dF, m.Wh, D, n, ts, tiles, bf.dxa, dB);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const int grid = (int)(tiles < (size_t)n_sm ? tiles : (size_t)n_sm);
@@ -1595,6 +1617,7 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
         ma.dxo = bf.dxa;
         ma.dxm = bf.dxb;
         ma.tiles = tiles;
+        ma.dB = dB;
         ma.do_db2 = hb == 0 && jac;   // VJP mode: db2 from the FP32 dX (below)
         ma.g = gacc;
         ma.g_stride = g_stride;
@@ -1616,9 +1639,9 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
       dxmid = bf.dxb;
       if (!jac) {   // db2 of this layer from FP32 data (its MLP output's dX: the head's for the last layer)
         if (l == m.layers - 1)
-          k_db2_head<<<(unsigned)(2 * n_sm), 256, 0, st>>>(bf.dF, Bpad, m.Wh, D, gacc, g_stride, b2[l]);
+          k_db2_head<<<(unsigned)(2 * n_sm), 256, 0, st>>>(bf.dF, Bpad, m.Wh, D, gacc, g_stride, b2[l], dB, tc);
         else
-          k_db2_rows<<<(unsigned)(4 * n_sm), 256, 0, st>>>(bf.dxa, tiles * kRows, D, gacc, g_stride, b2[l]);
+          k_db2_rows<<<(unsigned)(4 * n_sm), 256, 0, st>>>(bf.dxa, tiles * kRows, D, gacc, g_stride, b2[l], dB, tc);
       }
     }
     A1Args a1;
@@ -1628,6 +1651,7 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
     a1.dxm = dxmid;
     a1.dqkv = bf.dqkv;
     a1.tiles = tiles;
+    a1.dB = dB;
     a1.n = n;
     a1.ts = ts;
     a1.heads = m.heads;
@@ -1645,6 +1669,7 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
     a2.dxm = dxmid;
     a2.dxo = bf.dxa;
     a2.tiles = tiles;
+    a2.dB = dB;
     a2.n = n;
     a2.ts = ts;
     a2.embed_grad = l == 0;
@@ -1661,7 +1686,7 @@ cudaError_t TDO_OPFN(launch_bwdtc)(const DevModel &m, const DevModelBF16 &mb, co
     a2.jac = jo;
     k_bwd_attn2<D><<<grid, kA2Threads, A2Geo<D>::BYTES, st>>>(a2);
     if (l == 0 && !jo.nvirt)
-      k_embed_grad<<<(unsigned)(2 * n_sm), 256, 0, st>>>(bf.dxa, sig, sigp, B, n, ts, tiles, gacc, g_stride, off_e);
+      k_embed_grad<<<(unsigned)(2 * n_sm), 256, 0, st>>>(bf.dxa, sig, sigp, B, n, ts, tiles, gacc, g_stride, off_e, dB);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

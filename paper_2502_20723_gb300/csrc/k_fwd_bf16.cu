@@ -98,6 +98,7 @@ struct FwdStore {
   float *H;        // [tiles][ts][D] pooled vectors of the tile's sequences
   float *F;        // [tiles][ts][2] head outputs (F0, F1)
   size_t tiles;
+  const int64_t *dB;   // row count on the device, read at launch (null: the launch's B); B is then a bound
 };
 
 struct Ctl {
@@ -736,6 +737,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_bf16(DevModel m, DevModelBF
   uint32_t *cp = cs + 64;
   float2 *res = reinterpret_cast<float2 *>(sm + G::M_OFF + 16 + 8 + 512 + 1024);
   const int ts = seqs_per_tile(m.n_sites), tc = ts / 2;
+  if (st.dB) B = min(B, (size_t)*st.dB);
   const size_t ntiles = (B + tc - 1) / tc;
   for (size_t tile = blockIdx.x; tile < ntiles && !c.bad; tile += gridDim.x) {
     if (threadIdx.x < tc) {
@@ -800,7 +802,8 @@ template <int D, int HD>
 __global__ void __launch_bounds__(kThreads, 2)
     k_sample_bf16(DevModel m, DevModelBF16 mb, size_t n_chains, size_t n_sweeps, uint64_t seed, uint64_t counter,
                   uint32_t *__restrict__ sig, uint32_t *__restrict__ sigp, uint32_t *__restrict__ ssig,
-                  uint32_t *__restrict__ ssigp, unsigned long long *accepted, int *err, int diag) {
+                  uint32_t *__restrict__ ssigp, unsigned long long *accepted, int *err, int diag,
+                  const uint64_t *dcounter) {
   extern __shared__ __align__(1024) uint8_t sm[];
   using G = Geo<D>;
   Ctl c;
@@ -811,6 +814,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int n = m.n_sites;
   const int ts = seqs_per_tile(n), tc = ts / 2;
   const size_t ntiles = (n_chains + tc - 1) / tc;
+  if (dcounter) counter += *dcounter;   // a replayed graph: the step's counter is in device memory
   unsigned long long acc_count = 0;
   for (size_t tile = blockIdx.x; tile < ntiles && !c.bad; tile += gridDim.x) {
     const size_t ch = tile * tc + threadIdx.x;
@@ -1055,9 +1059,9 @@ static cudaError_t fwd_bf16_impl(const DevModel &m, const DevModelBF16 &mb, cons
 cudaError_t TDO_OPFN(launch_fwd_bf16_store)(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                                   const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
                                   cudaStream_t st, uint8_t *x_img, uint8_t *xmid_img, float *h, float *f,
-                                  size_t tiles) {
+                                  size_t tiles, const int64_t *dB) {
   if (B == 0) return cudaSuccess;
-  tdo::TDO_OPNS::FwdStore fs{x_img, xmid_img, h, f, tiles};
+  tdo::TDO_OPNS::FwdStore fs{x_img, xmid_img, h, f, tiles, dB};
   if (m.d == 64 && m.dh == 8) return fwd_bf16_impl<64, 8>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, fs);
   if (m.d == 64 && m.dh == 16) return fwd_bf16_impl<64, 16>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, fs);
   if (m.d == 32 && m.dh == 8) return fwd_bf16_impl<32, 8>(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, fs);
@@ -1075,7 +1079,7 @@ cudaError_t launch_wait_probe(int *err_flag, long long spin, cudaStream_t st) {
 cudaError_t TDO_OPFN(launch_fwd_bf16)(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig, const uint32_t *sigp,
                             size_t B, float2 *logrho, int *err_flag, int n_sm, cudaStream_t st) {
   return TDO_OPFN(launch_fwd_bf16_store)(m, mb, sig, sigp, B, logrho, err_flag, n_sm, st, nullptr, nullptr, nullptr,
-                                         nullptr, 0);
+                                         nullptr, 0, nullptr);
 }
 
 template <int D, int HD>
@@ -1115,7 +1119,7 @@ template <int D, int HD>
 static cudaError_t sample_bf16_impl(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
                                     uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
                                     uint32_t *ssigp, unsigned long long *accepted, int *err, int diag, int n_sm,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, const uint64_t *dcounter) {
   using namespace tdo::TDO_OPNS;
   const int bytes = Geo<D>::BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_sample_bf16<D, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1128,19 +1132,19 @@ static cudaError_t sample_bf16_impl(const DevModel &m, const DevModelBF16 &mb, s
   size_t grid = (size_t)n_sm * per_sm;
   if (grid > ntiles) grid = ntiles;
   k_sample_bf16<D, HD><<<(unsigned)grid, kThreads, bytes, st>>>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp,
-                                                               ssig, ssigp, accepted, err, diag);
+                                                               ssig, ssigp, accepted, err, diag, dcounter);
   return cudaGetLastError();
 }
 
 cudaError_t TDO_OPFN(launch_sample_bf16)(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
                                uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
                                uint32_t *ssigp, unsigned long long *accepted, int *err_flag, int diag, int n_sm,
-                               cudaStream_t st) {
+                               cudaStream_t st, const uint64_t *dcounter) {
   if (n_chains == 0) return cudaSuccess;
 #define TDO_SAMPLE_BF16(DD, HH)                                                                                   \
   if (m.d == DD && m.dh == HH)                                                                                     \
     return sample_bf16_impl<DD, HH>(m, mb, n_chains, n_sweeps, seed, counter, sig, sigp, ssig, ssigp, accepted,     \
-                                    err_flag, diag, n_sm, st);
+                                    err_flag, diag, n_sm, st, dcounter);
   TDO_SAMPLE_BF16(64, 8)
   TDO_SAMPLE_BF16(64, 16)
   TDO_SAMPLE_BF16(32, 8)

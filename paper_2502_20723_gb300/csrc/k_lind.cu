@@ -213,7 +213,9 @@ __global__ void k_params_f32(const double *__restrict__ theta, size_t P, const l
   }
 }
 
-__global__ void k_axpy(double *__restrict__ theta, const double *__restrict__ delta, double lr, size_t P) {
+__global__ void k_axpy(double *__restrict__ theta, const double *__restrict__ delta, double lr, size_t P,
+                       const int *__restrict__ gate) {
+  if (gate && !*gate) return;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x)
     theta[k] -= lr * delta[k];
 }
@@ -223,7 +225,9 @@ __global__ void k_axpy(double *__restrict__ theta, const double *__restrict__ de
 // theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).  FP64 throughout.
 __global__ void k_adam(double *__restrict__ theta, const double *__restrict__ delta, double *__restrict__ m,
                        double *__restrict__ v, size_t P, double lr, double b1, double b2, double eps, double c1,
-                       double c2) {
+                       double c2, const int *__restrict__ gate, const double *__restrict__ dc) {
+  if (gate && !*gate) return;
+  if (dc) { c1 = dc[0]; c2 = dc[1]; }
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
     const double d = delta[k];
     const double mk = b1 * m[k] + (1.0 - b1) * d;
@@ -232,6 +236,15 @@ __global__ void k_adam(double *__restrict__ theta, const double *__restrict__ de
     v[k] = vk;
     theta[k] -= lr * (mk / c1) / (sqrt(vk / c2) + eps);
   }
+}
+
+// Whether a replayed step may update the parameters: the CG solve ended without a breakdown or a non-finite
+// value (outcome 0 or 1), L_loc was finite and no bounded wait gave up -- the conditions under which the
+// step, run call by call, reaches its update.
+__global__ void k_step_gate(const double *__restrict__ outcome, const int *__restrict__ nonfinite,
+                            const int *__restrict__ err, int *__restrict__ ok) {
+  const double o = *outcome;
+  *ok = (o == 0.0 || o == 1.0) && *nonfinite == 0 && (err == nullptr || *err == 0);
 }
 
 // Ragged batches: counts of each chain length (shared-memory histogram per block, then global atomics).
@@ -356,14 +369,21 @@ cudaError_t launch_unpermute(const float2 *in, const uint32_t *perm, size_t B, f
   return cudaGetLastError();
 }
 
-cudaError_t launch_axpy_update(double *theta, const double *delta, double lr, size_t P, cudaStream_t st) {
-  tdo::k_axpy<<<grid_for(P, 256), 256, 0, st>>>(theta, delta, lr, P);
+cudaError_t launch_axpy_update(double *theta, const double *delta, double lr, size_t P, cudaStream_t st,
+                               const int *gate) {
+  tdo::k_axpy<<<grid_for(P, 256), 256, 0, st>>>(theta, delta, lr, P, gate);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adam_update(double *theta, const double *delta, double *m, double *v, size_t P, long long t,
-                               double lr, double b1, double b2, double eps, cudaStream_t st) {
+                               double lr, double b1, double b2, double eps, cudaStream_t st, const int *gate,
+                               const double *dc) {
   const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
-  tdo::k_adam<<<grid_for(P, 256), 256, 0, st>>>(theta, delta, m, v, P, lr, b1, b2, eps, c1, c2);
+  tdo::k_adam<<<grid_for(P, 256), 256, 0, st>>>(theta, delta, m, v, P, lr, b1, b2, eps, c1, c2, gate, dc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_gate(const double *outcome, const int *nonfinite, const int *err, int *ok, cudaStream_t st) {
+  tdo::k_step_gate<<<1, 1, 0, st>>>(outcome, nonfinite, err, ok);
   return cudaGetLastError();
 }

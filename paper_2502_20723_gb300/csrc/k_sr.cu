@@ -35,8 +35,9 @@ __device__ __forceinline__ void load4(const uint32_t *p, float2 (&c)[4]) {
 }
 
 enum {
-  S_RZ = 0, S_BN, S_AL, S_RN, S_DONE, S_IT, S_TOL, S_PAP, S_CR, S_CI, S_TR, S_TI, S_TT, S_COUNT
+  S_RZ = 0, S_BN, S_AL, S_RN, S_DONE, S_IT, S_TOL, S_PAP, S_CR, S_CI, S_TR, S_TI, S_TT, S_RESTART, S_COUNT
 };
+// S_RESTART (graph mode): 0 none, 1 a restart from x = 0 is pending, 2 the solve was restarted
 // S_DONE: 1 converged, 2 breakdown (p . S' p not positive: p = 0 before convergence), 3 a non-finite value
 // (in the right-hand side, the log-derivatives' moments or a product)
 enum { SR_CONVERGED = 1, SR_BREAKDOWN = 2, SR_NONFINITE = 3 };
@@ -781,8 +782,10 @@ __global__ void k_sr_p(size_t P, double *__restrict__ p, const double *__restric
 __global__ void k_sr_init(size_t P, const double *__restrict__ rhs, const double *__restrict__ x0,
                           const double *__restrict__ Ap, double *__restrict__ x, double *__restrict__ r,
                           double *__restrict__ z, double *__restrict__ p, const double *__restrict__ diag,
-                          double *__restrict__ part, double *__restrict__ part2, double *__restrict__ part3) {
+                          double *__restrict__ part, double *__restrict__ part2, double *__restrict__ part3,
+                          const double *gate) {
   __shared__ double sh[32];
+  if (gate && gate[S_RESTART] != 1.0) return;   // graph mode: only a pending restart runs it
   double rr = 0.0, rz = 0.0, bb = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
     const double b = rhs[k];
@@ -803,8 +806,10 @@ __global__ void k_sr_init(size_t P, const double *__restrict__ rhs, const double
 }
 
 __global__ void k_sr_init_scalars(const double *__restrict__ part, const double *__restrict__ part2,
-                                  const double *__restrict__ part3, int nb, double tol, double *__restrict__ sc) {
+                                  const double *__restrict__ part3, int nb, double tol, double *__restrict__ sc,
+                                  int gated) {
   __shared__ double sh[32];
+  if (gated && sc[S_RESTART] != 1.0) return;
   const double rr = sum_parts(part, nb, sh);
   const double rz = sum_parts(part2, nb, sh);
   const double bb = sum_parts(part3, nb, sh);
@@ -818,7 +823,22 @@ __global__ void k_sr_init_scalars(const double *__restrict__ part, const double 
     sc[S_PAP] = 0.0;
     if (!isfinite(rr) || !isfinite(rz) || !isfinite(bb)) sc[S_DONE] = SR_NONFINITE;
     else sc[S_DONE] = (rr <= tol * tol * bb) ? SR_CONVERGED : 0.0;
+    if (gated) sc[S_RESTART] = 2.0;
   }
+}
+
+// Last kernel of a CG iteration in graph mode: another iteration while the solve is neither done nor at
+// max_iter.  A breakdown or a non-finite value with a warm start (*warm != 0) and no restart yet marks a
+// restart from x = 0 as pending and asks for one more pass, whose first kernels re-initialise.
+__global__ void k_sr_cond(cudaGraphConditionalHandle h, double *__restrict__ sc, int max_iter, const int *warm) {
+  if (threadIdx.x != 0) return;
+  const double done = sc[S_DONE];
+  bool more = done == 0.0 && sc[S_IT] < (double)max_iter;
+  if ((done == SR_BREAKDOWN || done == SR_NONFINITE) && *warm && sc[S_RESTART] == 0.0) {
+    sc[S_RESTART] = 1.0;
+    more = true;
+  }
+  cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 __global__ void k_sr_clear(double *__restrict__ sc) {
@@ -1050,8 +1070,8 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const 
   nl += 3;
   cudaError_t e;
   if (x0 && (e = mv(x0)) != cudaSuccess) return e;
-  k_sr_init<<<nb, kSrBlock, 0, st>>>(P, rhs, x0, q.Ap, x, q.r, q.z, q.p, q.diag, q.part, q.part2, q.part3);
-  k_sr_init_scalars<<<1, 1024, 0, st>>>(q.part, q.part2, q.part3, nb, tol, q.sc);
+  k_sr_init<<<nb, kSrBlock, 0, st>>>(P, rhs, x0, q.Ap, x, q.r, q.z, q.p, q.diag, q.part, q.part2, q.part3, nullptr);
+  k_sr_init_scalars<<<1, 1024, 0, st>>>(q.part, q.part2, q.part3, nb, tol, q.sc, 0);
   nl += 2;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1095,6 +1115,83 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const 
   if (last_pap) *last_pap = h[S_PAP];
   return cudaSuccess;
 }
+
+// Records a while loop into the graph being captured on st: a conditional node (its condition 1 at every
+// launch of the graph when `initial`, else 0), whose body `body(stream, handle)` records on a stream of its
+// own; the capture on st then continues after the node.
+template <typename F>
+static cudaError_t capture_while(cudaStream_t st, unsigned initial, F &&body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureUnmatched;
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, initial, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np)) != cudaSuccess) return e;
+  cudaStream_t side;
+  if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(side, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    const cudaError_t eb = body(side, h);
+    cudaGraph_t out;
+    e = cudaStreamEndCapture(side, &out);
+    if (eb != cudaSuccess) e = eb;
+  }
+  cudaStreamDestroy(side);
+  if (e != cudaSuccess) return e;
+  return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// The CG solve recorded into the graph being captured on st.  The same launches as sr_cg_t with a warm
+// start from x (zero when there is no previous solution), the iterations in a while node: each pass runs
+// the restart kernels (no-ops unless a restart from x = 0 is pending), one iteration, and k_sr_cond.
+// *warm (device int) allows the restart, as a warm start does in sr_cg_t's caller.
+template <typename OT>
+static cudaError_t sr_cg_capture_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const double *rhs, double *x,
+                                   double shift, double tol, int max_iter, double *work, int product_mode,
+                                   const int *warm, int *err, int *shape, cudaStream_t st) {
+  SrPtrs q = sr_carve(work, Ns, P);
+  FusedPlan pl;
+  if constexpr (sizeof(OT) == 4)
+    if (product_mode == 1) pl = fused_plan(O2, Ns, P, ldo);
+  if (shape) { shape[0] = pl.C > 0 ? 1 : 0; shape[1] = pl.C; shape[2] = pl.G; }
+  const int nb = sr_blocks(P);
+  auto mv = [&](const double *v, cudaStream_t s) -> cudaError_t {
+    if constexpr (sizeof(OT) == 4)
+      if (pl.C > 0) return matvec_fused(O2, Ns, P, ldo, v, shift, q, nb, pl, err, s);
+    matvec(O2, Ns, P, ldo, v, shift, q, nb, s);
+    return cudaSuccess;
+  };
+  moments(O2, Ns, P, ldo, shift, q, nb, st);
+  k_sr_clear<<<1, 32, 0, st>>>(q.sc);
+  cudaError_t e;
+  if ((e = mv(x, st)) != cudaSuccess) return e;
+  k_sr_init<<<nb, kSrBlock, 0, st>>>(P, rhs, x, q.Ap, x, q.r, q.z, q.p, q.diag, q.part, q.part2, q.part3, nullptr);
+  k_sr_init_scalars<<<1, 1024, 0, st>>>(q.part, q.part2, q.part3, nb, tol, q.sc, 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return capture_while(st, max_iter > 0 ? 1u : 0u, [&](cudaStream_t s, cudaGraphConditionalHandle h) -> cudaError_t {
+    k_sr_init<<<nb, kSrBlock, 0, s>>>(P, rhs, nullptr, q.Ap, x, q.r, q.z, q.p, q.diag, q.part, q.part2, q.part3, q.sc);
+    k_sr_init_scalars<<<1, 1024, 0, s>>>(q.part, q.part2, q.part3, nb, tol, q.sc, 1);
+    cudaError_t ei = mv(q.p, s);
+    if (ei != cudaSuccess) return ei;
+    k_sr_alpha<<<1, 1024, 0, s>>>(q.part, nb, Ns, shift, q.sc);
+    k_sr_xr<<<nb, kSrBlock, 0, s>>>(P, x, q.r, q.z, q.p, q.Ap, q.diag, q.part, q.part2, q.sc);
+    k_sr_beta<<<1, 1024, 0, s>>>(q.part, q.part2, nb, q.sc);
+    k_sr_p<<<nb, kSrBlock, 0, s>>>(P, q.p, q.z, q.sc);
+    k_sr_cond<<<1, 32, 0, s>>>(h, q.sc, max_iter, warm);
+    return cudaGetLastError();
+  });
+}
 }  // namespace tdo
 
 // mv_ev (optional): mv_cap event pairs recorded around the S' v launches; *mv_used = pairs recorded.
@@ -1114,6 +1211,41 @@ cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, size_t ld
                         resid, outcome, last_pap, launches, mv_ev, mv_cap, mv_used, product_mode, err, shape, st);
   return tdo::sr_cg_t(reinterpret_cast<const float2 *>(O), Ns, P, ldo, rhs, x0, shift, tol, max_iter, x, work, iters,
                       resid, outcome, last_pap, launches, mv_ev, mv_cap, mv_used, product_mode, err, shape, st);
+}
+
+// Graph mode: the solve of sr_cg_impl recorded into the graph being captured on st (see sr_cg_capture_t);
+// warm start from x, restart from x = 0 after a breakdown or a non-finite value when *warm.  The result
+// is read after a launch of the graph by sr_cg_result.
+cudaError_t sr_cg_capture(const void *O, int o_bf16, size_t Ns, size_t P, size_t ldo, const double *rhs, double *x,
+                          double shift, double tol, int max_iter, double *work, int product_mode, const int *warm,
+                          int *err, int *shape, cudaStream_t st) {
+  if (o_bf16)
+    return tdo::sr_cg_capture_t(reinterpret_cast<const uint32_t *>(O), Ns, P, ldo, rhs, x, shift, tol, max_iter, work,
+                                product_mode, warm, err, shape, st);
+  return tdo::sr_cg_capture_t(reinterpret_cast<const float2 *>(O), Ns, P, ldo, rhs, x, shift, tol, max_iter, work,
+                              product_mode, warm, err, shape, st);
+}
+
+// The outcome of the last solve on work, as sr_cg_impl reports it, and whether it was restarted
+// (synchronises st).
+cudaError_t sr_cg_result(double *work, size_t Ns, size_t P, int *iters, double *resid, int *outcome,
+                         double *last_pap, int *restarted, cudaStream_t st) {
+  tdo::SrPtrs q = tdo::sr_carve(work, Ns, P);
+  double h[tdo::S_COUNT];
+  cudaError_t e = cudaMemcpyAsync(h, q.sc, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  if (iters) *iters = (int)h[tdo::S_IT];
+  if (resid) *resid = h[tdo::S_BN] > 0 ? sqrt(h[tdo::S_RN] / h[tdo::S_BN]) : 0.0;
+  if (outcome) *outcome = (int)h[tdo::S_DONE];
+  if (last_pap) *last_pap = h[tdo::S_PAP];
+  if (restarted) *restarted = h[tdo::S_RESTART] == 2.0 ? 1 : 0;
+  return cudaSuccess;
+}
+
+// Device address of the solve's outcome slot on work (0 max_iter, 1 converged, 2 breakdown, 3 non-finite).
+const double *sr_outcome_slot(double *work, size_t Ns, size_t P) {
+  return tdo::sr_carve(work, Ns, P).sc + tdo::S_DONE;
 }
 
 // One product (Re S + shift I) v with O as BF16 pairs [Ns][ldo] (ldo >= P), v and Ap FP64 [P] on the device.

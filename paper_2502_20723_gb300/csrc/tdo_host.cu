@@ -44,6 +44,12 @@ cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, size_t ld
                        int mv_cap, int *mv_used, int product_mode, int *err, int *shape, cudaStream_t st);
 cudaError_t launch_params_f32(const double *theta, size_t P, const long long *tab, int n_tensors,
                               float *dst, cudaStream_t st);
+cudaError_t sr_cg_capture(const void *O, int o_bf16, size_t Ns, size_t P, size_t ldo, const double *rhs, double *x,
+                          double shift, double tol, int max_iter, double *work, int product_mode, const int *warm,
+                          int *err, int *shape, cudaStream_t st);
+cudaError_t sr_cg_result(double *work, size_t Ns, size_t P, int *iters, double *resid, int *outcome,
+                         double *last_pap, int *restarted, cudaStream_t st);
+const double *sr_outcome_slot(double *work, size_t Ns, size_t P);
 size_t bf16_packed_bytes(const DevModel &m);
 struct BwdTcLayer {
   const uint8_t *w1t[2], *w2r[2], *w1r[2];
@@ -71,19 +77,19 @@ cudaError_t launch_jac_virtual(const uint32_t *sig, const uint32_t *sigp, size_t
 cudaError_t launch_bwdtc(const DevModel &m, const DevModelBF16 &mb, const BwdTcLayer *views, const BwdTcBuffers &bf,
                          const uint32_t *sig, const uint32_t *sigp, size_t B, const float2 *cot, float *gacc,
                          size_t g_stride, const long long *fo, int *err, int n_sm, cudaStream_t st,
-                         const BwdTcJac *jac = nullptr);
+                         const BwdTcJac *jac = nullptr, const int64_t *dB = nullptr);
 cudaError_t launch_bwdtc_f16(const DevModel &m, const DevModelBF16 &mb, const BwdTcLayer *views,
                              const BwdTcBuffers &bf, const uint32_t *sig, const uint32_t *sigp, size_t B,
                              const float2 *cot, float *gacc, size_t g_stride, const long long *fo, int *err, int n_sm,
-                             cudaStream_t st, const BwdTcJac *jac = nullptr);
+                             cudaStream_t st, const BwdTcJac *jac = nullptr, const int64_t *dB = nullptr);
 cudaError_t launch_fwd_bf16_store(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                                   const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
                                   cudaStream_t st, uint8_t *x_img, uint8_t *xmid_img, float *h, float *f,
-                                  size_t tiles);
+                                  size_t tiles, const int64_t *dB = nullptr);
 cudaError_t launch_fwd_bf16_store_f16(const DevModel &m, const DevModelBF16 &mb, const uint32_t *sig,
                                       const uint32_t *sigp, size_t B, float2 *logrho, int *err_flag, int n_sm,
                                       cudaStream_t st, uint8_t *x_img, uint8_t *xmid_img, float *h, float *f,
-                                      size_t tiles);
+                                      size_t tiles, const int64_t *dB = nullptr);
 // A tensor-core launcher of the context's operand type: fn (BF16) or fn_f16 (FP16).
 #define TC_LAUNCH(c, fn, ...) ((c)->f16 ? fn##_f16(__VA_ARGS__) : fn(__VA_ARGS__))
 // Evaluation-only launches (no parked activations): the E4M3 kernels and weights in FP8 contexts.
@@ -94,11 +100,16 @@ namespace {
 
 thread_local std::string g_create_error;
 
+// Bumped by every (re)allocation or release of a device buffer: a recorded step graph holds buffer
+// addresses, so it is recorded again when this has moved since.
+unsigned long long g_buf_gen = 0;
+
 struct DBuf {
   void *p = nullptr;
   size_t bytes = 0;
   cudaError_t ensure(size_t need) {
     if (need <= bytes) return cudaSuccess;
+    ++g_buf_gen;
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
@@ -109,7 +120,16 @@ struct DBuf {
     return cudaSuccess;
   }
   template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
-  void release() { if (p) cudaFree(p); p = nullptr; bytes = 0; }
+  void release() { if (p) { cudaFree(p); ++g_buf_gen; } p = nullptr; bytes = 0; }
+};
+
+// Per-step values of a replayed step graph, read by its kernels from device memory: the sampler's counter,
+// Adam's bias corrections, whether the solve starts from the previous solution (and may restart), and the
+// update's gate (written by the graph).
+struct StepDev {
+  uint64_t counter;
+  double c1, c2;
+  int warm, ok;
 };
 
 struct TensorLoc { long long flat, pad, size; };
@@ -174,6 +194,17 @@ struct tdo_ctx {
   int last_sr_restarts = 0;     // 1 when the warm-started solve failed and was rerun from x = 0
   int sr_product = TDO_SR_PRODUCT_TWO_PASS;   // or TDO_SR_PRODUCT_ONE_PASS (where the storage allows it)
   int last_sr_shape[3] = {0, 0, 0};   // one pass used, cluster size, clusters (last solve)
+  // whole-step CUDA graph (tdo_set_step_graph): the recorded step, the arguments and settings it was
+  // recorded for, and its per-step values (uploaded from pinned host memory before each launch)
+  bool step_graph = false;
+  bool capturing = false;              // a recording is in progress: no timing events, no host reads
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t gstream = nullptr;      // the graph's own stream (a legacy or per-thread default stream cannot
+  cudaEvent_t gevent = nullptr;        // be captured), ordered after and before the context's stream
+  std::vector<uint64_t> gkey;
+  DBuf gstep;                          // StepDev
+  StepDev *gstep_host = nullptr;       // pinned
+  long long graph_captures = 0, graph_replays = 0;
   // kernel timing (tdo_timing)
   bool timing = false;
   std::vector<TimingRec> trec;
@@ -185,7 +216,7 @@ struct Timed {
   tdo_ctx *c;
   int idx = -1;
   Timed(tdo_ctx *ctx, int group) : c(ctx) {
-    if (!c->timing) return;
+    if (!c->timing || c->capturing) return;
     cudaEvent_t a, b;
     if (c->epool.size() >= 2) { a = c->epool.back(); c->epool.pop_back(); b = c->epool.back(); c->epool.pop_back(); }
     else { cudaEventCreate(&a); cudaEventCreate(&b); }
@@ -447,7 +478,7 @@ static tdo_status refresh_params(tdo_ctx *c) {
 
 // Reports (and clears) a timeout flagged by a tensor-core kernel's bounded waits.
 static tdo_status check_err_flag(tdo_ctx *c) {
-  if (!c->tc) return TDO_OK;
+  if (!c->tc || c->capturing) return TDO_OK;   // a recording step graph reads the flag after its launch
   int f = 0;
   CU(c, cudaMemcpyAsync(&f, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaStreamSynchronize(c->stream));
@@ -587,6 +618,11 @@ extern "C" tdo_status tdo_destroy(tdo_ctx *c) {
                   &c->oref, &c->oref_scratch, &c->jac_vs, &c->jac_vp, &c->jac_vc, &c->jac_lr, &c->obs_rs,
                   &c->obs_rp, &c->obs_lr, &c->obs_part, &c->obs_out, &c->obs_local};
   for (DBuf *b : bufs) b->release();
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
+  if (c->gevent) cudaEventDestroy(c->gevent);
+  c->gstep.release();
+  if (c->gstep_host) cudaFreeHost(c->gstep_host);
   for (auto &r : c->trec) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : c->epool) cudaEventDestroy(e);
   delete c;
@@ -1432,6 +1468,262 @@ extern "C" double tdo_schedule_value(long long step, double v0, long long i_swit
   return v0 * (1.0 + cos(pi * (double)(step - i_switch) / (double)i_decay)) / 2.0 + alpha * v0;
 }
 
+// ----------------------------------------------------------------------------- whole-step graph
+// One optimisation-workflow step (sweeps, connections, L_loc and cost, gradient, log-derivatives, SR solve,
+// update) recorded once into a CUDA graph and replayed.  What the call-by-call step learns on the host
+// in the middle of a step stays on the device: the connected-row count (every buffer and grid is sized for
+// Ns x n_pat rows, and the kernels read the count from the scan's last offset), and the CG's iteration
+// count (a conditional while node).  The sampler's counter and Adam's bias corrections come from device
+// memory, uploaded before each launch; the update is skipped on the device when the solve fails or L_loc
+// is not finite, and the host reports the failure after the launch, as the call-by-call step does.
+
+// Tensor-core buffers of a forward store and its backward over `tiles` tiles.
+static tdo_status graph_alloc_tiles(tdo_ctx *c, size_t tiles) {
+  const int ts = 2 * (128 / (2 * c->n)) < 2 ? 2 : 2 * (128 / (2 * c->n));
+  const size_t D = c->dm.d, img = (size_t)128 * D * 2, L = c->dm.layers;
+  CU(c, c->act_x.ensure(L * tiles * img));
+  CU(c, c->act_xmid.ensure(c->dm.ffn > 0 ? L * tiles * img : 16));
+  CU(c, c->act_h.ensure(sizeof(float) * tiles * ts * D));
+  CU(c, c->act_f.ensure(sizeof(float) * tiles * ts * 2));
+  CU(c, c->act_dF.ensure(sizeof(float) * tiles * ts * 2));
+  CU(c, c->act_dxa.ensure(sizeof(float) * tiles * 128 * D));
+  CU(c, c->act_dxb.ensure(sizeof(float) * tiles * 128 * D));
+  CU(c, c->act_dqkv.ensure(tiles * 128 * 3 * D * 2));
+  return TDO_OK;
+}
+
+// Log-derivative buffers of B samples (jacobian_dev's).
+static tdo_status graph_alloc_jac(tdo_ctx *c, size_t B) {
+  if (bwdtc_jac_supported(c->dm)) {
+    const size_t nv = 2 * B;
+    CU(c, c->jac_vs.ensure(4 * nv));
+    CU(c, c->jac_vp.ensure(4 * nv));
+    CU(c, c->jac_vc.ensure(sizeof(float2) * nv));
+    CU(c, c->jac_lr.ensure(sizeof(float2) * nv));
+    return graph_alloc_tiles(c, tc_tiles(c, nv));
+  }
+  CU(c, c->scratch.ensure(sizeof(float) * bwd32_scratch_floats(c->dm, bwd32_grid(c->dm, B, 1, c->n_sm))));
+  return TDO_OK;
+}
+
+// Every allocation of a recorded step, made before the recording (a recording may not allocate).
+static tdo_status graph_alloc(tdo_ctx *c, size_t Ns, size_t ldo) {
+  const size_t M = (size_t)c->n_pat, R = Ns * M, P = c->P;
+  CU(c, c->conn_cnt.ensure(sizeof(int32_t) * Ns));
+  CU(c, c->conn_sig.ensure(sizeof(uint32_t) * Ns * M));
+  CU(c, c->conn_sigp.ensure(sizeof(uint32_t) * Ns * M));
+  CU(c, c->conn_coef.ensure(sizeof(float2) * Ns * M));
+  CU(c, c->offs.ensure(sizeof(int64_t) * (Ns + 1)));
+  CU(c, c->fsig.ensure(sizeof(uint32_t) * R));
+  CU(c, c->fsigp.ensure(sizeof(uint32_t) * R));
+  CU(c, c->fcoef.ensure(sizeof(float2) * R));
+  CU(c, c->flr.ensure(sizeof(float2) * R));
+  CU(c, c->cot.ensure(sizeof(float2) * R));
+  CU(c, c->lloc.ensure(sizeof(double2) * Ns));
+  CU(c, c->l2.ensure(sizeof(double) * Ns));
+  CU(c, c->stats.ensure(sizeof(double) * 4));
+  TRY(graph_alloc_tiles(c, tc_tiles(c, R)));
+  CU(c, c->gacc.ensure(sizeof(float) * 16 * ((P + 3) / 4 * 4)));
+  CU(c, c->grad.ensure(sizeof(double) * P));
+  CU(c, c->delta.ensure(sizeof(double) * P));
+  CU(c, c->Obuf.ensure(sizeof(uint16_t) * 2 * ldo * Ns));
+  const size_t nref = Ns < 64 ? Ns : 64;
+  if (c->Obuf.bytes < sizeof(float) * 2 * P * nref) CU(c, c->oref_scratch.ensure(sizeof(float) * 2 * P * nref));
+  CU(c, c->oref.ensure(sizeof(float) * 2 * P));
+  TRY(graph_alloc_jac(c, nref));
+  TRY(graph_alloc_jac(c, Ns));
+  CU(c, c->srwork.ensure(sizeof(double) * sr_work_doubles(Ns, P)));
+  CU(c, c->gstep.ensure(sizeof(StepDev)));
+  if (!c->gstep_host) {
+    void *h = nullptr;
+    CU(c, cudaHostAlloc(&h, sizeof(StepDev), cudaHostAllocDefault));
+    c->gstep_host = static_cast<StepDev *>(h);
+  }
+  return TDO_OK;
+}
+
+// The launches of one step, recorded on c->stream (capture in progress; graph_alloc done).
+static tdo_status graph_record(tdo_ctx *c, uint32_t *ds, uint32_t *dp, size_t Ns, size_t n_sweeps, uint64_t seed,
+                               double lr, double shift, size_t ldo) {
+  StepDev *gs = c->gstep.as<StepDev>();
+  const int M = c->n_pat;
+  const size_t R = Ns * (size_t)M, tiles = tc_tiles(c, R), P = c->P;
+  int *err = c->errflag.as<int>();
+  if (n_sweeps > 0)
+    CU(c, EVAL_LAUNCH(c, launch_sample_bf16, Ns, n_sweeps, seed, 0, ds, dp, nullptr, nullptr, nullptr, err, 0, c->n_sm,
+                      c->stream, &gs->counter));
+  CU(c, launch_connections(c->d_pat.as<ConnPattern>(), M, c->d_con.as<ConnContrib>(), ds, dp, Ns,
+                           c->conn_cnt.as<int32_t>(), c->conn_sig.as<uint32_t>(), c->conn_sigp.as<uint32_t>(),
+                           c->conn_coef.as<float2>(), c->stream));
+  CU(c, launch_scan(c->conn_cnt.as<int32_t>(), Ns, c->offs.as<int64_t>(), c->stream));
+  const int64_t *dtot = c->offs.as<int64_t>() + Ns;   // this step's connected rows
+  CU(c, launch_compact(c->conn_cnt.as<int32_t>(), c->offs.as<int64_t>(), Ns, M, c->conn_sig.as<uint32_t>(),
+                       c->conn_sigp.as<uint32_t>(), c->conn_coef.as<float2>(), c->fsig.as<uint32_t>(),
+                       c->fsigp.as<uint32_t>(), c->fcoef.as<float2>(), c->stream));
+  CU(c, TC_LAUNCH(c, launch_fwd_bf16_store, c->dm, c->dmb, c->fsig.as<uint32_t>(), c->fsigp.as<uint32_t>(), R,
+                  c->flr.as<float2>(), err, c->n_sm, c->stream, c->act_x.as<uint8_t>(),
+                  c->dm.ffn > 0 ? c->act_xmid.as<uint8_t>() : nullptr, c->act_h.as<float>(), c->act_f.as<float>(),
+                  tiles, dtot));
+  CU(c, cudaMemsetAsync(c->nonfinite.p, 0, sizeof(int), c->stream));
+  CU(c, launch_lloc(c->offs.as<int64_t>(), Ns, c->fcoef.as<float2>(), c->flr.as<float2>(), c->lloc.as<double2>(),
+                    c->l2.as<double>(), c->stats.as<double>(), c->nonfinite.as<int>(), c->stream));
+  CU(c, launch_cotangent(c->offs.as<int64_t>(), Ns, c->fcoef.as<float2>(), c->flr.as<float2>(), c->lloc.as<double2>(),
+                         c->stats.as<double>(), c->cot.as<float2>(), c->stream));
+  const int copies = 16;
+  const size_t stride = (P + 3) / 4 * 4;
+  CU(c, cudaMemsetAsync(c->gacc.p, 0, sizeof(float) * copies * stride, c->stream));
+  BwdTcBuffers bf{c->act_x.as<uint8_t>(), c->act_xmid.as<uint8_t>(), c->act_dqkv.as<uint8_t>(), c->act_h.as<float>(),
+                  c->act_f.as<float>(), c->act_dF.as<float>(), c->act_dxa.as<float>(), c->act_dxb.as<float>(), tiles,
+                  c->cscale.as<float>()};
+  CU(c, TC_LAUNCH(c, launch_bwdtc, c->dm, c->dmb, c->bwl, bf, c->fsig.as<uint32_t>(), c->fsigp.as<uint32_t>(), R,
+                  c->cot.as<float2>(), c->gacc.as<float>(), stride, c->flat_offsets, err, c->n_sm, c->stream, nullptr,
+                  dtot));
+  CU(c, launch_reduce_copies(c->gacc.as<float>(), copies, stride, P, c->grad.as<double>(), 0, c->stream,
+                             c->cscale.as<float>() + 1));
+  TRY(jacobian_bf16_for_sr(c, ds, dp, Ns, ldo));
+  CU(c, sr_cg_capture(c->Obuf.p, 1, Ns, P, ldo, c->grad.as<double>(), c->delta.as<double>(), shift, c->sr_tol,
+                      c->sr_max_iter, c->srwork.as<double>(), c->sr_product, &gs->warm, err, c->last_sr_shape,
+                      c->stream));
+  CU(c, launch_step_gate(sr_outcome_slot(c->srwork.as<double>(), Ns, P), c->nonfinite.as<int>(), err, &gs->ok,
+                         c->stream));
+  if (c->opt == TDO_OPT_ADAM)
+    CU(c, launch_adam_update(c->theta64.as<double>(), c->delta.as<double>(), c->adam_m.as<double>(),
+                             c->adam_v.as<double>(), P, 1, lr, c->adam_b1, c->adam_b2, c->adam_eps, c->stream, &gs->ok,
+                             &gs->c1));
+  else
+    CU(c, launch_axpy_update(c->theta64.as<double>(), c->delta.as<double>(), lr, P, c->stream, &gs->ok));
+  TRY(refresh_params(c));
+  return TDO_OK;
+}
+
+static uint64_t bits_of(double v) {
+  uint64_t u;
+  memcpy(&u, &v, sizeof(u));
+  return u;
+}
+
+// While a graph-mode step runs, the context's work goes to its graph stream, which starts after what
+// was queued on the context's stream and ends before anything queued there later.
+struct GraphStream {
+  tdo_ctx *c;
+  cudaStream_t saved;
+  explicit GraphStream(tdo_ctx *ctx) : c(ctx), saved(ctx->stream) {
+    cudaEventRecord(c->gevent, saved);
+    cudaStreamWaitEvent(c->gstream, c->gevent, 0);
+    c->stream = c->gstream;
+  }
+  ~GraphStream() {
+    cudaEventRecord(c->gevent, c->gstream);
+    cudaStreamWaitEvent(saved, c->gevent, 0);
+    c->stream = saved;
+  }
+};
+
+// tdo_vmc_step in graph mode: record the step when anything it was recorded for has changed, upload the
+// step's values, launch, then read the outcome (one synchronisation).
+static tdo_status vmc_step_graph(tdo_ctx *c, uint32_t *sig, uint32_t *sigp, size_t Ns, size_t n_sweeps,
+                                 uint64_t seed, uint64_t *counter, double lr, double shift, double *cost) {
+  if (Ns == 0) return fail(c, TDO_EINVAL, "Ns must be > 0");
+  if (!sig || !sigp) return fail(c, TDO_EINVAL, "NULL buffer");
+  if (!(shift > 0.0)) return fail(c, TDO_EINVAL, "diag_shift must be > 0");
+  if (!c->gstream) CU(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+  if (!c->gevent) CU(c, cudaEventCreateWithFlags(&c->gevent, cudaEventDisableTiming));
+  GraphStream on_graph_stream(c);
+  const bool hs = !is_device_ptr(sig), hp = !is_device_ptr(sigp);
+  uint32_t *ds = sig, *dp = sigp;
+  if (hs) { CU(c, c->stage_in[0].ensure(4 * Ns)); ds = c->stage_in[0].as<uint32_t>(); }
+  if (hp) { CU(c, c->stage_in[1].ensure(4 * Ns)); dp = c->stage_in[1].as<uint32_t>(); }
+  const size_t P = c->P, ldo = (P + 3) / 4 * 4;
+  TRY(graph_alloc(c, Ns, ldo));
+  const std::vector<uint64_t> key = {Ns, n_sweeps, seed, bits_of(lr), bits_of(shift), bits_of(c->sr_tol),
+                                     (uint64_t)c->sr_max_iter, (uint64_t)c->opt, bits_of(c->adam_b1),
+                                     bits_of(c->adam_b2), bits_of(c->adam_eps), (uint64_t)c->sr_product,
+                                     (uint64_t)(uintptr_t)ds, (uint64_t)(uintptr_t)dp, g_buf_gen};
+  if (!c->gexec || key != c->gkey) {
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    CU(c, cudaStreamSynchronize(c->stream));
+    CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+    c->capturing = true;
+    const unsigned long long gen = g_buf_gen;
+    const tdo_status rs = graph_record(c, ds, dp, Ns, n_sweeps, seed, lr, shift, ldo);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    c->capturing = false;
+    if (rs != TDO_OK) { if (g) cudaGraphDestroy(g); return rs; }
+    if (ee != cudaSuccess) { if (g) cudaGraphDestroy(g); CU(c, ee); }
+    if (g_buf_gen != gen) {
+      cudaGraphDestroy(g);
+      return fail(c, TDO_ECUDA, "step graph: a buffer was allocated while the step was recorded");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) { c->gexec = nullptr; CU(c, ei); }
+    c->gkey = key;
+    ++c->graph_captures;
+  }
+  // this step's values
+  StepDev *h = c->gstep_host;
+  h->counter = *counter;
+  const long long t = c->adam_t + 1;
+  h->c1 = 1.0 - pow(c->adam_b1, (double)t);
+  h->c2 = 1.0 - pow(c->adam_b2, (double)t);
+  h->warm = c->have_delta ? 1 : 0;
+  h->ok = 0;
+  if (!c->have_delta) CU(c, cudaMemsetAsync(c->delta.p, 0, sizeof(double) * P, c->stream));
+  CU(c, cudaMemcpyAsync(c->gstep.p, h, sizeof(StepDev), cudaMemcpyHostToDevice, c->stream));
+  if (hs) CU(c, cudaMemcpyAsync(ds, sig, 4 * Ns, cudaMemcpyHostToDevice, c->stream));
+  if (hp) CU(c, cudaMemcpyAsync(dp, sigp, 4 * Ns, cudaMemcpyHostToDevice, c->stream));
+  CU(c, cudaGraphLaunch(c->gexec, c->stream));
+  ++c->graph_replays;
+  *counter += (uint64_t)n_sweeps * (uint64_t)(2 * c->n);
+  if (hs) CU(c, cudaMemcpyAsync(sig, ds, 4 * Ns, cudaMemcpyDeviceToHost, c->stream));
+  if (hp) CU(c, cudaMemcpyAsync(sigp, dp, 4 * Ns, cudaMemcpyDeviceToHost, c->stream));
+  double st[2];
+  int nf = 0, ef = 0, ok = 0, iters = 0, outcome = 0, restarted = 0;
+  double resid = 0, pap = 0;
+  CU(c, cudaMemcpyAsync(st, c->stats.p, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaMemcpyAsync(&nf, c->nonfinite.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaMemcpyAsync(&ef, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaMemcpyAsync(&ok, &c->gstep.as<StepDev>()->ok, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, sr_cg_result(c->srwork.as<double>(), Ns, P, &iters, &resid, &outcome, &pap, &restarted, c->stream));
+  c->last_sr_iters = iters;
+  c->last_sr_resid = resid;
+  c->last_sr_outcome = outcome;
+  c->last_sr_pap = pap;
+  c->last_sr_restarts = restarted;
+  c->have_delta = ok != 0;
+  if (ef) {
+    CU(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->stream));
+    return fail(c, TDO_ETIMEOUT, "a tensor-core kernel's bounded wait gave up (results of that launch are invalid)");
+  }
+  if (nf) return fail(c, TDO_ENUMERIC, "non-finite log rho or L_loc (rho = 0 exactly, or non-finite parameters)");
+  TRY(sr_outcome_status(c, outcome));
+  if (c->opt == TDO_OPT_ADAM) c->adam_t = t;
+  if (cost) *cost = st[0] / (double)Ns;
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_set_step_graph(tdo_ctx *c, int enable) {
+  if (!c) return TDO_EINVAL;
+  if (enable && !(c->tc && c->tc_bwd))
+    return fail(c, TDO_EUNSUPPORTED, "the step graph needs a tensor-core context whose gradient runs on the tensor cores");
+  c->step_graph = enable != 0;
+  if (!c->step_graph && c->gexec) {
+    cudaStreamSynchronize(c->gstream);
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gkey.clear();
+  }
+  return TDO_OK;
+}
+
+extern "C" tdo_status tdo_step_graph_stats(const tdo_ctx *c, long long *recordings, long long *launches) {
+  if (!c) return TDO_EINVAL;
+  if (recordings) *recordings = c->graph_captures;
+  if (launches) *launches = c->graph_replays;
+  return TDO_OK;
+}
+
 extern "C" tdo_status tdo_vmc_step(tdo_ctx *c, uint32_t *sig, uint32_t *sigp, size_t n_chains, size_t n_sweeps,
                                    uint64_t seed, uint64_t *counter, long long step, const tdo_schedule *sched,
                                    double *cost) {
@@ -1440,6 +1732,11 @@ extern "C" tdo_status tdo_vmc_step(tdo_ctx *c, uint32_t *sig, uint32_t *sigp, si
   const tdo_schedule paper = {0.0061, 30000, 40000, 0.001, 0.004, 30000, 40000, 0.01};
   const tdo_schedule &sc = sched ? *sched : paper;
   if (sc.i_decay <= 0 || sc.i_decay_sr <= 0) return fail(c, TDO_EINVAL, "decay periods must be > 0");
+  if (c->step_graph) {
+    const double lr = tdo_schedule_value(step, sc.eta0, sc.i_switch, sc.i_decay, sc.alpha);
+    const double shift = tdo_schedule_value(step, sc.lambda0, sc.i_switch_sr, sc.i_decay_sr, sc.alpha_sr);
+    return vmc_step_graph(c, sig, sigp, n_chains, n_sweeps, seed, counter, lr, shift, cost);
+  }
   if (n_sweeps > 0) {
     TRY(tdo_sample(c, n_chains, n_sweeps, seed, *counter, sig, sigp, nullptr, nullptr, nullptr));
     *counter += (uint64_t)n_sweeps * (uint64_t)(2 * c->n);

@@ -98,11 +98,13 @@ cudaError_t launch_unpermute(const float2 *in, const uint32_t *perm, size_t B, f
 cudaError_t launch_sample_bf16(const DevModel &m, const DevModelBF16 &mb, size_t n_chains,
                                size_t n_sweeps, uint64_t seed, uint64_t counter, uint32_t *sig,
                                uint32_t *sigp, uint32_t *ssig, uint32_t *ssigp,
-                               unsigned long long *accepted, int *err_flag, int diag, int n_sm, cudaStream_t st);
+                               unsigned long long *accepted, int *err_flag, int diag, int n_sm, cudaStream_t st,
+                               const uint64_t *dcounter = nullptr);
 cudaError_t launch_sample_bf16_f16(const DevModel &m, const DevModelBF16 &mb, size_t n_chains,
                                    size_t n_sweeps, uint64_t seed, uint64_t counter, uint32_t *sig,
                                    uint32_t *sigp, uint32_t *ssig, uint32_t *ssigp,
-                                   unsigned long long *accepted, int *err_flag, int diag, int n_sm, cudaStream_t st);
+                                   unsigned long long *accepted, int *err_flag, int diag, int n_sm, cudaStream_t st,
+                                   const uint64_t *dcounter = nullptr);
 
 // Mixed-state observables.  Rows of the magnetisation estimator: sample s -> (alpha, alpha), then
 // (alpha, alpha ^ e_i) for i < N, at rows s (N + 1) + j.
@@ -154,10 +156,16 @@ cudaError_t launch_fwd_ragged_f8(const DevModel &m, const DevModelBF16 &mb, cons
 cudaError_t launch_sample_bf16_f8(const DevModel &m, const DevModelBF16 &mb, size_t n_chains, size_t n_sweeps,
                                   uint64_t seed, uint64_t counter, uint32_t *sig, uint32_t *sigp, uint32_t *ssig,
                                   uint32_t *ssigp, unsigned long long *accepted, int *err_flag, int diag, int n_sm,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const uint64_t *dcounter = nullptr);
 
-cudaError_t launch_axpy_update(double *theta, const double *delta, double lr, size_t P, cudaStream_t st);
+// gate (device int, may be NULL): the update is skipped when *gate is 0 (a replayed step whose solve failed).
+cudaError_t launch_axpy_update(double *theta, const double *delta, double lr, size_t P, cudaStream_t st,
+                               const int *gate = nullptr);
 // Adam step t (>= 1) on the direction delta with first and second moments m, v (FP64 [P], updated).
+// dc (device, may be NULL): the bias corrections 1 - b1^t, 1 - b2^t of the step, in place of t's.
 cudaError_t launch_adam_update(double *theta, const double *delta, double *m, double *v, size_t P, long long t,
-                               double lr, double b1, double b2, double eps, cudaStream_t st);
+                               double lr, double b1, double b2, double eps, cudaStream_t st,
+                               const int *gate = nullptr, const double *dc = nullptr);
+// *ok = the solve's outcome slot is 0 or 1, *nonfinite is 0 and *err (may be NULL) is 0.
+cudaError_t launch_step_gate(const double *outcome, const int *nonfinite, const int *err, int *ok, cudaStream_t st);
 

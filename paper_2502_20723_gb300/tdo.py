@@ -24,7 +24,7 @@ EXPORTS = ["tdo_model_num_params", "tdo_create", "tdo_destroy", "tdo_num_params"
            "tdo_set_params", "tdo_get_params", "tdo_log_rho", "tdo_log_rho_vjp", "tdo_jacobian",
            "tdo_connections", "tdo_local_estimator", "tdo_local_estimator_noalloc", "tdo_sample", "tdo_grad", "tdo_sr_solve", "tdo_set_sr_options", "tdo_sr_step",
            "tdo_timing", "tdo_timing_read", "tdo_sr_info", "tdo_sr_report", "tdo_set_sr_product", "tdo_sr_product_shape", "tdo_sr_apply", "tdo_wait_selftest", "tdo_set_optimizer", "tdo_log_rho_ragged", "tdo_ragged_tuning", "tdo_measure_peak", "tdo_last_error", "tdo_sample_diag", "tdo_magnetisation",
-           "tdo_purity", "tdo_schedule_value", "tdo_vmc_step"]
+           "tdo_purity", "tdo_schedule_value", "tdo_vmc_step", "tdo_set_step_graph", "tdo_step_graph_stats"]
 
 
 class TdoError(RuntimeError):
@@ -108,6 +108,8 @@ def lib() -> C.CDLL:
         L.tdo_schedule_value.argtypes = [C.c_longlong, C.c_double, C.c_longlong, C.c_longlong, C.c_double]
         L.tdo_schedule_value.restype = C.c_double
         L.tdo_vmc_step.argtypes = [vp, vp, vp, sz, sz, u64, C.POINTER(u64), C.c_longlong, C.POINTER(Schedule), dp]
+        L.tdo_set_step_graph.argtypes = [vp, i32]
+        L.tdo_step_graph_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
         L.tdo_grad.argtypes = [vp, vp, vp, sz, vp, dp, vp]
         L.tdo_sr_solve.argtypes = [vp, vp, sz, vp, C.c_double, C.c_double, i32, vp, C.POINTER(i32), dp]
         L.tdo_sr_step.argtypes = [vp, vp, vp, sz, C.c_double, C.c_double, dp]
@@ -328,6 +330,16 @@ class Context:
         self._chk(lib().tdo_vmc_step(self.h, _ptr(sig), _ptr(sigp), len(sig), n_sweeps, seed, C.byref(ctr), step,
                                      sched, C.byref(cost)))
         return cost.value, ctr.value
+
+    def set_step_graph(self, enable: bool):
+        """tdo_set_step_graph: vmc_step records its whole step into a CUDA graph once and replays it."""
+        self._chk(lib().tdo_set_step_graph(self.h, 1 if enable else 0))
+
+    def step_graph_stats(self):
+        """(recordings, launches) of the step graph (tdo_step_graph_stats)."""
+        a, b = C.c_longlong(), C.c_longlong()
+        self._chk(lib().tdo_step_graph_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def grad(self, sig, sigp, grad=None, O=None):
         Ns = len(sig)

@@ -78,6 +78,8 @@ def test_null_context_is_rejected_without_a_device(libtdo):
     assert libtdo.tdo_sr_product_shape(None, None, None, None) == einval
     assert libtdo.tdo_sr_apply(None, None, 4, 4, None, ctypes.c_double(0.1), None) == einval
     assert libtdo.tdo_wait_selftest(None, 16) == einval
+    assert libtdo.tdo_set_step_graph(None, 1) == einval
+    assert libtdo.tdo_step_graph_stats(None, None, None) == einval
     assert libtdo.tdo_set_optimizer(None, 1, 0.9, 0.999, 1e-8) == einval
     assert libtdo.tdo_log_rho_ragged(None, None, None, None, 4, None) == einval
     assert libtdo.tdo_ragged_tuning(None, 1, None, None, None) == einval
