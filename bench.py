@@ -5,9 +5,12 @@ Workload (the headline configuration): dissipative transverse-field Ising chain 
 gamma=1), transformer with token embedding, d=64, 8 heads, 4 layers, MLP 4d (P = 198,274 parameters,
 N(0, 0.02) seed 0), 16384 Metropolis chains per GPU, one sample per chain per step.
 
-One step = one VMC step through the C ABI: one Metropolis sweep (2N proposals per chain, tdo_sample),
-then tdo_sr_step on the chain states (connections, log rho of every connected configuration, L_loc and
-cost, cost gradient, log-derivatives, SR conjugate-gradient solve, parameter update).
+One step = one VMC step through the C ABI: one Metropolis sweep (2N proposals per chain), then the SR
+step on the chain states (connections, log rho of every connected configuration, L_loc and cost, cost
+gradient, log-derivatives, SR conjugate-gradient solve, parameter update).  The headline times each step
+as one launch of the whole-step CUDA graph (tdo_vmc_step with tdo_set_step_graph); the same trajectory
+run call by call (tdo_sample + tdo_sr_step), with CUDA events around every kernel group, gives the
+per-group breakdown and the rooflines.
 
 The timed arm is the FP16 tensor-core context (tcgen05 GEMMs with FP16 operands, FP32 accumulation);
 shorter comparison runs time the BF16 tensor-core and the FP32 CUDA-core contexts.  A BF16 backward's
@@ -200,37 +203,62 @@ def run_ours(args) -> dict | None:
                "theta": ctx.get_params(),
                "subset": ((sig[:SET_ERROR_SAMPLES].cpu().numpy().astype(np.int64) & 0xFFFFFFFF).astype(np.uint32),
                           (sigp[:SET_ERROR_SAMPLES].cpu().numpy().astype(np.int64) & 0xFFFFFFFF).astype(np.uint32))}
-        if e2e:
-            # end to end through the public API with host buffers (copies inside the timed region), on the
-            # same trajectory as the timed steps: a fresh context from the same parameters and chains, the
-            # same burn-in and warm-up, then the same `steps` steps with the chains in pinned host memory
-            ctx.close()
-            ctx = tdo.Context(prob, spec, theta, precision, stream=stream.cuda_stream)
-            sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
-            sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
-            counter[0] = 0
-            ctx.sample(sig, sigp, args.burn_in, seed, counter[0])
-            counter[0] += args.burn_in * 2 * N_SITES
-            for _ in range(warmup):
-                step()
-            hs = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
-            hp = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
-            hs.copy_(sig.cpu())
-            hp.copy_(sigp.cpu())
-            hs_np, hp_np = hs.numpy(), hp.numpy()
-            torch.cuda.synchronize()
-            e2e_costs = []
-            t0 = time.perf_counter()
-            for _ in range(steps):
-                flush.zero_()
-                ctx.sample(hs_np, hp_np, 1, seed, counter[0])          # H2D chains, D2H chains
-                counter[0] += 2 * N_SITES
-                e2e_costs.append(ctx.sr_step(hs_np, hp_np, LR, SHIFT))  # H2D samples, D2H cost
-            torch.cuda.synchronize()
-            out["e2e_steps_per_s"] = replicas_rate(world, steps, max_over_ranks(time.perf_counter() - t0, world))
-            # the same steps up to the order of float atomics in the gradient sums
-            out["e2e_cost_max_rel_diff"] = float(np.max(np.abs(np.array(e2e_costs) - np.array(costs)) / np.abs(costs)))
         ctx.close()
+        if e2e:
+            # the same trajectory again (a fresh context from the same parameters and chains, the same
+            # burn-in), each step one launch of the whole-step CUDA graph (tdo_set_step_graph + vmc_step):
+            # first with the chains on the device (CUDA events per step on the launching stream: the
+            # headline), then end to end with the chains in pinned host memory (copies inside the timed
+            # region, wall clock)
+            sched = tdo.Schedule(eta0=LR, lambda0=SHIFT)   # constant: the schedules switch at step 30000
+            for host in (False, True):
+                ctx = tdo.Context(prob, spec, theta, precision, stream=stream.cuda_stream)
+                sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
+                sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
+                ctx.sample(sig, sigp, args.burn_in, seed, 0)
+                ctr = args.burn_in * 2 * N_SITES
+                ctx.set_step_graph(True)
+                for k in range(warmup):
+                    _, ctr = ctx.vmc_step(sig, sigp, 1, seed, ctr, k, sched)
+                a, b = sig, sigp
+                if host:
+                    hs = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
+                    hp = torch.empty(N_SAMPLES, dtype=torch.int32).pin_memory()
+                    hs.copy_(sig.cpu())
+                    hp.copy_(sigp.cpu())
+                    a, b = hs.numpy(), hp.numpy()
+                torch.cuda.synchronize()
+                gcosts, giters = [], []
+                gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                       for _ in range(steps)]
+                if world > 1:
+                    dist.barrier()
+                torch.cuda.synchronize()
+                with ClockSampler(local) as gclk:
+                    t0 = time.perf_counter()
+                    for i in range(steps):
+                        flush.zero_()
+                        gev[i][0].record(stream)
+                        c_i, ctr = ctx.vmc_step(a, b, 1, seed, ctr, warmup + i, sched)
+                        gev[i][1].record(stream)
+                        gcosts.append(c_i)
+                        giters.append(ctx.sr_info()[0])
+                    torch.cuda.synchronize()
+                    wall = time.perf_counter() - t0
+                if world > 1:
+                    dist.barrier()
+                # the same steps as the call-by-call run up to the order of float atomics in the gradient
+                diff = float(np.max(np.abs(np.array(gcosts) - np.array(costs)) / np.abs(costs)))
+                rec, nl = ctx.step_graph_stats()
+                if host:
+                    out["e2e_steps_per_s"] = replicas_rate(world, steps, max_over_ranks(wall, world))
+                    out["e2e_cost_max_rel_diff"] = diff
+                else:
+                    out["graph"] = {"t_ms": max_over_ranks(sum(x.elapsed_time(y) for x, y in gev), world),
+                                    "costs": gcosts, "sr_iters": giters, "cost_max_rel_diff": diff,
+                                    "recordings": rec,
+                                    "launches": nl, "clocks": gclk.summary()}
+                ctx.close()
         return out
 
     peak_fp32 = tdo.measure_peak("fp32", stream.cuda_stream)
@@ -307,14 +335,15 @@ def run_ours(args) -> dict | None:
     dom = max(dom_ms, key=dom_ms.get)
     roof = dict(rooflines[dom])
     fwd_tflops = rooflines["fwd"]["achieved"]
+    gr = main["graph"]
     res = {
         "metric": METRIC,
-        "value": replicas_rate(world, args.steps, t_max * 1e-3),
+        "value": replicas_rate(world, args.steps, gr["t_ms"] * 1e-3),
         "unit": "VMC steps/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": t_max / args.steps,
+        "ms_per_step": gr["t_ms"] / args.steps,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -324,21 +353,33 @@ def run_ours(args) -> dict | None:
                    "mlp_ratio": MLP, "samples_per_gpu": N_SAMPLES, "params": P, "precision": args.precision,
                    "sweeps_per_step": 1, "lr": LR, "diag_shift": SHIFT,
                    "l2": "256 MB buffer written between timed steps",
+                   "timing": "each step one launch of the whole-step CUDA graph (tdo_set_step_graph), CUDA events "
+                             "per step; kernel groups, rooflines and gpu_launches from the call-by-call run of the "
+                             "same trajectory (tdo_sample + tdo_sr_step, CUDA events per kernel group)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "logrho_evals_per_s": (fwd_evals + sample_evals) * world * args.steps / (t_max * 1e-3),
         "logrho_evals_per_s_fwd_kernel": fwd_evals / (groups["fwd"]["ms"] * 1e-3) if groups["fwd"]["ms"] else None,
         "rows_per_step": {"lloc_rows": lloc_rows, "sample_evals": sample_evals},
         "breakdown_ms_per_step": {g: round(v["ms"], 3) for g, v in groups.items()},
-        "costs": [round(c, 6) for c in main["costs"]],
-        "sr_cg_iterations": main["sr_iters"],
+        "costs": [round(c, 6) for c in gr["costs"]],
+        "sr_cg_iterations": gr["sr_iters"],
+        "call_by_call": {"value": replicas_rate(world, args.steps, t_max * 1e-3), "unit": "VMC steps/s",
+                         "ms_per_step": t_max / args.steps, "costs": [round(c, 6) for c in main["costs"]],
+                         "sr_cg_iterations": main["sr_iters"],
+                         "clocks": clk_summary,
+                         "graph_cost_max_rel_diff": gr["cost_max_rel_diff"]},
+        "graph": {"recordings": gr["recordings"], "launches": gr["launches"]},
         "fwd_kernel_tflops": fwd_tflops,
         "roofline": roof,
         "rooflines": rooflines,
         "peaks_measured_here": {"fp32_fma_tflops": peak_fp32, "fp64_fma_tflops": peak_fp64},
-        "clocks": clk_summary,
+        "clocks": gr["clocks"],
+        # chains in (2 x 4 B per chain) and the step's 32-byte value block; chains out, the cost statistics
+        # (16 B), the L_loc, timeout and update flags (3 x 4 B) and the CG scalars (14 x 8 B)
         "e2e": {"value": main["e2e_steps_per_s"], "unit": "VMC steps/s",
-                "h2d_bytes_per_step": 4 * 4 * N_SAMPLES, "d2h_bytes_per_step": 2 * 4 * N_SAMPLES + 8,
-                "steps": args.steps, "trajectory": "the timed steps replayed from the same parameters and chains",
+                "h2d_bytes_per_step": 2 * 4 * N_SAMPLES + 32, "d2h_bytes_per_step": 2 * 4 * N_SAMPLES + 16 + 12 + 112,
+                "steps": args.steps, "call": "tdo_vmc_step in graph mode with the chains in pinned host memory",
+                "trajectory": "the timed steps replayed from the same parameters and chains",
                 "cost_max_rel_diff_vs_timed_steps": main["e2e_cost_max_rel_diff"]},
         "gpu_launches": launches,
     }
@@ -466,7 +507,8 @@ def config5_vmc(tdo, torch, stream, spec, theta, steps: dict = None) -> dict:
     is, for every N, one Metropolis sweep and one SR step (connections, L_loc, cost, gradient,
     log-derivatives, CG solve, update) on that length's share of the 32,768 chains, in a context per N
     with the same initial parameters.  Timed with CUDA events around the whole multi-length step after
-    warm-up steps, FP16 against FP32."""
+    warm-up steps, FP16 against FP32.  The FP16 contexts run each length's step as one launch of its
+    whole-step CUDA graph (tdo_set_step_graph); the FP32 contexts, which have no graph mode, call by call."""
     steps = steps or {"fp16": (2, 3), "fp32": (1, 2)}   # (warm-up, timed)
     per = CONFIG5_SAMPLES // len(CONFIG5_N)
     out = {"definition": "one sweep + one SR step of every chain length N in {8,12,16,20,24,32}, "
@@ -481,16 +523,24 @@ def config5_vmc(tdo, torch, stream, spec, theta, steps: dict = None) -> dict:
             sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
             sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
             ctx.sample(sig, sigp, 2, 91 + n, 0)
+            ctx.set_step_graph(prec != "fp32")
             ctxs.append(ctx)
             chains.append([sig, sigp, 2 * 2 * n])
         costs = []
+        sched = tdo.Schedule(eta0=LR, lambda0=SHIFT)
+        k_step = [0]
 
         def one_step():
             c = []
             for (ctx, ch), n in zip(zip(ctxs, chains), CONFIG5_N):
-                ctx.sample(ch[0], ch[1], 1, 91 + n, ch[2])
-                ch[2] += 2 * n
-                c.append(ctx.sr_step(ch[0], ch[1], LR, SHIFT))
+                if prec != "fp32":
+                    cost, ch[2] = ctx.vmc_step(ch[0], ch[1], 1, 91 + n, ch[2], k_step[0], sched)
+                    c.append(cost)
+                else:
+                    ctx.sample(ch[0], ch[1], 1, 91 + n, ch[2])
+                    ch[2] += 2 * n
+                    c.append(ctx.sr_step(ch[0], ch[1], LR, SHIFT))
+            k_step[0] += 1
             return c
 
         for _ in range(warm):
@@ -504,6 +554,7 @@ def config5_vmc(tdo, torch, stream, spec, theta, steps: dict = None) -> dict:
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / timed
         out[prec] = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "warmup": warm, "steps": timed,
+                     "graph": prec != "fp32",
                      "costs_last_step": dict(zip((str(n) for n in CONFIG5_N), (round(x, 5) for x in costs[-1])))}
         for ctx in ctxs:
             ctx.close()
