@@ -204,7 +204,7 @@ def run_ours(args) -> dict | None:
                "subset": ((sig[:SET_ERROR_SAMPLES].cpu().numpy().astype(np.int64) & 0xFFFFFFFF).astype(np.uint32),
                           (sigp[:SET_ERROR_SAMPLES].cpu().numpy().astype(np.int64) & 0xFFFFFFFF).astype(np.uint32))}
         ctx.close()
-        if e2e:
+        if e2e and not args.no_graph:
             # the same trajectory again (a fresh context from the same parameters and chains, the same
             # burn-in), each step one launch of the whole-step CUDA graph (tdo_set_step_graph + vmc_step):
             # first with the chains on the device (CUDA events per step on the launching stream: the
@@ -335,7 +335,10 @@ def run_ours(args) -> dict | None:
     dom = max(dom_ms, key=dom_ms.get)
     roof = dict(rooflines[dom])
     fwd_tflops = rooflines["fwd"]["achieved"]
-    gr = main["graph"]
+    # --no-graph (profiling runs: no conditional graph nodes under the profiler): the call-by-call run
+    # stands in for the graph leg and there is no end-to-end leg
+    gr = main.get("graph") or {"t_ms": t_max, "costs": main["costs"], "sr_iters": main["sr_iters"],
+                               "cost_max_rel_diff": 0.0, "recordings": 0, "launches": 0, "clocks": clk_summary}
     res = {
         "metric": METRIC,
         "value": replicas_rate(world, args.steps, gr["t_ms"] * 1e-3),
@@ -376,11 +379,11 @@ def run_ours(args) -> dict | None:
         "clocks": gr["clocks"],
         # chains in (2 x 4 B per chain) and the step's 32-byte value block; chains out, the cost statistics
         # (16 B), the L_loc, timeout and update flags (3 x 4 B) and the CG scalars (14 x 8 B)
-        "e2e": {"value": main["e2e_steps_per_s"], "unit": "VMC steps/s",
+        "e2e": {"value": main.get("e2e_steps_per_s"), "unit": "VMC steps/s",
                 "h2d_bytes_per_step": 2 * 4 * N_SAMPLES + 32, "d2h_bytes_per_step": 2 * 4 * N_SAMPLES + 16 + 12 + 112,
                 "steps": args.steps, "call": "tdo_vmc_step in graph mode with the chains in pinned host memory",
                 "trajectory": "the timed steps replayed from the same parameters and chains",
-                "cost_max_rel_diff_vs_timed_steps": main["e2e_cost_max_rel_diff"]},
+                "cost_max_rel_diff_vs_timed_steps": main.get("e2e_cost_max_rel_diff")},
         "gpu_launches": launches,
     }
     res["compare"] = {}
@@ -753,6 +756,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-config5", action="store_true", help="skip the uneven-length (N = 8..32) leg")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time call by call only (no step-graph or end-to-end leg): for profiler runs")
     ap.add_argument("--kernel-case", default=None, choices=["fwd", "grad", "jac", "sample", "sr"],
                     help="run one call of one kind on a reduced sample count (profiling) and exit")
     ap.add_argument("--case-samples", type=int, default=1024)

@@ -165,12 +165,16 @@ __device__ __forceinline__ void load2(Sync &s, uint32_t d0, const void *s0, uint
   }
 }
 
+// GELU (tanh form) at u into *g and its derivative, from one tanh.approx: with s = u^2,
+// t = tanh(u (k0 + k0 k1 s)) and h = (1 + t) / 2, gelu = u h and gelu' = h + (k0 / 2) u (1 - t^2)(1 + 3 k1 s).
 __device__ __forceinline__ float gelu_grad_fast(float u, float *g) {
   const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+  const float s = u * u;
   float t;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(k0 * fmaf(k1 * u, u * u, u)));
-  *g = 0.5f * u * (1.0f + t);
-  return 0.5f * (1.0f + t) + 0.5f * u * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * u * u);
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u * fmaf(k0 * k1, s, k0)));
+  const float h = fmaf(0.5f, t, 0.5f);
+  *g = u * h;
+  return fmaf(0.5f * k0, u * (fmaf(-t, t, 1.0f) * fmaf(3.0f * k1, s, 1.0f)), h);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
