@@ -155,6 +155,8 @@ def run_ours(args) -> dict | None:
 
     def measure(precision: str, steps: int, warmup: int, e2e: bool):
         ctx = tdo.Context(prob, spec, theta, precision, stream=stream.cuda_stream)
+        if precision != "fp32":
+            ctx.set_sr_product(args.sr_product)
         cfg_seed, seed = replica_seeds(rank)
         s0, s1 = synth.random_configs(N_SITES, N_SAMPLES, seed=cfg_seed)
         sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
@@ -195,7 +197,7 @@ def run_ours(args) -> dict | None:
             groups[g] = {"ms": ms / steps, "launches": n / steps}
         launches = int(sum(v["launches"] for v in groups.values()) * steps)
         ms, n = ctx.timing_read("sr_mv")   # the S' v kernel alone (inside "sr")
-        sr_mv = {"ms": ms / steps, "launches": n / steps}
+        sr_mv = {"ms": ms / steps, "launches": n / steps, "shape": ctx.sr_product_shape()}
         ctx.timing(False)
         lloc_rows = int(ctx.connections(sig, sigp)[0].sum().item())
         out = {"t_ms": max_over_ranks(t_ms, world), "groups": groups, "sr_mv": sr_mv, "launches": launches,
@@ -213,6 +215,8 @@ def run_ours(args) -> dict | None:
             sched = tdo.Schedule(eta0=LR, lambda0=SHIFT)   # constant: the schedules switch at step 30000
             for host in (False, True):
                 ctx = tdo.Context(prob, spec, theta, precision, stream=stream.cuda_stream)
+                if precision != "fp32":
+                    ctx.set_sr_product(args.sr_product)
                 sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
                 sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
                 ctx.sample(sig, sigp, args.burn_in, seed, 0)
@@ -318,16 +322,23 @@ def run_ours(args) -> dict | None:
     }
     mv = main["sr_mv"]
     ob = 8 if args.precision == "fp32" else 4   # tensor-core contexts store O - obar as BF16 pairs
-    byts = 2 * N_SAMPLES * P * ob
+    # algorithmic bytes of one product: O read once (what any product must stream); the two-pass product
+    # reads it twice, so its fraction is at most 1/2
+    byts = N_SAMPLES * P * ob
     ach = byts * mv["launches"] / (mv["ms"] * 1e-3) / 1e9 if mv["ms"] else 0.0
+    used = mv["shape"][0] if args.precision != "fp32" else 0
     traffic, traffic_src = None, None
-    if args.precision != "fp32":   # the capture is of the BF16-pair passes
-        per_row, traffic_src = sr_traffic_per_row()
+    if args.precision != "fp32":   # the captures are of the BF16-pair products
+        per_row, traffic_src = sr_traffic_per_row(mode=used)
         traffic = per_row * N_SAMPLES if per_row else None
-    rooflines["sr_mv"] = {"bound": "hbm", "kernel": "S' v product (k_sr_tpart + k_sr_wpart and reductions)",
+    kern = {0: "S' v product, two passes (k_sr_tpart + k_sr_wpart and reductions)",
+            1: "S' v product, one pass on thread-block clusters (k_sr_fused and reductions)",
+            2: "S' v product, one pass over the whole grid (k_sr_grid and reductions)"}[used]
+    rooflines["sr_mv"] = {"bound": "hbm", "kernel": kern, "product": SR_PRODUCT_NAMES[used],
                           "group": "sr_mv", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                           "traffic": traffic, "traffic_source": traffic_src,
-                          "algorithmic_per_launch": byts, "o_element_bytes": ob,
+                          "algorithmic_per_launch": byts, "algorithmic": "one read of O (Ns x P elements)",
+                          "o_element_bytes": ob, "o_reads_per_product": 2 if used == 0 else 1,
                           "products_per_step": mv["launches"], "ms_per_step": mv["ms"], "peak_source": hbm_src}
     # the headline roofline: the dominant kernel group of the timed steps
     dom_ms = {"fwd": groups["fwd"]["ms"], "bwd_vjp": groups["bwd_vjp"]["ms"], "sample": groups["sample"]["ms"],
@@ -355,6 +366,7 @@ def run_ours(args) -> dict | None:
         "config": {"workload": WORKLOAD, "n_sites": N_SITES, "d_model": D, "heads": HEADS, "layers": LAYERS,
                    "mlp_ratio": MLP, "samples_per_gpu": N_SAMPLES, "params": P, "precision": args.precision,
                    "sweeps_per_step": 1, "lr": LR, "diag_shift": SHIFT,
+                   "sr_product": args.sr_product if args.precision != "fp32" else "two_pass",
                    "l2": "256 MB buffer written between timed steps",
                    "timing": "each step one launch of the whole-step CUDA graph (tdo_set_step_graph), CUDA events "
                              "per step; kernel groups, rooflines and gpu_launches from the call-by-call run of the "
@@ -565,11 +577,19 @@ def config5_vmc(tdo, torch, stream, spec, theta, steps: dict = None) -> dict:
     return out
 
 
-def sr_traffic_per_row(prof: str = None, src: str = None):
-    """DRAM bytes per sample row of one S' v product from the committed ncu summary of the two passes,
-    valid only while the SR source has the SHA-1 recorded with that capture: (bytes or None, source)."""
+SR_PRODUCT_NAMES = {0: "two_pass", 1: "one_pass", 2: "grid"}
+SR_TRAFFIC_PROFILES = {0: "k_sr_tpart_wpart_ising_n16_d64_l4.md", 2: "k_sr_grid_ising_n16_d64_l4.md"}
+
+
+def sr_traffic_per_row(prof: str = None, src: str = None, mode: int = 0):
+    """DRAM bytes per sample row of one S' v product from the committed ncu summary of that product
+    (mode 0: the two passes, 2: the grid product), valid only while the SR source has the SHA-1 recorded
+    with that capture: (bytes or None, source)."""
     here = os.path.dirname(os.path.abspath(__file__))
-    prof = prof or os.path.join(here, "profiles", "k_sr_tpart_wpart_ising_n16_d64_l4.md")
+    if prof is None:
+        if mode not in SR_TRAFFIC_PROFILES:
+            return None, None
+        prof = os.path.join(here, "profiles", SR_TRAFFIC_PROFILES[mode])
     src = src or os.path.join(here, "paper_2502_20723_gb300", "csrc", "k_sr.cu")
     try:
         m = re.search(r"bench-traffic sr_mv: k_sr\.cu sha1=([0-9a-f]{40}) bytes_per_sample_row=(\d+)", open(prof).read())
@@ -580,8 +600,9 @@ def sr_traffic_per_row(prof: str = None, src: str = None):
         return None, None
     if m.group(1) != sha:
         return None, "k_sr.cu changed since the ncu capture in profiles/: traffic not known"
-    return int(m.group(2)), ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_sr_tpart + k_sr_wpart on "
-                             "1024 samples, scaled by the samples (profiles/k_sr_tpart_wpart_ising_n16_d64_l4.md)")
+    kern = "k_sr_tpart + k_sr_wpart" if "tpart" in os.path.basename(prof) else "k_sr_grid"
+    return int(m.group(2)), (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of {kern} on a reduced sample "
+                             f"count, scaled by the samples (profiles/{os.path.basename(prof)})")
 
 
 def set_error_report(gpu: dict, ref_l: np.ndarray, ref_c: float) -> dict:
@@ -722,6 +743,8 @@ def run_kernel_case(args) -> None:
     prob = synth.ising_chain(N_SITES, V=2.0, g=1.0, gamma=1.0)
     spec = synth.model_spec(D, HEADS, LAYERS, MLP)
     ctx = tdo.Context(prob, spec, synth.init_params(spec, seed=0), args.precision)
+    if args.precision != "fp32":
+        ctx.set_sr_product(args.sr_product)
     s0, s1 = synth.random_configs(N_SITES, args.case_samples, seed=1)
     sig = torch.as_tensor(s0.astype(np.int64)).to(torch.int32).cuda()
     sigp = torch.as_tensor(s1.astype(np.int64)).to(torch.int32).cuda()
@@ -761,6 +784,8 @@ def main():
     ap.add_argument("--kernel-case", default=None, choices=["fwd", "grad", "jac", "sample", "sr"],
                     help="run one call of one kind on a reduced sample count (profiling) and exit")
     ap.add_argument("--case-samples", type=int, default=1024)
+    ap.add_argument("--sr-product", default="two_pass", choices=["two_pass", "one_pass", "grid"],
+                    help="how the CG forms S' v in tensor-core contexts (tdo_set_sr_product)")
     ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample is not None:   # child process of the reference arm (single-thread timing)

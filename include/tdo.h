@@ -311,9 +311,16 @@ tdo_status tdo_sr_report(const tdo_ctx *ctx, int *outcome, double *last_pap, int
  * through distributed shared memory, and w is accumulated from the same copy of the row in shared
  * memory.  It reads O once, but each row costs two block barriers and one cluster exchange, and on a
  * GB300 it measured 1.3 times slower than two passes at the headline shape (198,274 parameters, 16,384
- * samples); it is kept as an option.  Both give the same products up to the order of FP32 partial sums
- * (each within 3e-7 of an FP64 evaluation of the definition). */
-enum { TDO_SR_PRODUCT_TWO_PASS = 0, TDO_SR_PRODUCT_ONE_PASS = 1 };
+ * samples); it is kept as an option.  All give the same products up to the order of FP32 partial sums
+ * (each within 3e-7 of an FP64 evaluation of the definition).
+ * TDO_SR_PRODUCT_GRID: also one pass where the log-derivatives are BF16 pairs on 16-byte rows, without
+ * clusters: one CTA per SM owns a parameter slab of every row; rows go in blocks of 8, bulk-copied into a
+ * ring of shared-memory stages; every CTA publishes its partials of t_s for a block to global memory with
+ * an arrival counter, dedicated exchange warps sum the partials of all CTAs (the same bits in every CTA)
+ * while the compute warps already work two blocks ahead, and w is accumulated from the same stage.  Its
+ * bounded waits watch the context's error flag (TDO_ETIMEOUT), so a launch whose CTAs cannot all run at
+ * once ends with that error instead of waiting. */
+enum { TDO_SR_PRODUCT_TWO_PASS = 0, TDO_SR_PRODUCT_ONE_PASS = 1, TDO_SR_PRODUCT_GRID = 2 };
 tdo_status tdo_set_sr_product(tdo_ctx *ctx, int mode);
 
 /* One product of the CG solve outside it: Ap = (Re S + shift I) v, S_ij = <O_i^* O_j> - <O_i^*><O_j> over
@@ -328,7 +335,8 @@ tdo_status tdo_sr_apply(tdo_ctx *ctx, const uint32_t *O, size_t Ns, size_t ldo, 
                         double *Ap);
 
 /* The last tdo_sr_step's (or tdo_sr_apply's) product shape (each pointer may be NULL): one_pass = 1 when
- * the one-pass product ran, cluster = CTAs per cluster, clusters = clusters launched (0, 0 for two
+ * the cluster product ran, 2 for the grid product, 0 for two passes; cluster = CTAs per cluster (1 for
+ * the grid product); clusters = clusters (or CTAs of the grid product) launched (0, 0 for two
  * passes).  A bounded wait of
  * the one-pass product that gives up makes tdo_sr_step return TDO_ETIMEOUT. */
 tdo_status tdo_sr_product_shape(const tdo_ctx *ctx, int *one_pass, int *cluster, int *clusters);

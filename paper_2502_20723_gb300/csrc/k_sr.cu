@@ -6,6 +6,7 @@
 // centring removes exactly; it keeps the BF16 rounding at the scale of O's spread, not of its mean).
 // One iteration streams O twice from HBM (t = Obar v per sample,
 // then w = Obar^H t per parameter) and is HBM-bound; both passes keep many independent loads in flight.
+// Two optional products read O once (k_sr_fused on thread-block clusters, k_sr_grid over the whole grid).
 // Products are formed in FP32 over runs of 32 terms and accumulated in FP64 (GB300's FP64 rate is far
 // below its FP32 rate); CG vectors and scalars are FP64 and stay on the device: a device flag ends the
 // iteration, the host looks at it between groups of iterations only.
@@ -81,10 +82,12 @@ __global__ void k_sr_vprep(size_t P, const double *__restrict__ v, const double2
   if (threadIdx.x == 0) { part[blockIdx.x] = a; part2[blockIdx.x] = b; }
 }
 
+// (zero, nzero: counters the next launch needs at zero, or NULL)
 __global__ void k_sr_cfin(const double *__restrict__ part, const double *__restrict__ part2, int nb,
-                          double *__restrict__ sc) {
+                          double *__restrict__ sc, unsigned *__restrict__ zero = nullptr, int nzero = 0) {
   __shared__ double sh[32];
   if (sc[S_DONE] != 0.0) return;
+  if (zero && (int)threadIdx.x < nzero) zero[threadIdx.x] = 0u;
   const double a = sum_parts(part, nb, sh);
   const double b = sum_parts(part2, nb, sh);
   if (threadIdx.x == 0) { sc[S_CR] = a; sc[S_CI] = b; }
@@ -709,6 +712,307 @@ __global__ void k_sr_wfin_dd(size_t Ns, size_t P, const double2 *__restrict__ me
   if (threadIdx.x == 0) part[blockIdx.x] = b;
 }
 
+// ---------------------------------------------------------------- one-pass product over the whole grid
+// S' v with O read from HBM once, without clusters.  G co-resident CTAs (one per SM) each own the
+// parameter slab [q SL, q SL + SL) of every row; rows go in blocks of kGR.  Warp roles in a CTA:
+//   - warp 0 (lane 0): bulk-copies the slab of every row of a block into a ring of `ns` stages;
+//   - warps 1 .. ne ("exchange"): block b belongs to warp 1 + b % ne.  It waits until every CTA has
+//     published its partials of block b (an arrival counter in global memory), sums the G partials of
+//     each row in a fixed order (every CTA gets the same bits of t_s), centres them as k_sr_tred does
+//     and hands t of the block to the compute warps through a shared-memory ring;
+//   - the other warps ("compute", 4 parameters per thread and group): at step b they form this CTA's
+//     partials of t_s = O_s . v for the rows of block b and publish them, then add Re(conj(O_sk) t_s)
+//     for the rows of block b - look from the same stage, which then goes back to the copier.
+// The exchange of block b thus has `look` steps of streaming to complete before its t is needed, and
+// the copies of the next ns - look - 1 blocks stay in flight meanwhile.  Exchange slots are reused
+// every kGPB blocks: a CTA publishes block b' only after its own w-part of block b' - 1 - look, which
+// needed every CTA's partials of that block, which each CTA published only after its w-part of
+// b' - 2 - 2 look, i.e. after it had read the partials of every block up to there; kGPB >= 2 look + 2
+// keeps a slot from being overwritten while a CTA may still read it.
+// Arithmetic: FP32 products and sums up to the CTA partial (per thread, a 32-lane tree, then the
+// compute warps in order), an FP32 sum over the G partials (G / 32 per lane, then a 32-lane tree), the
+// centring in FP64; w in FP32 runs of kRun rows accumulated in FP64 per parameter.
+// Every wait is bounded and watches the device error flag: a wait that gives up sets it, and every other
+// wait of every CTA then returns at once, so the launch ends (its results invalid) instead of hanging.
+constexpr int kGR = 8;               // sample rows per block
+constexpr int kGV = 2 * kGR;         // exchanged values per block: re, im of each row
+constexpr int kGPB = 16;             // exchange slots (counter + G x kGV partials each)
+constexpr int kGTB = 8;              // t slots in shared memory
+constexpr int kGMaxStages = 6;
+constexpr int kGLook = 2, kGExch = 4;   // blocks of lookahead; exchange warps
+constexpr int kGMaxCompute = 19;     // compute warps at most (768 threads in all)
+constexpr unsigned long long kGridWaitNs = 1000000000ull;   // a wait gives up after 1 s
+static_assert(kGPB >= 2 * kGLook + 2 && kGTB >= kGLook + kGExch && kRun % kGR == 0, "grid product rings");
+
+struct GridLayout {
+  int stage, tb, red, bars, bytes;   // bytes of one stage; byte offsets of the t ring, the warp partials
+                                     // (double-buffered) and the mbarriers; total
+};
+__host__ __device__ inline GridLayout grid_layout(int ngr, int ns, int nw) {
+  GridLayout L;
+  L.stage = kGR * 16 * ngr;   // kGR slab rows of 16 ngr bytes (every row on a 16-byte boundary)
+  L.tb = ns * L.stage;
+  L.red = L.tb + kGTB * kGR * 8;
+  L.bars = L.red + 2 * nw * kGV * 4;
+  L.bytes = L.bars + (2 * ns + 2 * kGTB) * 8;
+  return L;
+}
+
+__device__ __forceinline__ bool grid_aborted(const int *err) { return *reinterpret_cast<const volatile int *>(err) != 0; }
+__device__ __forceinline__ void mbar_arrive1(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait on a local mbarrier phase: false at once when the error flag is up (abort = true), and
+// false with the flag raised after `limit` ns.
+__device__ __forceinline__ bool grid_wait(uint32_t bar, uint32_t parity, int *err,
+                                          unsigned long long limit = kGridWaitNs, bool abort = true) {
+  if (tc::mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer_ns();
+  for (unsigned i = 1;; ++i) {
+    if (tc::mbar_try(bar, parity)) return true;
+    if ((i & 31) == 0) {
+      if (abort && grid_aborted(err)) return false;
+      if (gtimer_ns() - t0 > limit) {
+        atomicExch(err, 1);
+        return false;
+      }
+      __nanosleep(64);
+    }
+  }
+}
+// The whole warp waits until *c >= target (acquire), under the same rules.
+__device__ __forceinline__ bool grid_count_wait(const unsigned *c, unsigned target, int *err) {
+  if (__all_sync(0xffffffffu, ld_acquire_u32(c) >= target)) return true;
+  const unsigned long long t0 = gtimer_ns();
+  for (unsigned i = 1;; ++i) {
+    if (__all_sync(0xffffffffu, ld_acquire_u32(c) >= target)) return true;
+    if ((i & 31) == 0) {
+      if (__any_sync(0xffffffffu, grid_aborted(err))) return false;
+      const bool late = __shfl_sync(0xffffffffu, gtimer_ns() - t0 > kGridWaitNs ? 1 : 0, 0) != 0;
+      if (late) {
+        if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
+        return false;
+      }
+      __nanosleep(32);
+    }
+  }
+}
+// Sum over the 32 lanes of each of 16 values by recursive halving (16 shuffles): afterwards lane l holds
+// the warp's sum of value l >> 1, the same bits in lanes l and l ^ 1.
+__device__ __forceinline__ float xreduce16(float (&a)[16], int lane) {
+#pragma unroll
+  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float send = up ? a[j] : a[j + h];
+      const float keep = up ? a[j + h] : a[j];
+      a[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+// The four elements of group gi (columns 4 gi .. 4 gi + 3 of the slab), zero at and past kn: padding
+// columns are never data.
+__device__ __forceinline__ void grid_elems(const uint4 &u, int gi, int kn, float2 (&c)[4]) {
+  c[0] = cplx(u.x); c[1] = cplx(u.y); c[2] = cplx(u.z); c[3] = cplx(u.w);
+  if (4 * gi + 4 > kn)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (4 * gi + e >= kn) c[e] = make_float2(0.f, 0.f);
+}
+
+// w[k] = sum_s Re(conj(O[s][k]) t_s) for k < P and t (the centred O v, written by CTA 0).  xpart:
+// [kGPB][G][kGV] exchange partials; cnt: [kGPB] arrival counters, zero at the launch.
+template <int GPT>
+__global__ void __launch_bounds__(32 * (1 + kGExch + kGMaxCompute), 1)
+    k_sr_grid(const uint32_t *__restrict__ O, size_t Ns, size_t P, size_t ldo, int SL, int ns,
+              const float *__restrict__ vf, float2 *__restrict__ t, double *__restrict__ w,
+              float *__restrict__ xpart, unsigned *__restrict__ cnt, const double *__restrict__ sc, int *err) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  if (sc[S_DONE] != 0.0) return;   // the same value for every CTA: all of them leave here together
+  const int G = (int)gridDim.x, q = (int)blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = (int)(blockDim.x >> 5) - 1 - kGExch, nct = 32 * nw;
+  const int ngr_max = SL / 4;
+  const GridLayout L = grid_layout(ngr_max, ns, nw);
+  const size_t k0 = (size_t)q * SL;
+  const int kn = k0 < P ? (int)(P - k0 < (size_t)SL ? P - k0 : (size_t)SL) : 0;
+  const int ngr = (kn + 3) / 4;
+  const int nb = (int)((Ns + kGR - 1) / kGR);
+  const uint32_t base = tc::smem_u32(sm);
+  const uint32_t full = base + L.bars, empty = full + 8 * ns, tfull = empty + 8 * ns, tempty = tfull + 8 * kGTB;
+  float2 *tb = reinterpret_cast<float2 *>(sm + L.tb);
+  float *red = reinterpret_cast<float *>(sm + L.red);
+  if (tid == 0) {
+    for (int i = 0; i < ns; ++i) { tc::mbar_init(full + 8 * i, 1); tc::mbar_init(empty + 8 * i, (uint32_t)nw); }
+    for (int i = 0; i < kGTB; ++i) { tc::mbar_init(tfull + 8 * i, 1); tc::mbar_init(tempty + 8 * i, (uint32_t)nw); }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto rows_of = [&](int b) {
+    const size_t r0 = (size_t)b * kGR;
+    return (int)(Ns - r0 < (size_t)kGR ? Ns - r0 : (size_t)kGR);
+  };
+  if (warp == 0) {
+    if (lane == 0) {   // the copier
+      int fills[kGMaxStages];
+      for (int i = 0; i < kGMaxStages; ++i) fills[i] = 0;
+      const uint32_t rb = 16u * (uint32_t)ngr;   // bytes of one row's slab (inside the row: ldo, k0 multiples of 4)
+      for (int b = 0; b < nb; ++b) {
+        const int st = b % ns, m = b / ns;
+        if (m > 0) {   // the stage's previous block is done with; stop issuing once anything gave up
+          if (!grid_wait(empty + 8 * st, (uint32_t)((m - 1) & 1), err) || grid_aborted(err)) break;
+          tc::fence_proxy_async();
+        }
+        const int nr = rows_of(b);
+        tc::mbar_expect_tx(full + 8 * st, rb * (uint32_t)nr);
+        if (ngr > 0)
+          for (int r = 0; r < nr; ++r)
+            tc::bulk_g2s(base + (uint32_t)(st * L.stage + r * 16 * ngr_max), O + ((size_t)b * kGR + r) * ldo + k0, rb,
+                         full + 8 * st);
+        fills[st] = m + 1;
+      }
+      for (int st = 0; st < ns && st < kGMaxStages; ++st)   // no copy is still landing when the CTA exits
+        if (fills[st] > 0) grid_wait(full + 8 * st, (uint32_t)((fills[st] - 1) & 1), err, kGridWaitNs / 2, false);
+    }
+    __syncwarp();
+  } else if (warp <= kGExch) {   // an exchange warp
+    const double cr = sc[S_CR], ci = sc[S_CI];
+    for (int b = warp - 1; b < nb; b += kGExch) {
+      const int j = b % kGTB, m = b / kGTB, slot = b % kGPB;
+      if (m > 0) grid_wait(tempty + 8 * j, (uint32_t)((m - 1) & 1), err);
+      grid_count_wait(cnt + slot, (unsigned)G * (unsigned)(b / kGPB + 1), err);
+      float a[kGV];
+#pragma unroll
+      for (int x = 0; x < kGV; ++x) a[x] = 0.f;
+      const float4 *src = reinterpret_cast<const float4 *>(xpart + (size_t)slot * G * kGV);
+      for (int g = lane; g < G; g += 32) {
+#pragma unroll
+        for (int u = 0; u < kGV / 4; ++u) {
+          const float4 x = __ldcg(src + (size_t)g * (kGV / 4) + u);
+          a[4 * u] += x.x; a[4 * u + 1] += x.y; a[4 * u + 2] += x.z; a[4 * u + 3] += x.w;
+        }
+      }
+      const float s = xreduce16(a, lane);
+      const int idx = lane >> 1, r = idx >> 1, nr = rows_of(b);
+      if ((lane & 1) == 0) {
+        const float tv = r < nr ? (float)((double)s - ((idx & 1) ? ci : cr)) : 0.f;
+        reinterpret_cast<float *>(tb + j * kGR)[idx] = tv;
+        if (q == 0 && r < nr) reinterpret_cast<float *>(t + (size_t)b * kGR + r)[idx & 1] = tv;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(tfull + 8 * j);
+    }
+  } else {   // a compute warp
+    const int ct = tid - 32 * (1 + kGExch), cw = ct >> 5;
+    float v[GPT][4], f[GPT][4];
+    double wacc[GPT][4];
+#pragma unroll
+    for (int i = 0; i < GPT; ++i) {
+      const int gi = ct + nct * i;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int kk = 4 * gi + e;
+        v[i][e] = (gi < ngr && kk < kn) ? vf[k0 + kk] : 0.f;
+        f[i][e] = 0.f;
+        wacc[i][e] = 0.0;
+      }
+    }
+    for (int b = 0; b < nb + kGLook; ++b) {
+      if (b < nb) {   // this CTA's partials of t for block b
+        const int st = b % ns, nr = rows_of(b);
+        grid_wait(full + 8 * st, (uint32_t)((b / ns) & 1), err);
+        const uint4 *buf = reinterpret_cast<const uint4 *>(sm + (size_t)st * L.stage);
+        float a[kGV];
+#pragma unroll
+        for (int x = 0; x < kGV; ++x) a[x] = 0.f;
+#pragma unroll
+        for (int i = 0; i < GPT; ++i) {
+          const int gi = ct + nct * i;
+          if (gi < ngr) {
+#pragma unroll
+            for (int r = 0; r < kGR; ++r)
+              if (r < nr) {
+                float2 c[4];
+                grid_elems(buf[r * ngr_max + gi], gi, kn, c);
+                a[2 * r] = fmaf(c[0].x, v[i][0], fmaf(c[1].x, v[i][1], fmaf(c[2].x, v[i][2], fmaf(c[3].x, v[i][3], a[2 * r]))));
+                a[2 * r + 1] =
+                    fmaf(c[0].y, v[i][0], fmaf(c[1].y, v[i][1], fmaf(c[2].y, v[i][2], fmaf(c[3].y, v[i][3], a[2 * r + 1]))));
+              }
+          }
+        }
+        const float s = xreduce16(a, lane);
+        float *rb = red + (b & 1) * nw * kGV;
+        if ((lane & 1) == 0) rb[cw * kGV + (lane >> 1)] = s;
+        asm volatile("bar.sync 1, %0;" ::"r"(nct) : "memory");
+        if (cw == 0) {
+          if (lane < kGV) {
+            float x = 0.f;
+            for (int u = 0; u < nw; ++u) x += rb[u * kGV + lane];
+            xpart[((size_t)(b % kGPB) * G + q) * kGV + lane] = x;
+            __threadfence();
+          }
+          __syncwarp();
+          if (lane == 0) atomicAdd(cnt + b % kGPB, 1u);
+        }
+      }
+      const int bw = b - kGLook;
+      if (bw >= 0) {   // w over block bw, from the same stage
+        const int st = bw % ns, j = bw % kGTB, nr = rows_of(bw);
+        grid_wait(tfull + 8 * j, (uint32_t)((bw / kGTB) & 1), err);
+        const uint4 *buf = reinterpret_cast<const uint4 *>(sm + (size_t)st * L.stage);
+#pragma unroll
+        for (int r = 0; r < kGR; ++r)
+          if (r < nr) {
+            const float2 tv = tb[j * kGR + r];
+#pragma unroll
+            for (int i = 0; i < GPT; ++i) {
+              const int gi = ct + nct * i;
+              if (gi < ngr) {
+                float2 c[4];
+                grid_elems(buf[r * ngr_max + gi], gi, kn, c);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) f[i][e] = fmaf(c[e].x, tv.x, fmaf(c[e].y, tv.y, f[i][e]));
+              }
+            }
+          }
+        if ((bw + 1) % (kRun / kGR) == 0 || bw + 1 == nb)
+#pragma unroll
+          for (int i = 0; i < GPT; ++i)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              wacc[i][e] += (double)f[i][e];
+              f[i][e] = 0.f;
+            }
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive1(empty + 8 * st);
+          mbar_arrive1(tempty + 8 * j);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < GPT; ++i) {
+      const int gi = ct + nct * i;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (gi < ngr && 4 * gi + e < kn) w[k0 + 4 * gi + e] = wacc[i][e];
+    }
+  }
+  __syncthreads();
+}
+
 // alpha = r.z / p.S'p with p.S'p = (1/Ns) sum_s |t_s - tbar|^2 + shift p.p (the partials hold p.p)
 __global__ void k_sr_alpha(const double *__restrict__ part, int nb, size_t Ns, double shift, double *__restrict__ sc) {
   __shared__ double sh[32];
@@ -975,6 +1279,69 @@ static cudaError_t matvec_fused(const uint32_t *O, size_t Ns, size_t P, size_t l
   return cudaSuccess;
 }
 
+
+// The grid product's shape for this O: G CTAs (one per SM, fewer when P is small), slab SL, compute
+// warps, stages.  G = 0: not available (unaligned rows, no error flag, a slab too wide, or no room).
+struct GridPlan {
+  int G = 0, SL = 0, gpt = 0, threads = 0, ns = 0, bytes = 0;
+};
+constexpr size_t kGridXOff = 256;   // exchange partials after the counters in the moments' buffer
+static GridPlan grid_plan(const void *O, size_t Ns, size_t P, size_t ldo, const int *err) {
+  GridPlan pl;
+  if (!err || ldo % 4 != 0 || reinterpret_cast<uintptr_t>(O) % 16 != 0 || Ns == 0 || P == 0) return pl;
+  int dev = 0, smax = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return pl;
+  }
+  size_t G = (P + 255) / 256;
+  if (G > (size_t)nsm) G = (size_t)nsm;
+  if (G < 1) G = 1;
+  const size_t SL = ((P + G - 1) / G + 3) / 4 * 4;
+  const size_t ngr = SL / 4;
+  const int gpt = ngr <= 32u * kGMaxCompute ? 1 : (ngr <= 64u * kGMaxCompute ? 2 : 0);
+  if (gpt == 0) return pl;
+  const int nw = (int)((ngr + 32 * gpt - 1) / (32 * gpt));
+  int ns = kGMaxStages;
+  while (ns >= kGLook + 2 && grid_layout((int)ngr, ns, nw).bytes > smax) --ns;
+  if (ns < kGLook + 2) return pl;
+  // counters and partials live in the moments' buffer (3 kSampleGroups P doubles), free during the solve
+  if (kGridXOff + sizeof(float) * kGPB * G * kGV > 8 * 3 * (size_t)kSampleGroups * P) return pl;
+  const int bytes = grid_layout((int)ngr, ns, nw).bytes, threads = 32 * (1 + kGExch + nw);
+  const void *fn = gpt == 1 ? (const void *)k_sr_grid<1> : (const void *)k_sr_grid<2>;
+  int occ = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, bytes) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    return pl;
+  }
+  pl.G = (int)G;
+  pl.SL = (int)SL;
+  pl.gpt = gpt;
+  pl.threads = threads;
+  pl.ns = ns;
+  pl.bytes = bytes;
+  return pl;
+}
+
+// S' v -> Ap by the grid product: 5 launches, O streamed once.
+static cudaError_t matvec_grid(const uint32_t *O, size_t Ns, size_t P, size_t ldo, const double *v, double shift,
+                               SrPtrs &q, int nb, const GridPlan &pl, int *err, cudaStream_t st) {
+  k_sr_vprep<<<nb, kSrBlock, 0, st>>>(P, v, q.mean, q.vf, q.part, q.part2, q.sc);
+  unsigned *cnt = reinterpret_cast<unsigned *>(q.mpart);
+  float *xp = reinterpret_cast<float *>(reinterpret_cast<char *>(q.mpart) + kGridXOff);
+  k_sr_cfin<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc, cnt, kGPB);   // also zeroes the arrival counters
+  if (pl.gpt == 1)
+    k_sr_grid<1><<<pl.G, pl.threads, pl.bytes, st>>>(O, Ns, P, ldo, pl.SL, pl.ns, q.vf, q.t, q.wpart, xp, cnt, q.sc, err);
+  else
+    k_sr_grid<2><<<pl.G, pl.threads, pl.bytes, st>>>(O, Ns, P, ldo, pl.SL, pl.ns, q.vf, q.t, q.wpart, xp, cnt, q.sc, err);
+  k_sr_tsum<<<1, 1024, 0, st>>>(q.t, Ns, q.sc);
+  k_sr_wfin<<<nb, kSrBlock, 0, st>>>(Ns, P, q.mean, q.wpart, 1, v, shift, q.Ap, q.part, q.sc);
+  return cudaGetLastError();
+}
+
 }  // namespace tdo
 
 size_t sr_work_doubles(size_t Ns, size_t P) {
@@ -1011,11 +1378,20 @@ static cudaError_t sr_apply_t(const uint32_t *O2, size_t Ns, size_t P, size_t ld
   SrPtrs q = sr_carve(work, Ns, P);
   const int nb = sr_blocks(P);
   FusedPlan pl;
+  GridPlan gp;
   if (product_mode == 1) pl = fused_plan(O2, Ns, P, ldo);
-  if (shape) { shape[0] = pl.C > 0 ? 1 : 0; shape[1] = pl.C; shape[2] = pl.G; }
+  if (product_mode == 2) gp = grid_plan(O2, Ns, P, ldo, err);
+  if (shape) {
+    shape[0] = gp.G > 0 ? 2 : (pl.C > 0 ? 1 : 0);
+    shape[1] = gp.G > 0 ? 1 : pl.C;
+    shape[2] = gp.G > 0 ? gp.G : pl.G;
+  }
   moments(O2, Ns, P, ldo, shift, q, nb, st);
   k_sr_clear<<<1, 32, 0, st>>>(q.sc);
-  if (pl.C > 0) {
+  if (gp.G > 0) {
+    const cudaError_t e = matvec_grid(O2, Ns, P, ldo, v, shift, q, nb, gp, err, st);
+    if (e != cudaSuccess) return e;
+  } else if (pl.C > 0) {
     const cudaError_t e = matvec_fused(O2, Ns, P, ldo, v, shift, q, nb, pl, err, st);
     if (e != cudaSuccess) return e;
   } else {
@@ -1035,9 +1411,16 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const 
                            int *err, int *shape, cudaStream_t st) {
   SrPtrs q = sr_carve(work, Ns, P);
   FusedPlan pl;
-  if constexpr (sizeof(OT) == 4)
+  GridPlan gp;
+  if constexpr (sizeof(OT) == 4) {
     if (product_mode == 1) pl = fused_plan(O2, Ns, P, ldo);
-  if (shape) { shape[0] = pl.C > 0 ? 1 : 0; shape[1] = pl.C; shape[2] = pl.G; }
+    if (product_mode == 2) gp = grid_plan(O2, Ns, P, ldo, err);
+  }
+  if (shape) {
+    shape[0] = gp.G > 0 ? 2 : (pl.C > 0 ? 1 : 0);
+    shape[1] = gp.G > 0 ? 1 : pl.C;
+    shape[2] = gp.G > 0 ? gp.G : pl.G;
+  }
   const int nb = sr_blocks(P);
   long long nl = 0;
   int nmv = 0;
@@ -1046,7 +1429,11 @@ static cudaError_t sr_cg_t(const OT *O2, size_t Ns, size_t P, size_t ldo, const 
     const bool rec = mv_ev && nmv < mv_cap;
     if (rec) cudaEventRecord(mv_ev[2 * nmv], st);
     if constexpr (sizeof(OT) == 4) {
-      if (pl.C > 0) {
+      if (gp.G > 0) {
+        const cudaError_t e = matvec_grid(O2, Ns, P, ldo, v, shift, q, nb, gp, err, st);
+        if (e != cudaSuccess) return e;
+        nl += 5;
+      } else if (pl.C > 0) {
         const cudaError_t e = matvec_fused(O2, Ns, P, ldo, v, shift, q, nb, pl, err, st);
         if (e != cudaSuccess) return e;
         nl += 5;
@@ -1162,13 +1549,22 @@ static cudaError_t sr_cg_capture_t(const OT *O2, size_t Ns, size_t P, size_t ldo
                                    const int *warm, int *err, int *shape, cudaStream_t st) {
   SrPtrs q = sr_carve(work, Ns, P);
   FusedPlan pl;
-  if constexpr (sizeof(OT) == 4)
+  GridPlan gp;
+  if constexpr (sizeof(OT) == 4) {
     if (product_mode == 1) pl = fused_plan(O2, Ns, P, ldo);
-  if (shape) { shape[0] = pl.C > 0 ? 1 : 0; shape[1] = pl.C; shape[2] = pl.G; }
+    if (product_mode == 2) gp = grid_plan(O2, Ns, P, ldo, err);
+  }
+  if (shape) {
+    shape[0] = gp.G > 0 ? 2 : (pl.C > 0 ? 1 : 0);
+    shape[1] = gp.G > 0 ? 1 : pl.C;
+    shape[2] = gp.G > 0 ? gp.G : pl.G;
+  }
   const int nb = sr_blocks(P);
   auto mv = [&](const double *v, cudaStream_t s) -> cudaError_t {
-    if constexpr (sizeof(OT) == 4)
+    if constexpr (sizeof(OT) == 4) {
+      if (gp.G > 0) return matvec_grid(O2, Ns, P, ldo, v, shift, q, nb, gp, err, s);
       if (pl.C > 0) return matvec_fused(O2, Ns, P, ldo, v, shift, q, nb, pl, err, s);
+    }
     matvec(O2, Ns, P, ldo, v, shift, q, nb, s);
     return cudaSuccess;
   };
@@ -1197,10 +1593,11 @@ static cudaError_t sr_cg_capture_t(const OT *O2, size_t Ns, size_t P, size_t ldo
 // mv_ev (optional): mv_cap event pairs recorded around the S' v launches; *mv_used = pairs recorded.
 // o_bf16: O holds BF16 pairs (uint32 per element) instead of FP32 (re, im); ldo >= P: elements per row.
 // *outcome: 0 stopped at max_iter, 1 converged, 2 breakdown (p . S'p not positive), 3 a non-finite value;
-// *last_pap: the last p . S'p.  product_mode 0: two passes; 1: the one-pass product where O's storage and
-// shape allow it (BF16 pairs), else two passes.  err (device int, may be NULL): set when a bounded wait of the
-// one-pass product gave up.  shape (may be NULL): {one pass used, cluster size, clusters}.  The return
-// value reports CUDA errors only.
+// *last_pap: the last p . S'p.  product_mode 0: two passes; 1: the one-pass product on clusters, 2: the
+// one-pass product over the whole grid, each where O's storage and shape allow it (BF16 pairs; the grid
+// product also needs err), else two passes.  err (device int, may be NULL): set when a bounded wait of a
+// one-pass product gave up.  shape (may be NULL): {product used (0, 1, 2), cluster size (1 for the grid
+// product), clusters or CTAs}.  The return value reports CUDA errors only.
 cudaError_t sr_cg_impl(const void *O, int o_bf16, size_t Ns, size_t P, size_t ldo, const double *rhs, const double *x0,
                        double shift, double tol, int max_iter, double *x, double *work, int n_sm, int *iters,
                        double *resid, int *outcome, double *last_pap, long long *launches, cudaEvent_t *mv_ev,

@@ -1808,8 +1808,9 @@ extern "C" tdo_status tdo_wait_selftest(tdo_ctx *c, long long spin_limit) {
 
 extern "C" tdo_status tdo_set_sr_product(tdo_ctx *c, int mode) {
   if (!c) return TDO_EINVAL;
-  if (mode != TDO_SR_PRODUCT_TWO_PASS && mode != TDO_SR_PRODUCT_ONE_PASS)
-    return fail(c, TDO_EINVAL, "tdo_set_sr_product: mode must be TDO_SR_PRODUCT_TWO_PASS or TDO_SR_PRODUCT_ONE_PASS");
+  if (mode != TDO_SR_PRODUCT_TWO_PASS && mode != TDO_SR_PRODUCT_ONE_PASS && mode != TDO_SR_PRODUCT_GRID)
+    return fail(c, TDO_EINVAL,
+                "tdo_set_sr_product: mode must be TDO_SR_PRODUCT_TWO_PASS, TDO_SR_PRODUCT_ONE_PASS or TDO_SR_PRODUCT_GRID");
   c->sr_product = mode;
   return TDO_OK;
 }

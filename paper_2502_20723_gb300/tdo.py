@@ -376,9 +376,9 @@ class Context:
         return o.value, pap.value, r.value
 
     def set_sr_product(self, mode: str):
-        """tdo_set_sr_product: "two_pass" (default) or "one_pass" (thread-block clusters, where the
-        log-derivatives' storage allows it)."""
-        self._chk(lib().tdo_set_sr_product(self.h, {"two_pass": 0, "one_pass": 1}[mode]))
+        """tdo_set_sr_product: "two_pass" (default), "one_pass" (thread-block clusters) or "grid" (one pass
+        over the whole grid), the last two where the log-derivatives' storage allows it."""
+        self._chk(lib().tdo_set_sr_product(self.h, {"two_pass": 0, "one_pass": 1, "grid": 2}[mode]))
 
     def sr_apply(self, O_pairs, v, shift: float, out=None):
         """tdo_sr_apply: (Re S + shift I) v for log-derivatives O given as BF16 pairs (a device int32 / uint32
@@ -389,7 +389,8 @@ class Context:
         return out
 
     def sr_product_shape(self):
-        """(one pass used, CTAs per cluster, clusters) of the last SR step's products (tdo_sr_product_shape)."""
+        """(product used: 0 two passes, 1 clusters, 2 grid; CTAs per cluster; clusters or CTAs) of the last SR
+        step's products (tdo_sr_product_shape)."""
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         self._chk(lib().tdo_sr_product_shape(self.h, C.byref(a), C.byref(b), C.byref(c)))
         return a.value, b.value, c.value

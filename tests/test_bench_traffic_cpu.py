@@ -1,8 +1,11 @@
-"""The S'v roofline's `traffic` in the bench line comes from a committed ncu summary and is reported only
-while the SR source is the one that was captured (its SHA-1 recorded beside the figure); otherwise null."""
+"""The S'v roofline's `traffic` in the bench line comes from a committed ncu summary of the product in use
+(two passes or the grid product) and is reported only while the SR source is the one that was captured
+(its SHA-1 recorded beside the figure); otherwise null."""
 import importlib.util
 import os
 import shutil
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -14,11 +17,13 @@ def load_bench():
     return mod
 
 
-def test_committed_capture_matches_the_sr_source():
-    per_row, source = load_bench().sr_traffic_per_row()
+@pytest.mark.parametrize("mode,reads", [(0, 2), (2, 1)])
+def test_committed_capture_matches_the_sr_source(mode, reads):
+    per_row, source = load_bench().sr_traffic_per_row(mode=mode)
     assert per_row is not None, source
-    # one S'v product reads each BF16-pair row of O twice: 2 x 198,276 x 4 bytes, plus partial sums
-    assert 2 * 198276 * 4 <= per_row <= 1.01 * 2 * 198276 * 4
+    # one S'v product reads each BF16-pair row of O twice (two passes) or once (grid product):
+    # reads x 198,276 x 4 bytes, plus partial sums
+    assert reads * 198276 * 4 <= per_row <= 1.01 * reads * 198276 * 4
     assert "ncu" in source
 
 

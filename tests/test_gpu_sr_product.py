@@ -1,16 +1,21 @@
-"""The one-pass S'v product against the two-pass product (metric-tensor section: S v = (1/Ns) Re[Obar^H
+"""The one-pass S'v products against the two-pass product (metric-tensor section: S v = (1/Ns) Re[Obar^H
 (Obar v)] + shift v, S never formed).
 
-The one-pass product has thread-block clusters exchange t_s = O_s v in distributed shared memory and
-accumulate Re(O^H t) from the same copy of each row.  Both products run on the same tensor-core context,
-samples and parameters, and differ only in the order of the FP32 partial sums.  Checks:
+The cluster product ("one_pass") has thread-block clusters exchange t_s = O_s v in distributed shared
+memory; the grid product ("grid") has one CTA per SM own a parameter slab of every row and exchange the
+partials of t_s for each block of 8 rows through global memory.  Both accumulate Re(O^H t) from the same
+copy of each row.  All products run on the same tensor-core context, samples and parameters, and differ
+only in the order of the FP32 partial sums.  Checks:
   - two CG iterations (one full product enters the update) agree to 1e-5 relative (measured 1e-6 to
     2.3e-6: the residual update r - alpha S'p cancels, which amplifies the summation order);
   - CG to 1e-10 agrees to 1e-4 relative (the summation order, amplified by the condition number of
     S + shift I).
-The parameter counts give clusters of 1, 2, 4, 8 and 16 CTAs.  The sample counts leave clusters with
-uneven row counts, and with none (37 samples).  tdo_sr_apply, one product on its own, is compared element
-by element with the oracle's matrix-free product of the same BF16-rounded O in FP64, in both modes."""
+The parameter counts give clusters of 1, 2, 4, 8 and 16 CTAs, and grids of 17 to 152 CTAs whose last
+CTA holds a partial slab (or, at P = 49,858, no parameters at all).  The sample counts leave clusters with uneven row counts, and with none (37
+samples), and end the grid product on a partial block of rows.  tdo_sr_apply, one product on its own, is
+compared element by element with the oracle's matrix-free product of the same BF16-rounded O in FP64, in
+every mode.  The grid product also runs inside the whole-step CUDA graph: its first step there gives the
+call-by-call step's cost bit for bit and parameters within the gradient atomics' spread."""
 import numpy as np
 import pytest
 
@@ -45,11 +50,12 @@ def update(ctx, th, sig, sigp, mode, tol, iters):
     return (th - ctx.get_params()) / LR, ctx.sr_product_shape(), ctx.sr_info()[0]
 
 
+@pytest.mark.parametrize("mode", ["one_pass", "grid"])
 @pytest.mark.parametrize("d,h,L,r,Ns,C", [
     (32, 4, 1, 0, 64, 1), (64, 8, 1, 0, 96, 2), (64, 8, 1, 4, 300, 4), (64, 8, 2, 4, 37, 8),
     (64, 8, 4, 4, 512, 16),
 ])
-def test_one_pass_product_matches_two_pass(d, h, L, r, Ns, C):
+def test_one_pass_product_matches_two_pass(d, h, L, r, Ns, C, mode):
     from paper_2502_20723_gb300 import tdo
     n = 16
     spec = synth.model_spec(d, h, L, r)
@@ -59,13 +65,21 @@ def test_one_pass_product_matches_two_pass(d, h, L, r, Ns, C):
     ctx = tdo.Context(problem("ising", n), spec, th, "fp16")
     for tol, iters, bound in ((0.0, 2, 1e-5), (1e-10, 500, 1e-4)):
         d2, shape2, it2 = update(ctx, th, sig, sigp, "two_pass", tol, iters)
-        d1, shape1, it1 = update(ctx, th, sig, sigp, "one_pass", tol, iters)
+        d1, shape1, it1 = update(ctx, th, sig, sigp, mode, tol, iters)
         assert shape2 == (0, 0, 0)
-        assert shape1[0] == 1 and shape1[1] == C and 1 <= shape1[2] <= 24, shape1
+        if mode == "one_pass":
+            assert shape1[0] == 1 and shape1[1] == C and 1 <= shape1[2] <= 24, shape1
+        else:
+            assert shape1[0] == 2 and shape1[1] == 1 and shape1[2] == grid_ctas(th.size), shape1
         rel = np.linalg.norm(d1 - d2) / np.linalg.norm(d2)
         print(f"P={th.size} C={C} clusters={shape1[2]} Ns={Ns} iterations {it1}/{it2}: "
               f"relative difference {rel:.3e}")
         assert np.all(np.isfinite(d1)) and rel <= bound
+
+
+def grid_ctas(P):
+    """CTAs of the grid product: one per SM, at most one per 256 parameters."""
+    return min(torch.cuda.get_device_properties(0).multi_processor_count, (P + 255) // 256)
 
 
 NAN_PAIR = 0x7FC07FC0   # padding columns: a product that reads them as data turns non-finite
@@ -92,12 +106,40 @@ def test_sr_apply_matches_oracle_product(d, h, L, r, Ns, C):
     v = rng.standard_normal(P)
     ref = E.sr_product(O, v, SHIFT)
     got = {}
-    for mode in ("two_pass", "one_pass"):
+    for mode in ("two_pass", "one_pass", "grid"):
         ctx.set_sr_product(mode)
         got[mode] = ctx.sr_apply(pairs, torch.from_numpy(v).cuda(), SHIFT).cpu().numpy()
         shape = ctx.sr_product_shape()
-        assert shape[0] == (mode == "one_pass") and (mode != "one_pass" or shape[1] == C), shape
+        want = {"two_pass": (0, 0, 0), "one_pass": (1, C), "grid": (2, 1, grid_ctas(P))}[mode]
+        assert shape[:len(want)] == want, shape
         rel = np.linalg.norm(got[mode] - ref) / np.linalg.norm(ref)
         elem = np.abs(got[mode] - ref).max() / np.abs(ref).max()
         print(f"P={P} Ns={Ns} {mode} shape {shape}: relative error {rel:.3e}, max element error {elem:.3e}")
         assert np.all(np.isfinite(got[mode])) and rel <= 1e-5 and elem <= 1e-5
+
+
+def test_grid_product_in_step_graph():
+    """One whole-step graph launch with the grid product against the same step call by call with the grid
+    product: the cost bit for bit, the parameters within 2e-5 of the update (the gradient's float atomics;
+    the grid product itself has a fixed summation order), the same CG iteration count within one."""
+    from paper_2502_20723_gb300 import tdo
+    n, Ns = 16, 512
+    spec = synth.model_spec(64, 8, 2, 4)
+    th = synth.init_params(spec, seed=3)
+    s0, s1 = synth.random_configs(n, Ns, seed=29)
+    sched = tdo.Schedule(eta0=LR, lambda0=SHIFT)
+    res = []
+    for graph in (False, True):
+        ctx = tdo.Context(problem("ising", n), spec, th, "fp16")
+        ctx.set_sr_product("grid")
+        ctx.set_step_graph(graph)
+        sig, sigp = dev(s0), dev(s1)
+        cost, _ = ctx.vmc_step(sig, sigp, 1, 99, 7, 0, sched)
+        res.append((cost, ctx.get_params().copy(), ctx.sr_info()[0], ctx.sr_product_shape()))
+        ctx.close()
+    (ce, pe, ie, she), (cg, pg, ig, shg) = res
+    rel = np.linalg.norm(pg - pe) / np.linalg.norm(pe - th)
+    print(f"cost {cg} vs {ce}; CG iterations {ig} vs {ie}; parameters differ by {rel:.3e} of the update; "
+          f"shapes {shg} {she}")
+    assert she[0] == 2 and shg[0] == 2
+    assert cg == ce and rel <= 2e-5 and abs(ig - ie) <= 1
