@@ -315,11 +315,14 @@ tdo_status tdo_sr_report(const tdo_ctx *ctx, int *outcome, double *last_pap, int
  * (each within 3e-7 of an FP64 evaluation of the definition).
  * TDO_SR_PRODUCT_GRID: also one pass where the log-derivatives are BF16 pairs on 16-byte rows, without
  * clusters: one CTA per SM owns a parameter slab of every row; rows go in blocks of 8, bulk-copied into a
- * ring of shared-memory stages; every CTA publishes its partials of t_s for a block to global memory with
- * an arrival counter, dedicated exchange warps sum the partials of all CTAs (the same bits in every CTA)
- * while the compute warps already work two blocks ahead, and w is accumulated from the same stage.  Its
- * bounded waits watch the context's error flag (TDO_ETIMEOUT), so a launch whose CTAs cannot all run at
- * once ends with that error instead of waiting. */
+ * ring of shared-memory stages; every CTA publishes its partials of t_s for a block to global memory as
+ * tagged 64-bit words, dedicated exchange warps sum the partials of all CTAs (the same bits in every CTA)
+ * while the compute warps work eight blocks ahead; w is accumulated from a second copy of each block,
+ * served from L2, so DRAM reads O once.  On a GB300 at the headline shape it measured 4.50 ms per product
+ * against 4.08 ms for two passes: one CTA unpacks and multiplies every element twice within one read's
+ * time, and the SM's instruction issue, not DRAM, bounds it; it is kept as an option.  Its bounded waits
+ * watch the context's error flag (TDO_ETIMEOUT), so a launch whose CTAs cannot all run at once ends with
+ * that error instead of waiting. */
 enum { TDO_SR_PRODUCT_TWO_PASS = 0, TDO_SR_PRODUCT_ONE_PASS = 1, TDO_SR_PRODUCT_GRID = 2 };
 tdo_status tdo_set_sr_product(tdo_ctx *ctx, int mode);
 

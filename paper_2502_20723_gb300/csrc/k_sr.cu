@@ -65,11 +65,15 @@ __device__ __forceinline__ double sum_parts(const double *part, int n, double *s
 
 // vf = (float) v; block partials of mean . vf (re, im).  The centring term takes the same rounded copy
 // as the t-pass, so t = (O - mean) vf holds up to the products' rounding.
+// (zero, nzero: 16-byte words the next launch needs at zero, or NULL)
 __global__ void k_sr_vprep(size_t P, const double *__restrict__ v, const double2 *__restrict__ mean,
                            float *__restrict__ vf, double *__restrict__ part, double *__restrict__ part2,
-                           const double *__restrict__ sc) {
+                           const double *__restrict__ sc, uint4 *__restrict__ zero = nullptr, size_t nzero = 0) {
   __shared__ double sh[32];
   if (sc[S_DONE] != 0.0) return;
+  if (zero)
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nzero; i += gridDim.x * (size_t)blockDim.x)
+      zero[i] = make_uint4(0u, 0u, 0u, 0u);
   double cr = 0.0, ci = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P; k += gridDim.x * (size_t)blockDim.x) {
     const float xf = (float)v[k];
@@ -82,12 +86,10 @@ __global__ void k_sr_vprep(size_t P, const double *__restrict__ v, const double2
   if (threadIdx.x == 0) { part[blockIdx.x] = a; part2[blockIdx.x] = b; }
 }
 
-// (zero, nzero: counters the next launch needs at zero, or NULL)
 __global__ void k_sr_cfin(const double *__restrict__ part, const double *__restrict__ part2, int nb,
-                          double *__restrict__ sc, unsigned *__restrict__ zero = nullptr, int nzero = 0) {
+                          double *__restrict__ sc) {
   __shared__ double sh[32];
   if (sc[S_DONE] != 0.0) return;
-  if (zero && (int)threadIdx.x < nzero) zero[threadIdx.x] = 0u;
   const double a = sum_parts(part, nb, sh);
   const double b = sum_parts(part2, nb, sh);
   if (threadIdx.x == 0) { sc[S_CR] = a; sc[S_CI] = b; }
@@ -715,20 +717,29 @@ __global__ void k_sr_wfin_dd(size_t Ns, size_t P, const double2 *__restrict__ me
 // ---------------------------------------------------------------- one-pass product over the whole grid
 // S' v with O read from HBM once, without clusters.  G co-resident CTAs (one per SM) each own the
 // parameter slab [q SL, q SL + SL) of every row; rows go in blocks of kGR.  Warp roles in a CTA:
-//   - warp 0 (lane 0): bulk-copies the slab of every row of a block into a ring of `ns` stages;
-//   - warps 1 .. ne ("exchange"): block b belongs to warp 1 + b % ne.  It waits until every CTA has
-//     published its partials of block b (an arrival counter in global memory), sums the G partials of
-//     each row in a fixed order (every CTA gets the same bits of t_s), centres them as k_sr_tred does
-//     and hands t of the block to the compute warps through a shared-memory ring;
-//   - the other warps ("compute", 4 parameters per thread and group): at step b they form this CTA's
-//     partials of t_s = O_s . v for the rows of block b and publish them, then add Re(conj(O_sk) t_s)
-//     for the rows of block b - look from the same stage, which then goes back to the copier.
-// The exchange of block b thus has `look` steps of streaming to complete before its t is needed, and
-// the copies of the next ns - look - 1 blocks stay in flight meanwhile.  Exchange slots are reused
-// every kGPB blocks: a CTA publishes block b' only after its own w-part of block b' - 1 - look, which
-// needed every CTA's partials of that block, which each CTA published only after its w-part of
-// b' - 2 - 2 look, i.e. after it had read the partials of every block up to there; kGPB >= 2 look + 2
-// keeps a slot from being overwritten while a CTA may still read it.
+//   - warp 0 (lane 0): bulk-copies the slab of every row of a block from HBM into the t ring (ns1
+//     shared-memory stages), for the partials of t;
+//   - warp 1 (lane 0): bulk-copies the same slab again, kGLook blocks later, into the w ring (ns2
+//     stages).  Between the two reads the GPU streams about kGLook blocks (8 x 6.3 MB at the headline
+//     shape), far less than the 129 MB L2, so the second copy is served from L2 (evict-first hint: the
+//     line is not needed again) and DRAM sees O once;
+//   - the compute warps (4 parameters per thread and group): at step b they form their partials of
+//     t_s = O_s . v for the rows of block b from the t ring and leave them in shared memory, then add
+//     Re(conj(O_sk) t_s) for the rows of block b - kGLook from the w ring;
+//   - warp 2 ("publisher"): sums the compute warps' partials of block b and stores this CTA's 16 values
+//     (re, im of 8 rows) to the block's exchange slot in global memory, each as one 64-bit word with the
+//     block's tag in its high half, so a reader that sees the tag sees the value (no fence, no counter);
+//   - warps 3 .. 2 + kGExch ("exchange"): block b belongs to one of them in turn.  Once its own CTA has
+//     published kGAhead blocks further (an mbarrier: the warp sleeps, it does not spin), it reads the G
+//     CTAs' words of block b, again after a pause until every tag is there, sums them in a fixed order (every CTA gets the same bits of t_s), centres them as k_sr_tred
+//     does and hands t of the block to the compute warps through a shared-memory ring.
+// So the exchange of a block has kGLook steps of streaming to complete before its t is needed, and the
+// compute warps never wait on global memory.  At the headline shape shared memory holds three HBM
+// stages and two L2 stages of 42 KB.  The exchange slots are cleared before the launch (tag 0;
+// tags are b + 1) and reused every kGPB blocks: a CTA publishes block b' only after its own w-part of
+// block b' - 1 - kGLook, which needed every CTA's words of that block, which each CTA published only
+// after its w-part of b' - 2 - 2 kGLook, i.e. after it had read every block up to there; kGPB >= 2 kGLook
+// + 2 keeps a slot from being overwritten while a CTA may still read it.
 // Arithmetic: FP32 products and sums up to the CTA partial (per thread, a 32-lane tree, then the
 // compute warps in order), an FP32 sum over the G partials (G / 32 per lane, then a 32-lane tree), the
 // centring in FP64; w in FP32 runs of kRun rows accumulated in FP64 per parameter.
@@ -736,36 +747,35 @@ __global__ void k_sr_wfin_dd(size_t Ns, size_t P, const double2 *__restrict__ me
 // wait of every CTA then returns at once, so the launch ends (its results invalid) instead of hanging.
 constexpr int kGR = 8;               // sample rows per block
 constexpr int kGV = 2 * kGR;         // exchanged values per block: re, im of each row
-constexpr int kGPB = 16;             // exchange slots (counter + G x kGV partials each)
-constexpr int kGTB = 8;              // t slots in shared memory
-constexpr int kGMaxStages = 6;
-constexpr int kGLook = 2, kGExch = 4;   // blocks of lookahead; exchange warps
-constexpr int kGMaxCompute = 19;     // compute warps at most (768 threads in all)
+constexpr int kGLook = 8, kGExch = 6;   // blocks between a block's t-part and its w-part; exchange warps
+constexpr int kGAhead = 2;           // blocks this CTA has published beyond the one an exchange warp reads
+constexpr int kGPB = 32;             // exchange slots (G x kGV tagged words each)
+constexpr int kGTB = 16;             // t slots in shared memory
+constexpr int kGRB = 4;              // slots of the compute warps' partials in shared memory
+constexpr int kGMaxStages = 6;       // stages of either ring at most
+constexpr int kGMaxCompute = 16;     // compute warps at most (800 threads in all)
+constexpr int kGRoles = 3 + kGExch;  // copiers, publisher, exchange warps
 constexpr unsigned long long kGridWaitNs = 1000000000ull;   // a wait gives up after 1 s
 static_assert(kGPB >= 2 * kGLook + 2 && kGTB >= kGLook + kGExch && kRun % kGR == 0, "grid product rings");
 
 struct GridLayout {
-  int stage, tb, red, bars, bytes;   // bytes of one stage; byte offsets of the t ring, the warp partials
-                                     // (double-buffered) and the mbarriers; total
+  int stage, wring, tb, red, bars, bytes;   // bytes of one stage; byte offsets of the w ring, the t slots,
+                                            // the warp partials and the mbarriers; total
 };
-__host__ __device__ inline GridLayout grid_layout(int ngr, int ns, int nw) {
+__host__ __device__ inline GridLayout grid_layout(int ngr, int ns1, int ns2, int nw) {
   GridLayout L;
   L.stage = kGR * 16 * ngr;   // kGR slab rows of 16 ngr bytes (every row on a 16-byte boundary)
-  L.tb = ns * L.stage;
+  L.wring = ns1 * L.stage;
+  L.tb = L.wring + ns2 * L.stage;
   L.red = L.tb + kGTB * kGR * 8;
-  L.bars = L.red + 2 * nw * kGV * 4;
-  L.bytes = L.bars + (2 * ns + 2 * kGTB) * 8;
+  L.bars = L.red + kGRB * nw * kGV * 4;
+  L.bytes = L.bars + (2 * ns1 + 2 * ns2 + 3 * kGTB + 2 * kGRB) * 8;
   return L;
 }
 
 __device__ __forceinline__ bool grid_aborted(const int *err) { return *reinterpret_cast<const volatile int *>(err) != 0; }
 __device__ __forceinline__ void mbar_arrive1(uint32_t a) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
 }
 __device__ __forceinline__ unsigned long long gtimer_ns() {
   unsigned long long t;
@@ -790,28 +800,13 @@ __device__ __forceinline__ bool grid_wait(uint32_t bar, uint32_t parity, int *er
     }
   }
 }
-// The whole warp waits until *c >= target (acquire), under the same rules.
-__device__ __forceinline__ bool grid_count_wait(const unsigned *c, unsigned target, int *err) {
-  if (__all_sync(0xffffffffu, ld_acquire_u32(c) >= target)) return true;
-  const unsigned long long t0 = gtimer_ns();
-  for (unsigned i = 1;; ++i) {
-    if (__all_sync(0xffffffffu, ld_acquire_u32(c) >= target)) return true;
-    if ((i & 31) == 0) {
-      if (__any_sync(0xffffffffu, grid_aborted(err))) return false;
-      const bool late = __shfl_sync(0xffffffffu, gtimer_ns() - t0 > kGridWaitNs ? 1 : 0, 0) != 0;
-      if (late) {
-        if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
-        return false;
-      }
-      __nanosleep(32);
-    }
-  }
-}
-// Sum over the 32 lanes of each of 16 values by recursive halving (16 shuffles): afterwards lane l holds
-// the warp's sum of value l >> 1, the same bits in lanes l and l ^ 1.
-__device__ __forceinline__ float xreduce16(float (&a)[16], int lane) {
+// Sum over the 32 lanes of each of NV values (NV = 2, 4, ..., 32) by recursive halving (NV - 1 + 5 -
+// log2 NV shuffles): afterwards lane l holds the warp's sum of value l / (32 / NV), the same bits in all
+// 32 / NV lanes that hold it.
+template <int NV>
+__device__ __forceinline__ float xreduce(float (&a)[NV], int lane) {
 #pragma unroll
-  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+  for (int h = NV / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
     const bool up = (lane & o) != 0;
 #pragma unroll
     for (int j = 0; j < h; ++j) {
@@ -820,7 +815,10 @@ __device__ __forceinline__ float xreduce16(float (&a)[16], int lane) {
       a[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
+  float x = a[0];
+#pragma unroll
+  for (int o = 16 / NV; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
 }
 // The four elements of group gi (columns 4 gi .. 4 gi + 3 of the slab), zero at and past kn: padding
 // columns are never data.
@@ -832,31 +830,56 @@ __device__ __forceinline__ void grid_elems(const uint4 &u, int gi, int kn, float
       if (4 * gi + e >= kn) c[e] = make_float2(0.f, 0.f);
 }
 
-// w[k] = sum_s Re(conj(O[s][k]) t_s) for k < P and t (the centred O v, written by CTA 0).  xpart:
-// [kGPB][G][kGV] exchange partials; cnt: [kGPB] arrival counters, zero at the launch.
+// One row's slab into shared memory with an L2 evict-first policy (a copy whose lines are not read again).
+__device__ __forceinline__ void bulk_g2s_evict_first(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
+                                                     uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+      : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ ulonglong2 ld_relaxed_u64x2(const unsigned long long *p) {
+  ulonglong2 v;
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+  return v;
+}
+
+// w[k] = sum_s Re(conj(O[s][k]) t_s) for k < P and t (the centred O v, written by CTA 0).  xw:
+// [kGPB][G][kGV] tagged exchange words, all zero at the launch.
 template <int GPT>
-__global__ void __launch_bounds__(32 * (1 + kGExch + kGMaxCompute), 1)
-    k_sr_grid(const uint32_t *__restrict__ O, size_t Ns, size_t P, size_t ldo, int SL, int ns,
+__global__ void __launch_bounds__(32 * (kGRoles + kGMaxCompute), 1)
+    k_sr_grid(const uint32_t *__restrict__ O, size_t Ns, size_t P, size_t ldo, int SL, int ns1, int ns2,
               const float *__restrict__ vf, float2 *__restrict__ t, double *__restrict__ w,
-              float *__restrict__ xpart, unsigned *__restrict__ cnt, const double *__restrict__ sc, int *err) {
+              unsigned long long *__restrict__ xw, const double *__restrict__ sc, int *err) {
   extern __shared__ __align__(16) uint8_t sm[];
   if (sc[S_DONE] != 0.0) return;   // the same value for every CTA: all of them leave here together
   const int G = (int)gridDim.x, q = (int)blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nw = (int)(blockDim.x >> 5) - 1 - kGExch, nct = 32 * nw;
+  const int nw = (int)(blockDim.x >> 5) - kGRoles;
   const int ngr_max = SL / 4;
-  const GridLayout L = grid_layout(ngr_max, ns, nw);
+  const GridLayout L = grid_layout(ngr_max, ns1, ns2, nw);
   const size_t k0 = (size_t)q * SL;
   const int kn = k0 < P ? (int)(P - k0 < (size_t)SL ? P - k0 : (size_t)SL) : 0;
   const int ngr = (kn + 3) / 4;
   const int nb = (int)((Ns + kGR - 1) / kGR);
   const uint32_t base = tc::smem_u32(sm);
-  const uint32_t full = base + L.bars, empty = full + 8 * ns, tfull = empty + 8 * ns, tempty = tfull + 8 * kGTB;
+  // mbarriers: t ring full / empty, w ring full / empty, t slots full / empty, partial slots full / empty,
+  // block b published (slot b % kGTB)
+  const uint32_t tf = base + L.bars, te = tf + 8 * ns1, wf = te + 8 * ns1, we = wf + 8 * ns2, xf = we + 8 * ns2,
+                 xe = xf + 8 * kGTB, pf = xe + 8 * kGTB, pe = pf + 8 * kGRB, pb = pe + 8 * kGRB;
   float2 *tb = reinterpret_cast<float2 *>(sm + L.tb);
   float *red = reinterpret_cast<float *>(sm + L.red);
   if (tid == 0) {
-    for (int i = 0; i < ns; ++i) { tc::mbar_init(full + 8 * i, 1); tc::mbar_init(empty + 8 * i, (uint32_t)nw); }
-    for (int i = 0; i < kGTB; ++i) { tc::mbar_init(tfull + 8 * i, 1); tc::mbar_init(tempty + 8 * i, (uint32_t)nw); }
+    for (int i = 0; i < ns1; ++i) { tc::mbar_init(tf + 8 * i, 1); tc::mbar_init(te + 8 * i, (uint32_t)nw); }
+    for (int i = 0; i < ns2; ++i) { tc::mbar_init(wf + 8 * i, 1); tc::mbar_init(we + 8 * i, (uint32_t)nw); }
+    for (int i = 0; i < kGTB; ++i) { tc::mbar_init(xf + 8 * i, 1); tc::mbar_init(xe + 8 * i, (uint32_t)nw); }
+    for (int i = 0; i < kGRB; ++i) { tc::mbar_init(pf + 8 * i, (uint32_t)nw); tc::mbar_init(pe + 8 * i, 1); }
+    for (int i = 0; i < kGTB; ++i) tc::mbar_init(pb + 8 * i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -864,8 +887,13 @@ __global__ void __launch_bounds__(32 * (1 + kGExch + kGMaxCompute), 1)
     const size_t r0 = (size_t)b * kGR;
     return (int)(Ns - r0 < (size_t)kGR ? Ns - r0 : (size_t)kGR);
   };
-  if (warp == 0) {
-    if (lane == 0) {   // the copier
+  if (warp <= 1) {
+    if (lane == 0) {   // a copier: warp 0 fills the t ring, warp 1 the w ring
+      const int ns = warp == 0 ? ns1 : ns2;
+      const uint32_t full = warp == 0 ? tf : wf, empty = warp == 0 ? te : we;
+      const uint32_t ring = base + (uint32_t)(warp == 0 ? 0 : L.wring);
+      uint64_t pol = 0;
+      if (warp == 1) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
       int fills[kGMaxStages];
       for (int i = 0; i < kGMaxStages; ++i) fills[i] = 0;
       const uint32_t rb = 16u * (uint32_t)ngr;   // bytes of one row's slab (inside the row: ldo, k0 multiples of 4)
@@ -878,44 +906,81 @@ __global__ void __launch_bounds__(32 * (1 + kGExch + kGMaxCompute), 1)
         const int nr = rows_of(b);
         tc::mbar_expect_tx(full + 8 * st, rb * (uint32_t)nr);
         if (ngr > 0)
-          for (int r = 0; r < nr; ++r)
-            tc::bulk_g2s(base + (uint32_t)(st * L.stage + r * 16 * ngr_max), O + ((size_t)b * kGR + r) * ldo + k0, rb,
-                         full + 8 * st);
+          for (int r = 0; r < nr; ++r) {
+            const uint32_t dst = ring + (uint32_t)(st * L.stage + r * 16 * ngr_max);
+            const uint32_t *src = O + ((size_t)b * kGR + r) * ldo + k0;
+            if (warp == 0) tc::bulk_g2s(dst, src, rb, full + 8 * st);
+            else bulk_g2s_evict_first(dst, src, rb, full + 8 * st, pol);
+          }
         fills[st] = m + 1;
       }
       for (int st = 0; st < ns && st < kGMaxStages; ++st)   // no copy is still landing when the CTA exits
         if (fills[st] > 0) grid_wait(full + 8 * st, (uint32_t)((fills[st] - 1) & 1), err, kGridWaitNs / 2, false);
     }
     __syncwarp();
-  } else if (warp <= kGExch) {   // an exchange warp
-    const double cr = sc[S_CR], ci = sc[S_CI];
-    for (int b = warp - 1; b < nb; b += kGExch) {
-      const int j = b % kGTB, m = b / kGTB, slot = b % kGPB;
-      if (m > 0) grid_wait(tempty + 8 * j, (uint32_t)((m - 1) & 1), err);
-      grid_count_wait(cnt + slot, (unsigned)G * (unsigned)(b / kGPB + 1), err);
-      float a[kGV];
-#pragma unroll
-      for (int x = 0; x < kGV; ++x) a[x] = 0.f;
-      const float4 *src = reinterpret_cast<const float4 *>(xpart + (size_t)slot * G * kGV);
-      for (int g = lane; g < G; g += 32) {
-#pragma unroll
-        for (int u = 0; u < kGV / 4; ++u) {
-          const float4 x = __ldcg(src + (size_t)g * (kGV / 4) + u);
-          a[4 * u] += x.x; a[4 * u + 1] += x.y; a[4 * u + 2] += x.z; a[4 * u + 3] += x.w;
-        }
+  } else if (warp == 2) {   // the publisher
+    for (int b = 0; b < nb; ++b) {
+      const int rs = b % kGRB;
+      grid_wait(pf + 8 * rs, (uint32_t)((b / kGRB) & 1), err);
+      if (lane < kGV) {
+        const float *rb = red + rs * nw * kGV;
+        float x = 0.f;
+        for (int u = 0; u < nw; ++u) x += rb[u * kGV + lane];
+        st_relaxed_u64(xw + ((size_t)(b % kGPB) * G + q) * kGV + lane,
+                       (unsigned long long)__float_as_uint(x) | ((unsigned long long)(unsigned)(b + 1) << 32));
       }
-      const float s = xreduce16(a, lane);
-      const int idx = lane >> 1, r = idx >> 1, nr = rows_of(b);
-      if ((lane & 1) == 0) {
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive1(pe + 8 * rs);
+        mbar_arrive1(pb + 8 * (b % kGTB));
+      }
+    }
+  } else if (warp < kGRoles) {   // an exchange warp
+    const double cr = sc[S_CR], ci = sc[S_CI];
+    for (int b = warp - 3; b < nb; b += kGExch) {
+      const int j = b % kGTB, m = b / kGTB, slot = b % kGPB;
+      if (m > 0) grid_wait(xe + 8 * j, (uint32_t)((m - 1) & 1), err);
+      // this CTA has published block c (the other CTAs are about as far): the words of b are likely in
+      const int c = b + kGAhead < nb ? b + kGAhead : nb - 1;
+      grid_wait(pb + 8 * (c % kGTB), (uint32_t)((c / kGTB) & 1), err);
+      const unsigned tag = (unsigned)(b + 1);
+      const unsigned long long *src = xw + (size_t)slot * G * kGV;
+      float a[kGV];
+      const unsigned long long t0 = gtimer_ns();
+      for (unsigned it = 0;; ++it) {   // every word of the block, in a fixed order, until all tags are in
+        bool ready = true;
+#pragma unroll
+        for (int x = 0; x < kGV; ++x) a[x] = 0.f;
+        for (int g = lane; g < G; g += 32) {
+#pragma unroll
+          for (int u = 0; u < kGV / 2; ++u) {
+            const ulonglong2 x = ld_relaxed_u64x2(src + (size_t)g * kGV + 2 * u);
+            ready = ready && (unsigned)(x.x >> 32) == tag && (unsigned)(x.y >> 32) == tag;
+            a[2 * u] += __uint_as_float((unsigned)x.x);
+            a[2 * u + 1] += __uint_as_float((unsigned)x.y);
+          }
+        }
+        if (__all_sync(0xffffffffu, ready)) break;
+        if (__any_sync(0xffffffffu, grid_aborted(err))) break;
+        if (__shfl_sync(0xffffffffu, gtimer_ns() - t0 > kGridWaitNs ? 1 : 0, 0)) {
+          if (lane == 0) atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(256);
+      }
+      const float s = xreduce<kGV>(a, lane);
+      constexpr int span = 32 / kGV;   // lanes holding each value
+      const int idx = lane / span, r = idx >> 1, nr = rows_of(b);
+      if (lane % span == 0) {
         const float tv = r < nr ? (float)((double)s - ((idx & 1) ? ci : cr)) : 0.f;
         reinterpret_cast<float *>(tb + j * kGR)[idx] = tv;
         if (q == 0 && r < nr) reinterpret_cast<float *>(t + (size_t)b * kGR + r)[idx & 1] = tv;
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive1(tfull + 8 * j);
+      if (lane == 0) mbar_arrive1(xf + 8 * j);
     }
   } else {   // a compute warp
-    const int ct = tid - 32 * (1 + kGExch), cw = ct >> 5;
+    const int ct = tid - 32 * kGRoles, cw = ct >> 5, nct = 32 * nw;
     float v[GPT][4], f[GPT][4];
     double wacc[GPT][4];
 #pragma unroll
@@ -930,9 +995,9 @@ __global__ void __launch_bounds__(32 * (1 + kGExch + kGMaxCompute), 1)
       }
     }
     for (int b = 0; b < nb + kGLook; ++b) {
-      if (b < nb) {   // this CTA's partials of t for block b
-        const int st = b % ns, nr = rows_of(b);
-        grid_wait(full + 8 * st, (uint32_t)((b / ns) & 1), err);
+      if (b < nb) {   // this warp's partials of t for block b, from the t ring, to the publisher
+        const int st = b % ns1, nr = rows_of(b);
+        grid_wait(tf + 8 * st, (uint32_t)((b / ns1) & 1), err);
         const uint4 *buf = reinterpret_cast<const uint4 *>(sm + (size_t)st * L.stage);
         float a[kGV];
 #pragma unroll
@@ -952,26 +1017,21 @@ __global__ void __launch_bounds__(32 * (1 + kGExch + kGMaxCompute), 1)
               }
           }
         }
-        const float s = xreduce16(a, lane);
-        float *rb = red + (b & 1) * nw * kGV;
-        if ((lane & 1) == 0) rb[cw * kGV + (lane >> 1)] = s;
-        asm volatile("bar.sync 1, %0;" ::"r"(nct) : "memory");
-        if (cw == 0) {
-          if (lane < kGV) {
-            float x = 0.f;
-            for (int u = 0; u < nw; ++u) x += rb[u * kGV + lane];
-            xpart[((size_t)(b % kGPB) * G + q) * kGV + lane] = x;
-            __threadfence();
-          }
-          __syncwarp();
-          if (lane == 0) atomicAdd(cnt + b % kGPB, 1u);
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive1(te + 8 * st);   // this warp is done with the stage
+        const float s = xreduce<kGV>(a, lane);
+        const int rs = b % kGRB;
+        if (b >= kGRB) grid_wait(pe + 8 * rs, (uint32_t)((b / kGRB - 1) & 1), err);
+        if (lane % (32 / kGV) == 0) red[(rs * nw + cw) * kGV + lane / (32 / kGV)] = s;
+        __syncwarp();
+        if (lane == 0) mbar_arrive1(pf + 8 * rs);
       }
       const int bw = b - kGLook;
-      if (bw >= 0) {   // w over block bw, from the same stage
-        const int st = bw % ns, j = bw % kGTB, nr = rows_of(bw);
-        grid_wait(tfull + 8 * j, (uint32_t)((bw / kGTB) & 1), err);
-        const uint4 *buf = reinterpret_cast<const uint4 *>(sm + (size_t)st * L.stage);
+      if (bw >= 0) {   // w over block bw, from the w ring
+        const int st = bw % ns2, j = bw % kGTB, nr = rows_of(bw);
+        grid_wait(xf + 8 * j, (uint32_t)((bw / kGTB) & 1), err);
+        grid_wait(wf + 8 * st, (uint32_t)((bw / ns2) & 1), err);
+        const uint4 *buf = reinterpret_cast<const uint4 *>(sm + (size_t)L.wring + (size_t)st * L.stage);
 #pragma unroll
         for (int r = 0; r < kGR; ++r)
           if (r < nr) {
@@ -997,8 +1057,8 @@ __global__ void __launch_bounds__(32 * (1 + kGExch + kGMaxCompute), 1)
             }
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive1(empty + 8 * st);
-          mbar_arrive1(tempty + 8 * j);
+          mbar_arrive1(we + 8 * st);
+          mbar_arrive1(xe + 8 * j);
         }
       }
     }
@@ -1283,9 +1343,8 @@ static cudaError_t matvec_fused(const uint32_t *O, size_t Ns, size_t P, size_t l
 // The grid product's shape for this O: G CTAs (one per SM, fewer when P is small), slab SL, compute
 // warps, stages.  G = 0: not available (unaligned rows, no error flag, a slab too wide, or no room).
 struct GridPlan {
-  int G = 0, SL = 0, gpt = 0, threads = 0, ns = 0, bytes = 0;
+  int G = 0, SL = 0, gpt = 0, threads = 0, ns1 = 0, ns2 = 0, bytes = 0;
 };
-constexpr size_t kGridXOff = 256;   // exchange partials after the counters in the moments' buffer
 static GridPlan grid_plan(const void *O, size_t Ns, size_t P, size_t ldo, const int *err) {
   GridPlan pl;
   if (!err || ldo % 4 != 0 || reinterpret_cast<uintptr_t>(O) % 16 != 0 || Ns == 0 || P == 0) return pl;
@@ -1304,12 +1363,19 @@ static GridPlan grid_plan(const void *O, size_t Ns, size_t P, size_t ldo, const 
   const int gpt = ngr <= 32u * kGMaxCompute ? 1 : (ngr <= 64u * kGMaxCompute ? 2 : 0);
   if (gpt == 0) return pl;
   const int nw = (int)((ngr + 32 * gpt - 1) / (32 * gpt));
-  int ns = kGMaxStages;
-  while (ns >= kGLook + 2 && grid_layout((int)ngr, ns, nw).bytes > smax) --ns;
-  if (ns < kGLook + 2) return pl;
-  // counters and partials live in the moments' buffer (3 kSampleGroups P doubles), free during the solve
-  if (kGridXOff + sizeof(float) * kGPB * G * kGV > 8 * 3 * (size_t)kSampleGroups * P) return pl;
-  const int bytes = grid_layout((int)ngr, ns, nw).bytes, threads = 32 * (1 + kGExch + nw);
+  // t ring: the block being read and at least one landing; w ring: the same
+  static const int shapes[][2] = {{6, 4}, {5, 4}, {5, 3}, {4, 3}, {3, 2}, {2, 2}};
+  int ns1 = 0, ns2 = 0;
+  for (const auto &sh : shapes)
+    if (grid_layout((int)ngr, sh[0], sh[1], nw).bytes <= smax) {
+      ns1 = sh[0];
+      ns2 = sh[1];
+      break;
+    }
+  if (ns1 == 0) return pl;
+  // the exchange words live in the moments' buffer (3 kSampleGroups P doubles), free during the solve
+  if (sizeof(unsigned long long) * kGPB * G * kGV > 8 * 3 * (size_t)kSampleGroups * P) return pl;
+  const int bytes = grid_layout((int)ngr, ns1, ns2, nw).bytes, threads = 32 * (kGRoles + nw);
   const void *fn = gpt == 1 ? (const void *)k_sr_grid<1> : (const void *)k_sr_grid<2>;
   int occ = 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
@@ -1321,7 +1387,8 @@ static GridPlan grid_plan(const void *O, size_t Ns, size_t P, size_t ldo, const 
   pl.SL = (int)SL;
   pl.gpt = gpt;
   pl.threads = threads;
-  pl.ns = ns;
+  pl.ns1 = ns1;
+  pl.ns2 = ns2;
   pl.bytes = bytes;
   return pl;
 }
@@ -1329,14 +1396,16 @@ static GridPlan grid_plan(const void *O, size_t Ns, size_t P, size_t ldo, const 
 // S' v -> Ap by the grid product: 5 launches, O streamed once.
 static cudaError_t matvec_grid(const uint32_t *O, size_t Ns, size_t P, size_t ldo, const double *v, double shift,
                                SrPtrs &q, int nb, const GridPlan &pl, int *err, cudaStream_t st) {
-  k_sr_vprep<<<nb, kSrBlock, 0, st>>>(P, v, q.mean, q.vf, q.part, q.part2, q.sc);
-  unsigned *cnt = reinterpret_cast<unsigned *>(q.mpart);
-  float *xp = reinterpret_cast<float *>(reinterpret_cast<char *>(q.mpart) + kGridXOff);
-  k_sr_cfin<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc, cnt, kGPB);   // also zeroes the arrival counters
+  unsigned long long *xw = reinterpret_cast<unsigned long long *>(q.mpart);
+  const size_t nx = (size_t)kGPB * pl.G * kGV;
+  // also clears the exchange words (tag 0) for the grid kernel
+  k_sr_vprep<<<nb, kSrBlock, 0, st>>>(P, v, q.mean, q.vf, q.part, q.part2, q.sc, reinterpret_cast<uint4 *>(xw),
+                                      nx / 2);
+  k_sr_cfin<<<1, 1024, 0, st>>>(q.part, q.part2, nb, q.sc);
   if (pl.gpt == 1)
-    k_sr_grid<1><<<pl.G, pl.threads, pl.bytes, st>>>(O, Ns, P, ldo, pl.SL, pl.ns, q.vf, q.t, q.wpart, xp, cnt, q.sc, err);
+    k_sr_grid<1><<<pl.G, pl.threads, pl.bytes, st>>>(O, Ns, P, ldo, pl.SL, pl.ns1, pl.ns2, q.vf, q.t, q.wpart, xw, q.sc, err);
   else
-    k_sr_grid<2><<<pl.G, pl.threads, pl.bytes, st>>>(O, Ns, P, ldo, pl.SL, pl.ns, q.vf, q.t, q.wpart, xp, cnt, q.sc, err);
+    k_sr_grid<2><<<pl.G, pl.threads, pl.bytes, st>>>(O, Ns, P, ldo, pl.SL, pl.ns1, pl.ns2, q.vf, q.t, q.wpart, xw, q.sc, err);
   k_sr_tsum<<<1, 1024, 0, st>>>(q.t, Ns, q.sc);
   k_sr_wfin<<<nb, kSrBlock, 0, st>>>(Ns, P, q.mean, q.wpart, 1, v, shift, q.Ap, q.part, q.sc);
   return cudaGetLastError();

@@ -137,7 +137,10 @@ def test_graph_adam_and_host_chains():
     res = []
     for graph in (False, True):
         ctx = tdo.Context(problem("ising", n), spec, th, "fp16")
-        ctx.set_optimizer("adam")
+        # eps above the gradient atomics' noise on delta: with eps = 1e-8 the first Adam update is
+        # lr sign(delta_k), and a component of delta within that noise of zero flips sign between any two
+        # runs (measured: a change of about 2 lr in one parameter, 9.2e-3 of the update norm at P = 49,858)
+        ctx.set_optimizer("adam", 0.9, 0.999, 1e-3)
         res.append(run(ctx, s0, s1, 3, sched, graph, host=graph))
     assert compare(res[0], res[1], th) <= 2
 
