@@ -11,7 +11,8 @@ update theta_k - theta_0 after steps 1, 2, 3; graph against call-by-call: 4.0e-6
 2.1e-4.  The growth is the optimisation's, not the graph's: each step's gradient depends on the last
 step's parameters, a CG that crosses its tolerance one iteration earlier changes the update by about
 that tolerance, and Adam divides by the square root of small second moments (2.2e-3 after two Adam
-steps has been seen between the modes).  So, from the same parameters and chains:
+steps, and 9.2e-3 after one, have been seen between the modes: Adam's own bounds are 2e-2, 5e-2, 1e-1 of
+the update).  So, from the same parameters and chains:
   - the first step is deterministic up to the first gradient's atomics: the same cost bit for bit, the
     parameters within 2e-5 of the update;
   - over three steps the chains stay equal (the Metropolis decisions replay; a decision whose margin is
@@ -63,9 +64,14 @@ def run(ctx, s0, s1, steps, sched, graph, host=False, counter=7):
 
 
 PARAM_BOUND = (2e-5, 1e-2, 5e-2)
+# Adam divides each component of the SR direction by its own magnitude (plus eps), so a component within
+# the gradient atomics' noise of zero moves by up to 2 lr between any two runs: measured 9.2e-3 of the update
+# norm after step 1 at P = 49,858 (one such component).  A wrong bias correction 1 - beta^t changes every
+# component by tens of per cent, far above these bounds.
+ADAM_PARAM_BOUND = (2e-2, 5e-2, 1e-1)
 
 
-def compare(eager, graph, theta0):
+def compare(eager, graph, theta0, bounds=PARAM_BOUND):
     differing = 0
     for k, ((ce, ke, ie, he, pe), (cg, kg, ig, hg, pg)) in enumerate(zip(eager, graph)):
         assert ke == kg
@@ -76,7 +82,7 @@ def compare(eager, graph, theta0):
         rel = np.linalg.norm(pg - pe) / np.linalg.norm(pe - theta0)
         print(f"step {k + 1}: cost {cg:.8f} vs {ce:.8f}, CG iterations {ig} vs {ie}, parameters differ by "
               f"{rel:.3e} of the update")
-        assert rel <= PARAM_BOUND[k], rel
+        assert rel <= bounds[k], rel
         assert abs(ig - ie) <= 2, (ig, ie)
     return differing
 
@@ -137,12 +143,9 @@ def test_graph_adam_and_host_chains():
     res = []
     for graph in (False, True):
         ctx = tdo.Context(problem("ising", n), spec, th, "fp16")
-        # eps above the gradient atomics' noise on delta: with eps = 1e-8 the first Adam update is
-        # lr sign(delta_k), and a component of delta within that noise of zero flips sign between any two
-        # runs (measured: a change of about 2 lr in one parameter, 9.2e-3 of the update norm at P = 49,858)
-        ctx.set_optimizer("adam", 0.9, 0.999, 1e-3)
+        ctx.set_optimizer("adam")
         res.append(run(ctx, s0, s1, 3, sched, graph, host=graph))
-    assert compare(res[0], res[1], th) <= 2
+    assert compare(res[0], res[1], th, ADAM_PARAM_BOUND) <= 2
 
 
 def test_graph_nonfinite_parameters_leave_the_rest_unchanged():
