@@ -320,7 +320,7 @@ tdo_status tdo_sr_report(const tdo_ctx *ctx, int *outcome, double *last_pap, int
  * while the compute warps work eight blocks ahead; w is accumulated from a second copy of each block,
  * served from L2, so DRAM reads O once.  On a GB300 at the headline shape it measured 4.50 ms per product
  * against 4.08 ms for two passes: one CTA unpacks and multiplies every element twice within one read's
- * time, and the SM's instruction issue, not DRAM, bounds it; it is kept as an option.  Its bounded waits
+ * time, so the SM side, not DRAM, bounds it; it is kept as an option.  Its bounded waits
  * watch the context's error flag (TDO_ETIMEOUT), so a launch whose CTAs cannot all run at once ends with
  * that error instead of waiting. */
 enum { TDO_SR_PRODUCT_TWO_PASS = 0, TDO_SR_PRODUCT_ONE_PASS = 1, TDO_SR_PRODUCT_GRID = 2 };
